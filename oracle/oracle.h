@@ -1,0 +1,93 @@
+/*
+ * CPU oracle for the tensor-query-processor hot path -- TEST INFRASTRUCTURE.
+ *
+ * Only the tests, the smoke check and the benchmark's CPU-baseline leg may
+ * call this code.  It shares nothing with the CUDA library (no header, no
+ * helper, no table): it restates, row at a time, what the paper's relational
+ * operators compute (Section 5: filter, expressions, hash/sort equi-join,
+ * sort-based group-by aggregation) so that the GPU results can be checked
+ * element by element.
+ *
+ * All arithmetic is exact int64 with overflow detection; AVG is the single
+ * IEEE double division (double)SUM / (double)COUNT.
+ */
+#ifndef TQP_ORACLE_H
+#define TQP_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define OR_OK 0
+#define OR_ERR_INVALID 1
+#define OR_ERR_CAPACITY 4
+#define OR_ERR_OVERFLOW 5
+#define OR_ERR_NOMEM 6
+
+/* column element types */
+#define OR_I32 0
+#define OR_I64 1
+#define OR_U8 2
+
+/* comparison operators; BETWEEN is inclusive on both ends */
+#define OR_LT 0
+#define OR_LE 1
+#define OR_GT 2
+#define OR_GE 3
+#define OR_EQ 4
+#define OR_NE 5
+#define OR_BETWEEN 6
+
+/* postfix expression opcodes */
+#define OR_X_COL 0
+#define OR_X_CONST 1
+#define OR_X_ADD 2
+#define OR_X_SUB 3
+#define OR_X_MUL 4
+
+/* aggregate functions */
+#define OR_SUM 0
+#define OR_COUNT 1
+#define OR_AVG 2
+
+#define OR_MAX_EXPR 8
+
+typedef struct { const void* data; int32_t type; int32_t pad; } or_col;
+typedef struct { int32_t col; int32_t op; int64_t lo; int64_t hi; } or_pred;
+typedef struct { int32_t n; int32_t kind[OR_MAX_EXPR]; int64_t v[OR_MAX_EXPR]; } or_expr;
+typedef struct { int32_t fn; int32_t pad; or_expr expr; } or_agg;
+
+/*
+ * A query plan over a fact table and an optional dimension table:
+ *   filter(fact, preds) -> [equi-join fact.fact_fk = dim.dim_key]
+ *   -> [ungrouped SUM(sum_expr)] -> [GROUP BY group_cols: aggs] -> [top-k].
+ * Column indices in group_cols and in expressions address the concatenation
+ * (fact columns, then dim columns).  Predicates address fact columns only.
+ */
+typedef struct {
+    int64_t nfact; const or_col* fact; int32_t nfact_cols; int32_t pad0;
+    const or_pred* preds; int32_t npreds; int32_t pad1;
+    int64_t ndim; const or_col* dim; int32_t ndim_cols;   /* ndim_cols == 0: no join */
+    int32_t fact_fk; int32_t dim_key; int32_t pad2;
+    const int32_t* group_cols; int32_t ngc; int32_t pad3;
+    const or_agg* aggs; int32_t naggs; int32_t pad4;
+    const or_expr* sum_expr;                              /* NULL: no ungrouped sum */
+    int32_t topk; int32_t topk_agg;                       /* topk == 0: keep all groups */
+} or_plan;
+
+typedef struct {
+    int32_t* row_ids; int64_t cap_rows; int64_t num_rows;        /* surviving fact rows, ascending */
+    int32_t* pair_fact; int32_t* pair_dim; int64_t cap_pairs; int64_t num_pairs;
+    int64_t sum;
+    int64_t* keys; int64_t* ivals; double* fvals; int64_t cap_groups;
+    int64_t num_groups; int64_t total_groups;
+} or_out;
+
+int oracle_plan(const or_plan* plan, or_out* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

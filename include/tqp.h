@@ -1,0 +1,280 @@
+/*
+ * tqp.h -- C ABI of libtqp, a GB300 (sm_103a) library of columnar relational
+ * operators: the data-parallel hot path of a tensor query processor
+ * ("Query Processing on Tensor Computation Runtimes", VLDB 2022).
+ *
+ * Data model (paper Section 4.1): a table is a set of equally long columns,
+ * one dense array per column, rows identified by position ("virtual ids").
+ * Numeric columns only: int32, int64 and uint8.  Decimals are int64 fixed
+ * point (value x 10^scale) so every sum is an exact integer; dates are int32
+ * day numbers.
+ *
+ * Conventions for every entry point
+ *   - Pointers named d_* and every column's `data` are DEVICE pointers on the
+ *     context's device; the structs themselves (tqp_table, tqp_pred, ...) are
+ *     HOST memory read during the call only.
+ *   - The caller owns all inputs and outputs.  The library owns only the
+ *     context's scratch arena (hash tables, scan status words, partials),
+ *     which is either caller-provided device memory or allocated once at
+ *     context creation.
+ *   - Calls are asynchronous and stream-ordered on `stream` (a cudaStream_t;
+ *     NULL = legacy default stream).  Result counts are written to device
+ *     memory: no hidden host synchronisation (contrast the size-syncing
+ *     nonzero/masked_select of the paper's Section 6.5).
+ *   - The return value reports argument/launch errors found on the host.
+ *     Errors found on the device (output capacity exceeded, a bounded wait
+ *     that expired) are latched in the context and returned, then cleared,
+ *     by tqp_ctx_check().
+ *   - Column data must be 16-byte aligned (as from cudaMalloc / torch); this
+ *     lets the scans stage tiles with bulk asynchronous copies.
+ *   - A context serialises its scratch use: two calls on one context must not
+ *     overlap on the device (same stream, or ordered streams).  Use one
+ *     context per concurrent stream.
+ *   - Functions never abort or throw; tqp_last_error() gives the message of
+ *     the last failing call on this host thread.
+ */
+#ifndef TQP_H
+#define TQP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TQP_VERSION 100 /* 1.0.0 */
+
+#if defined(__GNUC__)
+#define TQP_API __attribute__((visibility("default")))
+#else
+#define TQP_API
+#endif
+
+typedef enum {
+    TQP_OK = 0,
+    TQP_ERR_INVALID_ARG = 1,   /* bad pointer, size, index, enum or alignment */
+    TQP_ERR_UNSUPPORTED = 2,   /* valid request outside what the kernels implement */
+    TQP_ERR_OUT_OF_MEMORY = 3, /* scratch arena too small (message says how much is needed) */
+    TQP_ERR_CAPACITY = 4,      /* an output or hash table was too small; counts still exact */
+    TQP_ERR_OVERFLOW = 5,      /* reserved: int64 overflow (inputs are required not to overflow) */
+    TQP_ERR_TIMEOUT = 6,       /* a bounded device-side wait expired; results are invalid */
+    TQP_ERR_CUDA = 7           /* a CUDA runtime call failed (message has the CUDA error) */
+} tqp_status;
+
+typedef enum { TQP_I32 = 0, TQP_I64 = 1, TQP_U8 = 2 } tqp_dtype;
+
+/* One column: device pointer to num_rows elements of `type`; `scale` is the
+ * decimal exponent of a fixed-point column (informational; arithmetic is on
+ * the stored integers). */
+typedef struct {
+    const void* data;
+    int32_t type;
+    int32_t scale;
+} tqp_column;
+
+typedef struct {
+    int64_t num_rows;         /* < 2^31 (row ids are int32) */
+    int32_t num_cols;
+    int32_t reserved;
+    const tqp_column* cols;   /* host array of num_cols columns */
+} tqp_table;
+
+/* Comparison predicates (paper Section 3.1 / 5.1); a list of predicates is
+ * their conjunction.  Comparisons are on the column value widened to int64.
+ * BETWEEN is inclusive: lo <= x <= hi. */
+typedef enum { TQP_LT = 0, TQP_LE, TQP_GT, TQP_GE, TQP_EQ, TQP_NE, TQP_BETWEEN } tqp_cmp;
+
+typedef struct {
+    int32_t col;   /* column index in the table */
+    int32_t op;    /* tqp_cmp */
+    int64_t lo;    /* operand (lower bound for BETWEEN) */
+    int64_t hi;    /* upper bound for BETWEEN, ignored otherwise */
+} tqp_pred;
+
+#define TQP_MAX_PREDS 8
+#define TQP_MAX_EXPR 8
+#define TQP_MAX_GROUP_COLS 4
+#define TQP_MAX_AGGS 8
+#define TQP_MAX_COLS 16
+
+/* Arithmetic expressions (paper Section 5.1: post-order traversal of the
+ * expression tree): a postfix program of at most 8 tokens over int64, stack
+ * depth at most 4.  TQP_X_COL pushes column v (for plans: fact columns first,
+ * then dimension columns), TQP_X_CONST pushes v, ADD/SUB/MUL pop b then a and
+ * push a op b.  Results must not overflow int64. */
+typedef enum { TQP_X_COL = 0, TQP_X_CONST, TQP_X_ADD, TQP_X_SUB, TQP_X_MUL } tqp_xop;
+
+typedef struct {
+    int32_t n;
+    int32_t op[TQP_MAX_EXPR];
+    int64_t v[TQP_MAX_EXPR];
+} tqp_expr;
+
+/* Aggregates (paper Section 5.4, Algorithm 3): SUM(expr) and COUNT(*) are
+ * exact int64; AVG(expr) is the IEEE double division SUM/COUNT. */
+typedef enum { TQP_SUM = 0, TQP_COUNT, TQP_AVG } tqp_aggfn;
+
+typedef struct {
+    int32_t fn;      /* tqp_aggfn */
+    int32_t reserved;
+    tqp_expr expr;   /* ignored for COUNT */
+} tqp_agg;
+
+typedef struct tqp_ctx tqp_ctx;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device`.  If d_arena is non-NULL it is a
+ * caller-owned device buffer of arena_bytes used as scratch (the library
+ * allocates nothing); if NULL the library cudaMallocs arena_bytes once and
+ * frees it in tqp_ctx_destroy.  *out receives the context. */
+TQP_API tqp_status tqp_ctx_create(int device, void* d_arena, size_t arena_bytes, tqp_ctx** out);
+TQP_API tqp_status tqp_ctx_destroy(tqp_ctx* ctx);
+
+/* Synchronise `stream`, then return (and clear) the first device-side error
+ * latched by calls on this context since the last check. */
+TQP_API tqp_status tqp_ctx_check(tqp_ctx* ctx, void* stream);
+
+/* Iteration cap of every device-side spin wait issued by calls on this
+ * context (default 1<<22 polls with back-off, well under a second).  After
+ * the cap a wait gives up and latches TQP_ERR_TIMEOUT. */
+TQP_API tqp_status tqp_ctx_set_wait_limit(tqp_ctx* ctx, int64_t polls);
+
+/* Scratch bytes of the context's arena. */
+TQP_API size_t tqp_ctx_arena_bytes(const tqp_ctx* ctx);
+
+/* Override the scan launch shape used by this context's calls: rows per
+ * tile (a multiple of 1024, at most 8192), pipeline stages (2..4) and CTAs
+ * per SM (1..2).  All zero restores the built-in choice.  Used by the
+ * autotuner and by tuning sweeps; results never depend on it. */
+TQP_API tqp_status tqp_ctx_set_tuning(tqp_ctx* ctx, int32_t tile_rows, int32_t stages, int32_t ctas_per_sm);
+
+TQP_API const char* tqp_last_error(void);
+TQP_API const char* tqp_status_string(tqp_status s);
+TQP_API int tqp_version(void);
+
+/* ---- operators ---------------------------------------------------------- */
+
+/*
+ * tqp_filter -- predicate evaluation with stream compaction and an optional
+ * fused projection-sum (paper Section 3.1, Listing 1 and the selection-vector
+ * form; expressions Section 5.1).
+ *
+ *   d_row_ids[0..k)  ascending int32 ids of the rows where every predicate
+ *                    holds (may be NULL: count and sum only); at most
+ *                    `capacity` ids are written.
+ *   *d_count         k, the exact number of passing rows (device int64).
+ *   *d_sum           SUM(sum_expr) over passing rows (device int64); both
+ *                    sum_expr and d_sum NULL to skip.
+ *
+ * k > capacity latches TQP_ERR_CAPACITY (ids beyond capacity are dropped;
+ * *d_count stays exact).  npreds may be 0 (every row passes).
+ */
+TQP_API tqp_status tqp_filter(tqp_ctx* ctx, const tqp_table* t,
+                      const tqp_pred* preds, int32_t npreds,
+                      const tqp_expr* sum_expr, int64_t* d_sum,
+                      int32_t* d_row_ids, int64_t capacity, int64_t* d_count,
+                      void* stream);
+
+/*
+ * tqp_groupby_agg -- hash group-by aggregation over the rows passing `preds`
+ * (paper Section 5.4, Algorithm 3 semantics: one output row per distinct key
+ * tuple, keys in ascending lexicographic order of the int64-widened values).
+ *
+ *   group_cols[0..ngc)  key column indices, 0 <= ngc <= 4; the key tuple's
+ *                       total width (8 bits per uint8, 32 per int32, 64 per
+ *                       int64 column) must be <= 64 bits.  ngc == 0 gives a
+ *                       single ungrouped output row (COUNT 0 / AVG NaN if no
+ *                       row passes).
+ *   d_keys   [G][ngc]   int64 key values, row-major        (may be NULL)
+ *   d_ivals  [G][naggs] SUM -> sum, COUNT -> count, AVG -> sum
+ *   d_fvals  [G][naggs] AVG -> (double)sum/(double)count, others 0.0
+ *                       (may be NULL when no AVG is requested)
+ *   *d_num_groups       G (device int64)
+ *
+ * capacity_groups bounds G and sizes the internal hash table; more groups
+ * latch TQP_ERR_CAPACITY and set *d_num_groups to -1.
+ */
+TQP_API tqp_status tqp_groupby_agg(tqp_ctx* ctx, const tqp_table* t,
+                           const tqp_pred* preds, int32_t npreds,
+                           const int32_t* group_cols, int32_t ngc,
+                           const tqp_agg* aggs, int32_t naggs,
+                           int64_t* d_keys, int64_t* d_ivals, double* d_fvals,
+                           int64_t capacity_groups, int64_t* d_num_groups,
+                           void* stream);
+
+/*
+ * tqp_hash_join -- inner equi-join build.key = probe.key returning index
+ * pairs (late materialisation, paper Sections 5.2-5.3; Algorithm 2's
+ * semantics, computed with an open-addressing table instead of collision
+ * rounds).  Keys must be int32 or int64 columns.
+ *
+ *   (d_build_idx[i], d_probe_idx[i])  the i-th matching pair, in canonical
+ *                       order: probe index ascending, then build index
+ *                       ascending; at most `capacity` pairs are written.
+ *   *d_count            exact number of pairs (device int64); more than
+ *                       capacity latches TQP_ERR_CAPACITY.
+ * Duplicate keys are allowed on both sides.
+ */
+TQP_API tqp_status tqp_hash_join(tqp_ctx* ctx,
+                         const tqp_table* build, int32_t build_key,
+                         const tqp_table* probe, int32_t probe_key,
+                         int32_t* d_build_idx, int32_t* d_probe_idx,
+                         int64_t capacity, int64_t* d_count, void* stream);
+
+/* ---- fixed operator plans ------------------------------------------------ */
+
+/*
+ * A fixed query plan (the executor of paper Section 4.2.5 runs a plan's
+ * operators in topological order; this is one fixed shape of such a plan):
+ *
+ *   scan(fact) -> filter(preds) -> [hash join fact.fact_fk = dim.dim_key]
+ *     -> [SUM(sum_expr)] -> [GROUP BY group_cols: aggs] -> [top-k]
+ *
+ * Column indices in group_cols and in expressions address fact columns
+ * 0..F-1 and then dim columns F..F+D-1.  With a join, each passing fact row
+ * contributes once per matching dim row.  topk > 0 keeps the k groups with
+ * the largest aggregate `topk_agg` (ties: smaller key first), in that order.
+ */
+typedef struct {
+    const tqp_table* fact;
+    tqp_pred preds[TQP_MAX_PREDS];
+    int32_t npreds;
+    int32_t emit_row_ids;       /* write passing fact row ids (ascending) */
+    const tqp_table* dim;       /* NULL: no join */
+    int32_t fact_fk;
+    int32_t dim_key;
+    int32_t group_cols[TQP_MAX_GROUP_COLS];
+    int32_t ngc;
+    int32_t naggs;
+    tqp_agg aggs[TQP_MAX_AGGS];
+    int32_t has_sum;            /* ungrouped SUM(sum_expr) over joined rows */
+    int32_t topk;               /* 0 = all groups in key order */
+    tqp_expr sum_expr;
+    int32_t topk_agg;
+    int32_t reserved;
+} tqp_plan;
+
+typedef struct {
+    int32_t* d_row_ids;        int64_t capacity_rows;   int64_t* d_num_rows;   /* passing fact rows */
+    int64_t* d_sum;                                                          /* ungrouped sum */
+    int64_t* d_keys;           int64_t* d_ivals;        double* d_fvals;
+    int64_t capacity_groups;   int64_t* d_num_groups;   int64_t* d_total_groups;
+    int64_t* d_num_joined;                                                   /* joined rows */
+} tqp_result;
+
+/* Run one plan.  All outputs are device pointers (any may be NULL when the
+ * plan does not produce it); capacity rules as in the operator calls. */
+TQP_API tqp_status tqp_run_plan(tqp_ctx* ctx, const tqp_plan* plan, const tqp_result* res, void* stream);
+
+/* Run n independent plans as one batch: every plan's work is cut into tiles
+ * that one persistent kernel launch drains from a device work queue (the
+ * paper runs queries one at a time, Section 4.3).  Results are identical to
+ * n calls of tqp_run_plan. */
+TQP_API tqp_status tqp_run_plans(tqp_ctx* ctx, const tqp_plan* plans, const tqp_result* res, int32_t n, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TQP_H */

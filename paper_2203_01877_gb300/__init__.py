@@ -1,0 +1,314 @@
+"""Python binding of libtqp (GB300 columnar relational operators).
+
+Thin ctypes marshalling over the C ABI in ``include/tqp.h``: every function
+here has the name of the C entry point it calls and only converts Python
+values (torch CUDA tensors, tuples) into the C structs.  All computation runs
+in the CUDA kernels of ``libtqp.so``; there is no CPU fallback -- importing
+works without the library, but every call raises if it is missing.
+
+Plan vocabulary (shared with the tests):
+
+* predicates ``(col, op, lo[, hi])`` with op in ``lt le gt ge eq ne between``;
+* expressions: postfix token lists ``("col", i)``, ``("const", v)``, ``"add"``,
+  ``"sub"``, ``"mul"``;
+* aggregates ``(fn, expr)`` with fn in ``sum count avg``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtqp.so")
+_LOCK = threading.Lock()
+_LIB = None
+
+OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_OUT_OF_MEMORY, ERR_CAPACITY, ERR_OVERFLOW, ERR_TIMEOUT, ERR_CUDA = range(8)
+I32, I64, U8 = 0, 1, 2
+MAX_PREDS, MAX_EXPR, MAX_GROUP_COLS, MAX_AGGS, MAX_COLS = 8, 8, 4, 8, 16
+_OPS = {"lt": 0, "le": 1, "gt": 2, "ge": 3, "eq": 4, "ne": 5, "between": 6}
+_XOPS = {"col": 0, "const": 1, "add": 2, "sub": 3, "mul": 4}
+_FNS = {"sum": 0, "count": 1, "avg": 2}
+
+
+class TqpError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"tqp status {status}: {msg}")
+        self.status = status
+
+
+class Column(C.Structure):
+    _fields_ = [("data", C.c_void_p), ("type", C.c_int32), ("scale", C.c_int32)]
+
+
+class Table(C.Structure):
+    _fields_ = [("num_rows", C.c_int64), ("num_cols", C.c_int32), ("reserved", C.c_int32),
+                ("cols", C.POINTER(Column))]
+
+
+class Pred(C.Structure):
+    _fields_ = [("col", C.c_int32), ("op", C.c_int32), ("lo", C.c_int64), ("hi", C.c_int64)]
+
+
+class Expr(C.Structure):
+    _fields_ = [("n", C.c_int32), ("op", C.c_int32 * MAX_EXPR), ("v", C.c_int64 * MAX_EXPR)]
+
+
+class Agg(C.Structure):
+    _fields_ = [("fn", C.c_int32), ("reserved", C.c_int32), ("expr", Expr)]
+
+
+class Plan(C.Structure):
+    _fields_ = [("fact", C.POINTER(Table)),
+                ("preds", Pred * MAX_PREDS), ("npreds", C.c_int32), ("emit_row_ids", C.c_int32),
+                ("dim", C.POINTER(Table)), ("fact_fk", C.c_int32), ("dim_key", C.c_int32),
+                ("group_cols", C.c_int32 * MAX_GROUP_COLS), ("ngc", C.c_int32), ("naggs", C.c_int32),
+                ("aggs", Agg * MAX_AGGS),
+                ("has_sum", C.c_int32), ("topk", C.c_int32),
+                ("sum_expr", Expr),
+                ("topk_agg", C.c_int32), ("reserved", C.c_int32)]
+
+
+class Result(C.Structure):
+    _fields_ = [("d_row_ids", C.c_void_p), ("capacity_rows", C.c_int64), ("d_num_rows", C.c_void_p),
+                ("d_sum", C.c_void_p),
+                ("d_keys", C.c_void_p), ("d_ivals", C.c_void_p), ("d_fvals", C.c_void_p),
+                ("capacity_groups", C.c_int64), ("d_num_groups", C.c_void_p), ("d_total_groups", C.c_void_p),
+                ("d_num_joined", C.c_void_p)]
+
+
+_P = C.c_void_p
+_SIGS = {
+    "tqp_ctx_create": (C.c_int, [C.c_int, _P, C.c_size_t, C.POINTER(_P)]),
+    "tqp_ctx_destroy": (C.c_int, [_P]),
+    "tqp_ctx_check": (C.c_int, [_P, _P]),
+    "tqp_ctx_set_wait_limit": (C.c_int, [_P, C.c_int64]),
+    "tqp_ctx_arena_bytes": (C.c_size_t, [_P]),
+    "tqp_ctx_set_tuning": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32]),
+    "tqp_last_error": (C.c_char_p, []),
+    "tqp_status_string": (C.c_char_p, [C.c_int]),
+    "tqp_version": (C.c_int, []),
+    "tqp_filter": (C.c_int, [_P, C.POINTER(Table), C.POINTER(Pred), C.c_int32, C.POINTER(Expr), _P, _P,
+                             C.c_int64, _P, _P]),
+    "tqp_groupby_agg": (C.c_int, [_P, C.POINTER(Table), C.POINTER(Pred), C.c_int32, C.POINTER(C.c_int32),
+                                  C.c_int32, C.POINTER(Agg), C.c_int32, _P, _P, _P, C.c_int64, _P, _P]),
+    "tqp_hash_join": (C.c_int, [_P, C.POINTER(Table), C.c_int32, C.POINTER(Table), C.c_int32, _P, _P,
+                                C.c_int64, _P, _P]),
+    "tqp_run_plan": (C.c_int, [_P, C.POINTER(Plan), C.POINTER(Result), _P]),
+    "tqp_run_plans": (C.c_int, [_P, C.POINTER(Plan), C.POINTER(Result), C.c_int32, _P]),
+}
+
+
+def lib():
+    """Load libtqp.so (raises if it has not been built)."""
+    global _LIB
+    with _LOCK:
+        if _LIB is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libtqp.so not built ({LIB_PATH}); run __graft_entry__.build()")
+            L = C.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(L, name, None)
+                if f is None:
+                    continue
+                f.restype = res
+                f.argtypes = args
+            _LIB = L
+    return _LIB
+
+
+def _check(status: int):
+    if status != OK:
+        raise TqpError(status, lib().tqp_last_error().decode())
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dtype_code(t) -> int:
+    import torch
+    m = {torch.int32: I32, torch.int64: I64, torch.uint8: U8}
+    if t.dtype not in m:
+        raise TypeError(f"unsupported column dtype {t.dtype}")
+    return m[t.dtype]
+
+
+class TableRef:
+    """A tqp_table over CUDA tensors (keeps the tensors and C structs alive)."""
+
+    def __init__(self, cols, scales=None):
+        cols = list(cols)
+        if not cols:
+            raise ValueError("a table needs at least one column")
+        n = cols[0].numel()
+        for c in cols:
+            if not c.is_cuda or not c.is_contiguous() or c.numel() != n:
+                raise ValueError("columns must be contiguous CUDA tensors of equal length")
+        self.tensors = cols
+        self.carr = (Column * len(cols))()
+        for i, c in enumerate(cols):
+            self.carr[i].data = c.data_ptr()
+            self.carr[i].type = _dtype_code(c)
+            self.carr[i].scale = (scales[i] if scales else 0)
+        self.t = Table(n, len(cols), 0, self.carr)
+
+    @property
+    def num_rows(self):
+        return self.t.num_rows
+
+    def ref(self):
+        return C.byref(self.t)
+
+
+def make_expr(tokens) -> Expr:
+    e = Expr()
+    toks = list(tokens)
+    if len(toks) > MAX_EXPR:
+        raise ValueError("expression longer than 8 tokens")
+    e.n = len(toks)
+    for i, tk in enumerate(toks):
+        if isinstance(tk, str):
+            e.op[i] = _XOPS[tk]
+        else:
+            e.op[i] = _XOPS[tk[0]]
+            e.v[i] = int(tk[1])
+    return e
+
+
+def make_preds(preds):
+    arr = (Pred * max(1, len(preds)))()
+    for i, (c, op, lo, *hi) in enumerate(preds):
+        arr[i].col, arr[i].op, arr[i].lo = int(c), _OPS[op], int(lo)
+        arr[i].hi = int(hi[0]) if hi else 0
+    return arr
+
+
+def make_aggs(aggs):
+    arr = (Agg * max(1, len(aggs)))()
+    for i, (fn, ex) in enumerate(aggs):
+        arr[i].fn = _FNS[fn]
+        if ex is not None:
+            arr[i].expr = make_expr(ex)
+    return arr
+
+
+class Context:
+    """A libtqp context; the scratch arena is a torch CUDA allocation."""
+
+    def __init__(self, device: int = 0, arena_bytes: int = 1 << 30):
+        import torch
+        self.device = device
+        self.arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device=f"cuda:{device}")
+        h = C.c_void_p()
+        _check(lib().tqp_ctx_create(device, C.c_void_p(self.arena.data_ptr()), int(arena_bytes), C.byref(h)))
+        self.h = h
+
+    def check(self, stream=None):
+        _check(lib().tqp_ctx_check(self.h, _stream(stream)))
+
+    def status(self, stream=None) -> int:
+        """Like check(), but returns the status code instead of raising."""
+        return lib().tqp_ctx_check(self.h, _stream(stream))
+
+    def set_tuning(self, tile_rows: int = 0, stages: int = 0, ctas_per_sm: int = 0):
+        _check(lib().tqp_ctx_set_tuning(self.h, int(tile_rows), int(stages), int(ctas_per_sm)))
+
+    def set_wait_limit(self, polls: int):
+        _check(lib().tqp_ctx_set_wait_limit(self.h, int(polls)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().tqp_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---- entry points (same names as the C ABI) ---------------------------------
+
+def tqp_filter(ctx: Context, table: TableRef, preds=(), sum_expr=None, d_sum=None, d_row_ids=None,
+               capacity: int = 0, d_count=None, stream=None):
+    pa = make_preds(preds)
+    se = C.byref(make_expr(sum_expr)) if sum_expr is not None else None
+    _check(lib().tqp_filter(ctx.h, table.ref(), pa, len(preds), se, _ptr(d_sum), _ptr(d_row_ids),
+                            int(capacity), _ptr(d_count), _stream(stream)))
+
+
+def tqp_groupby_agg(ctx: Context, table: TableRef, preds, group_cols, aggs, d_keys, d_ivals, d_fvals,
+                    capacity_groups: int, d_num_groups, stream=None):
+    pa = make_preds(preds)
+    gc = (C.c_int32 * max(1, len(group_cols)))(*[int(c) for c in group_cols])
+    ag = make_aggs(aggs)
+    _check(lib().tqp_groupby_agg(ctx.h, table.ref(), pa, len(preds), gc, len(group_cols), ag, len(aggs),
+                                 _ptr(d_keys), _ptr(d_ivals), _ptr(d_fvals), int(capacity_groups),
+                                 _ptr(d_num_groups), _stream(stream)))
+
+
+def tqp_hash_join(ctx: Context, build: TableRef, build_key: int, probe: TableRef, probe_key: int,
+                  d_build_idx, d_probe_idx, capacity: int, d_count, stream=None):
+    _check(lib().tqp_hash_join(ctx.h, build.ref(), int(build_key), probe.ref(), int(probe_key),
+                               _ptr(d_build_idx), _ptr(d_probe_idx), int(capacity), _ptr(d_count),
+                               _stream(stream)))
+
+
+def make_plan(fact: TableRef, preds=(), dim: TableRef | None = None, fact_fk=0, dim_key=0, group_cols=(),
+              aggs=(), sum_expr=None, topk=0, topk_agg=0, emit_row_ids=False) -> Plan:
+    p = Plan()
+    p.fact = C.pointer(fact.t)
+    if len(preds) > MAX_PREDS or len(group_cols) > MAX_GROUP_COLS or len(aggs) > MAX_AGGS:
+        raise ValueError("plan exceeds the fixed plan limits")
+    pa = make_preds(preds)
+    for i in range(len(preds)):
+        p.preds[i] = pa[i]
+    p.npreds = len(preds)
+    p.emit_row_ids = int(bool(emit_row_ids))
+    p.dim = C.pointer(dim.t) if dim is not None else None
+    p.fact_fk, p.dim_key = int(fact_fk), int(dim_key)
+    for i, c in enumerate(group_cols):
+        p.group_cols[i] = int(c)
+    p.ngc = len(group_cols)
+    ag = make_aggs(aggs)
+    for i in range(len(aggs)):
+        p.aggs[i] = ag[i]
+    p.naggs = len(aggs)
+    if sum_expr is not None:
+        p.has_sum = 1
+        p.sum_expr = make_expr(sum_expr)
+    p.topk, p.topk_agg = int(topk), int(topk_agg)
+    p._keep = (fact, dim)  # keep the tables' C structs alive
+    return p
+
+
+def make_result(d_row_ids=None, capacity_rows=0, d_num_rows=None, d_sum=None, d_keys=None, d_ivals=None,
+                d_fvals=None, capacity_groups=0, d_num_groups=None, d_total_groups=None,
+                d_num_joined=None) -> Result:
+    r = Result(_ptr(d_row_ids), int(capacity_rows), _ptr(d_num_rows), _ptr(d_sum), _ptr(d_keys), _ptr(d_ivals),
+               _ptr(d_fvals), int(capacity_groups), _ptr(d_num_groups), _ptr(d_total_groups), _ptr(d_num_joined))
+    r._keep = (d_row_ids, d_num_rows, d_sum, d_keys, d_ivals, d_fvals, d_num_groups, d_total_groups, d_num_joined)
+    return r
+
+
+def tqp_run_plan(ctx: Context, plan: Plan, result: Result, stream=None):
+    _check(lib().tqp_run_plan(ctx.h, C.byref(plan), C.byref(result), _stream(stream)))
+
+
+def tqp_run_plans(ctx: Context, plans, results, stream=None):
+    n = len(plans)
+    pa = (Plan * n)(*plans)
+    ra = (Result * n)(*results)
+    _check(lib().tqp_run_plans(ctx.h, pa, ra, n, _stream(stream)))

@@ -1,0 +1,139 @@
+// Device-side building blocks shared by the libtqp kernels (sm_103a).
+//
+//  * inline-PTX wrappers for mbarriers and bulk asynchronous (TMA engine)
+//    global->shared copies,
+//  * bounded spin waits that latch an error instead of hanging,
+//  * typed column loads widened to int64,
+//  * the postfix expression evaluator (register stack, no local memory),
+//  * packed group keys and integer hashing.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/tqp.h"
+
+namespace tqp {
+
+constexpr int kWarp = 32;
+
+// ---- error latch ---------------------------------------------------------
+// Every device-side error goes to one int in scratch: the first one wins.
+__device__ __forceinline__ void latch_error(int* err, int code) {
+    if (err) atomicCAS(err, 0, code);
+}
+__device__ __forceinline__ int read_error(const int* err) {
+    return err ? *(volatile const int*)err : 0;
+}
+
+// ---- relaxed gpu-scope 64-bit load/store (look-back status words) --------
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// ---- shared-memory addresses and mbarriers -------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Arrive once and announce `bytes` of asynchronous transactions.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Non-blocking test of phase completion (never suspends the thread, so a
+// bounded number of polls is a bounded time).
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase with parity `parity` to complete; false after `cap`
+// polls (each poll sleeps at most ~256 ns, so cap = 2^22 is about a second).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long cap) {
+    for (long long i = 0; i < cap; ++i) {
+        if (mbar_test_wait(bar, parity)) return true;
+        if (i >= 16) __nanosleep(i < 1024 ? 32 : 256);
+    }
+    return false;
+}
+
+// Bulk asynchronous copy global -> shared (TMA engine, non-tensor form).
+// dst, src 16-byte aligned; bytes a positive multiple of 16.  Completion is
+// signalled as transaction bytes on `bar`.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Named barrier over `nthreads` threads (id 1..15; 0 is __syncthreads).
+__device__ __forceinline__ void named_sync(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// ---- typed loads ------------------------------------------------------------
+__device__ __forceinline__ int esize_of(int type) { return type == TQP_I64 ? 8 : (type == TQP_I32 ? 4 : 1); }
+
+__device__ __forceinline__ int64_t load_typed(const unsigned char* base, int type, int64_t i) {
+    switch (type) {
+        case TQP_I32: return static_cast<int64_t>(reinterpret_cast<const int32_t*>(base)[i]);
+        case TQP_I64: return reinterpret_cast<const int64_t*>(base)[i];
+        default: return static_cast<int64_t>(base[i]);
+    }
+}
+
+__device__ __forceinline__ int64_t ldg_typed(const unsigned char* base, int type, int64_t i) {
+    switch (type) {
+        case TQP_I32: return static_cast<int64_t>(__ldg(reinterpret_cast<const int32_t*>(base) + i));
+        case TQP_I64: return __ldg(reinterpret_cast<const long long*>(base) + i);
+        default: return static_cast<int64_t>(__ldg(base + i));
+    }
+}
+
+// ---- integer hashing ----------------------------------------------------------
+// 64-bit finaliser (the SplitMix64 / MurMur3 fmix64 style mix): every input
+// bit affects every output bit, so masked low bits index a table well.
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z ^= z >> 33;
+    z *= 0xff51afd7ed558ccdULL;
+    z ^= z >> 33;
+    z *= 0xc4ceb9fe1a85ec53ULL;
+    z ^= z >> 33;
+    return z;
+}
+
+}  // namespace tqp

@@ -1,0 +1,321 @@
+// The staged scan engine: one persistent, warp-specialised CTA per SM slot.
+//
+// Rows are cut into tiles of T rows and tiles into contiguous chunks; a CTA
+// draws a chunk ticket from a global atomic counter and streams the chunk's
+// tiles.  The last warp (one elected lane) is the producer: for each tile it
+// issues one bulk asynchronous copy (cp.async.bulk, TMA engine) per staged
+// column into a ring of NS shared-memory stages, completion tracked with
+// transaction-count mbarriers.  Warps 0..kConsumerWarps-1 consume the stages
+// and run an operator-specific Body on every tile, then once per chunk.
+//
+// Chunk tickets (not blockIdx) order the chunks, so a chunk's predecessors
+// were always taken by CTAs already running -- the forward-progress
+// condition of a decoupled look-back over chunks.  Keeping the look-back at
+// chunk granularity (one per CTA, not one per tile) takes it off the
+// streaming path: with per-tile look-back the published-prefix frontier
+// advances only ~32 tiles per L2 round trip, far below HBM rate.
+//
+// A tile's column region holds floor16(rows * esize) bytes; the last < 16
+// bytes of a ragged final tile (and every column that is not staged) are
+// read with ordinary global loads.
+#pragma once
+
+#include "common.cuh"
+
+namespace tqp {
+
+constexpr int kConsumerWarps = 8;
+constexpr int kConsumers = kConsumerWarps * kWarp;
+constexpr int kEngineThreads = kConsumers + kWarp;
+constexpr int kMaxStages = 4;
+constexpr int kMaxStaged = 8;
+constexpr int kUnroll = 4;                                  // 32-row chunks per inner step
+constexpr int kRowQuantum = kConsumerWarps * kWarp * kUnroll;  // T must be a multiple
+constexpr int kMaxTileRows = 8192;
+constexpr int kMaxChunksPerWarp = kMaxTileRows / (kConsumerWarps * kWarp);
+constexpr int kBarConsumers = 1;                            // named barrier id
+
+struct ColRef {
+    const unsigned char* ptr;  // device column base
+    int32_t type;              // tqp_dtype
+    int32_t slot;              // staged slot, or -1
+    int32_t soff;              // byte offset of this column inside a stage
+    int32_t pad;
+};
+
+// Geometry and inputs of one scan (one table).
+struct ScanGeom {
+    int64_t n;         // rows
+    int64_t ntiles;
+    int32_t T;         // rows per tile, multiple of kRowQuantum
+    int32_t nstages;   // 2..kMaxStages
+    int32_t stage_bytes;
+    int32_t nstaged;
+    int32_t staged[kMaxStaged];  // column index per staged slot
+    int32_t ncols;
+    ColRef col[TQP_MAX_COLS];
+};
+
+// Range conditions: a row passes iff ((u64)(x - lo) <= span) != negate.
+// Every tqp_cmp maps onto one of these (NE is the negated point range).
+struct Cond {
+    int32_t col;
+    int32_t negate;
+    int64_t lo;
+    uint64_t span;
+};
+
+// Postfix expression with stack depth <= 4, evaluated in registers.
+struct DExpr {
+    int32_t n;
+    int32_t op[TQP_MAX_EXPR];
+    int64_t v[TQP_MAX_EXPR];
+};
+
+struct TileView {
+    const unsigned char* stage;  // shared-memory stage base
+    int64_t tile;
+    int64_t row0;
+    int32_t rows;
+};
+
+// Elements of a staged column present in shared memory: the bulk copy moves
+// floor16(rows * esize) bytes.
+__device__ __forceinline__ int staged_elems(int rows, int type) {
+    const int es = esize_of(type);
+    return static_cast<int>((static_cast<uint32_t>(rows) * es & ~15u) / es);
+}
+
+// Column value of tile row r (0 <= r < rows).
+__device__ __forceinline__ int64_t col_val(const ScanGeom& G, const TileView& v, int c, int r) {
+    const ColRef& cr = G.col[c];
+    if (cr.slot >= 0 && r < staged_elems(v.rows, cr.type)) return load_typed(v.stage + cr.soff, cr.type, r);
+    return ldg_typed(cr.ptr, cr.type, v.row0 + r);
+}
+
+// Evaluate a postfix expression for tile row r.  The stack lives in four
+// registers that shift on push/pop, so no dynamic indexing is needed.
+__device__ __forceinline__ int64_t eval_expr(const ScanGeom& G, const TileView& v, const DExpr& e, int r) {
+    int64_t s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+#pragma unroll
+    for (int i = 0; i < TQP_MAX_EXPR; ++i) {
+        if (i >= e.n) break;
+        const int op = e.op[i];
+        if (op <= TQP_X_CONST) {
+            const int64_t x = (op == TQP_X_COL) ? col_val(G, v, (int)e.v[i], r) : e.v[i];
+            s3 = s2; s2 = s1; s1 = s0; s0 = x;
+        } else {
+            const int64_t b = s0, a = s1;
+            s0 = (op == TQP_X_ADD) ? a + b : (op == TQP_X_SUB) ? a - b : a * b;
+            s1 = s2; s2 = s3;
+        }
+    }
+    return s0;
+}
+
+// Evaluate the conjunction of conditions for kUnroll rows r0 + 32*j.
+__device__ __forceinline__ void eval_conds(const ScanGeom& G, const TileView& v, const Cond* conds, int ncond,
+                                           int r0, bool (&ok)[kUnroll]) {
+#pragma unroll
+    for (int j = 0; j < kUnroll; ++j) ok[j] = (r0 + kWarp * j) < v.rows;
+    for (int q = 0; q < ncond; ++q) {
+        const Cond cd = conds[q];
+        const ColRef& cr = G.col[cd.col];
+        int64_t x[kUnroll];
+        const bool all_smem = cr.slot >= 0 && (r0 + kWarp * (kUnroll - 1)) < staged_elems(v.rows, cr.type);
+        if (all_smem) {
+            const unsigned char* b = v.stage + cr.soff;
+            if (cr.type == TQP_I32) {
+#pragma unroll
+                for (int j = 0; j < kUnroll; ++j) x[j] = reinterpret_cast<const int32_t*>(b)[r0 + kWarp * j];
+            } else if (cr.type == TQP_I64) {
+#pragma unroll
+                for (int j = 0; j < kUnroll; ++j) x[j] = reinterpret_cast<const int64_t*>(b)[r0 + kWarp * j];
+            } else {
+#pragma unroll
+                for (int j = 0; j < kUnroll; ++j) x[j] = b[r0 + kWarp * j];
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < kUnroll; ++j) x[j] = ok[j] ? col_val(G, v, cd.col, r0 + kWarp * j) : 0;
+        }
+#pragma unroll
+        for (int j = 0; j < kUnroll; ++j)
+            ok[j] = ok[j] && ((static_cast<uint64_t>(x[j]) - static_cast<uint64_t>(cd.lo) <= cd.span) != (cd.negate != 0));
+    }
+}
+
+// Shared-memory header of every engine CTA.
+struct EngineHeader {
+    uint64_t full[kMaxStages];
+    uint64_t empty[kMaxStages];
+    long long chunk;
+};
+constexpr int kHeaderBytes = 128;
+static_assert(sizeof(EngineHeader) <= kHeaderBytes, "engine header too large");
+
+// Work split: tiles are grouped into `nchunks` contiguous chunks of
+// `chunk_tiles` tiles; CTAs draw chunk tickets from `ticket`.
+struct EngineCtl {
+    unsigned long long* ticket;  // zeroed before the launch
+    int* err;
+    long long wait_cap;
+    long long chunk_tiles;
+    long long nchunks;
+};
+
+// Body interface (all consumer threads call each member):
+//   pass1(G, v, cw, lane)                  once per tile, reads the stage
+//   chunk_end(G, chunk, t0, t1, cw, lane)  after the chunk's last tile
+//   finish(G, cw, lane)                    after the CTA's last chunk
+// Body::kSmemBytes bytes of shared memory precede the stages.
+template <class Body>
+__device__ __forceinline__ void run_engine(const ScanGeom& G, const EngineCtl& ctl, Body& body,
+                                           unsigned char* smem) {
+    EngineHeader* h = reinterpret_cast<EngineHeader*>(smem);
+    unsigned char* stages = smem + kHeaderBytes + Body::kSmemBytes;
+    const int warp = threadIdx.x / kWarp;
+    const int lane = threadIdx.x % kWarp;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < G.nstages; ++s) {
+            mbar_init(&h->full[s], 1);
+            mbar_init(&h->empty[s], kConsumerWarps);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    long long it = 0;  // pipeline position, advanced identically by producer and consumers
+    bool failed = false;
+    while (true) {
+        if (threadIdx.x == 0) h->chunk = static_cast<long long>(atomicAdd(ctl.ticket, 1ULL));
+        __syncthreads();
+        const long long chunk = h->chunk;
+        __syncthreads();
+        if (chunk >= ctl.nchunks) break;
+        const long long t0 = chunk * ctl.chunk_tiles;
+        const long long t1 = (t0 + ctl.chunk_tiles < G.ntiles) ? t0 + ctl.chunk_tiles : G.ntiles;
+
+        if (warp == kConsumerWarps) {
+            // ---------------- producer: stage every tile of the chunk ----------------
+            if (lane == 0) {
+                for (long long t = t0; t < t1; ++t, ++it) {
+                    const int s = static_cast<int>(it % G.nstages);
+                    const uint32_t ph = static_cast<uint32_t>((it / G.nstages) & 1);
+                    if (!failed && !mbar_wait(&h->empty[s], ph ^ 1u, ctl.wait_cap)) {
+                        latch_error(ctl.err, TQP_ERR_TIMEOUT);
+                        failed = true;
+                    }
+                    const int64_t row0 = static_cast<int64_t>(t) * G.T;
+                    const int rows = static_cast<int>(G.n - row0 < G.T ? G.n - row0 : G.T);
+                    uint32_t total = 0;
+                    if (!failed)
+                        for (int k = 0; k < G.nstaged; ++k)
+                            total += (static_cast<uint32_t>(rows) * esize_of(G.col[G.staged[k]].type)) & ~15u;
+                    unsigned char* dst = stages + static_cast<size_t>(s) * G.stage_bytes;
+                    if (total == 0) {
+                        mbar_arrive(&h->full[s]);
+                    } else {
+                        mbar_arrive_expect_tx(&h->full[s], total);
+                        for (int k = 0; k < G.nstaged; ++k) {
+                            const ColRef& cr = G.col[G.staged[k]];
+                            const int es = esize_of(cr.type);
+                            const uint32_t bytes = (static_cast<uint32_t>(rows) * es) & ~15u;
+                            if (bytes) bulk_g2s(dst + cr.soff, cr.ptr + row0 * es, bytes, &h->full[s]);
+                        }
+                    }
+                }
+                // Drain: no bulk copy may still be landing when the chunk (or the
+                // CTA) ends, even if a consumer gave up waiting.  Phases the
+                // consumers already observed test as complete at once.
+                const long long issued = t1 - t0;
+                for (long long j = (issued > G.nstages ? issued - G.nstages : 0); j < issued; ++j) {
+                    const long long pos = it - issued + j;
+                    mbar_wait(&h->full[pos % G.nstages], static_cast<uint32_t>((pos / G.nstages) & 1),
+                              ctl.wait_cap);
+                }
+            }
+        } else {
+            // ---------------- consumers ----------------
+            const int cw = warp;
+            for (long long t = t0; t < t1; ++t, ++it) {
+                const int s = static_cast<int>(it % G.nstages);
+                const uint32_t ph = static_cast<uint32_t>((it / G.nstages) & 1);
+                if (!failed && !mbar_wait(&h->full[s], ph, ctl.wait_cap)) {
+                    latch_error(ctl.err, TQP_ERR_TIMEOUT);
+                    failed = true;
+                }
+                if (!failed) {
+                    TileView v;
+                    v.stage = stages + static_cast<size_t>(s) * G.stage_bytes;
+                    v.tile = t;
+                    v.row0 = static_cast<int64_t>(t) * G.T;
+                    v.rows = static_cast<int>(G.n - v.row0 < G.T ? G.n - v.row0 : G.T);
+                    body.pass1(G, v, cw, lane);
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&h->empty[s]);
+            }
+            body.chunk_end(G, chunk, t0, t1, cw, lane);
+        }
+        __syncthreads();
+    }
+    if (warp != kConsumerWarps) body.finish(G, warp, lane);
+}
+
+// ---- decoupled look-back (Merrill & Garland, "Single-pass Parallel Prefix
+// Scan with Decoupled Look-back", NVIDIA TR 2016) ----------------------------
+// Status word per tile: bits 63..62 flag (0 empty, 1 aggregate, 2 inclusive
+// prefix), bits 61..0 value.  Called by one full warp; returns the exclusive
+// prefix of `tile` and publishes its inclusive prefix.
+constexpr unsigned long long kFlagA = 1ULL << 62;
+constexpr unsigned long long kFlagP = 2ULL << 62;
+constexpr unsigned long long kValMask = (1ULL << 62) - 1;
+
+__device__ __forceinline__ unsigned long long lookback(unsigned long long* status, long long tile,
+                                                       unsigned long long agg, int lane, int* err,
+                                                       long long cap) {
+    if (tile == 0) {
+        if (lane == 0) st_relaxed_u64(&status[0], kFlagP | agg);
+        return 0;
+    }
+    if (lane == 0) st_relaxed_u64(&status[tile], kFlagA | agg);
+    unsigned long long excl = 0;
+    long long base = tile - 1;
+    long long polls = 0;
+    bool gave_up = false;
+    while (true) {
+        const long long idx = base - lane;
+        unsigned long long w = (idx >= 0) ? ld_relaxed_u64(&status[idx]) : kFlagP;
+        // wait until every lane sees a published word (warp-uniform decisions)
+        while (true) {
+            const bool pending = (w >> 62) == 0;
+            if (!__any_sync(0xffffffffu, pending)) break;
+            const bool stop = (++polls > cap) || read_error(err) == TQP_ERR_TIMEOUT;
+            if (__any_sync(0xffffffffu, stop)) {
+                gave_up = true;
+                break;
+            }
+            if (pending) {
+                __nanosleep(32);
+                w = ld_relaxed_u64(&status[idx]);
+            }
+        }
+        if (gave_up) break;
+        const uint32_t pmask = __ballot_sync(0xffffffffu, (w >> 62) == 2);
+        // lanes up to and including the nearest inclusive prefix contribute
+        const int stop = pmask ? (__ffs(pmask) - 1) : (kWarp - 1);
+        unsigned long long contrib = (lane <= stop) ? (w & kValMask) : 0ULL;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) contrib += __shfl_xor_sync(0xffffffffu, contrib, o);
+        excl += contrib;
+        if (pmask) break;
+        base -= kWarp;
+    }
+    if (gave_up && lane == 0) latch_error(err, TQP_ERR_TIMEOUT);
+    if (lane == 0) st_relaxed_u64(&status[tile], kFlagP | ((excl + agg) & kValMask));
+    return excl;
+}
+
+}  // namespace tqp

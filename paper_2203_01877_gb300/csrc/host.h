@@ -1,0 +1,99 @@
+// Host-side internals shared by the libtqp translation units: the context,
+// its scratch arena, error reporting and the lowering of API structs
+// (predicates, expressions, tables) into kernel parameter blocks.
+#pragma once
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstddef>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "engine.cuh"
+
+// Tile/launch choices for one scan; filled by the tuner (tune.cu).
+struct tqp_tuning {
+    int tile_rows;      // T, multiple of tqp::kRowQuantum
+    int stages;         // 2..kMaxStages
+    int ctas_per_sm;    // 0: as many as fit
+};
+
+struct tqp_ctx {
+    int device;
+    int num_sms;
+    int smem_optin;        // max dynamic shared memory per block (bytes)
+    int l2_bytes;
+    unsigned char* arena;  // device scratch
+    size_t arena_bytes;
+    bool owns_arena;
+    size_t used;           // bump offset of the current call
+    int* d_err;            // latched device error (persistent, arena start)
+    long long wait_cap;
+    tqp_tuning forced;     // tile_rows == 0: no override
+};
+
+namespace tqp {
+
+constexpr size_t kPersistentBytes = 256;   // arena prefix kept across calls (error word)
+constexpr long long kDefaultWaitCap = 1LL << 22;
+
+tqp_status fail(tqp_status s, const char* fmt, ...);
+tqp_status cuda_fail(cudaError_t e, const char* what);
+void clear_error();
+
+#define TQP_CUDA(call)                                          \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return ::tqp::cuda_fail(e_, #call); \
+    } while (0)
+
+#define TQP_TRY(expr)                       \
+    do {                                    \
+        tqp_status s_ = (expr);             \
+        if (s_ != TQP_OK) return s_;        \
+    } while (0)
+
+// Scratch arena: bump allocation, reset at the start of every API call.
+void arena_reset(tqp_ctx* ctx);
+// Returns nullptr (and records the shortfall) when the arena is exhausted.
+void* arena_alloc(tqp_ctx* ctx, size_t bytes, size_t align = 256);
+tqp_status arena_oom(tqp_ctx* ctx, size_t bytes);
+
+// Select the context's device for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev);
+    ~DeviceGuard();
+};
+
+tqp_status check_ctx(const tqp_ctx* ctx);
+tqp_status check_table(const tqp_table* t, const char* what);
+
+// Lower predicates to range conditions on `t`'s columns.
+tqp_status lower_preds(const tqp_table* t, const tqp_pred* preds, int32_t npreds, Cond* out, int* ncond);
+// Lower a postfix expression whose column operands address `ncols` columns.
+tqp_status lower_expr(const tqp_expr* e, int ncols, DExpr* out);
+// Column ids referenced by an expression.
+void expr_cols(const DExpr& e, std::vector<int>& cols);
+
+// Fill G for table t with the given staged columns (deduplicated, <= 8);
+// columns beyond the table (dim columns of a plan) are appended by callers.
+tqp_status make_geom(const tqp_ctx* ctx, const tqp_table* t, std::vector<int> staged, const tqp_tuning& tu,
+                     int body_smem, ScanGeom* G, size_t* smem_bytes);
+
+// Default tuning for a scan staging `bytes_per_row` bytes per row (the
+// context's override, when set, wins).
+tqp_tuning default_tuning(const tqp_ctx* ctx, int bytes_per_row, int body_smem);
+
+// Persistent grid size for an engine kernel.
+int engine_grid(const tqp_ctx* ctx, const void* kernel, size_t smem, int64_t ntiles, int ctas_per_sm);
+
+// Raise a kernel's dynamic shared-memory limit once per device.
+tqp_status allow_smem(const tqp_ctx* ctx, const void* kernel, bool* done_per_device);
+constexpr int kMaxDevices = 64;
+
+}  // namespace tqp

@@ -254,6 +254,9 @@ typedef struct {
     tqp_expr sum_expr;
     int32_t topk_agg;
     int32_t reserved;
+    int64_t max_groups;         /* bound on distinct groups, sizes the aggregation
+                                   table; 0 = the dim row count when grouping by
+                                   dim columns, else res->capacity_groups */
 } tqp_plan;
 
 typedef struct {
@@ -265,7 +268,13 @@ typedef struct {
 } tqp_result;
 
 /* Run one plan.  All outputs are device pointers (any may be NULL when the
- * plan does not produce it); capacity rules as in the operator calls. */
+ * plan does not produce it); capacity rules as in the operator calls.
+ *   d_num_rows    passing fact rows (before the join)
+ *   d_num_joined  joined rows (= passing fact rows without a join)
+ *   d_total_groups all groups (d_num_groups is min(topk, groups) with top-k)
+ * With a join, group columns must all be dim columns and every expression
+ * must use fact columns only (else TQP_ERR_UNSUPPORTED); without a join every
+ * column is a fact column. */
 TQP_API tqp_status tqp_run_plan(tqp_ctx* ctx, const tqp_plan* plan, const tqp_result* res, void* stream);
 
 /* Run n independent plans as one batch: every plan's work is cut into tiles

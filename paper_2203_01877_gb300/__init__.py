@@ -67,7 +67,7 @@ class Plan(C.Structure):
                 ("aggs", Agg * MAX_AGGS),
                 ("has_sum", C.c_int32), ("topk", C.c_int32),
                 ("sum_expr", Expr),
-                ("topk_agg", C.c_int32), ("reserved", C.c_int32)]
+                ("topk_agg", C.c_int32), ("reserved", C.c_int32), ("max_groups", C.c_int64)]
 
 
 class Result(C.Structure):
@@ -267,7 +267,7 @@ def tqp_hash_join(ctx: Context, build: TableRef, build_key: int, probe: TableRef
 
 
 def make_plan(fact: TableRef, preds=(), dim: TableRef | None = None, fact_fk=0, dim_key=0, group_cols=(),
-              aggs=(), sum_expr=None, topk=0, topk_agg=0, emit_row_ids=False) -> Plan:
+              aggs=(), sum_expr=None, topk=0, topk_agg=0, emit_row_ids=False, max_groups=0) -> Plan:
     p = Plan()
     p.fact = C.pointer(fact.t)
     if len(preds) > MAX_PREDS or len(group_cols) > MAX_GROUP_COLS or len(aggs) > MAX_AGGS:
@@ -290,6 +290,7 @@ def make_plan(fact: TableRef, preds=(), dim: TableRef | None = None, fact_fk=0, 
         p.has_sum = 1
         p.sum_expr = make_expr(sum_expr)
     p.topk, p.topk_agg = int(topk), int(topk_agg)
+    p.max_groups = int(max_groups)
     p._keep = (fact, dim)  # keep the tables' C structs alive
     return p
 

@@ -8,6 +8,7 @@
 //  * packed group keys and integer hashing.
 #pragma once
 
+#include <climits>
 #include <cstdint>
 #include <cuda_runtime.h>
 

@@ -138,6 +138,39 @@ tqp_status lower_preds(const tqp_table* t, const tqp_pred* preds, int32_t npreds
     return TQP_OK;
 }
 
+void lower_fast(const Cond* conds, int ncond, const ScanGeom& G, CondFast* out, int32_t* fast) {
+    *fast = 1;
+    for (int q = 0; q < ncond; ++q) {
+        const Cond& c = conds[q];
+        const ColRef& cr = G.col[c.col];
+        if (cr.slot < 0) *fast = 0;
+        CondFast& f = out[q];
+        f.soff = cr.soff;
+        f.type = cr.type;
+        f.pad = 0;
+        // clamp [lo, hi] to the values the column type can hold
+        const int64_t tmin = cr.type == TQP_U8 ? 0 : (cr.type == TQP_I32 ? INT32_MIN : INT64_MIN);
+        const int64_t tmax = cr.type == TQP_U8 ? 255 : (cr.type == TQP_I32 ? INT32_MAX : INT64_MAX);
+        f.negate = c.negate;
+        f.lo = 0;
+        f.span = ~0ULL;  // a test that holds for every value (also in 32 bits)
+        if (c.span == ~0ULL) continue;  // the range covers everything already
+        // lower_preds emits lo <= hi = lo + span without wrap-around
+        const int64_t lo = c.lo;
+        const int64_t hi = static_cast<int64_t>(static_cast<uint64_t>(lo) + c.span);
+        const int64_t clo = std::max(lo, tmin), chi = std::min(hi, tmax);
+        if (clo > chi) {
+            // no value of the type is in range: the test never holds, so the
+            // condition is the constant `negate`; express it with the
+            // always-true test and the opposite negation
+            f.negate = c.negate ? 0 : 1;
+        } else {
+            f.lo = clo;
+            f.span = static_cast<uint64_t>(chi) - static_cast<uint64_t>(clo);
+        }
+    }
+}
+
 tqp_status lower_expr(const tqp_expr* e, int ncols, DExpr* out) {
     if (!e) return fail(TQP_ERR_INVALID_ARG, "expression is NULL");
     if (e->n < 1 || e->n > TQP_MAX_EXPR)
@@ -245,9 +278,20 @@ int engine_grid(const tqp_ctx* ctx, const void* kernel, size_t smem, int64_t nti
     return static_cast<int>(std::max<int64_t>(g, 1));
 }
 
+__global__ void k_set_i64(long long* p, long long v) { *p = v; }
+
+tqp_status set_device_i64(long long* d_ptr, long long value, cudaStream_t stream) {
+    k_set_i64<<<1, 1, 0, stream>>>(d_ptr, value);
+    TQP_CUDA(cudaGetLastError());
+    return TQP_OK;
+}
+
 tqp_status allow_smem(const tqp_ctx* ctx, const void* kernel, bool* done_per_device) {
     if (ctx->device < kMaxDevices && done_per_device[ctx->device]) return TQP_OK;
-    TQP_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, ctx->smem_optin));
+    cudaFuncAttributes fa;
+    TQP_CUDA(cudaFuncGetAttributes(&fa, kernel));
+    const int dyn = ctx->smem_optin - static_cast<int>(fa.sharedSizeBytes);
+    TQP_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
     if (ctx->device < kMaxDevices) done_per_device[ctx->device] = true;
     return TQP_OK;
 }

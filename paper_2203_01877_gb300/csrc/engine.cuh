@@ -72,11 +72,24 @@ struct DExpr {
     int64_t v[TQP_MAX_EXPR];
 };
 
+// A condition lowered for the full-tile fast path: the column is staged at
+// byte `soff` of every stage and [lo, lo + span] has been clamped to the
+// column type's value range, so int32 / uint8 columns compare in 32 bits.
+struct CondFast {
+    int32_t soff;
+    int32_t type;
+    int32_t negate;
+    int32_t pad;
+    int64_t lo;
+    uint64_t span;
+};
+
 struct TileView {
     const unsigned char* stage;  // shared-memory stage base
     int64_t tile;
     int64_t row0;
     int32_t rows;
+    int32_t full;                // rows == T: every staged element is in smem
 };
 
 // Elements of a staged column present in shared memory: the bulk copy moves
@@ -89,8 +102,88 @@ __device__ __forceinline__ int staged_elems(int rows, int type) {
 // Column value of tile row r (0 <= r < rows).
 __device__ __forceinline__ int64_t col_val(const ScanGeom& G, const TileView& v, int c, int r) {
     const ColRef& cr = G.col[c];
-    if (cr.slot >= 0 && r < staged_elems(v.rows, cr.type)) return load_typed(v.stage + cr.soff, cr.type, r);
+    if (cr.slot >= 0 && (v.full || r < staged_elems(v.rows, cr.type))) return load_typed(v.stage + cr.soff, cr.type, r);
     return ldg_typed(cr.ptr, cr.type, v.row0 + r);
+}
+
+// Position of the n-th (0-based) set bit of m (n < popc(m)).
+__device__ __forceinline__ int nth_set_bit(uint32_t m, int n) {
+    int pos = 0;
+    int c = __popc(m & 0xFFFFu);
+    if (n >= c) { n -= c; pos += 16; m >>= 16; }
+    c = __popc(m & 0xFFu);
+    if (n >= c) { n -= c; pos += 8; m >>= 8; }
+    c = __popc(m & 0xFu);
+    if (n >= c) { n -= c; pos += 4; m >>= 4; }
+    c = __popc(m & 0x3u);
+    if (n >= c) { n -= c; pos += 2; m >>= 2; }
+    if (n >= static_cast<int>(m & 1u)) pos += 1;
+    return pos;
+}
+
+// Full-tile fast path: pass bits (bit j <-> row r0 + 32 j) of the conjunction,
+// every condition column staged.  U rows per lane amortise each condition's
+// setup; the range test is one subtract and one unsigned compare.
+template <int U>
+__device__ __forceinline__ uint32_t conds_full(const unsigned char* stage, const CondFast* cf, int ncond, int r0) {
+    uint32_t ok = (U >= 32) ? 0xffffffffu : ((1u << U) - 1u);
+    for (int q = 0; q < ncond; ++q) {
+        const CondFast c = cf[q];
+        const unsigned char* b = stage + c.soff;
+        uint32_t m = 0;
+        if (c.type == TQP_I64) {
+            const uint64_t lo = static_cast<uint64_t>(c.lo);
+#pragma unroll
+            for (int j = 0; j < U; ++j) {
+                const uint64_t x = reinterpret_cast<const uint64_t*>(b)[r0 + kWarp * j];
+                m |= static_cast<uint32_t>(x - lo <= c.span) << j;
+            }
+        } else if (c.type == TQP_I32) {
+            const uint32_t lo = static_cast<uint32_t>(c.lo), span = static_cast<uint32_t>(c.span);
+#pragma unroll
+            for (int j = 0; j < U; ++j) {
+                const uint32_t x = reinterpret_cast<const uint32_t*>(b)[r0 + kWarp * j];
+                m |= static_cast<uint32_t>(x - lo <= span) << j;
+            }
+        } else {
+            const uint32_t lo = static_cast<uint32_t>(c.lo), span = static_cast<uint32_t>(c.span);
+#pragma unroll
+            for (int j = 0; j < U; ++j) {
+                const uint32_t x = b[r0 + kWarp * j];
+                m |= static_cast<uint32_t>(x - lo <= span) << j;
+            }
+        }
+        ok &= c.negate ? ~m : m;
+    }
+    return ok;
+}
+
+// General path (ragged last tile, unstaged condition columns): 64-bit tests.
+template <int U>
+__device__ __forceinline__ uint32_t conds_general(const ScanGeom& G, const TileView& v, const Cond* conds,
+                                                  int ncond, int r0) {
+    uint32_t ok = 0;
+#pragma unroll
+    for (int j = 0; j < U; ++j) ok |= static_cast<uint32_t>(r0 + kWarp * j < v.rows) << j;
+    for (int q = 0; q < ncond; ++q) {
+        const Cond cd = conds[q];
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            if ((ok >> j) & 1u) {
+                const int64_t x = col_val(G, v, cd.col, r0 + kWarp * j);
+                const bool in = static_cast<uint64_t>(x) - static_cast<uint64_t>(cd.lo) <= cd.span;
+                if (in == (cd.negate != 0)) ok &= ~(1u << j);
+            }
+        }
+    }
+    return ok;
+}
+
+template <int U>
+__device__ __forceinline__ uint32_t eval_rows(const ScanGeom& G, const TileView& v, const CondFast* cf,
+                                              const Cond* conds, int ncond, bool fast, int r0) {
+    if (fast && v.full) return conds_full<U>(v.stage, cf, ncond, r0);
+    return conds_general<U>(G, v, conds, ncond, r0);
 }
 
 // Evaluate a postfix expression for tile row r.  The stack lives in four
@@ -111,38 +204,6 @@ __device__ __forceinline__ int64_t eval_expr(const ScanGeom& G, const TileView& 
         }
     }
     return s0;
-}
-
-// Evaluate the conjunction of conditions for kUnroll rows r0 + 32*j.
-__device__ __forceinline__ void eval_conds(const ScanGeom& G, const TileView& v, const Cond* conds, int ncond,
-                                           int r0, bool (&ok)[kUnroll]) {
-#pragma unroll
-    for (int j = 0; j < kUnroll; ++j) ok[j] = (r0 + kWarp * j) < v.rows;
-    for (int q = 0; q < ncond; ++q) {
-        const Cond cd = conds[q];
-        const ColRef& cr = G.col[cd.col];
-        int64_t x[kUnroll];
-        const bool all_smem = cr.slot >= 0 && (r0 + kWarp * (kUnroll - 1)) < staged_elems(v.rows, cr.type);
-        if (all_smem) {
-            const unsigned char* b = v.stage + cr.soff;
-            if (cr.type == TQP_I32) {
-#pragma unroll
-                for (int j = 0; j < kUnroll; ++j) x[j] = reinterpret_cast<const int32_t*>(b)[r0 + kWarp * j];
-            } else if (cr.type == TQP_I64) {
-#pragma unroll
-                for (int j = 0; j < kUnroll; ++j) x[j] = reinterpret_cast<const int64_t*>(b)[r0 + kWarp * j];
-            } else {
-#pragma unroll
-                for (int j = 0; j < kUnroll; ++j) x[j] = b[r0 + kWarp * j];
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < kUnroll; ++j) x[j] = ok[j] ? col_val(G, v, cd.col, r0 + kWarp * j) : 0;
-        }
-#pragma unroll
-        for (int j = 0; j < kUnroll; ++j)
-            ok[j] = ok[j] && ((static_cast<uint64_t>(x[j]) - static_cast<uint64_t>(cd.lo) <= cd.span) != (cd.negate != 0));
-    }
 }
 
 // Shared-memory header of every engine CTA.
@@ -252,6 +313,7 @@ __device__ __forceinline__ void run_engine(const ScanGeom& G, const EngineCtl& c
                     v.tile = t;
                     v.row0 = static_cast<int64_t>(t) * G.T;
                     v.rows = static_cast<int>(G.n - v.row0 < G.T ? G.n - v.row0 : G.T);
+                    v.full = v.rows == G.T;
                     body.pass1(G, v, cw, lane);
                 }
                 __syncwarp();

@@ -2,150 +2,129 @@
 //
 // Paper Section 3.1 (Listing 1: comparison mask then masked_select; the
 // selection-vector variant uses nonzero + index_select) and Section 5.1
-// (expressions).  One kernel does all of it:
-//   * pass 1, per tile: the producer warp stages the predicate columns in
-//     shared memory with bulk asynchronous copies; consumer warps evaluate the
-//     conjunction lane-per-row, take one warp ballot per 32 rows, store the
-//     ballot words (a 1-bit-per-row selection mask, 1/128 of a 16-byte row in
-//     size) and count with popc; the sum expression is evaluated for passing
-//     rows only (columns that are not staged are read lazily);
-//   * once per chunk: a decoupled look-back over chunk counts gives the
-//     chunk's output offset;
-//   * pass 2, per chunk: the chunk's mask words (still in L2) are expanded into
-//     ascending row ids with warp-cooperative, coalesced stores.
+// (expressions).  Two kernels, no host synchronisation and no inter-CTA
+// waiting on the streaming path:
+//   k_filter   the staged scan: the producer warp stages the predicate
+//              columns in shared memory with bulk asynchronous copies; consumer
+//              warps evaluate the conjunction lane-per-row, take one warp
+//              ballot per 32 rows and store it (a 1-bit-per-row selection
+//              mask, 1/128 of a 16-byte row), count with popc into per-block
+//              totals, and evaluate the sum expression for passing rows only
+//              (columns that are not staged are read lazily);
+//   k_compact  expands the mask (written moments before, so read from L2)
+//              into ascending int32 row ids: each block takes the total of all
+//              earlier blocks as its offset, then scans its own words with
+//              warp ballots/shuffles and writes ids with coalesced stores.
 // Count and sum are reduced per warp and added once per warp to scratch; the
-// last warp to finish publishes them, so no host synchronisation is needed.
+// last warp to finish publishes them.
+//
+// An earlier single-kernel form that chained tiles with a decoupled look-back
+// (per tile, then per chunk) was measured slower on GB300: per-tile look-back
+// advances the published-prefix frontier only ~32 tiles per L2 round trip, and
+// a per-chunk look-back leaves the expansion as a serial tail.  The offsets
+// here come straight from counts that are complete when k_compact starts.
 #include "host.h"
 
 namespace tqp {
+
+constexpr int kCompactRows = 65536;                  // rows per k_compact block
+constexpr int kCompactWords = kCompactRows / kWarp;  // 2048 mask words
+constexpr int kCompactThreads = 256;
 
 struct FilterArgs {
     ScanGeom G;
     EngineCtl ctl;
     int32_t ncond;
     int32_t has_sum;
+    int32_t fast;                // every condition column is staged
+    int32_t pad;
     Cond cond[TQP_MAX_PREDS];
+    CondFast cf[TQP_MAX_PREDS];
     DExpr sum;
-    int32_t* row_ids;            // nullable: count/sum only
-    int64_t capacity;
     int64_t* d_count;
     int64_t* d_sum;              // nullable
-    uint32_t* mask;              // one ballot word per 32 rows (with row_ids)
-    unsigned long long* status;  // per-chunk look-back words (zeroed)
+    int64_t capacity;            // row-id capacity, for the CAPACITY latch
+    uint32_t* mask;              // one ballot word per 32 rows; nullptr: count/sum only
+    uint32_t* block_tot;         // passing rows per kCompactRows block (zeroed)
     unsigned long long* acc;     // [0] sum, [1] count, [2] finished warps (zeroed)
 };
 
-// Scratch layout (bytes): ticket + acc[3], chunk status words, then the mask.
+// Scratch layout (bytes): ticket + acc[3], block totals, then the mask.
 struct FilterScratch {
-    size_t status_off, mask_off, bytes;
+    size_t tot_off, mask_off, bytes;
+    long long nblocks;
 };
 
-static FilterScratch filter_scratch_layout(const ScanGeom& G, long long nchunks, bool ids) {
+static FilterScratch filter_scratch_layout(const ScanGeom& G, bool ids) {
     FilterScratch s;
-    s.status_off = 4 * sizeof(unsigned long long);
-    s.mask_off = (s.status_off + (ids ? nchunks : 0) * sizeof(unsigned long long) + 255) / 256 * 256;
-    s.bytes = s.mask_off + (ids ? static_cast<size_t>(G.ntiles) * (G.T / 32) * sizeof(uint32_t) : 0);
+    s.nblocks = ids ? (G.n + kCompactRows - 1) / kCompactRows : 0;
+    s.tot_off = 4 * sizeof(unsigned long long);
+    s.mask_off = (s.tot_off + s.nblocks * sizeof(uint32_t) + 255) / 256 * 256;
+    s.bytes = s.mask_off + (ids ? static_cast<size_t>(G.ntiles) * (G.T / kWarp) * sizeof(uint32_t) : 0);
     return s;
 }
 
 struct FilterBody {
-    static constexpr int kSmemBytes = 128;  // warp totals [2][warps] + chunk offset
+    static constexpr int kSmemBytes = 0;
 
     const FilterArgs& A;
-    uint32_t* wtot;              // [2][kConsumerWarps]
-    unsigned long long* excl_sm;
     long long my_sum = 0;
-    unsigned long long my_cnt = 0;     // lane 0: rows passed by this warp (all chunks)
-    unsigned long long chunk_cnt = 0;  // lane 0: rows passed by this warp in the current chunk
+    unsigned long long my_cnt = 0;  // lane 0: rows passed by this warp
 
-    __device__ FilterBody(const FilterArgs& a, unsigned char* sm) : A(a) {
-        wtot = reinterpret_cast<uint32_t*>(sm);
-        excl_sm = reinterpret_cast<unsigned long long*>(sm + 2 * kConsumerWarps * 4);
+    __device__ FilterBody(const FilterArgs& a, unsigned char*) : A(a) {}
+
+    // U rows per lane (32 U rows per warp) starting at tile row rbase.
+    template <int U>
+    __device__ __forceinline__ void step(const ScanGeom& G, const TileView& v, int rbase, int lane) {
+        const uint32_t ok = eval_rows<U>(G, v, A.cf, A.cond, A.ncond, A.fast != 0, rbase + lane);
+        uint32_t b[U];
+        uint32_t cnt = 0;
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            b[j] = __ballot_sync(0xffffffffu, (ok >> j) & 1u);
+            cnt += __popc(b[j]);
+        }
+        if (lane == 0) {
+            my_cnt += cnt;
+            if (A.mask) {
+                const long long row = v.row0 + rbase;
+#pragma unroll
+                for (int j = 0; j < U; j += 4)
+                    *reinterpret_cast<uint4*>(A.mask + row / kWarp + j) = make_uint4(b[j], b[j + 1], b[j + 2], b[j + 3]);
+                if (cnt) atomicAdd(&A.block_tot[row / kCompactRows], cnt);
+            }
+        }
+        if (A.has_sum) {
+            // passing rows are dealt to lanes in order, one per lane per round
+            for (int s = lane; s < static_cast<int>(cnt); s += kWarp) {
+                int j = 0, before = 0;
+                uint32_t word = b[0];
+#pragma unroll
+                for (int jj = 0; jj + 1 < U; ++jj) {
+                    const int c = __popc(b[jj]);
+                    if (jj == j && s >= before + c) {
+                        before += c;
+                        j = jj + 1;
+                        word = b[jj + 1];
+                    }
+                }
+                const int bit = nth_set_bit(word, s - before);
+                my_sum += eval_expr(G, v, A.sum, rbase + kWarp * j + bit);
+            }
+        }
     }
 
     __device__ void pass1(const ScanGeom& G, const TileView& v, int cw, int lane) {
-        const int rw = G.T / kConsumerWarps;
-        const int chunks = rw / kWarp;
-        uint32_t cnt = 0;
-        for (int c = 0; c < chunks; c += kUnroll) {
-            const int rbase = cw * rw + c * kWarp;
-            if (rbase >= v.rows) break;  // words wholly past the table end are never read
-            bool ok[kUnroll];
-            eval_conds(G, v, A.cond, A.ncond, rbase + lane, ok);
-            uint32_t b[kUnroll];
-#pragma unroll
-            for (int j = 0; j < kUnroll; ++j) {
-                b[j] = __ballot_sync(0xffffffffu, ok[j]);
-                cnt += __popc(b[j]);
-                if (A.has_sum && ok[j]) my_sum += eval_expr(G, v, A.sum, rbase + kWarp * j + lane);
-            }
-            if (A.row_ids && lane == 0)
-                *reinterpret_cast<uint4*>(A.mask + (v.row0 + rbase) / kWarp) = make_uint4(b[0], b[1], b[2], b[3]);
+        const int rw = G.T / kConsumerWarps;  // a multiple of 128
+        int r = 0;
+        for (; r + 8 * kWarp <= rw; r += 8 * kWarp) {
+            if (cw * rw + r >= v.rows) return;  // mask words wholly past the table end are never read
+            step<8>(G, v, cw * rw + r, lane);
         }
-        if (lane == 0) chunk_cnt += cnt;
+        if (r < rw && cw * rw + r < v.rows) step<4>(G, v, cw * rw + r, lane);
     }
 
-    __device__ void chunk_end(const ScanGeom& G, long long chunk, long long t0, long long t1, int cw, int lane) {
-        if (lane == 0) my_cnt += chunk_cnt;
-        if (!A.row_ids) {
-            chunk_cnt = 0;
-            return;
-        }
-        if (lane == 0) wtot[cw] = static_cast<uint32_t>(chunk_cnt);
-        chunk_cnt = 0;
-        named_sync(kBarConsumers, kConsumers);
-        if (cw == 0) {
-            unsigned long long c = lane < kConsumerWarps ? wtot[lane] : 0ULL;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-            const unsigned long long ex = lookback(A.status, chunk, c, lane, A.ctl.err, A.ctl.wait_cap);
-            if (lane == 0) *excl_sm = ex;
-        }
-        named_sync(kBarConsumers, kConsumers);
-        unsigned long long running = *excl_sm;
-
-        // expand this chunk's mask words into row ids, 256 words per round
-        const long long w_begin = t0 * (G.T / kWarp);
-        const long long row_end = (t1 * G.T < G.n) ? t1 * G.T : G.n;
-        const long long w_end = (row_end + kWarp - 1) / kWarp;
-        const uint32_t lt = lanemask_lt();
-        int par = 0;
-        for (long long base = w_begin; base < w_end; base += kConsumers) {
-            const long long wi = base + cw * kWarp + lane;
-            const uint32_t word = wi < w_end ? A.mask[wi] : 0u;
-            const uint32_t c = __popc(word);
-            uint32_t incl = c;
-#pragma unroll
-            for (int o = 1; o < kWarp; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += y;
-            }
-            if (lane == kWarp - 1) wtot[par * kConsumerWarps + cw] = incl;
-            named_sync(kBarConsumers, kConsumers);
-            unsigned long long before = 0, round_total = 0;
-#pragma unroll
-            for (int w = 0; w < kConsumerWarps; ++w) {
-                const uint32_t x = wtot[par * kConsumerWarps + w];
-                before += (w < cw) ? x : 0u;
-                round_total += x;
-            }
-            const unsigned long long my_off = running + before + (incl - c);
-            uint32_t nz = __ballot_sync(0xffffffffu, word != 0u);
-            while (nz) {
-                const int j = __ffs(nz) - 1;
-                nz &= nz - 1;
-                const uint32_t wj = __shfl_sync(0xffffffffu, word, j);
-                const unsigned long long oj = __shfl_sync(0xffffffffu, my_off, j);
-                if ((wj >> lane) & 1u) {
-                    const unsigned long long pos = oj + __popc(wj & lt);
-                    if (pos < static_cast<unsigned long long>(A.capacity))
-                        A.row_ids[pos] = static_cast<int32_t>((base + cw * kWarp + j) * kWarp + lane);
-                }
-            }
-            running += round_total;
-            par ^= 1;
-        }
-    }
+    __device__ void chunk_end(const ScanGeom&, long long, long long, long long, int, int) {}
 
     __device__ void finish(const ScanGeom&, int cw, int lane) {
         long long s = my_sum;
@@ -162,8 +141,7 @@ struct FilterBody {
                 const unsigned long long tot_cnt = atomicAdd(&A.acc[1], 0ULL);
                 *A.d_count = static_cast<int64_t>(tot_cnt);
                 if (A.d_sum) *A.d_sum = static_cast<int64_t>(tot_sum);
-                if (A.row_ids && static_cast<long long>(tot_cnt) > A.capacity)
-                    latch_error(A.ctl.err, TQP_ERR_CAPACITY);
+                if (A.mask && static_cast<long long>(tot_cnt) > A.capacity) latch_error(A.ctl.err, TQP_ERR_CAPACITY);
             }
         }
     }
@@ -175,8 +153,69 @@ __global__ void __launch_bounds__(kEngineThreads, 2) k_filter(const __grid_const
     run_engine(A.G, A.ctl, body, smem);
 }
 
-// Lower a filter call into kernel arguments; *scratch_bytes receives the
-// scratch it needs and *grid / *smem the launch shape.
+// Expand the selection mask of rows [b * kCompactRows, ...) into row ids.
+__global__ void __launch_bounds__(kCompactThreads) k_compact(const uint32_t* __restrict__ mask,
+                                                             const uint32_t* __restrict__ block_tot, long long n,
+                                                             int32_t* __restrict__ row_ids, long long capacity) {
+    constexpr int W = kCompactThreads / kWarp;
+    __shared__ unsigned long long red[W];
+    __shared__ uint32_t wtot[2][W];
+    const int lane = threadIdx.x % kWarp, w = threadIdx.x / kWarp;
+    const long long b = blockIdx.x;
+    // offset of this block: every earlier block's total
+    unsigned long long before_blocks = 0;
+    for (long long i = threadIdx.x; i < b; i += kCompactThreads) before_blocks += block_tot[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) before_blocks += __shfl_xor_sync(0xffffffffu, before_blocks, o);
+    if (lane == 0) red[w] = before_blocks;
+    __syncthreads();
+    unsigned long long running = 0;
+#pragma unroll
+    for (int i = 0; i < W; ++i) running += red[i];
+
+    const long long nwords = (n + kWarp - 1) / kWarp;
+    const long long w0 = b * kCompactWords;
+    const long long w1 = (w0 + kCompactWords < nwords) ? w0 + kCompactWords : nwords;
+    const uint32_t lt = lanemask_lt();
+    int par = 0;
+    for (long long base = w0; base < w1; base += kCompactThreads) {
+        const long long wi = base + threadIdx.x;
+        const uint32_t word = wi < w1 ? mask[wi] : 0u;
+        const uint32_t c = __popc(word);
+        uint32_t incl = c;
+#pragma unroll
+        for (int o = 1; o < kWarp; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == kWarp - 1) wtot[par][w] = incl;
+        __syncthreads();
+        unsigned long long before = 0, round_total = 0;
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+            const uint32_t x = wtot[par][i];
+            before += (i < w) ? x : 0u;
+            round_total += x;
+        }
+        const unsigned long long my_off = running + before + (incl - c);
+        uint32_t nz = __ballot_sync(0xffffffffu, word != 0u);
+        while (nz) {
+            const int j = __ffs(nz) - 1;
+            nz &= nz - 1;
+            const uint32_t wj = __shfl_sync(0xffffffffu, word, j);
+            const unsigned long long oj = __shfl_sync(0xffffffffu, my_off, j);
+            if ((wj >> lane) & 1u) {
+                const unsigned long long pos = oj + __popc(wj & lt);
+                if (pos < static_cast<unsigned long long>(capacity))
+                    row_ids[pos] = static_cast<int32_t>((base + w * kWarp + j) * kWarp + lane);
+            }
+        }
+        running += round_total;
+        par ^= 1;
+    }
+}
+
+// Lower a filter call into kernel arguments and a launch shape.
 static tqp_status plan_filter(const tqp_ctx* ctx, const tqp_table* t, const tqp_pred* preds, int32_t npreds,
                               const tqp_expr* sum_expr, bool ids, const tqp_tuning* force, FilterArgs* A,
                               size_t* smem, int* grid, FilterScratch* lay) {
@@ -198,17 +237,18 @@ static tqp_status plan_filter(const tqp_ctx* ctx, const tqp_table* t, const tqp_
     for (int c : u) bpr += t->cols[c].type == TQP_I64 ? 8 : (t->cols[c].type == TQP_I32 ? 4 : 1);
     const tqp_tuning tu = force ? *force : default_tuning(ctx, bpr, FilterBody::kSmemBytes);
     TQP_TRY(make_geom(ctx, t, staged, tu, FilterBody::kSmemBytes, &A->G, smem));
+    lower_fast(A->cond, A->ncond, A->G, A->cf, &A->fast);
     static bool attr_done[kMaxDevices] = {};
     TQP_TRY(allow_smem(ctx, reinterpret_cast<const void*>(k_filter), attr_done));
     const int g = engine_grid(ctx, reinterpret_cast<const void*>(k_filter), *smem, A->G.ntiles, tu.ctas_per_sm);
     A->ctl.chunk_tiles = (A->G.ntiles + g - 1) / g;
     A->ctl.nchunks = (A->G.ntiles + A->ctl.chunk_tiles - 1) / A->ctl.chunk_tiles;
     *grid = static_cast<int>(A->ctl.nchunks);
-    *lay = filter_scratch_layout(A->G, A->ctl.nchunks, ids);
+    *lay = filter_scratch_layout(A->G, ids);
     return TQP_OK;
 }
 
-// Launch with caller-provided scratch of at least lay.bytes (zeroed here).
+// Launch with caller-provided scratch of at least lay.bytes (cleared here).
 static tqp_status launch_filter_with(FilterArgs& A, int grid, size_t smem, const FilterScratch& lay,
                                      void* scratch, int* d_err, long long wait_cap, int32_t* d_row_ids,
                                      int64_t capacity, int64_t* d_count, int64_t* d_sum, cudaStream_t stream) {
@@ -218,14 +258,18 @@ static tqp_status launch_filter_with(FilterArgs& A, int grid, size_t smem, const
     A.ctl.err = d_err;
     A.ctl.wait_cap = wait_cap;
     A.acc = reinterpret_cast<unsigned long long*>(sc) + 1;
-    A.status = reinterpret_cast<unsigned long long*>(sc + lay.status_off);
-    A.mask = reinterpret_cast<uint32_t*>(sc + lay.mask_off);
-    A.row_ids = d_row_ids;
+    A.block_tot = reinterpret_cast<uint32_t*>(sc + lay.tot_off);
+    A.mask = d_row_ids ? reinterpret_cast<uint32_t*>(sc + lay.mask_off) : nullptr;
     A.capacity = capacity;
     A.d_count = d_count;
     A.d_sum = d_sum;
     k_filter<<<grid, kEngineThreads, smem, stream>>>(A);
     TQP_CUDA(cudaGetLastError());
+    if (d_row_ids) {
+        k_compact<<<static_cast<unsigned>(lay.nblocks), kCompactThreads, 0, stream>>>(A.mask, A.block_tot, A.G.n,
+                                                                                       d_row_ids, capacity);
+        TQP_CUDA(cudaGetLastError());
+    }
     return TQP_OK;
 }
 

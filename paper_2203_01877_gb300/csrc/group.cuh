@@ -1,0 +1,130 @@
+// Aggregation-table pieces shared by the group-by scan and the plan runner:
+// packed order-preserving group keys, the global open-addressing table of
+// exact int64 accumulators, and the per-group output writer.
+#pragma once
+
+#include "engine.cuh"
+
+namespace tqp {
+
+constexpr unsigned long long kEmptyKey = ~0ULL;
+constexpr int kMaxAcc = 1 + TQP_MAX_AGGS;  // count + one sum per distinct expression
+constexpr int kSmemSlots = 256;
+constexpr int kSmemProbe = 8;
+constexpr int kSmallCap = 4096;            // finalize in one CTA up to this many table slots
+constexpr int kFinThreads = 1024;
+
+struct GroupSpec {
+    int32_t ngc;
+    int32_t width;                 // packed key bits (0..64)
+    int32_t key_col[TQP_MAX_GROUP_COLS];
+    int32_t key_bits[TQP_MAX_GROUP_COLS];
+    int32_t nacc;                  // accumulators; [0] is the row count
+    int32_t naggs;
+    int32_t agg_fn[TQP_MAX_AGGS];
+    int32_t agg_acc[TQP_MAX_AGGS];
+    DExpr acc_expr[TQP_MAX_AGGS];  // expression of accumulator a + 1
+    unsigned long long* keys;      // [cap + 1], kEmptyKey = free; slot cap holds the all-ones key
+    unsigned long long* acc;       // [(cap + 1) * nacc]
+    long long cap;                 // power of two
+    unsigned long long* ndistinct;
+    long long max_groups;
+};
+
+__device__ __forceinline__ uint64_t enc_key(int64_t x, int bits) {
+    if (bits == 8) return static_cast<uint64_t>(x) & 0xFFull;
+    if (bits == 32) return static_cast<uint64_t>(static_cast<uint32_t>(x) ^ 0x80000000u);
+    return static_cast<uint64_t>(x) ^ 0x8000000000000000ull;
+}
+
+__device__ __forceinline__ int64_t dec_key(uint64_t e, int bits) {
+    if (bits == 8) return static_cast<int64_t>(e & 0xFFull);
+    if (bits == 32) return static_cast<int64_t>(static_cast<int32_t>(static_cast<uint32_t>(e) ^ 0x80000000u));
+    return static_cast<int64_t>(e ^ 0x8000000000000000ull);
+}
+
+__device__ __forceinline__ uint64_t pack_key(const GroupSpec& S, const ScanGeom& G, const TileView& v, int r) {
+    uint64_t k = 0;
+    for (int i = 0; i < S.ngc; ++i) {
+        const int b = S.key_bits[i];
+        const uint64_t e = enc_key(col_val(G, v, S.key_col[i], r), b);
+        k = (b == 64) ? e : ((k << b) | e);
+    }
+    return k;
+}
+
+// Find or claim the global slot of `key`; -1 (and CAPACITY latched) if full.
+__device__ __forceinline__ long long gtab_slot(const GroupSpec& S, uint64_t key, int* err) {
+    if (key == kEmptyKey) return S.cap;
+    unsigned long long h = mix64(key) & static_cast<unsigned long long>(S.cap - 1);
+    for (long long i = 0; i < S.cap; ++i) {
+        const unsigned long long k = *reinterpret_cast<volatile unsigned long long*>(&S.keys[h]);
+        if (k == key) return static_cast<long long>(h);
+        if (k == kEmptyKey) {
+            const unsigned long long prev = atomicCAS(&S.keys[h], kEmptyKey, key);
+            if (prev == kEmptyKey) {
+                if (static_cast<long long>(atomicAdd(S.ndistinct, 1ULL)) >= S.max_groups)
+                    latch_error(err, TQP_ERR_CAPACITY);
+                return static_cast<long long>(h);
+            }
+            if (prev == key) return static_cast<long long>(h);
+        }
+        h = (h + 1) & static_cast<unsigned long long>(S.cap - 1);
+    }
+    latch_error(err, TQP_ERR_CAPACITY);
+    return -1;
+}
+
+struct GroupOut {
+    int64_t* keys;     // [G][ngc]
+    int64_t* ivals;    // [G][naggs]
+    double* fvals;     // [G][naggs]
+    long long capacity;
+    int64_t* num_groups;
+    int* err;
+};
+
+__device__ __forceinline__ void emit_group(const GroupSpec& S, const GroupOut& O, long long g, uint64_t key,
+                                           long long slot) {
+    if (O.keys) {
+        uint64_t k = key;
+        for (int i = S.ngc - 1; i >= 0; --i) {
+            const int b = S.key_bits[i];
+            const uint64_t e = (b == 64) ? k : (k & ((1ULL << b) - 1));
+            O.keys[g * S.ngc + i] = dec_key(e, b);
+            k = (b == 64) ? 0 : (k >> b);
+        }
+    }
+    const unsigned long long* a = slot >= 0 ? S.acc + slot * S.nacc : nullptr;
+    const long long cnt = a ? static_cast<long long>(a[0]) : 0;
+    for (int j = 0; j < S.naggs; ++j) {
+        const long long x = a ? static_cast<long long>(a[S.agg_acc[j]]) : 0;
+        if (O.ivals) O.ivals[g * S.naggs + j] = x;
+        if (O.fvals) {
+            double f = 0.0;
+            if (S.agg_fn[j] == TQP_AVG) f = __ddiv_rn(__ll2double_rn(x), __ll2double_rn(cnt));
+            O.fvals[g * S.naggs + j] = f;
+        }
+    }
+}
+
+// A slot is a group iff at least one row was counted into it (a slot may
+// be claimed in advance, e.g. for every dimension-table group of a join).
+__device__ __forceinline__ bool slot_used(const GroupSpec& S, long long i) {
+    return S.acc[i * S.nacc] != 0ULL;
+}
+
+
+// host side (groupby.cu)
+tqp_status lower_group(const int32_t* key_cols, const int32_t* key_types, int32_t ngc, const tqp_agg* aggs,
+                       int32_t naggs, int ncols, GroupSpec* S);
+long long group_table_cap(long long max_groups);
+size_t group_table_bytes(long long cap, int nacc);
+tqp_status group_table_init(GroupSpec* S, void* mem, long long cap, long long max_groups, cudaStream_t stream);
+tqp_status group_finalize(tqp_ctx* ctx, const GroupSpec& S, const GroupOut& O, cudaStream_t stream);
+// Top-k groups by accumulator of aggregate `agg` (descending; ties: key
+// ascending); writes min(k, G) rows in rank order and *total_groups = G.
+tqp_status group_topk(tqp_ctx* ctx, const GroupSpec& S, const GroupOut& O, int k, int agg,
+                      int64_t* total_groups, cudaStream_t stream);
+
+}  // namespace tqp

@@ -1,0 +1,587 @@
+// tqp_groupby_agg: hash group-by aggregation with exact int64 sums.
+//
+// Semantics of paper Section 5.4 (Algorithm 3: one output row per distinct
+// key tuple, keys ascending, aggregates evaluated per group), computed
+// without sorting the input:
+//   * group keys are packed into one order-preserving uint64 (uint8 -> 8 bits,
+//     int32 -> 32 bits with the sign bit flipped, int64 -> 64 bits flipped;
+//     first key column most significant), so unsigned order of packed keys is
+//     the lexicographic order of the int64-widened tuples;
+//   * each persistent CTA pre-aggregates into a shared-memory open-addressing
+//     table (bounded probing; rows that do not fit go straight to the global
+//     table), and flushes it once into a global open-addressing table with
+//     64-bit atomics -- few global atomics when groups are few (the Q1 shape);
+//   * finalize collects the occupied slots, orders them by packed key (one
+//     CTA bitonic sort for small tables, the radix sort otherwise), unpacks
+//     the keys and computes AVG as one IEEE division of the exact sum by the
+//     count.
+// int64 addition is associative and commutative, so the sums do not depend on
+// the order atomics land in.
+#include "host.h"
+#include "group.cuh"
+
+namespace tqp {
+
+tqp_status radix_sort_pairs(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, const long long* d_n,
+                            long long n_max, int begin_bit, int end_bit, void* scratch, cudaStream_t stream,
+                            bool* result_in_1);
+size_t radix_sort_scratch(long long n_max);
+
+struct GroupArgs {
+    ScanGeom G;
+    EngineCtl ctl;
+    int32_t ncond;
+    int32_t fast;
+    Cond cond[TQP_MAX_PREDS];
+    CondFast cf[TQP_MAX_PREDS];
+    GroupSpec S;
+};
+
+struct GroupBody {
+    static constexpr int kSmemBytes = kSmemSlots * 8 + kSmemSlots * kMaxAcc * 8;
+
+    const GroupArgs& A;
+    unsigned long long* skeys;
+    unsigned long long* sacc;
+
+    __device__ GroupBody(const GroupArgs& a, unsigned char* sm) : A(a) {
+        skeys = reinterpret_cast<unsigned long long*>(sm);
+        sacc = skeys + kSmemSlots;
+        for (int i = threadIdx.x; i < kSmemSlots; i += blockDim.x) skeys[i] = kEmptyKey;
+        for (int i = threadIdx.x; i < kSmemSlots * kMaxAcc; i += blockDim.x) sacc[i] = 0;
+    }
+
+    __device__ __forceinline__ int smem_slot(uint64_t key) {
+        if (key == kEmptyKey) return -1;
+        unsigned h = static_cast<unsigned>(mix64(key)) & (kSmemSlots - 1);
+#pragma unroll 1
+        for (int p = 0; p < kSmemProbe; ++p) {
+            const unsigned long long k = *reinterpret_cast<volatile unsigned long long*>(&skeys[h]);
+            if (k == key) return static_cast<int>(h);
+            if (k == kEmptyKey) {
+                const unsigned long long prev = atomicCAS(&skeys[h], kEmptyKey, key);
+                if (prev == kEmptyKey || prev == key) return static_cast<int>(h);
+            }
+            h = (h + 1) & (kSmemSlots - 1);
+        }
+        return -1;
+    }
+
+    __device__ __forceinline__ void add_row(const ScanGeom& G, const TileView& v, int r) {
+        const GroupSpec& S = A.S;
+        const uint64_t key = pack_key(S, G, v, r);
+        const int s = smem_slot(key);
+        if (s >= 0) {
+            unsigned long long* a = sacc + s * kMaxAcc;
+            atomicAdd(&a[0], 1ULL);
+            for (int i = 1; i < S.nacc; ++i)
+                atomicAdd(&a[i], static_cast<unsigned long long>(eval_expr(G, v, S.acc_expr[i - 1], r)));
+        } else {
+            const long long g = gtab_slot(S, key, A.ctl.err);
+            if (g < 0) return;
+            unsigned long long* a = S.acc + g * S.nacc;
+            atomicAdd(&a[0], 1ULL);
+            for (int i = 1; i < S.nacc; ++i)
+                atomicAdd(&a[i], static_cast<unsigned long long>(eval_expr(G, v, S.acc_expr[i - 1], r)));
+        }
+    }
+
+    __device__ void pass1(const ScanGeom& G, const TileView& v, int cw, int lane) {
+        const int rw = G.T / kConsumerWarps;  // a multiple of 128
+        for (int r = 0; r < rw; r += kUnroll * kWarp) {
+            const int rbase = cw * rw + r;
+            if (rbase >= v.rows) break;
+            const uint32_t ok = eval_rows<kUnroll>(G, v, A.cf, A.cond, A.ncond, A.fast != 0, rbase + lane);
+#pragma unroll
+            for (int j = 0; j < kUnroll; ++j)
+                if ((ok >> j) & 1u) add_row(G, v, rbase + kWarp * j + lane);
+        }
+    }
+
+    __device__ void chunk_end(const ScanGeom&, long long, long long, long long, int, int) {}
+
+    __device__ void finish(const ScanGeom&, int cw, int lane) {
+        named_sync(kBarConsumers, kConsumers);
+        const GroupSpec& S = A.S;
+        for (int i = cw * kWarp + lane; i < kSmemSlots; i += kConsumers) {
+            const unsigned long long key = skeys[i];
+            if (key == kEmptyKey) continue;
+            const long long g = gtab_slot(S, key, A.ctl.err);
+            if (g < 0) continue;
+            for (int a = 0; a < S.nacc; ++a) {
+                const unsigned long long x = sacc[i * kMaxAcc + a];
+                if (x) atomicAdd(&S.acc[g * S.nacc + a], x);
+            }
+        }
+    }
+};
+
+__global__ void __launch_bounds__(kEngineThreads, 2) k_groupby(const __grid_constant__ GroupArgs A) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    GroupBody body(A, smem + kHeaderBytes);
+    run_engine(A.G, A.ctl, body, smem);
+}
+
+// ---- finalize ----------------------------------------------------------------
+
+// One CTA: collect occupied slots, bitonic-sort (key, slot), emit.
+__global__ void __launch_bounds__(kFinThreads) k_groupby_finalize_small(const __grid_constant__ GroupSpec S,
+                                                                        const __grid_constant__ GroupOut O) {
+    extern __shared__ __align__(16) unsigned char fsm[];
+    const int P = 2 * kSmallCap;  // slots + special, padded to a power of two
+    unsigned long long* sk = reinterpret_cast<unsigned long long*>(fsm);
+    uint32_t* ss = reinterpret_cast<uint32_t*>(sk + P);
+    __shared__ int count;
+    if (threadIdx.x == 0) count = 0;
+    __syncthreads();
+    const bool overflow = static_cast<long long>(*S.ndistinct) > S.max_groups;
+    for (long long i = threadIdx.x; i <= S.cap; i += blockDim.x) {
+        if (slot_used(S, i)) {
+            const int p = atomicAdd(&count, 1);
+            if (p < P) {
+                sk[p] = i < S.cap ? S.keys[i] : kEmptyKey;
+                ss[p] = static_cast<uint32_t>(i);
+            }
+        }
+    }
+    __syncthreads();
+    const int G = min(count, P);
+    int n2 = 1;
+    while (n2 < G) n2 <<= 1;
+    for (int i = G + threadIdx.x; i < n2; i += blockDim.x) {
+        sk[i] = kEmptyKey;
+        ss[i] = 0xFFFFFFFFu;
+    }
+    __syncthreads();
+    for (int k = 2; k <= n2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const bool up = (i & k) == 0;
+                    const unsigned long long ki = sk[i], kl = sk[l];
+                    const uint32_t si = ss[i], sl = ss[l];
+                    const bool gt = (ki > kl) || (ki == kl && si > sl);
+                    if (gt == up) {
+                        sk[i] = kl; sk[l] = ki;
+                        ss[i] = sl; ss[l] = si;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (overflow || G > O.capacity) {
+        if (threadIdx.x == 0) {
+            *O.num_groups = -1;
+            latch_error(O.err, TQP_ERR_CAPACITY);
+        }
+        return;
+    }
+    if (S.ngc == 0 && G == 0) {  // ungrouped aggregate over no rows: one row, COUNT 0, AVG NaN
+        if (threadIdx.x == 0) {
+            emit_group(S, O, 0, 0, -1);
+            if (O.fvals)
+                for (int j = 0; j < S.naggs; ++j)
+                    if (S.agg_fn[j] == TQP_AVG) O.fvals[j] = __longlong_as_double(0x7ff8000000000000LL);
+            *O.num_groups = 1;
+        }
+        return;
+    }
+    for (int g = threadIdx.x; g < G; g += blockDim.x) emit_group(S, O, g, sk[g], ss[g]);
+    if (threadIdx.x == 0) *O.num_groups = G;
+}
+
+// Large tables: collect (key, slot) pairs, radix sort, emit.
+__global__ void k_groupby_collect(const __grid_constant__ GroupSpec S, uint64_t* pk, uint32_t* ps,
+                                  long long* n_out) {
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i <= S.cap;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        if (slot_used(S, i)) {
+            const long long p = static_cast<long long>(atomicAdd(reinterpret_cast<unsigned long long*>(n_out), 1ULL));
+            pk[p] = i < S.cap ? S.keys[i] : kEmptyKey;
+            ps[p] = static_cast<uint32_t>(i);
+        }
+    }
+}
+
+__global__ void k_groupby_emit(const __grid_constant__ GroupSpec S, const __grid_constant__ GroupOut O,
+                               const uint64_t* pk, const uint32_t* ps, const long long* n_in) {
+    const long long G = *n_in;
+    const bool overflow = static_cast<long long>(*S.ndistinct) > S.max_groups || G > O.capacity;
+    if (overflow) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            *O.num_groups = -1;
+            latch_error(O.err, TQP_ERR_CAPACITY);
+        }
+        return;
+    }
+    for (long long g = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; g < G;
+         g += static_cast<long long>(gridDim.x) * blockDim.x)
+        emit_group(S, O, g, pk[g], ps[g]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (S.ngc == 0 && G == 0) {
+            emit_group(S, O, 0, 0, -1);
+            if (O.fvals)
+                for (int j = 0; j < S.naggs; ++j)
+                    if (S.agg_fn[j] == TQP_AVG) O.fvals[j] = __longlong_as_double(0x7ff8000000000000LL);
+            *O.num_groups = 1;
+        } else {
+            *O.num_groups = G;
+        }
+    }
+}
+
+// ---- host ------------------------------------------------------------------------
+
+static bool same_expr(const DExpr& a, const DExpr& b) {
+    if (a.n != b.n) return false;
+    for (int i = 0; i < a.n; ++i)
+        if (a.op[i] != b.op[i] || a.v[i] != b.v[i]) return false;
+    return true;
+}
+
+// Fill the key/aggregate part of a GroupSpec (table pointers are set later).
+// key_types[i] is the dtype of key column i; exprs address `ncols` columns.
+tqp_status lower_group(const int32_t* key_cols, const int32_t* key_types, int32_t ngc, const tqp_agg* aggs,
+                       int32_t naggs, int ncols, GroupSpec* S) {
+    memset(S, 0, sizeof(*S));
+    if (ngc < 0 || ngc > TQP_MAX_GROUP_COLS)
+        return fail(TQP_ERR_INVALID_ARG, "ngc %d outside [0, %d]", ngc, TQP_MAX_GROUP_COLS);
+    if (naggs < 0 || naggs > TQP_MAX_AGGS)
+        return fail(TQP_ERR_INVALID_ARG, "naggs %d outside [0, %d]", naggs, TQP_MAX_AGGS);
+    if (naggs > 0 && !aggs) return fail(TQP_ERR_INVALID_ARG, "aggs is NULL");
+    S->ngc = ngc;
+    int width = 0;
+    for (int i = 0; i < ngc; ++i) {
+        if (key_cols[i] < 0 || key_cols[i] >= ncols)
+            return fail(TQP_ERR_INVALID_ARG, "group column %d out of range", key_cols[i]);
+        S->key_col[i] = key_cols[i];
+        S->key_bits[i] = key_types[i] == TQP_U8 ? 8 : (key_types[i] == TQP_I32 ? 32 : 64);
+        width += S->key_bits[i];
+    }
+    if (width > 64) return fail(TQP_ERR_UNSUPPORTED, "group key tuple is %d bits wide (at most 64 supported)", width);
+    S->width = width;
+    S->nacc = 1;
+    S->naggs = naggs;
+    for (int j = 0; j < naggs; ++j) {
+        const int fn = aggs[j].fn;
+        if (fn != TQP_SUM && fn != TQP_COUNT && fn != TQP_AVG)
+            return fail(TQP_ERR_INVALID_ARG, "aggregate %d: unknown function %d", j, fn);
+        S->agg_fn[j] = fn;
+        if (fn == TQP_COUNT) {
+            S->agg_acc[j] = 0;
+            continue;
+        }
+        DExpr e;
+        TQP_TRY(lower_expr(&aggs[j].expr, ncols, &e));
+        int found = -1;
+        for (int a = 1; a < S->nacc; ++a)
+            if (same_expr(S->acc_expr[a - 1], e)) found = a;
+        if (found < 0) {
+            found = S->nacc++;
+            S->acc_expr[found - 1] = e;
+        }
+        S->agg_acc[j] = found;
+    }
+    return TQP_OK;
+}
+
+long long group_table_cap(long long capacity_groups) {
+    long long cap = 64;
+    while (cap < 2 * capacity_groups) cap <<= 1;
+    return cap;
+}
+
+size_t group_table_bytes(long long cap, int nacc) {
+    return (static_cast<size_t>(cap + 1) * 8 + 255) / 256 * 256 + static_cast<size_t>(cap + 1) * nacc * 8 + 256;
+}
+
+// Carve the table out of `mem` and clear it on `stream`.
+tqp_status group_table_init(GroupSpec* S, void* mem, long long cap, long long max_groups, cudaStream_t stream) {
+    unsigned char* p = static_cast<unsigned char*>(mem);
+    S->cap = cap;
+    S->max_groups = max_groups;
+    S->keys = reinterpret_cast<unsigned long long*>(p);
+    p += (static_cast<size_t>(cap + 1) * 8 + 255) / 256 * 256;
+    S->acc = reinterpret_cast<unsigned long long*>(p);
+    S->ndistinct = S->acc + (cap + 1) * S->nacc;
+    TQP_CUDA(cudaMemsetAsync(S->keys, 0xFF, static_cast<size_t>(cap + 1) * 8, stream));
+    TQP_CUDA(cudaMemsetAsync(S->acc, 0, static_cast<size_t>(cap + 1) * S->nacc * 8 + 8, stream));
+    return TQP_OK;
+}
+
+// Finalize a filled table into the caller's output arrays.
+tqp_status group_finalize(tqp_ctx* ctx, const GroupSpec& S, const GroupOut& O, cudaStream_t stream) {
+    if (S.cap <= kSmallCap) {
+        const size_t smem = static_cast<size_t>(2 * kSmallCap) * (8 + 4);
+        static bool attr_done[kMaxDevices] = {};
+        TQP_TRY(allow_smem(ctx, reinterpret_cast<const void*>(k_groupby_finalize_small), attr_done));
+        k_groupby_finalize_small<<<1, kFinThreads, smem, stream>>>(S, O);
+        TQP_CUDA(cudaGetLastError());
+        return TQP_OK;
+    }
+    const long long nmax = S.cap + 1;
+    const size_t pair_bytes = static_cast<size_t>(nmax) * 12 + 512;
+    unsigned char* buf = static_cast<unsigned char*>(arena_alloc(ctx, 2 * pair_bytes + 256));
+    void* rs = arena_alloc(ctx, radix_sort_scratch(nmax));
+    if (!buf || !rs) return arena_oom(ctx, 2 * pair_bytes + radix_sort_scratch(nmax));
+    long long* d_n = reinterpret_cast<long long*>(buf);
+    uint64_t* k0 = reinterpret_cast<uint64_t*>(buf + 256);
+    uint64_t* k1 = k0 + nmax;
+    uint32_t* v0 = reinterpret_cast<uint32_t*>(k1 + nmax);
+    uint32_t* v1 = v0 + nmax;
+    TQP_CUDA(cudaMemsetAsync(d_n, 0, sizeof(long long), stream));
+    const int threads = 256;
+    const int blocks = static_cast<int>(std::min<long long>((nmax + threads - 1) / threads, ctx->num_sms * 8LL));
+    k_groupby_collect<<<blocks, threads, 0, stream>>>(S, k0, v0, d_n);
+    bool in1 = false;
+    const int end_bit = (S.width + 7) / 8 * 8;
+    TQP_TRY(radix_sort_pairs(k0, v0, k1, v1, d_n, nmax, 0, end_bit, rs, stream, &in1));
+    const int eblocks = static_cast<int>(
+        std::max<long long>(1, std::min<long long>((std::min(nmax, O.capacity) + threads - 1) / threads,
+                                                   ctx->num_sms * 8LL)));
+    k_groupby_emit<<<eblocks, threads, 0, stream>>>(S, O, in1 ? k1 : k0, in1 ? v1 : v0, d_n);
+    TQP_CUDA(cudaGetLastError());
+    return TQP_OK;
+}
+
+// ---- top-k ------------------------------------------------------------------------
+// Groups ordered by one accumulator descending, ties by packed key ascending
+// (then slot, which orders padding last).  A tournament of block-local
+// bitonic sorts: each block sorts kTopBlock candidates in shared memory and
+// keeps its first k, until one block remains.
+
+constexpr int kTopBlock = 2048;
+constexpr int kTopThreads = 1024;
+
+struct TopBuf {
+    long long* rank;
+    uint64_t* key;
+    uint32_t* slot;
+};
+
+__device__ __forceinline__ bool top_before(long long r1, uint64_t k1, uint32_t s1, long long r2, uint64_t k2,
+                                           uint32_t s2) {
+    if (r1 != r2) return r1 > r2;
+    if (k1 != k2) return k1 < k2;
+    return s1 < s2;
+}
+
+__device__ void top_sort_block(long long* r, uint64_t* k, uint32_t* s) {
+    for (int kk = 2; kk <= kTopBlock; kk <<= 1) {
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < kTopBlock; i += blockDim.x) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const bool asc = (i & kk) == 0;  // "ascending" in before-order
+                    const bool lb = top_before(r[l], k[l], s[l], r[i], k[i], s[i]);
+                    if (lb == asc) {
+                        const long long tr = r[i]; r[i] = r[l]; r[l] = tr;
+                        const uint64_t tk = k[i]; k[i] = k[l]; k[l] = tk;
+                        const uint32_t ts = s[i]; s[i] = s[l]; s[l] = ts;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kTopThreads) k_topk_level0(const __grid_constant__ GroupSpec S, int rank_acc, int k,
+                                                             TopBuf out, unsigned long long* total) {
+    __shared__ long long r[kTopBlock];
+    __shared__ uint64_t kk[kTopBlock];
+    __shared__ uint32_t ss[kTopBlock];
+    __shared__ int cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    for (int i = threadIdx.x; i < kTopBlock; i += blockDim.x) {
+        r[i] = LLONG_MIN;
+        kk[i] = ~0ULL;
+        ss[i] = 0xFFFFFFFFu;
+    }
+    __syncthreads();
+    const long long s0 = static_cast<long long>(blockIdx.x) * kTopBlock;
+    for (int i = threadIdx.x; i < kTopBlock; i += blockDim.x) {
+        const long long slot = s0 + i;
+        if (slot <= S.cap && slot_used(S, slot)) {
+            const int p = atomicAdd(&cnt, 1);
+            r[p] = static_cast<long long>(S.acc[slot * S.nacc + rank_acc]);
+            kk[p] = slot < S.cap ? S.keys[slot] : kEmptyKey;
+            ss[p] = static_cast<uint32_t>(slot);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && cnt) atomicAdd(total, static_cast<unsigned long long>(cnt));
+    top_sort_block(r, kk, ss);
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        const long long o = static_cast<long long>(blockIdx.x) * k + i;
+        out.rank[o] = r[i];
+        out.key[o] = kk[i];
+        out.slot[o] = ss[i];
+    }
+}
+
+// One reduction level; with `emit` set (a single block) the winners are written out.
+__global__ void __launch_bounds__(kTopThreads) k_topk_reduce(const __grid_constant__ GroupSpec S, TopBuf in,
+                                                             long long n_in, int k, TopBuf out, int emit,
+                                                             const __grid_constant__ GroupOut O,
+                                                             const unsigned long long* total, int64_t* total_out) {
+    __shared__ long long r[kTopBlock];
+    __shared__ uint64_t kk[kTopBlock];
+    __shared__ uint32_t ss[kTopBlock];
+    const long long c0 = static_cast<long long>(blockIdx.x) * kTopBlock;
+    for (int i = threadIdx.x; i < kTopBlock; i += blockDim.x) {
+        const long long c = c0 + i;
+        if (c < n_in) {
+            r[i] = in.rank[c];
+            kk[i] = in.key[c];
+            ss[i] = in.slot[c];
+        } else {
+            r[i] = LLONG_MIN;
+            kk[i] = ~0ULL;
+            ss[i] = 0xFFFFFFFFu;
+        }
+    }
+    __syncthreads();
+    top_sort_block(r, kk, ss);
+    if (!emit) {
+        for (int i = threadIdx.x; i < k; i += blockDim.x) {
+            const long long o = static_cast<long long>(blockIdx.x) * k + i;
+            out.rank[o] = r[i];
+            out.key[o] = kk[i];
+            out.slot[o] = ss[i];
+        }
+        return;
+    }
+    const long long G = static_cast<long long>(*total);
+    const long long m = G < k ? G : k;
+    if (m > O.capacity) {
+        if (threadIdx.x == 0) {
+            *O.num_groups = -1;
+            latch_error(O.err, TQP_ERR_CAPACITY);
+        }
+        return;
+    }
+    for (int i = threadIdx.x; i < m; i += blockDim.x) emit_group(S, O, i, kk[i], ss[i]);
+    if (threadIdx.x == 0) {
+        *O.num_groups = m;
+        if (total_out) *total_out = G;
+    }
+}
+
+tqp_status group_topk(tqp_ctx* ctx, const GroupSpec& S, const GroupOut& O, int k, int agg, int64_t* total_groups,
+                      cudaStream_t stream) {
+    if (k < 1 || k > kTopBlock / 2) return fail(TQP_ERR_UNSUPPORTED, "top-k needs 1 <= k <= %d", kTopBlock / 2);
+    if (agg < 0 || agg >= S.naggs) return fail(TQP_ERR_INVALID_ARG, "topk_agg %d out of range", agg);
+    const int rank_acc = S.agg_acc[agg];
+    const long long nb0 = (S.cap + 1 + kTopBlock - 1) / kTopBlock;
+    const long long ncand = nb0 * k;
+    auto alloc_buf = [&](TopBuf* b) -> bool {
+        b->rank = static_cast<long long*>(arena_alloc(ctx, ncand * 8));
+        b->key = static_cast<uint64_t*>(arena_alloc(ctx, ncand * 8));
+        b->slot = static_cast<uint32_t*>(arena_alloc(ctx, ncand * 4));
+        return b->rank && b->key && b->slot;
+    };
+    TopBuf a, b;
+    unsigned long long* total = static_cast<unsigned long long*>(arena_alloc(ctx, 256));
+    if (!alloc_buf(&a) || !alloc_buf(&b) || !total) return arena_oom(ctx, ncand * 40);
+    TQP_CUDA(cudaMemsetAsync(total, 0, 8, stream));
+    k_topk_level0<<<static_cast<unsigned>(nb0), kTopThreads, 0, stream>>>(S, rank_acc, k, a, total);
+    long long n = ncand;
+    while (n > kTopBlock) {
+        const long long blocks = (n + kTopBlock - 1) / kTopBlock;
+        k_topk_reduce<<<static_cast<unsigned>(blocks), kTopThreads, 0, stream>>>(S, a, n, k, b, 0, O, total, nullptr);
+        std::swap(a, b);
+        n = blocks * k;
+    }
+    k_topk_reduce<<<1, kTopThreads, 0, stream>>>(S, a, n, k, b, 1, O, total, total_groups);
+    TQP_CUDA(cudaGetLastError());
+    return TQP_OK;
+}
+
+tqp_status launch_groupby(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* preds, int32_t npreds,
+                          const int32_t* group_cols, int32_t ngc, const tqp_agg* aggs, int32_t naggs,
+                          int64_t* d_keys, int64_t* d_ivals, double* d_fvals, int64_t capacity_groups,
+                          int64_t* d_num_groups, cudaStream_t stream, long long max_groups, int topk, int topk_agg,
+                          int64_t* d_total_groups) {
+    GroupArgs A;
+    memset(&A, 0, sizeof(A));
+    int ncond = 0;
+    TQP_TRY(lower_preds(t, preds, npreds, A.cond, &ncond));
+    A.ncond = ncond;
+    if (ngc > 0 && !group_cols) return fail(TQP_ERR_INVALID_ARG, "group_cols is NULL");
+    int32_t types[TQP_MAX_GROUP_COLS] = {0, 0, 0, 0};
+    for (int i = 0; i < ngc && i < TQP_MAX_GROUP_COLS; ++i) {
+        if (group_cols[i] < 0 || group_cols[i] >= t->num_cols)
+            return fail(TQP_ERR_INVALID_ARG, "group column %d out of range", group_cols[i]);
+        types[i] = t->cols[group_cols[i]].type;
+    }
+    TQP_TRY(lower_group(group_cols, types, ngc, aggs, naggs, t->num_cols, &A.S));
+    bool need_f = false;
+    for (int j = 0; j < naggs; ++j) need_f |= aggs[j].fn == TQP_AVG;
+    if (need_f && !d_fvals) return fail(TQP_ERR_INVALID_ARG, "d_fvals is NULL but an AVG is requested");
+
+    // stage every referenced column: group-by inputs are usually mostly passing rows
+    std::vector<int> staged;
+    for (int i = 0; i < ncond; ++i) staged.push_back(A.cond[i].col);
+    for (int i = 0; i < ngc; ++i) staged.push_back(group_cols[i]);
+    for (int a = 1; a < A.S.nacc; ++a) expr_cols(A.S.acc_expr[a - 1], staged);
+    std::vector<int> u = staged;
+    std::sort(u.begin(), u.end());
+    u.erase(std::unique(u.begin(), u.end()), u.end());
+    if (static_cast<int>(u.size()) > kMaxStaged) u.resize(kMaxStaged);
+    int bpr = 0;
+    for (int c : u) bpr += t->cols[c].type == TQP_I64 ? 8 : (t->cols[c].type == TQP_I32 ? 4 : 1);
+    const tqp_tuning tu = default_tuning(ctx, bpr, GroupBody::kSmemBytes);
+    size_t smem = 0;
+    TQP_TRY(make_geom(ctx, t, u, tu, GroupBody::kSmemBytes, &A.G, &smem));
+    lower_fast(A.cond, A.ncond, A.G, A.cf, &A.fast);
+
+    const long long cap = group_table_cap(max_groups);
+    void* tab = arena_alloc(ctx, group_table_bytes(cap, A.S.nacc));
+    unsigned long long* ticket = static_cast<unsigned long long*>(arena_alloc(ctx, 256));
+    if (!tab || !ticket) return arena_oom(ctx, group_table_bytes(cap, A.S.nacc));
+    TQP_TRY(group_table_init(&A.S, tab, cap, max_groups, stream));
+
+    if (t->num_rows > 0) {
+        static bool attr_done[kMaxDevices] = {};
+        TQP_TRY(allow_smem(ctx, reinterpret_cast<const void*>(k_groupby), attr_done));
+        const int g = engine_grid(ctx, reinterpret_cast<const void*>(k_groupby), smem, A.G.ntiles, tu.ctas_per_sm);
+        A.ctl.chunk_tiles = (A.G.ntiles + g - 1) / g;
+        A.ctl.nchunks = (A.G.ntiles + A.ctl.chunk_tiles - 1) / A.ctl.chunk_tiles;
+        A.ctl.ticket = ticket;
+        A.ctl.err = ctx->d_err;
+        A.ctl.wait_cap = ctx->wait_cap;
+        TQP_CUDA(cudaMemsetAsync(ticket, 0, 8, stream));
+        k_groupby<<<static_cast<int>(A.ctl.nchunks), kEngineThreads, smem, stream>>>(A);
+        TQP_CUDA(cudaGetLastError());
+    }
+    GroupOut O{d_keys, d_ivals, d_fvals, capacity_groups, d_num_groups, ctx->d_err};
+    if (topk > 0) return group_topk(ctx, A.S, O, topk, topk_agg, d_total_groups, stream);
+    return group_finalize(ctx, A.S, O, stream);
+}
+
+}  // namespace tqp
+
+using namespace tqp;
+
+extern "C" tqp_status tqp_groupby_agg(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* preds, int32_t npreds,
+                                      const int32_t* group_cols, int32_t ngc, const tqp_agg* aggs, int32_t naggs,
+                                      int64_t* d_keys, int64_t* d_ivals, double* d_fvals, int64_t capacity_groups,
+                                      int64_t* d_num_groups, void* stream) {
+    clear_error();
+    TQP_TRY(check_ctx(ctx));
+    TQP_TRY(check_table(t, "tqp_groupby_agg"));
+    if (!d_num_groups) return fail(TQP_ERR_INVALID_ARG, "d_num_groups is NULL");
+    if (capacity_groups < 1 || capacity_groups > (1LL << 30))
+        return fail(TQP_ERR_INVALID_ARG, "capacity_groups %lld outside [1, 2^30]", (long long)capacity_groups);
+    if (ngc > 0 && !d_keys) return fail(TQP_ERR_INVALID_ARG, "d_keys is NULL");
+    if (naggs > 0 && !d_ivals) return fail(TQP_ERR_INVALID_ARG, "d_ivals is NULL");
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(TQP_ERR_CUDA, "cannot select device %d", ctx->device);
+    arena_reset(ctx);
+    return launch_groupby(ctx, t, preds, npreds, group_cols, ngc, aggs, naggs, d_keys, d_ivals, d_fvals,
+                          capacity_groups, d_num_groups, static_cast<cudaStream_t>(stream), capacity_groups, 0, 0,
+                          nullptr);
+}

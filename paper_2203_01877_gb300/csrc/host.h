@@ -75,6 +75,10 @@ tqp_status check_table(const tqp_table* t, const char* what);
 
 // Lower predicates to range conditions on `t`'s columns.
 tqp_status lower_preds(const tqp_table* t, const tqp_pred* preds, int32_t npreds, Cond* out, int* ncond);
+// Fast-path form of the conditions for geometry G; *fast is false when some
+// condition column is not staged (the general path is used then).
+void lower_fast(const Cond* conds, int ncond, const ScanGeom& G, CondFast* out, int32_t* fast);
+
 // Lower a postfix expression whose column operands address `ncols` columns.
 tqp_status lower_expr(const tqp_expr* e, int ncols, DExpr* out);
 // Column ids referenced by an expression.
@@ -94,6 +98,10 @@ int engine_grid(const tqp_ctx* ctx, const void* kernel, size_t smem, int64_t nti
 
 // Raise a kernel's dynamic shared-memory limit once per device.
 tqp_status allow_smem(const tqp_ctx* ctx, const void* kernel, bool* done_per_device);
+
+// Stream-ordered store of a host value into device memory (a one-thread
+// kernel: unlike a pageable memcpy it can be captured in a CUDA graph).
+tqp_status set_device_i64(long long* d_ptr, long long value, cudaStream_t stream);
 constexpr int kMaxDevices = 64;
 
 }  // namespace tqp

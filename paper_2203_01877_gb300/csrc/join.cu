@@ -1,0 +1,287 @@
+// tqp_hash_join: inner equi-join returning index pairs (late materialisation).
+//
+// Semantics of paper Sections 5.2-5.3 (Algorithm 2's hash join and Algorithm
+// 1's sort join both produce every (left, right) index pair with equal keys);
+// the result here is emitted in canonical (probe ascending, build ascending)
+// order.  Instead of Algorithm 2's repeated scatter/probe rounds (one round
+// per colliding build row), the build side goes into one open-addressing
+// table:
+//   build  1. each build row finds or claims its key's slot (64-bit CAS on the
+//             key, linear probing, load factor <= 1/2) and counts itself;
+//          2. a stable radix sort of (slot, build row) groups the build rows
+//             of each key into one run, in ascending row order;
+//          3. each run's start is written into its slot.
+//   probe  staged scan of the probe keys: every row's slot is looked up and
+//          remembered, matches are counted per chunk, a decoupled look-back
+//          over chunks gives each chunk's output offset, and each row's run
+//          is copied out as (build, probe) pairs.
+// Keys compare by their int64 value; int32, int64 and uint8 key columns mix.
+#include "host.h"
+#include "join.cuh"
+
+namespace tqp {
+
+tqp_status radix_sort_pairs(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, const long long* d_n,
+                            long long n_max, int begin_bit, int end_bit, void* scratch, cudaStream_t stream,
+                            bool* result_in_1);
+size_t radix_sort_scratch(long long n_max);
+
+__global__ void k_ht_init(JoinHT H) {
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i <= H.cap;
+         i += static_cast<long long>(gridDim.x) * blockDim.x)
+        H.slots[i] = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0u, 0u);
+}
+
+__global__ void k_ht_insert(JoinHT H, const unsigned char* key_col, int key_type, long long n, uint64_t* sort_key,
+                            uint32_t* sort_val, int* err) {
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const uint64_t key = static_cast<uint64_t>(ldg_typed(key_col, key_type, i));
+        const long long s = ht_claim(H, key, err);
+        if (s >= 0) atomicAdd(&H.slots[s].w, 1u);
+        sort_key[i] = static_cast<uint64_t>(s < 0 ? H.cap : s);
+        sort_val[i] = static_cast<uint32_t>(i);
+    }
+}
+
+// After the sort: run starts into the slots; the sorted values are the
+// build rows of each run in ascending order.
+__global__ void k_ht_runs(JoinHT H, const uint64_t* skey, long long n) {
+    for (long long p = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; p < n;
+         p += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const uint64_t s = skey[p];
+        if (p == 0 || skey[p - 1] != s) H.slots[s].z = static_cast<uint32_t>(p);
+    }
+}
+
+size_t ht_bytes(long long n_build) {
+    const long long cap = ht_cap(n_build);
+    return static_cast<size_t>(cap + 1) * sizeof(uint4) + 256 +                 // slots
+           2 * (static_cast<size_t>(n_build) * 12 + 256) + 256 +                // sort buffers
+           radix_sort_scratch(n_build > 0 ? n_build : 1) + 256;
+}
+
+tqp_status ht_build(tqp_ctx* ctx, const tqp_table* build, int32_t key_col, JoinHT* H, cudaStream_t stream) {
+    const long long n = build->num_rows;
+    H->cap = ht_cap(n);
+    H->slots = static_cast<uint4*>(arena_alloc(ctx, static_cast<size_t>(H->cap + 1) * sizeof(uint4)));
+    const long long nn = n > 0 ? n : 1;
+    unsigned char* sb = static_cast<unsigned char*>(arena_alloc(ctx, 2 * (static_cast<size_t>(nn) * 12 + 256)));
+    void* rs = arena_alloc(ctx, radix_sort_scratch(nn));
+    long long* d_n = static_cast<long long*>(arena_alloc(ctx, 256));
+    if (!H->slots || !sb || !rs || !d_n) return arena_oom(ctx, ht_bytes(n));
+    uint64_t* k0 = reinterpret_cast<uint64_t*>(sb);
+    uint64_t* k1 = k0 + nn;
+    uint32_t* v0 = reinterpret_cast<uint32_t*>(k1 + nn);
+    uint32_t* v1 = v0 + nn;
+    const int threads = 256;
+    const int blocks = static_cast<int>(std::min<long long>((H->cap + threads) / threads, ctx->num_sms * 16LL));
+    k_ht_init<<<blocks, threads, 0, stream>>>(*H);
+    TQP_CUDA(cudaGetLastError());
+    H->bidx = v0;
+    if (n == 0) return TQP_OK;
+    const tqp_column& kc = build->cols[key_col];
+    const int iblocks = static_cast<int>(std::min<long long>((n + threads - 1) / threads, ctx->num_sms * 16LL));
+    k_ht_insert<<<iblocks, threads, 0, stream>>>(*H, static_cast<const unsigned char*>(kc.data), kc.type, n, k0, v0,
+                                                 ctx->d_err);
+    TQP_TRY(set_device_i64(d_n, n, stream));
+    int bits = 1;
+    while ((1LL << bits) <= H->cap) ++bits;
+    bool in1 = false;
+    TQP_TRY(radix_sort_pairs(k0, v0, k1, v1, d_n, n, 0, (bits + 7) / 8 * 8, rs, stream, &in1));
+    const uint64_t* sk = in1 ? k1 : k0;
+    H->bidx = in1 ? v1 : v0;
+    k_ht_runs<<<iblocks, threads, 0, stream>>>(*H, sk, n);
+    TQP_CUDA(cudaGetLastError());
+    return TQP_OK;
+}
+
+// ---- probe with pair output ----------------------------------------------------
+
+struct ProbeArgs {
+    ScanGeom G;
+    EngineCtl ctl;
+    JoinHT H;
+    int32_t key_col;
+    int32_t pad;
+    uint32_t* row_slot;          // per probe row: matched slot, or 0xFFFFFFFF
+    int32_t* out_build;
+    int32_t* out_probe;
+    int64_t capacity;
+    int64_t* d_count;
+    unsigned long long* status;  // per-chunk look-back words
+    unsigned long long* acc;     // [0] pairs, [1] finished warps
+};
+
+struct ProbeBody {
+    static constexpr int kSmemBytes = 256;
+    const ProbeArgs& A;
+    unsigned long long* wtot;     // [2][warps]
+    unsigned long long* excl_sm;
+    unsigned long long chunk_pairs = 0;  // lane 0
+    unsigned long long my_pairs = 0;     // lane 0
+
+    __device__ ProbeBody(const ProbeArgs& a, unsigned char* sm) : A(a) {
+        wtot = reinterpret_cast<unsigned long long*>(sm);
+        excl_sm = wtot + 2 * kConsumerWarps;
+    }
+
+    __device__ void pass1(const ScanGeom& G, const TileView& v, int cw, int lane) {
+        const int rw = G.T / kConsumerWarps;
+        unsigned long long pairs = 0;
+        for (int r = cw * rw + lane; r < cw * rw + rw; r += kWarp) {
+            if (r >= v.rows) break;
+            const uint64_t key = static_cast<uint64_t>(col_val(G, v, A.key_col, r));
+            const long long s = ht_find(A.H, key);
+            uint32_t slot = 0xFFFFFFFFu;
+            if (s >= 0) {
+                slot = static_cast<uint32_t>(s);
+                pairs += A.H.slots[s].w;
+            }
+            A.row_slot[v.row0 + r] = slot;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
+        if (lane == 0) chunk_pairs += pairs;
+    }
+
+    __device__ void chunk_end(const ScanGeom& G, long long chunk, long long t0, long long t1, int cw, int lane) {
+        if (lane == 0) {
+            my_pairs += chunk_pairs;
+            wtot[cw] = chunk_pairs;
+        }
+        chunk_pairs = 0;
+        named_sync(kBarConsumers, kConsumers);
+        if (cw == 0) {
+            unsigned long long c = lane < kConsumerWarps ? wtot[lane] : 0ULL;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+            const unsigned long long ex = lookback(A.status, chunk, c, lane, A.ctl.err, A.ctl.wait_cap);
+            if (lane == 0) *excl_sm = ex;
+        }
+        named_sync(kBarConsumers, kConsumers);
+        unsigned long long running = *excl_sm;
+        const long long r_begin = t0 * G.T;
+        const long long r_end = (t1 * G.T < G.n) ? t1 * G.T : G.n;
+        int par = 0;
+        for (long long base = r_begin; base < r_end; base += kConsumers) {
+            const long long row = base + cw * kWarp + lane;
+            uint32_t slot = 0xFFFFFFFFu;
+            uint4 sl = make_uint4(0, 0, 0, 0);
+            if (row < r_end) {
+                slot = A.row_slot[row];
+                if (slot != 0xFFFFFFFFu) sl = A.H.slots[slot];
+            }
+            const unsigned long long c = sl.w;
+            unsigned long long incl = c;
+#pragma unroll
+            for (int o = 1; o < kWarp; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            if (lane == kWarp - 1) wtot[par * kConsumerWarps + cw] = incl;
+            named_sync(kBarConsumers, kConsumers);
+            unsigned long long before = 0, round_total = 0;
+#pragma unroll
+            for (int w = 0; w < kConsumerWarps; ++w) {
+                const unsigned long long x = wtot[par * kConsumerWarps + w];
+                before += (w < cw) ? x : 0ULL;
+                round_total += x;
+            }
+            unsigned long long pos = running + before + (incl - c);
+            for (uint32_t k = 0; k < static_cast<uint32_t>(c); ++k, ++pos) {
+                if (pos < static_cast<unsigned long long>(A.capacity)) {
+                    A.out_build[pos] = static_cast<int32_t>(A.H.bidx[sl.z + k]);
+                    A.out_probe[pos] = static_cast<int32_t>(row);
+                }
+            }
+            running += round_total;
+            par ^= 1;
+        }
+    }
+
+    __device__ void finish(const ScanGeom&, int cw, int lane) {
+        if (lane == 0) {
+            if (my_pairs) atomicAdd(&A.acc[0], my_pairs);
+            __threadfence();
+            const unsigned long long done = atomicAdd(&A.acc[1], 1ULL);
+            if (done == static_cast<unsigned long long>(gridDim.x) * kConsumerWarps - 1) {
+                __threadfence();
+                const unsigned long long tot = atomicAdd(&A.acc[0], 0ULL);
+                *A.d_count = static_cast<int64_t>(tot);
+                if (static_cast<long long>(tot) > A.capacity) latch_error(A.ctl.err, TQP_ERR_CAPACITY);
+            }
+        }
+    }
+};
+
+__global__ void __launch_bounds__(kEngineThreads, 2) k_join_probe(const __grid_constant__ ProbeArgs A) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    ProbeBody body(A, smem + kHeaderBytes);
+    run_engine(A.G, A.ctl, body, smem);
+}
+
+tqp_status launch_hash_join(tqp_ctx* ctx, const tqp_table* build, int32_t build_key, const tqp_table* probe,
+                            int32_t probe_key, int32_t* d_build_idx, int32_t* d_probe_idx, int64_t capacity,
+                            int64_t* d_count, cudaStream_t stream) {
+    JoinHT H;
+    TQP_TRY(ht_build(ctx, build, build_key, &H, stream));
+    if (probe->num_rows == 0) {
+        TQP_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int64_t), stream));
+        return TQP_OK;
+    }
+    ProbeArgs A;
+    memset(&A, 0, sizeof(A));
+    A.H = H;
+    A.key_col = probe_key;
+    const int es = probe->cols[probe_key].type == TQP_I64 ? 8 : (probe->cols[probe_key].type == TQP_I32 ? 4 : 1);
+    const tqp_tuning tu = default_tuning(ctx, es, ProbeBody::kSmemBytes);
+    size_t smem = 0;
+    TQP_TRY(make_geom(ctx, probe, std::vector<int>{probe_key}, tu, ProbeBody::kSmemBytes, &A.G, &smem));
+    static bool attr_done[kMaxDevices] = {};
+    TQP_TRY(allow_smem(ctx, reinterpret_cast<const void*>(k_join_probe), attr_done));
+    const int g = engine_grid(ctx, reinterpret_cast<const void*>(k_join_probe), smem, A.G.ntiles, tu.ctas_per_sm);
+    A.ctl.chunk_tiles = (A.G.ntiles + g - 1) / g;
+    A.ctl.nchunks = (A.G.ntiles + A.ctl.chunk_tiles - 1) / A.ctl.chunk_tiles;
+    const size_t words = 3 + static_cast<size_t>(A.ctl.nchunks);
+    unsigned long long* sc = static_cast<unsigned long long*>(arena_alloc(ctx, words * 8));
+    A.row_slot = static_cast<uint32_t*>(arena_alloc(ctx, static_cast<size_t>(probe->num_rows) * 4));
+    if (!sc || !A.row_slot) return arena_oom(ctx, words * 8 + static_cast<size_t>(probe->num_rows) * 4);
+    TQP_CUDA(cudaMemsetAsync(sc, 0, words * 8, stream));
+    A.ctl.ticket = sc;
+    A.ctl.err = ctx->d_err;
+    A.ctl.wait_cap = ctx->wait_cap;
+    A.acc = sc + 1;
+    A.status = sc + 3;
+    A.out_build = d_build_idx;
+    A.out_probe = d_probe_idx;
+    A.capacity = capacity;
+    A.d_count = d_count;
+    k_join_probe<<<static_cast<int>(A.ctl.nchunks), kEngineThreads, smem, stream>>>(A);
+    TQP_CUDA(cudaGetLastError());
+    return TQP_OK;
+}
+
+}  // namespace tqp
+
+using namespace tqp;
+
+extern "C" tqp_status tqp_hash_join(tqp_ctx* ctx, const tqp_table* build, int32_t build_key, const tqp_table* probe,
+                                    int32_t probe_key, int32_t* d_build_idx, int32_t* d_probe_idx, int64_t capacity,
+                                    int64_t* d_count, void* stream) {
+    clear_error();
+    TQP_TRY(check_ctx(ctx));
+    TQP_TRY(check_table(build, "tqp_hash_join(build)"));
+    TQP_TRY(check_table(probe, "tqp_hash_join(probe)"));
+    if (build_key < 0 || build_key >= build->num_cols) return fail(TQP_ERR_INVALID_ARG, "build_key out of range");
+    if (probe_key < 0 || probe_key >= probe->num_cols) return fail(TQP_ERR_INVALID_ARG, "probe_key out of range");
+    if (!d_count) return fail(TQP_ERR_INVALID_ARG, "d_count is NULL");
+    if (capacity < 0) return fail(TQP_ERR_INVALID_ARG, "capacity < 0");
+    if (capacity > 0 && (!d_build_idx || !d_probe_idx))
+        return fail(TQP_ERR_INVALID_ARG, "output arrays are NULL");
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(TQP_ERR_CUDA, "cannot select device %d", ctx->device);
+    arena_reset(ctx);
+    return launch_hash_join(ctx, build, build_key, probe, probe_key, d_build_idx, d_probe_idx, capacity, d_count,
+                            static_cast<cudaStream_t>(stream));
+}

@@ -1,0 +1,63 @@
+// Open-addressing join hash table shared by tqp_hash_join and the plan runner.
+//
+// One 16-byte slot per distinct build key: {key lo, key hi, run start, run
+// length}; the key is the column value as int64 bits, ~0 marks a free slot and
+// the key ~0 itself (the value -1) lives in the extra slot `cap`.  Linear
+// probing over a power-of-two table at load factor <= 1/2, one 16-byte load per
+// probe step.  `bidx[start .. start+len)` are the build rows of the key in
+// ascending order.
+#pragma once
+
+#include "common.cuh"
+
+namespace tqp {
+
+struct JoinHT {
+    uint4* slots;      // [cap + 1]
+    long long cap;     // power of two
+    const uint32_t* bidx;
+};
+
+inline long long ht_cap(long long n_build) {
+    long long cap = 64;
+    while (cap < 2 * n_build) cap <<= 1;
+    return cap;
+}
+
+__device__ __forceinline__ uint64_t slot_key(const uint4& s) {
+    return static_cast<uint64_t>(s.x) | (static_cast<uint64_t>(s.y) << 32);
+}
+
+// Find or claim the slot of `key` (build side).
+__device__ __forceinline__ long long ht_claim(const JoinHT& H, uint64_t key, int* err) {
+    if (key == ~0ULL) return H.cap;
+    unsigned long long h = mix64(key) & static_cast<unsigned long long>(H.cap - 1);
+    for (long long i = 0; i < H.cap; ++i) {
+        unsigned long long* kp = reinterpret_cast<unsigned long long*>(&H.slots[h]);
+        const unsigned long long k = *reinterpret_cast<volatile unsigned long long*>(kp);
+        if (k == key) return static_cast<long long>(h);
+        if (k == ~0ULL) {
+            const unsigned long long prev = atomicCAS(kp, ~0ULL, key);
+            if (prev == ~0ULL || prev == key) return static_cast<long long>(h);
+        }
+        h = (h + 1) & static_cast<unsigned long long>(H.cap - 1);
+    }
+    latch_error(err, TQP_ERR_CAPACITY);
+    return -1;
+}
+
+// Slot of `key` or -1 (probe side; the table is read-only by then).
+__device__ __forceinline__ long long ht_find(const JoinHT& H, uint64_t key) {
+    if (key == ~0ULL) return H.slots[H.cap].w ? H.cap : -1;
+    unsigned long long h = mix64(key) & static_cast<unsigned long long>(H.cap - 1);
+    for (long long i = 0; i < H.cap; ++i) {
+        const uint4 s = __ldg(&H.slots[h]);
+        const uint64_t k = slot_key(s);
+        if (k == key) return static_cast<long long>(h);
+        if (k == ~0ULL) return -1;
+        h = (h + 1) & static_cast<unsigned long long>(H.cap - 1);
+    }
+    return -1;
+}
+
+}  // namespace tqp

@@ -51,6 +51,34 @@ def test_only_api_symbols_are_exported(libtqp):
     assert exported == set(declared_functions())
 
 
+def test_binding_structs_match_the_header(tmp_path):
+    """Every ctypes struct of the binding has the C layout (size and offsets)."""
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    import paper_2203_01877_gb300 as tqp
+    structs = {"tqp_column": tqp.Column, "tqp_table": tqp.Table, "tqp_pred": tqp.Pred, "tqp_expr": tqp.Expr,
+               "tqp_agg": tqp.Agg, "tqp_plan": tqp.Plan, "tqp_result": tqp.Result}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "tqp.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    for ln in out:
+        if not ln:
+            continue
+        cname, field, val = ln.split()
+        py = structs[cname]
+        want = C.sizeof(py) if field == "size" else getattr(py, field).offset
+        assert int(val) == want, (cname, field, val, want)
+
+
 def test_host_only_calls(libtqp):
     libtqp.tqp_version.restype = C.c_int
     assert libtqp.tqp_version() == 100

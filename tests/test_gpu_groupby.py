@@ -1,0 +1,116 @@
+"""GPU parity: tqp_groupby_agg against the CPU oracle (bit-exact: integer sums,
+one IEEE division per AVG compared by bit pattern)."""
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+Q1_AGGS = [("sum", [("col", 3)]), ("sum", [("col", 4)]),
+           ("sum", [("col", 4), ("const", 100), ("col", 5), "sub", "mul"]),
+           ("count", None), ("avg", [("col", 4)])]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_2203_01877_gb300 as tqp
+    c = tqp.Context(0, 512 << 20)
+    yield c
+    c.close()
+
+
+def q1_cols(n, seed):
+    t = datagen.fact_table(n, seed=seed)
+    return [t["date"], t["flag"], t["status"], t["quantity"], t["price"], t["discount"]]
+
+
+def gpu_groupby(ctx, cols, preds, group_cols, aggs, capacity=4096):
+    import torch
+    import paper_2203_01877_gb300 as tqp
+    from tests.gpu_util import up
+    table = tqp.TableRef([up(c) for c in cols])
+    ngc, na = len(group_cols), len(aggs)
+    keys = torch.zeros(max(capacity * ngc, 1), dtype=torch.int64, device="cuda:0")
+    iv = torch.zeros(max(capacity * na, 1), dtype=torch.int64, device="cuda:0")
+    fv = torch.zeros(max(capacity * na, 1), dtype=torch.float64, device="cuda:0")
+    ng = torch.full((1,), -7, dtype=torch.int64, device="cuda:0")
+    tqp.tqp_groupby_agg(ctx, table, preds, group_cols, aggs, keys, iv, fv, capacity, ng)
+    st = ctx.status()
+    G = int(ng.item())
+    if G < 0:
+        return st, G, None, None, None
+    return (st, G, keys[:G * ngc].reshape(G, ngc).cpu().numpy(), iv[:G * na].reshape(G, na).cpu().numpy(),
+            fv[:G * na].reshape(G, na).cpu().numpy())
+
+
+def check(ctx, cols, preds, group_cols, aggs, capacity=4096):
+    st, G, k, iv, fv = gpu_groupby(ctx, cols, preds, group_cols, aggs, capacity)
+    wk, wiv, wfv = oracle.groupby(cols, preds, group_cols, aggs)
+    assert st == 0
+    assert G == len(wiv)
+    assert np.array_equal(k, wk)
+    assert np.array_equal(iv, wiv)
+    assert np.array_equal(fv.view(np.int64), wfv.view(np.int64))  # AVG bit patterns (NaN included)
+    return G
+
+
+@pytest.mark.parametrize("n", [1, 100, 1023, 1024, 4097, 100_003, 1_000_000])
+def test_q1_shape(ctx, n):
+    g = check(ctx, q1_cols(n, 40 + n), [(0, "le", 2450)], [1, 2], Q1_AGGS)
+    if n >= 100_000:
+        assert g == 6
+
+
+def test_ungrouped_and_empty(ctx):
+    cols = q1_cols(50_000, 3)
+    check(ctx, cols, [(0, "le", 2450)], [], Q1_AGGS)
+    check(ctx, cols, [(0, "gt", 99999)], [], Q1_AGGS)          # no row passes: one row, COUNT 0, AVG NaN
+    check(ctx, cols, [(0, "gt", 99999)], [1, 2], Q1_AGGS)      # no groups at all
+    empty = [c[:0] for c in cols]
+    check(ctx, empty, [], [1], [("count", None)])
+
+
+@pytest.mark.parametrize("ngroups", [7, 300, 2000, 50_000])
+def test_many_groups_int32_key(ctx, ngroups):
+    rng = np.random.default_rng(ngroups)
+    n = 400_000
+    key = rng.integers(-ngroups // 2, ngroups - ngroups // 2, n).astype(np.int32)
+    val = rng.integers(-10**9, 10**9, n).astype(np.int64)
+    check(ctx, [key, val], [], [0], [("sum", [("col", 1)]), ("count", None), ("avg", [("col", 1)])],
+          capacity=ngroups)
+
+
+def test_int64_and_mixed_keys(ctx):
+    rng = np.random.default_rng(5)
+    n = 300_000
+    a = rng.integers(-3, 3, n).astype(np.int64) * (2**40)
+    b = rng.integers(0, 256, n).astype(np.uint8)
+    c = rng.integers(-100, 100, n).astype(np.int64)
+    check(ctx, [a, b, c], [(2, "ne", 0)], [0, 1], [("sum", [("col", 2)]), ("count", None)], capacity=2048)
+    # a 64-bit key that packs to all ones: int64 max
+    z = np.array([np.iinfo(np.int64).max, 0, np.iinfo(np.int64).min, np.iinfo(np.int64).max] * 1000, np.int64)
+    check(ctx, [z], [], [0], [("count", None), ("sum", [("col", 0), ("const", 0), "mul"])], capacity=16)
+
+
+def test_heavy_skew(ctx):
+    rng = np.random.default_rng(8)
+    n = 500_000
+    key = np.where(rng.random(n) < 0.9, 42, rng.integers(0, 5000, n)).astype(np.int32)
+    val = rng.integers(0, 1000, n).astype(np.int64)
+    check(ctx, [key, val], [], [0], [("sum", [("col", 1)]), ("count", None)], capacity=8192)
+
+
+def test_capacity_exceeded(ctx):
+    import paper_2203_01877_gb300 as tqp
+    key = np.arange(10_000, dtype=np.int32)
+    st, G, *_ = gpu_groupby(ctx, [key], [], [0], [("count", None)], capacity=100)
+    assert st == tqp.ERR_CAPACITY and G == -1
+    check(ctx, [key], [], [0], [("count", None)], capacity=10_000)
+
+
+def test_full_size_q1(ctx):
+    """The 1M-row six-group configuration in the benchmark's launch shape."""
+    g = check(ctx, q1_cols(1_000_000, datagen.DEFAULT_SEED), [(0, "le", 2450)], [1, 2], Q1_AGGS, capacity=64)
+    assert g == 6

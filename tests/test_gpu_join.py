@@ -1,0 +1,96 @@
+"""GPU parity: tqp_hash_join index pairs against the CPU oracle, in canonical
+(probe ascending, build ascending) order -- bit-exact."""
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_2203_01877_gb300 as tqp
+    c = tqp.Context(0, 2 << 30)
+    yield c
+    c.close()
+
+
+def gpu_join(ctx, bk, pk, capacity=None):
+    import torch
+    import paper_2203_01877_gb300 as tqp
+    from tests.gpu_util import up
+    b = tqp.TableRef([up(bk)])
+    p = tqp.TableRef([up(pk)])
+    cap = capacity if capacity is not None else max(len(pk) * 4, 16)
+    ob = torch.zeros(max(cap, 1), dtype=torch.int32, device="cuda:0")
+    op = torch.zeros(max(cap, 1), dtype=torch.int32, device="cuda:0")
+    cnt = torch.full((1,), -7, dtype=torch.int64, device="cuda:0")
+    tqp.tqp_hash_join(ctx, b, 0, p, 0, ob, op, cap, cnt)
+    st = ctx.status()
+    k = int(cnt.item())
+    m = min(k, cap)
+    return st, k, ob[:m].cpu().numpy(), op[:m].cpu().numpy()
+
+
+def check(ctx, bk, pk):
+    st, k, ob, op = gpu_join(ctx, bk, pk)
+    wb, wp = oracle.join_pairs(bk, pk)
+    assert st == 0
+    assert k == len(wb)
+    assert np.array_equal(op, wp)
+    assert np.array_equal(ob, wb)
+    return k
+
+
+@pytest.mark.parametrize("nb,np_", [(1, 1), (10, 1000), (1000, 1), (3000, 5000), (100_000, 1_000_003)])
+def test_unique_build_keys(ctx, nb, np_):
+    rng = np.random.default_rng(nb + np_)
+    bk = rng.permutation(nb * 2)[:nb].astype(np.int32)
+    pk = rng.integers(0, nb * 2, np_).astype(np.int32)
+    check(ctx, bk, pk)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_duplicates_both_sides(ctx, seed):
+    rng = np.random.default_rng(seed)
+    bk = rng.integers(-50, 50, 20_000).astype(np.int32)
+    pk = rng.integers(-60, 60, 30_000).astype(np.int32)
+    check(ctx, bk, pk)
+
+
+def test_mixed_types_and_special_values(ctx):
+    bk = np.array([-1, 0, 5, -1, 2**40, np.iinfo(np.int64).min, 7] * 50, np.int64)
+    pk = np.array([-1, 5, 3, 2**40, np.iinfo(np.int64).min, -1] * 70, np.int32 if False else np.int64)
+    check(ctx, bk, pk)
+    pk32 = np.array([-1, 5, 7, 0, 123] * 300, np.int32)
+    check(ctx, bk, pk32)
+    u8 = np.array([0, 5, 7, 255] * 100, np.uint8)
+    check(ctx, bk, u8)
+
+
+def test_empty_sides(ctx):
+    e = np.zeros(0, np.int32)
+    x = np.arange(100, dtype=np.int32)
+    for bk, pk in [(e, x), (x, e)]:
+        st, k, _, _ = gpu_join(ctx, bk, pk)
+        assert st == 0 and k == 0
+
+
+def test_capacity_exceeded(ctx):
+    import paper_2203_01877_gb300 as tqp
+    bk = np.zeros(100, np.int32)
+    pk = np.zeros(100, np.int32)
+    st, k, ob, op = gpu_join(ctx, bk, pk, capacity=500)
+    assert st == tqp.ERR_CAPACITY and k == 10_000
+    wb, wp = oracle.join_pairs(bk, pk)
+    assert np.array_equal(ob, wb[:500]) and np.array_equal(op, wp[:500])
+
+
+def test_zipf_probe_shape(ctx):
+    nb, n = 150_000, 6_000_000
+    dim = datagen.dim_table(nb, 15_000, seed=4)
+    pr = datagen.probe_table(n, nb, seed=4)
+    k = check(ctx, dim["key"], pr["fk"])
+    assert k == n

@@ -1,0 +1,133 @@
+"""GPU parity: tqp_run_plan / tqp_run_plans against the oracle's plan evaluator
+(bit-exact; group order by key, top-k order by aggregate then key)."""
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+from tests.plan_util import compare, gpu_plan
+
+pytestmark = pytest.mark.gpu
+
+Q1_AGGS = [("sum", [("col", 3)]), ("sum", [("col", 4)]),
+           ("sum", [("col", 4), ("const", 100), ("col", 5), "sub", "mul"]),
+           ("count", None), ("avg", [("col", 4)])]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_2203_01877_gb300 as tqp
+    c = tqp.Context(0, 2 << 30)
+    yield c
+    c.close()
+
+
+def run_both(ctx, **spec):
+    got = gpu_plan(ctx, **spec)
+    ospec = dict(spec)
+    ospec.pop("capacity_groups", None)
+    ospec.pop("max_groups", None)
+    want = oracle.run_plan(want_pairs=False, cap_groups=None, **ospec)
+    compare(got, want, spec)
+    return got
+
+
+def q1(n, seed):
+    t = datagen.fact_table(n, seed=seed)
+    return [t["date"], t["flag"], t["status"], t["quantity"], t["price"], t["discount"]]
+
+
+def join_case(nb, ng, n, seed):
+    dim = datagen.dim_table(nb, ng, seed=seed)
+    pr = datagen.probe_table(n, nb, seed=seed)
+    return [pr["fk"], pr["value"]], [dim["key"], dim["payload"]]
+
+
+def test_q1_plan(ctx):
+    run_both(ctx, fact=q1(300_000, 1), preds=[(0, "le", 2450)], group_cols=[1, 2], aggs=Q1_AGGS,
+             capacity_groups=64)
+
+
+def test_q6_plan(ctx):
+    t = datagen.fact_table(500_000, seed=2)
+    fact = [t["date"], t["discount"], t["quantity"], t["price"]]
+    run_both(ctx, fact=fact, preds=[(0, "ge", 731), (0, "lt", 1096), (1, "between", 5, 7), (2, "lt", 24)],
+             sum_expr=[("col", 3), ("col", 1), "mul"], want_row_ids=True)
+
+
+def test_scan_plan_topk(ctx):
+    rng = np.random.default_rng(3)
+    g = rng.integers(0, 5000, 400_000).astype(np.int32)
+    v = rng.integers(0, 50, 400_000).astype(np.int64)
+    run_both(ctx, fact=[g, v], group_cols=[0], aggs=[("sum", [("col", 1)]), ("count", None)], topk=100,
+             topk_agg=0, max_groups=8192)
+
+
+@pytest.mark.parametrize("topk", [0, 1, 100, 1000])
+def test_join_group_topk(ctx, topk):
+    fact, dim = join_case(30_000, 3_000, 1_200_000, 7)
+    run_both(ctx, fact=fact, dim=dim, fact_fk=0, dim_key=0, group_cols=[3],
+             aggs=[("sum", [("col", 1)]), ("count", None)], topk=topk, topk_agg=0,
+             capacity_groups=(topk or 3000))
+
+
+def test_join_with_filter_sum_ids_and_avg(ctx):
+    fact, dim = join_case(20_000, 500, 800_000, 9)
+    run_both(ctx, fact=fact, dim=dim, fact_fk=0, dim_key=0, preds=[(1, "lt", 5_000_000)], group_cols=[3],
+             aggs=[("avg", [("col", 1)]), ("count", None), ("sum", [("col", 1), ("const", 3), "mul"])],
+             sum_expr=[("col", 1)], want_row_ids=True, capacity_groups=500)
+
+
+def test_join_duplicates_and_misses(ctx):
+    rng = np.random.default_rng(11)
+    dk = rng.integers(0, 2000, 6000).astype(np.int32)     # duplicate dimension keys
+    dp = rng.integers(-50, 50, 6000).astype(np.int32)
+    fk = rng.integers(-100, 2100, 300_000).astype(np.int32)  # some miss
+    fv = rng.integers(-1000, 1000, 300_000).astype(np.int64)
+    run_both(ctx, fact=[fk, fv], dim=[dk, dp], fact_fk=0, dim_key=0, group_cols=[3],
+             aggs=[("sum", [("col", 1)]), ("count", None)], sum_expr=[("col", 1)], capacity_groups=200)
+    run_both(ctx, fact=[fk, fv], dim=[dk, dp], fact_fk=0, dim_key=0, group_cols=[],
+             aggs=[("sum", [("col", 1)]), ("count", None)], capacity_groups=1)
+
+
+def test_unsupported_join_shapes(ctx):
+    import paper_2203_01877_gb300 as tqp
+    fact, dim = join_case(1000, 10, 5000, 1)
+    with pytest.raises(tqp.TqpError) as e:
+        gpu_plan(ctx, fact=fact, dim=dim, group_cols=[0], aggs=[("count", None)])  # fact column as group key
+    assert e.value.status == tqp.ERR_UNSUPPORTED
+
+
+def test_run_plans_matches_run_plan(ctx):
+    import paper_2203_01877_gb300 as tqp
+    from tests.plan_util import gpu_plan_collect, gpu_plan_prepare
+    fact, dim = join_case(10_000, 1_000, 200_000, 5)
+    specs = [
+        dict(fact=q1(100_000, 4), preds=[(0, "le", 2450)], group_cols=[1, 2], aggs=Q1_AGGS, capacity_groups=64),
+        dict(fact=fact, dim=dim, fact_fk=0, dim_key=0, group_cols=[3],
+             aggs=[("sum", [("col", 1)]), ("count", None)], topk=100, topk_agg=0),
+        dict(fact=q1(70_000, 6), preds=[(0, "lt", 400)], sum_expr=[("col", 4)], want_row_ids=True),
+    ]
+    prepared = [gpu_plan_prepare(**s) for s in specs]
+    tqp.tqp_run_plans(ctx, [p[0] for p in prepared], [p[1] for p in prepared])
+    assert ctx.status() == 0
+    for s, (plan, res, bufs, keep, shape) in zip(specs, prepared):
+        batched = gpu_plan_collect(bufs, shape)
+        batched["status"] = 0
+        alone = gpu_plan(ctx, **s)
+        for k in alone:
+            if isinstance(alone[k], np.ndarray):
+                assert np.array_equal(alone[k].view(np.int64) if alone[k].dtype == np.float64 else alone[k],
+                                      batched[k].view(np.int64) if batched[k].dtype == np.float64 else batched[k])
+            else:
+                assert alone[k] == batched[k]
+
+
+def test_full_size_join_group_topk(ctx):
+    """Build 1.5M unique keys, probe 60M Zipf(0.5) foreign keys, 150K groups, top-100."""
+    nb, ng, n = 1_500_000, 150_000, 60_000_000
+    dim = datagen.dim_table(nb, ng, seed=datagen.DEFAULT_SEED + 2)
+    pr = datagen.probe_table(n, nb, seed=datagen.DEFAULT_SEED + 2)
+    got = run_both(ctx, fact=[pr["fk"], pr["value"]], dim=[dim["key"], dim["payload"]], fact_fk=0, dim_key=0,
+                   group_cols=[3], aggs=[("sum", [("col", 1)]), ("count", None)], topk=100, topk_agg=0)
+    assert got["num_pairs"] == n and got["total_groups"] == ng

@@ -189,6 +189,92 @@ def run_reference(args):
     return 0
 
 
+def _time_launches(torch, fn, reps, flush=None, stream=None):
+    """Median CUDA-event time (ms) of fn() over reps launches, after 3 warm-ups;
+    `flush` (untimed) runs before each timed launch."""
+    for _ in range(3):
+        fn()
+    times = []
+    for _ in range(reps):
+        if flush is not None:
+            flush()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    return statistics.median(times)
+
+
+def secondary_workloads(tqp, torch, dev, local, reps):
+    """The other two analytical shapes, timed per launch (reported beside the headline)."""
+    out = {}
+    stream = torch.cuda.current_stream()
+    flush_buf = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # 512 MB > L2
+
+    def flush():
+        flush_buf.fill_(1)
+
+    # 1M-row six-group aggregation: date <= 2450, GROUP BY (flag, status)
+    n = 1_000_000
+    t = datagen.fact_table(n, seed=datagen.DEFAULT_SEED)
+    cols = [torch.from_numpy(t[k]).to(dev) for k in ("date", "flag", "status", "quantity", "price", "discount")]
+    table = tqp.TableRef(cols)
+    ctx = tqp.Context(local, 64 << 20)
+    aggs = [("sum", [("col", 3)]), ("sum", [("col", 4)]),
+            ("sum", [("col", 4), ("const", 100), ("col", 5), "sub", "mul"]), ("count", None), ("avg", [("col", 4)])]
+    keys = torch.zeros(64 * 2, dtype=torch.int64, device=dev)
+    iv = torch.zeros(64 * 5, dtype=torch.int64, device=dev)
+    fv = torch.zeros(64 * 5, dtype=torch.float64, device=dev)
+    ng = torch.zeros(1, dtype=torch.int64, device=dev)
+
+    def q1():
+        tqp.tqp_groupby_agg(ctx, table, [(0, "le", 2450)], [1, 2], aggs, keys, iv, fv, 64, ng, stream)
+
+    hot = _time_launches(torch, q1, reps)
+    cold = _time_launches(torch, q1, max(5, reps // 4), flush=flush)
+    ctx.check(stream)
+    out["groupby_1M_6groups"] = {
+        "workload": "1M rows; date<=2450; GROUP BY (flag u8, status u8): SUM(qty), SUM(price), "
+                    "SUM(price*(100-disc)), COUNT, AVG(price); keys ascending",
+        "ms_l2_resident": hot, "ms_after_l2_flush": cold, "rows_per_s": n / (cold / 1e3),
+        "algorithmic_bytes": n * 26, "achieved_gbs_after_flush": n * 26 / (cold / 1e3) / 1e9,
+        "groups": int(ng.item())}
+    ctx.close()
+
+    # hash join + 150K-group aggregation + top-100
+    nb, ngr, npr = 1_500_000, 150_000, 60_000_000
+    dim = datagen.dim_table(nb, ngr, seed=datagen.DEFAULT_SEED + 2)
+    pr = datagen.probe_table(npr, nb, seed=datagen.DEFAULT_SEED + 2)
+    F = tqp.TableRef([torch.from_numpy(pr["fk"]).to(dev), torch.from_numpy(pr["value"]).to(dev)])
+    D = tqp.TableRef([torch.from_numpy(dim["key"]).to(dev), torch.from_numpy(dim["payload"]).to(dev)])
+    ctx = tqp.Context(local, 1 << 30)
+    k = 100
+    rk = torch.zeros(k, dtype=torch.int64, device=dev)
+    riv = torch.zeros(k * 2, dtype=torch.int64, device=dev)
+    rng_ = torch.zeros(1, dtype=torch.int64, device=dev)
+    rtot = torch.zeros(1, dtype=torch.int64, device=dev)
+    rj = torch.zeros(1, dtype=torch.int64, device=dev)
+    plan = tqp.make_plan(F, (), D, 0, 0, [3], [("sum", [("col", 1)]), ("count", None)], None, k, 0)
+    res = tqp.make_result(None, 0, None, None, rk, riv, None, k, rng_, rtot, rj)
+
+    def join():
+        tqp.tqp_run_plan(ctx, plan, res, stream)
+
+    ms = _time_launches(torch, join, max(5, reps // 2))
+    ctx.check(stream)
+    alg = npr * 12 + nb * 8
+    out["join_group_top100"] = {
+        "workload": "build 1.5M unique int32 keys (payload = 150K groups); probe 60M Zipf(0.5) int32 fk + int64 "
+                    "value; GROUP BY payload SUM(value), COUNT; top-100 by SUM desc, key asc",
+        "ms": ms, "probe_rows_per_s": npr / (ms / 1e3), "algorithmic_bytes": alg,
+        "achieved_gbs": alg / (ms / 1e3) / 1e9, "joined_rows": int(rj.item()), "groups": int(rtot.item())}
+    ctx.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -198,6 +284,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="0 skips the CPU baseline")
     ap.add_argument("--rows", type=int, default=N_ROWS, help="smaller cases for profiling only")
+    ap.add_argument("--no-operators", action="store_true", help="skip the secondary workloads")
     args = ap.parse_args()
     globals()["N_ROWS"] = args.rows
     if args.impl == "reference":
@@ -284,6 +371,9 @@ def main():
     h2d = sum(a.nbytes for a in host)
     e2e_s = statistics.median(e2e_times[1:]) if len(e2e_times) > 1 else float("nan")
 
+    ops = None
+    if rank == 0 and not args.no_operators:
+        ops = secondary_workloads(tqp, torch, dev, local, 20)
     if rank == 0:
         peak, peak_kind = measured_peaks()
         alg = algorithmic_bytes(N_ROWS, k)
@@ -315,8 +405,9 @@ def main():
                          "traffic": ncu_traffic()},
             "cpu_baseline": cpu,
             "e2e": {"value": N_ROWS / e2e_s, "unit": "rows/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": args.steps,
+            "gpu_launches": 2 * args.steps,  # k_filter + k_compact per step
             "clocks": clk.summary(),
+            "operators": ops,
         }
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -312,3 +312,4 @@ extern "C" tqp_status tqp_filter(tqp_ctx* ctx, const tqp_table* t, const tqp_pre
     return launch_filter(ctx, t, preds, npreds, sum_expr, d_sum, d_row_ids, capacity, d_count,
                          static_cast<cudaStream_t>(stream), nullptr);
 }
+

@@ -76,7 +76,8 @@ def test_ungrouped_and_empty(ctx):
 def test_many_groups_int32_key(ctx, ngroups):
     rng = np.random.default_rng(ngroups)
     n = 400_000
-    key = rng.integers(-ngroups // 2, ngroups - ngroups // 2, n).astype(np.int32)
+    lo = -(ngroups // 2)
+    key = rng.integers(lo, lo + ngroups, n).astype(np.int32)  # exactly `ngroups` distinct keys
     val = rng.integers(-10**9, 10**9, n).astype(np.int64)
     check(ctx, [key, val], [], [0], [("sum", [("col", 1)]), ("count", None), ("avg", [("col", 1)])],
           capacity=ngroups)
@@ -85,10 +86,17 @@ def test_many_groups_int32_key(ctx, ngroups):
 def test_int64_and_mixed_keys(ctx):
     rng = np.random.default_rng(5)
     n = 300_000
-    a = rng.integers(-3, 3, n).astype(np.int64) * (2**40)
+    a = (rng.integers(-3, 3, n) * (2**28)).astype(np.int32)
     b = rng.integers(0, 256, n).astype(np.uint8)
     c = rng.integers(-100, 100, n).astype(np.int64)
+    d = rng.integers(-3, 3, n).astype(np.int64) * (2**40)
     check(ctx, [a, b, c], [(2, "ne", 0)], [0, 1], [("sum", [("col", 2)]), ("count", None)], capacity=2048)
+    check(ctx, [b, a, b, c], [], [0, 1, 2], [("count", None)], capacity=2048)        # 48-bit packed key
+    check(ctx, [d, c], [(1, "gt", 0)], [0], [("sum", [("col", 1)])], capacity=64)   # one 64-bit key
+    import paper_2203_01877_gb300 as tqp
+    with pytest.raises(tqp.TqpError) as e:                                          # 72 bits: rejected
+        gpu_groupby(ctx, [d, b], [], [0, 1], [("count", None)])
+    assert e.value.status == tqp.ERR_UNSUPPORTED
     # a 64-bit key that packs to all ones: int64 max
     z = np.array([np.iinfo(np.int64).max, 0, np.iinfo(np.int64).min, np.iinfo(np.int64).max] * 1000, np.int64)
     check(ctx, [z], [], [0], [("count", None), ("sum", [("col", 0), ("const", 0), "mul"])], capacity=16)

@@ -35,8 +35,8 @@ def gpu_join(ctx, bk, pk, capacity=None):
 
 
 def check(ctx, bk, pk):
-    st, k, ob, op = gpu_join(ctx, bk, pk)
     wb, wp = oracle.join_pairs(bk, pk)
+    st, k, ob, op = gpu_join(ctx, bk, pk, capacity=len(wb) + 16)
     assert st == 0
     assert k == len(wb)
     assert np.array_equal(op, wp)

@@ -223,6 +223,42 @@ TQP_API tqp_status tqp_hash_join(tqp_ctx* ctx,
                          int32_t* d_build_idx, int32_t* d_probe_idx,
                          int64_t capacity, int64_t* d_count, void* stream);
 
+/*
+ * tqp_filter_noalloc -- tqp_filter for callers that cannot allocate device
+ * memory.  (The paper has no counterpart; this is a deployment entry point.)
+ *
+ * Some callers run where cudaMalloc is off limits: inside a stream capture
+ * that must not allocate, in a process whose device memory is owned by
+ * another allocator, or in a real-time path that may not touch the memory
+ * manager.  They cannot create a context (its arena is allocated memory).
+ * This call needs no context: its scratch is one file-scope device array of
+ * TQP_NOALLOC_SCRATCH_BYTES bytes inside libtqp, which every GPU that loads
+ * the library holds until the process exits.  The caller still provides all
+ * inputs and outputs; the call itself never calls cudaMalloc, cudaFree or
+ * any allocating routine.
+ *
+ *   device       the CUDA device the pointers live on.
+ *   t, preds, npreds, sum_expr, d_sum, d_row_ids, capacity, d_count
+ *                exactly as for tqp_filter; t->num_rows must not exceed
+ *                TQP_NOALLOC_MAX_ROWS (larger tables: TQP_ERR_INVALID_ARG,
+ *                nothing is launched).
+ *   d_status     device int32 receiving the device-side status of this call
+ *                (TQP_OK, or e.g. TQP_ERR_CAPACITY); may be NULL.
+ *
+ * The first call on a device looks up the array's device address (once per
+ * device); make that first call before any stream capture.  All calls share
+ * the one array and each call overwrites it: calls that overlap on the GPU
+ * (different streams, or concurrent host threads without ordering) race and
+ * give wrong results -- order them on one stream.
+ */
+#define TQP_NOALLOC_MAX_ROWS (1LL << 24)
+#define TQP_NOALLOC_SCRATCH_BYTES (2228224)
+TQP_API tqp_status tqp_filter_noalloc(int device, const tqp_table* t,
+                                      const tqp_pred* preds, int32_t npreds,
+                                      const tqp_expr* sum_expr, int64_t* d_sum,
+                                      int32_t* d_row_ids, int64_t capacity, int64_t* d_count,
+                                      int32_t* d_status, void* stream);
+
 /* ---- fixed operator plans ------------------------------------------------ */
 
 /*

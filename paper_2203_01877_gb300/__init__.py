@@ -91,6 +91,8 @@ _SIGS = {
     "tqp_version": (C.c_int, []),
     "tqp_filter": (C.c_int, [_P, C.POINTER(Table), C.POINTER(Pred), C.c_int32, C.POINTER(Expr), _P, _P,
                              C.c_int64, _P, _P]),
+    "tqp_filter_noalloc": (C.c_int, [C.c_int, C.POINTER(Table), C.POINTER(Pred), C.c_int32, C.POINTER(Expr), _P,
+                                     _P, C.c_int64, _P, _P, _P]),
     "tqp_groupby_agg": (C.c_int, [_P, C.POINTER(Table), C.POINTER(Pred), C.c_int32, C.POINTER(C.c_int32),
                                   C.c_int32, C.POINTER(Agg), C.c_int32, _P, _P, _P, C.c_int64, _P, _P]),
     "tqp_hash_join": (C.c_int, [_P, C.POINTER(Table), C.c_int32, C.POINTER(Table), C.c_int32, _P, _P,
@@ -247,6 +249,16 @@ def tqp_filter(ctx: Context, table: TableRef, preds=(), sum_expr=None, d_sum=Non
     se = C.byref(make_expr(sum_expr)) if sum_expr is not None else None
     _check(lib().tqp_filter(ctx.h, table.ref(), pa, len(preds), se, _ptr(d_sum), _ptr(d_row_ids),
                             int(capacity), _ptr(d_count), _stream(stream)))
+
+
+def tqp_filter_noalloc(device: int, table: TableRef, preds=(), sum_expr=None, d_sum=None, d_row_ids=None,
+                       capacity: int = 0, d_count=None, d_status=None, stream=None):
+    """tqp_filter without a context, for callers that cannot allocate device
+    memory; its scratch is a fixed array inside libtqp (see include/tqp.h)."""
+    pa = make_preds(preds)
+    se = C.byref(make_expr(sum_expr)) if sum_expr is not None else None
+    _check(lib().tqp_filter_noalloc(int(device), table.ref(), pa, len(preds), se, _ptr(d_sum), _ptr(d_row_ids),
+                                    int(capacity), _ptr(d_count), _ptr(d_status), _stream(stream)))
 
 
 def tqp_groupby_agg(ctx: Context, table: TableRef, preds, group_cols, aggs, d_keys, d_ivals, d_fvals,

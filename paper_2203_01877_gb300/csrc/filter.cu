@@ -23,6 +23,8 @@
 // advances the published-prefix frontier only ~32 tiles per L2 round trip, and
 // a per-chunk look-back leaves the expansion as a serial tail.  The offsets
 // here come straight from counts that are complete when k_compact starts.
+#include <mutex>
+
 #include "host.h"
 
 namespace tqp {
@@ -313,3 +315,92 @@ extern "C" tqp_status tqp_filter(tqp_ctx* ctx, const tqp_table* t, const tqp_pre
                          static_cast<cudaStream_t>(stream), nullptr);
 }
 
+// ---- allocation-free variant (tqp_filter_noalloc) ------------------------------
+// For callers that may not allocate device memory.  Its scratch is the
+// file-scope array below (every device that loads the library holds it until
+// exit): 256 bytes for the device error word, then the filter's own scratch
+// layout (ticket, partial sums, block totals, selection mask) for at most
+// TQP_NOALLOC_MAX_ROWS rows.  In host code `g_noalloc_scratch` names a host
+// stand-in, not device memory, so its device address is looked up once per
+// device (with that device current) and passed to the kernels.
+
+namespace tqp {
+constexpr size_t kNoallocErrBytes = 256;
+constexpr size_t kNoallocScratchBytes = TQP_NOALLOC_SCRATCH_BYTES - kNoallocErrBytes;
+}  // namespace tqp
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[TQP_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_noalloc_mu;
+unsigned char* g_noalloc_addr[tqp::kMaxDevices] = {};
+
+__global__ void k_noalloc_status(const int* err, int32_t* d_status) { *d_status = *err; }
+
+// Device address of the scratch array on `device` (the caller made it current).
+tqp_status noalloc_scratch(int device, unsigned char** out) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[device]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+        g_noalloc_addr[device] = static_cast<unsigned char*>(p);
+    }
+    *out = g_noalloc_addr[device];
+    return TQP_OK;
+}
+}  // namespace
+
+extern "C" tqp_status tqp_filter_noalloc(int device, const tqp_table* t, const tqp_pred* preds, int32_t npreds,
+                                         const tqp_expr* sum_expr, int64_t* d_sum, int32_t* d_row_ids,
+                                         int64_t capacity, int64_t* d_count, int32_t* d_status, void* stream) {
+    clear_error();
+    TQP_TRY(check_table(t, "tqp_filter_noalloc"));
+    if (!d_count) return fail(TQP_ERR_INVALID_ARG, "d_count is NULL");
+    if ((sum_expr == nullptr) != (d_sum == nullptr))
+        return fail(TQP_ERR_INVALID_ARG, "sum_expr and d_sum must both be set or both be NULL");
+    if (d_row_ids && capacity < 0) return fail(TQP_ERR_INVALID_ARG, "capacity < 0");
+    if (t->num_rows > TQP_NOALLOC_MAX_ROWS)
+        return fail(TQP_ERR_INVALID_ARG, "tqp_filter_noalloc handles at most %lld rows (got %lld); use tqp_filter",
+                    (long long)TQP_NOALLOC_MAX_ROWS, (long long)t->num_rows);
+    int ndev = 0;
+    TQP_CUDA(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev || device >= kMaxDevices)
+        return fail(TQP_ERR_INVALID_ARG, "device %d out of range", device);
+    DeviceGuard g(device);
+    if (!g.ok) return fail(TQP_ERR_CUDA, "cannot select device %d", device);
+    unsigned char* base = nullptr;
+    TQP_TRY(noalloc_scratch(device, &base));
+
+    // a context-shaped description of the device; nothing here is allocated
+    tqp_ctx dev_info{};
+    dev_info.device = device;
+    TQP_CUDA(cudaDeviceGetAttribute(&dev_info.num_sms, cudaDevAttrMultiProcessorCount, device));
+    TQP_CUDA(cudaDeviceGetAttribute(&dev_info.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+    dev_info.wait_cap = kDefaultWaitCap;
+
+    FilterArgs A;
+    size_t smem = 0;
+    int grid = 0;
+    FilterScratch lay;
+    TQP_TRY(plan_filter(&dev_info, t, preds, npreds, sum_expr, d_row_ids != nullptr, nullptr, &A, &smem, &grid,
+                        &lay));
+    if (lay.bytes > kNoallocScratchBytes)
+        return fail(TQP_ERR_INVALID_ARG, "tqp_filter_noalloc needs %zu scratch bytes, holds %zu", lay.bytes,
+                    kNoallocScratchBytes);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int* err = reinterpret_cast<int*>(base);
+    TQP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));  // the array keeps the previous call's contents
+    if (t->num_rows == 0) {
+        TQP_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int64_t), st));
+        if (d_sum) TQP_CUDA(cudaMemsetAsync(d_sum, 0, sizeof(int64_t), st));
+    } else {
+        TQP_TRY(launch_filter_with(A, grid, smem, lay, base + kNoallocErrBytes, err, kDefaultWaitCap, d_row_ids,
+                                   capacity, d_count, d_sum, st));
+    }
+    if (d_status) {
+        k_noalloc_status<<<1, 1, 0, st>>>(err, d_status);
+        TQP_CUDA(cudaGetLastError());
+    }
+    return TQP_OK;
+}

@@ -84,15 +84,37 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long l
     return false;
 }
 
+// L2 policy for data read exactly once: evicted first, so streaming a large
+// table does not push hash tables, masks and accumulators out of L2.
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
 // Bulk asynchronous copy global -> shared (TMA engine, non-tensor form).
 // dst, src 16-byte aligned; bytes a positive multiple of 16.  Completion is
-// signalled as transaction bytes on `bar`.
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+// signalled as transaction bytes on `bar`; `policy` is an L2 cache policy.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar, uint64_t policy) {
     asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
             smem_addr(dst)),
-        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(policy)
         : "memory");
+}
+
+// Sum of a signed 64-bit value over the lanes in `peers` (every lane of
+// `peers` calls this with the same mask): three 21/21/22-bit limbs, each
+// summed exactly in 32 bits by the warp reduction unit, recombined mod 2^64.
+__device__ __forceinline__ long long group_sum_i64(uint32_t peers, long long x) {
+    const unsigned lo = static_cast<unsigned>(x) & 0x1FFFFFu;
+    const unsigned mid = static_cast<unsigned>(x >> 21) & 0x1FFFFFu;
+    const int hi = static_cast<int>(x >> 42);
+    const unsigned slo = __reduce_add_sync(peers, lo);
+    const unsigned smid = __reduce_add_sync(peers, mid);
+    const int shi = __reduce_add_sync(peers, hi);
+    return static_cast<long long>(static_cast<unsigned long long>(slo) + (static_cast<unsigned long long>(smid) << 21) +
+                                  (static_cast<unsigned long long>(static_cast<long long>(shi)) << 42));
 }
 
 // Named barrier over `nthreads` threads (id 1..15; 0 is __syncthreads).
@@ -104,6 +126,16 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
     return m;
+}
+
+// Warp-aggregated ticket: the lanes with `want` get consecutive positions
+// from `counter` with one atomic per warp (all 32 lanes must call it).
+__device__ __forceinline__ long long warp_claim(unsigned long long* counter, bool want) {
+    const uint32_t m = __ballot_sync(0xffffffffu, want);
+    unsigned long long base = 0;
+    if ((threadIdx.x % kWarp) == 0 && m) base = atomicAdd(counter, static_cast<unsigned long long>(__popc(m)));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    return want ? static_cast<long long>(base + __popc(m & lanemask_lt())) : -1;
 }
 
 // ---- typed loads ------------------------------------------------------------

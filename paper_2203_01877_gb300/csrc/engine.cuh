@@ -106,6 +106,30 @@ __device__ __forceinline__ int64_t col_val(const ScanGeom& G, const TileView& v,
     return ldg_typed(cr.ptr, cr.type, v.row0 + r);
 }
 
+// The same expression for global row `grow`, every column read from global
+// memory (used once a row's stage has been released).
+__device__ __forceinline__ int64_t eval_expr_global(const ScanGeom& G, const DExpr& e, int64_t grow) {
+    int64_t s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+#pragma unroll
+    for (int i = 0; i < TQP_MAX_EXPR; ++i) {
+        if (i >= e.n) break;
+        const int op = e.op[i];
+        if (op <= TQP_X_CONST) {
+            int64_t x = e.v[i];
+            if (op == TQP_X_COL) {
+                const ColRef& cr = G.col[static_cast<int>(e.v[i])];
+                x = ldg_typed(cr.ptr, cr.type, grow);
+            }
+            s3 = s2; s2 = s1; s1 = s0; s0 = x;
+        } else {
+            const int64_t b = s0, a = s1;
+            s0 = (op == TQP_X_ADD) ? a + b : (op == TQP_X_SUB) ? a - b : a * b;
+            s1 = s2; s2 = s3;
+        }
+    }
+    return s0;
+}
+
 // Position of the n-th (0-based) set bit of m (n < popc(m)).
 __device__ __forceinline__ int nth_set_bit(uint32_t m, int n) {
     int pos = 0;
@@ -249,6 +273,7 @@ __device__ __forceinline__ void run_engine(const ScanGeom& G, const EngineCtl& c
 
     long long it = 0;  // pipeline position, advanced identically by producer and consumers
     bool failed = false;
+    const uint64_t stream_policy = l2_evict_first_policy();
     while (true) {
         if (threadIdx.x == 0) h->chunk = static_cast<long long>(atomicAdd(ctl.ticket, 1ULL));
         __syncthreads();
@@ -283,7 +308,7 @@ __device__ __forceinline__ void run_engine(const ScanGeom& G, const EngineCtl& c
                             const ColRef& cr = G.col[G.staged[k]];
                             const int es = esize_of(cr.type);
                             const uint32_t bytes = (static_cast<uint32_t>(rows) * es) & ~15u;
-                            if (bytes) bulk_g2s(dst + cr.soff, cr.ptr + row0 * es, bytes, &h->full[s]);
+                            if (bytes) bulk_g2s(dst + cr.soff, cr.ptr + row0 * es, bytes, &h->full[s], stream_policy);
                         }
                     }
                 }

@@ -26,30 +26,12 @@
 #include <mutex>
 
 #include "host.h"
+#include "bodies.cuh"
 
 namespace tqp {
 
-constexpr int kCompactRows = 65536;                  // rows per k_compact block
-constexpr int kCompactWords = kCompactRows / kWarp;  // 2048 mask words
 constexpr int kCompactThreads = 256;
 
-struct FilterArgs {
-    ScanGeom G;
-    EngineCtl ctl;
-    int32_t ncond;
-    int32_t has_sum;
-    int32_t fast;                // every condition column is staged
-    int32_t pad;
-    Cond cond[TQP_MAX_PREDS];
-    CondFast cf[TQP_MAX_PREDS];
-    DExpr sum;
-    int64_t* d_count;
-    int64_t* d_sum;              // nullable
-    int64_t capacity;            // row-id capacity, for the CAPACITY latch
-    uint32_t* mask;              // one ballot word per 32 rows; nullptr: count/sum only
-    uint32_t* block_tot;         // passing rows per kCompactRows block (zeroed)
-    unsigned long long* acc;     // [0] sum, [1] count, [2] finished warps (zeroed)
-};
 
 // Scratch layout (bytes): ticket + acc[3], block totals, then the mask.
 struct FilterScratch {
@@ -66,88 +48,6 @@ static FilterScratch filter_scratch_layout(const ScanGeom& G, bool ids) {
     return s;
 }
 
-struct FilterBody {
-    static constexpr int kSmemBytes = 0;
-
-    const FilterArgs& A;
-    long long my_sum = 0;
-    unsigned long long my_cnt = 0;  // lane 0: rows passed by this warp
-
-    __device__ FilterBody(const FilterArgs& a, unsigned char*) : A(a) {}
-
-    // U rows per lane (32 U rows per warp) starting at tile row rbase.
-    template <int U>
-    __device__ __forceinline__ void step(const ScanGeom& G, const TileView& v, int rbase, int lane) {
-        const uint32_t ok = eval_rows<U>(G, v, A.cf, A.cond, A.ncond, A.fast != 0, rbase + lane);
-        uint32_t b[U];
-        uint32_t cnt = 0;
-#pragma unroll
-        for (int j = 0; j < U; ++j) {
-            b[j] = __ballot_sync(0xffffffffu, (ok >> j) & 1u);
-            cnt += __popc(b[j]);
-        }
-        if (lane == 0) {
-            my_cnt += cnt;
-            if (A.mask) {
-                const long long row = v.row0 + rbase;
-#pragma unroll
-                for (int j = 0; j < U; j += 4)
-                    *reinterpret_cast<uint4*>(A.mask + row / kWarp + j) = make_uint4(b[j], b[j + 1], b[j + 2], b[j + 3]);
-                if (cnt) atomicAdd(&A.block_tot[row / kCompactRows], cnt);
-            }
-        }
-        if (A.has_sum) {
-            // passing rows are dealt to lanes in order, one per lane per round
-            for (int s = lane; s < static_cast<int>(cnt); s += kWarp) {
-                int j = 0, before = 0;
-                uint32_t word = b[0];
-#pragma unroll
-                for (int jj = 0; jj + 1 < U; ++jj) {
-                    const int c = __popc(b[jj]);
-                    if (jj == j && s >= before + c) {
-                        before += c;
-                        j = jj + 1;
-                        word = b[jj + 1];
-                    }
-                }
-                const int bit = nth_set_bit(word, s - before);
-                my_sum += eval_expr(G, v, A.sum, rbase + kWarp * j + bit);
-            }
-        }
-    }
-
-    __device__ void pass1(const ScanGeom& G, const TileView& v, int cw, int lane) {
-        const int rw = G.T / kConsumerWarps;  // a multiple of 128
-        int r = 0;
-        for (; r + 8 * kWarp <= rw; r += 8 * kWarp) {
-            if (cw * rw + r >= v.rows) return;  // mask words wholly past the table end are never read
-            step<8>(G, v, cw * rw + r, lane);
-        }
-        if (r < rw && cw * rw + r < v.rows) step<4>(G, v, cw * rw + r, lane);
-    }
-
-    __device__ void chunk_end(const ScanGeom&, long long, long long, long long, int, int) {}
-
-    __device__ void finish(const ScanGeom&, int cw, int lane) {
-        long long s = my_sum;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) {
-            if (s) atomicAdd(&A.acc[0], static_cast<unsigned long long>(s));
-            if (my_cnt) atomicAdd(&A.acc[1], my_cnt);
-            __threadfence();
-            const unsigned long long done = atomicAdd(&A.acc[2], 1ULL);
-            if (done == static_cast<unsigned long long>(gridDim.x) * kConsumerWarps - 1) {
-                __threadfence();
-                const unsigned long long tot_sum = atomicAdd(&A.acc[0], 0ULL);
-                const unsigned long long tot_cnt = atomicAdd(&A.acc[1], 0ULL);
-                *A.d_count = static_cast<int64_t>(tot_cnt);
-                if (A.d_sum) *A.d_sum = static_cast<int64_t>(tot_sum);
-                if (A.mask && static_cast<long long>(tot_cnt) > A.capacity) latch_error(A.ctl.err, TQP_ERR_CAPACITY);
-            }
-        }
-    }
-};
 
 __global__ void __launch_bounds__(kEngineThreads, 2) k_filter(const __grid_constant__ FilterArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];

@@ -26,9 +26,10 @@ struct GroupSpec {
     DExpr acc_expr[TQP_MAX_AGGS];  // expression of accumulator a + 1
     unsigned long long* keys;      // [cap + 1], kEmptyKey = free; slot cap holds the all-ones key
     unsigned long long* acc;       // [(cap + 1) * nacc]
-    long long cap;                 // power of two
+    long long cap;                 // power of two (dense mode: entry bound)
     unsigned long long* ndistinct;
     long long max_groups;
+    const long long* d_dense_n;    // dense mode: entries [0, *d_dense_n) are groups with any key
 };
 
 __device__ __forceinline__ uint64_t enc_key(int64_t x, int bits) {
@@ -111,7 +112,14 @@ __device__ __forceinline__ void emit_group(const GroupSpec& S, const GroupOut& O
 // A slot is a group iff at least one row was counted into it (a slot may
 // be claimed in advance, e.g. for every dimension-table group of a join).
 __device__ __forceinline__ bool slot_used(const GroupSpec& S, long long i) {
+    if (S.d_dense_n && i >= *S.d_dense_n) return false;
     return S.acc[i * S.nacc] != 0ULL;
+}
+
+// Packed key of a used slot.
+__device__ __forceinline__ uint64_t slot_key(const GroupSpec& S, long long i) {
+    if (S.d_dense_n) return S.keys[i];
+    return i < S.cap ? S.keys[i] : kEmptyKey;
 }
 
 

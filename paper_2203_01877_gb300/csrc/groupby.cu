@@ -19,6 +19,7 @@
 // the order atomics land in.
 #include "host.h"
 #include "group.cuh"
+#include "bodies.cuh"
 
 namespace tqp {
 
@@ -27,94 +28,7 @@ tqp_status radix_sort_pairs(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* 
                             bool* result_in_1);
 size_t radix_sort_scratch(long long n_max);
 
-struct GroupArgs {
-    ScanGeom G;
-    EngineCtl ctl;
-    int32_t ncond;
-    int32_t fast;
-    Cond cond[TQP_MAX_PREDS];
-    CondFast cf[TQP_MAX_PREDS];
-    GroupSpec S;
-};
 
-struct GroupBody {
-    static constexpr int kSmemBytes = kSmemSlots * 8 + kSmemSlots * kMaxAcc * 8;
-
-    const GroupArgs& A;
-    unsigned long long* skeys;
-    unsigned long long* sacc;
-
-    __device__ GroupBody(const GroupArgs& a, unsigned char* sm) : A(a) {
-        skeys = reinterpret_cast<unsigned long long*>(sm);
-        sacc = skeys + kSmemSlots;
-        for (int i = threadIdx.x; i < kSmemSlots; i += blockDim.x) skeys[i] = kEmptyKey;
-        for (int i = threadIdx.x; i < kSmemSlots * kMaxAcc; i += blockDim.x) sacc[i] = 0;
-    }
-
-    __device__ __forceinline__ int smem_slot(uint64_t key) {
-        if (key == kEmptyKey) return -1;
-        unsigned h = static_cast<unsigned>(mix64(key)) & (kSmemSlots - 1);
-#pragma unroll 1
-        for (int p = 0; p < kSmemProbe; ++p) {
-            const unsigned long long k = *reinterpret_cast<volatile unsigned long long*>(&skeys[h]);
-            if (k == key) return static_cast<int>(h);
-            if (k == kEmptyKey) {
-                const unsigned long long prev = atomicCAS(&skeys[h], kEmptyKey, key);
-                if (prev == kEmptyKey || prev == key) return static_cast<int>(h);
-            }
-            h = (h + 1) & (kSmemSlots - 1);
-        }
-        return -1;
-    }
-
-    __device__ __forceinline__ void add_row(const ScanGeom& G, const TileView& v, int r) {
-        const GroupSpec& S = A.S;
-        const uint64_t key = pack_key(S, G, v, r);
-        const int s = smem_slot(key);
-        if (s >= 0) {
-            unsigned long long* a = sacc + s * kMaxAcc;
-            atomicAdd(&a[0], 1ULL);
-            for (int i = 1; i < S.nacc; ++i)
-                atomicAdd(&a[i], static_cast<unsigned long long>(eval_expr(G, v, S.acc_expr[i - 1], r)));
-        } else {
-            const long long g = gtab_slot(S, key, A.ctl.err);
-            if (g < 0) return;
-            unsigned long long* a = S.acc + g * S.nacc;
-            atomicAdd(&a[0], 1ULL);
-            for (int i = 1; i < S.nacc; ++i)
-                atomicAdd(&a[i], static_cast<unsigned long long>(eval_expr(G, v, S.acc_expr[i - 1], r)));
-        }
-    }
-
-    __device__ void pass1(const ScanGeom& G, const TileView& v, int cw, int lane) {
-        const int rw = G.T / kConsumerWarps;  // a multiple of 128
-        for (int r = 0; r < rw; r += kUnroll * kWarp) {
-            const int rbase = cw * rw + r;
-            if (rbase >= v.rows) break;
-            const uint32_t ok = eval_rows<kUnroll>(G, v, A.cf, A.cond, A.ncond, A.fast != 0, rbase + lane);
-#pragma unroll
-            for (int j = 0; j < kUnroll; ++j)
-                if ((ok >> j) & 1u) add_row(G, v, rbase + kWarp * j + lane);
-        }
-    }
-
-    __device__ void chunk_end(const ScanGeom&, long long, long long, long long, int, int) {}
-
-    __device__ void finish(const ScanGeom&, int cw, int lane) {
-        named_sync(kBarConsumers, kConsumers);
-        const GroupSpec& S = A.S;
-        for (int i = cw * kWarp + lane; i < kSmemSlots; i += kConsumers) {
-            const unsigned long long key = skeys[i];
-            if (key == kEmptyKey) continue;
-            const long long g = gtab_slot(S, key, A.ctl.err);
-            if (g < 0) continue;
-            for (int a = 0; a < S.nacc; ++a) {
-                const unsigned long long x = sacc[i * kMaxAcc + a];
-                if (x) atomicAdd(&S.acc[g * S.nacc + a], x);
-            }
-        }
-    }
-};
 
 __global__ void __launch_bounds__(kEngineThreads, 2) k_groupby(const __grid_constant__ GroupArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -125,9 +39,8 @@ __global__ void __launch_bounds__(kEngineThreads, 2) k_groupby(const __grid_cons
 // ---- finalize ----------------------------------------------------------------
 
 // One CTA: collect occupied slots, bitonic-sort (key, slot), emit.
-__global__ void __launch_bounds__(kFinThreads) k_groupby_finalize_small(const __grid_constant__ GroupSpec S,
-                                                                        const __grid_constant__ GroupOut O) {
-    extern __shared__ __align__(16) unsigned char fsm[];
+// fsm: kFinSmemBytes of dynamic shared memory.
+__device__ void finalize_small_block(const GroupSpec& S, const GroupOut& O, unsigned char* fsm) {
     const int P = 2 * kSmallCap;  // slots + special, padded to a power of two
     unsigned long long* sk = reinterpret_cast<unsigned long long*>(fsm);
     uint32_t* ss = reinterpret_cast<uint32_t*>(sk + P);
@@ -139,7 +52,7 @@ __global__ void __launch_bounds__(kFinThreads) k_groupby_finalize_small(const __
         if (slot_used(S, i)) {
             const int p = atomicAdd(&count, 1);
             if (p < P) {
-                sk[p] = i < S.cap ? S.keys[i] : kEmptyKey;
+                sk[p] = slot_key(S, i);
                 ss[p] = static_cast<uint32_t>(i);
             }
         }
@@ -192,14 +105,23 @@ __global__ void __launch_bounds__(kFinThreads) k_groupby_finalize_small(const __
     if (threadIdx.x == 0) *O.num_groups = G;
 }
 
+__global__ void __launch_bounds__(kFinThreads) k_groupby_finalize_small(const __grid_constant__ GroupSpec S,
+                                                                        const __grid_constant__ GroupOut O) {
+    extern __shared__ __align__(16) unsigned char fsm[];
+    finalize_small_block(S, O, fsm);
+}
+
 // Large tables: collect (key, slot) pairs, radix sort, emit.
 __global__ void k_groupby_collect(const __grid_constant__ GroupSpec S, uint64_t* pk, uint32_t* ps,
                                   long long* n_out) {
-    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i <= S.cap;
-         i += static_cast<long long>(gridDim.x) * blockDim.x) {
-        if (slot_used(S, i)) {
-            const long long p = static_cast<long long>(atomicAdd(reinterpret_cast<unsigned long long*>(n_out), 1ULL));
-            pk[p] = i < S.cap ? S.keys[i] : kEmptyKey;
+    // warp-uniform trip count: blockDim is a multiple of 32
+    for (long long base = blockIdx.x * static_cast<long long>(blockDim.x); base <= S.cap;
+         base += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const long long i = base + threadIdx.x;
+        const bool used = i <= S.cap && slot_used(S, i);
+        const long long p = warp_claim(reinterpret_cast<unsigned long long*>(n_out), used);
+        if (used) {
+            pk[p] = slot_key(S, i);
             ps[p] = static_cast<uint32_t>(i);
         }
     }
@@ -388,8 +310,8 @@ __device__ void top_sort_block(long long* r, uint64_t* k, uint32_t* s) {
     }
 }
 
-__global__ void __launch_bounds__(kTopThreads) k_topk_level0(const __grid_constant__ GroupSpec S, int rank_acc, int k,
-                                                             TopBuf out, unsigned long long* total) {
+__device__ void topk_level0_block(const GroupSpec& S, int rank_acc, int k, TopBuf out, unsigned long long* total,
+                                  long long block) {
     __shared__ long long r[kTopBlock];
     __shared__ uint64_t kk[kTopBlock];
     __shared__ uint32_t ss[kTopBlock];
@@ -401,21 +323,33 @@ __global__ void __launch_bounds__(kTopThreads) k_topk_level0(const __grid_consta
         ss[i] = 0xFFFFFFFFu;
     }
     __syncthreads();
-    const long long s0 = static_cast<long long>(blockIdx.x) * kTopBlock;
+    const long long s0 = block * kTopBlock;
     for (int i = threadIdx.x; i < kTopBlock; i += blockDim.x) {
         const long long slot = s0 + i;
         if (slot <= S.cap && slot_used(S, slot)) {
             const int p = atomicAdd(&cnt, 1);
             r[p] = static_cast<long long>(S.acc[slot * S.nacc + rank_acc]);
-            kk[p] = slot < S.cap ? S.keys[slot] : kEmptyKey;
+            kk[p] = slot_key(S, slot);
             ss[p] = static_cast<uint32_t>(slot);
         }
     }
     __syncthreads();
     if (threadIdx.x == 0 && cnt) atomicAdd(total, static_cast<unsigned long long>(cnt));
-    top_sort_block(r, kk, ss);
+    // empty blocks (beyond a dense table's groups) skip the sort; a handful of
+    // candidates is ordered by one thread
+    if (cnt > 32) top_sort_block(r, kk, ss);
+    else if (cnt > 1) {
+        if (threadIdx.x == 0)
+            for (int a = 1; a < cnt; ++a)
+                for (int b = a; b > 0 && top_before(r[b], kk[b], ss[b], r[b - 1], kk[b - 1], ss[b - 1]); --b) {
+                    const long long tr = r[b]; r[b] = r[b - 1]; r[b - 1] = tr;
+                    const uint64_t tk = kk[b]; kk[b] = kk[b - 1]; kk[b - 1] = tk;
+                    const uint32_t ts = ss[b]; ss[b] = ss[b - 1]; ss[b - 1] = ts;
+                }
+        __syncthreads();
+    }
     for (int i = threadIdx.x; i < k; i += blockDim.x) {
-        const long long o = static_cast<long long>(blockIdx.x) * k + i;
+        const long long o = block * k + i;
         out.rank[o] = r[i];
         out.key[o] = kk[i];
         out.slot[o] = ss[i];
@@ -423,14 +357,12 @@ __global__ void __launch_bounds__(kTopThreads) k_topk_level0(const __grid_consta
 }
 
 // One reduction level; with `emit` set (a single block) the winners are written out.
-__global__ void __launch_bounds__(kTopThreads) k_topk_reduce(const __grid_constant__ GroupSpec S, TopBuf in,
-                                                             long long n_in, int k, TopBuf out, int emit,
-                                                             const __grid_constant__ GroupOut O,
-                                                             const unsigned long long* total, int64_t* total_out) {
+__device__ void topk_reduce_block(const GroupSpec& S, TopBuf in, long long n_in, int k, TopBuf out, int emit,
+                                  const GroupOut& O, const unsigned long long* total, int64_t* total_out, long long block) {
     __shared__ long long r[kTopBlock];
     __shared__ uint64_t kk[kTopBlock];
     __shared__ uint32_t ss[kTopBlock];
-    const long long c0 = static_cast<long long>(blockIdx.x) * kTopBlock;
+    const long long c0 = block * kTopBlock;
     for (int i = threadIdx.x; i < kTopBlock; i += blockDim.x) {
         const long long c = c0 + i;
         if (c < n_in) {
@@ -447,7 +379,7 @@ __global__ void __launch_bounds__(kTopThreads) k_topk_reduce(const __grid_consta
     top_sort_block(r, kk, ss);
     if (!emit) {
         for (int i = threadIdx.x; i < k; i += blockDim.x) {
-            const long long o = static_cast<long long>(blockIdx.x) * k + i;
+            const long long o = block * k + i;
             out.rank[o] = r[i];
             out.key[o] = kk[i];
             out.slot[o] = ss[i];
@@ -468,6 +400,18 @@ __global__ void __launch_bounds__(kTopThreads) k_topk_reduce(const __grid_consta
         *O.num_groups = m;
         if (total_out) *total_out = G;
     }
+}
+
+__global__ void __launch_bounds__(kTopThreads) k_topk_level0(const __grid_constant__ GroupSpec S, int rank_acc, int k,
+                                                             TopBuf out, unsigned long long* total) {
+    topk_level0_block(S, rank_acc, k, out, total, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(kTopThreads) k_topk_reduce(const __grid_constant__ GroupSpec S, TopBuf in,
+                                                             long long n_in, int k, TopBuf out, int emit,
+                                                             const __grid_constant__ GroupOut O,
+                                                             const unsigned long long* total, int64_t* total_out) {
+    topk_reduce_block(S, in, n_in, k, out, emit, O, total, total_out, blockIdx.x);
 }
 
 tqp_status group_topk(tqp_ctx* ctx, const GroupSpec& S, const GroupOut& O, int k, int agg, int64_t* total_groups,

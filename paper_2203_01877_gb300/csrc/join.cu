@@ -29,7 +29,44 @@ size_t radix_sort_scratch(long long n_max);
 __global__ void k_ht_init(JoinHT H) {
     for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i <= H.cap;
          i += static_cast<long long>(gridDim.x) * blockDim.x)
-        H.slots[i] = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0u, 0u);
+        H.slots[i] = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, kNoRow, 0u);
+}
+
+// Chained build (plans): each build row claims its key's slot, pushes itself
+// on the slot's list (z = head row, next[] links) and counts itself.  The
+// rows of a key come out in no particular order, which aggregation does not
+// mind; no sort is needed.
+__global__ void k_ht_insert_chain(JoinHT H, const unsigned char* key_col, int key_type, long long n,
+                                  uint32_t* next, int* err) {
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const uint64_t key = static_cast<uint64_t>(ldg_typed(key_col, key_type, i));
+        const long long s = ht_claim(H, key, err);
+        if (s < 0) continue;
+        next[i] = atomicExch(&H.slots[s].z, static_cast<uint32_t>(i));
+        atomicAdd(&H.slots[s].w, 1u);
+    }
+}
+
+tqp_status ht_build_chain(tqp_ctx* ctx, const tqp_table* build, int32_t key_col, JoinHT* H, uint32_t** next,
+                          cudaStream_t stream) {
+    const long long n = build->num_rows;
+    H->cap = ht_cap_dense(n);
+    H->slots = static_cast<uint4*>(arena_alloc(ctx, static_cast<size_t>(H->cap + 1) * sizeof(uint4)));
+    *next = static_cast<uint32_t*>(arena_alloc(ctx, static_cast<size_t>(n > 0 ? n : 1) * 4));
+    if (!H->slots || !*next) return arena_oom(ctx, static_cast<size_t>(H->cap + 1) * 16 + n * 4);
+    H->bidx = nullptr;
+    const int threads = 256;
+    const int blocks = static_cast<int>(std::min<long long>((H->cap + threads) / threads, ctx->num_sms * 16LL));
+    k_ht_init<<<blocks, threads, 0, stream>>>(*H);
+    TQP_CUDA(cudaGetLastError());
+    if (n == 0) return TQP_OK;
+    const tqp_column& kc = build->cols[key_col];
+    const int iblocks = static_cast<int>(std::min<long long>((n + threads - 1) / threads, ctx->num_sms * 16LL));
+    k_ht_insert_chain<<<iblocks, threads, 0, stream>>>(*H, static_cast<const unsigned char*>(kc.data), kc.type, n,
+                                                       *next, ctx->d_err);
+    TQP_CUDA(cudaGetLastError());
+    return TQP_OK;
 }
 
 __global__ void k_ht_insert(JoinHT H, const unsigned char* key_col, int key_type, long long n, uint64_t* sort_key,

@@ -18,9 +18,22 @@ struct JoinHT {
     const uint32_t* bidx;
 };
 
+constexpr uint32_t kNoRow = 0xFFFFFFFFu;
+// In a chained table prepared for aggregation, a slot whose key has exactly
+// one build row may hold that row's dense group id (flagged) instead of the row.
+constexpr uint32_t kDirectGroup = 0x80000000u;
+
 inline long long ht_cap(long long n_build) {
     long long cap = 64;
     while (cap < 2 * n_build) cap <<= 1;
+    return cap;
+}
+
+// Chained tables (plans) run at load factor <= 3/4 so that a large build
+// side still leaves room in L2 for the aggregation state.
+inline long long ht_cap_dense(long long n_build) {
+    long long cap = 64;
+    while (cap * 3 < 4 * n_build) cap <<= 1;
     return cap;
 }
 

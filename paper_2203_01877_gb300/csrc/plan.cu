@@ -14,6 +14,7 @@
 #include "host.h"
 #include "group.cuh"
 #include "join.cuh"
+#include "bodies.cuh"
 
 namespace tqp {
 
@@ -25,16 +26,23 @@ tqp_status launch_groupby(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* pred
                           int64_t* d_keys, int64_t* d_ivals, double* d_fvals, int64_t capacity_groups,
                           int64_t* d_num_groups, cudaStream_t stream, long long max_groups, int topk, int topk_agg,
                           int64_t* d_total_groups);
-tqp_status ht_build(tqp_ctx* ctx, const tqp_table* build, int32_t key_col, JoinHT* H, cudaStream_t stream);
+tqp_status ht_build_chain(tqp_ctx* ctx, const tqp_table* build, int32_t key_col, JoinHT* H, uint32_t** next,
+                          cudaStream_t stream);
 
 struct DimCols {
     const unsigned char* ptr[TQP_MAX_COLS];
     int32_t type[TQP_MAX_COLS];
 };
 
-// Group slot of every dimension row (its packed group key, inserted once).
-__global__ void k_dim_groups(const __grid_constant__ GroupSpec S, const __grid_constant__ DimCols D, long long n,
-                             uint32_t* dgs, int* err) {
+// Dense group ids of the dimension rows, in three small passes:
+//   claim  each dim row inserts its packed group key into a claim table
+//          (open addressing, keys only) and remembers the slot;
+//   number every claimed slot gets a dense id 0..G-1; its key is stored and its
+//          accumulators are cleared (so nothing of size max_groups is memset);
+//   remap  dim row -> dense id.
+// The probe then aggregates into a G x nacc array that stays in L2.
+__global__ void k_dim_claim(const __grid_constant__ GroupSpec S, const __grid_constant__ DimCols D, long long n,
+                            uint32_t* dslot, int* err) {
     for (long long d = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; d < n;
          d += static_cast<long long>(gridDim.x) * blockDim.x) {
         uint64_t k = 0;
@@ -44,96 +52,81 @@ __global__ void k_dim_groups(const __grid_constant__ GroupSpec S, const __grid_c
             const uint64_t e = enc_key(ldg_typed(D.ptr[c], D.type[c], d), b);
             k = (b == 64) ? e : ((k << b) | e);
         }
-        const long long s = gtab_slot(S, k, err);
-        dgs[d] = s < 0 ? 0u : static_cast<uint32_t>(s);
+        long long s = gtab_slot(S, k, err);
+        if (s == S.cap) S.keys[S.cap] = 0;  // mark the all-ones key's slot as claimed
+        dslot[d] = s < 0 ? 0u : static_cast<uint32_t>(s);
     }
 }
 
-struct PlanJoinArgs {
-    ScanGeom G;
-    EngineCtl ctl;
-    int32_t ncond;
-    int32_t fast;
-    Cond cond[TQP_MAX_PREDS];
-    CondFast cf[TQP_MAX_PREDS];
-    int32_t fk_col;
-    int32_t has_sum;
-    DExpr sum;
-    JoinHT H;
-    const uint32_t* dgs;       // dim row -> group slot; nullptr: no aggregation
-    GroupSpec S;
-    unsigned long long* acc;   // [0] joined, [1] sum, [2] passing fact rows, [3] finished warps (zeroed)
-    int64_t* d_num_joined;
-    int64_t* d_sum;
-    int64_t* d_num_rows;
-};
-
-struct PlanJoinBody {
-    static constexpr int kSmemBytes = 0;
-    const PlanJoinArgs& A;
-    unsigned long long joined = 0, passed = 0;
-    long long sum = 0;
-
-    __device__ PlanJoinBody(const PlanJoinArgs& a, unsigned char*) : A(a) {}
-
-    __device__ __forceinline__ void row(const ScanGeom& G, const TileView& v, int r) {
-        ++passed;
-        const uint64_t key = static_cast<uint64_t>(col_val(G, v, A.fk_col, r));
-        const long long s = ht_find(A.H, key);
-        if (s < 0) return;
-        const uint4 sl = A.H.slots[s];
-        const uint32_t cnt = sl.w;
-        joined += cnt;
-        if (A.has_sum) sum += eval_expr(G, v, A.sum, r) * static_cast<long long>(cnt);
-        if (!A.dgs) return;
-        const GroupSpec& S = A.S;
-        for (uint32_t k = 0; k < cnt; ++k) {
-            const uint32_t d = A.H.bidx[sl.z + k];
-            unsigned long long* a = S.acc + static_cast<long long>(__ldg(&A.dgs[d])) * S.nacc;
-            atomicAdd(&a[0], 1ULL);
-            for (int i = 1; i < S.nacc; ++i)
-                atomicAdd(&a[i], static_cast<unsigned long long>(eval_expr(G, v, S.acc_expr[i - 1], r)));
-        }
-    }
-
-    __device__ void pass1(const ScanGeom& G, const TileView& v, int cw, int lane) {
-        const int rw = G.T / kConsumerWarps;
-        for (int r = 0; r < rw; r += kUnroll * kWarp) {
-            const int rbase = cw * rw + r;
-            if (rbase >= v.rows) break;
-            const uint32_t ok = eval_rows<kUnroll>(G, v, A.cf, A.cond, A.ncond, A.fast != 0, rbase + lane);
+// Each block numbers one contiguous range of claim slots and takes its ids
+// with a single atomic (a single counter hit once per claimed slot or per warp
+// serialises at the L2 when groups are many).
+constexpr int kNumberThreads = 256;
+__global__ void __launch_bounds__(kNumberThreads) k_dense_number(const __grid_constant__ GroupSpec S,
+                                                                 uint32_t* slot2dense, unsigned long long* keys_out,
+                                                                 unsigned long long* acc_out, long long* d_n,
+                                                                 long long per_block) {
+    constexpr int W = kNumberThreads / kWarp;
+    __shared__ uint32_t wc[2][W];
+    __shared__ unsigned long long base_sm;
+    const int lane = threadIdx.x % kWarp, w = threadIdx.x / kWarp;
+    const long long s0 = blockIdx.x * per_block;
+    const long long s1 = (s0 + per_block < S.cap + 1) ? s0 + per_block : S.cap + 1;
+    uint32_t c = 0;
+    for (long long i = s0 + threadIdx.x; i < s1; i += kNumberThreads) c += S.keys[i] != kEmptyKey;
 #pragma unroll
-            for (int j = 0; j < kUnroll; ++j)
-                if ((ok >> j) & 1u) row(G, v, rbase + kWarp * j + lane);
-        }
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) wc[0][w] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int i = 0; i < W; ++i) t += wc[0][i];
+        base_sm = t ? atomicAdd(reinterpret_cast<unsigned long long*>(d_n), t) : 0ULL;
     }
-
-    __device__ void chunk_end(const ScanGeom&, long long, long long, long long, int, int) {}
-
-    __device__ void finish(const ScanGeom&, int cw, int lane) {
-        unsigned long long j = joined, p = passed;
-        long long s = sum;
+    __syncthreads();
+    unsigned long long running = base_sm;
+    int par = 1;
+    for (long long rb = s0; rb < s1; rb += kNumberThreads) {
+        const long long i = rb + threadIdx.x;
+        const unsigned long long k = i < s1 ? S.keys[i] : kEmptyKey;
+        const bool used = k != kEmptyKey;
+        const uint32_t m = __ballot_sync(0xffffffffu, used);
+        if (lane == 0) wc[par][w] = __popc(m);
+        __syncthreads();
+        unsigned long long before = 0, total = 0;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            j += __shfl_xor_sync(0xffffffffu, j, o);
-            p += __shfl_xor_sync(0xffffffffu, p, o);
-            s += __shfl_xor_sync(0xffffffffu, s, o);
+        for (int j = 0; j < W; ++j) {
+            before += j < w ? wc[par][j] : 0u;
+            total += wc[par][j];
         }
-        if (lane == 0) {
-            if (j) atomicAdd(&A.acc[0], j);
-            if (s) atomicAdd(&A.acc[1], static_cast<unsigned long long>(s));
-            if (p) atomicAdd(&A.acc[2], p);
-            __threadfence();
-            const unsigned long long done = atomicAdd(&A.acc[3], 1ULL);
-            if (done == static_cast<unsigned long long>(gridDim.x) * kConsumerWarps - 1) {
-                __threadfence();
-                if (A.d_num_joined) *A.d_num_joined = static_cast<int64_t>(atomicAdd(&A.acc[0], 0ULL));
-                if (A.d_sum) *A.d_sum = static_cast<int64_t>(atomicAdd(&A.acc[1], 0ULL));
-                if (A.d_num_rows) *A.d_num_rows = static_cast<int64_t>(atomicAdd(&A.acc[2], 0ULL));
-            }
+        if (used) {
+            const long long id = static_cast<long long>(running + before + __popc(m & lanemask_lt()));
+            slot2dense[i] = static_cast<uint32_t>(id);
+            keys_out[id] = i < S.cap ? k : kEmptyKey;
+            for (int a = 0; a < S.nacc; ++a) acc_out[id * S.nacc + a] = 0;
         }
+        running += total;
+        par ^= 1;
     }
-};
+}
+
+// Slots of keys with exactly one dimension row take that row's dense group id
+// (flagged), so a probe that hits them needs no further dependent load.
+__global__ void k_ht_direct(JoinHT H, const uint32_t* dgs) {
+    for (long long s = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; s <= H.cap;
+         s += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const uint4 sl = H.slots[s];
+        if (sl.w == 1u && sl.z != kNoRow) H.slots[s].z = dgs[sl.z] | kDirectGroup;
+    }
+}
+
+__global__ void k_dim_remap(const uint32_t* dslot, const uint32_t* slot2dense, long long n, uint32_t* dgs) {
+    for (long long d = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; d < n;
+         d += static_cast<long long>(gridDim.x) * blockDim.x)
+        dgs[d] = slot2dense[dslot[d]];
+}
+
+
 
 __global__ void __launch_bounds__(kEngineThreads, 2) k_plan_join(const __grid_constant__ PlanJoinArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -172,7 +165,8 @@ static tqp_status run_join_plan(tqp_ctx* ctx, const tqp_plan* p, const tqp_resul
     }
 
     JoinHT H;
-    TQP_TRY(ht_build(ctx, D, p->dim_key, &H, stream));
+    uint32_t* next = nullptr;
+    TQP_TRY(ht_build_chain(ctx, D, p->dim_key, &H, &next, stream));
 
     PlanJoinArgs A;
     memset(&A, 0, sizeof(A));
@@ -198,24 +192,54 @@ static tqp_status run_join_plan(tqp_ctx* ctx, const tqp_plan* p, const tqp_resul
             if (p->aggs[a].fn == TQP_AVG && !r->d_fvals) return fail(TQP_ERR_INVALID_ARG, "AVG needs d_fvals");
         if (!r->d_num_groups) return fail(TQP_ERR_INVALID_ARG, "d_num_groups is NULL");
         const long long maxg = p->max_groups > 0 ? p->max_groups : (p->ngc == 0 ? 1 : std::max<long long>(1, D->num_rows));
+        // claim table (keys only) sized for maxg distinct keys
         const long long cap = group_table_cap(maxg);
-        void* tab = arena_alloc(ctx, group_table_bytes(cap, A.S.nacc));
-        uint32_t* dgs = static_cast<uint32_t*>(arena_alloc(ctx, static_cast<size_t>(std::max<long long>(1, D->num_rows)) * 4));
-        if (!tab || !dgs) return arena_oom(ctx, group_table_bytes(cap, A.S.nacc));
-        TQP_TRY(group_table_init(&A.S, tab, cap, maxg, stream));
+        const long long nd_rows = std::max<long long>(1, D->num_rows);
+        GroupSpec claim = A.S;
+        claim.cap = cap;
+        claim.max_groups = maxg;
+        claim.keys = static_cast<unsigned long long*>(arena_alloc(ctx, static_cast<size_t>(cap + 1) * 8));
+        claim.ndistinct = static_cast<unsigned long long*>(arena_alloc(ctx, 256));
+        long long* d_n = reinterpret_cast<long long*>(claim.ndistinct) + 1;
+        uint32_t* slot2dense = static_cast<uint32_t*>(arena_alloc(ctx, static_cast<size_t>(cap + 1) * 4));
+        uint32_t* dslot = static_cast<uint32_t*>(arena_alloc(ctx, static_cast<size_t>(nd_rows) * 4));
+        uint32_t* dgs = static_cast<uint32_t*>(arena_alloc(ctx, static_cast<size_t>(nd_rows) * 4));
+        // dense accumulators: one entry per distinct dim group (<= maxg, and <= cap + 1 claimed slots)
+        const long long dmax = std::min<long long>(maxg, cap + 1);
+        unsigned long long* dkeys = static_cast<unsigned long long*>(arena_alloc(ctx, static_cast<size_t>(dmax + 1) * 8));
+        unsigned long long* dacc =
+            static_cast<unsigned long long*>(arena_alloc(ctx, static_cast<size_t>(dmax + 1) * A.S.nacc * 8));
+        if (!claim.keys || !claim.ndistinct || !slot2dense || !dslot || !dgs || !dkeys || !dacc)
+            return arena_oom(ctx, static_cast<size_t>(cap) * 12 + static_cast<size_t>(dmax) * (8 + 8 * A.S.nacc));
+        TQP_CUDA(cudaMemsetAsync(claim.keys, 0xFF, static_cast<size_t>(cap + 1) * 8, stream));
+        TQP_CUDA(cudaMemsetAsync(claim.ndistinct, 0, 16, stream));
         DimCols DC;
         memset(&DC, 0, sizeof(DC));
         for (int c = 0; c < nd; ++c) {
             DC.ptr[c] = static_cast<const unsigned char*>(D->cols[c].data);
             DC.type[c] = D->cols[c].type;
         }
+        const int threads = 256;
         if (D->num_rows > 0) {
-            const int threads = 256;
             const int blocks = static_cast<int>(std::min<long long>((D->num_rows + threads - 1) / threads, ctx->num_sms * 16LL));
-            k_dim_groups<<<blocks, threads, 0, stream>>>(A.S, DC, D->num_rows, dgs, ctx->d_err);
+            k_dim_claim<<<blocks, threads, 0, stream>>>(claim, DC, D->num_rows, dslot, ctx->d_err);
+            const long long nb = std::max<long long>(1, std::min<long long>((cap + 1 + 2047) / 2048, ctx->num_sms * 4LL));
+            const long long per = (cap + 1 + nb - 1) / nb;
+            k_dense_number<<<static_cast<int>(nb), kNumberThreads, 0, stream>>>(claim, slot2dense, dkeys, dacc, d_n, per);
+            k_dim_remap<<<blocks, threads, 0, stream>>>(dslot, slot2dense, D->num_rows, dgs);
+            const int hblocks = static_cast<int>(std::min<long long>((H.cap + threads) / threads, ctx->num_sms * 16LL));
+            k_ht_direct<<<hblocks, threads, 0, stream>>>(H, dgs);
             TQP_CUDA(cudaGetLastError());
         }
+        // the aggregation state in dense form: entries [0, *d_n)
+        A.S.keys = dkeys;
+        A.S.acc = dacc;
+        A.S.cap = dmax;
+        A.S.max_groups = maxg;
+        A.S.ndistinct = reinterpret_cast<unsigned long long*>(d_n);
+        A.S.d_dense_n = d_n;
         A.dgs = dgs;
+        A.next = next;
     }
 
     // stage the conditions, the foreign key and every aggregated fact column

@@ -39,7 +39,7 @@ EXPR = [("col", 3), ("col", 1), "mul"]
 WORKLOAD = ("filter-project-reduce: 60M rows (date i32, discount i64, quantity i32, price i64); "
             "731<=date<1096 AND 5<=discount<=7 AND quantity<24; ascending int32 row ids + SUM(price*discount)")
 PROFILE_MD = os.path.join(ROOT, "profiles", "k_filter_q6_60M.md")
-KERNEL_SRCS = ["filter.cu", "engine.cuh", "common.cuh"]
+KERNEL_SRCS = ["filter.cu", "bodies.cuh", "engine.cuh", "common.cuh"]
 
 
 def gen_host(rank: int):
@@ -275,6 +275,114 @@ def secondary_workloads(tqp, torch, dev, local, reps):
     return out
 
 
+BATCH_PLANS = 512
+
+
+def batched_workload(tqp, torch, dev, local, reps, n_plans=BATCH_PLANS, seed=datagen.DEFAULT_SEED + 3):
+    """n_plans independent plans (q1 group-by, q6 filter-compact-sum, join-group-top-100 in turn) over tables of
+    log-uniform sizes in [10K, 5M] rows: one captured batch (tqp_batch_run) against one tqp_run_plan call per plan.
+    Every plan reads its own disjoint slice of the generated columns (no table is shared, so nothing stays in L2)."""
+    sizes = datagen.log_uniform_int(seed, 77, n_plans, 10_000, 5_000_000)
+    kinds = [i % 3 for i in range(n_plans)]
+    scan_rows = int(sum(int(s) for s, k in zip(sizes, kinds) if k != 2))
+    probe_rows = int(sum(int(s) for s, k in zip(sizes, kinds) if k == 2))
+    # slices start on 16-row boundaries (16-byte aligned for every column type)
+    ft = datagen.fact_table(scan_rows + 16 * n_plans, seed=seed, cols=("date", "flag", "status", "quantity", "price", "discount"))
+    fcols = {k: torch.from_numpy(v).to(dev) for k, v in ft.items()}
+    del ft
+    q1_aggs = [("sum", [("col", 3)]), ("sum", [("col", 4)]),
+               ("sum", [("col", 4), ("const", 100), ("col", 5), "sub", "mul"]), ("count", None),
+               ("avg", [("col", 4)])]
+    plans, results, keep = [], [], []
+    f0 = 0
+    alg_bytes = 0
+    for i, (n, kind) in enumerate(zip((int(s) for s in sizes), kinds)):
+        z = lambda m, dt=torch.int64: torch.zeros(max(m, 1), dtype=dt, device=dev)  # noqa: E731
+        if kind == 0:   # q1: date <= 2450, GROUP BY (flag, status)
+            T = tqp.TableRef([fcols[c][f0:f0 + n] for c in ("date", "flag", "status", "quantity", "price",
+                                                             "discount")])
+            f0 += (n + 15) // 16 * 16
+            b = dict(keys=z(64 * 2), iv=z(64 * 5), fv=z(64 * 5, torch.float64), ng=z(1), tot=z(1), nr=z(1))
+            plans.append(tqp.make_plan(T, [(0, "le", 2450)], None, 0, 0, [1, 2], q1_aggs))
+            results.append(tqp.make_result(None, 0, b["nr"], None, b["keys"], b["iv"], b["fv"], 64, b["ng"],
+                                           b["tot"], None))
+            alg_bytes += n * 26
+        elif kind == 1:  # q6: a 365-day window, discount in [5,7], quantity < 24; SUM(price*discount) + row ids
+            T = tqp.TableRef([fcols[c][f0:f0 + n] for c in ("date", "discount", "quantity", "price")])
+            f0 += (n + 15) // 16 * 16
+            b = dict(ids=z(n, torch.int32), nr=z(1), s=z(1))
+            plans.append(tqp.make_plan(T, [(0, "ge", 731), (0, "lt", 1096), (1, "between", 5, 7), (2, "lt", 24)],
+                                       sum_expr=[("col", 3), ("col", 1), "mul"], emit_row_ids=True))
+            results.append(tqp.make_result(b["ids"], n, b["nr"], b["s"]))
+            alg_bytes += n * 16 + int(n * 0.02) * 12
+        else:            # join: build nb = n/40 unique keys (nb/10 groups), probe n Zipf(0.5) keys, top-100
+            nb = max(1000, n // 40)
+            dim = datagen.dim_table(nb, max(1, nb // 10), seed=seed + i)
+            D = tqp.TableRef([torch.from_numpy(dim["key"]).to(dev), torch.from_numpy(dim["payload"]).to(dev)])
+            pr = datagen.probe_table(n, nb, seed=seed + i)
+            fk, val = torch.from_numpy(pr["fk"]).to(dev), torch.from_numpy(pr["value"]).to(dev)
+            F = tqp.TableRef([fk, val])
+            b = dict(keys=z(100), iv=z(200), ng=z(1), tot=z(1), nj=z(1), d=D, fk=fk, val=val)
+            plans.append(tqp.make_plan(F, (), D, 0, 0, [3], [("sum", [("col", 1)]), ("count", None)], None, 100, 0))
+            results.append(tqp.make_result(None, 0, None, None, b["keys"], b["iv"], None, 100, b["ng"], b["tot"],
+                                           b["nj"]))
+            alg_bytes += n * 12 + nb * 8
+        keep.append(b)
+    stream = torch.cuda.current_stream()
+    ctx = tqp.Context(local, 4 << 30)
+
+    def snapshot():
+        torch.cuda.synchronize()
+        return [torch.cat([t.flatten().view(torch.int64) if t.dtype == torch.float64 else t.flatten().to(torch.int64)
+                           for k, t in sorted(b.items()) if torch.is_tensor(t) and k not in ("fk", "val")]).cpu()
+                for b in keep]
+
+    def seq():
+        for p, r in zip(plans, results):
+            tqp.tqp_run_plan(ctx, p, r, stream)
+
+    def wall(fn, n):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(n):
+            fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / n * 1e3
+
+    seq_ms = _time_launches(torch, seq, max(3, reps // 4), stream=stream)
+    seq_wall = wall(seq, 3)
+    ctx.check(stream)
+    want = snapshot()
+    for b in keep:
+        for k, t in b.items():
+            if torch.is_tensor(t) and k not in ("fk", "val"):
+                t.fill_(-7)
+    batch = tqp.tqp_batch_create(ctx, plans, results)
+    run = lambda: tqp.tqp_batch_run(batch, stream)  # noqa: E731
+    bat_ms = _time_launches(torch, run, reps, stream=stream)
+    bat_wall = wall(run, reps)
+    ctx.check(stream)
+    got = snapshot()
+    identical = all(torch.equal(a, b) for a, b in zip(want, got))
+    tqp.tqp_batch_destroy(batch)
+    rp = lambda: tqp.tqp_run_plans(ctx, plans, results, stream)  # noqa: E731
+    rp_ms = _time_launches(torch, rp, max(3, reps // 4), stream=stream)
+    ctx.check(stream)
+    ctx.close()
+    rows = scan_rows + probe_rows
+    return {
+        "workload": f"{n_plans} plans (q1 group-by / q6 filter+ids+sum / join+group+top-100 in turn), table sizes "
+                    f"log-uniform in [10K, 5M] rows, {rows} rows in all, disjoint slices (no L2 reuse)",
+        "batched_graph_ms": bat_ms, "batched_graph_wall_ms": bat_wall,
+        "run_plans_ms": rp_ms, "sequential_ms": seq_ms, "sequential_wall_ms": seq_wall,
+        "batched_queries_per_s": n_plans / (bat_wall / 1e3), "sequential_queries_per_s": n_plans / (seq_wall / 1e3),
+        "speedup_wall": seq_wall / bat_wall, "rows": rows, "batched_rows_per_s": rows / (bat_ms / 1e3),
+        "algorithmic_bytes": alg_bytes, "batched_achieved_gbs": alg_bytes / (bat_ms / 1e3) / 1e9,
+        "identical_to_sequential": identical,
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -374,6 +482,7 @@ def main():
     ops = None
     if rank == 0 and not args.no_operators:
         ops = secondary_workloads(tqp, torch, dev, local, 20)
+        ops["batched_512"] = batched_workload(tqp, torch, dev, local, 20)
     if rank == 0:
         peak, peak_kind = measured_peaks()
         alg = algorithmic_bytes(N_ROWS, k)

@@ -313,11 +313,37 @@ typedef struct {
  * column is a fact column. */
 TQP_API tqp_status tqp_run_plan(tqp_ctx* ctx, const tqp_plan* plan, const tqp_result* res, void* stream);
 
-/* Run n independent plans as one batch: every plan's work is cut into tiles
- * that one persistent kernel launch drains from a device work queue (the
- * paper runs queries one at a time, Section 4.3).  Results are identical to
- * n calls of tqp_run_plan. */
+/* Run n independent plans as one batch.  The paper runs one query at a time
+ * with intra-operator parallelism (Section 4.3); here each phase of all plans
+ * is one kernel launch, and the scans of every plan are chunks that ONE
+ * persistent launch of the staged scan engine drains from a shared ticket
+ * counter, so small plans do not each pay a launch and a ramp-up.  Results
+ * (every output of every tqp_result) are identical to n calls of
+ * tqp_run_plan; plans whose group table needs the multi-kernel sort (more than
+ * 4096 table slots without top-k) run through the tqp_run_plan path after the
+ * batched kernels.  A malformed plan fails the call with its tqp_run_plan
+ * error (plans before it may already have been launched).
+ * Scratch comes from the context's arena (stream-ordered, like every call):
+ * the job descriptors are copied with cudaMemcpyAsync on `stream`. */
 TQP_API tqp_status tqp_run_plans(tqp_ctx* ctx, const tqp_plan* plans, const tqp_result* res, int32_t n, void* stream);
+
+/* A batch lowered once and replayed: tqp_batch_create lowers n plans as
+ * tqp_run_plans does, takes their scratch from a long-lived region at the top
+ * of the context's arena (released by tqp_batch_destroy; the region of the
+ * most recently created live batch is released first, all regions once no
+ * batch is left) and captures every kernel into a CUDA graph; tqp_batch_run
+ * launches that graph on `stream` (one launch per run).  The plans, tables
+ * and result structs are read during create only; the device buffers they
+ * point to must stay valid, and are re-read on every run, until destroy.
+ * Runs of one batch must not overlap one another (they share scratch).
+ * Errors: TQP_ERR_INVALID_ARG (NULL or n < 0), TQP_ERR_OUT_OF_MEMORY (arena
+ * too small for the long-lived region), any error tqp_run_plan would report
+ * for one of the plans.  tqp_batch_destroy synchronizes the device first. */
+typedef struct tqp_batch tqp_batch;
+TQP_API tqp_status tqp_batch_create(tqp_ctx* ctx, const tqp_plan* plans, const tqp_result* res, int32_t n,
+                                    tqp_batch** out);
+TQP_API tqp_status tqp_batch_run(tqp_batch* batch, void* stream);
+TQP_API tqp_status tqp_batch_destroy(tqp_batch* batch);
 
 #ifdef __cplusplus
 }

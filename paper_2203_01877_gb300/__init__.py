@@ -99,6 +99,9 @@ _SIGS = {
                                 C.c_int64, _P, _P]),
     "tqp_run_plan": (C.c_int, [_P, C.POINTER(Plan), C.POINTER(Result), _P]),
     "tqp_run_plans": (C.c_int, [_P, C.POINTER(Plan), C.POINTER(Result), C.c_int32, _P]),
+    "tqp_batch_create": (C.c_int, [_P, C.POINTER(Plan), C.POINTER(Result), C.c_int32, C.POINTER(_P)]),
+    "tqp_batch_run": (C.c_int, [_P, _P]),
+    "tqp_batch_destroy": (C.c_int, [_P]),
 }
 
 
@@ -325,3 +328,47 @@ def tqp_run_plans(ctx: Context, plans, results, stream=None):
     pa = (Plan * n)(*plans)
     ra = (Result * n)(*results)
     _check(lib().tqp_run_plans(ctx.h, pa, ra, n, _stream(stream)))
+
+
+class Batch:
+    """A lowered, graph-captured batch of plans (tqp_batch_create).
+
+    Holds the plans, results and context alive until ``tqp_batch_destroy``;
+    the device buffers they point to are re-read on every run."""
+
+    def __init__(self, ctx: Context, plans, results):
+        n = len(plans)
+        if n != len(results):
+            raise ValueError("one result per plan")
+        pa = (Plan * n)(*plans)
+        ra = (Result * n)(*results)
+        h = C.c_void_p()
+        _check(lib().tqp_batch_create(ctx.h, pa, ra, n, C.byref(h)))
+        self.h = h
+        self.ctx = ctx
+        self._keep = (list(plans), list(results))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().tqp_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tqp_batch_create(ctx: Context, plans, results) -> Batch:
+    return Batch(ctx, plans, results)
+
+
+def tqp_batch_run(batch: Batch, stream=None):
+    if not batch.h:
+        raise ValueError("batch was destroyed")
+    _check(lib().tqp_batch_run(batch.h, _stream(stream)))
+
+
+def tqp_batch_destroy(batch: Batch):
+    batch.close()

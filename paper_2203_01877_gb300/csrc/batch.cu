@@ -1,0 +1,967 @@
+// Batched execution of many independent plans: tqp_batch_create / _run /
+// _destroy and tqp_run_plans.
+//
+// The paper runs one query at a time with intra-operator parallelism only
+// (Section 4.3).  Here every plan of a batch is lowered into jobs once, and
+// each phase of all jobs runs as ONE kernel over a flattened block space
+// (a host-built map gives every block its job), so the number of launches
+// does not grow with the number of plans:
+//   fill      clear every job's scratch (tables, counters)
+//   build     chained hash tables + dimension group claims of all joins
+//   number    dense group ids (claim-table ranges)
+//   remap     dimension row -> dense group id
+//   direct    dense ids into the slots of unique build keys
+//   scan      ONE persistent launch of the staged scan engine: CTAs draw
+//             chunk tickets across all jobs' tables (uneven sizes balance
+//             themselves) and run the filter / group-by / joined-aggregation
+//             body of the chunk's job
+//   compact   selection masks -> row ids
+//   finalize  one CTA per small group table (keys ascending)
+//   top-k     the bitonic tournament, one launch per level for all plans
+// A tqp_batch is lowered and captured into a CUDA graph once; each run is
+// one graph launch.  Plans outside these shapes (large group tables without
+// top-k) run through the single-plan path after the batch's kernels, inside
+// the same graph, with scratch of their own.
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "host.h"
+#include "bodies.cuh"
+#include "dimgroups.cuh"
+#include "finalize.cuh"
+
+namespace tqp {
+
+tqp_status run_plan_one(tqp_ctx* ctx, const tqp_plan* p, const tqp_result* r, cudaStream_t stream);
+
+constexpr int kBatchTile = 1024;
+constexpr int kBatchStages = 3;
+constexpr int kJobFilter = 1, kJobGroup = 2, kJobJoin = 3;
+constexpr int kBodyMax = GroupBody::kSmemBytes > FilterBody::kSmemBytes ? GroupBody::kSmemBytes
+                                                                        : FilterBody::kSmemBytes;
+constexpr int kFlatThreads = 256;
+constexpr int kFillPer = 4096;  // 16-byte units per fill block
+constexpr int kRowsPer = 2048;  // elements per block of the element-wise phases
+constexpr int kFinSmemBytes = 2 * kSmallCap * (8 + 4);
+constexpr int kCounterBytes = 64;
+
+struct FillRange {
+    uint4* ptr;
+    long long n16;  // 16-byte units
+    uint4 pattern;
+    long long first_block;
+};
+
+struct BuildJob {
+    JoinHT H;
+    uint32_t* next;
+    const unsigned char* key_col;
+    int32_t key_type;
+    int32_t grouped;
+    long long nrows;
+    GroupSpec claim;
+    DimCols D;
+    uint32_t* dslot;
+    uint32_t* slot2dense;
+    uint32_t* dgs;
+    unsigned long long* dkeys;
+    unsigned long long* dacc;
+    long long* d_n;
+    long long row_block, num_block, slot_block;  // first block of this job in each phase
+};
+
+struct alignas(16) ScanJob {
+    int32_t kind;
+    int32_t pad;
+    long long chunk_base;
+    union U {
+        FilterArgs f;
+        GroupArgs g;
+        PlanJoinArgs j;
+    } u;
+};
+static_assert(sizeof(ScanJob) % 16 == 0, "ScanJob is copied in 16-byte units");
+
+struct CompactJob {
+    const uint32_t* mask;
+    const uint32_t* block_tot;
+    long long n;
+    int32_t* row_ids;
+    long long capacity;
+    long long first_block;
+};
+
+struct FinJob {
+    GroupSpec S;
+    GroupOut O;
+    int64_t* total_out;
+};
+
+struct TopJob {
+    GroupSpec S;
+    GroupOut O;
+    int32_t k;
+    int32_t rank_acc;
+    TopBuf buf[2];
+    unsigned long long* total;
+    int64_t* total_out;
+    long long first_block;  // level 0
+};
+
+struct TopItem {
+    int32_t job;
+    int32_t emit;
+    int32_t in_buf;
+    int32_t pad;
+    long long n_in;
+    long long first_block;
+};
+
+__global__ void __launch_bounds__(kFlatThreads) k_b_fill(const FillRange* R, const int32_t* bjob, int64_t* const* zero,
+                                                         int nzero) {
+    const FillRange& r = R[bjob[blockIdx.x]];
+    const long long u0 = (static_cast<long long>(blockIdx.x) - r.first_block) * kFillPer;
+    const long long u1 = (u0 + kFillPer < r.n16) ? u0 + kFillPer : r.n16;
+    for (long long u = u0 + threadIdx.x; u < u1; u += kFlatThreads) r.ptr[u] = r.pattern;
+    if (blockIdx.x == 0)
+        for (int i = threadIdx.x; i < nzero; i += kFlatThreads) *zero[i] = 0;
+}
+
+__global__ void __launch_bounds__(kFlatThreads) k_b_build(const BuildJob* B, const int32_t* bjob, int* err) {
+    const BuildJob& b = B[bjob[blockIdx.x]];
+    const long long i0 = (static_cast<long long>(blockIdx.x) - b.row_block) * kRowsPer;
+    const long long i1 = (i0 + kRowsPer < b.nrows) ? i0 + kRowsPer : b.nrows;
+    for (long long i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
+        ht_chain_insert_row(b.H, b.key_col, b.key_type, i, b.next, err);
+        if (b.grouped) dim_claim_row(b.claim, b.D, i, b.dslot, err);
+    }
+}
+
+__global__ void __launch_bounds__(kNumberThreads) k_b_number(const BuildJob* B, const int32_t* bjob) {
+    const BuildJob& b = B[bjob[blockIdx.x]];
+    const long long s0 = (static_cast<long long>(blockIdx.x) - b.num_block) * kRowsPer;
+    const long long s1 = (s0 + kRowsPer < b.claim.cap + 1) ? s0 + kRowsPer : b.claim.cap + 1;
+    dense_number_range(b.claim, b.slot2dense, b.dkeys, b.dacc, b.d_n, s0, s1);
+}
+
+__global__ void __launch_bounds__(kFlatThreads) k_b_remap(const BuildJob* B, const int32_t* bjob) {
+    const BuildJob& b = B[bjob[blockIdx.x]];
+    if (!b.grouped) return;
+    const long long i0 = (static_cast<long long>(blockIdx.x) - b.row_block) * kRowsPer;
+    const long long i1 = (i0 + kRowsPer < b.nrows) ? i0 + kRowsPer : b.nrows;
+    for (long long i = i0 + threadIdx.x; i < i1; i += kFlatThreads) b.dgs[i] = b.slot2dense[b.dslot[i]];
+}
+
+__global__ void __launch_bounds__(kFlatThreads) k_b_direct(const BuildJob* B, const int32_t* bjob) {
+    const BuildJob& b = B[bjob[blockIdx.x]];
+    const long long s0 = (static_cast<long long>(blockIdx.x) - b.slot_block) * kRowsPer;
+    const long long s1 = (s0 + kRowsPer < b.H.cap + 1) ? s0 + kRowsPer : b.H.cap + 1;
+    for (long long s = s0 + threadIdx.x; s < s1; s += kFlatThreads) ht_direct_slot(b.H, b.dgs, s);
+}
+
+template <class Body, class Args>
+__device__ __forceinline__ void scan_chunk(const Args& a, unsigned char* body_smem, long long local, EngineHeader* h,
+                                           unsigned char* stages, long long& it, bool& failed, uint64_t policy,
+                                           int warp, int lane) {
+    Body body(a, body_smem);
+    __syncthreads();
+    const long long t0 = local * a.ctl.chunk_tiles;
+    const long long t1 = (t0 + a.ctl.chunk_tiles < a.G.ntiles) ? t0 + a.ctl.chunk_tiles : a.G.ntiles;
+    run_chunk(a.G, a.ctl, body, local, t0, t1, h, stages, it, failed, policy, warp, lane);
+}
+
+// The persistent multi-plan scan: chunk tickets span every job's tables.
+__global__ void __launch_bounds__(kEngineThreads, 2) k_b_scan(const ScanJob* J, const int32_t* cjob,
+                                                              unsigned long long* ticket, long long total_chunks) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    constexpr int kJobBytes = (sizeof(ScanJob) + 127) / 128 * 128;
+    EngineHeader* h = reinterpret_cast<EngineHeader*>(smem);
+    ScanJob* sj = reinterpret_cast<ScanJob*>(smem + kHeaderBytes);
+    unsigned char* body_smem = smem + kHeaderBytes + kJobBytes;
+    unsigned char* stages = body_smem + kBodyMax;
+    __shared__ int job_sm;
+    const int warp = threadIdx.x / kWarp;
+    const int lane = threadIdx.x % kWarp;
+    init_stage_ring(h, kBatchStages);
+    __syncthreads();
+    long long it = 0;
+    bool failed = false;
+    const uint64_t policy = l2_evict_first_policy();
+    while (true) {
+        if (threadIdx.x == 0) {
+            const long long c = static_cast<long long>(atomicAdd(ticket, 1ULL));
+            h->chunk = c;
+            job_sm = c < total_chunks ? cjob[c] : -1;
+        }
+        __syncthreads();
+        const long long chunk = h->chunk;
+        if (chunk >= total_chunks) break;
+        {
+            const uint4* src = reinterpret_cast<const uint4*>(&J[job_sm]);
+            uint4* dst = reinterpret_cast<uint4*>(sj);
+            for (int i = threadIdx.x; i < static_cast<int>(sizeof(ScanJob) / 16); i += kEngineThreads) dst[i] = src[i];
+        }
+        __syncthreads();
+        const long long local = chunk - sj->chunk_base;
+        if (sj->kind == kJobFilter)
+            scan_chunk<FilterBody>(sj->u.f, body_smem, local, h, stages, it, failed, policy, warp, lane);
+        else if (sj->kind == kJobGroup)
+            scan_chunk<GroupBody>(sj->u.g, body_smem, local, h, stages, it, failed, policy, warp, lane);
+        else
+            scan_chunk<PlanJoinBody>(sj->u.j, body_smem, local, h, stages, it, failed, policy, warp, lane);
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kCompactThreads) k_b_compact(const CompactJob* C, const int32_t* bjob) {
+    const CompactJob& c = C[bjob[blockIdx.x]];
+    compact_block(c.mask, c.block_tot, c.n, c.row_ids, c.capacity, static_cast<long long>(blockIdx.x) - c.first_block);
+}
+
+__global__ void __launch_bounds__(kFinThreads) k_b_finalize(const FinJob* F) {
+    extern __shared__ __align__(16) unsigned char fsm[];
+    const FinJob& f = F[blockIdx.x];
+    finalize_small_block(f.S, f.O, fsm);
+    __syncthreads();
+    if (threadIdx.x == 0 && f.total_out) *f.total_out = *f.O.num_groups;
+}
+
+__global__ void __launch_bounds__(kTopThreads) k_b_topk0(const TopJob* T, const int32_t* bjob) {
+    const TopJob& t = T[bjob[blockIdx.x]];
+    topk_level0_block(t.S, t.rank_acc, t.k, t.buf[0], t.total, static_cast<long long>(blockIdx.x) - t.first_block);
+}
+
+__global__ void __launch_bounds__(kTopThreads) k_b_topk(const TopJob* T, const TopItem* items, const int32_t* bjob) {
+    const TopItem& it = items[bjob[blockIdx.x]];
+    const TopJob& t = T[it.job];
+    topk_reduce_block(t.S, t.buf[it.in_buf], it.n_in, t.k, t.buf[1 - it.in_buf], it.emit, t.O, t.total, t.total_out,
+                      static_cast<long long>(blockIdx.x) - it.first_block);
+}
+
+}  // namespace tqp
+
+using namespace tqp;
+
+struct tqp_batch {
+    tqp_ctx* ctx = nullptr;
+    bool persistent = false;  // scratch from the arena's long-lived top region
+    size_t top_before = 0;
+    size_t top_after = 0;
+    // lowered jobs
+    std::vector<FillRange> fill;
+    std::vector<int64_t*> zero;
+    std::vector<BuildJob> build;
+    std::vector<ScanJob> scan;
+    std::vector<CompactJob> compact;
+    std::vector<FinJob> fin;
+    std::vector<TopJob> top;
+    std::vector<std::vector<TopItem>> levels;
+    // block -> job maps, concatenated
+    std::vector<int32_t> maps;
+    long long fill_blocks = 0, row_blocks = 0, num_blocks = 0, slot_blocks = 0, scan_chunks = 0, compact_blocks = 0,
+              top0_blocks = 0;
+    std::vector<long long> level_blocks;
+    size_t off_fill = 0, off_row = 0, off_num = 0, off_slot = 0, off_scan = 0, off_compact = 0, off_top0 = 0;
+    std::vector<size_t> off_level;
+    // small zeroed counters share one slab (one fill range)
+    unsigned char* slab = nullptr;
+    size_t slab_bytes = 0, slab_used = 0;
+    // device copies
+    FillRange* d_fill = nullptr;
+    int64_t** d_zero = nullptr;
+    BuildJob* d_build = nullptr;
+    ScanJob* d_scan = nullptr;
+    CompactJob* d_compact = nullptr;
+    FinJob* d_fin = nullptr;
+    TopJob* d_top = nullptr;
+    std::vector<TopItem*> d_levels;
+    int32_t* d_maps = nullptr;
+    unsigned long long* d_ticket = nullptr;
+    size_t scan_smem = 0;
+    int scan_grid = 0;
+    // plans run through the single-plan path, and their scratch
+    std::vector<tqp_plan> fb_plans;
+    std::vector<tqp_result> fb_res;
+    unsigned char* fb_arena = nullptr;
+    size_t fb_bytes = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace tqp {
+
+static void* balloc(tqp_batch* b, size_t bytes) {
+    bytes = (bytes + 15) / 16 * 16;
+    return b->persistent ? arena_alloc_top(b->ctx, bytes) : arena_alloc(b->ctx, bytes);
+}
+
+static void add_fill(tqp_batch* b, void* ptr, size_t bytes, uint4 pattern) {
+    FillRange r;
+    r.ptr = static_cast<uint4*>(ptr);
+    r.n16 = static_cast<long long>((bytes + 15) / 16);
+    r.pattern = pattern;
+    r.first_block = 0;
+    if (r.n16 > 0) b->fill.push_back(r);
+}
+
+static const uint4 kZero16 = {0u, 0u, 0u, 0u};
+static const uint4 kOnes16 = {~0u, ~0u, ~0u, ~0u};
+
+// A zeroed 64-byte counter block from the slab (sized for every job's needs).
+static unsigned long long* counter(tqp_batch* b) {
+    unsigned long long* p = reinterpret_cast<unsigned long long*>(b->slab + b->slab_used);
+    b->slab_used += kCounterBytes;
+    return p;
+}
+
+// Staged geometry of one scan in the batch (fixed tile and stage count).
+static tqp_status batch_geom(const tqp_ctx* ctx, const tqp_table* t, std::vector<int> staged, ScanGeom* G) {
+    const tqp_tuning tu{kBatchTile, kBatchStages, 2};
+    size_t smem = 0;
+    std::sort(staged.begin(), staged.end());
+    staged.erase(std::unique(staged.begin(), staged.end()), staged.end());
+    if (static_cast<int>(staged.size()) > kMaxStaged) staged.resize(kMaxStaged);
+    return make_geom(ctx, t, staged, tu, 0, G, &smem);
+}
+
+static tqp_status add_filter_job(tqp_batch* b, const tqp_plan* p, const tqp_result* r, bool ids, bool with_sum,
+                                 int64_t* d_count, int64_t* d_count2) {
+    tqp_ctx* ctx = b->ctx;
+    ScanJob J;
+    memset(&J, 0, sizeof(J));
+    J.kind = kJobFilter;
+    FilterArgs& A = J.u.f;
+    int ncond = 0;
+    TQP_TRY(lower_preds(p->fact, p->preds, p->npreds, A.cond, &ncond));
+    A.ncond = ncond;
+    std::vector<int> staged;
+    for (int i = 0; i < ncond; ++i) staged.push_back(A.cond[i].col);
+    if (with_sum) {
+        TQP_TRY(lower_expr(&p->sum_expr, p->fact->num_cols, &A.sum));
+        A.has_sum = 1;
+        if (ncond == 0) expr_cols(A.sum, staged);
+    }
+    TQP_TRY(batch_geom(ctx, p->fact, staged, &A.G));
+    lower_fast(A.cond, A.ncond, A.G, A.cf, &A.fast);
+    A.acc = counter(b);
+    A.d_count = d_count;
+    A.d_count2 = d_count2;
+    A.d_sum = with_sum ? r->d_sum : nullptr;
+    if (ids) {
+        const long long nblocks = (A.G.n + kCompactRows - 1) / kCompactRows;
+        const size_t tot_bytes = static_cast<size_t>(nblocks) * 4 + 16;
+        const size_t mask_bytes = static_cast<size_t>(A.G.ntiles) * (A.G.T / kWarp) * 4;
+        A.block_tot = static_cast<uint32_t*>(balloc(b, tot_bytes));
+        A.mask = static_cast<uint32_t*>(balloc(b, mask_bytes + 16));
+        if (!A.block_tot || !A.mask) return arena_oom(ctx, tot_bytes + mask_bytes);
+        add_fill(b, A.block_tot, tot_bytes, kZero16);
+        A.capacity = r->capacity_rows;
+        if (nblocks > 0) {
+            CompactJob C{A.mask, A.block_tot, A.G.n, r->d_row_ids, r->capacity_rows, b->compact_blocks};
+            b->compact_blocks += nblocks;
+            b->compact.push_back(C);
+        }
+    }
+    A.ctl.err = ctx->d_err;
+    A.ctl.wait_cap = ctx->wait_cap;
+    if (A.G.ntiles == 0) {  // nothing is scanned: the results of an empty table
+        b->zero.push_back(d_count);
+        if (d_count2) b->zero.push_back(d_count2);
+        if (A.d_sum) b->zero.push_back(A.d_sum);
+        return TQP_OK;
+    }
+    b->scan.push_back(J);
+    return TQP_OK;
+}
+
+static tqp_status add_top_job(tqp_batch* b, const GroupSpec& S, const GroupOut& O, const tqp_plan* p,
+                              const tqp_result* r) {
+    TopJob T;
+    memset(&T, 0, sizeof(T));
+    T.S = S;
+    T.O = O;
+    T.k = p->topk;
+    T.rank_acc = S.agg_acc[p->topk_agg];
+    const long long nb0 = (S.cap + 1 + kTopBlock - 1) / kTopBlock;
+    for (int q = 0; q < 2; ++q) {
+        const size_t n = static_cast<size_t>(nb0) * T.k;
+        T.buf[q].rank = static_cast<long long*>(balloc(b, n * 8));
+        T.buf[q].key = static_cast<uint64_t*>(balloc(b, n * 8));
+        T.buf[q].slot = static_cast<uint32_t*>(balloc(b, n * 4));
+        if (!T.buf[q].rank || !T.buf[q].key || !T.buf[q].slot) return arena_oom(b->ctx, n * 20);
+    }
+    T.total = counter(b);
+    T.total_out = r->d_total_groups;
+    T.first_block = b->top0_blocks;
+    b->top0_blocks += nb0;
+    b->top.push_back(T);
+    return TQP_OK;
+}
+
+static tqp_status add_group_job(tqp_batch* b, const tqp_plan* p, const tqp_result* r) {
+    tqp_ctx* ctx = b->ctx;
+    const tqp_table* t = p->fact;
+    ScanJob J;
+    memset(&J, 0, sizeof(J));
+    J.kind = kJobGroup;
+    GroupArgs& A = J.u.g;
+    int ncond = 0;
+    TQP_TRY(lower_preds(t, p->preds, p->npreds, A.cond, &ncond));
+    A.ncond = ncond;
+    int32_t types[TQP_MAX_GROUP_COLS] = {0, 0, 0, 0};
+    for (int i = 0; i < p->ngc; ++i) types[i] = t->cols[p->group_cols[i]].type;
+    TQP_TRY(lower_group(p->group_cols, types, p->ngc, p->aggs, p->naggs, t->num_cols, &A.S));
+    std::vector<int> staged;
+    for (int i = 0; i < ncond; ++i) staged.push_back(A.cond[i].col);
+    for (int i = 0; i < p->ngc; ++i) staged.push_back(p->group_cols[i]);
+    for (int a = 1; a < A.S.nacc; ++a) expr_cols(A.S.acc_expr[a - 1], staged);
+    TQP_TRY(batch_geom(ctx, t, staged, &A.G));
+    lower_fast(A.cond, A.ncond, A.G, A.cf, &A.fast);
+    const long long maxg = p->max_groups > 0 ? p->max_groups : std::max<long long>(1, r->capacity_groups);
+    const long long cap = group_table_cap(maxg);
+    A.S.cap = cap;
+    A.S.max_groups = maxg;
+    const size_t key_bytes = static_cast<size_t>(cap + 1) * 8;
+    const size_t acc_bytes = static_cast<size_t>(cap + 1) * A.S.nacc * 8;
+    A.S.keys = static_cast<unsigned long long*>(balloc(b, key_bytes));
+    A.S.acc = static_cast<unsigned long long*>(balloc(b, acc_bytes));
+    A.S.ndistinct = counter(b);
+    if (!A.S.keys || !A.S.acc) return arena_oom(ctx, key_bytes + acc_bytes);
+    add_fill(b, A.S.keys, key_bytes, kOnes16);
+    add_fill(b, A.S.acc, acc_bytes, kZero16);
+    A.ctl.err = ctx->d_err;
+    A.ctl.wait_cap = ctx->wait_cap;
+    const GroupOut O{r->d_keys, r->d_ivals, r->d_fvals, r->capacity_groups, r->d_num_groups, ctx->d_err};
+    if (p->topk > 0) {
+        TQP_TRY(add_top_job(b, A.S, O, p, r));
+    } else {
+        FinJob F;
+        memset(&F, 0, sizeof(F));
+        F.S = A.S;
+        F.O = O;
+        F.total_out = r->d_total_groups;
+        b->fin.push_back(F);
+    }
+    if (A.G.ntiles > 0) b->scan.push_back(J);
+    return TQP_OK;
+}
+
+static tqp_status add_join_job(tqp_batch* b, const tqp_plan* p, const tqp_result* r) {
+    tqp_ctx* ctx = b->ctx;
+    const tqp_table* F = p->fact;
+    const tqp_table* D = p->dim;
+    const int nf = F->num_cols, nd = D->num_cols;
+    const long long ndr = D->num_rows;
+    const size_t nd_rows = static_cast<size_t>(std::max<long long>(1, ndr));
+    // build side: the chained table, and the dimension rows' dense group ids
+    BuildJob B;
+    memset(&B, 0, sizeof(B));
+    B.H.cap = ht_cap_dense(ndr);
+    B.H.slots = static_cast<uint4*>(balloc(b, static_cast<size_t>(B.H.cap + 1) * 16));
+    B.next = static_cast<uint32_t*>(balloc(b, nd_rows * 4));
+    if (!B.H.slots || !B.next) return arena_oom(ctx, static_cast<size_t>(B.H.cap + 1) * 16 + nd_rows * 4);
+    add_fill(b, B.H.slots, static_cast<size_t>(B.H.cap + 1) * 16, uint4{~0u, ~0u, kNoRow, 0u});
+    B.key_col = static_cast<const unsigned char*>(D->cols[p->dim_key].data);
+    B.key_type = D->cols[p->dim_key].type;
+    B.nrows = ndr;
+    for (int c = 0; c < nd; ++c) {
+        B.D.ptr[c] = static_cast<const unsigned char*>(D->cols[c].data);
+        B.D.type[c] = D->cols[c].type;
+    }
+    // probe side: filter + probe + aggregate, one fused scan body
+    ScanJob J;
+    memset(&J, 0, sizeof(J));
+    J.kind = kJobJoin;
+    PlanJoinArgs& A = J.u.j;
+    int ncond = 0;
+    TQP_TRY(lower_preds(F, p->preds, p->npreds, A.cond, &ncond));
+    A.ncond = ncond;
+    A.fk_col = p->fact_fk;
+    A.H = B.H;
+    A.next = B.next;
+    if (p->has_sum) {
+        TQP_TRY(lower_expr(&p->sum_expr, nf, &A.sum));
+        A.has_sum = 1;
+    }
+    const bool grouped = p->ngc > 0 || p->naggs > 0;
+    if (grouped) {
+        int32_t kc[TQP_MAX_GROUP_COLS], kt[TQP_MAX_GROUP_COLS];
+        for (int i = 0; i < p->ngc; ++i) {
+            kc[i] = p->group_cols[i] - nf;
+            kt[i] = D->cols[kc[i]].type;
+        }
+        TQP_TRY(lower_group(kc, kt, p->ngc, p->aggs, p->naggs, nf, &A.S));
+        const long long maxg = p->max_groups > 0 ? p->max_groups : (p->ngc == 0 ? 1 : std::max<long long>(1, ndr));
+        const long long cap = group_table_cap(maxg);
+        const long long dmax = std::min<long long>(maxg, cap + 1);
+        B.grouped = 1;
+        B.claim = A.S;
+        B.claim.cap = cap;
+        B.claim.max_groups = maxg;
+        B.claim.keys = static_cast<unsigned long long*>(balloc(b, static_cast<size_t>(cap + 1) * 8));
+        B.claim.ndistinct = counter(b);
+        B.d_n = reinterpret_cast<long long*>(B.claim.ndistinct) + 1;
+        B.slot2dense = static_cast<uint32_t*>(balloc(b, static_cast<size_t>(cap + 1) * 4));
+        B.dslot = static_cast<uint32_t*>(balloc(b, nd_rows * 4));
+        B.dgs = static_cast<uint32_t*>(balloc(b, nd_rows * 4));
+        B.dkeys = static_cast<unsigned long long*>(balloc(b, static_cast<size_t>(dmax + 1) * 8));
+        B.dacc = static_cast<unsigned long long*>(balloc(b, static_cast<size_t>(dmax + 1) * A.S.nacc * 8));
+        if (!B.claim.keys || !B.slot2dense || !B.dslot || !B.dgs || !B.dkeys || !B.dacc)
+            return arena_oom(ctx, static_cast<size_t>(cap) * 12 + static_cast<size_t>(dmax) * (8 + 8 * A.S.nacc));
+        add_fill(b, B.claim.keys, static_cast<size_t>(cap + 1) * 8, kOnes16);
+        // the aggregation state in dense form: entries [0, *d_n)
+        A.S.keys = B.dkeys;
+        A.S.acc = B.dacc;
+        A.S.cap = dmax;
+        A.S.max_groups = maxg;
+        A.S.ndistinct = reinterpret_cast<unsigned long long*>(B.d_n);
+        A.S.d_dense_n = B.d_n;
+        A.dgs = B.dgs;
+        const GroupOut O{r->d_keys, r->d_ivals, r->d_fvals, r->capacity_groups, r->d_num_groups, ctx->d_err};
+        if (p->topk > 0) {
+            TQP_TRY(add_top_job(b, A.S, O, p, r));
+        } else {
+            FinJob Fj;
+            memset(&Fj, 0, sizeof(Fj));
+            Fj.S = A.S;
+            Fj.O = O;
+            Fj.total_out = r->d_total_groups;
+            b->fin.push_back(Fj);
+        }
+    }
+    B.row_block = b->row_blocks;
+    b->row_blocks += (ndr + kRowsPer - 1) / kRowsPer;
+    if (B.grouped) {
+        B.num_block = b->num_blocks;
+        b->num_blocks += (B.claim.cap + 1 + kRowsPer - 1) / kRowsPer;
+        B.slot_block = b->slot_blocks;
+        b->slot_blocks += (B.H.cap + 1 + kRowsPer - 1) / kRowsPer;
+    }
+    std::vector<int> staged;
+    for (int i = 0; i < ncond; ++i) staged.push_back(A.cond[i].col);
+    staged.push_back(p->fact_fk);
+    if (A.has_sum) expr_cols(A.sum, staged);
+    for (int a = 1; a < A.S.nacc; ++a) expr_cols(A.S.acc_expr[a - 1], staged);
+    TQP_TRY(batch_geom(ctx, F, staged, &A.G));
+    lower_fast(A.cond, A.ncond, A.G, A.cf, &A.fast);
+    A.acc = counter(b);
+    A.d_num_joined = r->d_num_joined;
+    A.d_sum = p->has_sum ? r->d_sum : nullptr;
+    A.d_num_rows = (p->emit_row_ids && r->d_row_ids) ? nullptr : r->d_num_rows;
+    A.ctl.err = ctx->d_err;
+    A.ctl.wait_cap = ctx->wait_cap;
+    b->build.push_back(B);
+    if (A.G.ntiles > 0) {
+        b->scan.push_back(J);
+    } else {
+        if (A.d_num_joined) b->zero.push_back(A.d_num_joined);
+        if (A.d_sum) b->zero.push_back(A.d_sum);
+        if (A.d_num_rows) b->zero.push_back(A.d_num_rows);
+    }
+    if (p->emit_row_ids && r->d_row_ids) TQP_TRY(add_filter_job(b, p, r, true, false, r->d_num_rows, nullptr));
+    return TQP_OK;
+}
+
+static bool expr_in(const tqp_expr& e, int lo, int hi) {
+    for (int i = 0; i < e.n && i < TQP_MAX_EXPR; ++i)
+        if (e.op[i] == TQP_X_COL && (e.v[i] < lo || e.v[i] >= hi)) return false;
+    return true;
+}
+
+// Plans the batch lowers itself; the rest (including every malformed plan,
+// which then reports its error) take the single-plan path.
+static bool batchable(const tqp_plan* p, const tqp_result* r) {
+    if (!p->fact || p->npreds < 0 || p->npreds > TQP_MAX_PREDS) return false;
+    if (p->ngc < 0 || p->ngc > TQP_MAX_GROUP_COLS || p->naggs < 0 || p->naggs > TQP_MAX_AGGS) return false;
+    if (p->topk < 0 || p->topk > kTopBlock / 2) return false;
+    const bool grouped = p->ngc > 0 || p->naggs > 0;
+    if (grouped && (!r->d_num_groups || r->capacity_groups < 1)) return false;
+    if (grouped && p->topk > 0 && (p->topk_agg < 0 || p->topk_agg >= p->naggs)) return false;
+    const int nf = p->fact->num_cols;
+    for (int a = 0; a < p->naggs; ++a)
+        if (p->aggs[a].fn == TQP_AVG && !r->d_fvals) return false;
+    if (p->emit_row_ids && r->d_row_ids && !r->d_num_rows) return false;
+    if (!p->dim) {
+        for (int i = 0; i < p->ngc; ++i)
+            if (p->group_cols[i] < 0 || p->group_cols[i] >= nf) return false;
+        if (!grouped || p->topk > 0) return true;
+        const long long maxg = p->max_groups > 0 ? p->max_groups : std::max<long long>(1, r->capacity_groups);
+        return group_table_cap(maxg) <= kSmallCap;
+    }
+    const int nd = p->dim->num_cols;
+    if (p->fact_fk < 0 || p->fact_fk >= nf || p->dim_key < 0 || p->dim_key >= nd) return false;
+    for (int i = 0; i < p->ngc; ++i)
+        if (p->group_cols[i] < nf || p->group_cols[i] >= nf + nd) return false;
+    for (int a = 0; a < p->naggs; ++a)
+        if (p->aggs[a].fn != TQP_COUNT && !expr_in(p->aggs[a].expr, 0, nf)) return false;
+    if (p->has_sum && !expr_in(p->sum_expr, 0, nf)) return false;
+    if (grouped && p->topk == 0) {
+        const long long ndr = p->dim->num_rows;
+        const long long maxg = p->max_groups > 0 ? p->max_groups : (p->ngc == 0 ? 1 : std::max<long long>(1, ndr));
+        if (std::min<long long>(maxg, group_table_cap(maxg) + 1) > kSmallCap) return false;
+    }
+    return true;
+}
+
+static tqp_status lower_batch(tqp_batch* b, const tqp_plan* plans, const tqp_result* res, int32_t n) {
+    // per plan at most 4 counters (join + filter + top-k + spare) and the ticket
+    b->slab_bytes = static_cast<size_t>(kCounterBytes) * (4 * static_cast<size_t>(n) + 2);
+    b->slab = static_cast<unsigned char*>(balloc(b, b->slab_bytes));
+    if (!b->slab) return arena_oom(b->ctx, b->slab_bytes);
+    add_fill(b, b->slab, b->slab_bytes, kZero16);
+    b->d_ticket = counter(b);
+    for (int32_t i = 0; i < n; ++i) {
+        const tqp_plan* p = &plans[i];
+        const tqp_result* r = &res[i];
+        if (!batchable(p, r) || check_table(p->fact, "plan.fact") != TQP_OK ||
+            (p->dim && check_table(p->dim, "plan.dim") != TQP_OK)) {
+            clear_error();
+            b->fb_plans.push_back(*p);
+            b->fb_res.push_back(*r);
+            continue;
+        }
+        if (p->dim) {
+            TQP_TRY(add_join_job(b, p, r));
+            continue;
+        }
+        const bool grouped = p->ngc > 0 || p->naggs > 0;
+        const bool ids = p->emit_row_ids && r->d_row_ids;
+        const bool sum = p->has_sum && r->d_sum;
+        int64_t* cnt = r->d_num_rows ? r->d_num_rows : r->d_num_joined;
+        int64_t* cnt2 = r->d_num_rows ? r->d_num_joined : nullptr;
+        if (grouped) TQP_TRY(add_group_job(b, p, r));
+        if (ids || sum || cnt) {
+            if (!cnt) cnt = reinterpret_cast<int64_t*>(counter(b));
+            TQP_TRY(add_filter_job(b, p, r, ids, sum, cnt, cnt2));
+        }
+    }
+    return TQP_OK;
+}
+
+static long long job_tiles(const ScanJob& j) {
+    return j.kind == kJobFilter ? j.u.f.G.ntiles : j.kind == kJobGroup ? j.u.g.G.ntiles : j.u.j.G.ntiles;
+}
+static EngineCtl& job_ctl(ScanJob& j) {
+    return j.kind == kJobFilter ? j.u.f.ctl : j.kind == kJobGroup ? j.u.g.ctl : j.u.j.ctl;
+}
+static int job_stage_bytes(const ScanJob& j) {
+    return j.kind == kJobFilter ? j.u.f.G.stage_bytes : j.kind == kJobGroup ? j.u.g.G.stage_bytes : j.u.j.G.stage_bytes;
+}
+
+// Chunks of equal size across jobs (a job's last chunk may be short): about
+// four per persistent CTA, so that the uneven tails of the largest tables
+// still balance while each chunk amortises its pipeline fill.
+static void assign_chunks(tqp_batch* b) {
+    long long tiles = 0;
+    for (auto& j : b->scan) tiles += job_tiles(j);
+    const long long target = std::max<long long>(1, static_cast<long long>(b->scan_grid) * 4);
+    const long long ct = std::max<long long>(8, (tiles + target - 1) / target);
+    long long base = 0;
+    for (auto& j : b->scan) {
+        EngineCtl& ctl = job_ctl(j);
+        ctl.chunk_tiles = ct;
+        ctl.nchunks = (job_tiles(j) + ct - 1) / ct;
+        ctl.ticket = nullptr;
+        j.chunk_base = base;
+        base += ctl.nchunks;
+    }
+    b->scan_chunks = base;
+}
+
+// Top-k reduction levels: each level cuts every unfinished job's candidates
+// by kTopBlock / k; a job whose candidates fit one block emits in that level.
+static void plan_top_levels(tqp_batch* b) {
+    const size_t nt = b->top.size();
+    std::vector<long long> n(nt);
+    std::vector<int> buf(nt, 0);
+    std::vector<bool> done(nt, false);
+    for (size_t j = 0; j < nt; ++j) {
+        const long long nb0 = (j + 1 < nt ? b->top[j + 1].first_block : b->top0_blocks) - b->top[j].first_block;
+        n[j] = nb0 * b->top[j].k;
+    }
+    while (true) {
+        std::vector<TopItem> items;
+        long long blocks = 0;
+        for (size_t j = 0; j < nt; ++j) {
+            if (done[j]) continue;
+            TopItem it;
+            memset(&it, 0, sizeof(it));
+            it.job = static_cast<int32_t>(j);
+            it.in_buf = buf[j];
+            it.n_in = n[j];
+            it.first_block = blocks;
+            if (n[j] <= kTopBlock) {
+                it.emit = 1;
+                blocks += 1;
+                done[j] = true;
+            } else {
+                const long long nb = (n[j] + kTopBlock - 1) / kTopBlock;
+                blocks += nb;
+                n[j] = nb * b->top[j].k;
+                buf[j] ^= 1;
+            }
+            items.push_back(it);
+        }
+        if (items.empty()) break;
+        b->levels.push_back(items);
+        b->level_blocks.push_back(blocks);
+    }
+}
+
+// Block -> job maps of every flattened phase, in one array.
+static void build_maps(tqp_batch* b) {
+    auto& M = b->maps;
+    auto push = [&M](size_t j, long long nblocks) {
+        for (long long k = 0; k < nblocks; ++k) M.push_back(static_cast<int32_t>(j));
+    };
+    b->off_fill = M.size();
+    for (size_t r = 0; r < b->fill.size(); ++r) {
+        b->fill[r].first_block = static_cast<long long>(M.size() - b->off_fill);
+        push(r, (b->fill[r].n16 + kFillPer - 1) / kFillPer);
+    }
+    b->fill_blocks = static_cast<long long>(M.size() - b->off_fill);
+    b->off_row = M.size();
+    for (size_t j = 0; j < b->build.size(); ++j) push(j, (b->build[j].nrows + kRowsPer - 1) / kRowsPer);
+    b->off_num = M.size();
+    for (size_t j = 0; j < b->build.size(); ++j)
+        if (b->build[j].grouped) push(j, (b->build[j].claim.cap + 1 + kRowsPer - 1) / kRowsPer);
+    b->off_slot = M.size();
+    for (size_t j = 0; j < b->build.size(); ++j)
+        if (b->build[j].grouped) push(j, (b->build[j].H.cap + 1 + kRowsPer - 1) / kRowsPer);
+    b->off_scan = M.size();
+    for (size_t j = 0; j < b->scan.size(); ++j) push(j, job_ctl(b->scan[j]).nchunks);
+    b->off_compact = M.size();
+    for (size_t j = 0; j < b->compact.size(); ++j) push(j, (b->compact[j].n + kCompactRows - 1) / kCompactRows);
+    b->off_top0 = M.size();
+    for (size_t j = 0; j < b->top.size(); ++j)
+        push(j, (j + 1 < b->top.size() ? b->top[j + 1].first_block : b->top0_blocks) - b->top[j].first_block);
+    for (size_t L = 0; L < b->levels.size(); ++L) {
+        b->off_level.push_back(M.size());
+        const auto& items = b->levels[L];
+        for (size_t i = 0; i < items.size(); ++i)
+            push(i, items[i].emit ? 1 : (items[i].n_in + kTopBlock - 1) / kTopBlock);
+    }
+}
+
+// Descriptor upload: synchronous for a long-lived batch (before any run),
+// stream-ordered for a one-shot batch (earlier work on the stream may still
+// read the per-call scratch).
+template <class T>
+static tqp_status upload(tqp_batch* b, const std::vector<T>& v, T** out, cudaStream_t st) {
+    *out = nullptr;
+    if (v.empty()) return TQP_OK;
+    *out = static_cast<T*>(balloc(b, v.size() * sizeof(T)));
+    if (!*out) return arena_oom(b->ctx, v.size() * sizeof(T));
+    if (b->persistent) TQP_CUDA(cudaMemcpy(*out, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    else TQP_CUDA(cudaMemcpyAsync(*out, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+    return TQP_OK;
+}
+
+// The single-plan path for the plans the batch does not lower, with scratch
+// [base, base + bytes) of their own (they run one after another and share it).
+static tqp_status run_fallbacks(tqp_batch* b, cudaStream_t st, unsigned char* base, size_t bytes, size_t* need) {
+    tqp_ctx sub = *b->ctx;
+    sub.arena = base;
+    sub.arena_bytes = bytes;
+    sub.used = kPersistentBytes;
+    sub.top = bytes;
+    for (size_t i = 0; i < b->fb_plans.size(); ++i) {
+        const tqp_status s = run_plan_one(&sub, &b->fb_plans[i], &b->fb_res[i], st);
+        if (need) *need = std::max(*need, sub.used);
+        if (s != TQP_OK) return s;
+    }
+    return TQP_OK;
+}
+
+static tqp_status batch_launch(tqp_batch* b, cudaStream_t st) {
+    tqp_ctx* ctx = b->ctx;
+    const int32_t* M = b->d_maps;
+    if (b->fill_blocks)
+        k_b_fill<<<static_cast<unsigned>(b->fill_blocks), kFlatThreads, 0, st>>>(b->d_fill, M + b->off_fill, b->d_zero,
+                                                                                 static_cast<int>(b->zero.size()));
+    if (b->row_blocks)
+        k_b_build<<<static_cast<unsigned>(b->row_blocks), kFlatThreads, 0, st>>>(b->d_build, M + b->off_row, ctx->d_err);
+    if (b->num_blocks) {
+        k_b_number<<<static_cast<unsigned>(b->num_blocks), kNumberThreads, 0, st>>>(b->d_build, M + b->off_num);
+        if (b->row_blocks)
+            k_b_remap<<<static_cast<unsigned>(b->row_blocks), kFlatThreads, 0, st>>>(b->d_build, M + b->off_row);
+        if (b->slot_blocks)
+            k_b_direct<<<static_cast<unsigned>(b->slot_blocks), kFlatThreads, 0, st>>>(b->d_build, M + b->off_slot);
+    }
+    if (b->scan_chunks)
+        k_b_scan<<<b->scan_grid, kEngineThreads, b->scan_smem, st>>>(b->d_scan, M + b->off_scan, b->d_ticket,
+                                                                     b->scan_chunks);
+    if (b->compact_blocks)
+        k_b_compact<<<static_cast<unsigned>(b->compact_blocks), kCompactThreads, 0, st>>>(b->d_compact,
+                                                                                           M + b->off_compact);
+    if (!b->fin.empty())
+        k_b_finalize<<<static_cast<unsigned>(b->fin.size()), kFinThreads, kFinSmemBytes, st>>>(b->d_fin);
+    if (b->top0_blocks) {
+        k_b_topk0<<<static_cast<unsigned>(b->top0_blocks), kTopThreads, 0, st>>>(b->d_top, M + b->off_top0);
+        for (size_t L = 0; L < b->levels.size(); ++L)
+            k_b_topk<<<static_cast<unsigned>(b->level_blocks[L]), kTopThreads, 0, st>>>(b->d_top, b->d_levels[L],
+                                                                                       M + b->off_level[L]);
+    }
+    TQP_CUDA(cudaGetLastError());
+    return TQP_OK;
+}
+
+// Lower, lay out and upload every batched job (no launch).
+static tqp_status batch_prepare(tqp_ctx* ctx, const tqp_plan* plans, const tqp_result* res, int32_t n, tqp_batch* b,
+                                cudaStream_t st) {
+    static bool attr_scan[kMaxDevices] = {};
+    static bool attr_fin[kMaxDevices] = {};
+    TQP_TRY(allow_smem(ctx, reinterpret_cast<const void*>(k_b_scan), attr_scan));
+    TQP_TRY(allow_smem(ctx, reinterpret_cast<const void*>(k_b_finalize), attr_fin));
+    TQP_TRY(lower_batch(b, plans, res, n));
+    int max_stage = 128;
+    for (auto& j : b->scan) max_stage = std::max(max_stage, job_stage_bytes(j));
+    b->scan_smem = kHeaderBytes + (sizeof(ScanJob) + 127) / 128 * 128 + kBodyMax +
+                   static_cast<size_t>(kBatchStages) * max_stage;
+    if (b->scan_smem + 1024 > static_cast<size_t>(ctx->smem_optin))
+        return fail(TQP_ERR_UNSUPPORTED, "batched scan needs %zu bytes of shared memory", b->scan_smem);
+    int occ = 0;
+    TQP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_b_scan, kEngineThreads, b->scan_smem));
+    b->scan_grid = ctx->num_sms * std::max(1, std::min(occ, 2));
+    assign_chunks(b);
+    plan_top_levels(b);
+    build_maps(b);
+    TQP_TRY(upload(b, b->fill, &b->d_fill, st));
+    TQP_TRY(upload(b, b->zero, &b->d_zero, st));
+    TQP_TRY(upload(b, b->build, &b->d_build, st));
+    TQP_TRY(upload(b, b->scan, &b->d_scan, st));
+    TQP_TRY(upload(b, b->compact, &b->d_compact, st));
+    TQP_TRY(upload(b, b->fin, &b->d_fin, st));
+    TQP_TRY(upload(b, b->top, &b->d_top, st));
+    b->d_levels.resize(b->levels.size());
+    for (size_t L = 0; L < b->levels.size(); ++L) TQP_TRY(upload(b, b->levels[L], &b->d_levels[L], st));
+    TQP_TRY(upload(b, b->maps, &b->d_maps, st));
+    return TQP_OK;
+}
+
+static tqp_status capture(tqp_batch* b, cudaStream_t cs, bool with_batch, unsigned char* fb_base, size_t fb_bytes,
+                          size_t* need, cudaGraph_t* out) {
+    *out = nullptr;
+    TQP_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    tqp_status s = with_batch ? batch_launch(b, cs) : TQP_OK;
+    if (s == TQP_OK) s = run_fallbacks(b, cs, fb_base, fb_bytes, need);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(cs, &g);
+    if (s != TQP_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    *out = g;
+    return TQP_OK;
+}
+
+static tqp_status batch_create(tqp_ctx* ctx, const tqp_plan* plans, const tqp_result* res, int32_t n, tqp_batch* b) {
+    b->ctx = ctx;
+    b->persistent = true;
+    b->top_before = ctx->top;
+    TQP_TRY(batch_prepare(ctx, plans, res, n, b, nullptr));
+    cudaStream_t cs = nullptr;
+    TQP_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    tqp_status s = TQP_OK;
+    if (!b->fb_plans.empty()) {
+        // size the single-plan path's scratch (a capture that is never run),
+        // then give it a long-lived region of its own
+        const size_t lo = (ctx->used + 255) / 256 * 256;
+        size_t need = 0;
+        cudaGraph_t g = nullptr;
+        s = lo < ctx->top ? capture(b, cs, false, ctx->arena + lo, ctx->top - lo, &need, &g)
+                          : arena_oom(ctx, kPersistentBytes);
+        if (g) cudaGraphDestroy(g);
+        if (s == TQP_OK) {
+            b->fb_bytes = std::max<size_t>(need, kPersistentBytes);
+            b->fb_arena = static_cast<unsigned char*>(arena_alloc_top(ctx, b->fb_bytes));
+            if (!b->fb_arena) s = arena_oom(ctx, b->fb_bytes);
+        }
+    }
+    if (s == TQP_OK) s = capture(b, cs, true, b->fb_arena, b->fb_bytes, nullptr, &b->graph);
+    cudaStreamDestroy(cs);
+    TQP_TRY(s);
+    TQP_CUDA(cudaGraphInstantiate(&b->exec, b->graph, 0));
+    return TQP_OK;
+}
+
+static void release(tqp_batch* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    // long-lived regions are freed newest first; with no batch left the whole
+    // top region is free again
+    if (--b->ctx->live_batches == 0) b->ctx->top = b->ctx->arena_bytes;
+    else if (b->ctx->top < b->top_before && b->ctx->top == b->top_after) b->ctx->top = b->top_before;
+}
+
+}  // namespace tqp
+
+extern "C" {
+
+tqp_status tqp_batch_create(tqp_ctx* ctx, const tqp_plan* plans, const tqp_result* res, int32_t n, tqp_batch** out) {
+    clear_error();
+    TQP_TRY(check_ctx(ctx));
+    if (!out || n < 0 || (n > 0 && (!plans || !res))) return fail(TQP_ERR_INVALID_ARG, "bad batch arguments");
+    *out = nullptr;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(TQP_ERR_CUDA, "cannot select device %d", ctx->device);
+    tqp_batch* b = new (std::nothrow) tqp_batch();
+    if (!b) return fail(TQP_ERR_OUT_OF_MEMORY, "host allocation failed");
+    ++ctx->live_batches;
+    const tqp_status s = batch_create(ctx, plans, res, n, b);
+    b->top_after = ctx->top;
+    if (s != TQP_OK) {
+        release(b);
+        delete b;
+        return s;
+    }
+    *out = b;
+    return TQP_OK;
+}
+
+tqp_status tqp_batch_run(tqp_batch* b, void* stream) {
+    clear_error();
+    if (!b || !b->exec) return fail(TQP_ERR_INVALID_ARG, "batch is NULL");
+    DeviceGuard g(b->ctx->device);
+    if (!g.ok) return fail(TQP_ERR_CUDA, "cannot select device %d", b->ctx->device);
+    TQP_CUDA(cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(stream)));
+    return TQP_OK;
+}
+
+tqp_status tqp_batch_destroy(tqp_batch* b) {
+    clear_error();
+    if (!b) return TQP_OK;
+    {
+        DeviceGuard g(b->ctx->device);
+        cudaDeviceSynchronize();  // no replay may still read the batch's scratch
+        release(b);
+    }
+    delete b;
+    return TQP_OK;
+}
+
+tqp_status tqp_run_plans(tqp_ctx* ctx, const tqp_plan* plans, const tqp_result* res, int32_t n, void* stream) {
+    clear_error();
+    TQP_TRY(check_ctx(ctx));
+    if (n < 0 || (n > 0 && (!plans || !res))) return fail(TQP_ERR_INVALID_ARG, "bad plan array");
+    if (n == 0) return TQP_OK;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(TQP_ERR_CUDA, "cannot select device %d", ctx->device);
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    arena_reset(ctx);
+    tqp_batch b;
+    b.ctx = ctx;
+    b.persistent = false;
+    TQP_TRY(batch_prepare(ctx, plans, res, n, &b, st));
+    TQP_TRY(batch_launch(&b, st));
+    if (b.fb_plans.empty()) return TQP_OK;
+    const size_t lo = (ctx->used + 255) / 256 * 256;
+    if (lo >= ctx->top) return arena_oom(ctx, lo + kPersistentBytes);
+    return run_fallbacks(&b, st, ctx->arena + lo, ctx->top - lo, nullptr);
+}
+
+}  // extern "C"

@@ -41,12 +41,20 @@ void arena_reset(tqp_ctx* ctx) { ctx->used = kPersistentBytes; }
 
 void* arena_alloc(tqp_ctx* ctx, size_t bytes, size_t align) {
     size_t off = (ctx->used + align - 1) / align * align;
-    if (off + bytes > ctx->arena_bytes) {
+    if (off + bytes > ctx->top) {
         ctx->used = off + bytes;  // remember the demand for the error message
         return nullptr;
     }
     ctx->used = off + bytes;
     return ctx->arena + off;
+}
+
+void* arena_alloc_top(tqp_ctx* ctx, size_t bytes, size_t align) {
+    if (bytes > ctx->top) return nullptr;
+    const size_t start = (ctx->top - bytes) / align * align;
+    if (start < ctx->used || start < kPersistentBytes) return nullptr;
+    ctx->top = start;
+    return ctx->arena + start;
 }
 
 tqp_status arena_oom(tqp_ctx* ctx, size_t bytes) {
@@ -341,6 +349,7 @@ tqp_status tqp_ctx_create(int device, void* d_arena, size_t arena_bytes, tqp_ctx
     cudaDeviceGetAttribute(&ctx->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     cudaDeviceGetAttribute(&ctx->l2_bytes, cudaDevAttrL2CacheSize, device);
     ctx->arena_bytes = arena_bytes;
+    ctx->top = arena_bytes;
     ctx->wait_cap = kDefaultWaitCap;
     if (d_arena) {
         ctx->arena = static_cast<unsigned char*>(d_arena);

@@ -254,6 +254,90 @@ struct EngineCtl {
 //   chunk_end(G, chunk, t0, t1, cw, lane)  after the chunk's last tile
 //   finish(G, cw, lane)                    after the CTA's last chunk
 // Body::kSmemBytes bytes of shared memory precede the stages.
+// One chunk [t0, t1) of tiles through the stage ring.  `it` (the pipeline
+// position) and `failed` persist across chunks; producer and consumers advance
+// `it` identically, so every stage's mbarrier phase parity stays consistent.
+template <class Body>
+__device__ __forceinline__ void run_chunk(const ScanGeom& G, const EngineCtl& ctl, Body& body, long long chunk,
+                                          long long t0, long long t1, EngineHeader* h, unsigned char* stages,
+                                          long long& it, bool& failed, uint64_t stream_policy, int warp, int lane) {
+    if (warp == kConsumerWarps) {
+        // ---------------- producer: stage every tile of the chunk ----------------
+        if (lane == 0) {
+            for (long long t = t0; t < t1; ++t, ++it) {
+                const int s = static_cast<int>(it % G.nstages);
+                const uint32_t ph = static_cast<uint32_t>((it / G.nstages) & 1);
+                if (!failed && !mbar_wait(&h->empty[s], ph ^ 1u, ctl.wait_cap)) {
+                    latch_error(ctl.err, TQP_ERR_TIMEOUT);
+                    failed = true;
+                }
+                const int64_t row0 = static_cast<int64_t>(t) * G.T;
+                const int rows = static_cast<int>(G.n - row0 < G.T ? G.n - row0 : G.T);
+                uint32_t total = 0;
+                if (!failed)
+                    for (int k = 0; k < G.nstaged; ++k)
+                        total += (static_cast<uint32_t>(rows) * esize_of(G.col[G.staged[k]].type)) & ~15u;
+                unsigned char* dst = stages + static_cast<size_t>(s) * G.stage_bytes;
+                if (total == 0) {
+                    mbar_arrive(&h->full[s]);
+                } else {
+                    mbar_arrive_expect_tx(&h->full[s], total);
+                    for (int k = 0; k < G.nstaged; ++k) {
+                        const ColRef& cr = G.col[G.staged[k]];
+                        const int es = esize_of(cr.type);
+                        const uint32_t bytes = (static_cast<uint32_t>(rows) * es) & ~15u;
+                        if (bytes) bulk_g2s(dst + cr.soff, cr.ptr + row0 * es, bytes, &h->full[s], stream_policy);
+                    }
+                }
+            }
+            // Drain: no bulk copy may still be landing when the chunk (or the
+            // CTA) ends, even if a consumer gave up waiting.  Phases the
+            // consumers already observed test as complete at once.
+            const long long issued = t1 - t0;
+            for (long long j = (issued > G.nstages ? issued - G.nstages : 0); j < issued; ++j) {
+                const long long pos = it - issued + j;
+                mbar_wait(&h->full[pos % G.nstages], static_cast<uint32_t>((pos / G.nstages) & 1), ctl.wait_cap);
+            }
+        } else {
+            it += t1 - t0;
+        }
+    } else {
+        // ---------------- consumers ----------------
+        const int cw = warp;
+        for (long long t = t0; t < t1; ++t, ++it) {
+            const int s = static_cast<int>(it % G.nstages);
+            const uint32_t ph = static_cast<uint32_t>((it / G.nstages) & 1);
+            if (!failed && !mbar_wait(&h->full[s], ph, ctl.wait_cap)) {
+                latch_error(ctl.err, TQP_ERR_TIMEOUT);
+                failed = true;
+            }
+            if (!failed) {
+                TileView v;
+                v.stage = stages + static_cast<size_t>(s) * G.stage_bytes;
+                v.tile = t;
+                v.row0 = static_cast<int64_t>(t) * G.T;
+                v.rows = static_cast<int>(G.n - v.row0 < G.T ? G.n - v.row0 : G.T);
+                v.full = v.rows == G.T;
+                body.pass1(G, v, cw, lane);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&h->empty[s]);
+        }
+        body.chunk_end(G, chunk, t0, t1, cw, lane);
+    }
+}
+
+// Initialise the stage ring's mbarriers (thread 0; callers __syncthreads after).
+__device__ __forceinline__ void init_stage_ring(EngineHeader* h, int nstages) {
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < nstages; ++s) {
+            mbar_init(&h->full[s], 1);
+            mbar_init(&h->empty[s], kConsumerWarps);
+        }
+        fence_mbar_init();
+    }
+}
+
 template <class Body>
 __device__ __forceinline__ void run_engine(const ScanGeom& G, const EngineCtl& ctl, Body& body,
                                            unsigned char* smem) {
@@ -261,17 +345,10 @@ __device__ __forceinline__ void run_engine(const ScanGeom& G, const EngineCtl& c
     unsigned char* stages = smem + kHeaderBytes + Body::kSmemBytes;
     const int warp = threadIdx.x / kWarp;
     const int lane = threadIdx.x % kWarp;
-
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < G.nstages; ++s) {
-            mbar_init(&h->full[s], 1);
-            mbar_init(&h->empty[s], kConsumerWarps);
-        }
-        fence_mbar_init();
-    }
+    init_stage_ring(h, G.nstages);
     __syncthreads();
 
-    long long it = 0;  // pipeline position, advanced identically by producer and consumers
+    long long it = 0;
     bool failed = false;
     const uint64_t stream_policy = l2_evict_first_policy();
     while (true) {
@@ -282,70 +359,7 @@ __device__ __forceinline__ void run_engine(const ScanGeom& G, const EngineCtl& c
         if (chunk >= ctl.nchunks) break;
         const long long t0 = chunk * ctl.chunk_tiles;
         const long long t1 = (t0 + ctl.chunk_tiles < G.ntiles) ? t0 + ctl.chunk_tiles : G.ntiles;
-
-        if (warp == kConsumerWarps) {
-            // ---------------- producer: stage every tile of the chunk ----------------
-            if (lane == 0) {
-                for (long long t = t0; t < t1; ++t, ++it) {
-                    const int s = static_cast<int>(it % G.nstages);
-                    const uint32_t ph = static_cast<uint32_t>((it / G.nstages) & 1);
-                    if (!failed && !mbar_wait(&h->empty[s], ph ^ 1u, ctl.wait_cap)) {
-                        latch_error(ctl.err, TQP_ERR_TIMEOUT);
-                        failed = true;
-                    }
-                    const int64_t row0 = static_cast<int64_t>(t) * G.T;
-                    const int rows = static_cast<int>(G.n - row0 < G.T ? G.n - row0 : G.T);
-                    uint32_t total = 0;
-                    if (!failed)
-                        for (int k = 0; k < G.nstaged; ++k)
-                            total += (static_cast<uint32_t>(rows) * esize_of(G.col[G.staged[k]].type)) & ~15u;
-                    unsigned char* dst = stages + static_cast<size_t>(s) * G.stage_bytes;
-                    if (total == 0) {
-                        mbar_arrive(&h->full[s]);
-                    } else {
-                        mbar_arrive_expect_tx(&h->full[s], total);
-                        for (int k = 0; k < G.nstaged; ++k) {
-                            const ColRef& cr = G.col[G.staged[k]];
-                            const int es = esize_of(cr.type);
-                            const uint32_t bytes = (static_cast<uint32_t>(rows) * es) & ~15u;
-                            if (bytes) bulk_g2s(dst + cr.soff, cr.ptr + row0 * es, bytes, &h->full[s], stream_policy);
-                        }
-                    }
-                }
-                // Drain: no bulk copy may still be landing when the chunk (or the
-                // CTA) ends, even if a consumer gave up waiting.  Phases the
-                // consumers already observed test as complete at once.
-                const long long issued = t1 - t0;
-                for (long long j = (issued > G.nstages ? issued - G.nstages : 0); j < issued; ++j) {
-                    const long long pos = it - issued + j;
-                    mbar_wait(&h->full[pos % G.nstages], static_cast<uint32_t>((pos / G.nstages) & 1),
-                              ctl.wait_cap);
-                }
-            }
-        } else {
-            // ---------------- consumers ----------------
-            const int cw = warp;
-            for (long long t = t0; t < t1; ++t, ++it) {
-                const int s = static_cast<int>(it % G.nstages);
-                const uint32_t ph = static_cast<uint32_t>((it / G.nstages) & 1);
-                if (!failed && !mbar_wait(&h->full[s], ph, ctl.wait_cap)) {
-                    latch_error(ctl.err, TQP_ERR_TIMEOUT);
-                    failed = true;
-                }
-                if (!failed) {
-                    TileView v;
-                    v.stage = stages + static_cast<size_t>(s) * G.stage_bytes;
-                    v.tile = t;
-                    v.row0 = static_cast<int64_t>(t) * G.T;
-                    v.rows = static_cast<int>(G.n - v.row0 < G.T ? G.n - v.row0 : G.T);
-                    v.full = v.rows == G.T;
-                    body.pass1(G, v, cw, lane);
-                }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&h->empty[s]);
-            }
-            body.chunk_end(G, chunk, t0, t1, cw, lane);
-        }
+        run_chunk(G, ctl, body, chunk, t0, t1, h, stages, it, failed, stream_policy, warp, lane);
         __syncthreads();
     }
     if (warp != kConsumerWarps) body.finish(G, warp, lane);

@@ -30,7 +30,6 @@
 
 namespace tqp {
 
-constexpr int kCompactThreads = 256;
 
 
 // Scratch layout (bytes): ticket + acc[3], block totals, then the mask.
@@ -55,66 +54,10 @@ __global__ void __launch_bounds__(kEngineThreads, 2) k_filter(const __grid_const
     run_engine(A.G, A.ctl, body, smem);
 }
 
-// Expand the selection mask of rows [b * kCompactRows, ...) into row ids.
 __global__ void __launch_bounds__(kCompactThreads) k_compact(const uint32_t* __restrict__ mask,
                                                              const uint32_t* __restrict__ block_tot, long long n,
                                                              int32_t* __restrict__ row_ids, long long capacity) {
-    constexpr int W = kCompactThreads / kWarp;
-    __shared__ unsigned long long red[W];
-    __shared__ uint32_t wtot[2][W];
-    const int lane = threadIdx.x % kWarp, w = threadIdx.x / kWarp;
-    const long long b = blockIdx.x;
-    // offset of this block: every earlier block's total
-    unsigned long long before_blocks = 0;
-    for (long long i = threadIdx.x; i < b; i += kCompactThreads) before_blocks += block_tot[i];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) before_blocks += __shfl_xor_sync(0xffffffffu, before_blocks, o);
-    if (lane == 0) red[w] = before_blocks;
-    __syncthreads();
-    unsigned long long running = 0;
-#pragma unroll
-    for (int i = 0; i < W; ++i) running += red[i];
-
-    const long long nwords = (n + kWarp - 1) / kWarp;
-    const long long w0 = b * kCompactWords;
-    const long long w1 = (w0 + kCompactWords < nwords) ? w0 + kCompactWords : nwords;
-    const uint32_t lt = lanemask_lt();
-    int par = 0;
-    for (long long base = w0; base < w1; base += kCompactThreads) {
-        const long long wi = base + threadIdx.x;
-        const uint32_t word = wi < w1 ? mask[wi] : 0u;
-        const uint32_t c = __popc(word);
-        uint32_t incl = c;
-#pragma unroll
-        for (int o = 1; o < kWarp; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        if (lane == kWarp - 1) wtot[par][w] = incl;
-        __syncthreads();
-        unsigned long long before = 0, round_total = 0;
-#pragma unroll
-        for (int i = 0; i < W; ++i) {
-            const uint32_t x = wtot[par][i];
-            before += (i < w) ? x : 0u;
-            round_total += x;
-        }
-        const unsigned long long my_off = running + before + (incl - c);
-        uint32_t nz = __ballot_sync(0xffffffffu, word != 0u);
-        while (nz) {
-            const int j = __ffs(nz) - 1;
-            nz &= nz - 1;
-            const uint32_t wj = __shfl_sync(0xffffffffu, word, j);
-            const unsigned long long oj = __shfl_sync(0xffffffffu, my_off, j);
-            if ((wj >> lane) & 1u) {
-                const unsigned long long pos = oj + __popc(wj & lt);
-                if (pos < static_cast<unsigned long long>(capacity))
-                    row_ids[pos] = static_cast<int32_t>((base + w * kWarp + j) * kWarp + lane);
-            }
-        }
-        running += round_total;
-        par ^= 1;
-    }
+    compact_block(mask, block_tot, n, row_ids, capacity, blockIdx.x);
 }
 
 // Lower a filter call into kernel arguments and a launch shape.

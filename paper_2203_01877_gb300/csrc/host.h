@@ -30,6 +30,8 @@ struct tqp_ctx {
     size_t arena_bytes;
     bool owns_arena;
     size_t used;           // bump offset of the current call
+    size_t top;            // start of the long-lived region (batches) at the arena's end
+    int live_batches;      // batches holding long-lived regions
     int* d_err;            // latched device error (persistent, arena start)
     long long wait_cap;
     tqp_tuning forced;     // tile_rows == 0: no override
@@ -60,6 +62,9 @@ void clear_error();
 void arena_reset(tqp_ctx* ctx);
 // Returns nullptr (and records the shortfall) when the arena is exhausted.
 void* arena_alloc(tqp_ctx* ctx, size_t bytes, size_t align = 256);
+// Long-lived allocation from the arena's end (survives arena_reset; freed by
+// moving ctx->top back, newest first).
+void* arena_alloc_top(tqp_ctx* ctx, size_t bytes, size_t align = 256);
 tqp_status arena_oom(tqp_ctx* ctx, size_t bytes);
 
 // Select the context's device for the duration of a call.

@@ -18,6 +18,7 @@
 // Keys compare by their int64 value; int32, int64 and uint8 key columns mix.
 #include "host.h"
 #include "join.cuh"
+#include "dimgroups.cuh"
 
 namespace tqp {
 
@@ -39,13 +40,8 @@ __global__ void k_ht_init(JoinHT H) {
 __global__ void k_ht_insert_chain(JoinHT H, const unsigned char* key_col, int key_type, long long n,
                                   uint32_t* next, int* err) {
     for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
-         i += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const uint64_t key = static_cast<uint64_t>(ldg_typed(key_col, key_type, i));
-        const long long s = ht_claim(H, key, err);
-        if (s < 0) continue;
-        next[i] = atomicExch(&H.slots[s].z, static_cast<uint32_t>(i));
-        atomicAdd(&H.slots[s].w, 1u);
-    }
+         i += static_cast<long long>(gridDim.x) * blockDim.x)
+        ht_chain_insert_row(H, key_col, key_type, i, next, err);
 }
 
 tqp_status ht_build_chain(tqp_ctx* ctx, const tqp_table* build, int32_t key_col, JoinHT* H, uint32_t** next,

@@ -15,6 +15,7 @@
 #include "group.cuh"
 #include "join.cuh"
 #include "bodies.cuh"
+#include "dimgroups.cuh"
 
 namespace tqp {
 
@@ -29,11 +30,6 @@ tqp_status launch_groupby(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* pred
 tqp_status ht_build_chain(tqp_ctx* ctx, const tqp_table* build, int32_t key_col, JoinHT* H, uint32_t** next,
                           cudaStream_t stream);
 
-struct DimCols {
-    const unsigned char* ptr[TQP_MAX_COLS];
-    int32_t type[TQP_MAX_COLS];
-};
-
 // Dense group ids of the dimension rows, in three small passes:
 //   claim  each dim row inserts its packed group key into a claim table
 //          (open addressing, keys only) and remembers the slot;
@@ -44,80 +40,23 @@ struct DimCols {
 __global__ void k_dim_claim(const __grid_constant__ GroupSpec S, const __grid_constant__ DimCols D, long long n,
                             uint32_t* dslot, int* err) {
     for (long long d = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; d < n;
-         d += static_cast<long long>(gridDim.x) * blockDim.x) {
-        uint64_t k = 0;
-        for (int i = 0; i < S.ngc; ++i) {
-            const int b = S.key_bits[i];
-            const int c = S.key_col[i];
-            const uint64_t e = enc_key(ldg_typed(D.ptr[c], D.type[c], d), b);
-            k = (b == 64) ? e : ((k << b) | e);
-        }
-        long long s = gtab_slot(S, k, err);
-        if (s == S.cap) S.keys[S.cap] = 0;  // mark the all-ones key's slot as claimed
-        dslot[d] = s < 0 ? 0u : static_cast<uint32_t>(s);
-    }
+         d += static_cast<long long>(gridDim.x) * blockDim.x)
+        dim_claim_row(S, D, d, dslot, err);
 }
 
-// Each block numbers one contiguous range of claim slots and takes its ids
-// with a single atomic (a single counter hit once per claimed slot or per warp
-// serialises at the L2 when groups are many).
-constexpr int kNumberThreads = 256;
 __global__ void __launch_bounds__(kNumberThreads) k_dense_number(const __grid_constant__ GroupSpec S,
                                                                  uint32_t* slot2dense, unsigned long long* keys_out,
                                                                  unsigned long long* acc_out, long long* d_n,
                                                                  long long per_block) {
-    constexpr int W = kNumberThreads / kWarp;
-    __shared__ uint32_t wc[2][W];
-    __shared__ unsigned long long base_sm;
-    const int lane = threadIdx.x % kWarp, w = threadIdx.x / kWarp;
     const long long s0 = blockIdx.x * per_block;
     const long long s1 = (s0 + per_block < S.cap + 1) ? s0 + per_block : S.cap + 1;
-    uint32_t c = 0;
-    for (long long i = s0 + threadIdx.x; i < s1; i += kNumberThreads) c += S.keys[i] != kEmptyKey;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    if (lane == 0) wc[0][w] = c;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long t = 0;
-        for (int i = 0; i < W; ++i) t += wc[0][i];
-        base_sm = t ? atomicAdd(reinterpret_cast<unsigned long long*>(d_n), t) : 0ULL;
-    }
-    __syncthreads();
-    unsigned long long running = base_sm;
-    int par = 1;
-    for (long long rb = s0; rb < s1; rb += kNumberThreads) {
-        const long long i = rb + threadIdx.x;
-        const unsigned long long k = i < s1 ? S.keys[i] : kEmptyKey;
-        const bool used = k != kEmptyKey;
-        const uint32_t m = __ballot_sync(0xffffffffu, used);
-        if (lane == 0) wc[par][w] = __popc(m);
-        __syncthreads();
-        unsigned long long before = 0, total = 0;
-#pragma unroll
-        for (int j = 0; j < W; ++j) {
-            before += j < w ? wc[par][j] : 0u;
-            total += wc[par][j];
-        }
-        if (used) {
-            const long long id = static_cast<long long>(running + before + __popc(m & lanemask_lt()));
-            slot2dense[i] = static_cast<uint32_t>(id);
-            keys_out[id] = i < S.cap ? k : kEmptyKey;
-            for (int a = 0; a < S.nacc; ++a) acc_out[id * S.nacc + a] = 0;
-        }
-        running += total;
-        par ^= 1;
-    }
+    dense_number_range(S, slot2dense, keys_out, acc_out, d_n, s0, s1);
 }
 
-// Slots of keys with exactly one dimension row take that row's dense group id
-// (flagged), so a probe that hits them needs no further dependent load.
 __global__ void k_ht_direct(JoinHT H, const uint32_t* dgs) {
     for (long long s = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; s <= H.cap;
-         s += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const uint4 sl = H.slots[s];
-        if (sl.w == 1u && sl.z != kNoRow) H.slots[s].z = dgs[sl.z] | kDirectGroup;
-    }
+         s += static_cast<long long>(gridDim.x) * blockDim.x)
+        ht_direct_slot(H, dgs, s);
 }
 
 __global__ void k_dim_remap(const uint32_t* dslot, const uint32_t* slot2dense, long long n, uint32_t* dgs) {
@@ -125,8 +64,6 @@ __global__ void k_dim_remap(const uint32_t* dslot, const uint32_t* slot2dense, l
          d += static_cast<long long>(gridDim.x) * blockDim.x)
         dgs[d] = slot2dense[dslot[d]];
 }
-
-
 
 __global__ void __launch_bounds__(kEngineThreads, 2) k_plan_join(const __grid_constant__ PlanJoinArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -344,15 +281,4 @@ extern "C" tqp_status tqp_run_plan(tqp_ctx* ctx, const tqp_plan* plan, const tqp
     DeviceGuard g(ctx->device);
     if (!g.ok) return fail(TQP_ERR_CUDA, "cannot select device %d", ctx->device);
     return run_plan_one(ctx, plan, res, static_cast<cudaStream_t>(stream));
-}
-
-extern "C" tqp_status tqp_run_plans(tqp_ctx* ctx, const tqp_plan* plans, const tqp_result* res, int32_t n,
-                                    void* stream) {
-    clear_error();
-    TQP_TRY(check_ctx(ctx));
-    if (n < 0 || (n > 0 && (!plans || !res))) return fail(TQP_ERR_INVALID_ARG, "bad plan array");
-    DeviceGuard g(ctx->device);
-    if (!g.ok) return fail(TQP_ERR_CUDA, "cannot select device %d", ctx->device);
-    for (int32_t i = 0; i < n; ++i) TQP_TRY(run_plan_one(ctx, &plans[i], &res[i], static_cast<cudaStream_t>(stream)));
-    return TQP_OK;
 }

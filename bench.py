@@ -278,10 +278,10 @@ def secondary_workloads(tqp, torch, dev, local, reps):
 BATCH_PLANS = 512
 
 
-def batched_workload(tqp, torch, dev, local, reps, n_plans=BATCH_PLANS, seed=datagen.DEFAULT_SEED + 3):
+def batched_plans(tqp, torch, dev, n_plans=BATCH_PLANS, seed=datagen.DEFAULT_SEED + 3):
     """n_plans independent plans (q1 group-by, q6 filter-compact-sum, join-group-top-100 in turn) over tables of
-    log-uniform sizes in [10K, 5M] rows: one captured batch (tqp_batch_run) against one tqp_run_plan call per plan.
-    Every plan reads its own disjoint slice of the generated columns (no table is shared, so nothing stays in L2)."""
+    log-uniform sizes in [10K, 5M] rows.  Every plan reads its own disjoint slice of the generated columns (no
+    table is shared, so nothing stays in L2).  Returns (plans, results, buffers, meta)."""
     sizes = datagen.log_uniform_int(seed, 77, n_plans, 10_000, 5_000_000)
     kinds = [i % 3 for i in range(n_plans)]
     scan_rows = int(sum(int(s) for s, k in zip(sizes, kinds) if k != 2))
@@ -327,15 +327,37 @@ def batched_workload(tqp, torch, dev, local, reps, n_plans=BATCH_PLANS, seed=dat
             results.append(tqp.make_result(None, 0, None, None, b["keys"], b["iv"], None, 100, b["ng"], b["tot"],
                                            b["nj"]))
             alg_bytes += n * 12 + nb * 8
+        b["kind"] = kind
         keep.append(b)
+    meta = {"scan_rows": scan_rows, "probe_rows": probe_rows, "alg_bytes": alg_bytes}
+    return plans, results, keep, meta
+
+
+def batched_snapshot(torch, keep):
+    """The written part of every plan's outputs (counts, sums, groups, row ids), as int64 host tensors."""
+    torch.cuda.synchronize()
+    out = []
+    for b in keep:
+        if b["kind"] == 0:
+            g = max(int(b["ng"].item()), 0)
+            parts = [b["ng"], b["tot"], b["nr"], b["keys"][:2 * g], b["iv"][:5 * g], b["fv"][:5 * g].view(torch.int64)]
+        elif b["kind"] == 1:
+            k = min(max(int(b["nr"].item()), 0), b["ids"].numel())
+            parts = [b["nr"], b["s"], b["ids"][:k].to(torch.int64)]
+        else:
+            g = max(int(b["ng"].item()), 0)
+            parts = [b["ng"], b["tot"], b["nj"], b["keys"][:g], b["iv"][:2 * g]]
+        out.append(torch.cat([x.flatten() for x in parts]).cpu())
+    return out
+
+
+def batched_workload(tqp, torch, dev, local, reps, n_plans=BATCH_PLANS):
+    """The batched mix: one captured batch (tqp_batch_run) against one tqp_run_plan call per plan."""
+    plans, results, keep, meta = batched_plans(tqp, torch, dev, n_plans)
+    scan_rows, probe_rows, alg_bytes = meta["scan_rows"], meta["probe_rows"], meta["alg_bytes"]
     stream = torch.cuda.current_stream()
     ctx = tqp.Context(local, 4 << 30)
-
-    def snapshot():
-        torch.cuda.synchronize()
-        return [torch.cat([t.flatten().view(torch.int64) if t.dtype == torch.float64 else t.flatten().to(torch.int64)
-                           for k, t in sorted(b.items()) if torch.is_tensor(t) and k not in ("fk", "val")]).cpu()
-                for b in keep]
+    snapshot = lambda: batched_snapshot(torch, keep)  # noqa: E731
 
     def seq():
         for p, r in zip(plans, results):
@@ -355,9 +377,9 @@ def batched_workload(tqp, torch, dev, local, reps, n_plans=BATCH_PLANS, seed=dat
     ctx.check(stream)
     want = snapshot()
     for b in keep:
-        for k, t in b.items():
-            if torch.is_tensor(t) and k not in ("fk", "val"):
-                t.fill_(-7)
+        for k in ("keys", "iv", "fv", "ng", "tot", "nr", "ids", "s", "nj"):
+            if k in b:
+                b[k].fill_(-7)
     batch = tqp.tqp_batch_create(ctx, plans, results)
     run = lambda: tqp.tqp_batch_run(batch, stream)  # noqa: E731
     bat_ms = _time_launches(torch, run, reps, stream=stream)

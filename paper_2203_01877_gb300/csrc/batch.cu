@@ -11,10 +11,11 @@
 //   number    dense group ids (claim-table ranges)
 //   remap     dimension row -> dense group id
 //   direct    dense ids into the slots of unique build keys
-//   scan      ONE persistent launch of the staged scan engine: CTAs draw
-//             chunk tickets across all jobs' tables (uneven sizes balance
-//             themselves) and run the filter / group-by / joined-aggregation
-//             body of the chunk's job
+//   scan      one persistent launch of the staged scan engine per body kind
+//             (filter, group-by, joined aggregation): CTAs draw chunk
+//             tickets across the tables of every job of that kind (uneven
+//             sizes balance themselves); each kind gets its own shared-memory
+//             layout and occupancy
 //   compact   selection masks -> row ids
 //   finalize  one CTA per small group table (keys ascending)
 //   top-k     the bitonic tournament, one launch per level for all plans
@@ -38,8 +39,7 @@ tqp_status run_plan_one(tqp_ctx* ctx, const tqp_plan* p, const tqp_result* r, cu
 constexpr int kBatchTile = 1024;
 constexpr int kBatchStages = 3;
 constexpr int kJobFilter = 1, kJobGroup = 2, kJobJoin = 3;
-constexpr int kBodyMax = GroupBody::kSmemBytes > FilterBody::kSmemBytes ? GroupBody::kSmemBytes
-                                                                        : FilterBody::kSmemBytes;
+constexpr int kKinds = 3;  // scan bodies: filter, group-by, joined aggregation
 constexpr int kFlatThreads = 256;
 constexpr int kFillPer = 4096;  // 16-byte units per fill block
 constexpr int kRowsPer = 2048;  // elements per block of the element-wise phases
@@ -171,15 +171,31 @@ __device__ __forceinline__ void scan_chunk(const Args& a, unsigned char* body_sm
     run_chunk(a.G, a.ctl, body, local, t0, t1, h, stages, it, failed, policy, warp, lane);
 }
 
-// The persistent multi-plan scan: chunk tickets span every job's tables.
-__global__ void __launch_bounds__(kEngineThreads, 2) k_b_scan(const ScanJob* J, const int32_t* cjob,
+template <class Body> struct BodyArgs;
+template <> struct BodyArgs<FilterBody> {
+    static __device__ __forceinline__ const FilterArgs& of(const ScanJob& j) { return j.u.f; }
+};
+template <> struct BodyArgs<GroupBody> {
+    static __device__ __forceinline__ const GroupArgs& of(const ScanJob& j) { return j.u.g; }
+};
+template <> struct BodyArgs<PlanJoinBody> {
+    static __device__ __forceinline__ const PlanJoinArgs& of(const ScanJob& j) { return j.u.j; }
+};
+
+constexpr int kJobBytes = (sizeof(ScanJob) + 127) / 128 * 128;
+template <class Body>
+constexpr int body_bytes() { return (Body::kSmemBytes + 127) / 128 * 128; }
+
+// The persistent multi-plan scan of one body kind: chunk tickets span the
+// tables of every job of that kind.
+template <class Body>
+__global__ void __launch_bounds__(kEngineThreads, Body::kMinBlocks) k_b_scan(const ScanJob* J, const int32_t* cjob,
                                                               unsigned long long* ticket, long long total_chunks) {
     extern __shared__ __align__(128) unsigned char smem[];
-    constexpr int kJobBytes = (sizeof(ScanJob) + 127) / 128 * 128;
     EngineHeader* h = reinterpret_cast<EngineHeader*>(smem);
     ScanJob* sj = reinterpret_cast<ScanJob*>(smem + kHeaderBytes);
     unsigned char* body_smem = smem + kHeaderBytes + kJobBytes;
-    unsigned char* stages = body_smem + kBodyMax;
+    unsigned char* stages = body_smem + body_bytes<Body>();
     __shared__ int job_sm;
     const int warp = threadIdx.x / kWarp;
     const int lane = threadIdx.x % kWarp;
@@ -204,12 +220,7 @@ __global__ void __launch_bounds__(kEngineThreads, 2) k_b_scan(const ScanJob* J, 
         }
         __syncthreads();
         const long long local = chunk - sj->chunk_base;
-        if (sj->kind == kJobFilter)
-            scan_chunk<FilterBody>(sj->u.f, body_smem, local, h, stages, it, failed, policy, warp, lane);
-        else if (sj->kind == kJobGroup)
-            scan_chunk<GroupBody>(sj->u.g, body_smem, local, h, stages, it, failed, policy, warp, lane);
-        else
-            scan_chunk<PlanJoinBody>(sj->u.j, body_smem, local, h, stages, it, failed, policy, warp, lane);
+        scan_chunk<Body>(BodyArgs<Body>::of(*sj), body_smem, local, h, stages, it, failed, policy, warp, lane);
         __syncthreads();
     }
 }
@@ -252,17 +263,18 @@ struct tqp_batch {
     std::vector<FillRange> fill;
     std::vector<int64_t*> zero;
     std::vector<BuildJob> build;
-    std::vector<ScanJob> scan;
+    std::vector<ScanJob> scan[kKinds];
     std::vector<CompactJob> compact;
     std::vector<FinJob> fin;
     std::vector<TopJob> top;
     std::vector<std::vector<TopItem>> levels;
     // block -> job maps, concatenated
     std::vector<int32_t> maps;
-    long long fill_blocks = 0, row_blocks = 0, num_blocks = 0, slot_blocks = 0, scan_chunks = 0, compact_blocks = 0,
-              top0_blocks = 0;
+    long long fill_blocks = 0, row_blocks = 0, num_blocks = 0, slot_blocks = 0, compact_blocks = 0, top0_blocks = 0;
+    long long scan_chunks[kKinds] = {0, 0, 0};
     std::vector<long long> level_blocks;
-    size_t off_fill = 0, off_row = 0, off_num = 0, off_slot = 0, off_scan = 0, off_compact = 0, off_top0 = 0;
+    size_t off_fill = 0, off_row = 0, off_num = 0, off_slot = 0, off_compact = 0, off_top0 = 0;
+    size_t off_scan[kKinds] = {0, 0, 0};
     std::vector<size_t> off_level;
     // small zeroed counters share one slab (one fill range)
     unsigned char* slab = nullptr;
@@ -271,15 +283,15 @@ struct tqp_batch {
     FillRange* d_fill = nullptr;
     int64_t** d_zero = nullptr;
     BuildJob* d_build = nullptr;
-    ScanJob* d_scan = nullptr;
+    ScanJob* d_scan[kKinds] = {nullptr, nullptr, nullptr};
     CompactJob* d_compact = nullptr;
     FinJob* d_fin = nullptr;
     TopJob* d_top = nullptr;
     std::vector<TopItem*> d_levels;
     int32_t* d_maps = nullptr;
-    unsigned long long* d_ticket = nullptr;
-    size_t scan_smem = 0;
-    int scan_grid = 0;
+    unsigned long long* d_ticket[kKinds] = {nullptr, nullptr, nullptr};
+    size_t scan_smem[kKinds] = {0, 0, 0};
+    int scan_grid[kKinds] = {0, 0, 0};
     // plans run through the single-plan path, and their scratch
     std::vector<tqp_plan> fb_plans;
     std::vector<tqp_result> fb_res;
@@ -371,7 +383,7 @@ static tqp_status add_filter_job(tqp_batch* b, const tqp_plan* p, const tqp_resu
         if (A.d_sum) b->zero.push_back(A.d_sum);
         return TQP_OK;
     }
-    b->scan.push_back(J);
+    b->scan[kJobFilter - 1].push_back(J);
     return TQP_OK;
 }
 
@@ -418,6 +430,7 @@ static tqp_status add_group_job(tqp_batch* b, const tqp_plan* p, const tqp_resul
     for (int a = 1; a < A.S.nacc; ++a) expr_cols(A.S.acc_expr[a - 1], staged);
     TQP_TRY(batch_geom(ctx, t, staged, &A.G));
     lower_fast(A.cond, A.ncond, A.G, A.cf, &A.fast);
+    lower_group_fast(&A);
     const long long maxg = p->max_groups > 0 ? p->max_groups : std::max<long long>(1, r->capacity_groups);
     const long long cap = group_table_cap(maxg);
     A.S.cap = cap;
@@ -443,7 +456,7 @@ static tqp_status add_group_job(tqp_batch* b, const tqp_plan* p, const tqp_resul
         F.total_out = r->d_total_groups;
         b->fin.push_back(F);
     }
-    if (A.G.ntiles > 0) b->scan.push_back(J);
+    if (A.G.ntiles > 0) b->scan[kJobGroup - 1].push_back(J);
     return TQP_OK;
 }
 
@@ -553,7 +566,7 @@ static tqp_status add_join_job(tqp_batch* b, const tqp_plan* p, const tqp_result
     A.ctl.wait_cap = ctx->wait_cap;
     b->build.push_back(B);
     if (A.G.ntiles > 0) {
-        b->scan.push_back(J);
+        b->scan[kJobJoin - 1].push_back(J);
     } else {
         if (A.d_num_joined) b->zero.push_back(A.d_num_joined);
         if (A.d_sum) b->zero.push_back(A.d_sum);
@@ -605,12 +618,12 @@ static bool batchable(const tqp_plan* p, const tqp_result* r) {
 }
 
 static tqp_status lower_batch(tqp_batch* b, const tqp_plan* plans, const tqp_result* res, int32_t n) {
-    // per plan at most 4 counters (join + filter + top-k + spare) and the ticket
-    b->slab_bytes = static_cast<size_t>(kCounterBytes) * (4 * static_cast<size_t>(n) + 2);
+    // per plan at most 4 counters (join + filter + top-k + spare) and the tickets
+    b->slab_bytes = static_cast<size_t>(kCounterBytes) * (4 * static_cast<size_t>(n) + kKinds + 1);
     b->slab = static_cast<unsigned char*>(balloc(b, b->slab_bytes));
     if (!b->slab) return arena_oom(b->ctx, b->slab_bytes);
     add_fill(b, b->slab, b->slab_bytes, kZero16);
-    b->d_ticket = counter(b);
+    for (int k = 0; k < kKinds; ++k) b->d_ticket[k] = counter(b);
     for (int32_t i = 0; i < n; ++i) {
         const tqp_plan* p = &plans[i];
         const tqp_result* r = &res[i];
@@ -649,16 +662,16 @@ static int job_stage_bytes(const ScanJob& j) {
     return j.kind == kJobFilter ? j.u.f.G.stage_bytes : j.kind == kJobGroup ? j.u.g.G.stage_bytes : j.u.j.G.stage_bytes;
 }
 
-// Chunks of equal size across jobs (a job's last chunk may be short): about
-// four per persistent CTA, so that the uneven tails of the largest tables
-// still balance while each chunk amortises its pipeline fill.
-static void assign_chunks(tqp_batch* b) {
+// Chunks of equal size across the jobs of one kind (a job's last chunk may be
+// short): about four per persistent CTA, so that the uneven tails of the
+// largest tables still balance while each chunk amortises its pipeline fill.
+static void assign_chunks(tqp_batch* b, int k) {
     long long tiles = 0;
-    for (auto& j : b->scan) tiles += job_tiles(j);
-    const long long target = std::max<long long>(1, static_cast<long long>(b->scan_grid) * 4);
+    for (auto& j : b->scan[k]) tiles += job_tiles(j);
+    const long long target = std::max<long long>(1, static_cast<long long>(b->scan_grid[k]) * 4);
     const long long ct = std::max<long long>(8, (tiles + target - 1) / target);
     long long base = 0;
-    for (auto& j : b->scan) {
+    for (auto& j : b->scan[k]) {
         EngineCtl& ctl = job_ctl(j);
         ctl.chunk_tiles = ct;
         ctl.nchunks = (job_tiles(j) + ct - 1) / ct;
@@ -666,7 +679,7 @@ static void assign_chunks(tqp_batch* b) {
         j.chunk_base = base;
         base += ctl.nchunks;
     }
-    b->scan_chunks = base;
+    b->scan_chunks[k] = base;
 }
 
 // Top-k reduction levels: each level cuts every unfinished job's candidates
@@ -729,8 +742,10 @@ static void build_maps(tqp_batch* b) {
     b->off_slot = M.size();
     for (size_t j = 0; j < b->build.size(); ++j)
         if (b->build[j].grouped) push(j, (b->build[j].H.cap + 1 + kRowsPer - 1) / kRowsPer);
-    b->off_scan = M.size();
-    for (size_t j = 0; j < b->scan.size(); ++j) push(j, job_ctl(b->scan[j]).nchunks);
+    for (int k = 0; k < kKinds; ++k) {
+        b->off_scan[k] = M.size();
+        for (size_t j = 0; j < b->scan[k].size(); ++j) push(j, job_ctl(b->scan[k][j]).nchunks);
+    }
     b->off_compact = M.size();
     for (size_t j = 0; j < b->compact.size(); ++j) push(j, (b->compact[j].n + kCompactRows - 1) / kCompactRows);
     b->off_top0 = M.size();
@@ -789,9 +804,15 @@ static tqp_status batch_launch(tqp_batch* b, cudaStream_t st) {
         if (b->slot_blocks)
             k_b_direct<<<static_cast<unsigned>(b->slot_blocks), kFlatThreads, 0, st>>>(b->d_build, M + b->off_slot);
     }
-    if (b->scan_chunks)
-        k_b_scan<<<b->scan_grid, kEngineThreads, b->scan_smem, st>>>(b->d_scan, M + b->off_scan, b->d_ticket,
-                                                                     b->scan_chunks);
+    if (b->scan_chunks[0])
+        k_b_scan<FilterBody><<<b->scan_grid[0], kEngineThreads, b->scan_smem[0], st>>>(
+            b->d_scan[0], M + b->off_scan[0], b->d_ticket[0], b->scan_chunks[0]);
+    if (b->scan_chunks[1])
+        k_b_scan<GroupBody><<<b->scan_grid[1], kEngineThreads, b->scan_smem[1], st>>>(
+            b->d_scan[1], M + b->off_scan[1], b->d_ticket[1], b->scan_chunks[1]);
+    if (b->scan_chunks[2])
+        k_b_scan<PlanJoinBody><<<b->scan_grid[2], kEngineThreads, b->scan_smem[2], st>>>(
+            b->d_scan[2], M + b->off_scan[2], b->d_ticket[2], b->scan_chunks[2]);
     if (b->compact_blocks)
         k_b_compact<<<static_cast<unsigned>(b->compact_blocks), kCompactThreads, 0, st>>>(b->d_compact,
                                                                                            M + b->off_compact);
@@ -808,29 +829,40 @@ static tqp_status batch_launch(tqp_batch* b, cudaStream_t st) {
 }
 
 // Lower, lay out and upload every batched job (no launch).
+// Launch shape of the scan of one body kind: the largest stage of its jobs.
+template <class Body>
+static tqp_status scan_shape(tqp_batch* b, int k) {
+    static bool attr[kMaxDevices] = {};
+    tqp_ctx* ctx = b->ctx;
+    if (b->scan[k].empty()) return TQP_OK;
+    TQP_TRY(allow_smem(ctx, reinterpret_cast<const void*>(k_b_scan<Body>), attr));
+    int max_stage = 128;
+    for (auto& j : b->scan[k]) max_stage = std::max(max_stage, job_stage_bytes(j));
+    b->scan_smem[k] = kHeaderBytes + kJobBytes + body_bytes<Body>() + static_cast<size_t>(kBatchStages) * max_stage;
+    if (b->scan_smem[k] + 1024 > static_cast<size_t>(ctx->smem_optin))
+        return fail(TQP_ERR_UNSUPPORTED, "batched scan needs %zu bytes of shared memory", b->scan_smem[k]);
+    int occ = 0;
+    TQP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_b_scan<Body>, kEngineThreads, b->scan_smem[k]));
+    b->scan_grid[k] = ctx->num_sms * std::max(1, std::min(occ, 2));
+    assign_chunks(b, k);
+    return TQP_OK;
+}
+
+// Lower, lay out and upload every batched job (no launch).
 static tqp_status batch_prepare(tqp_ctx* ctx, const tqp_plan* plans, const tqp_result* res, int32_t n, tqp_batch* b,
                                 cudaStream_t st) {
-    static bool attr_scan[kMaxDevices] = {};
     static bool attr_fin[kMaxDevices] = {};
-    TQP_TRY(allow_smem(ctx, reinterpret_cast<const void*>(k_b_scan), attr_scan));
     TQP_TRY(allow_smem(ctx, reinterpret_cast<const void*>(k_b_finalize), attr_fin));
     TQP_TRY(lower_batch(b, plans, res, n));
-    int max_stage = 128;
-    for (auto& j : b->scan) max_stage = std::max(max_stage, job_stage_bytes(j));
-    b->scan_smem = kHeaderBytes + (sizeof(ScanJob) + 127) / 128 * 128 + kBodyMax +
-                   static_cast<size_t>(kBatchStages) * max_stage;
-    if (b->scan_smem + 1024 > static_cast<size_t>(ctx->smem_optin))
-        return fail(TQP_ERR_UNSUPPORTED, "batched scan needs %zu bytes of shared memory", b->scan_smem);
-    int occ = 0;
-    TQP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_b_scan, kEngineThreads, b->scan_smem));
-    b->scan_grid = ctx->num_sms * std::max(1, std::min(occ, 2));
-    assign_chunks(b);
+    TQP_TRY(scan_shape<FilterBody>(b, 0));
+    TQP_TRY(scan_shape<GroupBody>(b, 1));
+    TQP_TRY(scan_shape<PlanJoinBody>(b, 2));
     plan_top_levels(b);
     build_maps(b);
     TQP_TRY(upload(b, b->fill, &b->d_fill, st));
     TQP_TRY(upload(b, b->zero, &b->d_zero, st));
     TQP_TRY(upload(b, b->build, &b->d_build, st));
-    TQP_TRY(upload(b, b->scan, &b->d_scan, st));
+    for (int k = 0; k < kKinds; ++k) TQP_TRY(upload(b, b->scan[k], &b->d_scan[k], st));
     TQP_TRY(upload(b, b->compact, &b->d_compact, st));
     TQP_TRY(upload(b, b->fin, &b->d_fin, st));
     TQP_TRY(upload(b, b->top, &b->d_top, st));

@@ -48,6 +48,7 @@ struct FilterArgs {
 };
 
 struct FilterBody {
+    static constexpr int kMinBlocks = 2;
     // Per consumer warp: passing global row ids whose sum expression is still
     // to be evaluated (one step's <= 256 rows plus a partial round of < 32).
     static constexpr int kQueue = 8 * kWarp + kWarp;
@@ -165,7 +166,12 @@ struct FilterBody {
     __device__ void finish(const ScanGeom&, int, int) {}
 };
 
-// ---- group-by: shared-memory pre-aggregation into the global table ---------------
+// ---- group-by: warp pre-aggregation into the global table -------------------------
+
+constexpr int kWarpSlots = 32;   // groups of a warp's collective cache
+constexpr int kFastSums = 4;     // sum accumulators of the closed-form fast path
+constexpr int kLaneSlots = 8;    // groups of a warp's lane-private tables
+constexpr int kLaneAcc = 4;      // accumulators (count + sums) the lane-private tables hold
 
 struct GroupArgs {
     ScanGeom G;
@@ -175,101 +181,308 @@ struct GroupArgs {
     Cond cond[TQP_MAX_PREDS];
     CondFast cf[TQP_MAX_PREDS];
     GroupSpec S;
+    int32_t kfast;                          // full tiles: keys and sums straight from the stage
+    int32_t pad;
+    int32_t key_soff[TQP_MAX_GROUP_COLS];
+    int32_t key_type[TQP_MAX_GROUP_COLS];
+    ProdForm pf[kFastSums];                 // accumulator a + 1 in closed form
 };
 
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// Aggregation staged by locality (the paper reduces per group with a
+// scatter-add, Section 5.4):
+//   lane    while a warp has seen at most kLaneSlots distinct keys in the
+//           chunk and the plan has at most kLaneAcc accumulators, every lane
+//           adds its own rows into its own accumulators in shared memory,
+//           laid out [group][accumulator][lane] (no bank conflicts, no
+//           atomics, no warp collectives per row); group ids come from the
+//           warp's key list, held in registers.  At chunk end the 32 lane
+//           partials of each group are summed with shuffles and added to the
+//           global table, one atomic per accumulator.
+//   warp    otherwise lanes whose rows share a key are combined
+//           (__match_any_sync, exact 64-bit sums through the warp reduction
+//           unit) and the group's leader lane adds them to the warp's cache
+//           of kWarpSlots groups, flushed to the global table when full and
+//           at chunk end.  A warp whose key list overflows switches to this
+//           mode for the rest of the chunk.
 struct GroupBody {
-    static constexpr int kSmemBytes = kSmemSlots * 8 + kSmemSlots * kMaxAcc * 8;
+    static constexpr int kLaneBytes = kLaneSlots * kLaneAcc * kWarp * 8;
+    static constexpr int kCacheBytes = kWarpSlots * 8 + kWarpSlots * kMaxAcc * 8;  // aliases the lane area
+    static constexpr int kAreaBytes = kLaneBytes > kCacheBytes ? kLaneBytes : kCacheBytes;
+    static constexpr int kWarpBytes = kAreaBytes + kLaneSlots * 8 + 16;
+    static constexpr int kSmemBytes = kConsumerWarps * kWarpBytes;
+    static constexpr int kMinBlocks = 1;  // the lane tables leave room for one CTA per SM
 
     const GroupArgs& A;
-    unsigned long long* skeys;
-    unsigned long long* sacc;
+    unsigned long long* area;    // lane mode: [kLaneSlots][kLaneAcc][32]; warp mode: keys[32], acc[32][kMaxAcc]
+    unsigned long long* dkeys;   // lane mode: the warp's keys, in id order
+    uint32_t* wocc;              // warp mode: occupancy bits of the cache slots
+    uint64_t dk[kLaneSlots];     // lane mode: the warp's keys (the same in every lane)
+    int nused = 0;               // lane mode: keys in dk (warp-uniform)
+    int mode = 0;                // 0 lane, 1 warp (warp-uniform)
 
     __device__ GroupBody(const GroupArgs& a, unsigned char* sm) : A(a) {
-        skeys = reinterpret_cast<unsigned long long*>(sm);
-        sacc = skeys + kSmemSlots;
-        for (int i = threadIdx.x; i < kSmemSlots; i += blockDim.x) skeys[i] = kEmptyKey;
-        for (int i = threadIdx.x; i < kSmemSlots * kMaxAcc; i += blockDim.x) sacc[i] = 0;
+        const int w = threadIdx.x / kWarp;
+        const int ww = w < kConsumerWarps ? w : 0;
+        area = reinterpret_cast<unsigned long long*>(sm + ww * kWarpBytes);
+        dkeys = area + kAreaBytes / 8;
+        wocc = reinterpret_cast<uint32_t*>(dkeys + kLaneSlots);
+        uint4* z = reinterpret_cast<uint4*>(sm);
+        for (int i = threadIdx.x; i < kSmemBytes / 16; i += blockDim.x) z[i] = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+        for (int d = 0; d < kLaneSlots; ++d) dk[d] = 0;
+        mode = A.S.nacc <= kLaneAcc ? 0 : 1;
     }
 
-    __device__ __forceinline__ int smem_slot(uint64_t key) {
-        if (key == kEmptyKey) return -1;
-        unsigned h = static_cast<unsigned>(mix64(key)) & (kSmemSlots - 1);
-#pragma unroll 1
-        for (int p = 0; p < kSmemProbe; ++p) {
-            const unsigned long long k = *reinterpret_cast<volatile unsigned long long*>(&skeys[h]);
-            if (k == key) return static_cast<int>(h);
-            if (k == kEmptyKey) {
-                const unsigned long long prev = atomicCAS(&skeys[h], kEmptyKey, key);
-                if (prev == kEmptyKey || prev == key) return static_cast<int>(h);
+    // ---- lane mode ----
+
+    // Every group's lane partials into the global table; the tables are empty afterwards.
+    __device__ __forceinline__ void flush_lanes(int lane) {
+        __syncwarp();
+        const GroupSpec& S = A.S;
+        const long long gl = lane < nused ? gtab_slot(S, dkeys[lane], A.ctl.err) : -1;
+        for (int d = 0; d < nused; ++d) {
+            const long long g = __shfl_sync(0xffffffffu, gl, d);
+#pragma unroll
+            for (int a = 0; a < kLaneAcc; ++a) {
+                if (a < S.nacc) {
+                    unsigned long long* p = area + (d * kLaneAcc + a) * kWarp + lane;
+                    const unsigned long long x = warp_sum_u64(*p);
+                    *p = 0;
+                    if (lane == 0 && x && g >= 0) atomicAdd(&S.acc[g * S.nacc + a], x);
+                }
             }
-            h = (h + 1) & (kSmemSlots - 1);
         }
-        return -1;
+        nused = 0;
+        __syncwarp();
     }
 
-    // One row per lane (act: the row passed).  Lanes whose rows share a
-    // shared-memory slot are combined first (__match_any_sync), so each slot
-    // takes one atomic per accumulator per warp instead of one per row: with
-    // few groups (the Q1 shape) most of a warp's rows hit the same slots.
-    __device__ __forceinline__ void add_rows(const ScanGeom& G, const TileView& v, int r, bool act) {
+    // Rows of one lane each into the lane tables; false (nothing added) when
+    // the warp's key list overflows: the caller switches to warp mode.
+    __device__ __forceinline__ bool lane_add(bool act, uint64_t key, const int64_t (&val)[kFastSums], int lane) {
+        int id = -1;
+#pragma unroll
+        for (int d = 0; d < kLaneSlots; ++d)
+            if (d < nused && key == dk[d]) id = d;
+        bool miss = act && id < 0;
+        while (__any_sync(0xffffffffu, miss)) {
+            if (nused == kLaneSlots) return false;
+            const int src = __ffs(__ballot_sync(0xffffffffu, miss)) - 1;
+            const uint64_t k = __shfl_sync(0xffffffffu, key, src);
+#pragma unroll
+            for (int d = 0; d < kLaneSlots; ++d)
+                if (d == nused) dk[d] = k;
+            if (lane == 0) dkeys[nused] = k;
+            if (miss && key == k) {
+                id = nused;
+                miss = false;
+            }
+            ++nused;
+        }
+        if (act) {
+            unsigned long long* p = area + id * (kLaneAcc * kWarp) + lane;
+            p[0] += 1;
+#pragma unroll
+            for (int a = 0; a < kLaneAcc - 1; ++a)
+                if (a + 1 < A.S.nacc) p[(a + 1) * kWarp] += static_cast<unsigned long long>(val[a]);
+        }
+        return true;
+    }
+
+    // ---- warp mode ----
+
+    // Every cached group into the global table; the cache is empty (and the
+    // area all zero) afterwards.
+    __device__ __forceinline__ void flush_cache(int lane) {
+        __syncwarp();
+        const uint32_t occ = *reinterpret_cast<volatile uint32_t*>(wocc);
+        const GroupSpec& S = A.S;
+        unsigned long long* wkeys = area;
+        unsigned long long* wacc = area + kWarpSlots;
+        if ((occ >> lane) & 1u) {
+            const long long g = gtab_slot(S, wkeys[lane], A.ctl.err);
+            for (int a = 0; a < S.nacc; ++a) {
+                const unsigned long long x = wacc[lane * kMaxAcc + a];
+                if (x && g >= 0) atomicAdd(&S.acc[g * S.nacc + a], x);
+                wacc[lane * kMaxAcc + a] = 0;
+            }
+        }
+        wkeys[lane] = 0;
+        __syncwarp();
+        if (lane == 0) *wocc = 0;
+        __syncwarp();
+    }
+
+    // Warp-collective: the cache slot of each leader's key (claimed if new;
+    // the cache is flushed first if some leader finds no free slot).
+    __device__ __forceinline__ int slot_of(bool lead, uint64_t key, int lane) {
+        unsigned long long* wkeys = area;
+        const unsigned h0 = static_cast<unsigned>(mix64(key)) & (kWarpSlots - 1);
+        unsigned h = h0;
+        int s = -1, tries = 0;
+        while (true) {
+            const bool need = lead && s < 0;
+            if (!__any_sync(0xffffffffu, need)) break;
+            if (need) {
+                const uint32_t occ = *reinterpret_cast<volatile uint32_t*>(wocc);
+                if ((occ >> h) & 1u) {
+                    if (wkeys[h] == key) s = static_cast<int>(h);
+                } else if (!((atomicOr(wocc, 1u << h) >> h) & 1u)) {
+                    wkeys[h] = key;
+                    s = static_cast<int>(h);
+                }
+                if (s < 0) {
+                    h = (h + 1) & (kWarpSlots - 1);
+                    ++tries;
+                }
+            }
+            __syncwarp();
+            if (__any_sync(0xffffffffu, need && s < 0 && tries >= kWarpSlots)) {
+                flush_cache(lane);  // all leaders start over in an empty cache
+                s = -1;
+                tries = 0;
+                h = h0;
+            }
+        }
+        return s;
+    }
+
+    // Lanes with act set hold one row each (key, count 1, sums val[0..nsum)).
+    template <int NS>
+    __device__ __forceinline__ void warp_add(bool act, uint64_t key, const int64_t (&val)[NS], int nsum, int lane) {
+        const uint32_t actm = __ballot_sync(0xffffffffu, act);
+        if (!actm) return;
+        const uint32_t peers = __match_any_sync(0xffffffffu, key) & actm;
+        const bool lead = act && lane == __ffs(peers) - 1;
+        const int s = slot_of(lead, key, lane);
+        if (!act) return;
+        unsigned long long* a = area + kWarpSlots + (s < 0 ? 0 : s) * kMaxAcc;
+        if (lead) a[0] += __popc(peers);
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+            if (i < nsum) {
+                const long long x = group_sum_i64(peers, val[i]);
+                if (lead) a[i + 1] += static_cast<unsigned long long>(x);
+            }
+        }
+    }
+
+    // One row per lane (act: the row passed) in the warp's current mode.
+    template <int NS>
+    __device__ __forceinline__ void add(bool act, uint64_t key, const int64_t (&val)[NS], int lane) {
+        const int nsum = A.S.nacc - 1;
+        if (mode == 0) {
+            int64_t v4[kFastSums];
+#pragma unroll
+            for (int i = 0; i < kFastSums; ++i) v4[i] = i < NS ? val[i < NS ? i : 0] : 0;
+            if (lane_add(act, key, v4, lane)) return;
+            flush_lanes(lane);  // key list full: warp mode for the rest of the chunk
+            mode = 1;
+        }
+        warp_add<NS>(act, key, val, nsum, lane);
+    }
+
+    // Full tile, closed-form sums: U rows per lane with hoisted type dispatch.
+    template <int U>
+    __device__ __forceinline__ void step_fast(const TileView& v, int rbase, int lane) {
+        const GroupSpec& S = A.S;
+        const int r0 = rbase + lane;
+        const uint32_t ok = conds_full<U>(v.stage, A.cf, A.ncond, r0);
+        if (!__any_sync(0xffffffffu, ok)) return;
+        uint64_t key[U];
+#pragma unroll
+        for (int j = 0; j < U; ++j) key[j] = 0;
+#pragma unroll
+        for (int i = 0; i < TQP_MAX_GROUP_COLS; ++i) {
+            if (i >= S.ngc) break;
+            int64_t x[U];
+            const int t = A.key_type[i];
+            load_rows<U>(v.stage + A.key_soff[i], t, r0, x);
+            if (t == TQP_U8) {
+#pragma unroll
+                for (int j = 0; j < U; ++j) key[j] = (key[j] << 8) | (static_cast<uint64_t>(x[j]) & 0xFFu);
+            } else if (t == TQP_I32) {
+#pragma unroll
+                for (int j = 0; j < U; ++j)
+                    key[j] = (key[j] << 32) | static_cast<uint64_t>(static_cast<uint32_t>(x[j]) ^ 0x80000000u);
+            } else {
+#pragma unroll
+                for (int j = 0; j < U; ++j) key[j] = static_cast<uint64_t>(x[j]) ^ 0x8000000000000000ull;
+            }
+        }
+        const int nsum = S.nacc - 1;
+        int64_t val[kFastSums][U];
+#pragma unroll
+        for (int a = 0; a < kFastSums; ++a) {
+            if (a < nsum) {
+                prod_eval<U>(A.pf[a], v.stage, r0, val[a]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < U; ++j) val[a][j] = 0;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            int64_t vj[kFastSums];
+#pragma unroll
+            for (int a = 0; a < kFastSums; ++a) vj[a] = val[a][j];
+            add<kFastSums>((ok >> j) & 1u, key[j], vj, lane);
+        }
+    }
+
+    // Any tile and expression: one row per lane, interpreted.
+    __device__ __forceinline__ void step_general(const ScanGeom& G, const TileView& v, int r, bool act, int lane) {
         const GroupSpec& S = A.S;
         uint64_t key = 0;
-        int s = -2;  // -2: no row, -1: not in the shared table
+        int64_t vals[kMaxAcc - 1];
+#pragma unroll
+        for (int i = 0; i < kMaxAcc - 1; ++i) vals[i] = 0;
         if (act) {
             key = pack_key(S, G, v, r);
-            s = smem_slot(key);
+#pragma unroll
+            for (int i = 0; i < kMaxAcc - 1; ++i)
+                if (i < S.nacc - 1) vals[i] = eval_expr(G, v, S.acc_expr[i], r);
         }
-        const uint32_t peers = __match_any_sync(0xffffffffu, s);
-        if (s >= 0) {
-            const bool leader = (threadIdx.x % kWarp) == static_cast<unsigned>(__ffs(peers) - 1);
-            unsigned long long* a = sacc + s * kMaxAcc;
-            if (leader) atomicAdd(&a[0], static_cast<unsigned long long>(__popc(peers)));
-            for (int i = 1; i < S.nacc; ++i) {
-                const long long x = group_sum_i64(peers, eval_expr(G, v, S.acc_expr[i - 1], r));
-                if (leader && x) atomicAdd(&a[i], static_cast<unsigned long long>(x));
-            }
-        } else if (s == -1) {
-            const long long g = gtab_slot(S, key, A.ctl.err);
-            if (g < 0) return;
-            unsigned long long* a = S.acc + g * S.nacc;
-            atomicAdd(&a[0], 1ULL);
-            for (int i = 1; i < S.nacc; ++i)
-                atomicAdd(&a[i], static_cast<unsigned long long>(eval_expr(G, v, S.acc_expr[i - 1], r)));
-        }
+        add<kMaxAcc - 1>(act, key, vals, lane);
     }
 
     __device__ void pass1(const ScanGeom& G, const TileView& v, int cw, int lane) {
         const int rw = G.T / kConsumerWarps;  // a multiple of 128
+        if (A.kfast && A.fast && v.full) {
+            for (int r = 0; r < rw; r += kUnroll * kWarp) step_fast<kUnroll>(v, cw * rw + r, lane);
+            return;
+        }
         for (int r = 0; r < rw; r += kUnroll * kWarp) {
             const int rbase = cw * rw + r;
             if (rbase >= v.rows) break;
             const uint32_t ok = eval_rows<kUnroll>(G, v, A.cf, A.cond, A.ncond, A.fast != 0, rbase + lane);
 #pragma unroll
             for (int j = 0; j < kUnroll; ++j)
-                if (__any_sync(0xffffffffu, (ok >> j) & 1u)) add_rows(G, v, rbase + kWarp * j + lane, (ok >> j) & 1u);
+                if (__any_sync(0xffffffffu, (ok >> j) & 1u))
+                    step_general(G, v, rbase + kWarp * j + lane, (ok >> j) & 1u, lane);
         }
     }
 
-    // Flush the shared table into the global one and clear it for the next chunk.
-    __device__ void chunk_end(const ScanGeom&, long long, long long, long long, int cw, int lane) {
-        named_sync(kBarConsumers, kConsumers);
-        const GroupSpec& S = A.S;
-        for (int i = cw * kWarp + lane; i < kSmemSlots; i += kConsumers) {
-            const unsigned long long key = skeys[i];
-            if (key == kEmptyKey) continue;
-            const long long g = gtab_slot(S, key, A.ctl.err);
-            for (int a = 0; a < S.nacc; ++a) {
-                const unsigned long long x = sacc[i * kMaxAcc + a];
-                if (x && g >= 0) atomicAdd(&S.acc[g * S.nacc + a], x);
-                sacc[i * kMaxAcc + a] = 0;
-            }
-            skeys[i] = kEmptyKey;
+    __device__ void chunk_end(const ScanGeom&, long long, long long, long long, int, int lane) {
+        if (mode == 0) {
+            flush_lanes(lane);
+        } else {
+            flush_cache(lane);
+            mode = A.S.nacc <= kLaneAcc ? 0 : 1;
         }
-        named_sync(kBarConsumers, kConsumers);
     }
 
     __device__ void finish(const ScanGeom&, int, int) {}
 };
+
+// Host: fill the fast-path fields of A from its geometry (kfast = 0 when the
+// keys or sums are not all staged, or the sums are not in closed form).
+void lower_group_fast(GroupArgs* A);
 
 // ---- joined plan: filter + probe + aggregate into dense group accumulators --------
 
@@ -294,6 +507,7 @@ struct PlanJoinArgs {
 };
 
 struct PlanJoinBody {
+    static constexpr int kMinBlocks = 2;
     static constexpr int kSmemBytes = 0;
     const PlanJoinArgs& A;
     unsigned long long joined = 0, passed = 0;

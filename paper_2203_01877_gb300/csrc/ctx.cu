@@ -210,6 +210,85 @@ tqp_status lower_expr(const tqp_expr* e, int ncols, DExpr* out) {
     return TQP_OK;
 }
 
+// Symbolic evaluation of the postfix program over affine terms a * x + b
+// (x one column, or none for a constant), mod 2^64.
+namespace {
+struct Aff {
+    int col;  // -1: constant b
+    uint64_t a, b;
+};
+struct Sym {
+    int nf;   // 1: affine f[0]; 2: product f[0] * f[1]
+    Aff f[2];
+};
+bool is_const(const Sym& s) { return s.nf == 1 && s.f[0].col < 0; }
+Aff scale(Aff t, uint64_t k) {
+    t.a *= k;
+    t.b *= k;
+    return t;
+}
+}  // namespace
+
+bool lower_prod(const DExpr& e, const ScanGeom& G, ProdForm* out) {
+    Sym st[TQP_MAX_EXPR];
+    int sp = 0;
+    for (int i = 0; i < e.n; ++i) {
+        const int op = e.op[i];
+        if (op == TQP_X_COL || op == TQP_X_CONST) {
+            Sym s;
+            s.nf = 1;
+            s.f[0] = op == TQP_X_COL ? Aff{static_cast<int>(e.v[i]), 1u, 0u}
+                                     : Aff{-1, 0u, static_cast<uint64_t>(e.v[i])};
+            st[sp++] = s;
+            continue;
+        }
+        if (sp < 2) return false;
+        const Sym y = st[--sp];
+        const Sym x = st[--sp];
+        Sym r;
+        if (op == TQP_X_ADD || op == TQP_X_SUB) {
+            if (x.nf != 1 || y.nf != 1) return false;
+            if (x.f[0].col >= 0 && y.f[0].col >= 0 && x.f[0].col != y.f[0].col) return false;
+            const uint64_t sg = op == TQP_X_ADD ? 1u : ~0ull;  // +1 or -1 mod 2^64
+            r.nf = 1;
+            r.f[0].col = x.f[0].col >= 0 ? x.f[0].col : y.f[0].col;
+            r.f[0].a = x.f[0].a + sg * y.f[0].a;
+            r.f[0].b = x.f[0].b + sg * y.f[0].b;
+        } else {  // MUL
+            if (is_const(y)) {
+                r = x;
+                r.f[0] = scale(x.f[0], y.f[0].b);
+            } else if (is_const(x)) {
+                r = y;
+                r.f[0] = scale(y.f[0], x.f[0].b);
+            } else if (x.nf == 1 && y.nf == 1) {
+                r.nf = 2;
+                r.f[0] = x.f[0];
+                r.f[1] = y.f[0];
+            } else {
+                return false;
+            }
+        }
+        st[sp++] = r;
+    }
+    if (sp != 1) return false;
+    const Sym& s = st[0];
+    for (int k = 0; k < 2; ++k) {
+        const Aff t = k < s.nf ? s.f[k] : Aff{-1, 0u, 1u};
+        if (t.col >= 0) {
+            if (t.col >= G.ncols || G.col[t.col].slot < 0) return false;
+            out->soff[k] = G.col[t.col].soff;
+            out->type[k] = G.col[t.col].type;
+        } else {
+            out->soff[k] = 0;
+            out->type[k] = -1;
+        }
+        out->a[k] = static_cast<int64_t>(t.a);
+        out->b[k] = static_cast<int64_t>(t.b);
+    }
+    return true;
+}
+
 void expr_cols(const DExpr& e, std::vector<int>& cols) {
     for (int i = 0; i < e.n; ++i)
         if (e.op[i] == TQP_X_COL) cols.push_back(static_cast<int>(e.v[i]));

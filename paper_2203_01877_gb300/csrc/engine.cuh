@@ -84,6 +84,60 @@ struct CondFast {
     uint64_t span;
 };
 
+// An expression in closed form over staged columns: the product of two affine
+// factors (a_i * x_i + b_i), evaluated mod 2^64 like the postfix program it
+// came from (ring arithmetic, so the rewrite is exact).  A factor with
+// type < 0 is the constant b_i.  Covers x, x * k, x + k, x * y and
+// x * (k - y), the shapes of the paper's aggregates (Section 5.4).
+struct ProdForm {
+    int32_t soff[2];
+    int32_t type[2];
+    int64_t a[2];
+    int64_t b[2];
+};
+
+// x[j] = column value of tile row r0 + 32 j (the column is staged at `col`).
+template <int U>
+__device__ __forceinline__ void load_rows(const unsigned char* col, int type, int r0, int64_t (&x)[U]) {
+    if (type == TQP_I64) {
+#pragma unroll
+        for (int j = 0; j < U; ++j) x[j] = reinterpret_cast<const int64_t*>(col)[r0 + 32 * j];
+    } else if (type == TQP_I32) {
+#pragma unroll
+        for (int j = 0; j < U; ++j) x[j] = reinterpret_cast<const int32_t*>(col)[r0 + 32 * j];
+    } else {
+#pragma unroll
+        for (int j = 0; j < U; ++j) x[j] = col[r0 + 32 * j];
+    }
+}
+
+template <int U>
+__device__ __forceinline__ void prod_eval(const ProdForm& f, const unsigned char* stage, int r0, int64_t (&out)[U]) {
+    int64_t x[U];
+    if (f.type[0] >= 0) {
+        load_rows<U>(stage + f.soff[0], f.type[0], r0, x);
+#pragma unroll
+        for (int j = 0; j < U; ++j)
+            out[j] = static_cast<int64_t>(static_cast<uint64_t>(x[j]) * static_cast<uint64_t>(f.a[0]) +
+                                          static_cast<uint64_t>(f.b[0]));
+    } else {
+#pragma unroll
+        for (int j = 0; j < U; ++j) out[j] = f.b[0];
+    }
+    if (f.type[1] >= 0) {
+        load_rows<U>(stage + f.soff[1], f.type[1], r0, x);
+#pragma unroll
+        for (int j = 0; j < U; ++j)
+            out[j] = static_cast<int64_t>(static_cast<uint64_t>(out[j]) *
+                                          (static_cast<uint64_t>(x[j]) * static_cast<uint64_t>(f.a[1]) +
+                                           static_cast<uint64_t>(f.b[1])));
+    } else if (f.b[1] != 1) {
+#pragma unroll
+        for (int j = 0; j < U; ++j)
+            out[j] = static_cast<int64_t>(static_cast<uint64_t>(out[j]) * static_cast<uint64_t>(f.b[1]));
+    }
+}
+
 struct TileView {
     const unsigned char* stage;  // shared-memory stage base
     int64_t tile;
@@ -338,11 +392,29 @@ __device__ __forceinline__ void init_stage_ring(EngineHeader* h, int nstages) {
     }
 }
 
+// Kernel arguments copied into shared memory (after the engine header): the
+// hot loops then read them with shared-memory loads instead of dynamically
+// indexed constant-bank or generic parameter loads.
+template <class Args>
+constexpr int args_bytes() { return (static_cast<int>(sizeof(Args)) + 127) / 128 * 128; }
+
+template <class Args>
+__device__ __forceinline__ const Args& stage_args(const Args& p, unsigned char* dst) {
+    static_assert(sizeof(Args) % 4 == 0, "argument blocks are copied in 4-byte words");
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(&p);
+    uint32_t* d = reinterpret_cast<uint32_t*>(dst);
+    for (int i = threadIdx.x; i < static_cast<int>(sizeof(Args) / 4); i += blockDim.x) d[i] = src[i];
+    __syncthreads();
+    return *reinterpret_cast<const Args*>(dst);
+}
+
+// Dynamic shared memory: header | `extra` bytes (the staged arguments) |
+// Body::kSmemBytes | stages.
 template <class Body>
 __device__ __forceinline__ void run_engine(const ScanGeom& G, const EngineCtl& ctl, Body& body,
-                                           unsigned char* smem) {
+                                           unsigned char* smem, int extra = 0) {
     EngineHeader* h = reinterpret_cast<EngineHeader*>(smem);
-    unsigned char* stages = smem + kHeaderBytes + Body::kSmemBytes;
+    unsigned char* stages = smem + kHeaderBytes + extra + Body::kSmemBytes;
     const int warp = threadIdx.x / kWarp;
     const int lane = threadIdx.x % kWarp;
     init_stage_ring(h, G.nstages);

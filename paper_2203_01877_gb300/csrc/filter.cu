@@ -48,10 +48,11 @@ static FilterScratch filter_scratch_layout(const ScanGeom& G, bool ids) {
 }
 
 
-__global__ void __launch_bounds__(kEngineThreads, 2) k_filter(const __grid_constant__ FilterArgs A) {
+__global__ void __launch_bounds__(kEngineThreads, 2) k_filter(const __grid_constant__ FilterArgs P) {
     extern __shared__ __align__(128) unsigned char smem[];
-    FilterBody body(A, smem + kHeaderBytes);
-    run_engine(A.G, A.ctl, body, smem);
+    const FilterArgs& A = stage_args(P, smem + kHeaderBytes);
+    FilterBody body(A, smem + kHeaderBytes + args_bytes<FilterArgs>());
+    run_engine(A.G, A.ctl, body, smem, args_bytes<FilterArgs>());
 }
 
 __global__ void __launch_bounds__(kCompactThreads) k_compact(const uint32_t* __restrict__ mask,
@@ -80,8 +81,8 @@ static tqp_status plan_filter(const tqp_ctx* ctx, const tqp_table* t, const tqp_
     u.erase(std::unique(u.begin(), u.end()), u.end());
     int bpr = 0;
     for (int c : u) bpr += t->cols[c].type == TQP_I64 ? 8 : (t->cols[c].type == TQP_I32 ? 4 : 1);
-    const tqp_tuning tu = force ? *force : default_tuning(ctx, bpr, FilterBody::kSmemBytes);
-    TQP_TRY(make_geom(ctx, t, staged, tu, FilterBody::kSmemBytes, &A->G, smem));
+    const tqp_tuning tu = force ? *force : default_tuning(ctx, bpr, FilterBody::kSmemBytes + args_bytes<FilterArgs>());
+    TQP_TRY(make_geom(ctx, t, staged, tu, FilterBody::kSmemBytes + args_bytes<FilterArgs>(), &A->G, smem));
     lower_fast(A->cond, A->ncond, A->G, A->cf, &A->fast);
     static bool attr_done[kMaxDevices] = {};
     TQP_TRY(allow_smem(ctx, reinterpret_cast<const void*>(k_filter), attr_done));

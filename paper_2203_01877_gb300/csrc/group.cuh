@@ -9,8 +9,6 @@ namespace tqp {
 
 constexpr unsigned long long kEmptyKey = ~0ULL;
 constexpr int kMaxAcc = 1 + TQP_MAX_AGGS;  // count + one sum per distinct expression
-constexpr int kSmemSlots = 256;
-constexpr int kSmemProbe = 8;
 constexpr int kSmallCap = 4096;            // finalize in one CTA up to this many table slots
 constexpr int kFinThreads = 1024;
 

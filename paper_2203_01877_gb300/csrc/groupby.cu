@@ -31,10 +31,11 @@ size_t radix_sort_scratch(long long n_max);
 
 
 
-__global__ void __launch_bounds__(kEngineThreads, 2) k_groupby(const __grid_constant__ GroupArgs A) {
+__global__ void __launch_bounds__(kEngineThreads, GroupBody::kMinBlocks) k_groupby(const __grid_constant__ GroupArgs P) {
     extern __shared__ __align__(128) unsigned char smem[];
-    GroupBody body(A, smem + kHeaderBytes);
-    run_engine(A.G, A.ctl, body, smem);
+    const GroupArgs& A = stage_args(P, smem + kHeaderBytes);
+    GroupBody body(A, smem + kHeaderBytes + args_bytes<GroupArgs>());
+    run_engine(A.G, A.ctl, body, smem, args_bytes<GroupArgs>());
 }
 
 // ---- finalize ----------------------------------------------------------------
@@ -244,6 +245,23 @@ tqp_status group_topk(tqp_ctx* ctx, const GroupSpec& S, const GroupOut& O, int k
     return TQP_OK;
 }
 
+void lower_group_fast(GroupArgs* A) {
+    A->kfast = 0;
+    const GroupSpec& S = A->S;
+    if (S.nacc - 1 > kFastSums) return;
+    for (int i = 0; i < S.ngc; ++i) {
+        const int c = S.key_col[i];
+        if (c < 0 || c >= A->G.ncols || A->G.col[c].slot < 0) return;
+        const int t = A->G.col[c].type;
+        if (S.key_bits[i] != (t == TQP_U8 ? 8 : (t == TQP_I32 ? 32 : 64))) return;
+        A->key_soff[i] = A->G.col[c].soff;
+        A->key_type[i] = t;
+    }
+    for (int a = 0; a + 1 < S.nacc; ++a)
+        if (!lower_prod(S.acc_expr[a], A->G, &A->pf[a])) return;
+    A->kfast = 1;
+}
+
 tqp_status launch_groupby(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* preds, int32_t npreds,
                           const int32_t* group_cols, int32_t ngc, const tqp_agg* aggs, int32_t naggs,
                           int64_t* d_keys, int64_t* d_ivals, double* d_fvals, int64_t capacity_groups,
@@ -277,10 +295,11 @@ tqp_status launch_groupby(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* pred
     if (static_cast<int>(u.size()) > kMaxStaged) u.resize(kMaxStaged);
     int bpr = 0;
     for (int c : u) bpr += t->cols[c].type == TQP_I64 ? 8 : (t->cols[c].type == TQP_I32 ? 4 : 1);
-    const tqp_tuning tu = default_tuning(ctx, bpr, GroupBody::kSmemBytes);
+    const tqp_tuning tu = default_tuning(ctx, bpr, GroupBody::kSmemBytes + args_bytes<GroupArgs>());
     size_t smem = 0;
-    TQP_TRY(make_geom(ctx, t, u, tu, GroupBody::kSmemBytes, &A.G, &smem));
+    TQP_TRY(make_geom(ctx, t, u, tu, GroupBody::kSmemBytes + args_bytes<GroupArgs>(), &A.G, &smem));
     lower_fast(A.cond, A.ncond, A.G, A.cf, &A.fast);
+    lower_group_fast(&A);
 
     const long long cap = group_table_cap(max_groups);
     void* tab = arena_alloc(ctx, group_table_bytes(cap, A.S.nacc));

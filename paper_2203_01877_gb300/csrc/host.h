@@ -86,6 +86,10 @@ void lower_fast(const Cond* conds, int ncond, const ScanGeom& G, CondFast* out, 
 
 // Lower a postfix expression whose column operands address `ncols` columns.
 tqp_status lower_expr(const tqp_expr* e, int ncols, DExpr* out);
+// Closed form of an expression whose columns are staged in G (see ProdForm);
+// false when it is not a product of two affine factors or reads an unstaged
+// column (the interpreter handles it then).
+bool lower_prod(const DExpr& e, const ScanGeom& G, ProdForm* out);
 // Column ids referenced by an expression.
 void expr_cols(const DExpr& e, std::vector<int>& cols);
 

@@ -248,10 +248,11 @@ struct ProbeBody {
     }
 };
 
-__global__ void __launch_bounds__(kEngineThreads, 2) k_join_probe(const __grid_constant__ ProbeArgs A) {
+__global__ void __launch_bounds__(kEngineThreads, 2) k_join_probe(const __grid_constant__ ProbeArgs P) {
     extern __shared__ __align__(128) unsigned char smem[];
-    ProbeBody body(A, smem + kHeaderBytes);
-    run_engine(A.G, A.ctl, body, smem);
+    const ProbeArgs& A = stage_args(P, smem + kHeaderBytes);
+    ProbeBody body(A, smem + kHeaderBytes + args_bytes<ProbeArgs>());
+    run_engine(A.G, A.ctl, body, smem, args_bytes<ProbeArgs>());
 }
 
 tqp_status launch_hash_join(tqp_ctx* ctx, const tqp_table* build, int32_t build_key, const tqp_table* probe,
@@ -268,9 +269,9 @@ tqp_status launch_hash_join(tqp_ctx* ctx, const tqp_table* build, int32_t build_
     A.H = H;
     A.key_col = probe_key;
     const int es = probe->cols[probe_key].type == TQP_I64 ? 8 : (probe->cols[probe_key].type == TQP_I32 ? 4 : 1);
-    const tqp_tuning tu = default_tuning(ctx, es, ProbeBody::kSmemBytes);
+    const tqp_tuning tu = default_tuning(ctx, es, ProbeBody::kSmemBytes + args_bytes<ProbeArgs>());
     size_t smem = 0;
-    TQP_TRY(make_geom(ctx, probe, std::vector<int>{probe_key}, tu, ProbeBody::kSmemBytes, &A.G, &smem));
+    TQP_TRY(make_geom(ctx, probe, std::vector<int>{probe_key}, tu, ProbeBody::kSmemBytes + args_bytes<ProbeArgs>(), &A.G, &smem));
     static bool attr_done[kMaxDevices] = {};
     TQP_TRY(allow_smem(ctx, reinterpret_cast<const void*>(k_join_probe), attr_done));
     const int g = engine_grid(ctx, reinterpret_cast<const void*>(k_join_probe), smem, A.G.ntiles, tu.ctas_per_sm);

@@ -65,10 +65,11 @@ __global__ void k_dim_remap(const uint32_t* dslot, const uint32_t* slot2dense, l
         dgs[d] = slot2dense[dslot[d]];
 }
 
-__global__ void __launch_bounds__(kEngineThreads, 2) k_plan_join(const __grid_constant__ PlanJoinArgs A) {
+__global__ void __launch_bounds__(kEngineThreads, 2) k_plan_join(const __grid_constant__ PlanJoinArgs P) {
     extern __shared__ __align__(128) unsigned char smem[];
-    PlanJoinBody body(A, smem + kHeaderBytes);
-    run_engine(A.G, A.ctl, body, smem);
+    const PlanJoinArgs& A = stage_args(P, smem + kHeaderBytes);
+    PlanJoinBody body(A, smem + kHeaderBytes + args_bytes<PlanJoinArgs>());
+    run_engine(A.G, A.ctl, body, smem, args_bytes<PlanJoinArgs>());
 }
 
 static bool expr_uses_only(const tqp_expr& e, int lo, int hi) {
@@ -190,9 +191,9 @@ static tqp_status run_join_plan(tqp_ctx* ctx, const tqp_plan* p, const tqp_resul
     if (static_cast<int>(staged.size()) > kMaxStaged) staged.resize(kMaxStaged);
     int bpr = 0;
     for (int c : staged) bpr += F->cols[c].type == TQP_I64 ? 8 : (F->cols[c].type == TQP_I32 ? 4 : 1);
-    const tqp_tuning tu = default_tuning(ctx, bpr, PlanJoinBody::kSmemBytes);
+    const tqp_tuning tu = default_tuning(ctx, bpr, PlanJoinBody::kSmemBytes + args_bytes<PlanJoinArgs>());
     size_t smem = 0;
-    TQP_TRY(make_geom(ctx, F, staged, tu, PlanJoinBody::kSmemBytes, &A.G, &smem));
+    TQP_TRY(make_geom(ctx, F, staged, tu, PlanJoinBody::kSmemBytes + args_bytes<PlanJoinArgs>(), &A.G, &smem));
     lower_fast(A.cond, A.ncond, A.G, A.cf, &A.fast);
 
     unsigned long long* sc = static_cast<unsigned long long*>(arena_alloc(ctx, 8 * 8));

@@ -7,6 +7,7 @@
 // (a host-built map gives every block its job), so the number of launches
 // does not grow with the number of plans:
 //   fill      clear every job's scratch (tables, counters)
+//   range     build-key [min, max] of every join (direct-mapped tables)
 //   build     chained hash tables + dimension group claims of all joins
 //   number    dense group ids (claim-table ranges)
 //   remap     dimension row -> dense group id
@@ -126,6 +127,13 @@ __global__ void __launch_bounds__(kFlatThreads) k_b_fill(const FillRange* R, con
     for (long long u = u0 + threadIdx.x; u < u1; u += kFlatThreads) r.ptr[u] = r.pattern;
     if (blockIdx.x == 0)
         for (int i = threadIdx.x; i < nzero; i += kFlatThreads) *zero[i] = 0;
+}
+
+__global__ void __launch_bounds__(kFlatThreads) k_b_range(const BuildJob* B, const int32_t* bjob) {
+    const BuildJob& b = B[bjob[blockIdx.x]];
+    const long long i0 = (static_cast<long long>(blockIdx.x) - b.row_block) * kRowsPer;
+    const long long i1 = (i0 + kRowsPer < b.nrows) ? i0 + kRowsPer : b.nrows;
+    ht_key_range(b.H, b.key_col, b.key_type, i0 + threadIdx.x, i1, kFlatThreads);
 }
 
 __global__ void __launch_bounds__(kFlatThreads) k_b_build(const BuildJob* B, const int32_t* bjob, int* err) {
@@ -475,6 +483,10 @@ static tqp_status add_join_job(tqp_batch* b, const tqp_plan* p, const tqp_result
     B.next = static_cast<uint32_t*>(balloc(b, nd_rows * 4));
     if (!B.H.slots || !B.next) return arena_oom(ctx, static_cast<size_t>(B.H.cap + 1) * 16 + nd_rows * 4);
     add_fill(b, B.H.slots, static_cast<size_t>(B.H.cap + 1) * 16, uint4{~0u, ~0u, kNoRow, 0u});
+    long long* meta = static_cast<long long*>(balloc(b, 16));
+    if (!meta) return arena_oom(ctx, 16);
+    add_fill(b, meta, 16, uint4{~0u, 0x7FFFFFFFu, 0u, 0x80000000u});  // min = INT64_MAX, max = INT64_MIN
+    B.H.meta = meta;
     B.key_col = static_cast<const unsigned char*>(D->cols[p->dim_key].data);
     B.key_type = D->cols[p->dim_key].type;
     B.nrows = ndr;
@@ -558,6 +570,7 @@ static tqp_status add_join_job(tqp_batch* b, const tqp_plan* p, const tqp_result
     for (int a = 1; a < A.S.nacc; ++a) expr_cols(A.S.acc_expr[a - 1], staged);
     TQP_TRY(batch_geom(ctx, F, staged, &A.G));
     lower_fast(A.cond, A.ncond, A.G, A.cf, &A.fast);
+    lower_join_fast(&A);
     A.acc = counter(b);
     A.d_num_joined = r->d_num_joined;
     A.d_sum = p->has_sum ? r->d_sum : nullptr;
@@ -795,6 +808,8 @@ static tqp_status batch_launch(tqp_batch* b, cudaStream_t st) {
     if (b->fill_blocks)
         k_b_fill<<<static_cast<unsigned>(b->fill_blocks), kFlatThreads, 0, st>>>(b->d_fill, M + b->off_fill, b->d_zero,
                                                                                  static_cast<int>(b->zero.size()));
+    if (b->row_blocks)
+        k_b_range<<<static_cast<unsigned>(b->row_blocks), kFlatThreads, 0, st>>>(b->d_build, M + b->off_row);
     if (b->row_blocks)
         k_b_build<<<static_cast<unsigned>(b->row_blocks), kFlatThreads, 0, st>>>(b->d_build, M + b->off_row, ctx->d_err);
     if (b->num_blocks) {

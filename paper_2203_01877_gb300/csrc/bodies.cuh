@@ -504,46 +504,151 @@ struct PlanJoinArgs {
     int64_t* d_num_joined;
     int64_t* d_sum;
     int64_t* d_num_rows;
+    // full-tile fast path: foreign key and sums read straight from the stage
+    int32_t pjfast;
+    int32_t fk_soff;
+    int32_t fk_type;
+    int32_t nsum;              // accumulators after the count (S.nacc - 1)
+    ProdForm psum;             // the ungrouped sum
+    ProdForm pacc[kFastSums];  // accumulator a + 1
 };
 
 struct PlanJoinBody {
     static constexpr int kMinBlocks = 2;
     static constexpr int kSmemBytes = 0;
+    static constexpr int kU = kUnroll;  // probes in flight per lane
     const PlanJoinArgs& A;
     unsigned long long joined = 0, passed = 0;
     long long sum = 0;
 
     __device__ PlanJoinBody(const PlanJoinArgs& a, unsigned char*) : A(a) {}
 
-    // Aggregate one joined fact row r into its slot's group(s).
+    // Add one joined row (count `cnt` matches, sums x[]) to the group(s) of its slot.
+    __device__ __forceinline__ void add_groups(const uint4& sl, const int64_t (&x)[kFastSums], int nsum) {
+        const GroupSpec& S = A.S;
+        if (sl.z & kDirectGroup) {  // a unique key whose dense group id sits in the slot
+            unsigned long long* a = S.acc + static_cast<long long>(sl.z & ~kDirectGroup) * S.nacc;
+            atomicAdd(&a[0], 1ULL);
+#pragma unroll
+            for (int i = 0; i < kFastSums; ++i)
+                if (i < nsum) atomicAdd(&a[i + 1], static_cast<unsigned long long>(x[i]));
+            return;
+        }
+        uint32_t d = sl.z;
+        for (uint32_t k = 0; k < sl.w; ++k) {
+            unsigned long long* a = S.acc + static_cast<long long>(__ldg(&A.dgs[d])) * S.nacc;
+            atomicAdd(&a[0], 1ULL);
+#pragma unroll
+            for (int i = 0; i < kFastSums; ++i)
+                if (i < nsum) atomicAdd(&a[i + 1], static_cast<unsigned long long>(x[i]));
+            if (k + 1 < sl.w) d = __ldg(&A.next[d]);
+        }
+    }
+
+    // Aggregate one joined fact row r into its slot's group(s) (general path).
     __device__ __forceinline__ void aggregate(const ScanGeom& G, const TileView& v, int r, const uint4& sl) {
         const uint32_t cnt = sl.w;
         joined += cnt;
         if (A.has_sum) sum += eval_expr(G, v, A.sum, r) * static_cast<long long>(cnt);
         if (!A.dgs) return;
         const GroupSpec& S = A.S;
-        if (sl.z & kDirectGroup) {  // a unique key whose dense group id sits in the slot
-            unsigned long long* a = S.acc + static_cast<long long>(sl.z & ~kDirectGroup) * S.nacc;
-            atomicAdd(&a[0], 1ULL);
-            for (int i = 1; i < S.nacc; ++i)
-                atomicAdd(&a[i], static_cast<unsigned long long>(eval_expr(G, v, S.acc_expr[i - 1], r)));
+        if (S.nacc - 1 <= kFastSums) {
+            int64_t x[kFastSums];
+#pragma unroll
+            for (int i = 0; i < kFastSums; ++i) x[i] = i < S.nacc - 1 ? eval_expr(G, v, S.acc_expr[i], r) : 0;
+            add_groups(sl, x, S.nacc - 1);
             return;
         }
         uint32_t d = sl.z;
+        const bool direct_group = (sl.z & kDirectGroup) != 0;
         for (uint32_t k = 0; k < cnt; ++k) {
-            unsigned long long* a = S.acc + static_cast<long long>(__ldg(&A.dgs[d])) * S.nacc;
+            const long long g = direct_group ? static_cast<long long>(sl.z & ~kDirectGroup) : __ldg(&A.dgs[d]);
+            unsigned long long* a = S.acc + g * S.nacc;
             atomicAdd(&a[0], 1ULL);
             for (int i = 1; i < S.nacc; ++i)
                 atomicAdd(&a[i], static_cast<unsigned long long>(eval_expr(G, v, S.acc_expr[i - 1], r)));
-            if (k + 1 < cnt) d = __ldg(&A.next[d]);
+            if (!direct_group && k + 1 < cnt) d = __ldg(&A.next[d]);
         }
     }
 
-    // kUnroll rows per lane are probed together: their first slot loads are
-    // independent and in flight at once (the probe is latency-bound otherwise).
+    // Slot index of key (hashed tables: the home slot; the caller probes on).
+    __device__ __forceinline__ unsigned long long home(uint64_t key, bool direct, long long kmin, bool& in) const {
+        if (direct) {
+            const unsigned long long s = key - static_cast<uint64_t>(kmin);
+            in = s < static_cast<unsigned long long>(A.H.cap);
+            return in ? s : 0;
+        }
+        in = true;
+        return key == ~0ULL ? static_cast<unsigned long long>(A.H.cap)
+                            : (mix64(key) & static_cast<unsigned long long>(A.H.cap - 1));
+    }
+
+    // The matching slot of `key` given its home slot's contents (w = 0: no match).
+    __device__ __forceinline__ uint4 resolve(uint64_t key, bool direct, unsigned long long hh, uint4 s) const {
+        if (direct || key == ~0ULL) return s;  // direct: the slot is the key's; ~0 lives in the extra slot
+        const unsigned long long mask = static_cast<unsigned long long>(A.H.cap - 1);
+        for (long long i = 0; i < A.H.cap; ++i) {
+            const uint64_t k = slot_key(s);
+            if (k == key) return s;
+            if (k == ~0ULL) break;
+            hh = (hh + 1) & mask;
+            s = __ldg(&A.H.slots[hh]);
+        }
+        return make_uint4(0u, 0u, 0u, 0u);
+    }
+
+    // Full tile: kU rows per lane, foreign keys and sums from the stage, the
+    // rows' slot loads in flight together.
+    __device__ __forceinline__ void step_fast(const TileView& v, int rbase, bool direct, long long kmin) {
+        const int r0 = rbase + (threadIdx.x % kWarp);
+        const uint32_t ok = conds_full<kU>(v.stage, A.cf, A.ncond, r0);
+        if (!__any_sync(0xffffffffu, ok)) return;
+        int64_t fk[kU];
+        load_rows<kU>(v.stage + A.fk_soff, A.fk_type, r0, fk);
+        unsigned long long hh[kU];
+        uint4 sl[kU];
+#pragma unroll
+        for (int j = 0; j < kU; ++j) {
+            bool in = false;
+            hh[j] = home(static_cast<uint64_t>(fk[j]), direct, kmin, in);
+            sl[j] = make_uint4(0u, 0u, 0u, 0u);
+            if (((ok >> j) & 1u) && in) sl[j] = __ldg(&A.H.slots[hh[j]]);
+        }
+        passed += __popc(ok);
+        int64_t sv[kU];
+        if (A.has_sum) prod_eval<kU>(A.psum, v.stage, r0, sv);
+        const int nsum = A.nsum;
+#pragma unroll
+        for (int j = 0; j < kU; ++j) {
+            if (!((ok >> j) & 1u)) continue;
+            const uint4 s = resolve(static_cast<uint64_t>(fk[j]), direct, hh[j], sl[j]);
+            if (!s.w) continue;
+            joined += s.w;
+            if (A.has_sum) sum += sv[j] * static_cast<long long>(s.w);
+            if (A.dgs) {
+                int64_t x[kFastSums];
+#pragma unroll
+                for (int i = 0; i < kFastSums; ++i) {
+                    x[i] = 0;
+                    if (i < nsum) {
+                        int64_t t[1];
+                        prod_eval<1>(A.pacc[i], v.stage, r0 + kWarp * j, t);
+                        x[i] = t[0];
+                    }
+                }
+                add_groups(s, x, nsum);
+            }
+        }
+    }
+
     __device__ void pass1(const ScanGeom& G, const TileView& v, int cw, int lane) {
         const int rw = G.T / kConsumerWarps;
-        const unsigned long long mask = static_cast<unsigned long long>(A.H.cap - 1);
+        long long kmin = 0;
+        const bool direct = ht_is_direct(A.H, &kmin);
+        if (A.pjfast && A.fast && v.full) {
+            for (int r = 0; r < rw; r += kU * kWarp) step_fast(v, cw * rw + r, direct, kmin);
+            return;
+        }
         for (int r = 0; r < rw; r += kUnroll * kWarp) {
             const int rbase = cw * rw + r;
             if (rbase >= v.rows) break;
@@ -555,34 +660,20 @@ struct PlanJoinBody {
             for (int j = 0; j < kUnroll; ++j) {
                 key[j] = 0;
                 h[j] = 0;
+                sl[j] = make_uint4(0u, 0u, 0u, 0u);
                 if ((ok >> j) & 1u) {
                     key[j] = static_cast<uint64_t>(col_val(G, v, A.fk_col, rbase + kWarp * j + lane));
-                    h[j] = key[j] == ~0ULL ? static_cast<unsigned long long>(A.H.cap) : (mix64(key[j]) & mask);
+                    bool in = false;
+                    h[j] = home(key[j], direct, kmin, in);
+                    if (in) sl[j] = __ldg(&A.H.slots[h[j]]);
                 }
             }
-#pragma unroll
-            for (int j = 0; j < kUnroll; ++j)
-                if ((ok >> j) & 1u) sl[j] = __ldg(&A.H.slots[h[j]]);
 #pragma unroll
             for (int j = 0; j < kUnroll; ++j) {
                 if (!((ok >> j) & 1u)) continue;
                 ++passed;
-                if (key[j] == ~0ULL) {  // the value -1 lives in the extra slot
-                    if (sl[j].w) aggregate(G, v, rbase + kWarp * j + lane, sl[j]);
-                    continue;
-                }
-                uint4 s = sl[j];
-                unsigned long long hh = h[j];
-                for (long long i = 0; i < A.H.cap; ++i) {
-                    const uint64_t k = slot_key(s);
-                    if (k == key[j]) {
-                        aggregate(G, v, rbase + kWarp * j + lane, s);
-                        break;
-                    }
-                    if (k == ~0ULL) break;
-                    hh = (hh + 1) & mask;
-                    s = __ldg(&A.H.slots[hh]);
-                }
+                const uint4 s = resolve(key[j], direct, h[j], sl[j]);
+                if (s.w) aggregate(G, v, rbase + kWarp * j + lane, s);
             }
         }
     }
@@ -612,6 +703,10 @@ struct PlanJoinBody {
 
     __device__ void finish(const ScanGeom&, int, int) {}
 };
+
+// Host: fill the fast-path fields of A from its geometry (pjfast = 0 when the
+// foreign key or a summed column is not staged or a sum is not in closed form).
+void lower_join_fast(PlanJoinArgs* A);
 
 // ---- selection-mask expansion (second filter kernel) ------------------------------
 

@@ -86,12 +86,42 @@ __device__ __forceinline__ void ht_direct_slot(const JoinHT& H, const uint32_t* 
     if (sl.w == 1u && sl.z != kNoRow) H.slots[s].z = dgs[sl.z] | kDirectGroup;
 }
 
+// Build-key range of a chained table: rows [i0, i1) into H.meta (min, max).
+__device__ __forceinline__ void ht_key_range(const JoinHT& H, const unsigned char* key_col, int key_type,
+                                             long long i0, long long i1, long long stride) {
+    long long lo = LLONG_MAX, hi = LLONG_MIN;
+    for (long long i = i0; i < i1; i += stride) {
+        const long long k = ldg_typed(key_col, key_type, i);
+        lo = k < lo ? k : lo;
+        hi = k > hi ? k : hi;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long l2 = __shfl_xor_sync(0xffffffffu, lo, o), h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+        lo = l2 < lo ? l2 : lo;
+        hi = h2 > hi ? h2 : hi;
+    }
+    if ((threadIdx.x % kWarp) == 0 && lo <= hi) {
+        long long* m = const_cast<long long*>(H.meta);
+        atomicMin(&m[0], lo);
+        atomicMax(&m[1], hi);
+    }
+}
+
 // Chained build: row i claims its key's slot, pushes itself on the slot's
 // list (z = head row, next[] links) and counts itself.
 __device__ __forceinline__ void ht_chain_insert_row(const JoinHT& H, const unsigned char* key_col, int key_type,
                                                     long long i, uint32_t* next, int* err) {
     const uint64_t key = static_cast<uint64_t>(ldg_typed(key_col, key_type, i));
-    const long long s = ht_claim(H, key, err);
+    long long kmin = 0;
+    long long s;
+    if (ht_is_direct(H, &kmin)) {
+        s = static_cast<long long>(key - static_cast<uint64_t>(kmin));
+        H.slots[s].x = static_cast<uint32_t>(key);
+        H.slots[s].y = static_cast<uint32_t>(key >> 32);
+    } else {
+        s = ht_claim(H, key, err);
+    }
     if (s < 0) return;
     next[i] = atomicExch(&H.slots[s].z, static_cast<uint32_t>(i));
     atomicAdd(&H.slots[s].w, 1u);

@@ -37,6 +37,16 @@ __global__ void k_ht_init(JoinHT H) {
 // on the slot's list (z = head row, next[] links) and counts itself.  The
 // rows of a key come out in no particular order, which aggregation does not
 // mind; no sort is needed.
+__global__ void k_ht_meta_init(long long* meta) {
+    meta[0] = LLONG_MAX;
+    meta[1] = LLONG_MIN;
+}
+
+__global__ void k_ht_key_range(JoinHT H, const unsigned char* key_col, int key_type, long long n) {
+    const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+    ht_key_range(H, key_col, key_type, blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x, n, stride);
+}
+
 __global__ void k_ht_insert_chain(JoinHT H, const unsigned char* key_col, int key_type, long long n,
                                   uint32_t* next, int* err) {
     for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
@@ -50,15 +60,19 @@ tqp_status ht_build_chain(tqp_ctx* ctx, const tqp_table* build, int32_t key_col,
     H->cap = ht_cap_dense(n);
     H->slots = static_cast<uint4*>(arena_alloc(ctx, static_cast<size_t>(H->cap + 1) * sizeof(uint4)));
     *next = static_cast<uint32_t*>(arena_alloc(ctx, static_cast<size_t>(n > 0 ? n : 1) * 4));
-    if (!H->slots || !*next) return arena_oom(ctx, static_cast<size_t>(H->cap + 1) * 16 + n * 4);
+    long long* meta = static_cast<long long*>(arena_alloc(ctx, 64));
+    if (!H->slots || !*next || !meta) return arena_oom(ctx, static_cast<size_t>(H->cap + 1) * 16 + n * 4);
     H->bidx = nullptr;
+    H->meta = meta;
     const int threads = 256;
     const int blocks = static_cast<int>(std::min<long long>((H->cap + threads) / threads, ctx->num_sms * 16LL));
     k_ht_init<<<blocks, threads, 0, stream>>>(*H);
+    k_ht_meta_init<<<1, 1, 0, stream>>>(meta);
     TQP_CUDA(cudaGetLastError());
     if (n == 0) return TQP_OK;
     const tqp_column& kc = build->cols[key_col];
     const int iblocks = static_cast<int>(std::min<long long>((n + threads - 1) / threads, ctx->num_sms * 16LL));
+    k_ht_key_range<<<iblocks, threads, 0, stream>>>(*H, static_cast<const unsigned char*>(kc.data), kc.type, n);
     k_ht_insert_chain<<<iblocks, threads, 0, stream>>>(*H, static_cast<const unsigned char*>(kc.data), kc.type, n,
                                                        *next, ctx->d_err);
     TQP_CUDA(cudaGetLastError());
@@ -97,6 +111,7 @@ size_t ht_bytes(long long n_build) {
 tqp_status ht_build(tqp_ctx* ctx, const tqp_table* build, int32_t key_col, JoinHT* H, cudaStream_t stream) {
     const long long n = build->num_rows;
     H->cap = ht_cap(n);
+    H->meta = nullptr;
     H->slots = static_cast<uint4*>(arena_alloc(ctx, static_cast<size_t>(H->cap + 1) * sizeof(uint4)));
     const long long nn = n > 0 ? n : 1;
     unsigned char* sb = static_cast<unsigned char*>(arena_alloc(ctx, 2 * (static_cast<size_t>(nn) * 12 + 256)));

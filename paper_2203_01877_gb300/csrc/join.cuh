@@ -16,7 +16,22 @@ struct JoinHT {
     uint4* slots;      // [cap + 1]
     long long cap;     // power of two
     const uint32_t* bidx;
+    // Chained tables only: the build keys' [min, max] (meta[0], meta[1]),
+    // reduced on the device before the inserts.  When max - min < cap the
+    // table is direct-mapped: key k lives in slot k - min, one probe, no
+    // collisions (dense surrogate keys, the usual star-schema build side).
+    // nullptr: hashed.
+    const long long* meta;
 };
+
+// Direct-mapped?  (and the key offset).  Uniform across the grid.
+__device__ __forceinline__ bool ht_is_direct(const JoinHT& H, long long* kmin) {
+    if (!H.meta) return false;
+    const long long lo = __ldg(&H.meta[0]), hi = __ldg(&H.meta[1]);
+    *kmin = lo;
+    return hi >= lo && static_cast<unsigned long long>(hi) - static_cast<unsigned long long>(lo) <
+                           static_cast<unsigned long long>(H.cap);
+}
 
 constexpr uint32_t kNoRow = 0xFFFFFFFFu;
 // In a chained table prepared for aggregation, a slot whose key has exactly

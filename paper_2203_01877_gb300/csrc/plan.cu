@@ -72,6 +72,22 @@ __global__ void __launch_bounds__(kEngineThreads, 2) k_plan_join(const __grid_co
     run_engine(A.G, A.ctl, body, smem, args_bytes<PlanJoinArgs>());
 }
 
+void lower_join_fast(PlanJoinArgs* A) {
+    A->pjfast = 0;
+    A->nsum = A->S.nacc > 0 ? A->S.nacc - 1 : 0;
+    const ColRef& fk = A->G.col[A->fk_col];
+    if (fk.slot < 0) return;
+    A->fk_soff = fk.soff;
+    A->fk_type = fk.type;
+    if (A->has_sum && !lower_prod(A->sum, A->G, &A->psum)) return;
+    if (A->dgs) {
+        if (A->nsum > kFastSums) return;
+        for (int a = 0; a < A->nsum; ++a)
+            if (!lower_prod(A->S.acc_expr[a], A->G, &A->pacc[a])) return;
+    }
+    A->pjfast = 1;
+}
+
 static bool expr_uses_only(const tqp_expr& e, int lo, int hi) {
     for (int i = 0; i < e.n && i < TQP_MAX_EXPR; ++i)
         if (e.op[i] == TQP_X_COL && (e.v[i] < lo || e.v[i] >= hi)) return false;
@@ -195,6 +211,7 @@ static tqp_status run_join_plan(tqp_ctx* ctx, const tqp_plan* p, const tqp_resul
     size_t smem = 0;
     TQP_TRY(make_geom(ctx, F, staged, tu, PlanJoinBody::kSmemBytes + args_bytes<PlanJoinArgs>(), &A.G, &smem));
     lower_fast(A.cond, A.ncond, A.G, A.cf, &A.fast);
+    lower_join_fast(&A);
 
     unsigned long long* sc = static_cast<unsigned long long*>(arena_alloc(ctx, 8 * 8));
     if (!sc) return arena_oom(ctx, 64);

@@ -225,6 +225,15 @@ struct GroupBody {
     uint64_t dk[kLaneSlots];     // lane mode: the warp's keys (the same in every lane)
     int nused = 0;               // lane mode: keys in dk (warp-uniform)
     int mode = 0;                // 0 lane, 1 warp (warp-uniform)
+    bool kw32 = false;           // packed keys fit 32 bits
+    // Full-tile fast path operands in registers (the argument block is in
+    // shared memory, and the accumulator stores would force it to be re-read).
+    static constexpr int kHotConds = 2;
+    static constexpr int kHotSums = 3;
+    HotCond hc[kHotConds];
+    HotProd hp[kHotSums];
+    uint32_t hk[TQP_MAX_GROUP_COLS];  // key columns
+    int hncond = 0, hngc = 0, hnsum = 0;
 
     __device__ GroupBody(const GroupArgs& a, unsigned char* sm) : A(a) {
         const int w = threadIdx.x / kWarp;
@@ -237,6 +246,21 @@ struct GroupBody {
 #pragma unroll
         for (int d = 0; d < kLaneSlots; ++d) dk[d] = 0;
         mode = A.S.nacc <= kLaneAcc ? 0 : 1;
+        kw32 = A.S.width <= 32;
+        if (A.kfast) {
+            hncond = A.ncond;
+            hngc = A.S.ngc;
+            hnsum = A.S.nacc - 1;
+#pragma unroll
+            for (int q = 0; q < kHotConds; ++q)
+                if (q < hncond) hc[q].load(A.cf[q]);
+#pragma unroll
+            for (int i = 0; i < TQP_MAX_GROUP_COLS; ++i)
+                hk[i] = i < hngc ? hot_desc(A.key_soff[i], A.key_type[i], 0, 0) : 0u;
+#pragma unroll
+            for (int a2 = 0; a2 < kHotSums; ++a2)
+                if (a2 < hnsum) hp[a2].load(A.pf[a2]);
+        }
     }
 
     // ---- lane mode ----
@@ -266,9 +290,16 @@ struct GroupBody {
     // the warp's key list overflows: the caller switches to warp mode.
     __device__ __forceinline__ bool lane_add(bool act, uint64_t key, const int64_t (&val)[kFastSums], int lane) {
         int id = -1;
+        if (kw32) {  // packed keys of at most 32 bits compare in 32 bits
+            const uint32_t k = static_cast<uint32_t>(key);
 #pragma unroll
-        for (int d = 0; d < kLaneSlots; ++d)
-            if (d < nused && key == dk[d]) id = d;
+            for (int d = 0; d < kLaneSlots; ++d)
+                if (d < nused && k == static_cast<uint32_t>(dk[d])) id = d;
+        } else {
+#pragma unroll
+            for (int d = 0; d < kLaneSlots; ++d)
+                if (d < nused && key == dk[d]) id = d;
+        }
         bool miss = act && id < 0;
         while (__any_sync(0xffffffffu, miss)) {
             if (nused == kLaneSlots) return false;
@@ -290,6 +321,91 @@ struct GroupBody {
 #pragma unroll
             for (int a = 0; a < kLaneAcc - 1; ++a)
                 if (a + 1 < A.S.nacc) p[(a + 1) * kWarp] += static_cast<unsigned long long>(val[a]);
+        }
+        return true;
+    }
+
+    // The U rows of every lane (pass bits `ok`) into the lane tables at once:
+    // ids first, rows of one lane with the same id folded together, then the
+    // accumulators read, summed and written with the addresses of a lane's
+    // rows all distinct -- independent chains instead of one serial
+    // read-modify-write per row.  False (nothing added) if the key list
+    // overflows.
+    template <int U>
+    __device__ __forceinline__ bool lane_step(uint32_t ok, const uint64_t (&key)[U], int64_t (&val)[kFastSums][U],
+                                              int lane) {
+        int id[U];
+        bool miss = false;
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            id[j] = -1;
+            if (kw32) {
+                const uint32_t k = static_cast<uint32_t>(key[j]);
+#pragma unroll
+                for (int d = 0; d < kLaneSlots; ++d)
+                    if (d < nused && k == static_cast<uint32_t>(dk[d])) id[j] = d;
+            } else {
+#pragma unroll
+                for (int d = 0; d < kLaneSlots; ++d)
+                    if (d < nused && key[j] == dk[d]) id[j] = d;
+            }
+            miss |= ((ok >> j) & 1u) && id[j] < 0;
+        }
+        if (__any_sync(0xffffffffu, miss)) {  // new keys: extend the warp's list, row by row (rare)
+#pragma unroll
+            for (int j = 0; j < U; ++j) {
+                bool m = ((ok >> j) & 1u) && id[j] < 0;
+                while (__any_sync(0xffffffffu, m)) {
+                    if (nused == kLaneSlots) return false;
+                    const int src = __ffs(__ballot_sync(0xffffffffu, m)) - 1;
+                    const uint64_t k = __shfl_sync(0xffffffffu, key[j], src);
+#pragma unroll
+                    for (int d = 0; d < kLaneSlots; ++d)
+                        if (d == nused) dk[d] = k;
+                    if (lane == 0) dkeys[nused] = k;
+#pragma unroll
+                    for (int i = 0; i < U; ++i)
+                        if (((ok >> i) & 1u) && id[i] < 0 && key[i] == k) id[i] = nused;
+                    ++nused;
+                    m = ((ok >> j) & 1u) && id[j] < 0;
+                }
+            }
+        }
+        // fold rows of this lane that share a group
+        uint32_t act = ok;
+        unsigned long long cnt[U];
+#pragma unroll
+        for (int j = 0; j < U; ++j) cnt[j] = 1;
+#pragma unroll
+        for (int j = 1; j < U; ++j) {
+            bool done = false;
+#pragma unroll
+            for (int k = 0; k < j; ++k) {
+                if (!done && ((act >> k) & 1u) && ((act >> j) & 1u) && id[k] == id[j]) {
+                    cnt[k] += cnt[j];
+#pragma unroll
+                    for (int a = 0; a < kFastSums; ++a) val[a][k] += val[a][j];
+                    act &= ~(1u << j);
+                    done = true;
+                }
+            }
+        }
+        const int nacc = A.S.nacc;
+        unsigned long long* p[U];
+#pragma unroll
+        for (int j = 0; j < U; ++j) p[j] = area + (id[j] < 0 ? 0 : id[j]) * (kLaneAcc * kWarp) + lane;
+#pragma unroll
+        for (int a = 0; a < kLaneAcc; ++a) {
+            if (a < nacc) {
+                unsigned long long old[U];
+#pragma unroll
+                for (int j = 0; j < U; ++j)
+                    if ((act >> j) & 1u) old[j] = p[j][a * kWarp];
+#pragma unroll
+                for (int j = 0; j < U; ++j)
+                    if ((act >> j) & 1u)
+                        p[j][a * kWarp] = old[j] + (a == 0 ? cnt[j] : static_cast<unsigned long long>(val[a - 1][j]));
+            }
         }
         return true;
     }
@@ -387,22 +503,25 @@ struct GroupBody {
         warp_add<NS>(act, key, val, nsum, lane);
     }
 
-    // Full tile, closed-form sums: U rows per lane with hoisted type dispatch.
+    // Full tile, closed-form sums: U rows per lane, operands from registers.
     template <int U>
     __device__ __forceinline__ void step_fast(const TileView& v, int rbase, int lane) {
-        const GroupSpec& S = A.S;
         const int r0 = rbase + lane;
-        const uint32_t ok = conds_full<U>(v.stage, A.cf, A.ncond, r0);
+        uint32_t ok = (1u << U) - 1u;
+#pragma unroll
+        for (int q = 0; q < kHotConds; ++q)
+            if (q < hncond) ok &= hc[q].template eval<U>(v.stage, r0);
+        if (hncond > kHotConds) ok &= conds_full<U>(v.stage, A.cf + kHotConds, hncond - kHotConds, r0);
         if (!__any_sync(0xffffffffu, ok)) return;
         uint64_t key[U];
 #pragma unroll
         for (int j = 0; j < U; ++j) key[j] = 0;
 #pragma unroll
         for (int i = 0; i < TQP_MAX_GROUP_COLS; ++i) {
-            if (i >= S.ngc) break;
+            if (i >= hngc) break;
             int64_t x[U];
-            const int t = A.key_type[i];
-            load_rows<U>(v.stage + A.key_soff[i], t, r0, x);
+            const int t = (hk[i] >> 20) & 3;
+            load_rows<U>(v.stage + (hk[i] & 0xFFFFFu), t, r0, x);
             if (t == TQP_U8) {
 #pragma unroll
                 for (int j = 0; j < U; ++j) key[j] = (key[j] << 8) | (static_cast<uint64_t>(x[j]) & 0xFFu);
@@ -415,16 +534,21 @@ struct GroupBody {
                 for (int j = 0; j < U; ++j) key[j] = static_cast<uint64_t>(x[j]) ^ 0x8000000000000000ull;
             }
         }
-        const int nsum = S.nacc - 1;
         int64_t val[kFastSums][U];
 #pragma unroll
         for (int a = 0; a < kFastSums; ++a) {
-            if (a < nsum) {
-                prod_eval<U>(A.pf[a], v.stage, r0, val[a]);
+            if (a < hnsum) {
+                if (a < kHotSums) hp[a < kHotSums ? a : 0].template eval<U>(v.stage, r0, val[a]);
+                else prod_eval<U>(A.pf[a], v.stage, r0, val[a]);
             } else {
 #pragma unroll
                 for (int j = 0; j < U; ++j) val[a][j] = 0;
             }
+        }
+        if (mode == 0) {
+            if (lane_step<U>(ok, key, val, lane)) return;
+            flush_lanes(lane);  // key list full: warp mode for the rest of the chunk
+            mode = 1;
         }
 #pragma unroll
         for (int j = 0; j < U; ++j) {
@@ -514,9 +638,11 @@ struct PlanJoinArgs {
 };
 
 struct PlanJoinBody {
-    static constexpr int kMinBlocks = 2;
+    // One CTA per SM: the probe keeps its rows' slot loads, keys and sums in
+    // registers, more than two 9-warp CTAs per SM leave (96 per thread).
+    static constexpr int kMinBlocks = 1;
     static constexpr int kSmemBytes = 0;
-    static constexpr int kU = kUnroll;  // probes in flight per lane
+    static constexpr int kJoinSums = 2; // sums of the fast path
     const PlanJoinArgs& A;
     unsigned long long joined = 0, passed = 0;
     long long sum = 0;
@@ -598,8 +724,13 @@ struct PlanJoinBody {
     }
 
     // Full tile: kU rows per lane, foreign keys and sums from the stage, the
-    // rows' slot loads in flight together.
-    __device__ __forceinline__ void step_fast(const TileView& v, int rbase, bool direct, long long kmin) {
+    // rows' slot loads in flight together.  Hot arguments are read into
+    // registers once per tile (the argument block lives in shared memory).
+    template <int kU>
+    __device__ __forceinline__ void step_fast(const TileView& v, int rbase, bool direct, long long kmin,
+                                              const uint4* __restrict__ slots, long long cap,
+                                              unsigned long long* __restrict__ gacc, int nacc, bool has_sum,
+                                              bool grouped) {
         const int r0 = rbase + (threadIdx.x % kWarp);
         const uint32_t ok = conds_full<kU>(v.stage, A.cf, A.ncond, r0);
         if (!__any_sync(0xffffffffu, ok)) return;
@@ -609,34 +740,45 @@ struct PlanJoinBody {
         uint4 sl[kU];
 #pragma unroll
         for (int j = 0; j < kU; ++j) {
-            bool in = false;
-            hh[j] = home(static_cast<uint64_t>(fk[j]), direct, kmin, in);
+            const uint64_t key = static_cast<uint64_t>(fk[j]);
+            bool in;
+            if (direct) {
+                hh[j] = key - static_cast<uint64_t>(kmin);
+                in = hh[j] < static_cast<unsigned long long>(cap);
+            } else {
+                hh[j] = key == ~0ULL ? static_cast<unsigned long long>(cap)
+                                     : (mix64(key) & static_cast<unsigned long long>(cap - 1));
+                in = true;
+            }
             sl[j] = make_uint4(0u, 0u, 0u, 0u);
-            if (((ok >> j) & 1u) && in) sl[j] = __ldg(&A.H.slots[hh[j]]);
+            if (((ok >> j) & 1u) && in) sl[j] = __ldg(&slots[hh[j]]);
         }
         passed += __popc(ok);
         int64_t sv[kU];
-        if (A.has_sum) prod_eval<kU>(A.psum, v.stage, r0, sv);
-        const int nsum = A.nsum;
+        if (has_sum) prod_eval<kU>(A.psum, v.stage, r0, sv);
+        int64_t xv[kJoinSums][kU];
+#pragma unroll
+        for (int i = 0; i < kJoinSums; ++i)
+            if (grouped && i < nacc - 1) prod_eval<kU>(A.pacc[i], v.stage, r0, xv[i]);
 #pragma unroll
         for (int j = 0; j < kU; ++j) {
             if (!((ok >> j) & 1u)) continue;
             const uint4 s = resolve(static_cast<uint64_t>(fk[j]), direct, hh[j], sl[j]);
             if (!s.w) continue;
             joined += s.w;
-            if (A.has_sum) sum += sv[j] * static_cast<long long>(s.w);
-            if (A.dgs) {
+            if (has_sum) sum += sv[j] * static_cast<long long>(s.w);
+            if (!grouped) continue;
+            if (s.z & kDirectGroup) {
+                unsigned long long* a = gacc + static_cast<long long>(s.z & ~kDirectGroup) * nacc;
+                atomicAdd(&a[0], 1ULL);
+#pragma unroll
+                for (int i = 0; i < kJoinSums; ++i)
+                    if (i < nacc - 1) atomicAdd(&a[i + 1], static_cast<unsigned long long>(xv[i][j]));
+            } else {
                 int64_t x[kFastSums];
 #pragma unroll
-                for (int i = 0; i < kFastSums; ++i) {
-                    x[i] = 0;
-                    if (i < nsum) {
-                        int64_t t[1];
-                        prod_eval<1>(A.pacc[i], v.stage, r0 + kWarp * j, t);
-                        x[i] = t[0];
-                    }
-                }
-                add_groups(s, x, nsum);
+                for (int i = 0; i < kFastSums; ++i) x[i] = i < kJoinSums ? xv[i < kJoinSums ? i : 0][j] : 0;
+                add_groups(s, x, nacc - 1);
             }
         }
     }
@@ -646,7 +788,14 @@ struct PlanJoinBody {
         long long kmin = 0;
         const bool direct = ht_is_direct(A.H, &kmin);
         if (A.pjfast && A.fast && v.full) {
-            for (int r = 0; r < rw; r += kU * kWarp) step_fast(v, cw * rw + r, direct, kmin);
+            const uint4* slots = A.H.slots;
+            const long long cap = A.H.cap;
+            unsigned long long* gacc = A.S.acc;
+            const int nacc = A.S.nacc;
+            const bool has_sum = A.has_sum != 0, grouped = A.dgs != nullptr;
+            // rw is a multiple of 128 = kUnroll * 32
+            for (int r = 0; r < rw; r += kUnroll * kWarp)
+                step_fast<kUnroll>(v, cw * rw + r, direct, kmin, slots, cap, gacc, nacc, has_sum, grouped);
             return;
         }
         for (int r = 0; r < rw; r += kUnroll * kWarp) {

@@ -273,15 +273,18 @@ bool lower_prod(const DExpr& e, const ScanGeom& G, ProdForm* out) {
     }
     if (sp != 1) return false;
     const Sym& s = st[0];
+    memset(out, 0, sizeof(*out));
     for (int k = 0; k < 2; ++k) {
-        const Aff t = k < s.nf ? s.f[k] : Aff{-1, 0u, 1u};
+        Aff t = k < s.nf ? s.f[k] : Aff{-1, 0u, 1u};
+        if (t.col >= 0 && t.a == 0) t.col = -1;  // 0 * x + b is the constant b
         if (t.col >= 0) {
             if (t.col >= G.ncols || G.col[t.col].slot < 0) return false;
             out->soff[k] = G.col[t.col].soff;
             out->type[k] = G.col[t.col].type;
+            out->kind[k] = t.a == 1u ? (t.b == 0u ? kFacPlain : kFacAdd) : (t.a == ~0ull ? kFacRsub : kFacAffine);
         } else {
-            out->soff[k] = 0;
             out->type[k] = -1;
+            out->kind[k] = kFacConst;
         }
         out->a[k] = static_cast<int64_t>(t.a);
         out->b[k] = static_cast<int64_t>(t.b);

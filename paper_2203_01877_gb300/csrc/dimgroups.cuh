@@ -86,7 +86,8 @@ __device__ __forceinline__ void ht_direct_slot(const JoinHT& H, const uint32_t* 
     if (sl.w == 1u && sl.z != kNoRow) H.slots[s].z = dgs[sl.z] | kDirectGroup;
 }
 
-// Build-key range of a chained table: rows [i0, i1) into H.meta (min, max).
+// Build-key range of a chained table: rows i0, i0 + stride, ... < i1 into
+// H.meta (min, max).  Called by every thread of a block (block-wide sync).
 __device__ __forceinline__ void ht_key_range(const JoinHT& H, const unsigned char* key_col, int key_type,
                                              long long i0, long long i1, long long stride) {
     long long lo = LLONG_MAX, hi = LLONG_MIN;
@@ -101,10 +102,24 @@ __device__ __forceinline__ void ht_key_range(const JoinHT& H, const unsigned cha
         lo = l2 < lo ? l2 : lo;
         hi = h2 > hi ? h2 : hi;
     }
-    if ((threadIdx.x % kWarp) == 0 && lo <= hi) {
-        long long* m = const_cast<long long*>(H.meta);
-        atomicMin(&m[0], lo);
-        atomicMax(&m[1], hi);
+    // one atomic pair per block (every warp of the block calls this)
+    __shared__ long long blo[32], bhi[32];
+    const int w = threadIdx.x / kWarp, nw = (blockDim.x + kWarp - 1) / kWarp;
+    if ((threadIdx.x % kWarp) == 0) {
+        blo[w] = lo;
+        bhi[w] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < nw; ++i) {
+            lo = blo[i] < lo ? blo[i] : lo;
+            hi = bhi[i] > hi ? bhi[i] : hi;
+        }
+        if (lo <= hi) {
+            long long* m = const_cast<long long*>(H.meta);
+            atomicMin(&m[0], lo);
+            atomicMax(&m[1], hi);
+        }
     }
 }
 

@@ -86,12 +86,17 @@ struct CondFast {
 
 // An expression in closed form over staged columns: the product of two affine
 // factors (a_i * x_i + b_i), evaluated mod 2^64 like the postfix program it
-// came from (ring arithmetic, so the rewrite is exact).  A factor with
-// type < 0 is the constant b_i.  Covers x, x * k, x + k, x * y and
-// x * (k - y), the shapes of the paper's aggregates (Section 5.4).
+// came from (ring arithmetic, so the rewrite is exact).  Each factor is
+// classified on the host so that the common shapes cost no multiply:
+// constant b, x, x + b, b - x, or a * x + b.  Covers x, x * k, x + k, x * y
+// and x * (k - y), the shapes of the paper's aggregates (Section 5.4).
+enum : int32_t { kFacConst = 0, kFacPlain = 1, kFacAdd = 2, kFacRsub = 3, kFacAffine = 4 };
+
 struct ProdForm {
     int32_t soff[2];
     int32_t type[2];
+    int32_t kind[2];
+    int32_t pad[2];
     int64_t a[2];
     int64_t b[2];
 };
@@ -112,31 +117,152 @@ __device__ __forceinline__ void load_rows(const unsigned char* col, int type, in
 }
 
 template <int U>
-__device__ __forceinline__ void prod_eval(const ProdForm& f, const unsigned char* stage, int r0, int64_t (&out)[U]) {
-    int64_t x[U];
-    if (f.type[0] >= 0) {
-        load_rows<U>(stage + f.soff[0], f.type[0], r0, x);
+__device__ __forceinline__ void factor_eval(const ProdForm& f, int i, const unsigned char* stage, int r0,
+                                            int64_t (&x)[U]) {
+    const int kind = f.kind[i];
+    const int64_t b = f.b[i];
+    if (kind == kFacConst) {
 #pragma unroll
-        for (int j = 0; j < U; ++j)
-            out[j] = static_cast<int64_t>(static_cast<uint64_t>(x[j]) * static_cast<uint64_t>(f.a[0]) +
-                                          static_cast<uint64_t>(f.b[0]));
-    } else {
-#pragma unroll
-        for (int j = 0; j < U; ++j) out[j] = f.b[0];
+        for (int j = 0; j < U; ++j) x[j] = b;
+        return;
     }
-    if (f.type[1] >= 0) {
-        load_rows<U>(stage + f.soff[1], f.type[1], r0, x);
+    load_rows<U>(stage + f.soff[i], f.type[i], r0, x);
+    if (kind == kFacPlain) return;
+    if (kind == kFacAdd) {
+#pragma unroll
+        for (int j = 0; j < U; ++j) x[j] = static_cast<int64_t>(static_cast<uint64_t>(x[j]) + static_cast<uint64_t>(b));
+    } else if (kind == kFacRsub) {
+#pragma unroll
+        for (int j = 0; j < U; ++j) x[j] = static_cast<int64_t>(static_cast<uint64_t>(b) - static_cast<uint64_t>(x[j]));
+    } else {
+        const uint64_t a = static_cast<uint64_t>(f.a[i]);
 #pragma unroll
         for (int j = 0; j < U; ++j)
-            out[j] = static_cast<int64_t>(static_cast<uint64_t>(out[j]) *
-                                          (static_cast<uint64_t>(x[j]) * static_cast<uint64_t>(f.a[1]) +
-                                           static_cast<uint64_t>(f.b[1])));
-    } else if (f.b[1] != 1) {
-#pragma unroll
-        for (int j = 0; j < U; ++j)
-            out[j] = static_cast<int64_t>(static_cast<uint64_t>(out[j]) * static_cast<uint64_t>(f.b[1]));
+            x[j] = static_cast<int64_t>(static_cast<uint64_t>(x[j]) * a + static_cast<uint64_t>(b));
     }
 }
+
+template <int U>
+__device__ __forceinline__ void prod_eval(const ProdForm& f, const unsigned char* stage, int r0, int64_t (&out)[U]) {
+    factor_eval<U>(f, 0, stage, r0, out);
+    if (f.kind[1] == kFacConst) {
+        if (f.b[1] != 1) {
+            const uint64_t k = static_cast<uint64_t>(f.b[1]);
+#pragma unroll
+            for (int j = 0; j < U; ++j) out[j] = static_cast<int64_t>(static_cast<uint64_t>(out[j]) * k);
+        }
+        return;
+    }
+    int64_t y[U];
+    factor_eval<U>(f, 1, stage, r0, y);
+#pragma unroll
+    for (int j = 0; j < U; ++j)
+        out[j] = static_cast<int64_t>(static_cast<uint64_t>(out[j]) * static_cast<uint64_t>(y[j]));
+}
+
+// Operand descriptors held in registers by the scan bodies (loaded once per
+// CTA from the argument block): bits 0..19 stage byte offset, 20..21 column
+// type, 22..24 factor kind, 25 negated condition.
+__device__ __forceinline__ uint32_t hot_desc(int soff, int type, int kind, int negate) {
+    return static_cast<uint32_t>(soff) | (static_cast<uint32_t>(type & 3) << 20) |
+           (static_cast<uint32_t>(kind & 7) << 22) | (static_cast<uint32_t>(negate & 1) << 25);
+}
+
+template <int U>
+__device__ __forceinline__ void hot_factor(uint32_t d, int64_t a, int64_t b, const unsigned char* stage, int r0,
+                                           int64_t (&x)[U]) {
+    const int kind = (d >> 22) & 7;
+    if (kind == kFacConst) {
+#pragma unroll
+        for (int j = 0; j < U; ++j) x[j] = b;
+        return;
+    }
+    load_rows<U>(stage + (d & 0xFFFFFu), (d >> 20) & 3, r0, x);
+    if (kind == kFacPlain) return;
+    if (kind == kFacAdd) {
+#pragma unroll
+        for (int j = 0; j < U; ++j) x[j] = static_cast<int64_t>(static_cast<uint64_t>(x[j]) + static_cast<uint64_t>(b));
+    } else if (kind == kFacRsub) {
+#pragma unroll
+        for (int j = 0; j < U; ++j) x[j] = static_cast<int64_t>(static_cast<uint64_t>(b) - static_cast<uint64_t>(x[j]));
+    } else {
+#pragma unroll
+        for (int j = 0; j < U; ++j)
+            x[j] = static_cast<int64_t>(static_cast<uint64_t>(x[j]) * static_cast<uint64_t>(a) + static_cast<uint64_t>(b));
+    }
+}
+
+// A closed-form expression (ProdForm) held in registers.
+struct HotProd {
+    uint32_t d[2];
+    int64_t a[2], b[2];
+    __device__ __forceinline__ void load(const ProdForm& f) {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            d[i] = hot_desc(f.soff[i], f.type[i] < 0 ? 0 : f.type[i], f.kind[i], 0);
+            a[i] = f.a[i];
+            b[i] = f.b[i];
+        }
+    }
+    template <int U>
+    __device__ __forceinline__ void eval(const unsigned char* stage, int r0, int64_t (&out)[U]) const {
+        hot_factor<U>(d[0], a[0], b[0], stage, r0, out);
+        if (((d[1] >> 22) & 7) == kFacConst) {
+            if (b[1] != 1) {
+#pragma unroll
+                for (int j = 0; j < U; ++j)
+                    out[j] = static_cast<int64_t>(static_cast<uint64_t>(out[j]) * static_cast<uint64_t>(b[1]));
+            }
+            return;
+        }
+        int64_t y[U];
+        hot_factor<U>(d[1], a[1], b[1], stage, r0, y);
+#pragma unroll
+        for (int j = 0; j < U; ++j)
+            out[j] = static_cast<int64_t>(static_cast<uint64_t>(out[j]) * static_cast<uint64_t>(y[j]));
+    }
+};
+
+// A full-tile range condition (CondFast) held in registers.
+struct HotCond {
+    uint32_t d;
+    int64_t lo;
+    uint64_t span;
+    __device__ __forceinline__ void load(const CondFast& c) {
+        d = hot_desc(c.soff, c.type, 0, c.negate);
+        lo = c.lo;
+        span = c.span;
+    }
+    // pass bits of rows r0 + 32 j
+    template <int U>
+    __device__ __forceinline__ uint32_t eval(const unsigned char* stage, int r0) const {
+        const unsigned char* b = stage + (d & 0xFFFFFu);
+        const int type = (d >> 20) & 3;
+        uint32_t m = 0;
+        if (type == TQP_I64) {
+#pragma unroll
+            for (int j = 0; j < U; ++j) {
+                const uint64_t x = reinterpret_cast<const uint64_t*>(b)[r0 + kWarp * j];
+                m |= static_cast<uint32_t>(x - static_cast<uint64_t>(lo) <= span) << j;
+            }
+        } else if (type == TQP_I32) {
+            const uint32_t l = static_cast<uint32_t>(lo), sp = static_cast<uint32_t>(span);
+#pragma unroll
+            for (int j = 0; j < U; ++j) {
+                const uint32_t x = reinterpret_cast<const uint32_t*>(b)[r0 + kWarp * j];
+                m |= static_cast<uint32_t>(x - l <= sp) << j;
+            }
+        } else {
+            const uint32_t l = static_cast<uint32_t>(lo), sp = static_cast<uint32_t>(span);
+#pragma unroll
+            for (int j = 0; j < U; ++j) {
+                const uint32_t x = b[r0 + kWarp * j];
+                m |= static_cast<uint32_t>(x - l <= sp) << j;
+            }
+        }
+        return (d >> 25) & 1u ? ~m : m;
+    }
+};
 
 struct TileView {
     const unsigned char* stage;  // shared-memory stage base

@@ -65,7 +65,7 @@ __global__ void k_dim_remap(const uint32_t* dslot, const uint32_t* slot2dense, l
         dgs[d] = slot2dense[dslot[d]];
 }
 
-__global__ void __launch_bounds__(kEngineThreads, 2) k_plan_join(const __grid_constant__ PlanJoinArgs P) {
+__global__ void __launch_bounds__(kEngineThreads, PlanJoinBody::kMinBlocks) k_plan_join(const __grid_constant__ PlanJoinArgs P) {
     extern __shared__ __align__(128) unsigned char smem[];
     const PlanJoinArgs& A = stage_args(P, smem + kHeaderBytes);
     PlanJoinBody body(A, smem + kHeaderBytes + args_bytes<PlanJoinArgs>());
@@ -81,7 +81,7 @@ void lower_join_fast(PlanJoinArgs* A) {
     A->fk_type = fk.type;
     if (A->has_sum && !lower_prod(A->sum, A->G, &A->psum)) return;
     if (A->dgs) {
-        if (A->nsum > kFastSums) return;
+        if (A->nsum > PlanJoinBody::kJoinSums) return;
         for (int a = 0; a < A->nsum; ++a)
             if (!lower_prod(A->S.acc_expr[a], A->G, &A->pacc[a])) return;
     }

@@ -293,6 +293,9 @@ typedef struct {
     int64_t max_groups;         /* bound on distinct groups, sizes the aggregation
                                    table; 0 = the dim row count when grouping by
                                    dim columns, else res->capacity_groups */
+    const struct tqp_dim* prepared; /* NULL, or `dim` prepared by tqp_dim_prepare with
+                                   this plan's dim_key and group columns: the join
+                                   then reuses its resident hash table */
 } tqp_plan;
 
 typedef struct {
@@ -302,6 +305,27 @@ typedef struct {
     int64_t capacity_groups;   int64_t* d_num_groups;   int64_t* d_total_groups;
     int64_t* d_num_joined;                                                   /* joined rows */
 } tqp_result;
+
+/* A dimension table prepared once for many joined plans (resident build
+ * side).  tqp_dim_prepare builds the chained hash table of `dim` on key_col
+ * (direct-mapped when the keys span at most twice the row count, else
+ * hashed) and the dense group id of every dim row for group_cols (dim column
+ * indices, at most TQP_MAX_GROUP_COLS; ngc = 0: one group), and keeps them in a
+ * long-lived region at the top of the context's arena until tqp_dim_destroy
+ * (regions are freed newest first; all of them once no batch, server or
+ * prepared dimension is left).  max_groups bounds the distinct groups (0: the
+ * row count).  It synchronizes `stream` (setup, not a hot-path call).  The
+ * dim table's device columns must stay valid and unchanged while plans use
+ * the prepared form.  A plan uses it by setting plan.prepared; plan.dim,
+ * plan.dim_key and the plan's group columns (as F + group_cols[i]) must match
+ * (else TQP_ERR_INVALID_ARG).  Errors: TQP_ERR_INVALID_ARG, TQP_ERR_CAPACITY
+ * (more groups than max_groups), TQP_ERR_OUT_OF_MEMORY (arena too small). */
+typedef struct tqp_dim tqp_dim;
+TQP_API tqp_status tqp_dim_prepare(tqp_ctx* ctx, const tqp_table* dim, int32_t key_col, const int32_t* group_cols,
+                                   int32_t ngc, int64_t max_groups, void* stream, tqp_dim** out);
+/* Number of groups of a prepared dimension (host value). */
+TQP_API int64_t tqp_dim_groups(const tqp_dim* d);
+TQP_API tqp_status tqp_dim_destroy(tqp_dim* d);
 
 /* Run one plan.  All outputs are device pointers (any may be NULL when the
  * plan does not produce it); capacity rules as in the operator calls.

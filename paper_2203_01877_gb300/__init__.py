@@ -67,7 +67,8 @@ class Plan(C.Structure):
                 ("aggs", Agg * MAX_AGGS),
                 ("has_sum", C.c_int32), ("topk", C.c_int32),
                 ("sum_expr", Expr),
-                ("topk_agg", C.c_int32), ("reserved", C.c_int32), ("max_groups", C.c_int64)]
+                ("topk_agg", C.c_int32), ("reserved", C.c_int32), ("max_groups", C.c_int64),
+                ("prepared", C.c_void_p)]
 
 
 class Result(C.Structure):
@@ -102,6 +103,10 @@ _SIGS = {
     "tqp_batch_create": (C.c_int, [_P, C.POINTER(Plan), C.POINTER(Result), C.c_int32, C.POINTER(_P)]),
     "tqp_batch_run": (C.c_int, [_P, _P]),
     "tqp_batch_destroy": (C.c_int, [_P]),
+    "tqp_dim_prepare": (C.c_int, [_P, C.POINTER(Table), C.c_int32, C.POINTER(C.c_int32), C.c_int32, C.c_int64, _P,
+                                  C.POINTER(_P)]),
+    "tqp_dim_groups": (C.c_int64, [_P]),
+    "tqp_dim_destroy": (C.c_int, [_P]),
 }
 
 
@@ -282,7 +287,8 @@ def tqp_hash_join(ctx: Context, build: TableRef, build_key: int, probe: TableRef
 
 
 def make_plan(fact: TableRef, preds=(), dim: TableRef | None = None, fact_fk=0, dim_key=0, group_cols=(),
-              aggs=(), sum_expr=None, topk=0, topk_agg=0, emit_row_ids=False, max_groups=0) -> Plan:
+              aggs=(), sum_expr=None, topk=0, topk_agg=0, emit_row_ids=False, max_groups=0,
+              prepared: "PreparedDim | None" = None) -> Plan:
     p = Plan()
     p.fact = C.pointer(fact.t)
     if len(preds) > MAX_PREDS or len(group_cols) > MAX_GROUP_COLS or len(aggs) > MAX_AGGS:
@@ -306,7 +312,8 @@ def make_plan(fact: TableRef, preds=(), dim: TableRef | None = None, fact_fk=0, 
         p.sum_expr = make_expr(sum_expr)
     p.topk, p.topk_agg = int(topk), int(topk_agg)
     p.max_groups = int(max_groups)
-    p._keep = (fact, dim)  # keep the tables' C structs alive
+    p.prepared = prepared.h if prepared is not None else None
+    p._keep = (fact, dim, prepared)  # keep the tables' C structs alive
     return p
 
 
@@ -372,3 +379,40 @@ def tqp_batch_run(batch: Batch, stream=None):
 
 def tqp_batch_destroy(batch: Batch):
     batch.close()
+
+
+class PreparedDim:
+    """A dimension table prepared once for many joined plans (tqp_dim_prepare)."""
+
+    def __init__(self, ctx: Context, dim: TableRef, key_col: int, group_cols=(), max_groups: int = 0, stream=None):
+        gc = (C.c_int32 * max(1, len(group_cols)))(*[int(c) for c in group_cols])
+        h = C.c_void_p()
+        _check(lib().tqp_dim_prepare(ctx.h, C.byref(dim.t), int(key_col), gc, len(group_cols), int(max_groups),
+                                     _stream(stream), C.byref(h)))
+        self.h = h
+        self.ctx = ctx
+        self.dim = dim
+
+    @property
+    def groups(self) -> int:
+        return int(lib().tqp_dim_groups(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().tqp_dim_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tqp_dim_prepare(ctx: Context, dim: TableRef, key_col: int, group_cols=(), max_groups: int = 0,
+                    stream=None) -> PreparedDim:
+    return PreparedDim(ctx, dim, key_col, group_cols, max_groups, stream)
+
+
+def tqp_dim_destroy(d: PreparedDim):
+    d.close()

@@ -31,6 +31,7 @@
 #include "host.h"
 #include "bodies.cuh"
 #include "dimgroups.cuh"
+#include "dim.cuh"
 #include "finalize.cuh"
 
 namespace tqp {
@@ -472,27 +473,34 @@ static tqp_status add_join_job(tqp_batch* b, const tqp_plan* p, const tqp_result
     tqp_ctx* ctx = b->ctx;
     const tqp_table* F = p->fact;
     const tqp_table* D = p->dim;
+    const tqp_dim* pd = p->prepared;
     const int nf = F->num_cols, nd = D->num_cols;
     const long long ndr = D->num_rows;
     const size_t nd_rows = static_cast<size_t>(std::max<long long>(1, ndr));
     // build side: the chained table, and the dimension rows' dense group ids
+    // (a prepared dimension has both resident)
     BuildJob B;
     memset(&B, 0, sizeof(B));
-    B.H.cap = ht_cap_dense(ndr);
-    B.H.slots = static_cast<uint4*>(balloc(b, static_cast<size_t>(B.H.cap + 1) * 16));
-    B.next = static_cast<uint32_t*>(balloc(b, nd_rows * 4));
-    if (!B.H.slots || !B.next) return arena_oom(ctx, static_cast<size_t>(B.H.cap + 1) * 16 + nd_rows * 4);
-    add_fill(b, B.H.slots, static_cast<size_t>(B.H.cap + 1) * 16, uint4{~0u, ~0u, kNoRow, 0u});
-    long long* meta = static_cast<long long*>(balloc(b, 16));
-    if (!meta) return arena_oom(ctx, 16);
-    add_fill(b, meta, 16, uint4{~0u, 0x7FFFFFFFu, 0u, 0x80000000u});  // min = INT64_MAX, max = INT64_MIN
-    B.H.meta = meta;
-    B.key_col = static_cast<const unsigned char*>(D->cols[p->dim_key].data);
-    B.key_type = D->cols[p->dim_key].type;
-    B.nrows = ndr;
-    for (int c = 0; c < nd; ++c) {
-        B.D.ptr[c] = static_cast<const unsigned char*>(D->cols[c].data);
-        B.D.type[c] = D->cols[c].type;
+    if (pd) {
+        B.H = pd->H;
+        B.next = pd->next;
+    } else {
+        B.H.cap = ht_cap_dense(ndr);
+        B.H.slots = static_cast<uint4*>(balloc(b, static_cast<size_t>(B.H.cap + 1) * 16));
+        B.next = static_cast<uint32_t*>(balloc(b, nd_rows * 4));
+        if (!B.H.slots || !B.next) return arena_oom(ctx, static_cast<size_t>(B.H.cap + 1) * 16 + nd_rows * 4);
+        add_fill(b, B.H.slots, static_cast<size_t>(B.H.cap + 1) * 16, uint4{~0u, ~0u, kNoRow, 0u});
+        long long* meta = static_cast<long long*>(balloc(b, 16));
+        if (!meta) return arena_oom(ctx, 16);
+        add_fill(b, meta, 16, uint4{~0u, 0x7FFFFFFFu, 0u, 0x80000000u});  // min = INT64_MAX, max = INT64_MIN
+        B.H.meta = meta;
+        B.key_col = static_cast<const unsigned char*>(D->cols[p->dim_key].data);
+        B.key_type = D->cols[p->dim_key].type;
+        B.nrows = ndr;
+        for (int c = 0; c < nd; ++c) {
+            B.D.ptr[c] = static_cast<const unsigned char*>(D->cols[c].data);
+            B.D.type[c] = D->cols[c].type;
+        }
     }
     // probe side: filter + probe + aggregate, one fused scan body
     ScanJob J;
@@ -517,32 +525,47 @@ static tqp_status add_join_job(tqp_batch* b, const tqp_plan* p, const tqp_result
             kt[i] = D->cols[kc[i]].type;
         }
         TQP_TRY(lower_group(kc, kt, p->ngc, p->aggs, p->naggs, nf, &A.S));
-        const long long maxg = p->max_groups > 0 ? p->max_groups : (p->ngc == 0 ? 1 : std::max<long long>(1, ndr));
-        const long long cap = group_table_cap(maxg);
-        const long long dmax = std::min<long long>(maxg, cap + 1);
-        B.grouped = 1;
-        B.claim = A.S;
-        B.claim.cap = cap;
-        B.claim.max_groups = maxg;
-        B.claim.keys = static_cast<unsigned long long*>(balloc(b, static_cast<size_t>(cap + 1) * 8));
-        B.claim.ndistinct = counter(b);
-        B.d_n = reinterpret_cast<long long*>(B.claim.ndistinct) + 1;
-        B.slot2dense = static_cast<uint32_t*>(balloc(b, static_cast<size_t>(cap + 1) * 4));
-        B.dslot = static_cast<uint32_t*>(balloc(b, nd_rows * 4));
-        B.dgs = static_cast<uint32_t*>(balloc(b, nd_rows * 4));
-        B.dkeys = static_cast<unsigned long long*>(balloc(b, static_cast<size_t>(dmax + 1) * 8));
-        B.dacc = static_cast<unsigned long long*>(balloc(b, static_cast<size_t>(dmax + 1) * A.S.nacc * 8));
-        if (!B.claim.keys || !B.slot2dense || !B.dslot || !B.dgs || !B.dkeys || !B.dacc)
-            return arena_oom(ctx, static_cast<size_t>(cap) * 12 + static_cast<size_t>(dmax) * (8 + 8 * A.S.nacc));
-        add_fill(b, B.claim.keys, static_cast<size_t>(cap + 1) * 8, kOnes16);
-        // the aggregation state in dense form: entries [0, *d_n)
-        A.S.keys = B.dkeys;
-        A.S.acc = B.dacc;
-        A.S.cap = dmax;
-        A.S.max_groups = maxg;
-        A.S.ndistinct = reinterpret_cast<unsigned long long*>(B.d_n);
-        A.S.d_dense_n = B.d_n;
-        A.dgs = B.dgs;
+        if (pd) {
+            const size_t acc_bytes = static_cast<size_t>(pd->groups + 1) * A.S.nacc * 8;
+            unsigned long long* dacc = static_cast<unsigned long long*>(balloc(b, acc_bytes));
+            if (!dacc) return arena_oom(ctx, acc_bytes);
+            add_fill(b, dacc, acc_bytes, kZero16);
+            A.S.keys = pd->dkeys;
+            A.S.acc = dacc;
+            A.S.cap = pd->groups;
+            A.S.max_groups = pd->groups;
+            A.S.ndistinct = reinterpret_cast<unsigned long long*>(pd->d_groups);
+            A.S.d_dense_n = pd->d_groups;
+            A.dgs = pd->dgs;
+        } else {
+            const long long maxg =
+                p->max_groups > 0 ? p->max_groups : (p->ngc == 0 ? 1 : std::max<long long>(1, ndr));
+            const long long cap = group_table_cap(maxg);
+            const long long dmax = std::min<long long>(maxg, cap + 1);
+            B.grouped = 1;
+            B.claim = A.S;
+            B.claim.cap = cap;
+            B.claim.max_groups = maxg;
+            B.claim.keys = static_cast<unsigned long long*>(balloc(b, static_cast<size_t>(cap + 1) * 8));
+            B.claim.ndistinct = counter(b);
+            B.d_n = reinterpret_cast<long long*>(B.claim.ndistinct) + 1;
+            B.slot2dense = static_cast<uint32_t*>(balloc(b, static_cast<size_t>(cap + 1) * 4));
+            B.dslot = static_cast<uint32_t*>(balloc(b, nd_rows * 4));
+            B.dgs = static_cast<uint32_t*>(balloc(b, nd_rows * 4));
+            B.dkeys = static_cast<unsigned long long*>(balloc(b, static_cast<size_t>(dmax + 1) * 8));
+            B.dacc = static_cast<unsigned long long*>(balloc(b, static_cast<size_t>(dmax + 1) * A.S.nacc * 8));
+            if (!B.claim.keys || !B.slot2dense || !B.dslot || !B.dgs || !B.dkeys || !B.dacc)
+                return arena_oom(ctx, static_cast<size_t>(cap) * 12 + static_cast<size_t>(dmax) * (8 + 8 * A.S.nacc));
+            add_fill(b, B.claim.keys, static_cast<size_t>(cap + 1) * 8, kOnes16);
+            // the aggregation state in dense form: entries [0, *d_n)
+            A.S.keys = B.dkeys;
+            A.S.acc = B.dacc;
+            A.S.cap = dmax;
+            A.S.max_groups = maxg;
+            A.S.ndistinct = reinterpret_cast<unsigned long long*>(B.d_n);
+            A.S.d_dense_n = B.d_n;
+            A.dgs = B.dgs;
+        }
         const GroupOut O{r->d_keys, r->d_ivals, r->d_fvals, r->capacity_groups, r->d_num_groups, ctx->d_err};
         if (p->topk > 0) {
             TQP_TRY(add_top_job(b, A.S, O, p, r));
@@ -555,13 +578,16 @@ static tqp_status add_join_job(tqp_batch* b, const tqp_plan* p, const tqp_result
             b->fin.push_back(Fj);
         }
     }
-    B.row_block = b->row_blocks;
-    b->row_blocks += (ndr + kRowsPer - 1) / kRowsPer;
-    if (B.grouped) {
-        B.num_block = b->num_blocks;
-        b->num_blocks += (B.claim.cap + 1 + kRowsPer - 1) / kRowsPer;
-        B.slot_block = b->slot_blocks;
-        b->slot_blocks += (B.H.cap + 1 + kRowsPer - 1) / kRowsPer;
+    if (!pd) {
+        B.row_block = b->row_blocks;
+        b->row_blocks += (ndr + kRowsPer - 1) / kRowsPer;
+        if (B.grouped) {
+            B.num_block = b->num_blocks;
+            b->num_blocks += (B.claim.cap + 1 + kRowsPer - 1) / kRowsPer;
+            B.slot_block = b->slot_blocks;
+            b->slot_blocks += (B.H.cap + 1 + kRowsPer - 1) / kRowsPer;
+        }
+        b->build.push_back(B);
     }
     std::vector<int> staged;
     for (int i = 0; i < ncond; ++i) staged.push_back(A.cond[i].col);
@@ -577,7 +603,6 @@ static tqp_status add_join_job(tqp_batch* b, const tqp_plan* p, const tqp_result
     A.d_num_rows = (p->emit_row_ids && r->d_row_ids) ? nullptr : r->d_num_rows;
     A.ctl.err = ctx->d_err;
     A.ctl.wait_cap = ctx->wait_cap;
-    b->build.push_back(B);
     if (A.G.ntiles > 0) {
         b->scan[kJobJoin - 1].push_back(J);
     } else {
@@ -597,7 +622,7 @@ static bool expr_in(const tqp_expr& e, int lo, int hi) {
 
 // Plans the batch lowers itself; the rest (including every malformed plan,
 // which then reports its error) take the single-plan path.
-static bool batchable(const tqp_plan* p, const tqp_result* r) {
+static bool batchable(const tqp_ctx* ctx, const tqp_plan* p, const tqp_result* r) {
     if (!p->fact || p->npreds < 0 || p->npreds > TQP_MAX_PREDS) return false;
     if (p->ngc < 0 || p->ngc > TQP_MAX_GROUP_COLS || p->naggs < 0 || p->naggs > TQP_MAX_AGGS) return false;
     if (p->topk < 0 || p->topk > kTopBlock / 2) return false;
@@ -622,6 +647,10 @@ static bool batchable(const tqp_plan* p, const tqp_result* r) {
     for (int a = 0; a < p->naggs; ++a)
         if (p->aggs[a].fn != TQP_COUNT && !expr_in(p->aggs[a].expr, 0, nf)) return false;
     if (p->has_sum && !expr_in(p->sum_expr, 0, nf)) return false;
+    if (p->prepared) {
+        if (check_prepared(ctx, p) != TQP_OK) return false;  // the single-plan path reports it
+        return !(grouped && p->topk == 0 && p->prepared->groups > kSmallCap);
+    }
     if (grouped && p->topk == 0) {
         const long long ndr = p->dim->num_rows;
         const long long maxg = p->max_groups > 0 ? p->max_groups : (p->ngc == 0 ? 1 : std::max<long long>(1, ndr));
@@ -640,7 +669,7 @@ static tqp_status lower_batch(tqp_batch* b, const tqp_plan* plans, const tqp_res
     for (int32_t i = 0; i < n; ++i) {
         const tqp_plan* p = &plans[i];
         const tqp_result* r = &res[i];
-        if (!batchable(p, r) || check_table(p->fact, "plan.fact") != TQP_OK ||
+        if (!batchable(b->ctx, p, r) || check_table(p->fact, "plan.fact") != TQP_OK ||
             (p->dim && check_table(p->dim, "plan.dim") != TQP_OK)) {
             clear_error();
             b->fb_plans.push_back(*p);
@@ -939,10 +968,7 @@ static void release(tqp_batch* b) {
     if (b->graph) cudaGraphDestroy(b->graph);
     b->exec = nullptr;
     b->graph = nullptr;
-    // long-lived regions are freed newest first; with no batch left the whole
-    // top region is free again
-    if (--b->ctx->live_batches == 0) b->ctx->top = b->ctx->arena_bytes;
-    else if (b->ctx->top < b->top_before && b->ctx->top == b->top_after) b->ctx->top = b->top_before;
+    top_close(b->ctx, b->top_before, b->top_after);
 }
 
 }  // namespace tqp
@@ -958,7 +984,7 @@ tqp_status tqp_batch_create(tqp_ctx* ctx, const tqp_plan* plans, const tqp_resul
     if (!g.ok) return fail(TQP_ERR_CUDA, "cannot select device %d", ctx->device);
     tqp_batch* b = new (std::nothrow) tqp_batch();
     if (!b) return fail(TQP_ERR_OUT_OF_MEMORY, "host allocation failed");
-    ++ctx->live_batches;
+    top_open(ctx);
     const tqp_status s = batch_create(ctx, plans, res, n, b);
     b->top_after = ctx->top;
     if (s != TQP_OK) {

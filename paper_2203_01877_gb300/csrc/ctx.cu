@@ -57,6 +57,28 @@ void* arena_alloc_top(tqp_ctx* ctx, size_t bytes, size_t align) {
     return ctx->arena + start;
 }
 
+void top_open(tqp_ctx* ctx) { ++ctx->live_regions; }
+
+void top_close(tqp_ctx* ctx, size_t before, size_t after) {
+    if (--ctx->live_regions <= 0) {
+        ctx->live_regions = 0;
+        ctx->top = ctx->arena_bytes;
+    } else if (ctx->top < before && ctx->top == after) {
+        ctx->top = before;
+    }
+}
+
+tqp_status take_device_error(tqp_ctx* ctx, cudaStream_t stream) {
+    TQP_CUDA(cudaStreamSynchronize(stream));
+    int err = 0;
+    TQP_CUDA(cudaMemcpy(&err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err != 0) {
+        TQP_CUDA(cudaMemset(ctx->d_err, 0, sizeof(int)));
+        return fail(static_cast<tqp_status>(err), "device reported: %s", tqp_status_string(static_cast<tqp_status>(err)));
+    }
+    return TQP_OK;
+}
+
 tqp_status arena_oom(tqp_ctx* ctx, size_t bytes) {
     return fail(TQP_ERR_OUT_OF_MEMORY, "scratch arena too small: need at least %zu bytes (arena holds %zu)",
                 std::max(ctx->used, bytes), ctx->arena_bytes);
@@ -499,16 +521,7 @@ tqp_status tqp_ctx_check(tqp_ctx* ctx, void* stream) {
     clear_error();
     TQP_TRY(check_ctx(ctx));
     DeviceGuard g(ctx->device);
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    TQP_CUDA(cudaStreamSynchronize(st));
-    int err = 0;
-    TQP_CUDA(cudaMemcpy(&err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (err != 0) {
-        TQP_CUDA(cudaMemset(ctx->d_err, 0, sizeof(int)));
-        return fail(static_cast<tqp_status>(err), "device reported: %s",
-                    tqp_status_string(static_cast<tqp_status>(err)));
-    }
-    return TQP_OK;
+    return take_device_error(ctx, static_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

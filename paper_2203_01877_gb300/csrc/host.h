@@ -31,7 +31,7 @@ struct tqp_ctx {
     bool owns_arena;
     size_t used;           // bump offset of the current call
     size_t top;            // start of the long-lived region (batches) at the arena's end
-    int live_batches;      // batches holding long-lived regions
+    int live_regions;      // long-lived regions (batches, prepared dimensions, servers)
     int* d_err;            // latched device error (persistent, arena start)
     long long wait_cap;
     tqp_tuning forced;     // tile_rows == 0: no override
@@ -66,6 +66,14 @@ void* arena_alloc(tqp_ctx* ctx, size_t bytes, size_t align = 256);
 // moving ctx->top back, newest first).
 void* arena_alloc_top(tqp_ctx* ctx, size_t bytes, size_t align = 256);
 tqp_status arena_oom(tqp_ctx* ctx, size_t bytes);
+// Long-lived regions at the arena's top (batches, prepared dimensions,
+// servers): open one before its first arena_alloc_top, close it with the top
+// offsets seen before and after its allocations.  Regions are freed newest
+// first; once none is left the whole top is free again.
+void top_open(tqp_ctx* ctx);
+void top_close(tqp_ctx* ctx, size_t before, size_t after);
+// Synchronize `stream` and return (and clear) the context's latched device error.
+tqp_status take_device_error(tqp_ctx* ctx, cudaStream_t stream);
 
 // Select the context's device for the duration of a call.
 struct DeviceGuard {

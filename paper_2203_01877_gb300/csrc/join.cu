@@ -54,6 +54,42 @@ __global__ void k_ht_insert_chain(JoinHT H, const unsigned char* key_col, int ke
         ht_chain_insert_row(H, key_col, key_type, i, next, err);
 }
 
+// Key range of a chained table's build side into meta[0..1] (device).
+tqp_status ht_key_range_launch(const tqp_ctx* ctx, const tqp_table* build, int32_t key_col, long long* meta,
+                               cudaStream_t stream) {
+    k_ht_meta_init<<<1, 1, 0, stream>>>(meta);
+    TQP_CUDA(cudaGetLastError());
+    const long long n = build->num_rows;
+    if (n == 0) return TQP_OK;
+    JoinHT R;
+    memset(&R, 0, sizeof(R));
+    R.meta = meta;
+    const tqp_column& kc = build->cols[key_col];
+    const int threads = 256;
+    const int blocks = static_cast<int>(std::min<long long>((n + threads - 1) / threads, ctx->num_sms * 16LL));
+    k_ht_key_range<<<blocks, threads, 0, stream>>>(R, static_cast<const unsigned char*>(kc.data), kc.type, n);
+    TQP_CUDA(cudaGetLastError());
+    return TQP_OK;
+}
+
+// Chained inserts into H (slots [cap + 1] and next [n] provided; H.meta holds
+// the key range already).
+tqp_status ht_chain_insert_launch(const tqp_ctx* ctx, const tqp_table* build, int32_t key_col, const JoinHT& H,
+                                  uint32_t* next, cudaStream_t stream) {
+    const int threads = 256;
+    const int blocks = static_cast<int>(std::min<long long>((H.cap + threads) / threads, ctx->num_sms * 16LL));
+    k_ht_init<<<blocks, threads, 0, stream>>>(H);
+    TQP_CUDA(cudaGetLastError());
+    const long long n = build->num_rows;
+    if (n == 0) return TQP_OK;
+    const tqp_column& kc = build->cols[key_col];
+    const int iblocks = static_cast<int>(std::min<long long>((n + threads - 1) / threads, ctx->num_sms * 16LL));
+    k_ht_insert_chain<<<iblocks, threads, 0, stream>>>(H, static_cast<const unsigned char*>(kc.data), kc.type, n, next,
+                                                       ctx->d_err);
+    TQP_CUDA(cudaGetLastError());
+    return TQP_OK;
+}
+
 tqp_status ht_build_chain(tqp_ctx* ctx, const tqp_table* build, int32_t key_col, JoinHT* H, uint32_t** next,
                           cudaStream_t stream) {
     const long long n = build->num_rows;
@@ -64,19 +100,8 @@ tqp_status ht_build_chain(tqp_ctx* ctx, const tqp_table* build, int32_t key_col,
     if (!H->slots || !*next || !meta) return arena_oom(ctx, static_cast<size_t>(H->cap + 1) * 16 + n * 4);
     H->bidx = nullptr;
     H->meta = meta;
-    const int threads = 256;
-    const int blocks = static_cast<int>(std::min<long long>((H->cap + threads) / threads, ctx->num_sms * 16LL));
-    k_ht_init<<<blocks, threads, 0, stream>>>(*H);
-    k_ht_meta_init<<<1, 1, 0, stream>>>(meta);
-    TQP_CUDA(cudaGetLastError());
-    if (n == 0) return TQP_OK;
-    const tqp_column& kc = build->cols[key_col];
-    const int iblocks = static_cast<int>(std::min<long long>((n + threads - 1) / threads, ctx->num_sms * 16LL));
-    k_ht_key_range<<<iblocks, threads, 0, stream>>>(*H, static_cast<const unsigned char*>(kc.data), kc.type, n);
-    k_ht_insert_chain<<<iblocks, threads, 0, stream>>>(*H, static_cast<const unsigned char*>(kc.data), kc.type, n,
-                                                       *next, ctx->d_err);
-    TQP_CUDA(cudaGetLastError());
-    return TQP_OK;
+    TQP_TRY(ht_key_range_launch(ctx, build, key_col, meta, stream));
+    return ht_chain_insert_launch(ctx, build, key_col, *H, *next, stream);
 }
 
 __global__ void k_ht_insert(JoinHT H, const unsigned char* key_col, int key_type, long long n, uint64_t* sort_key,

@@ -11,11 +11,14 @@
 // table: the join result is never materialised.  Group keys are dimension
 // columns, so each dimension row's group slot is resolved once, before the
 // probe (k_dim_groups), and a probe costs one table lookup plus atomics.
+#include <new>
+
 #include "host.h"
 #include "group.cuh"
 #include "join.cuh"
 #include "bodies.cuh"
 #include "dimgroups.cuh"
+#include "dim.cuh"
 
 namespace tqp {
 
@@ -29,6 +32,10 @@ tqp_status launch_groupby(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* pred
                           int64_t* d_total_groups);
 tqp_status ht_build_chain(tqp_ctx* ctx, const tqp_table* build, int32_t key_col, JoinHT* H, uint32_t** next,
                           cudaStream_t stream);
+tqp_status ht_key_range_launch(const tqp_ctx* ctx, const tqp_table* build, int32_t key_col, long long* meta,
+                               cudaStream_t stream);
+tqp_status ht_chain_insert_launch(const tqp_ctx* ctx, const tqp_table* build, int32_t key_col, const JoinHT& H,
+                                  uint32_t* next, cudaStream_t stream);
 
 // Dense group ids of the dimension rows, in three small passes:
 //   claim  each dim row inserts its packed group key into a claim table
@@ -94,6 +101,59 @@ static bool expr_uses_only(const tqp_expr& e, int lo, int hi) {
     return true;
 }
 
+tqp_status dense_groups_launch(tqp_ctx* ctx, const tqp_table* D, const GroupSpec& S, long long maxg,
+                               const JoinHT* H, uint32_t* dgs, unsigned long long* dkeys, unsigned long long* dacc,
+                               unsigned long long* ndistinct, cudaStream_t stream) {
+    const long long cap = group_table_cap(maxg);
+    const long long nd_rows = std::max<long long>(1, D->num_rows);
+    GroupSpec claim = S;
+    claim.cap = cap;
+    claim.max_groups = maxg;
+    claim.ndistinct = ndistinct;
+    claim.keys = static_cast<unsigned long long*>(arena_alloc(ctx, static_cast<size_t>(cap + 1) * 8));
+    uint32_t* slot2dense = static_cast<uint32_t*>(arena_alloc(ctx, static_cast<size_t>(cap + 1) * 4));
+    uint32_t* dslot = static_cast<uint32_t*>(arena_alloc(ctx, static_cast<size_t>(nd_rows) * 4));
+    if (!claim.keys || !slot2dense || !dslot) return arena_oom(ctx, static_cast<size_t>(cap) * 12 + nd_rows * 4);
+    long long* d_n = reinterpret_cast<long long*>(ndistinct) + 1;
+    TQP_CUDA(cudaMemsetAsync(claim.keys, 0xFF, static_cast<size_t>(cap + 1) * 8, stream));
+    TQP_CUDA(cudaMemsetAsync(ndistinct, 0, 16, stream));
+    if (D->num_rows == 0) return TQP_OK;
+    DimCols DC;
+    memset(&DC, 0, sizeof(DC));
+    for (int c = 0; c < D->num_cols; ++c) {
+        DC.ptr[c] = static_cast<const unsigned char*>(D->cols[c].data);
+        DC.type[c] = D->cols[c].type;
+    }
+    const int threads = 256;
+    const int blocks = static_cast<int>(std::min<long long>((D->num_rows + threads - 1) / threads, ctx->num_sms * 16LL));
+    k_dim_claim<<<blocks, threads, 0, stream>>>(claim, DC, D->num_rows, dslot, ctx->d_err);
+    const long long nb = std::max<long long>(1, std::min<long long>((cap + 1 + 2047) / 2048, ctx->num_sms * 4LL));
+    const long long per = (cap + 1 + nb - 1) / nb;
+    k_dense_number<<<static_cast<int>(nb), kNumberThreads, 0, stream>>>(claim, slot2dense, dkeys, dacc, d_n, per);
+    k_dim_remap<<<blocks, threads, 0, stream>>>(dslot, slot2dense, D->num_rows, dgs);
+    if (H) {
+        const int hblocks = static_cast<int>(std::min<long long>((H->cap + threads) / threads, ctx->num_sms * 16LL));
+        k_ht_direct<<<hblocks, threads, 0, stream>>>(*H, dgs);
+    }
+    TQP_CUDA(cudaGetLastError());
+    return TQP_OK;
+}
+
+tqp_status check_prepared(const tqp_ctx* ctx, const tqp_plan* p) {
+    const tqp_dim* pd = p->prepared;
+    if (pd->ctx != ctx) return fail(TQP_ERR_INVALID_ARG, "plan.prepared belongs to another context");
+    if (!p->dim || p->dim->num_rows != pd->nrows || p->dim_key != pd->key_col ||
+        p->dim->cols[p->dim_key].data != pd->key_data)
+        return fail(TQP_ERR_INVALID_ARG, "plan.prepared was prepared for another dimension table or key");
+    if (p->ngc > 0 || p->naggs > 0) {
+        if (p->ngc != pd->ngc) return fail(TQP_ERR_INVALID_ARG, "plan.prepared has other group columns");
+        for (int i = 0; i < p->ngc; ++i)
+            if (p->group_cols[i] - p->fact->num_cols != pd->group_cols[i])
+                return fail(TQP_ERR_INVALID_ARG, "plan.prepared has other group columns");
+    }
+    return TQP_OK;
+}
+
 static tqp_status run_join_plan(tqp_ctx* ctx, const tqp_plan* p, const tqp_result* r, cudaStream_t stream) {
     const tqp_table* F = p->fact;
     const tqp_table* D = p->dim;
@@ -110,6 +170,8 @@ static tqp_status run_join_plan(tqp_ctx* ctx, const tqp_plan* p, const tqp_resul
             return fail(TQP_ERR_UNSUPPORTED, "with a join, aggregate expressions must use fact columns only");
     if (p->has_sum && !expr_uses_only(p->sum_expr, 0, nf))
         return fail(TQP_ERR_UNSUPPORTED, "with a join, the sum expression must use fact columns only");
+    const tqp_dim* pd = p->prepared;
+    if (pd) TQP_TRY(check_prepared(ctx, p));
 
     // passing fact row ids (before the join) come from the filter kernel
     if (p->emit_row_ids && r->d_row_ids) {
@@ -120,7 +182,12 @@ static tqp_status run_join_plan(tqp_ctx* ctx, const tqp_plan* p, const tqp_resul
 
     JoinHT H;
     uint32_t* next = nullptr;
-    TQP_TRY(ht_build_chain(ctx, D, p->dim_key, &H, &next, stream));
+    if (pd) {
+        H = pd->H;
+        next = pd->next;
+    } else {
+        TQP_TRY(ht_build_chain(ctx, D, p->dim_key, &H, &next, stream));
+    }
 
     PlanJoinArgs A;
     memset(&A, 0, sizeof(A));
@@ -129,6 +196,7 @@ static tqp_status run_join_plan(tqp_ctx* ctx, const tqp_plan* p, const tqp_resul
     A.ncond = ncond;
     A.fk_col = p->fact_fk;
     A.H = H;
+    A.next = next;
     if (p->has_sum) {
         TQP_TRY(lower_expr(&p->sum_expr, nf, &A.sum));
         A.has_sum = 1;
@@ -145,55 +213,45 @@ static tqp_status run_join_plan(tqp_ctx* ctx, const tqp_plan* p, const tqp_resul
         for (int a = 0; a < p->naggs; ++a)
             if (p->aggs[a].fn == TQP_AVG && !r->d_fvals) return fail(TQP_ERR_INVALID_ARG, "AVG needs d_fvals");
         if (!r->d_num_groups) return fail(TQP_ERR_INVALID_ARG, "d_num_groups is NULL");
-        const long long maxg = p->max_groups > 0 ? p->max_groups : (p->ngc == 0 ? 1 : std::max<long long>(1, D->num_rows));
-        // claim table (keys only) sized for maxg distinct keys
-        const long long cap = group_table_cap(maxg);
-        const long long nd_rows = std::max<long long>(1, D->num_rows);
-        GroupSpec claim = A.S;
-        claim.cap = cap;
-        claim.max_groups = maxg;
-        claim.keys = static_cast<unsigned long long*>(arena_alloc(ctx, static_cast<size_t>(cap + 1) * 8));
-        claim.ndistinct = static_cast<unsigned long long*>(arena_alloc(ctx, 256));
-        long long* d_n = reinterpret_cast<long long*>(claim.ndistinct) + 1;
-        uint32_t* slot2dense = static_cast<uint32_t*>(arena_alloc(ctx, static_cast<size_t>(cap + 1) * 4));
-        uint32_t* dslot = static_cast<uint32_t*>(arena_alloc(ctx, static_cast<size_t>(nd_rows) * 4));
-        uint32_t* dgs = static_cast<uint32_t*>(arena_alloc(ctx, static_cast<size_t>(nd_rows) * 4));
-        // dense accumulators: one entry per distinct dim group (<= maxg, and <= cap + 1 claimed slots)
-        const long long dmax = std::min<long long>(maxg, cap + 1);
-        unsigned long long* dkeys = static_cast<unsigned long long*>(arena_alloc(ctx, static_cast<size_t>(dmax + 1) * 8));
-        unsigned long long* dacc =
-            static_cast<unsigned long long*>(arena_alloc(ctx, static_cast<size_t>(dmax + 1) * A.S.nacc * 8));
-        if (!claim.keys || !claim.ndistinct || !slot2dense || !dslot || !dgs || !dkeys || !dacc)
-            return arena_oom(ctx, static_cast<size_t>(cap) * 12 + static_cast<size_t>(dmax) * (8 + 8 * A.S.nacc));
-        TQP_CUDA(cudaMemsetAsync(claim.keys, 0xFF, static_cast<size_t>(cap + 1) * 8, stream));
-        TQP_CUDA(cudaMemsetAsync(claim.ndistinct, 0, 16, stream));
-        DimCols DC;
-        memset(&DC, 0, sizeof(DC));
-        for (int c = 0; c < nd; ++c) {
-            DC.ptr[c] = static_cast<const unsigned char*>(D->cols[c].data);
-            DC.type[c] = D->cols[c].type;
+        if (pd) {
+            // resident dense ids and keys; this plan's accumulators only
+            const size_t acc_bytes = static_cast<size_t>(pd->groups + 1) * A.S.nacc * 8;
+            unsigned long long* dacc = static_cast<unsigned long long*>(arena_alloc(ctx, acc_bytes));
+            if (!dacc) return arena_oom(ctx, acc_bytes);
+            TQP_CUDA(cudaMemsetAsync(dacc, 0, acc_bytes, stream));
+            A.S.keys = pd->dkeys;
+            A.S.acc = dacc;
+            A.S.cap = pd->groups;
+            A.S.max_groups = pd->groups;
+            A.S.ndistinct = reinterpret_cast<unsigned long long*>(pd->d_groups);
+            A.S.d_dense_n = pd->d_groups;
+            A.dgs = pd->dgs;
+        } else {
+            const long long maxg =
+                p->max_groups > 0 ? p->max_groups : (p->ngc == 0 ? 1 : std::max<long long>(1, D->num_rows));
+            const long long cap = group_table_cap(maxg);
+            const long long nd_rows = std::max<long long>(1, D->num_rows);
+            // dense accumulators: one entry per distinct dim group (<= maxg, and <= cap + 1 claimed slots)
+            const long long dmax = std::min<long long>(maxg, cap + 1);
+            unsigned long long* nds = static_cast<unsigned long long*>(arena_alloc(ctx, 256));
+            uint32_t* dgs = static_cast<uint32_t*>(arena_alloc(ctx, static_cast<size_t>(nd_rows) * 4));
+            unsigned long long* dkeys =
+                static_cast<unsigned long long*>(arena_alloc(ctx, static_cast<size_t>(dmax + 1) * 8));
+            unsigned long long* dacc =
+                static_cast<unsigned long long*>(arena_alloc(ctx, static_cast<size_t>(dmax + 1) * A.S.nacc * 8));
+            if (!nds || !dgs || !dkeys || !dacc)
+                return arena_oom(ctx, static_cast<size_t>(dmax) * (8 + 8 * A.S.nacc) + nd_rows * 4);
+            TQP_TRY(dense_groups_launch(ctx, D, A.S, maxg, &H, dgs, dkeys, dacc, nds, stream));
+            long long* d_n = reinterpret_cast<long long*>(nds) + 1;
+            // the aggregation state in dense form: entries [0, *d_n)
+            A.S.keys = dkeys;
+            A.S.acc = dacc;
+            A.S.cap = dmax;
+            A.S.max_groups = maxg;
+            A.S.ndistinct = reinterpret_cast<unsigned long long*>(d_n);
+            A.S.d_dense_n = d_n;
+            A.dgs = dgs;
         }
-        const int threads = 256;
-        if (D->num_rows > 0) {
-            const int blocks = static_cast<int>(std::min<long long>((D->num_rows + threads - 1) / threads, ctx->num_sms * 16LL));
-            k_dim_claim<<<blocks, threads, 0, stream>>>(claim, DC, D->num_rows, dslot, ctx->d_err);
-            const long long nb = std::max<long long>(1, std::min<long long>((cap + 1 + 2047) / 2048, ctx->num_sms * 4LL));
-            const long long per = (cap + 1 + nb - 1) / nb;
-            k_dense_number<<<static_cast<int>(nb), kNumberThreads, 0, stream>>>(claim, slot2dense, dkeys, dacc, d_n, per);
-            k_dim_remap<<<blocks, threads, 0, stream>>>(dslot, slot2dense, D->num_rows, dgs);
-            const int hblocks = static_cast<int>(std::min<long long>((H.cap + threads) / threads, ctx->num_sms * 16LL));
-            k_ht_direct<<<hblocks, threads, 0, stream>>>(H, dgs);
-            TQP_CUDA(cudaGetLastError());
-        }
-        // the aggregation state in dense form: entries [0, *d_n)
-        A.S.keys = dkeys;
-        A.S.acc = dacc;
-        A.S.cap = dmax;
-        A.S.max_groups = maxg;
-        A.S.ndistinct = reinterpret_cast<unsigned long long*>(d_n);
-        A.S.d_dense_n = d_n;
-        A.dgs = dgs;
-        A.next = next;
     }
 
     // stage the conditions, the foreign key and every aggregated fact column
@@ -289,9 +347,111 @@ tqp_status run_plan_one(tqp_ctx* ctx, const tqp_plan* p, const tqp_result* r, cu
     return run_scan_plan(ctx, p, r, stream);
 }
 
+static void* top_bytes(tqp_ctx* ctx, size_t bytes) { return arena_alloc_top(ctx, (bytes + 15) / 16 * 16); }
+
+static tqp_status dim_prepare(tqp_ctx* ctx, const tqp_table* D, int32_t key_col, const int32_t* group_cols,
+                              int32_t ngc, int64_t max_groups, tqp_dim* d, cudaStream_t st) {
+    const long long n = D->num_rows;
+    d->nrows = n;
+    d->key_col = key_col;
+    d->ngc = ngc;
+    for (int i = 0; i < ngc; ++i) d->group_cols[i] = group_cols[i];
+    d->key_data = D->cols[key_col].data;
+    // key range first: dense keys get a direct-mapped table sized to their range
+    long long* meta = static_cast<long long*>(top_bytes(ctx, 64));
+    if (!meta) return arena_oom(ctx, 64);
+    TQP_TRY(ht_key_range_launch(ctx, D, key_col, meta, st));
+    long long mm[2] = {0, -1};
+    TQP_CUDA(cudaMemcpyAsync(mm, meta, sizeof(mm), cudaMemcpyDeviceToHost, st));
+    TQP_CUDA(cudaStreamSynchronize(st));
+    const bool dense = n > 0 && mm[1] >= mm[0] &&
+                       static_cast<unsigned long long>(mm[1]) - static_cast<unsigned long long>(mm[0]) <
+                           2ull * static_cast<unsigned long long>(n) + 64;
+    d->H.cap = dense ? mm[1] - mm[0] + 1 : ht_cap_dense(n);
+    d->H.meta = meta;
+    d->H.bidx = nullptr;
+    d->H.slots = static_cast<uint4*>(top_bytes(ctx, static_cast<size_t>(d->H.cap + 1) * 16));
+    d->next = static_cast<uint32_t*>(top_bytes(ctx, static_cast<size_t>(std::max<long long>(1, n)) * 4));
+    d->dgs = static_cast<uint32_t*>(top_bytes(ctx, static_cast<size_t>(std::max<long long>(1, n)) * 4));
+    d->d_groups = static_cast<long long*>(top_bytes(ctx, 16));
+    if (!d->H.slots || !d->next || !d->dgs || !d->d_groups)
+        return arena_oom(ctx, static_cast<size_t>(d->H.cap) * 16 + static_cast<size_t>(n) * 8);
+    TQP_TRY(ht_chain_insert_launch(ctx, D, key_col, d->H, d->next, st));
+    // dense group ids of the rows (per-call scratch holds the claim table)
+    int32_t kt[TQP_MAX_GROUP_COLS] = {0, 0, 0, 0};
+    for (int i = 0; i < ngc; ++i) kt[i] = D->cols[group_cols[i]].type;
+    GroupSpec S;
+    TQP_TRY(lower_group(group_cols, kt, ngc, nullptr, 0, D->num_cols, &S));
+    const long long maxg = max_groups > 0 ? max_groups : (ngc == 0 ? 1 : std::max<long long>(1, n));
+    const long long dmax = std::min<long long>(maxg, group_table_cap(maxg) + 1);
+    unsigned long long* nds = static_cast<unsigned long long*>(arena_alloc(ctx, 256));
+    unsigned long long* dkeys = static_cast<unsigned long long*>(arena_alloc(ctx, static_cast<size_t>(dmax + 1) * 8));
+    unsigned long long* dacc =
+        static_cast<unsigned long long*>(arena_alloc(ctx, static_cast<size_t>(dmax + 1) * S.nacc * 8));
+    if (!nds || !dkeys || !dacc) return arena_oom(ctx, static_cast<size_t>(dmax) * 16);
+    TQP_TRY(dense_groups_launch(ctx, D, S, maxg, &d->H, d->dgs, dkeys, dacc, nds, st));
+    TQP_TRY(take_device_error(ctx, st));
+    long long G = 0;
+    TQP_CUDA(cudaMemcpy(&G, reinterpret_cast<long long*>(nds) + 1, sizeof(G), cudaMemcpyDeviceToHost));
+    if (G > maxg) return fail(TQP_ERR_CAPACITY, "dimension has more than max_groups = %lld groups", (long long)maxg);
+    d->groups = G;
+    d->dkeys = static_cast<unsigned long long*>(top_bytes(ctx, static_cast<size_t>(G + 1) * 8));
+    if (!d->dkeys) return arena_oom(ctx, static_cast<size_t>(G + 1) * 8);
+    TQP_CUDA(cudaMemcpy(d->dkeys, dkeys, static_cast<size_t>(G + 1) * 8, cudaMemcpyDeviceToDevice));
+    TQP_CUDA(cudaMemcpy(d->d_groups, &G, sizeof(G), cudaMemcpyHostToDevice));
+    TQP_CUDA(cudaDeviceSynchronize());
+    return TQP_OK;
+}
+
 }  // namespace tqp
 
 using namespace tqp;
+
+extern "C" tqp_status tqp_dim_prepare(tqp_ctx* ctx, const tqp_table* dim, int32_t key_col, const int32_t* group_cols,
+                                      int32_t ngc, int64_t max_groups, void* stream, tqp_dim** out) {
+    clear_error();
+    TQP_TRY(check_ctx(ctx));
+    if (!out) return fail(TQP_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    TQP_TRY(check_table(dim, "dim"));
+    if (key_col < 0 || key_col >= dim->num_cols) return fail(TQP_ERR_INVALID_ARG, "key_col out of range");
+    if (ngc < 0 || ngc > TQP_MAX_GROUP_COLS || (ngc > 0 && !group_cols))
+        return fail(TQP_ERR_INVALID_ARG, "bad group columns");
+    for (int i = 0; i < ngc; ++i)
+        if (group_cols[i] < 0 || group_cols[i] >= dim->num_cols)
+            return fail(TQP_ERR_INVALID_ARG, "group column %d out of range", group_cols[i]);
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(TQP_ERR_CUDA, "cannot select device %d", ctx->device);
+    arena_reset(ctx);
+    tqp_dim* d = new (std::nothrow) tqp_dim();
+    if (!d) return fail(TQP_ERR_OUT_OF_MEMORY, "host allocation failed");
+    d->ctx = ctx;
+    top_open(ctx);
+    d->top_before = ctx->top;
+    const tqp_status s = dim_prepare(ctx, dim, key_col, group_cols, ngc, max_groups, d, static_cast<cudaStream_t>(stream));
+    d->top_after = ctx->top;
+    if (s != TQP_OK) {
+        top_close(ctx, d->top_before, d->top_after);
+        delete d;
+        return s;
+    }
+    *out = d;
+    return TQP_OK;
+}
+
+extern "C" int64_t tqp_dim_groups(const tqp_dim* d) { return d ? d->groups : -1; }
+
+extern "C" tqp_status tqp_dim_destroy(tqp_dim* d) {
+    clear_error();
+    if (!d) return TQP_OK;
+    {
+        DeviceGuard g(d->ctx->device);
+        cudaDeviceSynchronize();  // no plan in flight may still read the prepared tables
+        top_close(d->ctx, d->top_before, d->top_after);
+    }
+    delete d;
+    return TQP_OK;
+}
 
 extern "C" tqp_status tqp_run_plan(tqp_ctx* ctx, const tqp_plan* plan, const tqp_result* res, void* stream) {
     clear_error();

@@ -313,7 +313,8 @@ typedef struct {
  * indices, at most TQP_MAX_GROUP_COLS; ngc = 0: one group), and keeps them in a
  * long-lived region at the top of the context's arena until tqp_dim_destroy
  * (regions are freed newest first; all of them once no batch, server or
- * prepared dimension is left).  max_groups bounds the distinct groups (0: the
+ * prepared dimension is left); plans on any context of the same device may
+ * use it while the preparing context lives.  max_groups bounds the distinct groups (0: the
  * row count).  It synchronizes `stream` (setup, not a hot-path call).  The
  * dim table's device columns must stay valid and unchanged while plans use
  * the prepared form.  A plan uses it by setting plan.prepared; plan.dim,
@@ -368,6 +369,53 @@ TQP_API tqp_status tqp_batch_create(tqp_ctx* ctx, const tqp_plan* plans, const t
                                     tqp_batch** out);
 TQP_API tqp_status tqp_batch_run(tqp_batch* batch, void* stream);
 TQP_API tqp_status tqp_batch_destroy(tqp_batch* batch);
+
+/* ---- serving ------------------------------------------------------------ */
+
+/* A server runs submitted plans with continuous batching (the paper runs one
+ * query at a time, Section 4.3): a host dispatcher thread takes pending plans
+ * in arrival order into free in-flight slots as one batch each (the batched
+ * executor of tqp_run_plans), while earlier batches are still on the device.
+ * Each slot has its own stream and its own share of a scratch budget taken
+ * from a long-lived region of the context's arena: a batch is admitted only
+ * if its scratch (hash tables, selection masks, group tables) fits the share
+ * (admission by free HBM budget; an oversized batch is split, a single plan
+ * that does not fit completes with TQP_ERR_OUT_OF_MEMORY).  Results are
+ * identical to tqp_run_plan of each plan alone.
+ *   max_batch     plans per batch (1 = one query at a time)
+ *   max_inflight  batches on the device at once (1..8)
+ *   budget_bytes  scratch for all in-flight batches together
+ * The context must not be used for other calls while the server lives. */
+typedef struct {
+    int32_t max_batch;
+    int32_t max_inflight;
+    int64_t budget_bytes;
+} tqp_server_config;
+
+/* One finished request: its tag, status, the size of the batch it ran in,
+ * and host-clock seconds from submission to launch and to completion (seen
+ * by the dispatcher polling the batch's event). */
+typedef struct {
+    uint64_t tag;
+    int32_t status;
+    int32_t batch_size;
+    double queue_s;
+    double latency_s;
+} tqp_completion;
+
+typedef struct tqp_server tqp_server;
+TQP_API tqp_status tqp_server_create(tqp_ctx* ctx, const tqp_server_config* cfg, tqp_server** out);
+/* Queue a plan (copied; its tables, prepared dimension and result buffers
+ * must stay valid until the request completes).  Thread-safe. */
+TQP_API tqp_status tqp_server_submit(tqp_server* s, const tqp_plan* plan, const tqp_result* res, uint64_t tag);
+/* Move up to max finished requests into out[]; returns how many (>= 0), or
+ * -1 if s or out is NULL.  Thread-safe. */
+TQP_API int32_t tqp_server_poll(tqp_server* s, tqp_completion* out, int32_t max);
+/* Wait until every submitted request has finished (TQP_ERR_TIMEOUT after
+ * timeout_s seconds). */
+TQP_API tqp_status tqp_server_drain(tqp_server* s, double timeout_s);
+/* Stop the dispatcher after the queued work and release the region. */
+TQP_API tqp_status tqp_server_destroy(tqp_server* s);
 
 #ifdef __cplusplus
 }

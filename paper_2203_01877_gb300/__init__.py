@@ -107,6 +107,11 @@ _SIGS = {
                                   C.POINTER(_P)]),
     "tqp_dim_groups": (C.c_int64, [_P]),
     "tqp_dim_destroy": (C.c_int, [_P]),
+    "tqp_server_create": (C.c_int, [_P, C.c_void_p, C.POINTER(_P)]),
+    "tqp_server_submit": (C.c_int, [_P, C.POINTER(Plan), C.POINTER(Result), C.c_uint64]),
+    "tqp_server_poll": (C.c_int32, [_P, C.c_void_p, C.c_int32]),
+    "tqp_server_drain": (C.c_int, [_P, C.c_double]),
+    "tqp_server_destroy": (C.c_int, [_P]),
 }
 
 
@@ -416,3 +421,73 @@ def tqp_dim_prepare(ctx: Context, dim: TableRef, key_col: int, group_cols=(), ma
 
 def tqp_dim_destroy(d: PreparedDim):
     d.close()
+
+
+class ServerConfig(C.Structure):
+    _fields_ = [("max_batch", C.c_int32), ("max_inflight", C.c_int32), ("budget_bytes", C.c_int64)]
+
+
+class Completion(C.Structure):
+    _fields_ = [("tag", C.c_uint64), ("status", C.c_int32), ("batch_size", C.c_int32), ("queue_s", C.c_double),
+                ("latency_s", C.c_double)]
+
+
+class Server:
+    """Continuous batching of submitted plans (tqp_server_*).
+
+    The caller keeps each submitted plan's tables and result buffers alive until
+    its completion is polled."""
+
+    def __init__(self, ctx: Context, max_batch: int = 64, max_inflight: int = 2, budget_bytes: int = 1 << 30):
+        cfg = ServerConfig(int(max_batch), int(max_inflight), int(budget_bytes))
+        h = C.c_void_p()
+        _check(lib().tqp_server_create(ctx.h, C.byref(cfg), C.byref(h)))
+        self.h = h
+        self.ctx = ctx
+        self._buf = (Completion * 4096)()
+
+    def submit(self, plan: Plan, result: Result, tag: int):
+        _check(lib().tqp_server_submit(self.h, C.byref(plan), C.byref(result), int(tag)))
+
+    def poll(self):
+        """Finished requests since the last poll: list of (tag, status, batch_size, queue_s, latency_s)."""
+        out = []
+        while True:
+            k = lib().tqp_server_poll(self.h, self._buf, len(self._buf))
+            out.extend((c.tag, c.status, c.batch_size, c.queue_s, c.latency_s) for c in self._buf[:k])
+            if k < len(self._buf):
+                return out
+
+    def drain(self, timeout_s: float = 60.0):
+        _check(lib().tqp_server_drain(self.h, float(timeout_s)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().tqp_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tqp_server_create(ctx: Context, max_batch: int = 64, max_inflight: int = 2, budget_bytes: int = 1 << 30) -> Server:
+    return Server(ctx, max_batch, max_inflight, budget_bytes)
+
+
+def tqp_server_submit(server: Server, plan: Plan, result: Result, tag: int):
+    server.submit(plan, result, tag)
+
+
+def tqp_server_poll(server: Server):
+    return server.poll()
+
+
+def tqp_server_drain(server: Server, timeout_s: float = 60.0):
+    server.drain(timeout_s)
+
+
+def tqp_server_destroy(server: Server):
+    server.close()

@@ -71,7 +71,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     tmp = LIB + f".{os.getpid()}.tmp"
     libdir = _cuda_lib_dir(nv)
     cmd = [nv, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
-           "-Xlinker", f"-rpath,{libdir}", "-L", libdir]
+           "-Xlinker", f"-rpath,{libdir}", "-L", libdir, "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -963,6 +963,19 @@ static tqp_status batch_create(tqp_ctx* ctx, const tqp_plan* plans, const tqp_re
     return TQP_OK;
 }
 
+tqp_status run_plans_on(tqp_ctx* ctx, const tqp_plan* plans, const tqp_result* res, int32_t n, cudaStream_t st) {
+    arena_reset(ctx);
+    tqp_batch b;
+    b.ctx = ctx;
+    b.persistent = false;
+    TQP_TRY(batch_prepare(ctx, plans, res, n, &b, st));
+    TQP_TRY(batch_launch(&b, st));
+    if (b.fb_plans.empty()) return TQP_OK;
+    const size_t lo = (ctx->used + 255) / 256 * 256;
+    if (lo >= ctx->top) return arena_oom(ctx, lo + kPersistentBytes);
+    return run_fallbacks(&b, st, ctx->arena + lo, ctx->top - lo, nullptr);
+}
+
 static void release(tqp_batch* b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
@@ -1024,17 +1037,7 @@ tqp_status tqp_run_plans(tqp_ctx* ctx, const tqp_plan* plans, const tqp_result* 
     if (n == 0) return TQP_OK;
     DeviceGuard g(ctx->device);
     if (!g.ok) return fail(TQP_ERR_CUDA, "cannot select device %d", ctx->device);
-    const cudaStream_t st = static_cast<cudaStream_t>(stream);
-    arena_reset(ctx);
-    tqp_batch b;
-    b.ctx = ctx;
-    b.persistent = false;
-    TQP_TRY(batch_prepare(ctx, plans, res, n, &b, st));
-    TQP_TRY(batch_launch(&b, st));
-    if (b.fb_plans.empty()) return TQP_OK;
-    const size_t lo = (ctx->used + 255) / 256 * 256;
-    if (lo >= ctx->top) return arena_oom(ctx, lo + kPersistentBytes);
-    return run_fallbacks(&b, st, ctx->arena + lo, ctx->top - lo, nullptr);
+    return run_plans_on(ctx, plans, res, n, static_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

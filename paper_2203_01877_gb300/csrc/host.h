@@ -121,4 +121,8 @@ tqp_status allow_smem(const tqp_ctx* ctx, const void* kernel, bool* done_per_dev
 tqp_status set_device_i64(long long* d_ptr, long long value, cudaStream_t stream);
 constexpr int kMaxDevices = 64;
 
+// One-shot batched run of n plans in ctx's per-call scratch on `stream` (the
+// body of tqp_run_plans; the server calls it with a slot's sub-context).
+tqp_status run_plans_on(tqp_ctx* ctx, const tqp_plan* plans, const tqp_result* res, int32_t n, cudaStream_t stream);
+
 }  // namespace tqp

@@ -141,7 +141,7 @@ tqp_status dense_groups_launch(tqp_ctx* ctx, const tqp_table* D, const GroupSpec
 
 tqp_status check_prepared(const tqp_ctx* ctx, const tqp_plan* p) {
     const tqp_dim* pd = p->prepared;
-    if (pd->ctx != ctx) return fail(TQP_ERR_INVALID_ARG, "plan.prepared belongs to another context");
+    if (pd->ctx->device != ctx->device) return fail(TQP_ERR_INVALID_ARG, "plan.prepared lives on another device");
     if (!p->dim || p->dim->num_rows != pd->nrows || p->dim_key != pd->key_col ||
         p->dim->cols[p->dim_key].data != pd->key_data)
         return fail(TQP_ERR_INVALID_ARG, "plan.prepared was prepared for another dimension table or key");

@@ -405,6 +405,138 @@ def batched_workload(tqp, torch, dev, local, reps, n_plans=BATCH_PLANS):
     }
 
 
+SERVE_FACT_ROWS = 600_000_000
+SERVE_DIM_ROWS = 15_000_000
+SERVE_POOL = 512  # result buffer sets, reused round-robin
+
+
+def serving_workload(tqp, torch, dev, local, seconds=10.0, rate=2000.0, sweep=(2000, 6000, 16000),
+                     sweep_seconds=1.0, fact_rows=SERVE_FACT_ROWS, dim_rows=SERVE_DIM_ROWS):
+    """Open-loop Poisson arrivals of the three plan shapes over seeded row ranges of a resident fact table
+    (config-0 columns) joined, for the join shape, with a prepared resident dimension; continuous batching
+    (tqp_server, 64 plans per batch, 3 batches in flight) against one-at-a-time FIFO (1 plan, 1 in flight)."""
+    from datagen import torch_gen
+    seed = datagen.DEFAULT_SEED + 4
+    t_setup = time.perf_counter()
+    names = ("date", "flag", "status", "quantity", "price", "discount", "key")
+    fact = torch_gen.fact_table(fact_rows, seed=seed, cols=names, device=dev)
+    d = datagen.dim_table(dim_rows, 150_000, seed=seed)
+    D = tqp.TableRef([torch.from_numpy(d["key"]).to(dev), torch.from_numpy(d["payload"]).to(dev)])
+    del d
+    pctx = tqp.Context(local, 2 << 30)
+    pdim = tqp.tqp_dim_prepare(pctx, D, 0, [1], max_groups=150_000)
+    q1_aggs = [("sum", [("col", 3)]), ("sum", [("col", 4)]),
+               ("sum", [("col", 4), ("const", 100), ("col", 5), "sub", "mul"]), ("count", None),
+               ("avg", [("col", 4)])]
+    q6_preds = [(0, "ge", 731), (0, "lt", 1096), (1, "between", 5, 7), (2, "lt", 24)]
+    max_rows = 5_000_000
+    pool = []
+    for _ in range(SERVE_POOL):
+        z = lambda m, dt=torch.int64: torch.zeros(m, dtype=dt, device=dev)  # noqa: E731
+        pool.append(dict(ids=z(max_rows, torch.int32), keys=z(128), iv=z(320), fv=z(320, torch.float64), ng=z(1),
+                         tot=z(1), nr=z(1), s=z(1), nj=z(1)))
+    nq_max = int(max(rate * seconds, max(sweep) * sweep_seconds)) + 1
+    sizes = datagen.log_uniform_int(seed, 91, nq_max, 10_000, max_rows)
+    offs = datagen.uniform_int(seed, 92, nq_max, 0, (fact_rows - max_rows) // 16, np.int64) * 16
+    views = {}
+
+    def query(i):
+        kind, n, r0 = i % 3, int(sizes[i]), int(offs[i])
+        b = pool[i % SERVE_POOL]
+        if kind == 0:
+            T = tqp.TableRef([fact[c][r0:r0 + n] for c in names[:6]])
+            plan = tqp.make_plan(T, [(0, "le", 2450)], None, 0, 0, [1, 2], q1_aggs)
+            res = tqp.make_result(None, 0, b["nr"], None, b["keys"], b["iv"], b["fv"], 64, b["ng"], b["tot"], None)
+        elif kind == 1:
+            T = tqp.TableRef([fact[c][r0:r0 + n] for c in ("date", "discount", "quantity", "price")])
+            plan = tqp.make_plan(T, q6_preds, sum_expr=[("col", 3), ("col", 1), "mul"], emit_row_ids=True)
+            res = tqp.make_result(b["ids"], n, b["nr"], b["s"])
+        else:
+            T = tqp.TableRef([fact["key"][r0:r0 + n], fact["price"][r0:r0 + n]])
+            plan = tqp.make_plan(T, (), D, 0, 0, [3], [("sum", [("col", 1)]), ("count", None)], None, 100, 0,
+                                 prepared=pdim)
+            res = tqp.make_result(None, 0, None, None, b["keys"], b["iv"], None, 100, b["ng"], b["tot"], b["nj"])
+        views[i] = T
+        return plan, res
+
+    queries = [query(i) for i in range(nq_max)]
+    setup_s = time.perf_counter() - t_setup
+
+    def run(max_batch, max_inflight, qps, nq):
+        budget = 4 << 30
+        ctx = tqp.Context(local, budget + (256 << 20))
+        srv = tqp.Server(ctx, max_batch=max_batch, max_inflight=max_inflight, budget_bytes=budget)
+        rng = np.random.default_rng(int(qps) * 7 + max_batch)
+        arrive = np.cumsum(rng.exponential(1.0 / qps, nq))
+        sub_t = np.zeros(nq)
+        done = {}
+        t0 = time.perf_counter()
+        for i in range(nq):
+            target = t0 + arrive[i]
+            while True:
+                now = time.perf_counter()
+                if now >= target:
+                    break
+                if target - now > 3e-4:
+                    for c in srv.poll():
+                        done[c[0]] = c
+            while i >= SERVE_POOL and (i - SERVE_POOL) not in done:  # the result set is still in use
+                for c in srv.poll():
+                    done[c[0]] = c
+            sub_t[i] = time.perf_counter()
+            srv.submit(queries[i][0], queries[i][1], i)
+            if i % 32 == 31:
+                for c in srv.poll():
+                    done[c[0]] = c
+        srv.drain(300.0)
+        for c in srv.poll():
+            done[c[0]] = c
+        srv.close()
+        ctx.close()
+        lat = np.array([done[i][4] for i in range(nq)])
+        end = max(sub_t[i] + done[i][4] for i in range(nq))
+        errors = sum(1 for i in range(nq) if done[i][1] != 0)
+        return {"offered_qps": qps, "queries": nq, "qps": nq / (end - sub_t[0]),
+                "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                "mean_batch": float(np.mean([done[i][2] for i in range(nq)])), "errors": errors}
+
+    nq = int(rate * seconds)
+    cont = run(64, 3, rate, nq)
+    fifo = run(1, 1, rate, nq)
+    # the served results of a sample equal the same plans run alone
+    actx = tqp.Context(local, 1 << 30)
+    same = True
+    for i in range(nq - 6, nq):
+        b = pool[i % SERVE_POOL]
+        before = [t.clone() for t in (b["nr"], b["s"], b["ng"], b["tot"], b["nj"], b["keys"], b["iv"])]
+        tqp.tqp_run_plan(actx, queries[i][0], queries[i][1])
+        actx.check()
+        after = [b["nr"], b["s"], b["ng"], b["tot"], b["nj"], b["keys"], b["iv"]]
+        same &= all(torch.equal(x, y) for x, y in zip(before, after))
+    actx.close()
+    rows = []
+    for qps in sweep:
+        n_s = int(qps * sweep_seconds)
+        rows.append({"offered_qps": qps, "continuous": run(64, 3, qps, n_s), "one_at_a_time": run(1, 1, qps, n_s)})
+
+    def best(key, limit_ms=10.0):
+        ok = [r[key]["qps"] for r in rows if r[key]["p99_ms"] <= limit_ms and r[key]["errors"] == 0]
+        return max(ok) if ok else None
+
+    tqp.tqp_dim_destroy(pdim)
+    pctx.close()
+    return {
+        "workload": f"{fact_rows // 1_000_000}M-row resident fact table (config-0 columns, {fact_rows * 30 / 1e9:.0f} GB) "
+                    f"+ prepared {dim_rows // 1_000_000}M-row dimension; open-loop Poisson arrivals; each query one of "
+                    "q1 group-by / q6 filter+ids+sum / join+group+top-100 over a seeded row range of "
+                    "log-uniform [10K, 5M] rows",
+        "rate_qps": rate, "seconds": seconds, "continuous_batching": cont, "one_at_a_time": fifo,
+        "served_equals_alone_sample": bool(same), "sweep": rows,
+        "qps_at_p99_le_10ms": {"continuous": best("continuous"), "one_at_a_time": best("one_at_a_time")},
+        "setup_s": setup_s,
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -415,6 +547,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="0 skips the CPU baseline")
     ap.add_argument("--rows", type=int, default=N_ROWS, help="smaller cases for profiling only")
     ap.add_argument("--no-operators", action="store_true", help="skip the secondary workloads")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving workload")
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
     args = ap.parse_args()
     globals()["N_ROWS"] = args.rows
     if args.impl == "reference":
@@ -505,6 +639,8 @@ def main():
     if rank == 0 and not args.no_operators:
         ops = secondary_workloads(tqp, torch, dev, local, 20)
         ops["batched_512"] = batched_workload(tqp, torch, dev, local, 20)
+        if not args.no_serving:
+            ops["serving"] = serving_workload(tqp, torch, dev, local, seconds=args.serve_seconds)
     if rank == 0:
         peak, peak_kind = measured_peaks()
         alg = algorithmic_bytes(N_ROWS, k)

@@ -2,6 +2,7 @@
 import math
 
 import numpy as np
+import pytest
 
 import datagen
 
@@ -70,3 +71,17 @@ def test_zipf_frequencies():
     for rank in (0, 1, 9, 99, 999):
         sd = math.sqrt(n * p[rank] * (1 - p[rank]))
         assert abs(c[rank] - n * p[rank]) < 5 * sd + 1
+
+
+def test_torch_generator_matches_numpy():
+    """The device generator (run here on CPU tensors) reproduces the NumPy values exactly."""
+    torch = pytest.importorskip("torch")
+    from datagen import torch_gen
+    for row0 in (0, 12345, (1 << 40) + 7):
+        a = datagen.fact_table(50_003, seed=datagen.DEFAULT_SEED + 3, row0=row0)
+        b = torch_gen.fact_table(50_003, seed=datagen.DEFAULT_SEED + 3, device="cpu", row0=row0)
+        for k in a:
+            assert np.array_equal(a[k], b[k].numpy()), (k, row0)
+    x = np.arange(1000, dtype=np.uint64) * np.uint64(0x9E3779B97F4A7C15)
+    got = torch_gen.splitmix64(torch.from_numpy(x.view(np.int64).copy())).numpy().view(np.uint64)
+    assert np.array_equal(got, datagen.splitmix64(x))

@@ -150,6 +150,20 @@ TQP_API size_t tqp_ctx_arena_bytes(const tqp_ctx* ctx);
  * autotuner and by tuning sweeps; results never depend on it. */
 TQP_API tqp_status tqp_ctx_set_tuning(tqp_ctx* ctx, int32_t tile_rows, int32_t stages, int32_t ctas_per_sm);
 
+/* Autotuning: with it on, the first call of each shape class (operator, log2
+ * of the row count, bytes per row it scans, output kinds) times every
+ * candidate launch shape -- rows per tile 1024..8192, 2..4 stages, 1..2 CTAs
+ * per SM, and for joins that build a hash table the load factor (capacity x1
+ * or x2) -- on the call's stream, synchronously, and keeps the fastest for
+ * later calls of the class; tqp_batch_create likewise picks the batch's tile
+ * size.  Results never depend on the choice.  A tqp_ctx_set_tuning override
+ * takes precedence.  The choices can be saved to and loaded from a JSON file
+ * (one entry per line: key, tile_rows, stages, ctas_per_sm, ht_scale, ms). */
+TQP_API tqp_status tqp_ctx_set_autotune(tqp_ctx* ctx, int32_t enable);
+TQP_API int32_t tqp_ctx_tuned_count(const tqp_ctx* ctx);
+TQP_API tqp_status tqp_ctx_save_tuning(const tqp_ctx* ctx, const char* path);
+TQP_API tqp_status tqp_ctx_load_tuning(tqp_ctx* ctx, const char* path);
+
 TQP_API const char* tqp_last_error(void);
 TQP_API const char* tqp_status_string(tqp_status s);
 TQP_API int tqp_version(void);

@@ -107,6 +107,10 @@ _SIGS = {
                                   C.POINTER(_P)]),
     "tqp_dim_groups": (C.c_int64, [_P]),
     "tqp_dim_destroy": (C.c_int, [_P]),
+    "tqp_ctx_set_autotune": (C.c_int, [_P, C.c_int32]),
+    "tqp_ctx_tuned_count": (C.c_int32, [_P]),
+    "tqp_ctx_save_tuning": (C.c_int, [_P, C.c_char_p]),
+    "tqp_ctx_load_tuning": (C.c_int, [_P, C.c_char_p]),
     "tqp_server_create": (C.c_int, [_P, C.c_void_p, C.POINTER(_P)]),
     "tqp_server_submit": (C.c_int, [_P, C.POINTER(Plan), C.POINTER(Result), C.c_uint64]),
     "tqp_server_poll": (C.c_int32, [_P, C.c_void_p, C.c_int32]),
@@ -238,6 +242,19 @@ class Context:
 
     def set_tuning(self, tile_rows: int = 0, stages: int = 0, ctas_per_sm: int = 0):
         _check(lib().tqp_ctx_set_tuning(self.h, int(tile_rows), int(stages), int(ctas_per_sm)))
+
+    def set_autotune(self, enable: bool = True):
+        _check(lib().tqp_ctx_set_autotune(self.h, int(bool(enable))))
+
+    @property
+    def tuned_count(self) -> int:
+        return int(lib().tqp_ctx_tuned_count(self.h))
+
+    def save_tuning(self, path: str):
+        _check(lib().tqp_ctx_save_tuning(self.h, os.fsencode(path)))
+
+    def load_tuning(self, path: str):
+        _check(lib().tqp_ctx_load_tuning(self.h, os.fsencode(path)))
 
     def set_wait_limit(self, polls: int):
         _check(lib().tqp_ctx_set_wait_limit(self.h, int(polls)))

@@ -266,6 +266,7 @@ using namespace tqp;
 struct tqp_batch {
     tqp_ctx* ctx = nullptr;
     bool persistent = false;  // scratch from the arena's long-lived top region
+    int tile = tqp::kBatchTile;  // rows per tile of the scans (clamped per job to what fits)
     size_t top_before = 0;
     size_t top_after = 0;
     // lowered jobs
@@ -336,14 +337,23 @@ static unsigned long long* counter(tqp_batch* b) {
     return p;
 }
 
-// Staged geometry of one scan in the batch (fixed tile and stage count).
-static tqp_status batch_geom(const tqp_ctx* ctx, const tqp_table* t, std::vector<int> staged, ScanGeom* G) {
-    const tqp_tuning tu{kBatchTile, kBatchStages, 2};
-    size_t smem = 0;
+// Staged geometry of one scan in the batch: the batch's tile size (3 stages),
+// halved until the stages fit beside the body of the job's kind.
+static tqp_status batch_geom(const tqp_batch* b, const tqp_table* t, std::vector<int> staged, int body_bytes,
+                             ScanGeom* G) {
     std::sort(staged.begin(), staged.end());
     staged.erase(std::unique(staged.begin(), staged.end()), staged.end());
     if (static_cast<int>(staged.size()) > kMaxStaged) staged.resize(kMaxStaged);
-    return make_geom(ctx, t, staged, tu, 0, G, &smem);
+    int stage_row = 0;
+    for (int c : staged) stage_row += t->cols[c].type == TQP_I64 ? 8 : (t->cols[c].type == TQP_I32 ? 4 : 1);
+    const long long room = static_cast<long long>(b->ctx->smem_optin) - 1024 - kHeaderBytes - kJobBytes - body_bytes;
+    int T = b->tile;
+    while (T > kBatchTile && static_cast<long long>(kBatchStages) * (static_cast<long long>(T) * stage_row +
+                                                                     128LL * kMaxStaged) > room)
+        T /= 2;
+    const tqp_tuning tu{T, kBatchStages, 2, 1};
+    size_t smem = 0;
+    return make_geom(b->ctx, t, staged, tu, 0, G, &smem);
 }
 
 static tqp_status add_filter_job(tqp_batch* b, const tqp_plan* p, const tqp_result* r, bool ids, bool with_sum,
@@ -363,7 +373,7 @@ static tqp_status add_filter_job(tqp_batch* b, const tqp_plan* p, const tqp_resu
         A.has_sum = 1;
         if (ncond == 0) expr_cols(A.sum, staged);
     }
-    TQP_TRY(batch_geom(ctx, p->fact, staged, &A.G));
+    TQP_TRY(batch_geom(b, p->fact, staged, body_bytes<FilterBody>(), &A.G));
     lower_fast(A.cond, A.ncond, A.G, A.cf, &A.fast);
     A.acc = counter(b);
     A.d_count = d_count;
@@ -437,7 +447,7 @@ static tqp_status add_group_job(tqp_batch* b, const tqp_plan* p, const tqp_resul
     for (int i = 0; i < ncond; ++i) staged.push_back(A.cond[i].col);
     for (int i = 0; i < p->ngc; ++i) staged.push_back(p->group_cols[i]);
     for (int a = 1; a < A.S.nacc; ++a) expr_cols(A.S.acc_expr[a - 1], staged);
-    TQP_TRY(batch_geom(ctx, t, staged, &A.G));
+    TQP_TRY(batch_geom(b, t, staged, body_bytes<GroupBody>(), &A.G));
     lower_fast(A.cond, A.ncond, A.G, A.cf, &A.fast);
     lower_group_fast(&A);
     const long long maxg = p->max_groups > 0 ? p->max_groups : std::max<long long>(1, r->capacity_groups);
@@ -594,7 +604,7 @@ static tqp_status add_join_job(tqp_batch* b, const tqp_plan* p, const tqp_result
     staged.push_back(p->fact_fk);
     if (A.has_sum) expr_cols(A.sum, staged);
     for (int a = 1; a < A.S.nacc; ++a) expr_cols(A.S.acc_expr[a - 1], staged);
-    TQP_TRY(batch_geom(ctx, F, staged, &A.G));
+    TQP_TRY(batch_geom(b, F, staged, body_bytes<PlanJoinBody>(), &A.G));
     lower_fast(A.cond, A.ncond, A.G, A.cf, &A.fast);
     lower_join_fast(&A);
     A.acc = counter(b);
@@ -984,6 +994,45 @@ static void release(tqp_batch* b) {
     top_close(b->ctx, b->top_before, b->top_after);
 }
 
+// Autotuning of a batch: build it with each candidate tile size, time one
+// replay (after a warm-up replay) and keep the fastest.
+static tqp_status tune_batch_tile(tqp_ctx* ctx, const tqp_plan* plans, const tqp_result* res, int32_t n, int* tile) {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    TQP_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    TQP_CUDA(cudaEventCreate(&ev[0]));
+    TQP_CUDA(cudaEventCreate(&ev[1]));
+    double best = 1e30;
+    for (int T = kBatchTile; T <= 4 * kBatchTile; T *= 2) {
+        tqp_batch* c = new (std::nothrow) tqp_batch();
+        if (!c) break;
+        c->tile = T;
+        top_open(ctx);
+        tqp_status s = batch_create(ctx, plans, res, n, c);
+        c->top_after = ctx->top;
+        if (s == TQP_OK) {
+            cudaGraphLaunch(c->exec, st);
+            cudaEventRecord(ev[0], st);
+            cudaGraphLaunch(c->exec, st);
+            cudaEventRecord(ev[1], st);
+            float ms = 0.f;
+            if (cudaEventSynchronize(ev[1]) == cudaSuccess && cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess &&
+                ms < best) {
+                best = ms;
+                *tile = T;
+            }
+        }
+        cudaStreamSynchronize(st);
+        release(c);
+        delete c;
+    }
+    clear_error();
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    cudaStreamDestroy(st);
+    return TQP_OK;
+}
+
 }  // namespace tqp
 
 extern "C" {
@@ -995,8 +1044,11 @@ tqp_status tqp_batch_create(tqp_ctx* ctx, const tqp_plan* plans, const tqp_resul
     *out = nullptr;
     DeviceGuard g(ctx->device);
     if (!g.ok) return fail(TQP_ERR_CUDA, "cannot select device %d", ctx->device);
+    int tile = kBatchTile;
+    if (ctx->tuner && ctx->tuner->enabled) TQP_TRY(tune_batch_tile(ctx, plans, res, n, &tile));
     tqp_batch* b = new (std::nothrow) tqp_batch();
     if (!b) return fail(TQP_ERR_OUT_OF_MEMORY, "host allocation failed");
+    b->tile = tile;
     top_open(ctx);
     const tqp_status s = batch_create(ctx, plans, res, n, b);
     b->top_after = ctx->top;

@@ -323,7 +323,8 @@ static int esize_host(int type) { return type == TQP_I64 ? 8 : (type == TQP_I32 
 
 tqp_tuning default_tuning(const tqp_ctx* ctx, int bytes_per_row, int body_smem) {
     if (ctx->forced.tile_rows > 0) return ctx->forced;
-    tqp_tuning tu;
+    tqp_tuning tu{0, 0, 0, 1};
+    if (ctx->tuner && ctx->cur_key[0] && ctx->tuner->lookup(ctx->cur_key, &tu)) return tu;
     const int per_sm = 227 * 1024;
     // Two CTAs per SM: one can compute while the other waits on look-back.
     int budget = per_sm / 2 - kHeaderBytes - body_smem - 1024;
@@ -482,6 +483,7 @@ tqp_status tqp_ctx_destroy(tqp_ctx* ctx) {
     clear_error();
     if (!ctx) return TQP_OK;
     tqp_status s = TQP_OK;
+    tuner_destroy(ctx);
     if (ctx->owns_arena) {
         DeviceGuard g(ctx->device);
         cudaError_t e = cudaFree(ctx->arena);
@@ -505,7 +507,7 @@ tqp_status tqp_ctx_set_tuning(tqp_ctx* ctx, int32_t tile_rows, int32_t stages, i
     clear_error();
     TQP_TRY(check_ctx(ctx));
     if (tile_rows == 0 && stages == 0 && ctas_per_sm == 0) {
-        ctx->forced = tqp_tuning{0, 0, 0};
+        ctx->forced = tqp_tuning{0, 0, 0, 0};
         return TQP_OK;
     }
     if (tile_rows < kRowQuantum || tile_rows > kMaxTileRows || tile_rows % kRowQuantum)
@@ -513,7 +515,7 @@ tqp_status tqp_ctx_set_tuning(tqp_ctx* ctx, int32_t tile_rows, int32_t stages, i
                     kRowQuantum, kMaxTileRows);
     if (stages < 2 || stages > kMaxStages) return fail(TQP_ERR_INVALID_ARG, "stages must be in [2, %d]", kMaxStages);
     if (ctas_per_sm < 1 || ctas_per_sm > 2) return fail(TQP_ERR_INVALID_ARG, "ctas_per_sm must be 1 or 2");
-    ctx->forced = tqp_tuning{tile_rows, stages, ctas_per_sm};
+    ctx->forced = tqp_tuning{tile_rows, stages, ctas_per_sm, 1};
     return TQP_OK;
 }
 

@@ -25,6 +25,8 @@
 // here come straight from counts that are complete when k_compact starts.
 #include <mutex>
 
+#include <cstdio>
+
 #include "host.h"
 #include "bodies.cuh"
 
@@ -154,9 +156,18 @@ extern "C" tqp_status tqp_filter(tqp_ctx* ctx, const tqp_table* t, const tqp_pre
     if (d_row_ids && capacity < 0) return fail(TQP_ERR_INVALID_ARG, "capacity < 0");
     DeviceGuard g(ctx->device);
     if (!g.ok) return fail(TQP_ERR_CUDA, "cannot select device %d", ctx->device);
-    arena_reset(ctx);
-    return launch_filter(ctx, t, preds, npreds, sum_expr, d_sum, d_row_ids, capacity, d_count,
-                         static_cast<cudaStream_t>(stream), nullptr);
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::vector<int> cols;
+    for (int i = 0; i < npreds && i < TQP_MAX_PREDS && preds; ++i) cols.push_back(preds[i].col);
+    if (npreds == 0) expr_col_ids(sum_expr, cols);
+    char key[96];
+    snprintf(key, sizeof(key), "filter r%d b%d i%d s%d", rows_class(t->num_rows), row_bytes(t, cols),
+             d_row_ids ? 1 : 0, sum_expr ? 1 : 0);
+    auto run = [&]() {
+        arena_reset(ctx);
+        return launch_filter(ctx, t, preds, npreds, sum_expr, d_sum, d_row_ids, capacity, d_count, st, nullptr);
+    };
+    return tuned(ctx, key, st, false, run);
 }
 
 // ---- allocation-free variant (tqp_filter_noalloc) ------------------------------

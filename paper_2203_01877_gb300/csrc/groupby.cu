@@ -17,6 +17,8 @@
 //     count.
 // int64 addition is associative and commutative, so the sums do not depend on
 // the order atomics land in.
+#include <cstdio>
+
 #include "host.h"
 #include "group.cuh"
 #include "bodies.cuh"
@@ -343,8 +345,18 @@ extern "C" tqp_status tqp_groupby_agg(tqp_ctx* ctx, const tqp_table* t, const tq
     if (naggs > 0 && !d_ivals) return fail(TQP_ERR_INVALID_ARG, "d_ivals is NULL");
     DeviceGuard g(ctx->device);
     if (!g.ok) return fail(TQP_ERR_CUDA, "cannot select device %d", ctx->device);
-    arena_reset(ctx);
-    return launch_groupby(ctx, t, preds, npreds, group_cols, ngc, aggs, naggs, d_keys, d_ivals, d_fvals,
-                          capacity_groups, d_num_groups, static_cast<cudaStream_t>(stream), capacity_groups, 0, 0,
-                          nullptr);
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::vector<int> cols;
+    for (int i = 0; i < npreds && i < TQP_MAX_PREDS && preds; ++i) cols.push_back(preds[i].col);
+    for (int i = 0; i < ngc && i < TQP_MAX_GROUP_COLS && group_cols; ++i) cols.push_back(group_cols[i]);
+    for (int a = 0; a < naggs && a < TQP_MAX_AGGS && aggs; ++a)
+        if (aggs[a].fn != TQP_COUNT) expr_col_ids(&aggs[a].expr, cols);
+    char key[96];
+    snprintf(key, sizeof(key), "groupby r%d b%d g%d a%d", rows_class(t->num_rows), row_bytes(t, cols), ngc, naggs);
+    auto run = [&]() {
+        arena_reset(ctx);
+        return launch_groupby(ctx, t, preds, npreds, group_cols, ngc, aggs, naggs, d_keys, d_ivals, d_fvals,
+                              capacity_groups, d_num_groups, st, capacity_groups, 0, 0, nullptr);
+    };
+    return tuned(ctx, key, st, false, run);
 }

@@ -8,6 +8,9 @@
 #include <cstddef>
 #include <cstdint>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -19,7 +22,25 @@ struct tqp_tuning {
     int tile_rows;      // T, multiple of tqp::kRowQuantum
     int stages;         // 2..kMaxStages
     int ctas_per_sm;    // 0: as many as fit
+    int ht_scale;       // hash-table capacity multiplier (1 or 2: half the load factor); 0 = 1
 };
+
+namespace tqp {
+// Autotuner state: the chosen launch shape (and its time) per shape class.
+struct Tuner {
+    bool enabled = false;
+    std::mutex mu;
+    std::map<std::string, tqp_tuning> table;
+    std::map<std::string, double> ms;
+    bool lookup(const char* key, tqp_tuning* out) {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = table.find(key);
+        if (it == table.end()) return false;
+        *out = it->second;
+        return true;
+    }
+};
+}  // namespace tqp
 
 struct tqp_ctx {
     int device;
@@ -35,6 +56,8 @@ struct tqp_ctx {
     int* d_err;            // latched device error (persistent, arena start)
     long long wait_cap;
     tqp_tuning forced;     // tile_rows == 0: no override
+    tqp::Tuner* tuner;     // autotuner state (owned by the context; shared by sub-contexts)
+    char cur_key[96];      // shape class of the running call ("" outside tuned calls)
 };
 
 namespace tqp {
@@ -109,6 +132,27 @@ tqp_status make_geom(const tqp_ctx* ctx, const tqp_table* t, std::vector<int> st
 // Default tuning for a scan staging `bytes_per_row` bytes per row (the
 // context's override, when set, wins).
 tqp_tuning default_tuning(const tqp_ctx* ctx, int bytes_per_row, int body_smem);
+
+// Hash-table capacity multiplier of the running call (forced or tuned; 1 by default).
+int ht_scale(const tqp_ctx* ctx);
+
+// Run `run` (a whole operator call, idempotent) under the tuning of shape
+// class `key`: with autotuning on and `key` new, every candidate launch shape
+// (and hash-table load factor when `has_ht`) is timed on `stream` first and
+// the fastest is remembered; the outputs are the same for every candidate.
+tqp_status tuned_call(tqp_ctx* ctx, const char* key, cudaStream_t stream, bool has_ht, tqp_status (*run)(void*),
+                      void* arg);
+template <class F>
+tqp_status tuned(tqp_ctx* ctx, const char* key, cudaStream_t stream, bool has_ht, F& f) {
+    return tuned_call(ctx, key, stream, has_ht, [](void* a) { return (*static_cast<F*>(a))(); }, &f);
+}
+void tuner_destroy(tqp_ctx* ctx);
+// Bytes per row of the distinct columns `cols` of t.
+int row_bytes(const tqp_table* t, std::vector<int> cols);
+// Columns an expression reads (expression may be NULL).
+void expr_col_ids(const tqp_expr* e, std::vector<int>& cols);
+// floor(log2(max(n, 1))): the row-count part of a shape class.
+int rows_class(long long n);
 
 // Persistent grid size for an engine kernel.
 int engine_grid(const tqp_ctx* ctx, const void* kernel, size_t smem, int64_t ntiles, int ctas_per_sm);

@@ -16,6 +16,8 @@
 //          over chunks gives each chunk's output offset, and each row's run
 //          is copied out as (build, probe) pairs.
 // Keys compare by their int64 value; int32, int64 and uint8 key columns mix.
+#include <cstdio>
+
 #include "host.h"
 #include "join.cuh"
 #include "dimgroups.cuh"
@@ -93,7 +95,7 @@ tqp_status ht_chain_insert_launch(const tqp_ctx* ctx, const tqp_table* build, in
 tqp_status ht_build_chain(tqp_ctx* ctx, const tqp_table* build, int32_t key_col, JoinHT* H, uint32_t** next,
                           cudaStream_t stream) {
     const long long n = build->num_rows;
-    H->cap = ht_cap_dense(n);
+    H->cap = ht_cap_dense(n) * ht_scale(ctx);
     H->slots = static_cast<uint4*>(arena_alloc(ctx, static_cast<size_t>(H->cap + 1) * sizeof(uint4)));
     *next = static_cast<uint32_t*>(arena_alloc(ctx, static_cast<size_t>(n > 0 ? n : 1) * 4));
     long long* meta = static_cast<long long*>(arena_alloc(ctx, 64));
@@ -135,7 +137,7 @@ size_t ht_bytes(long long n_build) {
 
 tqp_status ht_build(tqp_ctx* ctx, const tqp_table* build, int32_t key_col, JoinHT* H, cudaStream_t stream) {
     const long long n = build->num_rows;
-    H->cap = ht_cap(n);
+    H->cap = ht_cap(n) * ht_scale(ctx);
     H->meta = nullptr;
     H->slots = static_cast<uint4*>(arena_alloc(ctx, static_cast<size_t>(H->cap + 1) * sizeof(uint4)));
     const long long nn = n > 0 ? n : 1;
@@ -355,7 +357,14 @@ extern "C" tqp_status tqp_hash_join(tqp_ctx* ctx, const tqp_table* build, int32_
         return fail(TQP_ERR_INVALID_ARG, "output arrays are NULL");
     DeviceGuard g(ctx->device);
     if (!g.ok) return fail(TQP_ERR_CUDA, "cannot select device %d", ctx->device);
-    arena_reset(ctx);
-    return launch_hash_join(ctx, build, build_key, probe, probe_key, d_build_idx, d_probe_idx, capacity, d_count,
-                            static_cast<cudaStream_t>(stream));
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char key[96];
+    snprintf(key, sizeof(key), "hashjoin r%d b%d n%d", rows_class(probe->num_rows),
+             row_bytes(probe, std::vector<int>{probe_key}), rows_class(build->num_rows));
+    auto run = [&]() {
+        arena_reset(ctx);
+        return launch_hash_join(ctx, build, build_key, probe, probe_key, d_build_idx, d_probe_idx, capacity,
+                                d_count, st);
+    };
+    return tuned(ctx, key, st, true, run);
 }

@@ -11,6 +11,7 @@
 // table: the join result is never materialised.  Group keys are dimension
 // columns, so each dimension row's group slot is resolved once, before the
 // probe (k_dim_groups), and a probe costs one table lookup plus atomics.
+#include <cstdio>
 #include <new>
 
 #include "host.h"
@@ -458,5 +459,19 @@ extern "C" tqp_status tqp_run_plan(tqp_ctx* ctx, const tqp_plan* plan, const tqp
     TQP_TRY(check_ctx(ctx));
     DeviceGuard g(ctx->device);
     if (!g.ok) return fail(TQP_ERR_CUDA, "cannot select device %d", ctx->device);
-    return run_plan_one(ctx, plan, res, static_cast<cudaStream_t>(stream));
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (!plan || !res || !plan->fact) return run_plan_one(ctx, plan, res, st);  // reports the error
+    std::vector<int> cols;
+    for (int i = 0; i < plan->npreds && i < TQP_MAX_PREDS; ++i) cols.push_back(plan->preds[i].col);
+    if (plan->dim) cols.push_back(plan->fact_fk);
+    for (int i = 0; i < plan->ngc && i < TQP_MAX_GROUP_COLS && !plan->dim; ++i) cols.push_back(plan->group_cols[i]);
+    for (int a = 0; a < plan->naggs && a < TQP_MAX_AGGS; ++a)
+        if (plan->aggs[a].fn != TQP_COUNT) expr_col_ids(&plan->aggs[a].expr, cols);
+    if (plan->has_sum) expr_col_ids(&plan->sum_expr, cols);
+    char key[96];
+    snprintf(key, sizeof(key), "plan r%d b%d j%d p%d g%d k%d", rows_class(plan->fact->num_rows),
+             row_bytes(plan->fact, cols), plan->dim ? rows_class(plan->dim->num_rows) + 1 : 0,
+             plan->prepared ? 1 : 0, plan->ngc + plan->naggs > 0 ? 1 : 0, plan->topk > 0 ? 1 : 0);
+    auto run = [&]() { return run_plan_one(ctx, plan, res, st); };
+    return tuned(ctx, key, st, plan->dim != nullptr && !plan->prepared, run);
 }

@@ -223,6 +223,7 @@ def secondary_workloads(tqp, torch, dev, local, reps):
     cols = [torch.from_numpy(t[k]).to(dev) for k in ("date", "flag", "status", "quantity", "price", "discount")]
     table = tqp.TableRef(cols)
     ctx = tqp.Context(local, 64 << 20)
+    ctx.set_autotune(True)
     aggs = [("sum", [("col", 3)]), ("sum", [("col", 4)]),
             ("sum", [("col", 4), ("const", 100), ("col", 5), "sub", "mul"]), ("count", None), ("avg", [("col", 4)])]
     keys = torch.zeros(64 * 2, dtype=torch.int64, device=dev)
@@ -251,6 +252,7 @@ def secondary_workloads(tqp, torch, dev, local, reps):
     F = tqp.TableRef([torch.from_numpy(pr["fk"]).to(dev), torch.from_numpy(pr["value"]).to(dev)])
     D = tqp.TableRef([torch.from_numpy(dim["key"]).to(dev), torch.from_numpy(dim["payload"]).to(dev)])
     ctx = tqp.Context(local, 1 << 30)
+    ctx.set_autotune(True)
     k = 100
     rk = torch.zeros(k, dtype=torch.int64, device=dev)
     riv = torch.zeros(k * 2, dtype=torch.int64, device=dev)
@@ -357,6 +359,7 @@ def batched_workload(tqp, torch, dev, local, reps, n_plans=BATCH_PLANS):
     scan_rows, probe_rows, alg_bytes = meta["scan_rows"], meta["probe_rows"], meta["alg_bytes"]
     stream = torch.cuda.current_stream()
     ctx = tqp.Context(local, 4 << 30)
+    ctx.set_autotune(True)  # both arms: launch shapes (and the batch's tile size) picked by timing candidates
     snapshot = lambda: batched_snapshot(torch, keep)  # noqa: E731
 
     def seq():
@@ -537,6 +540,62 @@ def serving_workload(tqp, torch, dev, local, seconds=10.0, rate=2000.0, sweep=(2
     }
 
 
+def profile_case(args):
+    """One operator at a profiling size, for ncu: the first call autotunes, the next `--steps` calls run
+    inside the NVTX range "tqp_profile" (capture them with --nvtx --nvtx-include "tqp_profile/")."""
+    import torch
+    import paper_2203_01877_gb300 as tqp
+    dev = torch.device("cuda:0")
+    st = torch.cuda.current_stream()
+    ctx = tqp.Context(0, 2 << 30)
+    ctx.set_autotune(True)
+    n = args.rows
+    if args.case == "filter":
+        t = datagen.fact_table(n, seed=datagen.DEFAULT_SEED + 1, cols=["date", "discount", "quantity", "price"])
+        T = tqp.TableRef([torch.from_numpy(t[c]).to(dev) for c in ("date", "discount", "quantity", "price")])
+        ids = torch.empty(n, dtype=torch.int32, device=dev)
+        cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+        sm = torch.zeros(1, dtype=torch.int64, device=dev)
+        fn = lambda: tqp.tqp_filter(ctx, T, PREDS, EXPR, sm, ids, n, cnt, st)  # noqa: E731
+    elif args.case == "groupby":
+        t = datagen.fact_table(n, seed=datagen.DEFAULT_SEED)
+        T = tqp.TableRef([torch.from_numpy(t[c]).to(dev) for c in ("date", "flag", "status", "quantity", "price",
+                                                                     "discount")])
+        aggs = [("sum", [("col", 3)]), ("sum", [("col", 4)]),
+                ("sum", [("col", 4), ("const", 100), ("col", 5), "sub", "mul"]), ("count", None),
+                ("avg", [("col", 4)])]
+        keys = torch.zeros(128, dtype=torch.int64, device=dev)
+        iv = torch.zeros(320, dtype=torch.int64, device=dev)
+        fv = torch.zeros(320, dtype=torch.float64, device=dev)
+        ng = torch.zeros(1, dtype=torch.int64, device=dev)
+        fn = lambda: tqp.tqp_groupby_agg(ctx, T, [(0, "le", 2450)], [1, 2], aggs, keys, iv, fv, 64, ng, st)  # noqa
+    elif args.case == "join":
+        nb, ngr = 1_500_000, 150_000
+        dim = datagen.dim_table(nb, ngr, seed=datagen.DEFAULT_SEED + 2)
+        pr = datagen.probe_table(n, nb, seed=datagen.DEFAULT_SEED + 2)
+        F = tqp.TableRef([torch.from_numpy(pr["fk"]).to(dev), torch.from_numpy(pr["value"]).to(dev)])
+        D = tqp.TableRef([torch.from_numpy(dim["key"]).to(dev), torch.from_numpy(dim["payload"]).to(dev)])
+        z = lambda m: torch.zeros(m, dtype=torch.int64, device=dev)  # noqa: E731
+        rk, riv, rng_, rtot, rj = z(100), z(200), z(1), z(1), z(1)
+        plan = tqp.make_plan(F, (), D, 0, 0, [3], [("sum", [("col", 1)]), ("count", None)], None, 100, 0)
+        res = tqp.make_result(None, 0, None, None, rk, riv, None, 100, rng_, rtot, rj)
+        fn = lambda: tqp.tqp_run_plan(ctx, plan, res, st)  # noqa: E731
+    else:  # the batched 512-plan mix
+        plans, results, keep, meta = batched_plans(tqp, torch, dev)
+        batch = tqp.tqp_batch_create(ctx, plans, results)
+        fn = lambda: tqp.tqp_batch_run(batch, st)  # noqa: E731
+    fn()
+    ctx.check(st)
+    torch.cuda.nvtx.range_push("tqp_profile")
+    for _ in range(args.steps):
+        fn()
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    ctx.check(st)
+    print(json.dumps({"case": args.case, "rows": n, "launched_steps": args.steps}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -549,10 +608,14 @@ def main():
     ap.add_argument("--no-operators", action="store_true", help="skip the secondary workloads")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving workload")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--case", choices=["filter", "groupby", "join", "batch"], default=None,
+                    help="profiling: run one operator (first call autotunes; --steps calls in NVTX range tqp_profile)")
     args = ap.parse_args()
     globals()["N_ROWS"] = args.rows
     if args.impl == "reference":
         return run_reference(args)
+    if args.case:
+        return profile_case(args)
 
     import torch
     import torch.distributed as dist
@@ -571,6 +634,7 @@ def main():
     cols = [torch.from_numpy(a).to(dev) for a in host]
     table = tqp.TableRef(cols)
     ctx = tqp.Context(local, 64 << 20)
+    ctx.set_autotune(True)  # the first (warm-up) call picks the launch shape
     ids = torch.empty(N_ROWS, dtype=torch.int32, device=dev)
     cnt = torch.zeros(1, dtype=torch.int64, device=dev)
     s = torch.zeros(1, dtype=torch.int64, device=dev)

@@ -15,7 +15,7 @@ namespace tqp {
 
 constexpr int kCompactRows = 65536;                  // rows per compaction block of the selection mask
 constexpr int kCompactWords = kCompactRows / kWarp;  // 2048 mask words
-constexpr int kCompactThreads = 256;
+constexpr int kCompactThreads = 1024;
 
 // Count one (chunk, warp) completion; true for the very last one of the scan.
 __device__ __forceinline__ bool last_completion(unsigned long long* done, long long nchunks) {
@@ -860,64 +860,60 @@ void lower_join_fast(PlanJoinArgs* A);
 // ---- selection-mask expansion (second filter kernel) ------------------------------
 
 // Expand the selection mask of rows [b * kCompactRows, ...) into row ids.
-// Called by a whole block of kCompactThreads threads for mask block b.
+// Called by a whole block of kCompactThreads threads for mask block b: each
+// thread takes two consecutive mask words (64 rows), one block-wide exclusive
+// scan of their bit counts gives every thread its output offset, and each
+// thread writes the ids of its own set bits (ascending, so the output is).
 __device__ __forceinline__ void compact_block(const uint32_t* __restrict__ mask, const uint32_t* __restrict__ block_tot,
                                               long long n, int32_t* __restrict__ row_ids, long long capacity,
                                               long long b) {
+    static_assert(kCompactWords == 2 * kCompactThreads, "two mask words per thread");
     constexpr int W = kCompactThreads / kWarp;
     __shared__ unsigned long long red[W];
-    __shared__ uint32_t wtot[2][W];
+    __shared__ uint32_t wsum[W];
     const int lane = threadIdx.x % kWarp, w = threadIdx.x / kWarp;
     // offset of this block: every earlier block's total
     unsigned long long before_blocks = 0;
     for (long long i = threadIdx.x; i < b; i += kCompactThreads) before_blocks += block_tot[i];
+    // this thread's two words
+    const long long nwords = (n + kWarp - 1) / kWarp;
+    const long long wi = b * kCompactWords + 2 * threadIdx.x;
+    const uint32_t m0 = wi < nwords ? mask[wi] : 0u;
+    const uint32_t m1 = wi + 1 < nwords ? mask[wi + 1] : 0u;
+    const uint32_t c = __popc(m0) + __popc(m1);
+    uint32_t incl = c;
+#pragma unroll
+    for (int o = 1; o < kWarp; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) before_blocks += __shfl_xor_sync(0xffffffffu, before_blocks, o);
+    if (lane == kWarp - 1) wsum[w] = incl;
     if (lane == 0) red[w] = before_blocks;
     __syncthreads();
-    unsigned long long running = 0;
+    unsigned long long base = 0;
+    uint32_t before_warps = 0;
 #pragma unroll
-    for (int i = 0; i < W; ++i) running += red[i];
-
-    const long long nwords = (n + kWarp - 1) / kWarp;
-    const long long w0 = b * kCompactWords;
-    const long long w1 = (w0 + kCompactWords < nwords) ? w0 + kCompactWords : nwords;
-    const uint32_t lt = lanemask_lt();
-    int par = 0;
-    for (long long base = w0; base < w1; base += kCompactThreads) {
-        const long long wi = base + threadIdx.x;
-        const uint32_t word = wi < w1 ? mask[wi] : 0u;
-        const uint32_t c = __popc(word);
-        uint32_t incl = c;
-#pragma unroll
-        for (int o = 1; o < kWarp; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        if (lane == kWarp - 1) wtot[par][w] = incl;
-        __syncthreads();
-        unsigned long long before = 0, round_total = 0;
-#pragma unroll
-        for (int i = 0; i < W; ++i) {
-            const uint32_t x = wtot[par][i];
-            before += (i < w) ? x : 0u;
-            round_total += x;
-        }
-        const unsigned long long my_off = running + before + (incl - c);
-        uint32_t nz = __ballot_sync(0xffffffffu, word != 0u);
-        while (nz) {
-            const int j = __ffs(nz) - 1;
-            nz &= nz - 1;
-            const uint32_t wj = __shfl_sync(0xffffffffu, word, j);
-            const unsigned long long oj = __shfl_sync(0xffffffffu, my_off, j);
-            if ((wj >> lane) & 1u) {
-                const unsigned long long pos = oj + __popc(wj & lt);
-                if (pos < static_cast<unsigned long long>(capacity))
-                    row_ids[pos] = static_cast<int32_t>((base + w * kWarp + j) * kWarp + lane);
-            }
-        }
-        running += round_total;
-        par ^= 1;
+    for (int i = 0; i < W; ++i) {
+        base += red[i];
+        before_warps += i < w ? wsum[i] : 0u;
+    }
+    unsigned long long pos = base + before_warps + (incl - c);
+    const long long row0 = wi * kWarp;
+    uint32_t m = m0;
+    while (m) {
+        const int bit = __ffs(m) - 1;
+        m &= m - 1;
+        if (pos < static_cast<unsigned long long>(capacity)) row_ids[pos] = static_cast<int32_t>(row0 + bit);
+        ++pos;
+    }
+    m = m1;
+    while (m) {
+        const int bit = __ffs(m) - 1;
+        m &= m - 1;
+        if (pos < static_cast<unsigned long long>(capacity)) row_ids[pos] = static_cast<int32_t>(row0 + kWarp + bit);
+        ++pos;
     }
 }
 

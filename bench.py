@@ -208,8 +208,22 @@ def _time_launches(torch, fn, reps, flush=None, stream=None):
     return statistics.median(times)
 
 
-def secondary_workloads(tqp, torch, dev, local, reps):
-    """The other two analytical shapes, timed per launch (reported beside the headline)."""
+def oracle_plan_rate(spec, rows, seconds):
+    """Rows/s of the CPU oracle's plan evaluator (one thread) on `spec`: runs until `seconds` pass (at least
+    twice), median of the later half."""
+    import oracle
+    times = []
+    t_end = time.perf_counter() + seconds
+    while len(times) < 2 or (time.perf_counter() < t_end and len(times) < 8):
+        t0 = time.perf_counter()
+        oracle.run_plan(want_pairs=False, cap_groups=None, **spec)
+        times.append(time.perf_counter() - t0)
+    return rows / statistics.median(times[len(times) // 2:]), len(times)
+
+
+def secondary_workloads(tqp, torch, dev, local, reps, cpu_seconds=0.0):
+    """The other two analytical shapes, timed per launch (reported beside the headline), each with the CPU
+    oracle timed on the same inputs (config 0 in full, config 2 on a 6M-row probe sample)."""
     out = {}
     stream = torch.cuda.current_stream()
     flush_buf = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # 512 MB > L2
@@ -243,6 +257,12 @@ def secondary_workloads(tqp, torch, dev, local, reps):
         "ms_l2_resident": hot, "ms_after_l2_flush": cold, "rows_per_s": n / (cold / 1e3),
         "algorithmic_bytes": n * 26, "achieved_gbs_after_flush": n * 26 / (cold / 1e3) / 1e9,
         "groups": int(ng.item())}
+    if cpu_seconds > 0:
+        spec = dict(fact=[t[k] for k in ("date", "flag", "status", "quantity", "price", "discount")],
+                    preds=[(0, "le", 2450)], group_cols=[1, 2], aggs=aggs, want_row_ids=False)
+        rate, runs = oracle_plan_rate(spec, n, cpu_seconds)
+        out["groupby_1M_6groups"]["cpu_baseline"] = {"value": rate, "unit": "rows/s", "cores": 1, "kind": "oracle",
+                                                     "sample": f"the full 1M-row workload, {runs} runs"}
     ctx.close()
 
     # hash join + 150K-group aggregation + top-100
@@ -274,6 +294,16 @@ def secondary_workloads(tqp, torch, dev, local, reps):
         "ms": ms, "probe_rows_per_s": npr / (ms / 1e3), "algorithmic_bytes": alg,
         "achieved_gbs": alg / (ms / 1e3) / 1e9, "joined_rows": int(rj.item()), "groups": int(rtot.item())}
     ctx.close()
+    if cpu_seconds > 0:
+        ns = 6_000_000
+        spec = dict(fact=[pr["fk"][:ns], pr["value"][:ns]], dim=[dim["key"], dim["payload"]], fact_fk=0, dim_key=0,
+                    group_cols=[3], aggs=[("sum", [("col", 1)]), ("count", None)], topk=k, topk_agg=0,
+                    want_row_ids=False)
+        rate, runs = oracle_plan_rate(spec, ns, cpu_seconds)
+        out["join_group_top100"]["cpu_baseline"] = {"value": rate, "unit": "probe rows/s", "cores": 1,
+                                                    "kind": "oracle",
+                                                    "sample": f"first {ns} probe rows with the full build side, "
+                                                              f"{runs} runs"}
     return out
 
 
@@ -701,7 +731,7 @@ def main():
 
     ops = None
     if rank == 0 and not args.no_operators:
-        ops = secondary_workloads(tqp, torch, dev, local, 20)
+        ops = secondary_workloads(tqp, torch, dev, local, 20, cpu_seconds=min(args.cpu_seconds, 5.0))
         ops["batched_512"] = batched_workload(tqp, torch, dev, local, 20)
         if not args.no_serving:
             ops["serving"] = serving_workload(tqp, torch, dev, local, seconds=args.serve_seconds)

@@ -19,7 +19,9 @@
 //             layout and occupancy
 //   compact   selection masks -> row ids
 //   finalize  one CTA per small group table (keys ascending)
-//   top-k     the bitonic tournament, one launch per level for all plans
+//   top-k     radix select of the k-th largest (three histogram passes, a
+//             collect and one sort per plan); the bitonic tournament, one
+//             launch per level, only for plans whose select ends in ties
 // A tqp_batch is lowered and captured into a CUDA graph once; each run is
 // one graph launch.  Plans outside these shapes (large group tables without
 // top-k) run through the single-plan path after the batch's kernels, inside
@@ -106,9 +108,13 @@ struct TopJob {
     int32_t k;
     int32_t rank_acc;
     TopBuf buf[2];
+    TopBuf cand;
+    TopSel* sel;
     unsigned long long* total;
     int64_t* total_out;
-    long long first_block;  // level 0
+    long long first_block;  // level 0 of the tournament
+    long long sel_block;    // first block in the radix-select passes
+    long long sel_nblocks;
 };
 
 struct TopItem {
@@ -249,14 +255,31 @@ __global__ void __launch_bounds__(kFinThreads) k_b_finalize(const FinJob* F) {
 
 __global__ void __launch_bounds__(kTopThreads) k_b_topk0(const TopJob* T, const int32_t* bjob) {
     const TopJob& t = T[bjob[blockIdx.x]];
-    topk_level0_block(t.S, t.rank_acc, t.k, t.buf[0], t.total, static_cast<long long>(blockIdx.x) - t.first_block);
+    topk_level0_block(t.S, t.rank_acc, t.k, t.buf[0], t.total, static_cast<long long>(blockIdx.x) - t.first_block,
+                      &t.sel->fallback);
 }
 
 __global__ void __launch_bounds__(kTopThreads) k_b_topk(const TopJob* T, const TopItem* items, const int32_t* bjob) {
     const TopItem& it = items[bjob[blockIdx.x]];
     const TopJob& t = T[it.job];
     topk_reduce_block(t.S, t.buf[it.in_buf], it.n_in, t.k, t.buf[1 - it.in_buf], it.emit, t.O, t.total, t.total_out,
-                      static_cast<long long>(blockIdx.x) - it.first_block);
+                      static_cast<long long>(blockIdx.x) - it.first_block, &t.sel->fallback);
+}
+
+__global__ void __launch_bounds__(kSelThreads) k_b_sel(const TopJob* T, const int32_t* bjob, int pass) {
+    const TopJob& t = T[bjob[blockIdx.x]];
+    topsel_pass_block(t.S, t.rank_acc, t.k, t.sel, pass, static_cast<long long>(blockIdx.x) - t.sel_block,
+                      t.sel_nblocks);
+}
+
+__global__ void __launch_bounds__(kSelThreads) k_b_selcollect(const TopJob* T, const int32_t* bjob) {
+    const TopJob& t = T[bjob[blockIdx.x]];
+    topsel_collect_block(t.S, t.rank_acc, t.sel, t.cand, static_cast<long long>(blockIdx.x) - t.sel_block);
+}
+
+__global__ void __launch_bounds__(kTopThreads) k_b_selemit(const TopJob* T) {
+    const TopJob& t = T[blockIdx.x];
+    topsel_emit_block(t.S, t.k, t.sel, t.cand, t.O, t.total_out);
 }
 
 }  // namespace tqp
@@ -280,10 +303,11 @@ struct tqp_batch {
     std::vector<std::vector<TopItem>> levels;
     // block -> job maps, concatenated
     std::vector<int32_t> maps;
-    long long fill_blocks = 0, row_blocks = 0, num_blocks = 0, slot_blocks = 0, compact_blocks = 0, top0_blocks = 0;
+    long long fill_blocks = 0, row_blocks = 0, num_blocks = 0, slot_blocks = 0, compact_blocks = 0, top0_blocks = 0,
+              sel_blocks = 0;
     long long scan_chunks[kKinds] = {0, 0, 0};
     std::vector<long long> level_blocks;
-    size_t off_fill = 0, off_row = 0, off_num = 0, off_slot = 0, off_compact = 0, off_top0 = 0;
+    size_t off_fill = 0, off_row = 0, off_num = 0, off_slot = 0, off_compact = 0, off_top0 = 0, off_sel = 0;
     size_t off_scan[kKinds] = {0, 0, 0};
     std::vector<size_t> off_level;
     // small zeroed counters share one slab (one fill range)
@@ -422,10 +446,19 @@ static tqp_status add_top_job(tqp_batch* b, const GroupSpec& S, const GroupOut& 
         T.buf[q].slot = static_cast<uint32_t*>(balloc(b, n * 4));
         if (!T.buf[q].rank || !T.buf[q].key || !T.buf[q].slot) return arena_oom(b->ctx, n * 20);
     }
+    T.cand.rank = static_cast<long long*>(balloc(b, kSelCand * 8));
+    T.cand.key = static_cast<uint64_t*>(balloc(b, kSelCand * 8));
+    T.cand.slot = static_cast<uint32_t*>(balloc(b, kSelCand * 4));
+    T.sel = static_cast<TopSel*>(balloc(b, sizeof(TopSel)));
+    if (!T.cand.rank || !T.cand.key || !T.cand.slot || !T.sel) return arena_oom(b->ctx, sizeof(TopSel) + kSelCand * 20);
+    add_fill(b, T.sel, sizeof(TopSel), kZero16);
     T.total = counter(b);
     T.total_out = r->d_total_groups;
     T.first_block = b->top0_blocks;
     b->top0_blocks += nb0;
+    T.sel_nblocks = (S.cap + 1 + kSelSlots - 1) / kSelSlots;
+    T.sel_block = b->sel_blocks;
+    b->sel_blocks += T.sel_nblocks;
     b->top.push_back(T);
     return TQP_OK;
 }
@@ -800,6 +833,8 @@ static void build_maps(tqp_batch* b) {
     }
     b->off_compact = M.size();
     for (size_t j = 0; j < b->compact.size(); ++j) push(j, (b->compact[j].n + kCompactRows - 1) / kCompactRows);
+    b->off_sel = M.size();
+    for (size_t j = 0; j < b->top.size(); ++j) push(j, b->top[j].sel_nblocks);
     b->off_top0 = M.size();
     for (size_t j = 0; j < b->top.size(); ++j)
         push(j, (j + 1 < b->top.size() ? b->top[j + 1].first_block : b->top0_blocks) - b->top[j].first_block);
@@ -872,6 +907,12 @@ static tqp_status batch_launch(tqp_batch* b, cudaStream_t st) {
                                                                                            M + b->off_compact);
     if (!b->fin.empty())
         k_b_finalize<<<static_cast<unsigned>(b->fin.size()), kFinThreads, kFinSmemBytes, st>>>(b->d_fin);
+    if (b->sel_blocks) {
+        for (int pass = 0; pass < kSelPasses; ++pass)
+            k_b_sel<<<static_cast<unsigned>(b->sel_blocks), kSelThreads, 0, st>>>(b->d_top, M + b->off_sel, pass);
+        k_b_selcollect<<<static_cast<unsigned>(b->sel_blocks), kSelThreads, 0, st>>>(b->d_top, M + b->off_sel);
+        k_b_selemit<<<static_cast<unsigned>(b->top.size()), kTopThreads, 0, st>>>(b->d_top);
+    }
     if (b->top0_blocks) {
         k_b_topk0<<<static_cast<unsigned>(b->top0_blocks), kTopThreads, 0, st>>>(b->d_top, M + b->off_top0);
         for (size_t L = 0; L < b->levels.size(); ++L)

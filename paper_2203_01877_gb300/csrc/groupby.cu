@@ -206,15 +206,33 @@ tqp_status group_finalize(tqp_ctx* ctx, const GroupSpec& S, const GroupOut& O, c
 }
 
 __global__ void __launch_bounds__(kTopThreads) k_topk_level0(const __grid_constant__ GroupSpec S, int rank_acc, int k,
-                                                             TopBuf out, unsigned long long* total) {
-    topk_level0_block(S, rank_acc, k, out, total, blockIdx.x);
+                                                             TopBuf out, unsigned long long* total,
+                                                             const unsigned int* run) {
+    topk_level0_block(S, rank_acc, k, out, total, blockIdx.x, run);
 }
 
 __global__ void __launch_bounds__(kTopThreads) k_topk_reduce(const __grid_constant__ GroupSpec S, TopBuf in,
                                                              long long n_in, int k, TopBuf out, int emit,
                                                              const __grid_constant__ GroupOut O,
-                                                             const unsigned long long* total, int64_t* total_out) {
-    topk_reduce_block(S, in, n_in, k, out, emit, O, total, total_out, blockIdx.x);
+                                                             const unsigned long long* total, int64_t* total_out,
+                                                             const unsigned int* run) {
+    topk_reduce_block(S, in, n_in, k, out, emit, O, total, total_out, blockIdx.x, run);
+}
+
+__global__ void __launch_bounds__(kSelThreads) k_topsel_pass(const __grid_constant__ GroupSpec S, int rank_acc, int k,
+                                                             TopSel* sel, int pass, long long nblocks) {
+    topsel_pass_block(S, rank_acc, k, sel, pass, blockIdx.x, nblocks);
+}
+
+__global__ void __launch_bounds__(kSelThreads) k_topsel_collect(const __grid_constant__ GroupSpec S, int rank_acc,
+                                                                TopSel* sel, TopBuf cand) {
+    topsel_collect_block(S, rank_acc, sel, cand, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(kTopThreads) k_topsel_emit(const __grid_constant__ GroupSpec S, int k, const TopSel* sel,
+                                                             TopBuf cand, const __grid_constant__ GroupOut O,
+                                                             int64_t* total_out) {
+    topsel_emit_block(S, k, sel, cand, O, total_out);
 }
 
 tqp_status group_topk(tqp_ctx* ctx, const GroupSpec& S, const GroupOut& O, int k, int agg, int64_t* total_groups,
@@ -230,19 +248,34 @@ tqp_status group_topk(tqp_ctx* ctx, const GroupSpec& S, const GroupOut& O, int k
         b->slot = static_cast<uint32_t*>(arena_alloc(ctx, ncand * 4));
         return b->rank && b->key && b->slot;
     };
-    TopBuf a, b;
+    TopBuf a, b, cand;
     unsigned long long* total = static_cast<unsigned long long*>(arena_alloc(ctx, 256));
-    if (!alloc_buf(&a) || !alloc_buf(&b) || !total) return arena_oom(ctx, ncand * 40);
+    TopSel* sel = static_cast<TopSel*>(arena_alloc(ctx, sizeof(TopSel)));
+    cand.rank = static_cast<long long*>(arena_alloc(ctx, kSelCand * 8));
+    cand.key = static_cast<uint64_t*>(arena_alloc(ctx, kSelCand * 8));
+    cand.slot = static_cast<uint32_t*>(arena_alloc(ctx, kSelCand * 4));
+    if (!alloc_buf(&a) || !alloc_buf(&b) || !total || !sel || !cand.rank || !cand.key || !cand.slot)
+        return arena_oom(ctx, ncand * 40 + sizeof(TopSel) + kSelCand * 20);
     TQP_CUDA(cudaMemsetAsync(total, 0, 8, stream));
-    k_topk_level0<<<static_cast<unsigned>(nb0), kTopThreads, 0, stream>>>(S, rank_acc, k, a, total);
+    TQP_CUDA(cudaMemsetAsync(sel, 0, sizeof(TopSel), stream));
+    // radix select of the k-th largest, then one sort of the candidates
+    const long long nbs = (S.cap + 1 + kSelSlots - 1) / kSelSlots;
+    for (int pass = 0; pass < kSelPasses; ++pass)
+        k_topsel_pass<<<static_cast<unsigned>(nbs), kSelThreads, 0, stream>>>(S, rank_acc, k, sel, pass, nbs);
+    k_topsel_collect<<<static_cast<unsigned>(nbs), kSelThreads, 0, stream>>>(S, rank_acc, sel, cand);
+    k_topsel_emit<<<1, kTopThreads, 0, stream>>>(S, k, sel, cand, O, total_groups);
+    // the tournament, only when the select ended with too many ties (its blocks return early otherwise)
+    const unsigned int* run = &sel->fallback;
+    k_topk_level0<<<static_cast<unsigned>(nb0), kTopThreads, 0, stream>>>(S, rank_acc, k, a, total, run);
     long long n = ncand;
     while (n > kTopBlock) {
         const long long blocks = (n + kTopBlock - 1) / kTopBlock;
-        k_topk_reduce<<<static_cast<unsigned>(blocks), kTopThreads, 0, stream>>>(S, a, n, k, b, 0, O, total, nullptr);
+        k_topk_reduce<<<static_cast<unsigned>(blocks), kTopThreads, 0, stream>>>(S, a, n, k, b, 0, O, total, nullptr,
+                                                                              run);
         std::swap(a, b);
         n = blocks * k;
     }
-    k_topk_reduce<<<1, kTopThreads, 0, stream>>>(S, a, n, k, b, 1, O, total, total_groups);
+    k_topk_reduce<<<1, kTopThreads, 0, stream>>>(S, a, n, k, b, 1, O, total, total_groups, run);
     TQP_CUDA(cudaGetLastError());
     return TQP_OK;
 }

@@ -63,6 +63,37 @@ def test_scan_plan_topk(ctx):
              topk_agg=0, max_groups=8192)
 
 
+@pytest.mark.parametrize("dist", ["ties", "signed_wide", "few_groups", "near_ties", "all_equal_sum"])
+def test_topk_rank_distributions(ctx, dist):
+    """Top-k over rank distributions that take each route of the selection:
+    decided by the first (log-scale) pass, by later passes, and by ties that
+    leave more candidates than one block sorts."""
+    rng = np.random.default_rng(11)
+    n = 300_000
+    if dist == "ties":            # every group has 4 rows: top-k by COUNT is all ties
+        g = np.repeat(np.arange(n // 4, dtype=np.int32), 4)
+        v = rng.integers(-5, 5, n).astype(np.int64)
+        agg, k = 1, 1000
+    elif dist == "signed_wide":   # sums of both signs over 15 decades
+        g = rng.integers(0, 40_000, n).astype(np.int32)
+        v = (np.sign(rng.standard_normal(n)) * 10.0 ** rng.uniform(0, 15, n)).astype(np.int64)
+        agg, k = 0, 500
+    elif dist == "few_groups":    # fewer groups than k
+        g = rng.integers(0, 37, n).astype(np.int32)
+        v = rng.integers(-1000, 1000, n).astype(np.int64)
+        agg, k = 0, 100
+    elif dist == "near_ties":     # large sums within a narrow band: decided in a late pass
+        g = rng.integers(0, 60_000, n).astype(np.int32)
+        v = (10**12 + rng.integers(0, 4, n)).astype(np.int64)
+        agg, k = 0, 300
+    else:                         # every group the same sum: the tie order (key) decides
+        g = np.repeat(rng.permutation(n // 3).astype(np.int32), 3)
+        v = np.full(n, -7, dtype=np.int64)
+        agg, k = 0, 64
+    run_both(ctx, fact=[g, v], group_cols=[0], aggs=[("sum", [("col", 1)]), ("count", None)], topk=k,
+             topk_agg=agg, max_groups=200_000)
+
+
 @pytest.mark.parametrize("topk", [0, 1, 100, 1000])
 def test_join_group_topk(ctx, topk):
     fact, dim = join_case(30_000, 3_000, 1_200_000, 7)

@@ -278,7 +278,7 @@ struct GroupBody {
                     unsigned long long* p = area + (d * kLaneAcc + a) * kWarp + lane;
                     const unsigned long long x = warp_sum_u64(*p);
                     *p = 0;
-                    if (lane == 0 && x && g >= 0) atomicAdd(&S.acc[g * S.nacc + a], x);
+                    if (lane == 0 && x && g >= 0) red_add_u64(&S.acc[g * S.nacc + a], x);
                 }
             }
         }
@@ -424,7 +424,7 @@ struct GroupBody {
             const long long g = gtab_slot(S, wkeys[lane], A.ctl.err);
             for (int a = 0; a < S.nacc; ++a) {
                 const unsigned long long x = wacc[lane * kMaxAcc + a];
-                if (x && g >= 0) atomicAdd(&S.acc[g * S.nacc + a], x);
+                if (x && g >= 0) red_add_u64(&S.acc[g * S.nacc + a], x);
                 wacc[lane * kMaxAcc + a] = 0;
             }
         }
@@ -635,6 +635,12 @@ struct PlanJoinArgs {
     int32_t nsum;              // accumulators after the count (S.nacc - 1)
     ProdForm psum;             // the ungrouped sum
     ProdForm pacc[kFastSums];  // accumulator a + 1
+    // Aggregation by join key first (direct-mapped tables, full tiles): each
+    // fact row adds to its key's entry kacc[(fk - min) * nk + i] (count, the
+    // group sums, then the ungrouped sum), and a second kernel folds every
+    // dimension row's key entry into its group.  nullptr: off.
+    unsigned long long* kacc;
+    int32_t nk;
 };
 
 struct PlanJoinBody {
@@ -654,19 +660,19 @@ struct PlanJoinBody {
         const GroupSpec& S = A.S;
         if (sl.z & kDirectGroup) {  // a unique key whose dense group id sits in the slot
             unsigned long long* a = S.acc + static_cast<long long>(sl.z & ~kDirectGroup) * S.nacc;
-            atomicAdd(&a[0], 1ULL);
+            red_add_u64(&a[0], 1ULL);
 #pragma unroll
             for (int i = 0; i < kFastSums; ++i)
-                if (i < nsum) atomicAdd(&a[i + 1], static_cast<unsigned long long>(x[i]));
+                if (i < nsum) red_add_u64(&a[i + 1], static_cast<unsigned long long>(x[i]));
             return;
         }
         uint32_t d = sl.z;
         for (uint32_t k = 0; k < sl.w; ++k) {
             unsigned long long* a = S.acc + static_cast<long long>(__ldg(&A.dgs[d])) * S.nacc;
-            atomicAdd(&a[0], 1ULL);
+            red_add_u64(&a[0], 1ULL);
 #pragma unroll
             for (int i = 0; i < kFastSums; ++i)
-                if (i < nsum) atomicAdd(&a[i + 1], static_cast<unsigned long long>(x[i]));
+                if (i < nsum) red_add_u64(&a[i + 1], static_cast<unsigned long long>(x[i]));
             if (k + 1 < sl.w) d = __ldg(&A.next[d]);
         }
     }
@@ -690,9 +696,9 @@ struct PlanJoinBody {
         for (uint32_t k = 0; k < cnt; ++k) {
             const long long g = direct_group ? static_cast<long long>(sl.z & ~kDirectGroup) : __ldg(&A.dgs[d]);
             unsigned long long* a = S.acc + g * S.nacc;
-            atomicAdd(&a[0], 1ULL);
+            red_add_u64(&a[0], 1ULL);
             for (int i = 1; i < S.nacc; ++i)
-                atomicAdd(&a[i], static_cast<unsigned long long>(eval_expr(G, v, S.acc_expr[i - 1], r)));
+                red_add_u64(&a[i], static_cast<unsigned long long>(eval_expr(G, v, S.acc_expr[i - 1], r)));
             if (!direct_group && k + 1 < cnt) d = __ldg(&A.next[d]);
         }
     }
@@ -730,12 +736,35 @@ struct PlanJoinBody {
     __device__ __forceinline__ void step_fast(const TileView& v, int rbase, bool direct, long long kmin,
                                               const uint4* __restrict__ slots, long long cap,
                                               unsigned long long* __restrict__ gacc, int nacc, bool has_sum,
-                                              bool grouped) {
+                                              bool grouped, unsigned long long* __restrict__ kacc,
+                                              unsigned long long krange) {
         const int r0 = rbase + (threadIdx.x % kWarp);
         const uint32_t ok = conds_full<kU>(v.stage, A.cf, A.ncond, r0);
         if (!__any_sync(0xffffffffu, ok)) return;
         int64_t fk[kU];
         load_rows<kU>(v.stage + A.fk_soff, A.fk_type, r0, fk);
+        if (kacc) {  // by join key: no slot load; the fold adds the matches to their groups
+            passed += __popc(ok);
+            int64_t sv[kU];
+            if (has_sum) prod_eval<kU>(A.psum, v.stage, r0, sv);
+            int64_t xv[kJoinSums][kU];
+#pragma unroll
+            for (int i = 0; i < kJoinSums; ++i)
+                if (i < nacc - 1) prod_eval<kU>(A.pacc[i], v.stage, r0, xv[i]);
+            const int nk = A.nk;
+#pragma unroll
+            for (int j = 0; j < kU; ++j) {
+                const unsigned long long e = static_cast<uint64_t>(fk[j]) - static_cast<uint64_t>(kmin);
+                if (!((ok >> j) & 1u) || e >= krange) continue;
+                unsigned long long* a = kacc + e * nk;
+                red_add_u64(&a[0], 1ULL);
+#pragma unroll
+                for (int i = 0; i < kJoinSums; ++i)
+                    if (i < nacc - 1) red_add_u64(&a[i + 1], static_cast<unsigned long long>(xv[i][j]));
+                if (has_sum) red_add_u64(&a[nacc], static_cast<unsigned long long>(sv[j]));
+            }
+            return;
+        }
         unsigned long long hh[kU];
         uint4 sl[kU];
 #pragma unroll
@@ -770,10 +799,10 @@ struct PlanJoinBody {
             if (!grouped) continue;
             if (s.z & kDirectGroup) {
                 unsigned long long* a = gacc + static_cast<long long>(s.z & ~kDirectGroup) * nacc;
-                atomicAdd(&a[0], 1ULL);
+                red_add_u64(&a[0], 1ULL);
 #pragma unroll
                 for (int i = 0; i < kJoinSums; ++i)
-                    if (i < nacc - 1) atomicAdd(&a[i + 1], static_cast<unsigned long long>(xv[i][j]));
+                    if (i < nacc - 1) red_add_u64(&a[i + 1], static_cast<unsigned long long>(xv[i][j]));
             } else {
                 int64_t x[kFastSums];
 #pragma unroll
@@ -793,9 +822,12 @@ struct PlanJoinBody {
             unsigned long long* gacc = A.S.acc;
             const int nacc = A.S.nacc;
             const bool has_sum = A.has_sum != 0, grouped = A.dgs != nullptr;
+            unsigned long long* kacc = direct ? A.kacc : nullptr;
+            const unsigned long long krange = kacc ? static_cast<unsigned long long>(__ldg(&A.H.meta[1]) - kmin) + 1 : 0;
             // rw is a multiple of 128 = kUnroll * 32
             for (int r = 0; r < rw; r += kUnroll * kWarp)
-                step_fast<kUnroll>(v, cw * rw + r, direct, kmin, slots, cap, gacc, nacc, has_sum, grouped);
+                step_fast<kUnroll>(v, cw * rw + r, direct, kmin, slots, cap, gacc, nacc, has_sum, grouped, kacc,
+                                   krange);
             return;
         }
         for (int r = 0; r < rw; r += kUnroll * kWarp) {
@@ -843,8 +875,10 @@ struct PlanJoinBody {
             if (s) atomicAdd(&A.acc[1], static_cast<unsigned long long>(s));
             if (p) atomicAdd(&A.acc[2], p);
             if (last_completion(&A.acc[3], A.ctl.nchunks)) {
-                if (A.d_num_joined) *A.d_num_joined = static_cast<int64_t>(atomicAdd(&A.acc[0], 0ULL));
-                if (A.d_sum) *A.d_sum = static_cast<int64_t>(atomicAdd(&A.acc[1], 0ULL));
+                long long kmin;
+                const bool folded = A.kacc && ht_is_direct(A.H, &kmin);  // the fold writes joined and sum
+                if (A.d_num_joined && !folded) *A.d_num_joined = static_cast<int64_t>(atomicAdd(&A.acc[0], 0ULL));
+                if (A.d_sum && !folded) *A.d_sum = static_cast<int64_t>(atomicAdd(&A.acc[1], 0ULL));
                 if (A.d_num_rows) *A.d_num_rows = static_cast<int64_t>(atomicAdd(&A.acc[2], 0ULL));
             }
         }

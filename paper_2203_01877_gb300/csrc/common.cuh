@@ -38,6 +38,14 @@ __device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned l
 }
 
 // ---- shared-memory addresses and mbarriers -------------------------------
+// Fire-and-forget 64-bit add to global memory (a RED, no value returned).
+// Accumulator pointers often come from shared memory (staged kernel
+// arguments), where the compiler cannot tell that they address global memory
+// and would otherwise emit a generic atomic that returns the old value.
+__device__ __forceinline__ void red_add_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "l"(v));
+}
+
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }

@@ -73,6 +73,73 @@ __global__ void k_dim_remap(const uint32_t* dslot, const uint32_t* slot2dense, l
         dgs[d] = slot2dense[dslot[d]];
 }
 
+// Zero the key-first accumulators over a direct-mapped table's key range
+// (a hashed table leaves them unused).
+__global__ void k_keyfirst_zero(const JoinHT H, unsigned long long* kacc, int nk) {
+    long long kmin;
+    if (!ht_is_direct(H, &kmin)) return;
+    const long long n = (__ldg(&H.meta[1]) - kmin + 1) * nk;
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x)
+        kacc[i] = 0;
+}
+
+// Fold the key-first accumulators into the groups: every dimension row adds
+// its key's entry (the fact rows that matched it) to its group, and to the
+// joined-pair count and the ungrouped sum.  The last block writes those two
+// results.  Nothing to do for a hashed table: the probe aggregated by group.
+constexpr int kFoldThreads = 256;
+__global__ void __launch_bounds__(kFoldThreads) k_keyfirst_fold(const JoinHT H, const unsigned char* dkey, int dkey_type,
+                                                                long long nd, const uint32_t* dgs,
+                                                                const __grid_constant__ GroupSpec S,
+                                                                const unsigned long long* kacc, int nk, int has_sum,
+                                                                unsigned long long* acc, int64_t* d_num_joined,
+                                                                int64_t* d_sum) {
+    long long kmin;
+    if (!ht_is_direct(H, &kmin)) return;
+    const unsigned long long krange = static_cast<unsigned long long>(__ldg(&H.meta[1]) - kmin) + 1;
+    unsigned long long joined = 0;
+    long long sum = 0;
+    for (long long d = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; d < nd;
+         d += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const unsigned long long e =
+            static_cast<uint64_t>(ldg_typed(dkey, dkey_type, d)) - static_cast<uint64_t>(kmin);
+        if (e >= krange) continue;
+        const unsigned long long* a = kacc + e * nk;
+        const unsigned long long c = __ldg(&a[0]);
+        if (!c) continue;
+        unsigned long long* ga = S.acc + static_cast<long long>(__ldg(&dgs[d])) * S.nacc;
+        red_add_u64(&ga[0], c);
+        for (int i = 1; i < S.nacc; ++i) red_add_u64(&ga[i], __ldg(&a[i]));
+        joined += c;
+        if (has_sum) sum += static_cast<long long>(__ldg(&a[S.nacc]));
+    }
+    __shared__ unsigned long long rj[kFoldThreads / 32];
+    __shared__ long long rs[kFoldThreads / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        joined += __shfl_xor_sync(0xffffffffu, joined, o);
+        sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    }
+    if (threadIdx.x % 32 == 0) {
+        rj[threadIdx.x / 32] = joined;
+        rs[threadIdx.x / 32] = sum;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    for (int w = 1; w < kFoldThreads / 32; ++w) {
+        joined += rj[w];
+        sum += rs[w];
+    }
+    if (joined) atomicAdd(&acc[0], joined);
+    if (sum) atomicAdd(&acc[1], static_cast<unsigned long long>(sum));
+    __threadfence();
+    if (atomicAdd(&acc[4], 1ULL) != gridDim.x - 1ULL) return;
+    __threadfence();
+    if (d_num_joined) *d_num_joined = static_cast<int64_t>(atomicAdd(&acc[0], 0ULL));
+    if (d_sum) *d_sum = static_cast<int64_t>(atomicAdd(&acc[1], 0ULL));
+}
+
 __global__ void __launch_bounds__(kEngineThreads, PlanJoinBody::kMinBlocks) k_plan_join(const __grid_constant__ PlanJoinArgs P) {
     extern __shared__ __align__(128) unsigned char smem[];
     const PlanJoinArgs& A = stage_args(P, smem + kHeaderBytes);
@@ -276,6 +343,22 @@ static tqp_status run_join_plan(tqp_ctx* ctx, const tqp_plan* p, const tqp_resul
     if (!sc) return arena_oom(ctx, 64);
     TQP_CUDA(cudaMemsetAsync(sc, 0, 8 * 8, stream));
     A.acc = sc + 1;
+    // Aggregate by join key first when the fact rows outnumber the build rows:
+    // a probe row then costs its key entry's atomics only (no slot load), and
+    // one pass over the build rows moves the per-key totals to the groups.
+    // Used only if the table turns out direct-mapped; off when scratch is short.
+    if (grouped && A.pjfast && A.fast && H.meta && F->num_rows >= 2 * std::max<long long>(1, D->num_rows)) {
+        A.nk = A.S.nacc + (A.has_sum ? 1 : 0);
+        const size_t used = ctx->used;
+        A.kacc = static_cast<unsigned long long*>(arena_alloc(ctx, static_cast<size_t>(H.cap) * A.nk * 8));
+        if (!A.kacc) ctx->used = used;
+    }
+    if (A.kacc) {
+        const long long n = H.cap * A.nk;
+        const int blocks = static_cast<int>(std::min<long long>((n + 1023) / 1024, 8LL * ctx->num_sms));
+        k_keyfirst_zero<<<std::max(blocks, 1), 256, 0, stream>>>(A.H, A.kacc, A.nk);
+        TQP_CUDA(cudaGetLastError());
+    }
     A.d_num_joined = r->d_num_joined;
     A.d_sum = p->has_sum ? r->d_sum : nullptr;
     A.d_num_rows = (p->emit_row_ids && r->d_row_ids) ? nullptr : r->d_num_rows;
@@ -290,6 +373,15 @@ static tqp_status run_join_plan(tqp_ctx* ctx, const tqp_plan* p, const tqp_resul
         A.ctl.wait_cap = ctx->wait_cap;
         k_plan_join<<<static_cast<int>(A.ctl.nchunks), kEngineThreads, smem, stream>>>(A);
         TQP_CUDA(cudaGetLastError());
+        if (A.kacc) {
+            const long long nd = D->num_rows;
+            const int blocks =
+                static_cast<int>(std::min<long long>((nd + kFoldThreads - 1) / kFoldThreads, 4LL * ctx->num_sms));
+            k_keyfirst_fold<<<std::max(blocks, 1), kFoldThreads, 0, stream>>>(
+                A.H, static_cast<const unsigned char*>(D->cols[p->dim_key].data), D->cols[p->dim_key].type, nd, A.dgs,
+                A.S, A.kacc, A.nk, A.has_sum, A.acc, A.d_num_joined, A.d_sum);
+            TQP_CUDA(cudaGetLastError());
+        }
     } else {
         if (A.d_num_joined) TQP_CUDA(cudaMemsetAsync(A.d_num_joined, 0, 8, stream));
         if (A.d_sum) TQP_CUDA(cudaMemsetAsync(A.d_sum, 0, 8, stream));

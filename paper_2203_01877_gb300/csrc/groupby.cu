@@ -23,6 +23,7 @@
 #include "group.cuh"
 #include "bodies.cuh"
 #include "finalize.cuh"
+#include "groupdirect.cuh"
 
 namespace tqp {
 
@@ -38,6 +39,11 @@ __global__ void __launch_bounds__(kEngineThreads, GroupBody::kMinBlocks) k_group
     const GroupArgs& A = stage_args(P, smem + kHeaderBytes);
     GroupBody body(A, smem + kHeaderBytes + args_bytes<GroupArgs>());
     run_engine(A.G, A.ctl, body, smem, args_bytes<GroupArgs>());
+}
+
+__global__ void __launch_bounds__(kDirThreads, kDirMinBlocks) k_groupby_direct(const __grid_constant__ GroupDirectArgs A) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    group_direct_block(A, dsm);
 }
 
 // ---- finalize ----------------------------------------------------------------
@@ -297,6 +303,56 @@ void lower_group_fast(GroupArgs* A) {
     A->kfast = 1;
 }
 
+// The direct (unstaged) kernel applies when groups are few (max_groups <=
+// kDirMaxGroups), the accumulators are the count and at most three
+// closed-form sums, and conditions are at most kDirConds.  Columns are
+// 16-byte aligned, as every table requires, so its vector loads are too.
+// Lowered through a geometry whose stage offset of every column is its
+// column number, so that the lowered forms name columns.
+constexpr long long kDirMaxGroups = 64;
+
+static bool lower_group_direct(const tqp_table* t, const GroupArgs& A, long long max_groups, GroupDirectArgs* D) {
+    if (max_groups > kDirMaxGroups || A.ncond > kDirConds || A.S.nacc > kDirAcc || t->num_rows <= 0) return false;
+    ScanGeom G;
+    memset(&G, 0, sizeof(G));
+    G.n = t->num_rows;
+    G.ncols = t->num_cols;
+    for (int c = 0; c < t->num_cols; ++c) {
+        G.col[c].ptr = static_cast<const unsigned char*>(t->cols[c].data);
+        G.col[c].type = t->cols[c].type;
+        G.col[c].slot = 0;
+        G.col[c].soff = c;
+    }
+    memset(D, 0, sizeof(*D));
+    D->n = t->num_rows;
+    CondFast cf[TQP_MAX_PREDS];
+    int32_t fast = 0;
+    lower_fast(A.cond, A.ncond, G, cf, &fast);
+    if (!fast) return false;
+    D->ncond = A.ncond;
+    for (int q = 0; q < A.ncond; ++q) {
+        const int c = cf[q].soff;
+        D->cond[q] = DirCond{G.col[c].ptr, cf[q].type, cf[q].negate, cf[q].lo, cf[q].span};
+    }
+    D->ngc = A.S.ngc;
+    for (int i = 0; i < A.S.ngc; ++i) {
+        const int c = A.S.key_col[i];
+        D->key[i] = DirCol{G.col[c].ptr, t->cols[c].type, 0};
+    }
+    D->nsum = A.S.nacc - 1;
+    for (int a = 0; a < D->nsum; ++a) {
+        ProdForm pf;
+        if (!lower_prod(A.S.acc_expr[a], G, &pf)) return false;
+        for (int k = 0; k < 2; ++k) {
+            const bool col = pf.kind[k] != kFacConst;
+            D->f[a][k] = DirFactor{col ? G.col[pf.soff[k]].ptr : nullptr, col ? pf.type[k] : 0, pf.kind[k], pf.a[k],
+                                   pf.b[k]};
+        }
+    }
+    D->kw32 = A.S.width <= 32;
+    return true;
+}
+
 tqp_status launch_groupby(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* preds, int32_t npreds,
                           const int32_t* group_cols, int32_t ngc, const tqp_agg* aggs, int32_t naggs,
                           int64_t* d_keys, int64_t* d_ivals, double* d_fvals, int64_t capacity_groups,
@@ -342,7 +398,23 @@ tqp_status launch_groupby(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* pred
     if (!tab || !ticket) return arena_oom(ctx, group_table_bytes(cap, A.S.nacc));
     TQP_TRY(group_table_init(&A.S, tab, cap, max_groups, stream));
 
-    if (t->num_rows > 0) {
+    GroupDirectArgs D;
+    if (lower_group_direct(t, A, max_groups, &D)) {
+        D.S = A.S;
+        D.err = ctx->d_err;
+        static bool attr_done[kMaxDevices] = {};
+        TQP_TRY(allow_smem(ctx, reinterpret_cast<const void*>(k_groupby_direct), attr_done));
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_groupby_direct, kDirThreads, kDirSmemBytes) !=
+                cudaSuccess ||
+            occ < 1)
+            occ = 1;
+        const long long nq = (t->num_rows + 3) / 4;
+        const long long blocks = std::min<long long>((nq + kDirThreads - 1) / kDirThreads,
+                                                     static_cast<long long>(occ) * ctx->num_sms);
+        k_groupby_direct<<<static_cast<unsigned>(std::max<long long>(blocks, 1)), kDirThreads, kDirSmemBytes, stream>>>(D);
+        TQP_CUDA(cudaGetLastError());
+    } else if (t->num_rows > 0) {
         static bool attr_done[kMaxDevices] = {};
         TQP_TRY(allow_smem(ctx, reinterpret_cast<const void*>(k_groupby), attr_done));
         const int g = engine_grid(ctx, reinterpret_cast<const void*>(k_groupby), smem, A.G.ntiles, tu.ctas_per_sm);

@@ -122,3 +122,55 @@ def test_full_size_q1(ctx):
     """The 1M-row six-group configuration in the benchmark's launch shape."""
     g = check(ctx, q1_cols(1_000_000, datagen.DEFAULT_SEED), [(0, "le", 2450)], [1, 2], Q1_AGGS, capacity=64)
     assert g == 6
+
+
+# ---- few groups (at most 64): the unstaged vector-load kernel ----------------------
+
+
+@pytest.mark.parametrize("n", [1, 3, 100, 1023, 1025, 4097, 100_003])
+def test_few_groups_q1_ragged(ctx, n):
+    """Row counts that leave a ragged last quad of rows and partial warps."""
+    g = check(ctx, q1_cols(n, 70 + n), [(0, "le", 2450)], [1, 2], Q1_AGGS, capacity=64)
+    if n >= 100_000:
+        assert g == 6
+
+
+@pytest.mark.parametrize("ngroups", [9, 33, 64])
+def test_few_groups_list_overflow(ctx, ngroups):
+    """More distinct keys per warp step than the warp's key list holds: the
+    list is flushed and restarted, and rows that still do not fit go to the
+    global table one by one."""
+    rng = np.random.default_rng(100 + ngroups)
+    n = 300_001
+    key = rng.integers(0, ngroups, n).astype(np.int32) * 7 - 100
+    flag = rng.integers(0, 3, n).astype(np.uint8)
+    val = rng.integers(-10**12, 10**12, n).astype(np.int64)
+    check(ctx, [key, flag, val], [(1, "ne", 1)], [0], [("sum", [("col", 2)]), ("count", None),
+                                                       ("avg", [("col", 2)])], capacity=64)
+
+
+def test_few_groups_all_conditions_and_keys(ctx):
+    """Four conditions (i64, i32, u8), a three-column packed key (u8, i32, u8)
+    and three distinct closed-form sums."""
+    t = datagen.fact_table(200_000, seed=77)
+    cols = [t["date"], t["flag"], t["status"], t["quantity"], t["price"], t["discount"]]
+    preds = [(0, "ge", 100), (3, "lt", 45), (5, "between", 1, 9), (1, "ne", 2)]
+    aggs = [("sum", [("col", 4), ("col", 5), "mul"]), ("sum", [("col", 3), ("const", 3), "add"]),
+            ("count", None), ("sum", [("const", 50), ("col", 3), "sub"])]
+    k = (t["quantity"] % 4).astype(np.int32)
+    check(ctx, cols + [k], preds, [1, 6, 2], aggs, capacity=64)
+
+
+def test_few_groups_ungrouped_and_64bit_key(ctx):
+    cols = q1_cols(77_777, 5)
+    check(ctx, cols, [(0, "le", 2450)], [], Q1_AGGS, capacity=64)
+    check(ctx, cols, [(0, "gt", 99999)], [], Q1_AGGS, capacity=64)   # no row passes: one row, COUNT 0, AVG NaN
+    d = (np.arange(77_777) % 5).astype(np.int64) * (2**45) - 2**62
+    check(ctx, [d, cols[4]], [], [0], [("sum", [("col", 1)]), ("count", None)], capacity=8)
+
+
+def test_few_groups_capacity_exceeded(ctx):
+    import paper_2203_01877_gb300 as tqp
+    key = (np.arange(200_000) % 100).astype(np.int32)
+    st, G, *_ = gpu_groupby(ctx, [key], [], [0], [("count", None)], capacity=64)
+    assert st == tqp.ERR_CAPACITY and G == -1

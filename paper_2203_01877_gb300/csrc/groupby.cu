@@ -46,6 +46,11 @@ __global__ void __launch_bounds__(kDirThreads, kDirMinBlocks) k_groupby_direct(c
     group_direct_block(A, dsm);
 }
 
+__global__ void __launch_bounds__(kDirThreads) k_groupby_keyrange(const __grid_constant__ GroupDirectArgs A,
+                                                                  unsigned long long* kmeta) {
+    group_direct_range_block(A, kmeta);
+}
+
 // ---- finalize ----------------------------------------------------------------
 
 __global__ void __launch_bounds__(kFinThreads) k_groupby_finalize_small(const __grid_constant__ GroupSpec S,
@@ -325,6 +330,17 @@ static bool lower_group_direct(const tqp_table* t, const GroupArgs& A, long long
     }
     memset(D, 0, sizeof(*D));
     D->n = t->num_rows;
+    // the distinct columns a step reads, each with its block in a warp slot
+    int lane_bytes = 0;
+    auto pref = [&](int c) -> int {
+        for (int i = 0; i < D->npref; ++i)
+            if (D->pref[i].p == G.col[c].ptr && D->pref[i].type == G.col[c].type) return i;
+        if (D->npref == kDirPrefCols) return -1;
+        const int es = t->cols[c].type == TQP_I64 ? 8 : (t->cols[c].type == TQP_I32 ? 4 : 1);
+        D->pref[D->npref] = DirPref{G.col[c].ptr, t->cols[c].type, 32 * lane_bytes};
+        lane_bytes += 4 * es;
+        return D->npref++;
+    };
     CondFast cf[TQP_MAX_PREDS];
     int32_t fast = 0;
     lower_fast(A.cond, A.ncond, G, cf, &fast);
@@ -332,12 +348,14 @@ static bool lower_group_direct(const tqp_table* t, const GroupArgs& A, long long
     D->ncond = A.ncond;
     for (int q = 0; q < A.ncond; ++q) {
         const int c = cf[q].soff;
-        D->cond[q] = DirCond{G.col[c].ptr, cf[q].type, cf[q].negate, cf[q].lo, cf[q].span};
+        D->cond[q] = DirCond{G.col[c].ptr, cf[q].type, cf[q].negate, cf[q].lo, cf[q].span, pref(c), 0};
+        if (D->cond[q].pc < 0) return false;
     }
     D->ngc = A.S.ngc;
     for (int i = 0; i < A.S.ngc; ++i) {
         const int c = A.S.key_col[i];
-        D->key[i] = DirCol{G.col[c].ptr, t->cols[c].type, 0};
+        D->key[i] = DirCol{G.col[c].ptr, t->cols[c].type, pref(c)};
+        if (D->key[i].pc < 0) return false;
     }
     D->nsum = A.S.nacc - 1;
     for (int a = 0; a < D->nsum; ++a) {
@@ -345,12 +363,14 @@ static bool lower_group_direct(const tqp_table* t, const GroupArgs& A, long long
         if (!lower_prod(A.S.acc_expr[a], G, &pf)) return false;
         for (int k = 0; k < 2; ++k) {
             const bool col = pf.kind[k] != kFacConst;
+            const int pc = col ? pref(pf.soff[k]) : 0;
+            if (pc < 0) return false;
             D->f[a][k] = DirFactor{col ? G.col[pf.soff[k]].ptr : nullptr, col ? pf.type[k] : 0, pf.kind[k], pf.a[k],
-                                   pf.b[k]};
+                                   pf.b[k], pc, 0};
         }
     }
     D->kw32 = A.S.width <= 32;
-    return true;
+    return lane_bytes <= kDirLaneBytes;
 }
 
 tqp_status launch_groupby(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* preds, int32_t npreds,
@@ -412,6 +432,16 @@ tqp_status launch_groupby(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* pred
         const long long nq = (t->num_rows + 3) / 4;
         const long long blocks = std::min<long long>((nq + kDirThreads - 1) / kDirThreads,
                                                      static_cast<long long>(occ) * ctx->num_sms);
+        if (D.ngc > 0) {  // key ranges first: few distinct values get dense slot ids
+            unsigned long long* kmeta = static_cast<unsigned long long*>(arena_alloc(ctx, 2 * kDirKeys * 8));
+            if (!kmeta) return arena_oom(ctx, 2 * kDirKeys * 8);
+            TQP_CUDA(cudaMemsetAsync(kmeta, 0, 2 * kDirKeys * 8, stream));
+            k_groupby_keyrange<<<static_cast<unsigned>(std::max<long long>(
+                                     std::min<long long>(blocks, 4LL * ctx->num_sms), 1)),
+                                 kDirThreads, 0, stream>>>(D, kmeta);
+            TQP_CUDA(cudaGetLastError());
+            D.kmeta = kmeta;
+        }
         k_groupby_direct<<<static_cast<unsigned>(std::max<long long>(blocks, 1)), kDirThreads, kDirSmemBytes, stream>>>(D);
         TQP_CUDA(cudaGetLastError());
     } else if (t->num_rows > 0) {

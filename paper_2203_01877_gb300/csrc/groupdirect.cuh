@@ -1,19 +1,26 @@
-// Group-by for few groups without staging (the aggregation of Section 5.4,
-// one output row per distinct key tuple, for the shape where the key domain
-// is small, e.g. the six (flag, status) groups of the scan-aggregate query).
+// Group-by for few groups without the staged scan engine (the aggregation
+// of Section 5.4, one output row per distinct key tuple, for the shape where
+// the key domain is small, e.g. the six (flag, status) groups of the
+// scan-aggregate query).
 //
-// Every thread reads four consecutive rows of each column with one vector
-// load (16 bytes of int32, two 16-byte pairs of int64, 4 bytes of uint8), so
-// a warp covers 128 consecutive rows per step and nothing is staged through
-// shared memory.  Rows are added into lane-private accumulator tables in
-// shared memory ([slot][acc][lane] per warp: no two lanes share an address,
-// no atomics), with the four rows of a lane that share a group folded first.
-// The warp's keys live in a list of kDirSlots entries held in registers
-// (identical in every lane).  When a step brings more distinct keys than the
-// list holds, the warp flushes its tables into the global table and starts a
-// new list; rows that still do not fit go to the global table one by one.
-// With few threads' worth of state per SM the kernel runs two CTAs of eight
-// warps per SM, and the accumulators reach the global table once per warp.
+// A warp takes 32 quads of rows at a time (four consecutive rows per lane,
+// 128 rows per step).  The columns a step reads are fetched one step ahead
+// with asynchronous 16- and 4-byte copies (cp.async) into a per-warp slot in
+// shared memory, so their memory latency overlaps the previous step's
+// arithmetic; the lane then reads its four values of a column with one
+// vector load from the slot.  Rows are added into lane-private accumulator
+// tables in shared memory ([slot][acc][lane] per warp: no two lanes share an
+// address, no atomics), with the four rows of a lane that share a group
+// folded first.  The warp's keys live in a list of kDirSlots entries held in
+// registers (identical in every lane).  When a step brings more distinct keys
+// than the list holds, the warp flushes its tables into the global table and
+// starts a new list; rows that still do not fit go to the global table one
+// by one.  The last, partial steps read global memory directly.
+//
+// Dense ids: a first pass reduces each key column's [min, max]; when the
+// product of the ranges is at most kDirSlots, a row's slot is its mixed-radix
+// index sum_i (x_i - min_i) * stride_i -- no key packing, no list lookup --
+// and the flush rebuilds each used slot's packed key from its index.
 #pragma once
 
 #include "group.cuh"
@@ -28,12 +35,36 @@ constexpr int kDirConds = 4;
 constexpr int kDirKeys = TQP_MAX_GROUP_COLS;
 constexpr int kDirSums = kDirAcc - 1;
 constexpr int kDirWarpWords = kDirSlots * kDirAcc * 32;
-constexpr int kDirSmemBytes = (kDirThreads / 32) * kDirWarpWords * 8;  // 64 KB
+constexpr int kDirTableBytes = (kDirThreads / 32) * kDirWarpWords * 8;  // 64 KB
+constexpr int kDirPrefCols = 8;          // distinct columns a step reads
+constexpr int kDirLaneBytes = 128;       // their bytes per lane (four rows)
+constexpr int kDirSlotBytes = 32 * kDirLaneBytes;
+constexpr int kDirDenseOff = kDirTableBytes + (kDirThreads / 32) * kDirSlotBytes;
+constexpr int kDirSmemBytes = kDirDenseOff + 128;  // 96 KB + the dense-id parameters
+
+// Dense ids of the CTA (computed once from the key ranges).
+struct DirDense {
+    long long kmin[kDirKeys];
+    int32_t stride[kDirKeys];
+    int32_t range[kDirKeys];
+    int32_t P;      // slots in use: the product of the ranges
+    int32_t dense;  // 1: ids are mixed-radix indices
+};
+static_assert(sizeof(DirDense) <= 128, "dense parameters");
+
+// A column fetched ahead: its block in a warp slot starts at `off` and holds
+// the four values of every lane (esize 8: [half][lane][16 B]; 4: [lane][16 B];
+// 1: [lane][4 B]).
+struct DirPref {
+    const unsigned char* p;
+    int32_t type;
+    int32_t off;
+};
 
 struct DirCol {
     const unsigned char* p;
     int32_t type;
-    int32_t pad;
+    int32_t pc;  // index in GroupDirectArgs::pref
 };
 
 // A range condition on a column: a row passes iff ((x - lo) <= span) != negate
@@ -44,6 +75,8 @@ struct DirCond {
     int32_t negate;
     int64_t lo;
     uint64_t span;
+    int32_t pc;
+    int32_t pad;
 };
 
 // One affine factor a * x + b of a closed-form sum (kind as in ProdForm).
@@ -53,6 +86,8 @@ struct DirFactor {
     int32_t kind;
     int64_t a;
     int64_t b;
+    int32_t pc;
+    int32_t pad;
 };
 
 struct GroupDirectArgs {
@@ -61,49 +96,96 @@ struct GroupDirectArgs {
     DirCond cond[kDirConds];
     DirCol key[kDirKeys];
     DirFactor f[kDirSums][2];
+    int32_t npref;
+    int32_t pad;
+    DirPref pref[kDirPrefCols];
     GroupSpec S;
     int* err;
+    // key ranges from the first pass: [2 i] = max of ~enc(x), [2 i + 1] = max
+    // of enc(x), enc(x) = x ^ 2^63 (so the first is ~enc(min)); nullptr: none
+    const unsigned long long* kmeta;
 };
 
-// x[j] = row 4 q + j of a column.  kFull: all four rows exist (one vector
-// load of the 16-byte aligned column); otherwise rows from `n` on read as 0.
-template <bool kFull>
-__device__ __forceinline__ void dir_load4(const unsigned char* p, int type, long long q, long long n,
-                                          int64_t (&x)[4]) {
-    if constexpr (kFull) {
-        if (type == TQP_I64) {
-            const longlong2* v = reinterpret_cast<const longlong2*>(p) + 2 * q;
-            const longlong2 a = __ldg(v), b = __ldg(v + 1);
-            x[0] = a.x;
-            x[1] = a.y;
-            x[2] = b.x;
-            x[3] = b.y;
-        } else if (type == TQP_I32) {
-            const int4 v = __ldg(reinterpret_cast<const int4*>(p) + q);
-            x[0] = v.x;
-            x[1] = v.y;
-            x[2] = v.z;
-            x[3] = v.w;
-        } else {
-            const unsigned w = __ldg(reinterpret_cast<const unsigned*>(p) + q);
+// ---- asynchronous copies into the warp slot ----
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Fetch quad q (four rows, all in the table) of every prefetched column into the slot.
+__device__ __forceinline__ void dir_prefetch(const GroupDirectArgs& A, unsigned char* slot, long long q, int lane) {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) x[j] = (w >> (8 * j)) & 0xFFu;
+    for (int c = 0; c < kDirPrefCols; ++c) {
+        if (c < A.npref) {
+            const DirPref& pc = A.pref[c];
+            unsigned char* d = slot + pc.off;
+            if (pc.type == TQP_I64) {
+                const unsigned char* g = pc.p + q * 32;
+                cp_async16(d + lane * 16, g);
+                cp_async16(d + 512 + lane * 16, g + 16);
+            } else if (pc.type == TQP_I32) {
+                cp_async16(d + lane * 16, pc.p + q * 16);
+            } else {
+                cp_async4(d + lane * 4, pc.p + q * 4);
+            }
         }
+    }
+    cp_async_commit();
+}
+
+// The lane's four values of prefetched column c from the slot.
+__device__ __forceinline__ void dir_slot4(const GroupDirectArgs& A, const unsigned char* slot, int c, int lane,
+                                          int64_t (&x)[4]) {
+    const DirPref& pc = A.pref[c];
+    const unsigned char* d = slot + pc.off;
+    if (pc.type == TQP_I64) {
+        const longlong2 a = *reinterpret_cast<const longlong2*>(d + lane * 16);
+        const longlong2 b = *reinterpret_cast<const longlong2*>(d + 512 + lane * 16);
+        x[0] = a.x;
+        x[1] = a.y;
+        x[2] = b.x;
+        x[3] = b.y;
+    } else if (pc.type == TQP_I32) {
+        const int4 v = *reinterpret_cast<const int4*>(d + lane * 16);
+        x[0] = v.x;
+        x[1] = v.y;
+        x[2] = v.z;
+        x[3] = v.w;
     } else {
+        const unsigned w = *reinterpret_cast<const unsigned*>(d + lane * 4);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) x[j] = (w >> (8 * j)) & 0xFFu;
+    }
+}
+
+// x[j] = row 4 q + j of a column: from the warp slot (kSlot: the step was
+// prefetched) or from global memory, rows from `n` on reading as 0.
+template <bool kSlot>
+__device__ __forceinline__ void dir_load4(const GroupDirectArgs& A, const unsigned char* slot, int pc,
+                                          const unsigned char* p, int type, long long q, int lane, int64_t (&x)[4]) {
+    if constexpr (kSlot) {
+        dir_slot4(A, slot, pc, lane, x);
+    } else {
+        const long long n = A.n;
 #pragma unroll
         for (int j = 0; j < 4; ++j) x[j] = 4 * q + j < n ? ldg_typed(p, type, 4 * q + j) : 0;
     }
 }
 
-template <bool kFull>
-__device__ __forceinline__ void dir_factor(const DirFactor& f, long long q, long long n, int64_t (&x)[4]) {
+template <bool kSlot>
+__device__ __forceinline__ void dir_factor(const GroupDirectArgs& A, const unsigned char* slot, const DirFactor& f,
+                                           long long q, int lane, int64_t (&x)[4]) {
     const int kind = f.kind;
     if (kind == kFacConst) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) x[j] = f.b;
         return;
     }
-    dir_load4<kFull>(f.p, f.type, q, n, x);
+    dir_load4<kSlot>(A, slot, f.pc, f.p, f.type, q, lane, x);
     if (kind == kFacPlain) return;
     const uint64_t b = static_cast<uint64_t>(f.b);
     if (kind == kFacAdd) {
@@ -146,10 +228,91 @@ __device__ __forceinline__ void dir_flush(const GroupDirectArgs& A, unsigned lon
     __syncwarp();
 }
 
+// Dense ids: every used slot's lane partials into the global table (its
+// packed key rebuilt from the slot index); the tables are zero afterwards.
+__device__ __forceinline__ void dir_flush_dense(const GroupDirectArgs& A, const DirDense& Dn, unsigned long long* area,
+                                                int lane) {
+    __syncwarp();
+    const GroupSpec& S = A.S;
+    for (int d = 0; d < Dn.P; ++d) {
+        unsigned long long* p0 = area + (d * kDirAcc) * 32 + lane;
+        unsigned long long c = *p0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if (c == 0) continue;  // no row of this warp in the slot (warp-uniform)
+        long long g = -1;
+        if (lane == 0) {
+            uint64_t key = 0;
+            for (int i = 0; i < A.ngc; ++i) {
+                const long long x = Dn.kmin[i] + (d / Dn.stride[i]) % Dn.range[i];
+                const int b = S.key_bits[i];
+                const uint64_t e = enc_key(x, b);
+                key = b == 64 ? e : ((key << b) | e);
+            }
+            g = gtab_slot(S, key, A.err);
+        }
+        g = __shfl_sync(0xffffffffu, g, 0);
+#pragma unroll
+        for (int a = 0; a < kDirAcc; ++a) {
+            if (a < S.nacc) {
+                unsigned long long* p = area + (d * kDirAcc + a) * 32 + lane;
+                unsigned long long x = a == 0 ? c : *p;
+                if (a > 0)
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                *p = 0;
+                if (lane == 0 && x && g >= 0) red_add_u64(&S.acc[g * S.nacc + a], x);
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// Rows of a lane (pass bits `ok`, slots id[j]) into its lane tables: rows
+// with the same slot folded first, so that the read-add-writes of the
+// remaining rows touch distinct addresses and issue together instead of
+// forming one dependent chain through shared memory.
+__device__ __forceinline__ void dir_rmw(const GroupDirectArgs& A, unsigned long long* area, uint32_t ok,
+                                        const int (&id)[4], int64_t (&val)[kDirSums][4], int lane) {
+    uint32_t act = ok;
+    unsigned long long cnt[4] = {1, 1, 1, 1};
+#pragma unroll
+    for (int j = 1; j < 4; ++j) {
+        bool done = false;
+#pragma unroll
+        for (int k = 0; k < j; ++k) {
+            if (!done && ((act >> k) & 1u) && ((act >> j) & 1u) && id[k] == id[j]) {
+                cnt[k] += cnt[j];
+#pragma unroll
+                for (int a = 0; a < kDirSums; ++a) val[a][k] += val[a][j];
+                act &= ~(1u << j);
+                done = true;
+            }
+        }
+    }
+    const int nacc = A.S.nacc;
+    unsigned long long* p[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)  // (rows outside `act` are not touched: their ids may be anything)
+        p[j] = area + (static_cast<unsigned>(id[j]) < static_cast<unsigned>(kDirSlots) ? id[j] : 0) * (kDirAcc * 32) + lane;
+#pragma unroll
+    for (int a = 0; a < kDirAcc; ++a) {
+        if (a < nacc) {
+            unsigned long long old[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if ((act >> j) & 1u) old[j] = p[j][a * 32];
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if ((act >> j) & 1u)
+                    p[j][a * 32] = old[j] + (a == 0 ? cnt[j] : static_cast<unsigned long long>(val[a - 1][j]));
+        }
+    }
+}
+
 // The four rows of every lane (pass bits `ok`) into the lane tables: ids from
-// the warp's key list (extended with new keys), rows of a lane with the same
-// id folded, then one read-add-write per (distinct id, accumulator).  False,
-// with nothing added, when the list would overflow.
+// the warp's key list (extended with new keys), then dir_rmw.  False, with
+// nothing added, when the list would overflow.
 __device__ __forceinline__ bool dir_lane_step(const GroupDirectArgs& A, unsigned long long* area,
                                               uint64_t (&dk)[kDirSlots], int& nused, uint32_t ok,
                                               const uint64_t (&key)[4], int64_t (&val)[kDirSums][4], int lane) {
@@ -202,53 +365,22 @@ __device__ __forceinline__ bool dir_lane_step(const GroupDirectArgs& A, unsigned
         for (int j = 0; j < 4; ++j) id[j] = nid[j];
         nused = nn;
     }
-    // fold rows of this lane that share a group
-    uint32_t act = ok;
-    unsigned long long cnt[4] = {1, 1, 1, 1};
-#pragma unroll
-    for (int j = 1; j < 4; ++j) {
-        bool done = false;
-#pragma unroll
-        for (int k = 0; k < j; ++k) {
-            if (!done && ((act >> k) & 1u) && ((act >> j) & 1u) && id[k] == id[j]) {
-                cnt[k] += cnt[j];
-#pragma unroll
-                for (int a = 0; a < kDirSums; ++a) val[a][k] += val[a][j];
-                act &= ~(1u << j);
-                done = true;
-            }
-        }
-    }
-    const int nacc = A.S.nacc;
-    unsigned long long* p[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) p[j] = area + (id[j] < 0 ? 0 : id[j]) * (kDirAcc * 32) + lane;
-#pragma unroll
-    for (int a = 0; a < kDirAcc; ++a) {
-        if (a < nacc) {
-            unsigned long long old[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if ((act >> j) & 1u) old[j] = p[j][a * 32];
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if ((act >> j) & 1u)
-                    p[j][a * 32] = old[j] + (a == 0 ? cnt[j] : static_cast<unsigned long long>(val[a - 1][j]));
-        }
-    }
+    dir_rmw(A, area, ok, id, val, lane);
     return true;
 }
 
-// One warp step: the quad q of every lane (kFull: every lane's quad holds
-// four rows of the table; otherwise quads at or past nq hold none).
-template <bool kFull>
-__device__ __forceinline__ void dir_step(const GroupDirectArgs& A, unsigned long long* area, uint64_t (&dk)[kDirSlots],
-                                         int& nused, long long q, int lane) {
+// One warp step: the quad q of every lane.  kSlot: every lane's quad holds
+// four rows of the table and sits in the warp slot; otherwise quads at or
+// past the end hold none and are read from global memory.
+template <bool kSlot, bool kDense>
+__device__ __forceinline__ void dir_step(const GroupDirectArgs& A, const DirDense& Dn, unsigned long long* area,
+                                         unsigned char* slot, uint64_t (&dk)[kDirSlots], int& nused, long long q,
+                                         int lane, long long next = -1) {
     const GroupSpec& S = A.S;
     const long long n = A.n;
     uint32_t ok = 0xFu;
     long long qq = q;
-    if (!kFull) {
+    if (!kSlot) {
         const long long nq = (n + 3) / 4;
         qq = q < nq ? q : 0;
         ok = 0;
@@ -261,7 +393,7 @@ __device__ __forceinline__ void dir_step(const GroupDirectArgs& A, unsigned long
         if (c < A.ncond) {
             const DirCond& cd = A.cond[c];
             int64_t x[4];
-            dir_load4<kFull>(cd.p, cd.type, qq, n, x);
+            dir_load4<kSlot>(A, slot, cd.pc, cd.p, cd.type, qq, lane, x);
             uint32_t m = 0;
             if (cd.type == TQP_I64) {
 #pragma unroll
@@ -275,15 +407,28 @@ __device__ __forceinline__ void dir_step(const GroupDirectArgs& A, unsigned long
             ok &= cd.negate ? ~m : m;
         }
     }
-    if (!__any_sync(0xffffffffu, ok != 0)) return;
+    if (!__any_sync(0xffffffffu, ok != 0)) {
+        if (kSlot && next >= 0) {
+            __syncwarp();
+            dir_prefetch(A, slot, next, lane);
+        }
+        return;
+    }
     uint64_t key[4] = {0, 0, 0, 0};
+    int id[4] = {0, 0, 0, 0};
 #pragma unroll
     for (int i = 0; i < kDirKeys; ++i) {
         if (i < A.ngc) {
             int64_t x[4];
-            dir_load4<kFull>(A.key[i].p, A.key[i].type, qq, n, x);
+            dir_load4<kSlot>(A, slot, A.key[i].pc, A.key[i].p, A.key[i].type, qq, lane, x);
             const int b = S.key_bits[i];
-            if (b == 8) {
+            if constexpr (kDense) {  // mixed-radix slot index (every key lies in its column's range)
+                const long long lo = Dn.kmin[i];
+                const int st = Dn.stride[i];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) id[j] += static_cast<int>(x[j] - lo) * st;
+            } else {
+              if (b == 8) {
 #pragma unroll
                 for (int j = 0; j < 4; ++j) key[j] = (key[j] << 8) | (static_cast<uint64_t>(x[j]) & 0xFFu);
             } else if (b == 32) {
@@ -294,16 +439,17 @@ __device__ __forceinline__ void dir_step(const GroupDirectArgs& A, unsigned long
 #pragma unroll
                 for (int j = 0; j < 4; ++j) key[j] = static_cast<uint64_t>(x[j]) ^ 0x8000000000000000ull;
             }
+            }
         }
     }
     int64_t val[kDirSums][4];
 #pragma unroll
     for (int a = 0; a < kDirSums; ++a) {
         if (a < A.nsum) {
-            dir_factor<kFull>(A.f[a][0], qq, n, val[a]);
+            dir_factor<kSlot>(A, slot, A.f[a][0], qq, lane, val[a]);
             if (A.f[a][1].kind != kFacConst || A.f[a][1].b != 1) {
                 int64_t y[4];
-                dir_factor<kFull>(A.f[a][1], qq, n, y);
+                dir_factor<kSlot>(A, slot, A.f[a][1], qq, lane, y);
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
                     val[a][j] = static_cast<int64_t>(static_cast<uint64_t>(val[a][j]) * static_cast<uint64_t>(y[j]));
@@ -312,6 +458,14 @@ __device__ __forceinline__ void dir_step(const GroupDirectArgs& A, unsigned long
 #pragma unroll
             for (int j = 0; j < 4; ++j) val[a][j] = 0;
         }
+    }
+    if (kSlot && next >= 0) {  // every slot value is in registers: refill the slot with the next step
+        __syncwarp();
+        dir_prefetch(A, slot, next, lane);
+    }
+    if constexpr (kDense) {
+        dir_rmw(A, area, ok, id, val, lane);
+        return;
     }
     if (dir_lane_step(A, area, dk, nused, ok, key, val, lane)) return;
     dir_flush(A, area, dk, nused, lane);  // list full: flush and start a new one
@@ -330,14 +484,32 @@ __device__ __forceinline__ void dir_step(const GroupDirectArgs& A, unsigned long
     }
 }
 
-// One CTA of the direct group-by: warps take 32 quads at a time in a
-// grid-stride loop (warp-uniform trip count); steps whose 32 quads all lie
-// within the table take the vector-load path.
-__device__ __forceinline__ void group_direct_block(const GroupDirectArgs& A, unsigned char* smem) {
-    const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
-    unsigned long long* area = reinterpret_cast<unsigned long long*>(smem) + w * kDirWarpWords;
-    for (int i = lane; i < kDirWarpWords; i += 32) area[i] = 0;
-    __syncwarp();
+// Dense-id parameters from the key ranges (one thread per CTA).
+__device__ __forceinline__ void dir_dense_init(const GroupDirectArgs& A, DirDense* Dn) {
+    Dn->dense = 0;
+    Dn->P = 1;
+    if (A.ngc > 0 && !A.kmeta) return;
+    long long P = 1;
+    for (int i = A.ngc - 1; i >= 0; --i) {
+        // encoded bounds compare as unsigned; rows exist, so elo <= ehi
+        const unsigned long long elo = ~A.kmeta[2 * i], ehi = A.kmeta[2 * i + 1];
+        if (ehi < elo || ehi - elo >= static_cast<unsigned long long>(kDirSlots)) return;
+        const unsigned long long r = ehi - elo + 1;
+        Dn->kmin[i] = static_cast<long long>(elo ^ (1ULL << 63));
+        Dn->range[i] = static_cast<int32_t>(r);
+        Dn->stride[i] = static_cast<int32_t>(P);
+        P *= static_cast<long long>(r);
+        if (P > kDirSlots) return;
+    }
+    Dn->P = static_cast<int32_t>(P);
+    Dn->dense = 1;
+}
+
+// The warp's grid-stride loop: 32 quads per step; a step whose quads all lie
+// within the table is fetched into the warp slot one step ahead.
+template <bool kDense>
+__device__ __forceinline__ void dir_loop(const GroupDirectArgs& A, const DirDense& Dn, unsigned long long* area,
+                                         unsigned char* slot, int lane, int w) {
     uint64_t dk[kDirSlots];
 #pragma unroll
     for (int d = 0; d < kDirSlots; ++d) dk[d] = 0;
@@ -345,11 +517,105 @@ __device__ __forceinline__ void group_direct_block(const GroupDirectArgs& A, uns
     const long long nq = (A.n + 3) / 4;
     const long long nfull = A.n / 4;  // quads with four rows
     const long long stride = static_cast<long long>(gridDim.x) * kDirThreads;
-    for (long long base = static_cast<long long>(blockIdx.x) * kDirThreads + w * 32; base < nq; base += stride) {
-        if (base + 32 <= nfull) dir_step<true>(A, area, dk, nused, base + lane, lane);
-        else dir_step<false>(A, area, dk, nused, base + lane, lane);
+    long long base = static_cast<long long>(blockIdx.x) * kDirThreads + w * 32;
+    bool have = base + 32 <= nfull;  // the slot receives step `base`
+    if (have) dir_prefetch(A, slot, base + lane, lane);
+    for (; base < nq; base += stride) {
+        if (have) {
+            const long long next = base + stride;
+            const bool nhave = next + 32 <= nfull;
+            cp_async_wait_all();
+            __syncwarp();
+            // dir_step moves the step's values to registers, then refills the slot
+            dir_step<true, kDense>(A, Dn, area, slot, dk, nused, base + lane, lane, nhave ? next + lane : -1);
+            have = nhave;
+        } else {
+            dir_step<false, kDense>(A, Dn, area, slot, dk, nused, base + lane, lane);
+        }
     }
-    dir_flush(A, area, dk, nused, lane);
+    if constexpr (kDense) dir_flush_dense(A, Dn, area, lane);
+    else dir_flush(A, area, dk, nused, lane);
+}
+
+// One CTA of the direct group-by.
+__device__ __forceinline__ void group_direct_block(const GroupDirectArgs& A, unsigned char* smem) {
+    const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
+    unsigned long long* area = reinterpret_cast<unsigned long long*>(smem) + w * kDirWarpWords;
+    unsigned char* slot = smem + kDirTableBytes + w * kDirSlotBytes;
+    DirDense* Dn = reinterpret_cast<DirDense*>(smem + kDirDenseOff);
+    if (threadIdx.x == 0) dir_dense_init(A, Dn);
+    for (int i = lane; i < kDirWarpWords; i += 32) area[i] = 0;
+    __syncthreads();
+    if (Dn->dense) dir_loop<true>(A, *Dn, area, slot, lane, w);
+    else dir_loop<false>(A, *Dn, area, slot, lane, w);
+}
+
+// First pass: [min, max] of every key column (encoded as the kmeta words;
+// zeroed before the launch).  Each column is read in 16-byte chunks, four
+// chunks per thread in flight; the ragged end is read element by element.
+__device__ __forceinline__ void dir_minmax16(const uint4& v, int type, unsigned long long& mx, unsigned long long& mn) {
+    auto upd = [&](long long x) {
+        const unsigned long long e = static_cast<unsigned long long>(x) ^ (1ULL << 63);
+        mx = e > mx ? e : mx;
+        mn = ~e > mn ? ~e : mn;
+    };
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+    if (type == TQP_I64) {
+        upd(static_cast<long long>((static_cast<unsigned long long>(w[1]) << 32) | w[0]));
+        upd(static_cast<long long>((static_cast<unsigned long long>(w[3]) << 32) | w[2]));
+    } else if (type == TQP_I32) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) upd(static_cast<int32_t>(w[k]));
+    } else {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) upd((w[k / 4] >> (8 * (k % 4))) & 0xFFu);
+    }
+}
+
+__device__ __forceinline__ void group_direct_range_block(const GroupDirectArgs& A, unsigned long long* kmeta) {
+    __shared__ unsigned long long red[kDirThreads / 32][2];
+    const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
+    const long long n = A.n;
+    const long long tid = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    const long long nth = static_cast<long long>(gridDim.x) * blockDim.x;
+    for (int i = 0; i < A.ngc; ++i) {
+        const int type = A.key[i].type;
+        const int es = type == TQP_I64 ? 8 : (type == TQP_I32 ? 4 : 1);
+        const uint4* p = reinterpret_cast<const uint4*>(A.key[i].p);
+        const long long nchunk = n * es / 16;  // whole 16-byte chunks
+        unsigned long long mx = 0, mn = 0;
+        long long c = tid;
+        for (; c + 3 * nth < nchunk; c += 4 * nth) {
+            uint4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = __ldg(p + c + u * nth);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) dir_minmax16(v[u], type, mx, mn);
+        }
+        for (; c < nchunk; c += nth) dir_minmax16(__ldg(p + c), type, mx, mn);
+        for (long long r = nchunk * 16 / es + tid; r < n; r += nth) {
+            const unsigned long long e = static_cast<unsigned long long>(ldg_typed(A.key[i].p, type, r)) ^ (1ULL << 63);
+            mx = e > mx ? e : mx;
+            mn = ~e > mn ? ~e : mn;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long a = __shfl_xor_sync(0xffffffffu, mx, o), b = __shfl_xor_sync(0xffffffffu, mn, o);
+            mx = a > mx ? a : mx;
+            mn = b > mn ? b : mn;
+        }
+        if (lane == 0) {
+            red[w][0] = mn;
+            red[w][1] = mx;
+        }
+        __syncthreads();
+        if (threadIdx.x < 2) {
+            unsigned long long v = 0;
+            for (int k = 0; k < static_cast<int>(blockDim.x) / 32; ++k) v = red[k][threadIdx.x] > v ? red[k][threadIdx.x] : v;
+            atomicMax(&kmeta[2 * i + threadIdx.x], v);
+        }
+        __syncthreads();
+    }
 }
 
 }  // namespace tqp

@@ -174,3 +174,31 @@ def test_few_groups_capacity_exceeded(ctx):
     key = (np.arange(200_000) % 100).astype(np.int32)
     st, G, *_ = gpu_groupby(ctx, [key], [], [0], [("count", None)], capacity=64)
     assert st == tqp.ERR_CAPACITY and G == -1
+
+
+@pytest.mark.parametrize("case", ["i32_i32_negative", "i64_negative", "u8_eight", "nine_values", "single_value"])
+def test_few_groups_dense_ids(ctx, case):
+    """Key columns whose ranges multiply to at most eight slots take mixed-radix
+    slot ids (keys rebuilt from the slot index at the flush); nine values do not."""
+    rng = np.random.default_rng(hash(case) % 2**32)
+    n = 123_457
+    val = rng.integers(-10**12, 10**12, n).astype(np.int64)
+    if case == "i32_i32_negative":
+        a = (rng.integers(0, 2, n) - 2**31).astype(np.int32)
+        b = rng.integers(-5, -2, n).astype(np.int32)
+        cols, gc = [a, b, val], [0, 1]
+    elif case == "i64_negative":
+        a = (rng.integers(0, 7, n) - 2**62).astype(np.int64)
+        cols, gc = [a, val], [0]
+    elif case == "u8_eight":
+        a = rng.integers(248, 256, n).astype(np.uint8)
+        cols, gc = [a, val], [0]
+    elif case == "nine_values":
+        a = rng.integers(-4, 5, n).astype(np.int32)
+        cols, gc = [a, val], [0]
+    else:
+        a = np.full(n, 2**31 - 1, dtype=np.int32)
+        cols, gc = [a, val], [0]
+    vc = len(cols) - 1
+    check(ctx, cols, [(vc, "gt", -10**11)], gc, [("sum", [("col", vc)]), ("count", None), ("avg", [("col", vc)])],
+          capacity=16)

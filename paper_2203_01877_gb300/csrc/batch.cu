@@ -12,15 +12,19 @@
 //   number    dense group ids (claim-table ranges)
 //   remap     dimension row -> dense group id
 //   direct    dense ids into the slots of unique build keys
+//   few-group group-bys (at most 64 groups, closed-form sums): the key-range
+//             pass, then the direct kernel (vector reads one warp step ahead,
+//             lane-private tables), each job a contiguous range of blocks
 //   scan      one persistent launch of the staged scan engine per body kind
 //             (filter, group-by, joined aggregation): CTAs draw chunk
 //             tickets across the tables of every job of that kind (uneven
 //             sizes balance themselves); each kind gets its own shared-memory
 //             layout and occupancy
+//   fold      joins that aggregated by join key: key totals -> groups
 //   compact   selection masks -> row ids
 //   finalize  one CTA per small group table (keys ascending)
-//   top-k     radix select of the k-th largest (three histogram passes, a
-//             collect and one sort per plan); the bitonic tournament, one
+//   top-k     radix select of the k-th largest (histogram passes, a collect
+//             and one sort per plan); the bitonic tournament, one
 //             launch per level, only for plans whose select ends in ties
 // A tqp_batch is lowered and captured into a CUDA graph once; each run is
 // one graph launch.  Plans outside these shapes (large group tables without
@@ -35,10 +39,12 @@
 #include "dimgroups.cuh"
 #include "dim.cuh"
 #include "finalize.cuh"
+#include "groupdirect.cuh"
 
 namespace tqp {
 
 tqp_status run_plan_one(tqp_ctx* ctx, const tqp_plan* p, const tqp_result* r, cudaStream_t stream);
+bool lower_group_direct(const tqp_table* t, const GroupArgs& A, long long max_groups, GroupDirectArgs* D);
 
 constexpr int kBatchTile = 1024;
 constexpr int kBatchStages = 3;
@@ -116,6 +122,38 @@ struct TopJob {
     long long sel_block;    // first block in the radix-select passes
     long long sel_nblocks;
 };
+
+// The fold of a join that aggregated by join key first (blocks
+// [first_block, first_block + nblocks) of its launch).
+struct FoldJob {
+    JoinHT H;
+    const unsigned char* dkey;
+    int32_t dkey_type;
+    int32_t nk;
+    long long nd;
+    const uint32_t* dgs;
+    GroupSpec S;
+    const unsigned long long* kacc;
+    unsigned long long* acc;
+    int64_t* d_num_joined;
+    int64_t* d_sum;
+    int32_t has_sum;
+    int32_t pad;
+    long long first_block, nblocks;
+};
+constexpr long long kFoldRowsPerBlock = 8 * kFoldThreads;
+
+// A few-groups group-by run by the direct kernel: blocks [first_block,
+// first_block + nblocks) of its launch, and of the key-range pass.
+struct DirJob {
+    GroupDirectArgs A;
+    unsigned long long* kmeta;  // = A.kmeta (zeroed by the fill), written by the range pass
+    long long first_block, nblocks;
+    long long range_first, range_nblocks;
+};
+constexpr int kDirArgsBytes = (static_cast<int>(sizeof(GroupDirectArgs)) + 127) / 128 * 128;
+constexpr long long kDirRowsPerBlock = 32768;    // direct kernel: 32 128-row steps per warp
+constexpr long long kDirRangeRowsPerBlock = 65536;
 
 struct TopItem {
     int32_t job;
@@ -245,6 +283,26 @@ __global__ void __launch_bounds__(kCompactThreads) k_b_compact(const CompactJob*
     compact_block(c.mask, c.block_tot, c.n, c.row_ids, c.capacity, static_cast<long long>(blockIdx.x) - c.first_block);
 }
 
+__global__ void __launch_bounds__(kFoldThreads) k_b_fold(const FoldJob* J, const int32_t* bjob) {
+    const FoldJob& f = J[bjob[blockIdx.x]];
+    keyfirst_fold_block(f.H, f.dkey, f.dkey_type, f.nd, f.dgs, f.S, f.kacc, f.nk, f.has_sum, f.acc, f.d_num_joined,
+                        f.d_sum, static_cast<long long>(blockIdx.x) - f.first_block, f.nblocks);
+}
+
+__global__ void __launch_bounds__(kDirThreads) k_b_grange(const DirJob* J, const int32_t* bjob) {
+    const DirJob& j = J[bjob[blockIdx.x]];
+    group_direct_range_block(j.A, j.kmeta, static_cast<long long>(blockIdx.x) - j.range_first, j.range_nblocks);
+}
+
+// The job's arguments are copied into shared memory after the kernel's own
+// layout, so the hot loop reads them with shared-memory loads.
+__global__ void __launch_bounds__(kDirThreads, kDirMinBlocks) k_b_gdirect(const DirJob* J, const int32_t* bjob) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    const DirJob& j = J[bjob[blockIdx.x]];
+    const GroupDirectArgs& A = stage_args(j.A, dsm + kDirSmemBytes);
+    group_direct_block(A, dsm, static_cast<long long>(blockIdx.x) - j.first_block, j.nblocks);
+}
+
 __global__ void __launch_bounds__(kFinThreads) k_b_finalize(const FinJob* F) {
     extern __shared__ __align__(16) unsigned char fsm[];
     const FinJob& f = F[blockIdx.x];
@@ -300,14 +358,17 @@ struct tqp_batch {
     std::vector<CompactJob> compact;
     std::vector<FinJob> fin;
     std::vector<TopJob> top;
+    std::vector<DirJob> gdir;
+    std::vector<FoldJob> fold;
     std::vector<std::vector<TopItem>> levels;
     // block -> job maps, concatenated
     std::vector<int32_t> maps;
     long long fill_blocks = 0, row_blocks = 0, num_blocks = 0, slot_blocks = 0, compact_blocks = 0, top0_blocks = 0,
-              sel_blocks = 0;
+              sel_blocks = 0, grange_blocks = 0, gdirect_blocks = 0, fold_blocks = 0;
     long long scan_chunks[kKinds] = {0, 0, 0};
     std::vector<long long> level_blocks;
-    size_t off_fill = 0, off_row = 0, off_num = 0, off_slot = 0, off_compact = 0, off_top0 = 0, off_sel = 0;
+    size_t off_fill = 0, off_row = 0, off_num = 0, off_slot = 0, off_compact = 0, off_top0 = 0, off_sel = 0,
+           off_grange = 0, off_gdirect = 0, off_fold = 0;
     size_t off_scan[kKinds] = {0, 0, 0};
     std::vector<size_t> off_level;
     // small zeroed counters share one slab (one fill range)
@@ -321,6 +382,8 @@ struct tqp_batch {
     CompactJob* d_compact = nullptr;
     FinJob* d_fin = nullptr;
     TopJob* d_top = nullptr;
+    DirJob* d_gdir = nullptr;
+    FoldJob* d_fold = nullptr;
     std::vector<TopItem*> d_levels;
     int32_t* d_maps = nullptr;
     unsigned long long* d_ticket[kKinds] = {nullptr, nullptr, nullptr};
@@ -508,6 +571,24 @@ static tqp_status add_group_job(tqp_batch* b, const tqp_plan* p, const tqp_resul
         F.total_out = r->d_total_groups;
         b->fin.push_back(F);
     }
+    DirJob D;
+    memset(&D, 0, sizeof(D));
+    if (lower_group_direct(t, A, maxg, &D.A)) {
+        D.A.S = A.S;
+        D.A.err = ctx->d_err;
+        if (D.A.ngc > 0) {
+            D.kmeta = counter(b);
+            D.A.kmeta = D.kmeta;
+            D.range_first = b->grange_blocks;
+            D.range_nblocks = (t->num_rows + kDirRangeRowsPerBlock - 1) / kDirRangeRowsPerBlock;
+            b->grange_blocks += D.range_nblocks;
+        }
+        D.first_block = b->gdirect_blocks;
+        D.nblocks = (t->num_rows + kDirRowsPerBlock - 1) / kDirRowsPerBlock;
+        b->gdirect_blocks += D.nblocks;
+        b->gdir.push_back(D);
+        return TQP_OK;
+    }
     if (A.G.ntiles > 0) b->scan[kJobGroup - 1].push_back(J);
     return TQP_OK;
 }
@@ -646,6 +727,33 @@ static tqp_status add_join_job(tqp_batch* b, const tqp_plan* p, const tqp_result
     A.d_num_rows = (p->emit_row_ids && r->d_row_ids) ? nullptr : r->d_num_rows;
     A.ctl.err = ctx->d_err;
     A.ctl.wait_cap = ctx->wait_cap;
+    // aggregation by join key first (used on the device only if the table is
+    // direct-mapped), as in the single-plan path
+    if (grouped && A.pjfast && A.fast && A.H.meta && A.G.ntiles > 0 && F->num_rows >= 2 * std::max<long long>(1, ndr)) {
+        A.nk = A.S.nacc + (A.has_sum ? 1 : 0);
+        const size_t kbytes = static_cast<size_t>(A.H.cap) * A.nk * 8;
+        A.kacc = static_cast<unsigned long long*>(balloc(b, kbytes));
+        if (!A.kacc) return arena_oom(ctx, kbytes);
+        add_fill(b, A.kacc, kbytes, kZero16);
+        FoldJob Fo;
+        memset(&Fo, 0, sizeof(Fo));
+        Fo.H = A.H;
+        Fo.dkey = static_cast<const unsigned char*>(D->cols[p->dim_key].data);
+        Fo.dkey_type = D->cols[p->dim_key].type;
+        Fo.nk = A.nk;
+        Fo.nd = ndr;
+        Fo.dgs = A.dgs;
+        Fo.S = A.S;
+        Fo.kacc = A.kacc;
+        Fo.acc = A.acc;
+        Fo.d_num_joined = A.d_num_joined;
+        Fo.d_sum = A.d_sum;
+        Fo.has_sum = A.has_sum;
+        Fo.first_block = b->fold_blocks;
+        Fo.nblocks = std::max<long long>(1, (ndr + kFoldRowsPerBlock - 1) / kFoldRowsPerBlock);
+        b->fold_blocks += Fo.nblocks;
+        b->fold.push_back(Fo);
+    }
     if (A.G.ntiles > 0) {
         b->scan[kJobJoin - 1].push_back(J);
     } else {
@@ -703,8 +811,9 @@ static bool batchable(const tqp_ctx* ctx, const tqp_plan* p, const tqp_result* r
 }
 
 static tqp_status lower_batch(tqp_batch* b, const tqp_plan* plans, const tqp_result* res, int32_t n) {
-    // per plan at most 4 counters (join + filter + top-k + spare) and the tickets
-    b->slab_bytes = static_cast<size_t>(kCounterBytes) * (4 * static_cast<size_t>(n) + kKinds + 1);
+    // per plan at most 6 counters (group table, key ranges, top-k, filter, a
+    // count, spare) and the tickets
+    b->slab_bytes = static_cast<size_t>(kCounterBytes) * (6 * static_cast<size_t>(n) + kKinds + 1);
     b->slab = static_cast<unsigned char*>(balloc(b, b->slab_bytes));
     if (!b->slab) return arena_oom(b->ctx, b->slab_bytes);
     add_fill(b, b->slab, b->slab_bytes, kZero16);
@@ -831,6 +940,12 @@ static void build_maps(tqp_batch* b) {
         b->off_scan[k] = M.size();
         for (size_t j = 0; j < b->scan[k].size(); ++j) push(j, job_ctl(b->scan[k][j]).nchunks);
     }
+    b->off_grange = M.size();
+    for (size_t j = 0; j < b->gdir.size(); ++j) push(j, b->gdir[j].range_nblocks);
+    b->off_gdirect = M.size();
+    for (size_t j = 0; j < b->gdir.size(); ++j) push(j, b->gdir[j].nblocks);
+    b->off_fold = M.size();
+    for (size_t j = 0; j < b->fold.size(); ++j) push(j, b->fold[j].nblocks);
     b->off_compact = M.size();
     for (size_t j = 0; j < b->compact.size(); ++j) push(j, (b->compact[j].n + kCompactRows - 1) / kCompactRows);
     b->off_sel = M.size();
@@ -893,6 +1008,11 @@ static tqp_status batch_launch(tqp_batch* b, cudaStream_t st) {
         if (b->slot_blocks)
             k_b_direct<<<static_cast<unsigned>(b->slot_blocks), kFlatThreads, 0, st>>>(b->d_build, M + b->off_slot);
     }
+    if (b->grange_blocks)
+        k_b_grange<<<static_cast<unsigned>(b->grange_blocks), kDirThreads, 0, st>>>(b->d_gdir, M + b->off_grange);
+    if (b->gdirect_blocks)
+        k_b_gdirect<<<static_cast<unsigned>(b->gdirect_blocks), kDirThreads, kDirSmemBytes + kDirArgsBytes, st>>>(
+            b->d_gdir, M + b->off_gdirect);
     if (b->scan_chunks[0])
         k_b_scan<FilterBody><<<b->scan_grid[0], kEngineThreads, b->scan_smem[0], st>>>(
             b->d_scan[0], M + b->off_scan[0], b->d_ticket[0], b->scan_chunks[0]);
@@ -902,6 +1022,8 @@ static tqp_status batch_launch(tqp_batch* b, cudaStream_t st) {
     if (b->scan_chunks[2])
         k_b_scan<PlanJoinBody><<<b->scan_grid[2], kEngineThreads, b->scan_smem[2], st>>>(
             b->d_scan[2], M + b->off_scan[2], b->d_ticket[2], b->scan_chunks[2]);
+    if (b->fold_blocks)
+        k_b_fold<<<static_cast<unsigned>(b->fold_blocks), kFoldThreads, 0, st>>>(b->d_fold, M + b->off_fold);
     if (b->compact_blocks)
         k_b_compact<<<static_cast<unsigned>(b->compact_blocks), kCompactThreads, 0, st>>>(b->d_compact,
                                                                                            M + b->off_compact);
@@ -946,8 +1068,9 @@ static tqp_status scan_shape(tqp_batch* b, int k) {
 // Lower, lay out and upload every batched job (no launch).
 static tqp_status batch_prepare(tqp_ctx* ctx, const tqp_plan* plans, const tqp_result* res, int32_t n, tqp_batch* b,
                                 cudaStream_t st) {
-    static bool attr_fin[kMaxDevices] = {};
+    static bool attr_fin[kMaxDevices] = {}, attr_dir[kMaxDevices] = {};
     TQP_TRY(allow_smem(ctx, reinterpret_cast<const void*>(k_b_finalize), attr_fin));
+    TQP_TRY(allow_smem(ctx, reinterpret_cast<const void*>(k_b_gdirect), attr_dir));
     TQP_TRY(lower_batch(b, plans, res, n));
     TQP_TRY(scan_shape<FilterBody>(b, 0));
     TQP_TRY(scan_shape<GroupBody>(b, 1));
@@ -961,6 +1084,8 @@ static tqp_status batch_prepare(tqp_ctx* ctx, const tqp_plan* plans, const tqp_r
     TQP_TRY(upload(b, b->compact, &b->d_compact, st));
     TQP_TRY(upload(b, b->fin, &b->d_fin, st));
     TQP_TRY(upload(b, b->top, &b->d_top, st));
+    TQP_TRY(upload(b, b->gdir, &b->d_gdir, st));
+    TQP_TRY(upload(b, b->fold, &b->d_fold, st));
     b->d_levels.resize(b->levels.size());
     for (size_t L = 0; L < b->levels.size(); ++L) TQP_TRY(upload(b, b->levels[L], &b->d_levels[L], st));
     TQP_TRY(upload(b, b->maps, &b->d_maps, st));

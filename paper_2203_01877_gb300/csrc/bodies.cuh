@@ -891,6 +891,61 @@ struct PlanJoinBody {
 // foreign key or a summed column is not staged or a sum is not in closed form).
 void lower_join_fast(PlanJoinArgs* A);
 
+// Fold the key-first accumulators into the groups: every dimension row adds
+// its key's entry (the fact rows that matched it) to its group, and to the
+// joined-pair count and the ungrouped sum (acc[0], acc[1]).  Block vb of vg;
+// the last block to finish (counted in acc[4]) writes those two results.
+// Nothing to do for a hashed table: the probe aggregated by group.
+constexpr int kFoldThreads = 256;
+__device__ __forceinline__ void keyfirst_fold_block(const JoinHT& H, const unsigned char* dkey, int dkey_type,
+                                                    long long nd, const uint32_t* dgs, const GroupSpec& S,
+                                                    const unsigned long long* kacc, int nk, int has_sum,
+                                                    unsigned long long* acc, int64_t* d_num_joined, int64_t* d_sum,
+                                                    long long vb, long long vg) {
+    long long kmin;
+    if (!ht_is_direct(H, &kmin)) return;
+    const unsigned long long krange = static_cast<unsigned long long>(__ldg(&H.meta[1]) - kmin) + 1;
+    unsigned long long joined = 0;
+    long long sum = 0;
+    for (long long d = vb * kFoldThreads + threadIdx.x; d < nd; d += vg * kFoldThreads) {
+        const unsigned long long e =
+            static_cast<uint64_t>(ldg_typed(dkey, dkey_type, d)) - static_cast<uint64_t>(kmin);
+        if (e >= krange) continue;
+        const unsigned long long* a = kacc + e * nk;
+        const unsigned long long c = __ldg(&a[0]);
+        if (!c) continue;
+        unsigned long long* ga = S.acc + static_cast<long long>(__ldg(&dgs[d])) * S.nacc;
+        red_add_u64(&ga[0], c);
+        for (int i = 1; i < S.nacc; ++i) red_add_u64(&ga[i], __ldg(&a[i]));
+        joined += c;
+        if (has_sum) sum += static_cast<long long>(__ldg(&a[S.nacc]));
+    }
+    __shared__ unsigned long long rj[kFoldThreads / 32];
+    __shared__ long long rs[kFoldThreads / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        joined += __shfl_xor_sync(0xffffffffu, joined, o);
+        sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    }
+    if (threadIdx.x % 32 == 0) {
+        rj[threadIdx.x / 32] = joined;
+        rs[threadIdx.x / 32] = sum;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    for (int w = 1; w < kFoldThreads / 32; ++w) {
+        joined += rj[w];
+        sum += rs[w];
+    }
+    if (joined) atomicAdd(&acc[0], joined);
+    if (sum) atomicAdd(&acc[1], static_cast<unsigned long long>(sum));
+    __threadfence();
+    if (atomicAdd(&acc[4], 1ULL) != static_cast<unsigned long long>(vg) - 1ULL) return;
+    __threadfence();
+    if (d_num_joined) *d_num_joined = static_cast<int64_t>(atomicAdd(&acc[0], 0ULL));
+    if (d_sum) *d_sum = static_cast<int64_t>(atomicAdd(&acc[1], 0ULL));
+}
+
 // ---- selection-mask expansion (second filter kernel) ------------------------------
 
 // Expand the selection mask of rows [b * kCompactRows, ...) into row ids.

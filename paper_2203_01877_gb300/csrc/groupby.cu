@@ -43,12 +43,12 @@ __global__ void __launch_bounds__(kEngineThreads, GroupBody::kMinBlocks) k_group
 
 __global__ void __launch_bounds__(kDirThreads, kDirMinBlocks) k_groupby_direct(const __grid_constant__ GroupDirectArgs A) {
     extern __shared__ __align__(16) unsigned char dsm[];
-    group_direct_block(A, dsm);
+    group_direct_block(A, dsm, blockIdx.x, gridDim.x);
 }
 
 __global__ void __launch_bounds__(kDirThreads) k_groupby_keyrange(const __grid_constant__ GroupDirectArgs A,
                                                                   unsigned long long* kmeta) {
-    group_direct_range_block(A, kmeta);
+    group_direct_range_block(A, kmeta, blockIdx.x, gridDim.x);
 }
 
 // ---- finalize ----------------------------------------------------------------
@@ -316,7 +316,7 @@ void lower_group_fast(GroupArgs* A) {
 // column number, so that the lowered forms name columns.
 constexpr long long kDirMaxGroups = 64;
 
-static bool lower_group_direct(const tqp_table* t, const GroupArgs& A, long long max_groups, GroupDirectArgs* D) {
+bool lower_group_direct(const tqp_table* t, const GroupArgs& A, long long max_groups, GroupDirectArgs* D) {
     if (max_groups > kDirMaxGroups || A.ncond > kDirConds || A.S.nacc > kDirAcc || t->num_rows <= 0) return false;
     ScanGeom G;
     memset(&G, 0, sizeof(G));

@@ -509,15 +509,15 @@ __device__ __forceinline__ void dir_dense_init(const GroupDirectArgs& A, DirDens
 // within the table is fetched into the warp slot one step ahead.
 template <bool kDense>
 __device__ __forceinline__ void dir_loop(const GroupDirectArgs& A, const DirDense& Dn, unsigned long long* area,
-                                         unsigned char* slot, int lane, int w) {
+                                         unsigned char* slot, int lane, int w, long long vb, long long vg) {
     uint64_t dk[kDirSlots];
 #pragma unroll
     for (int d = 0; d < kDirSlots; ++d) dk[d] = 0;
     int nused = 0;
     const long long nq = (A.n + 3) / 4;
     const long long nfull = A.n / 4;  // quads with four rows
-    const long long stride = static_cast<long long>(gridDim.x) * kDirThreads;
-    long long base = static_cast<long long>(blockIdx.x) * kDirThreads + w * 32;
+    const long long stride = vg * kDirThreads;
+    long long base = vb * kDirThreads + w * 32;
     bool have = base + 32 <= nfull;  // the slot receives step `base`
     if (have) dir_prefetch(A, slot, base + lane, lane);
     for (; base < nq; base += stride) {
@@ -537,8 +537,9 @@ __device__ __forceinline__ void dir_loop(const GroupDirectArgs& A, const DirDens
     else dir_flush(A, area, dk, nused, lane);
 }
 
-// One CTA of the direct group-by.
-__device__ __forceinline__ void group_direct_block(const GroupDirectArgs& A, unsigned char* smem) {
+// One CTA of the direct group-by: block vb of vg blocks working on this table.
+__device__ __forceinline__ void group_direct_block(const GroupDirectArgs& A, unsigned char* smem, long long vb,
+                                                   long long vg) {
     const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
     unsigned long long* area = reinterpret_cast<unsigned long long*>(smem) + w * kDirWarpWords;
     unsigned char* slot = smem + kDirTableBytes + w * kDirSlotBytes;
@@ -546,38 +547,28 @@ __device__ __forceinline__ void group_direct_block(const GroupDirectArgs& A, uns
     if (threadIdx.x == 0) dir_dense_init(A, Dn);
     for (int i = lane; i < kDirWarpWords; i += 32) area[i] = 0;
     __syncthreads();
-    if (Dn->dense) dir_loop<true>(A, *Dn, area, slot, lane, w);
-    else dir_loop<false>(A, *Dn, area, slot, lane, w);
+    if (Dn->dense) dir_loop<true>(A, *Dn, area, slot, lane, w, vb, vg);
+    else dir_loop<false>(A, *Dn, area, slot, lane, w, vb, vg);
 }
 
 // First pass: [min, max] of every key column (encoded as the kmeta words;
 // zeroed before the launch).  Each column is read in 16-byte chunks, four
-// chunks per thread in flight; the ragged end is read element by element.
-__device__ __forceinline__ void dir_minmax16(const uint4& v, int type, unsigned long long& mx, unsigned long long& mn) {
-    auto upd = [&](long long x) {
-        const unsigned long long e = static_cast<unsigned long long>(x) ^ (1ULL << 63);
-        mx = e > mx ? e : mx;
-        mn = ~e > mn ? ~e : mn;
-    };
-    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-    if (type == TQP_I64) {
-        upd(static_cast<long long>((static_cast<unsigned long long>(w[1]) << 32) | w[0]));
-        upd(static_cast<long long>((static_cast<unsigned long long>(w[3]) << 32) | w[2]));
-    } else if (type == TQP_I32) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) upd(static_cast<int32_t>(w[k]));
-    } else {
-#pragma unroll
-        for (int k = 0; k < 16; ++k) upd((w[k / 4] >> (8 * (k % 4))) & 0xFFu);
-    }
+// chunks per thread in flight, and reduced in its own width: four bytes per
+// instruction for uint8 (SIMD byte min/max), 32-bit for int32; the ragged
+// end is read element by element.
+__device__ __forceinline__ void dir_enc_update(long long x, unsigned long long& mx, unsigned long long& mn) {
+    const unsigned long long e = static_cast<unsigned long long>(x) ^ (1ULL << 63);
+    mx = e > mx ? e : mx;
+    mn = ~e > mn ? ~e : mn;
 }
 
-__device__ __forceinline__ void group_direct_range_block(const GroupDirectArgs& A, unsigned long long* kmeta) {
+__device__ __forceinline__ void group_direct_range_block(const GroupDirectArgs& A, unsigned long long* kmeta,
+                                                         long long vb, long long vg) {
     __shared__ unsigned long long red[kDirThreads / 32][2];
     const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
     const long long n = A.n;
-    const long long tid = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
-    const long long nth = static_cast<long long>(gridDim.x) * blockDim.x;
+    const long long tid = vb * blockDim.x + threadIdx.x;
+    const long long nth = vg * blockDim.x;
     for (int i = 0; i < A.ngc; ++i) {
         const int type = A.key[i].type;
         const int es = type == TQP_I64 ? 8 : (type == TQP_I32 ? 4 : 1);
@@ -585,19 +576,66 @@ __device__ __forceinline__ void group_direct_range_block(const GroupDirectArgs& 
         const long long nchunk = n * es / 16;  // whole 16-byte chunks
         unsigned long long mx = 0, mn = 0;
         long long c = tid;
-        for (; c + 3 * nth < nchunk; c += 4 * nth) {
-            uint4 v[4];
+        if (type == TQP_U8) {
+            unsigned lo4 = 0xFFFFFFFFu, hi4 = 0;
+            for (; c + 3 * nth < nchunk; c += 4 * nth) {
+                uint4 v[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) v[u] = __ldg(p + c + u * nth);
+                for (int u = 0; u < 4; ++u) v[u] = __ldg(p + c + u * nth);
 #pragma unroll
-            for (int u = 0; u < 4; ++u) dir_minmax16(v[u], type, mx, mn);
+                for (int u = 0; u < 4; ++u) {
+                    lo4 = __vminu4(__vminu4(lo4, v[u].x), __vminu4(v[u].y, __vminu4(v[u].z, v[u].w)));
+                    hi4 = __vmaxu4(__vmaxu4(hi4, v[u].x), __vmaxu4(v[u].y, __vmaxu4(v[u].z, v[u].w)));
+                }
+            }
+            for (; c < nchunk; c += nth) {
+                const uint4 v = __ldg(p + c);
+                lo4 = __vminu4(__vminu4(lo4, v.x), __vminu4(v.y, __vminu4(v.z, v.w)));
+                hi4 = __vmaxu4(__vmaxu4(hi4, v.x), __vmaxu4(v.y, __vmaxu4(v.z, v.w)));
+            }
+            if (lo4 != 0xFFFFFFFFu || hi4 != 0) {  // at least one chunk seen
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    dir_enc_update((lo4 >> (8 * k)) & 0xFFu, mx, mn);
+                    dir_enc_update((hi4 >> (8 * k)) & 0xFFu, mx, mn);
+                }
+            }
+        } else if (type == TQP_I32) {
+            int lo = INT_MAX, hi = INT_MIN;
+            bool seen = false;
+            for (; c + 3 * nth < nchunk; c += 4 * nth) {
+                uint4 v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) v[u] = __ldg(p + c + u * nth);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    lo = min(lo, min(min(static_cast<int>(v[u].x), static_cast<int>(v[u].y)),
+                                     min(static_cast<int>(v[u].z), static_cast<int>(v[u].w))));
+                    hi = max(hi, max(max(static_cast<int>(v[u].x), static_cast<int>(v[u].y)),
+                                     max(static_cast<int>(v[u].z), static_cast<int>(v[u].w))));
+                }
+                seen = true;
+            }
+            for (; c < nchunk; c += nth) {
+                const uint4 v = __ldg(p + c);
+                lo = min(lo, min(min(static_cast<int>(v.x), static_cast<int>(v.y)),
+                                 min(static_cast<int>(v.z), static_cast<int>(v.w))));
+                hi = max(hi, max(max(static_cast<int>(v.x), static_cast<int>(v.y)),
+                                 max(static_cast<int>(v.z), static_cast<int>(v.w))));
+                seen = true;
+            }
+            if (seen) {
+                dir_enc_update(lo, mx, mn);
+                dir_enc_update(hi, mx, mn);
+            }
+        } else {
+            for (; c < nchunk; c += nth) {
+                const uint4 v = __ldg(p + c);
+                dir_enc_update(static_cast<long long>((static_cast<unsigned long long>(v.y) << 32) | v.x), mx, mn);
+                dir_enc_update(static_cast<long long>((static_cast<unsigned long long>(v.w) << 32) | v.z), mx, mn);
+            }
         }
-        for (; c < nchunk; c += nth) dir_minmax16(__ldg(p + c), type, mx, mn);
-        for (long long r = nchunk * 16 / es + tid; r < n; r += nth) {
-            const unsigned long long e = static_cast<unsigned long long>(ldg_typed(A.key[i].p, type, r)) ^ (1ULL << 63);
-            mx = e > mx ? e : mx;
-            mn = ~e > mn ? ~e : mn;
-        }
+        for (long long r = nchunk * 16 / es + tid; r < n; r += nth) dir_enc_update(ldg_typed(A.key[i].p, type, r), mx, mn);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             const unsigned long long a = __shfl_xor_sync(0xffffffffu, mx, o), b = __shfl_xor_sync(0xffffffffu, mn, o);

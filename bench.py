@@ -495,6 +495,30 @@ def serving_workload(tqp, torch, dev, local, seconds=10.0, rate=2000.0, sweep=(2
     queries = [query(i) for i in range(nq_max)]
     setup_s = time.perf_counter() - t_setup
 
+    # the scan-aggregate query over the whole resident table (600M rows, 15.6 GB of its columns)
+    g600 = None
+    if fact_rows >= 100_000_000:
+        gctx = tqp.Context(local, 256 << 20)
+        gctx.set_autotune(True)
+        T = tqp.TableRef([fact[c] for c in names[:6]])
+        b = pool[0]
+        st = torch.cuda.current_stream()
+        fn = lambda: tqp.tqp_groupby_agg(gctx, T, [(0, "le", 2450)], [1, 2], q1_aggs, b["keys"], b["iv"],  # noqa
+                                         b["fv"], 64, b["ng"], st)
+        ms = _time_launches(torch, fn, 5, stream=st)
+        gctx.check(st)
+        ng = int(b["ng"].item())
+        counted = int(b["iv"][:ng * 5].view(ng, 5)[:, 3].sum().item())
+        expect = int((fact["date"] <= 2450).sum().item())
+        alg = fact_rows * 26
+        g600 = {"workload": f"{fact_rows // 1_000_000}M rows (the resident serving table); date<=2450; GROUP BY "
+                            "(flag u8, status u8): SUM(qty), SUM(price), SUM(price*(100-disc)), COUNT, AVG(price)",
+                "ms": ms, "rows_per_s": fact_rows / (ms / 1e3), "algorithmic_bytes": alg,
+                "achieved_gbs": alg / (ms / 1e3) / 1e9, "frac_of_measured_hbm": alg / (ms / 1e3) / 1e9 / measured_peaks()[0],
+                "groups": ng, "counts_sum_to_passing_rows": counted == expect}
+        gctx.close()
+        del T
+
     def run(max_batch, max_inflight, qps, nq):
         budget = 4 << 30
         ctx = tqp.Context(local, budget + (256 << 20))
@@ -567,7 +591,7 @@ def serving_workload(tqp, torch, dev, local, seconds=10.0, rate=2000.0, sweep=(2
         "served_equals_alone_sample": bool(same), "sweep": rows,
         "qps_at_p99_le_10ms": {"continuous": best("continuous"), "one_at_a_time": best("one_at_a_time")},
         "setup_s": setup_s,
-    }
+    }, g600
 
 
 def profile_case(args):
@@ -734,7 +758,9 @@ def main():
         ops = secondary_workloads(tqp, torch, dev, local, 20, cpu_seconds=min(args.cpu_seconds, 5.0))
         ops["batched_512"] = batched_workload(tqp, torch, dev, local, 20)
         if not args.no_serving:
-            ops["serving"] = serving_workload(tqp, torch, dev, local, seconds=args.serve_seconds)
+            ops["serving"], g600 = serving_workload(tqp, torch, dev, local, seconds=args.serve_seconds)
+            if g600:
+                ops["groupby_600M_6groups"] = g600
     if rank == 0:
         peak, peak_kind = measured_peaks()
         alg = algorithmic_bytes(N_ROWS, k)

@@ -332,14 +332,15 @@ bool lower_group_direct(const tqp_table* t, const GroupArgs& A, long long max_gr
     D->n = t->num_rows;
     // the distinct columns a step reads, each with its block in a warp slot
     int lane_bytes = 0;
+    // (returns the column's block offset in a warp slot, -1 when the slot is full)
     auto pref = [&](int c) -> int {
         for (int i = 0; i < D->npref; ++i)
-            if (D->pref[i].p == G.col[c].ptr && D->pref[i].type == G.col[c].type) return i;
+            if (D->pref[i].p == G.col[c].ptr && D->pref[i].type == G.col[c].type) return D->pref[i].off;
         if (D->npref == kDirPrefCols) return -1;
         const int es = t->cols[c].type == TQP_I64 ? 8 : (t->cols[c].type == TQP_I32 ? 4 : 1);
         D->pref[D->npref] = DirPref{G.col[c].ptr, t->cols[c].type, 32 * lane_bytes};
         lane_bytes += 4 * es;
-        return D->npref++;
+        return D->pref[D->npref++].off;
     };
     CondFast cf[TQP_MAX_PREDS];
     int32_t fast = 0;
@@ -349,13 +350,13 @@ bool lower_group_direct(const tqp_table* t, const GroupArgs& A, long long max_gr
     for (int q = 0; q < A.ncond; ++q) {
         const int c = cf[q].soff;
         D->cond[q] = DirCond{G.col[c].ptr, cf[q].type, cf[q].negate, cf[q].lo, cf[q].span, pref(c), 0};
-        if (D->cond[q].pc < 0) return false;
+        if (D->cond[q].soff < 0) return false;
     }
     D->ngc = A.S.ngc;
     for (int i = 0; i < A.S.ngc; ++i) {
         const int c = A.S.key_col[i];
         D->key[i] = DirCol{G.col[c].ptr, t->cols[c].type, pref(c)};
-        if (D->key[i].pc < 0) return false;
+        if (D->key[i].soff < 0) return false;
     }
     D->nsum = A.S.nacc - 1;
     for (int a = 0; a < D->nsum; ++a) {
@@ -363,10 +364,10 @@ bool lower_group_direct(const tqp_table* t, const GroupArgs& A, long long max_gr
         if (!lower_prod(A.S.acc_expr[a], G, &pf)) return false;
         for (int k = 0; k < 2; ++k) {
             const bool col = pf.kind[k] != kFacConst;
-            const int pc = col ? pref(pf.soff[k]) : 0;
-            if (pc < 0) return false;
+            const int so = col ? pref(pf.soff[k]) : 0;
+            if (so < 0) return false;
             D->f[a][k] = DirFactor{col ? G.col[pf.soff[k]].ptr : nullptr, col ? pf.type[k] : 0, pf.kind[k], pf.a[k],
-                                   pf.b[k], pc, 0};
+                                   pf.b[k], so, 0};
         }
     }
     D->kw32 = A.S.width <= 32;

@@ -64,7 +64,7 @@ struct DirPref {
 struct DirCol {
     const unsigned char* p;
     int32_t type;
-    int32_t pc;  // index in GroupDirectArgs::pref
+    int32_t soff;  // byte offset of its block in a warp slot (GroupDirectArgs::pref)
 };
 
 // A range condition on a column: a row passes iff ((x - lo) <= span) != negate
@@ -75,7 +75,7 @@ struct DirCond {
     int32_t negate;
     int64_t lo;
     uint64_t span;
-    int32_t pc;
+    int32_t soff;
     int32_t pad;
 };
 
@@ -86,7 +86,7 @@ struct DirFactor {
     int32_t kind;
     int64_t a;
     int64_t b;
-    int32_t pc;
+    int32_t soff;
     int32_t pad;
 };
 
@@ -137,19 +137,17 @@ __device__ __forceinline__ void dir_prefetch(const GroupDirectArgs& A, unsigned 
     cp_async_commit();
 }
 
-// The lane's four values of prefetched column c from the slot.
-__device__ __forceinline__ void dir_slot4(const GroupDirectArgs& A, const unsigned char* slot, int c, int lane,
-                                          int64_t (&x)[4]) {
-    const DirPref& pc = A.pref[c];
-    const unsigned char* d = slot + pc.off;
-    if (pc.type == TQP_I64) {
+// The lane's four values of a prefetched column (block at byte `soff` of the slot).
+__device__ __forceinline__ void dir_slot4(const unsigned char* slot, int soff, int type, int lane, int64_t (&x)[4]) {
+    const unsigned char* d = slot + soff;
+    if (type == TQP_I64) {
         const longlong2 a = *reinterpret_cast<const longlong2*>(d + lane * 16);
         const longlong2 b = *reinterpret_cast<const longlong2*>(d + 512 + lane * 16);
         x[0] = a.x;
         x[1] = a.y;
         x[2] = b.x;
         x[3] = b.y;
-    } else if (pc.type == TQP_I32) {
+    } else if (type == TQP_I32) {
         const int4 v = *reinterpret_cast<const int4*>(d + lane * 16);
         x[0] = v.x;
         x[1] = v.y;
@@ -165,10 +163,10 @@ __device__ __forceinline__ void dir_slot4(const GroupDirectArgs& A, const unsign
 // x[j] = row 4 q + j of a column: from the warp slot (kSlot: the step was
 // prefetched) or from global memory, rows from `n` on reading as 0.
 template <bool kSlot>
-__device__ __forceinline__ void dir_load4(const GroupDirectArgs& A, const unsigned char* slot, int pc,
+__device__ __forceinline__ void dir_load4(const GroupDirectArgs& A, const unsigned char* slot, int soff,
                                           const unsigned char* p, int type, long long q, int lane, int64_t (&x)[4]) {
     if constexpr (kSlot) {
-        dir_slot4(A, slot, pc, lane, x);
+        dir_slot4(slot, soff, type, lane, x);
     } else {
         const long long n = A.n;
 #pragma unroll
@@ -185,7 +183,7 @@ __device__ __forceinline__ void dir_factor(const GroupDirectArgs& A, const unsig
         for (int j = 0; j < 4; ++j) x[j] = f.b;
         return;
     }
-    dir_load4<kSlot>(A, slot, f.pc, f.p, f.type, q, lane, x);
+    dir_load4<kSlot>(A, slot, f.soff, f.p, f.type, q, lane, x);
     if (kind == kFacPlain) return;
     const uint64_t b = static_cast<uint64_t>(f.b);
     if (kind == kFacAdd) {
@@ -393,7 +391,7 @@ __device__ __forceinline__ void dir_step(const GroupDirectArgs& A, const DirDens
         if (c < A.ncond) {
             const DirCond& cd = A.cond[c];
             int64_t x[4];
-            dir_load4<kSlot>(A, slot, cd.pc, cd.p, cd.type, qq, lane, x);
+            dir_load4<kSlot>(A, slot, cd.soff, cd.p, cd.type, qq, lane, x);
             uint32_t m = 0;
             if (cd.type == TQP_I64) {
 #pragma unroll
@@ -420,7 +418,7 @@ __device__ __forceinline__ void dir_step(const GroupDirectArgs& A, const DirDens
     for (int i = 0; i < kDirKeys; ++i) {
         if (i < A.ngc) {
             int64_t x[4];
-            dir_load4<kSlot>(A, slot, A.key[i].pc, A.key[i].p, A.key[i].type, qq, lane, x);
+            dir_load4<kSlot>(A, slot, A.key[i].soff, A.key[i].p, A.key[i].type, qq, lane, x);
             const int b = S.key_bits[i];
             if constexpr (kDense) {  // mixed-radix slot index (every key lies in its column's range)
                 const long long lo = Dn.kmin[i];

@@ -49,6 +49,9 @@ def mixed_specs():
     g = rng.integers(0, 20_000, 150_001).astype(np.int32)
     v = rng.integers(-100, 100, 150_001).astype(np.int64)
     empty_q1 = [c[:0] for c in q1(10, 7)]
+    kk = (rng.integers(0, 20, 123_457) * 3 - 7).astype(np.int32)
+    fl = rng.integers(0, 3, 123_457).astype(np.uint8)
+    v2 = rng.integers(-10**9, 10**9, 123_457).astype(np.int64)
     return [
         # filter: count only; count + sum + row ids
         dict(fact=q1(100_003, 1), preds=[(0, "le", 2450)]),
@@ -57,6 +60,9 @@ def mixed_specs():
         dict(fact=q1(100_000, 4), preds=[(0, "le", 2450)], group_cols=[1, 2], aggs=Q1_AGGS, capacity_groups=64),
         dict(fact=[g, v], group_cols=[0], aggs=[("sum", [("col", 1)]), ("count", None)], topk=10, topk_agg=0,
              max_groups=32768),
+        # few groups with keys too sparse for dense slot ids (warp key lists, flushed when full)
+        dict(fact=[kk, fl, v2], preds=[(1, "ne", 1)], group_cols=[0],
+             aggs=[("sum", [("col", 2)]), ("count", None), ("avg", [("col", 2)])], capacity_groups=32),
         # a large group table without top-k: the single-plan path, inside the batch
         dict(fact=[g, v], group_cols=[0], aggs=[("count", None)], capacity_groups=20_000),
         # joins: grouped top-k; filtered, averaged, with sum and row ids; ungrouped sum

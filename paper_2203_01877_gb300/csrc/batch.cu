@@ -291,7 +291,8 @@ __global__ void __launch_bounds__(kFoldThreads) k_b_fold(const FoldJob* J, const
 
 __global__ void __launch_bounds__(kDirThreads) k_b_grange(const DirJob* J, const int32_t* bjob) {
     const DirJob& j = J[bjob[blockIdx.x]];
-    group_direct_range_block(j.A, j.kmeta, static_cast<long long>(blockIdx.x) - j.range_first, j.range_nblocks);
+    group_direct_range_block(j.A, j.kmeta, nullptr, static_cast<long long>(blockIdx.x) - j.range_first,
+                             j.range_nblocks);
 }
 
 // The job's arguments are copied into shared memory after the kernel's own

@@ -126,7 +126,8 @@ tqp_status lower_group(const int32_t* key_cols, const int32_t* key_types, int32_
                        int32_t naggs, int ncols, GroupSpec* S);
 long long group_table_cap(long long max_groups);
 size_t group_table_bytes(long long cap, int nacc);
-tqp_status group_table_init(GroupSpec* S, void* mem, long long cap, long long max_groups, cudaStream_t stream);
+tqp_status group_table_init(GroupSpec* S, void* mem, long long cap, long long max_groups, cudaStream_t stream,
+                            bool clear = true);
 tqp_status group_finalize(tqp_ctx* ctx, const GroupSpec& S, const GroupOut& O, cudaStream_t stream);
 // Top-k groups by accumulator of aggregate `agg` (descending; ties: key
 // ascending); writes min(k, G) rows in rank order and *total_groups = G.

@@ -46,9 +46,9 @@ __global__ void __launch_bounds__(kDirThreads, kDirMinBlocks) k_groupby_direct(c
     group_direct_block(A, dsm, blockIdx.x, gridDim.x);
 }
 
-__global__ void __launch_bounds__(kDirThreads) k_groupby_keyrange(const __grid_constant__ GroupDirectArgs A,
-                                                                  unsigned long long* kmeta) {
-    group_direct_range_block(A, kmeta, blockIdx.x, gridDim.x);
+__global__ void __launch_bounds__(kDirThreads) k_groupby_dprep(const __grid_constant__ GroupDirectArgs A,
+                                                               unsigned long long* kpart) {
+    group_direct_prep_block(A, kpart, blockIdx.x, gridDim.x);
 }
 
 // ---- finalize ----------------------------------------------------------------
@@ -168,7 +168,8 @@ size_t group_table_bytes(long long cap, int nacc) {
 }
 
 // Carve the table out of `mem` and clear it on `stream`.
-tqp_status group_table_init(GroupSpec* S, void* mem, long long cap, long long max_groups, cudaStream_t stream) {
+tqp_status group_table_init(GroupSpec* S, void* mem, long long cap, long long max_groups, cudaStream_t stream,
+                            bool clear) {
     unsigned char* p = static_cast<unsigned char*>(mem);
     S->cap = cap;
     S->max_groups = max_groups;
@@ -176,6 +177,7 @@ tqp_status group_table_init(GroupSpec* S, void* mem, long long cap, long long ma
     p += (static_cast<size_t>(cap + 1) * 8 + 255) / 256 * 256;
     S->acc = reinterpret_cast<unsigned long long*>(p);
     S->ndistinct = S->acc + (cap + 1) * S->nacc;
+    if (!clear) return TQP_OK;  // the caller's first kernel clears it
     TQP_CUDA(cudaMemsetAsync(S->keys, 0xFF, static_cast<size_t>(cap + 1) * 8, stream));
     TQP_CUDA(cudaMemsetAsync(S->acc, 0, static_cast<size_t>(cap + 1) * S->nacc * 8 + 8, stream));
     return TQP_OK;
@@ -417,12 +419,18 @@ tqp_status launch_groupby(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* pred
     void* tab = arena_alloc(ctx, group_table_bytes(cap, A.S.nacc));
     unsigned long long* ticket = static_cast<unsigned long long*>(arena_alloc(ctx, 256));
     if (!tab || !ticket) return arena_oom(ctx, group_table_bytes(cap, A.S.nacc));
-    TQP_TRY(group_table_init(&A.S, tab, cap, max_groups, stream));
-
+    GroupOut O{d_keys, d_ivals, d_fvals, capacity_groups, d_num_groups, ctx->d_err};
     GroupDirectArgs D;
-    if (lower_group_direct(t, A, max_groups, &D)) {
+    const bool direct = lower_group_direct(t, A, max_groups, &D);
+    TQP_TRY(group_table_init(&A.S, tab, cap, max_groups, stream, !direct));
+
+    if (direct) {
+        // two launches: the range pass (which also clears the table), then the
+        // aggregation, whose last CTA finalizes the table unless top-k follows
         D.S = A.S;
         D.err = ctx->d_err;
+        D.O = O;
+        D.fin = topk > 0 ? 0 : 1;
         static bool attr_done[kMaxDevices] = {};
         TQP_TRY(allow_smem(ctx, reinterpret_cast<const void*>(k_groupby_direct), attr_done));
         int occ = 0;
@@ -433,18 +441,25 @@ tqp_status launch_groupby(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* pred
         const long long nq = (t->num_rows + 3) / 4;
         const long long blocks = std::min<long long>((nq + kDirThreads - 1) / kDirThreads,
                                                      static_cast<long long>(occ) * ctx->num_sms);
-        if (D.ngc > 0) {  // key ranges first: few distinct values get dense slot ids
-            unsigned long long* kmeta = static_cast<unsigned long long*>(arena_alloc(ctx, 2 * kDirKeys * 8));
-            if (!kmeta) return arena_oom(ctx, 2 * kDirKeys * 8);
-            TQP_CUDA(cudaMemsetAsync(kmeta, 0, 2 * kDirKeys * 8, stream));
-            k_groupby_keyrange<<<static_cast<unsigned>(std::max<long long>(
-                                     std::min<long long>(blocks, 4LL * ctx->num_sms), 1)),
-                                 kDirThreads, 0, stream>>>(D, kmeta);
-            TQP_CUDA(cudaGetLastError());
-            D.kmeta = kmeta;
+        // key ranges first (few distinct values get dense slot ids): one
+        // record per range block, reduced by every CTA of the aggregation
+        const int nparts = static_cast<int>(
+            std::max<long long>(1, std::min<long long>((t->num_rows + 8191) / 8192, ctx->num_sms)));
+        unsigned long long* kpart =
+            static_cast<unsigned long long*>(arena_alloc(ctx, static_cast<size_t>(nparts) * 2 * kDirKeys * 8));
+        unsigned int* done = static_cast<unsigned int*>(arena_alloc(ctx, 16));
+        if (!kpart || !done) return arena_oom(ctx, static_cast<size_t>(nparts) * 2 * kDirKeys * 8 + 16);
+        D.done = done;
+        if (D.ngc > 0) {
+            D.kpart = kpart;
+            D.nparts = nparts;
         }
+        k_groupby_dprep<<<D.ngc > 0 ? nparts : 1, kDirThreads, 0, stream>>>(D, kpart);
+        TQP_CUDA(cudaGetLastError());
         k_groupby_direct<<<static_cast<unsigned>(std::max<long long>(blocks, 1)), kDirThreads, kDirSmemBytes, stream>>>(D);
         TQP_CUDA(cudaGetLastError());
+        if (topk > 0) return group_topk(ctx, A.S, O, topk, topk_agg, d_total_groups, stream);
+        return TQP_OK;
     } else if (t->num_rows > 0) {
         static bool attr_done[kMaxDevices] = {};
         TQP_TRY(allow_smem(ctx, reinterpret_cast<const void*>(k_groupby), attr_done));
@@ -458,7 +473,6 @@ tqp_status launch_groupby(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* pred
         k_groupby<<<static_cast<int>(A.ctl.nchunks), kEngineThreads, smem, stream>>>(A);
         TQP_CUDA(cudaGetLastError());
     }
-    GroupOut O{d_keys, d_ivals, d_fvals, capacity_groups, d_num_groups, ctx->d_err};
     if (topk > 0) return group_topk(ctx, A.S, O, topk, topk_agg, d_total_groups, stream);
     return group_finalize(ctx, A.S, O, stream);
 }

@@ -23,7 +23,7 @@
 // and the flush rebuilds each used slot's packed key from its index.
 #pragma once
 
-#include "group.cuh"
+#include "finalize.cuh"
 
 namespace tqp {
 
@@ -51,6 +51,8 @@ struct DirDense {
     int32_t dense;  // 1: ids are mixed-radix indices
 };
 static_assert(sizeof(DirDense) <= 128, "dense parameters");
+// the last CTA finalizes the table in the (then unused) lane tables and slots
+static_assert(kDirSmemBytes >= 2 * kSmallCap * (8 + 4), "finalize scratch");
 
 // A column fetched ahead: its block in a warp slot starts at `off` and holds
 // the four values of every lane (esize 8: [half][lane][16 B]; 4: [lane][16 B];
@@ -101,9 +103,16 @@ struct GroupDirectArgs {
     DirPref pref[kDirPrefCols];
     GroupSpec S;
     int* err;
-    // key ranges from the first pass: [2 i] = max of ~enc(x), [2 i + 1] = max
-    // of enc(x), enc(x) = x ^ 2^63 (so the first is ~enc(min)); nullptr: none
+    // key ranges from the first pass, as [2 i] = max of ~enc(x) and [2 i + 1]
+    // = max of enc(x), enc(x) = x ^ 2^63 (so the first is ~enc(min)): either
+    // reduced into kmeta, or one record of 2 kDirKeys words per range block
+    // in kpart (nparts records); both nullptr: no key columns
     const unsigned long long* kmeta;
+    const unsigned long long* kpart;
+    int32_t nparts;
+    int32_t fin;              // 1: the last CTA finalizes the table into O
+    unsigned int* done;       // CTAs finished (zeroed by the range pass when fin)
+    GroupOut O;
 };
 
 // ---- asynchronous copies into the warp slot ----
@@ -226,44 +235,45 @@ __device__ __forceinline__ void dir_flush(const GroupDirectArgs& A, unsigned lon
     __syncwarp();
 }
 
-// Dense ids: every used slot's lane partials into the global table (its
-// packed key rebuilt from the slot index); the tables are zero afterwards.
-__device__ __forceinline__ void dir_flush_dense(const GroupDirectArgs& A, const DirDense& Dn, unsigned long long* area,
-                                                int lane) {
-    __syncwarp();
+// Dense ids, after every warp of the CTA has finished: the CTA's partials of
+// each used slot into the global table (its packed key rebuilt from the slot
+// index).  Warp w takes the (slot, accumulator) pairs w, w + 8, ...: each
+// lane sums its column over the eight warps' tables, the warp sums the
+// lanes, and one reduction per pair and CTA goes to L2.
+__device__ __forceinline__ void dir_flush_dense_cta(const GroupDirectArgs& A, const DirDense& Dn,
+                                                    unsigned long long* tables, int lane, int w) {
     const GroupSpec& S = A.S;
-    for (int d = 0; d < Dn.P; ++d) {
-        unsigned long long* p0 = area + (d * kDirAcc) * 32 + lane;
-        unsigned long long c = *p0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-        if (c == 0) continue;  // no row of this warp in the slot (warp-uniform)
+    __shared__ long long gslot[kDirSlots];
+    if (w == 0) {  // the global entry of every slot some row reached
         long long g = -1;
-        if (lane == 0) {
-            uint64_t key = 0;
-            for (int i = 0; i < A.ngc; ++i) {
-                const long long x = Dn.kmin[i] + (d / Dn.stride[i]) % Dn.range[i];
-                const int b = S.key_bits[i];
-                const uint64_t e = enc_key(x, b);
-                key = b == 64 ? e : ((key << b) | e);
-            }
-            g = gtab_slot(S, key, A.err);
-        }
-        g = __shfl_sync(0xffffffffu, g, 0);
-#pragma unroll
-        for (int a = 0; a < kDirAcc; ++a) {
-            if (a < S.nacc) {
-                unsigned long long* p = area + (d * kDirAcc + a) * 32 + lane;
-                unsigned long long x = a == 0 ? c : *p;
-                if (a > 0)
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-                *p = 0;
-                if (lane == 0 && x && g >= 0) red_add_u64(&S.acc[g * S.nacc + a], x);
+        if (lane < Dn.P) {
+            unsigned long long c = 0;
+            for (int v = 0; v < kDirThreads / 32; ++v)
+                for (int l = 0; l < 32; ++l) c += tables[v * kDirWarpWords + (lane * kDirAcc) * 32 + l];
+            if (c) {
+                uint64_t key = 0;
+                for (int i = 0; i < A.ngc; ++i) {
+                    const long long x = Dn.kmin[i] + (lane / Dn.stride[i]) % Dn.range[i];
+                    const int b = S.key_bits[i];
+                    const uint64_t e = enc_key(x, b);
+                    key = b == 64 ? e : ((key << b) | e);
+                }
+                g = gtab_slot(S, key, A.err);
             }
         }
+        if (lane < kDirSlots) gslot[lane] = g;
     }
-    __syncwarp();
+    __syncthreads();
+    const int npairs = Dn.P * S.nacc;
+    for (int pr = w; pr < npairs; pr += kDirThreads / 32) {
+        const int d = pr / S.nacc, a = pr % S.nacc;
+        if (gslot[d] < 0) continue;  // (warp-uniform) no row reached slot d
+        unsigned long long x = 0;
+        for (int v = 0; v < kDirThreads / 32; ++v) x += tables[v * kDirWarpWords + (d * kDirAcc + a) * 32 + lane];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0 && x) red_add_u64(&S.acc[gslot[d] * S.nacc + a], x);
+    }
 }
 
 // Rows of a lane (pass bits `ok`, slots id[j]) into its lane tables: rows
@@ -482,15 +492,17 @@ __device__ __forceinline__ void dir_step(const GroupDirectArgs& A, const DirDens
     }
 }
 
-// Dense-id parameters from the key ranges (one thread per CTA).
-__device__ __forceinline__ void dir_dense_init(const GroupDirectArgs& A, DirDense* Dn) {
+// Dense-id parameters from the encoded key bounds (one thread per CTA):
+// ea[i] = ~enc(min_i), eb[i] = enc(max_i).
+__device__ __forceinline__ void dir_dense_init(const GroupDirectArgs& A, const unsigned long long* ea,
+                                               const unsigned long long* eb, bool have, DirDense* Dn) {
     Dn->dense = 0;
     Dn->P = 1;
-    if (A.ngc > 0 && !A.kmeta) return;
+    if (A.ngc > 0 && !have) return;
     long long P = 1;
     for (int i = A.ngc - 1; i >= 0; --i) {
         // encoded bounds compare as unsigned; rows exist, so elo <= ehi
-        const unsigned long long elo = ~A.kmeta[2 * i], ehi = A.kmeta[2 * i + 1];
+        const unsigned long long elo = ~ea[i], ehi = eb[i];
         if (ehi < elo || ehi - elo >= static_cast<unsigned long long>(kDirSlots)) return;
         const unsigned long long r = ehi - elo + 1;
         Dn->kmin[i] = static_cast<long long>(elo ^ (1ULL << 63));
@@ -501,6 +513,36 @@ __device__ __forceinline__ void dir_dense_init(const GroupDirectArgs& A, DirDens
     }
     Dn->P = static_cast<int32_t>(P);
     Dn->dense = 1;
+}
+
+// Warp 0 of a CTA: the key bounds (reduced from the range blocks' records if
+// needed), then the dense-id parameters.
+__device__ __forceinline__ void dir_dense_setup(const GroupDirectArgs& A, DirDense* Dn, int lane) {
+    unsigned long long ea[kDirKeys], eb[kDirKeys];
+    const bool have = A.kmeta || A.kpart;
+#pragma unroll
+    for (int i = 0; i < kDirKeys; ++i) {
+        ea[i] = eb[i] = 0;
+        if (i < A.ngc) {
+            if (A.kpart) {
+                for (int p = lane; p < A.nparts; p += 32) {
+                    const unsigned long long a = A.kpart[p * 2 * kDirKeys + 2 * i], b = A.kpart[p * 2 * kDirKeys + 2 * i + 1];
+                    ea[i] = a > ea[i] ? a : ea[i];
+                    eb[i] = b > eb[i] ? b : eb[i];
+                }
+            } else if (A.kmeta && lane == 0) {
+                ea[i] = A.kmeta[2 * i];
+                eb[i] = A.kmeta[2 * i + 1];
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long a = __shfl_xor_sync(0xffffffffu, ea[i], o), b = __shfl_xor_sync(0xffffffffu, eb[i], o);
+                ea[i] = a > ea[i] ? a : ea[i];
+                eb[i] = b > eb[i] ? b : eb[i];
+            }
+        }
+    }
+    if (lane == 0) dir_dense_init(A, ea, eb, have, Dn);
 }
 
 // The warp's grid-stride loop: 32 quads per step; a step whose quads all lie
@@ -531,8 +573,7 @@ __device__ __forceinline__ void dir_loop(const GroupDirectArgs& A, const DirDens
             dir_step<false, kDense>(A, Dn, area, slot, dk, nused, base + lane, lane);
         }
     }
-    if constexpr (kDense) dir_flush_dense(A, Dn, area, lane);
-    else dir_flush(A, area, dk, nused, lane);
+    if constexpr (!kDense) dir_flush(A, area, dk, nused, lane);  // dense: the CTA flushes once
 }
 
 // One CTA of the direct group-by: block vb of vg blocks working on this table.
@@ -542,11 +583,29 @@ __device__ __forceinline__ void group_direct_block(const GroupDirectArgs& A, uns
     unsigned long long* area = reinterpret_cast<unsigned long long*>(smem) + w * kDirWarpWords;
     unsigned char* slot = smem + kDirTableBytes + w * kDirSlotBytes;
     DirDense* Dn = reinterpret_cast<DirDense*>(smem + kDirDenseOff);
-    if (threadIdx.x == 0) dir_dense_init(A, Dn);
+    if (w == 0) dir_dense_setup(A, Dn, lane);
     for (int i = lane; i < kDirWarpWords; i += 32) area[i] = 0;
     __syncthreads();
-    if (Dn->dense) dir_loop<true>(A, *Dn, area, slot, lane, w, vb, vg);
-    else dir_loop<false>(A, *Dn, area, slot, lane, w, vb, vg);
+    if (Dn->dense) {
+        dir_loop<true>(A, *Dn, area, slot, lane, w, vb, vg);
+        __syncthreads();
+        dir_flush_dense_cta(A, *Dn, reinterpret_cast<unsigned long long*>(smem), lane, w);
+    } else {
+        dir_loop<false>(A, *Dn, area, slot, lane, w, vb, vg);
+    }
+    if (!A.fin) return;
+    // the last CTA to finish finalizes the table (every CTA's adds are
+    // ordered before its count by the fence)
+    __shared__ int last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(A.done, 1u) == static_cast<unsigned int>(vg - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    finalize_small_block(A.S, A.O, smem);
 }
 
 // First pass: [min, max] of every key column (encoded as the kmeta words;
@@ -561,7 +620,7 @@ __device__ __forceinline__ void dir_enc_update(long long x, unsigned long long& 
 }
 
 __device__ __forceinline__ void group_direct_range_block(const GroupDirectArgs& A, unsigned long long* kmeta,
-                                                         long long vb, long long vg) {
+                                                         unsigned long long* kpart, long long vb, long long vg) {
     __shared__ unsigned long long red[kDirThreads / 32][2];
     const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
     const long long n = A.n;
@@ -648,10 +707,27 @@ __device__ __forceinline__ void group_direct_range_block(const GroupDirectArgs& 
         if (threadIdx.x < 2) {
             unsigned long long v = 0;
             for (int k = 0; k < static_cast<int>(blockDim.x) / 32; ++k) v = red[k][threadIdx.x] > v ? red[k][threadIdx.x] : v;
-            atomicMax(&kmeta[2 * i + threadIdx.x], v);
+            if (kpart) kpart[vb * 2 * kDirKeys + 2 * i + threadIdx.x] = v;
+            else atomicMax(&kmeta[2 * i + threadIdx.x], v);
         }
         __syncthreads();
     }
+}
+
+// The single-call form of the first pass: block 0 also clears the group
+// table and the CTA counter of the direct kernel that follows.
+__device__ __forceinline__ void group_direct_prep_block(const GroupDirectArgs& A, unsigned long long* kpart,
+                                                        long long vb, long long vg) {
+    if (vb == 0) {
+        const GroupSpec& S = A.S;
+        for (long long i = threadIdx.x; i <= S.cap; i += blockDim.x) S.keys[i] = kEmptyKey;
+        for (long long i = threadIdx.x; i < (S.cap + 1) * S.nacc; i += blockDim.x) S.acc[i] = 0;
+        if (threadIdx.x == 0) {
+            *S.ndistinct = 0;
+            if (A.done) *A.done = 0;
+        }
+    }
+    if (A.ngc > 0) group_direct_range_block(A, nullptr, kpart, vb, vg);
 }
 
 }  // namespace tqp

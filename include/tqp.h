@@ -27,6 +27,13 @@
  *     by tqp_ctx_check().
  *   - Column data must be 16-byte aligned (as from cudaMalloc / torch); this
  *     lets the scans stage tiles with bulk asynchronous copies.
+ *   - One exception to device-resident columns: tqp_filter accepts a column
+ *     in pinned (page-locked) host memory when the filter reads it only at
+ *     passing rows -- a column that appears in sum_expr but in no predicate
+ *     while at least one predicate remains after lowering.  The GPU then
+ *     reads those rows in place over the host link (late materialisation of
+ *     a projected column); any other use of host memory is rejected with
+ *     TQP_ERR_INVALID_ARG.
  *   - A context serialises its scratch use: two calls on one context must not
  *     overlap on the device (same stream, or ordered streams).  Use one
  *     context per concurrent stream.
@@ -64,7 +71,8 @@ typedef enum {
 
 typedef enum { TQP_I32 = 0, TQP_I64 = 1, TQP_U8 = 2 } tqp_dtype;
 
-/* One column: device pointer to num_rows elements of `type`; `scale` is the
+/* One column: device pointer (or, for tqp_filter, see the conventions above)
+ * to num_rows elements of `type`; `scale` is the
  * decimal exponent of a fixed-point column (informational; arithmetic is on
  * the stored integers). */
 typedef struct {

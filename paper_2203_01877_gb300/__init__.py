@@ -164,16 +164,21 @@ def _dtype_code(t) -> int:
 
 
 class TableRef:
-    """A tqp_table over CUDA tensors (keeps the tensors and C structs alive)."""
+    """A tqp_table over CUDA tensors (keeps the tensors and C structs alive).
+    With host_ok, a column may also be a pinned CPU tensor: tqp_filter reads
+    such a column in place at passing rows (a projected column); every other
+    use is rejected by the library."""
 
-    def __init__(self, cols, scales=None):
+    def __init__(self, cols, scales=None, host_ok=False):
         cols = list(cols)
         if not cols:
             raise ValueError("a table needs at least one column")
         n = cols[0].numel()
         for c in cols:
-            if not c.is_cuda or not c.is_contiguous() or c.numel() != n:
-                raise ValueError("columns must be contiguous CUDA tensors of equal length")
+            on_host = host_ok and not c.is_cuda and c.is_pinned()
+            if not (c.is_cuda or on_host) or not c.is_contiguous() or c.numel() != n:
+                raise ValueError("columns must be contiguous CUDA tensors (or pinned host tensors with host_ok) "
+                                 "of equal length")
         self.tensors = cols
         self.carr = (Column * len(cols))()
         for i, c in enumerate(cols):

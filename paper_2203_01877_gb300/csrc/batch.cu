@@ -774,6 +774,16 @@ static bool expr_in(const tqp_expr& e, int lo, int hi) {
 
 // Plans the batch lowers itself; the rest (including every malformed plan,
 // which then reports its error) take the single-plan path.
+// (every column of its tables in device memory: host columns, allowed in one
+// place only, go through the single-plan path and its checks)
+static bool all_device(const tqp_table* t) {
+    std::vector<int> cols;
+    for (int c = 0; c < t->num_cols; ++c) cols.push_back(c);
+    const bool ok = check_device_cols(t, cols, "batch") == TQP_OK;
+    clear_error();
+    return ok;
+}
+
 static bool batchable(const tqp_ctx* ctx, const tqp_plan* p, const tqp_result* r) {
     if (!p->fact || p->npreds < 0 || p->npreds > TQP_MAX_PREDS) return false;
     if (p->ngc < 0 || p->ngc > TQP_MAX_GROUP_COLS || p->naggs < 0 || p->naggs > TQP_MAX_AGGS) return false;
@@ -823,7 +833,8 @@ static tqp_status lower_batch(tqp_batch* b, const tqp_plan* plans, const tqp_res
         const tqp_plan* p = &plans[i];
         const tqp_result* r = &res[i];
         if (!batchable(b->ctx, p, r) || check_table(p->fact, "plan.fact") != TQP_OK ||
-            (p->dim && check_table(p->dim, "plan.dim") != TQP_OK)) {
+            (p->dim && check_table(p->dim, "plan.dim") != TQP_OK) || !all_device(p->fact) ||
+            (p->dim && !all_device(p->dim))) {
             clear_error();
             b->fb_plans.push_back(*p);
             b->fb_res.push_back(*r);

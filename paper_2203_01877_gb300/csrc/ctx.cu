@@ -107,6 +107,23 @@ tqp_status check_table(const tqp_table* t, const char* what) {
     return TQP_OK;
 }
 
+// Columns `cols` of t must be device (or managed) memory: they are staged
+// with bulk asynchronous copies.
+tqp_status check_device_cols(const tqp_table* t, const std::vector<int>& cols, const char* what) {
+    for (int c : cols) {
+        if (c < 0 || c >= t->num_cols || !t->cols[c].data) continue;
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, t->cols[c].data) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(TQP_ERR_INVALID_ARG, "%s: column %d is not CUDA-visible memory", what, c);
+        }
+        if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+            return fail(TQP_ERR_INVALID_ARG,
+                        "%s: column %d is host memory; only columns read at passing rows may be", what, c);
+    }
+    return TQP_OK;
+}
+
 tqp_status lower_preds(const tqp_table* t, const tqp_pred* preds, int32_t npreds, Cond* out, int* ncond) {
     if (npreds < 0 || npreds > TQP_MAX_PREDS)
         return fail(TQP_ERR_INVALID_ARG, "npreds %d outside [0, %d]", npreds, TQP_MAX_PREDS);

@@ -81,6 +81,7 @@ static tqp_status plan_filter(const tqp_ctx* ctx, const tqp_table* t, const tqp_
     std::vector<int> u = staged;
     std::sort(u.begin(), u.end());
     u.erase(std::unique(u.begin(), u.end()), u.end());
+    TQP_TRY(check_device_cols(t, u, "tqp_filter"));  // the rest are read at passing rows only
     int bpr = 0;
     for (int c : u) bpr += t->cols[c].type == TQP_I64 ? 8 : (t->cols[c].type == TQP_I32 ? 4 : 1);
     const tqp_tuning tu = force ? *force : default_tuning(ctx, bpr, FilterBody::kSmemBytes + args_bytes<FilterArgs>());

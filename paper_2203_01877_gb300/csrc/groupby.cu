@@ -403,6 +403,7 @@ tqp_status launch_groupby(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* pred
     for (int i = 0; i < ncond; ++i) staged.push_back(A.cond[i].col);
     for (int i = 0; i < ngc; ++i) staged.push_back(group_cols[i]);
     for (int a = 1; a < A.S.nacc; ++a) expr_cols(A.S.acc_expr[a - 1], staged);
+    TQP_TRY(check_device_cols(t, staged, "tqp_groupby_agg"));
     std::vector<int> u = staged;
     std::sort(u.begin(), u.end());
     u.erase(std::unique(u.begin(), u.end()), u.end());

@@ -108,6 +108,7 @@ struct DeviceGuard {
 
 tqp_status check_ctx(const tqp_ctx* ctx);
 tqp_status check_table(const tqp_table* t, const char* what);
+tqp_status check_device_cols(const tqp_table* t, const std::vector<int>& cols, const char* what);
 
 // Lower predicates to range conditions on `t`'s columns.
 tqp_status lower_preds(const tqp_table* t, const tqp_pred* preds, int32_t npreds, Cond* out, int* ncond);

@@ -349,6 +349,8 @@ extern "C" tqp_status tqp_hash_join(tqp_ctx* ctx, const tqp_table* build, int32_
     TQP_TRY(check_ctx(ctx));
     TQP_TRY(check_table(build, "tqp_hash_join(build)"));
     TQP_TRY(check_table(probe, "tqp_hash_join(probe)"));
+    TQP_TRY(check_device_cols(build, {build_key}, "tqp_hash_join(build)"));
+    TQP_TRY(check_device_cols(probe, {probe_key}, "tqp_hash_join(probe)"));
     if (build_key < 0 || build_key >= build->num_cols) return fail(TQP_ERR_INVALID_ARG, "build_key out of range");
     if (probe_key < 0 || probe_key >= probe->num_cols) return fail(TQP_ERR_INVALID_ARG, "probe_key out of range");
     if (!d_count) return fail(TQP_ERR_INVALID_ARG, "d_count is NULL");

@@ -194,6 +194,11 @@ static tqp_status run_join_plan(tqp_ctx* ctx, const tqp_plan* p, const tqp_resul
         return fail(TQP_ERR_UNSUPPORTED, "with a join, the sum expression must use fact columns only");
     const tqp_dim* pd = p->prepared;
     if (pd) TQP_TRY(check_prepared(ctx, p));
+    {
+        std::vector<int> dcols{p->dim_key};
+        for (int i = 0; i < p->ngc; ++i) dcols.push_back(p->group_cols[i] - nf);
+        TQP_TRY(check_device_cols(D, dcols, "tqp_run_plan(dim)"));
+    }
 
     // passing fact row ids (before the join) come from the filter kernel
     if (p->emit_row_ids && r->d_row_ids) {
@@ -284,6 +289,7 @@ static tqp_status run_join_plan(tqp_ctx* ctx, const tqp_plan* p, const tqp_resul
     for (int a = 1; a < A.S.nacc; ++a) expr_cols(A.S.acc_expr[a - 1], staged);
     std::sort(staged.begin(), staged.end());
     staged.erase(std::unique(staged.begin(), staged.end()), staged.end());
+    TQP_TRY(check_device_cols(F, staged, "tqp_run_plan(fact)"));
     if (static_cast<int>(staged.size()) > kMaxStaged) staged.resize(kMaxStaged);
     int bpr = 0;
     for (int c : staged) bpr += F->cols[c].type == TQP_I64 ? 8 : (F->cols[c].type == TQP_I32 ? 4 : 1);
@@ -398,6 +404,11 @@ static void* top_bytes(tqp_ctx* ctx, size_t bytes) { return arena_alloc_top(ctx,
 
 static tqp_status dim_prepare(tqp_ctx* ctx, const tqp_table* D, int32_t key_col, const int32_t* group_cols,
                               int32_t ngc, int64_t max_groups, tqp_dim* d, cudaStream_t st) {
+    {
+        std::vector<int> cols{key_col};
+        for (int i = 0; i < ngc; ++i) cols.push_back(group_cols[i]);
+        TQP_TRY(check_device_cols(D, cols, "tqp_dim_prepare"));
+    }
     const long long n = D->num_rows;
     d->nrows = n;
     d->key_col = key_col;

@@ -144,3 +144,49 @@ def test_full_size_filter_project_reduce(ctx):
     finally:
         big.close()
     assert 1_000_000 < k < 1_150_000
+
+
+def test_filter_host_projected_column(ctx):
+    """A projected column in pinned host memory (read in place at passing rows
+    only) gives the same row ids, count and sum as the device-resident table."""
+    import torch
+    import paper_2203_01877_gb300 as tqp
+    t = datagen.fact_table(2_000_003, seed=31, cols=["date", "discount", "quantity", "price"])
+    dev = [torch.from_numpy(t[c]).cuda() for c in ("date", "discount", "quantity", "price")]
+    preds = [(0, "ge", 731), (0, "lt", 1096), (1, "between", 5, 7), (2, "lt", 24)]
+    expr = [("col", 3), ("col", 1), "mul"]
+    outs = []
+    for host_price in (False, True):
+        cols = list(dev)
+        if host_price:
+            cols[3] = torch.from_numpy(t["price"]).pin_memory()
+        T = tqp.TableRef(cols, host_ok=True)
+        ids = torch.full((len(t["date"]),), -1, dtype=torch.int32, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        s = torch.zeros(1, dtype=torch.int64, device="cuda")
+        tqp.tqp_filter(ctx, T, preds, expr, s, ids, len(t["date"]), cnt)
+        assert ctx.status() == 0
+        k = int(cnt.item())
+        outs.append((k, int(s.item()), ids[:k].cpu()))
+    assert outs[0][0] == outs[1][0] and outs[0][1] == outs[1][1] and torch.equal(outs[0][2], outs[1][2])
+
+
+def test_filter_host_staged_column_rejected(ctx):
+    """Host memory where the scan stages the column (a predicate column, or any
+    column of another operator) is refused on the host, before any launch."""
+    import torch
+    import paper_2203_01877_gb300 as tqp
+    t = datagen.fact_table(10_000, seed=32, cols=["date", "price"])
+    hd = torch.from_numpy(t["date"]).pin_memory()
+    dp = torch.from_numpy(t["price"]).cuda()
+    T = tqp.TableRef([hd, dp], host_ok=True)
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    with pytest.raises(tqp.TqpError) as e:
+        tqp.tqp_filter(ctx, T, [(0, "lt", 100)], None, None, None, 0, cnt)
+    assert e.value.status == tqp.ERR_INVALID_ARG
+    keys = torch.zeros(64, dtype=torch.int64, device="cuda")
+    iv = torch.zeros(64, dtype=torch.int64, device="cuda")
+    ng = torch.zeros(1, dtype=torch.int64, device="cuda")
+    with pytest.raises(tqp.TqpError) as e:
+        tqp.tqp_groupby_agg(ctx, T, [], [0], [("count", None)], keys, iv, None, 64, ng)
+    assert e.value.status == tqp.ERR_INVALID_ARG

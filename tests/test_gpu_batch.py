@@ -63,6 +63,9 @@ def mixed_specs():
         # few groups with keys too sparse for dense slot ids (warp key lists, flushed when full)
         dict(fact=[kk, fl, v2], preds=[(1, "ne", 1)], group_cols=[0],
              aggs=[("sum", [("col", 2)]), ("count", None), ("avg", [("col", 2)])], capacity_groups=32),
+        # few groups with top-k (the direct kernel, then the selection)
+        dict(fact=q1(80_000, 9), preds=[(0, "le", 2450)], group_cols=[1, 2], aggs=Q1_AGGS, topk=3, topk_agg=2,
+             max_groups=16, capacity_groups=3),
         # a large group table without top-k: the single-plan path, inside the batch
         dict(fact=[g, v], group_cols=[0], aggs=[("count", None)], capacity_groups=20_000),
         # joins: grouped top-k; filtered, averaged, with sum and row ids; ungrouped sum

@@ -94,6 +94,14 @@ def test_topk_rank_distributions(ctx, dist):
              topk_agg=agg, max_groups=200_000)
 
 
+@pytest.mark.parametrize("k", [1, 4, 6, 10])
+def test_few_groups_topk(ctx, k):
+    """Top-k over a few-groups aggregate: the direct kernel fills the table and
+    leaves it to the selection (k above the number of groups included)."""
+    run_both(ctx, fact=q1(200_001, 60 + k), preds=[(0, "le", 2450)], group_cols=[1, 2], aggs=Q1_AGGS, topk=k,
+             topk_agg=1, max_groups=16, capacity_groups=k)
+
+
 @pytest.mark.parametrize("topk", [0, 1, 100, 1000])
 def test_join_group_topk(ctx, topk):
     fact, dim = join_case(30_000, 3_000, 1_200_000, 7)

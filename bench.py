@@ -223,7 +223,7 @@ def oracle_plan_rate(spec, rows, seconds):
 
 def secondary_workloads(tqp, torch, dev, local, reps, cpu_seconds=0.0):
     """The other two analytical shapes, timed per launch (reported beside the headline), each with the CPU
-    oracle timed on the same inputs (config 0 in full, config 2 on a 6M-row probe sample)."""
+    oracle timed on the same inputs (the 1M-row aggregate in full, the join on a 6M-row probe sample)."""
     out = {}
     stream = torch.cuda.current_stream()
     flush_buf = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # 512 MB > L2
@@ -446,7 +446,7 @@ SERVE_POOL = 512  # result buffer sets, reused round-robin
 def serving_workload(tqp, torch, dev, local, seconds=10.0, rate=2000.0, sweep=(2000, 6000, 16000),
                      sweep_seconds=1.0, fact_rows=SERVE_FACT_ROWS, dim_rows=SERVE_DIM_ROWS):
     """Open-loop Poisson arrivals of the three plan shapes over seeded row ranges of a resident fact table
-    (config-0 columns) joined, for the join shape, with a prepared resident dimension; continuous batching
+    (the scan-aggregate columns) joined, for the join shape, with a prepared resident dimension; continuous batching
     (tqp_server, 64 plans per batch, 3 batches in flight) against one-at-a-time FIFO (1 plan, 1 in flight)."""
     from datagen import torch_gen
     seed = datagen.DEFAULT_SEED + 4
@@ -583,7 +583,7 @@ def serving_workload(tqp, torch, dev, local, seconds=10.0, rate=2000.0, sweep=(2
     tqp.tqp_dim_destroy(pdim)
     pctx.close()
     return {
-        "workload": f"{fact_rows // 1_000_000}M-row resident fact table (config-0 columns, {fact_rows * 30 / 1e9:.0f} GB) "
+        "workload": f"{fact_rows // 1_000_000}M-row resident fact table (scan-aggregate columns, {fact_rows * 30 / 1e9:.0f} GB) "
                     f"+ prepared {dim_rows // 1_000_000}M-row dimension; open-loop Poisson arrivals; each query one of "
                     "q1 group-by / q6 filter+ids+sum / join+group+top-100 over a seeded row range of "
                     "log-uniform [10K, 5M] rows",

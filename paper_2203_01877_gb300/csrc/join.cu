@@ -179,7 +179,7 @@ struct ProbeArgs {
     JoinHT H;
     int32_t key_col;
     int32_t pad;
-    uint32_t* row_slot;          // per probe row: matched slot, or 0xFFFFFFFF
+    uint2* row_run;              // per probe row: its key's run (first bidx index, length); length 0: no match
     int32_t* out_build;
     int32_t* out_probe;
     int64_t capacity;
@@ -201,19 +201,53 @@ struct ProbeBody {
         excl_sm = wtot + 2 * kConsumerWarps;
     }
 
+    // Four rows per lane: their home slots are loaded together, then each
+    // row walks its probe sequence (rarely past the home slot at load factor
+    // <= 1/2) and records its key's run for the second pass.
     __device__ void pass1(const ScanGeom& G, const TileView& v, int cw, int lane) {
-        const int rw = G.T / kConsumerWarps;
+        const int rw = G.T / kConsumerWarps;  // a multiple of 128
+        const JoinHT& H = A.H;
+        const unsigned long long mask = static_cast<unsigned long long>(H.cap - 1);
         unsigned long long pairs = 0;
-        for (int r = cw * rw + lane; r < cw * rw + rw; r += kWarp) {
-            if (r >= v.rows) break;
-            const uint64_t key = static_cast<uint64_t>(col_val(G, v, A.key_col, r));
-            const long long s = ht_find(A.H, key);
-            uint32_t slot = 0xFFFFFFFFu;
-            if (s >= 0) {
-                slot = static_cast<uint32_t>(s);
-                pairs += A.H.slots[s].w;
+        for (int base = cw * rw; base < cw * rw + rw; base += 4 * kWarp) {
+            if (base >= v.rows) break;
+            uint64_t key[4];
+            unsigned long long h[4];
+            uint4 sl[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int r = base + kWarp * j + lane;
+                key[j] = 0;
+                h[j] = 0;
+                sl[j] = make_uint4(0u, 0u, 0u, 0u);
+                if (r < v.rows) {
+                    key[j] = static_cast<uint64_t>(col_val(G, v, A.key_col, r));
+                    h[j] = key[j] == ~0ULL ? static_cast<unsigned long long>(H.cap) : (mix64(key[j]) & mask);
+                    sl[j] = __ldg(&H.slots[h[j]]);
+                }
             }
-            A.row_slot[v.row0 + r] = slot;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int r = base + kWarp * j + lane;
+                if (r >= v.rows) continue;
+                uint4 s = sl[j];
+                bool hit;
+                if (key[j] == ~0ULL) {  // the all-ones key lives in the extra slot
+                    hit = s.w != 0;
+                } else {
+                    unsigned long long hh = h[j];
+                    for (long long i = 0; i < H.cap; ++i) {
+                        const uint64_t k = slot_key(s);
+                        if (k == key[j] || k == ~0ULL) break;
+                        hh = (hh + 1) & mask;
+                        s = __ldg(&H.slots[hh]);
+                    }
+                    hit = slot_key(s) == key[j];
+                }
+                const uint2 run = hit ? make_uint2(s.z, s.w) : make_uint2(0u, 0u);
+                pairs += run.y;
+                A.row_run[v.row0 + r] = run;
+            }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
@@ -241,13 +275,9 @@ struct ProbeBody {
         int par = 0;
         for (long long base = r_begin; base < r_end; base += kConsumers) {
             const long long row = base + cw * kWarp + lane;
-            uint32_t slot = 0xFFFFFFFFu;
-            uint4 sl = make_uint4(0, 0, 0, 0);
-            if (row < r_end) {
-                slot = A.row_slot[row];
-                if (slot != 0xFFFFFFFFu) sl = A.H.slots[slot];
-            }
-            const unsigned long long c = sl.w;
+            uint2 run = make_uint2(0u, 0u);
+            if (row < r_end) run = A.row_run[row];
+            const unsigned long long c = run.y;
             unsigned long long incl = c;
 #pragma unroll
             for (int o = 1; o < kWarp; o <<= 1) {
@@ -266,7 +296,7 @@ struct ProbeBody {
             unsigned long long pos = running + before + (incl - c);
             for (uint32_t k = 0; k < static_cast<uint32_t>(c); ++k, ++pos) {
                 if (pos < static_cast<unsigned long long>(A.capacity)) {
-                    A.out_build[pos] = static_cast<int32_t>(A.H.bidx[sl.z + k]);
+                    A.out_build[pos] = static_cast<int32_t>(A.H.bidx[run.x + k]);
                     A.out_probe[pos] = static_cast<int32_t>(row);
                 }
             }
@@ -321,8 +351,8 @@ tqp_status launch_hash_join(tqp_ctx* ctx, const tqp_table* build, int32_t build_
     A.ctl.nchunks = (A.G.ntiles + A.ctl.chunk_tiles - 1) / A.ctl.chunk_tiles;
     const size_t words = 3 + static_cast<size_t>(A.ctl.nchunks);
     unsigned long long* sc = static_cast<unsigned long long*>(arena_alloc(ctx, words * 8));
-    A.row_slot = static_cast<uint32_t*>(arena_alloc(ctx, static_cast<size_t>(probe->num_rows) * 4));
-    if (!sc || !A.row_slot) return arena_oom(ctx, words * 8 + static_cast<size_t>(probe->num_rows) * 4);
+    A.row_run = static_cast<uint2*>(arena_alloc(ctx, static_cast<size_t>(probe->num_rows) * 8));
+    if (!sc || !A.row_run) return arena_oom(ctx, words * 8 + static_cast<size_t>(probe->num_rows) * 8);
     TQP_CUDA(cudaMemsetAsync(sc, 0, words * 8, stream));
     A.ctl.ticket = sc;
     A.ctl.err = ctx->d_err;

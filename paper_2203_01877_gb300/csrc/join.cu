@@ -270,14 +270,25 @@ struct ProbeBody {
         }
         named_sync(kBarConsumers, kConsumers);
         unsigned long long running = *excl_sm;
-        const long long r_begin = t0 * G.T;
+        const long long r_begin = t0 * G.T;  // a multiple of 1024: every lane's four rows start 32-byte aligned
         const long long r_end = (t1 * G.T < G.n) ? t1 * G.T : G.n;
         int par = 0;
-        for (long long base = r_begin; base < r_end; base += kConsumers) {
-            const long long row = base + cw * kWarp + lane;
-            uint2 run = make_uint2(0u, 0u);
-            if (row < r_end) run = A.row_run[row];
-            const unsigned long long c = run.y;
+        // rounds of 4 * kConsumers rows, four consecutive rows per lane (row order = lane order)
+        for (long long base = r_begin; base < r_end; base += 4 * kConsumers) {
+            const long long r0 = base + 4LL * (cw * kWarp + lane);
+            uint2 run[4];
+            if (r0 + 4 <= r_end) {
+                const uint4* p = reinterpret_cast<const uint4*>(A.row_run + r0);
+                const uint4 a = p[0], b = p[1];
+                run[0] = make_uint2(a.x, a.y);
+                run[1] = make_uint2(a.z, a.w);
+                run[2] = make_uint2(b.x, b.y);
+                run[3] = make_uint2(b.z, b.w);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) run[j] = r0 + j < r_end ? A.row_run[r0 + j] : make_uint2(0u, 0u);
+            }
+            const unsigned long long c = static_cast<unsigned long long>(run[0].y) + run[1].y + run[2].y + run[3].y;
             unsigned long long incl = c;
 #pragma unroll
             for (int o = 1; o < kWarp; o <<= 1) {
@@ -294,10 +305,13 @@ struct ProbeBody {
                 round_total += x;
             }
             unsigned long long pos = running + before + (incl - c);
-            for (uint32_t k = 0; k < static_cast<uint32_t>(c); ++k, ++pos) {
-                if (pos < static_cast<unsigned long long>(A.capacity)) {
-                    A.out_build[pos] = static_cast<int32_t>(A.H.bidx[run.x + k]);
-                    A.out_probe[pos] = static_cast<int32_t>(row);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                for (uint32_t k = 0; k < run[j].y; ++k, ++pos) {
+                    if (pos < static_cast<unsigned long long>(A.capacity)) {
+                        A.out_build[pos] = static_cast<int32_t>(A.H.bidx[run[j].x + k]);
+                        A.out_probe[pos] = static_cast<int32_t>(r0 + j);
+                    }
                 }
             }
             running += round_total;

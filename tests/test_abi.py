@@ -92,3 +92,15 @@ def test_host_only_calls(libtqp):
     assert b"ctx" in libtqp.tqp_last_error()
     libtqp.tqp_ctx_destroy.restype = C.c_int
     assert libtqp.tqp_ctx_destroy(None) == 0
+
+
+def test_tableref_accepts_host_columns_only_on_request():
+    """TableRef takes CUDA tensors; a host tensor only with host_ok and only
+    when it is pinned (the library then decides where host memory may be read)."""
+    torch = pytest.importorskip("torch")
+    import paper_2203_01877_gb300 as tqp
+    host = torch.zeros(16, dtype=torch.int64)
+    with pytest.raises(ValueError):
+        tqp.TableRef([host])
+    with pytest.raises(ValueError):
+        tqp.TableRef([host], host_ok=True)  # pageable, not pinned

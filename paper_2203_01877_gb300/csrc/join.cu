@@ -106,12 +106,23 @@ tqp_status ht_build_chain(tqp_ctx* ctx, const tqp_table* build, int32_t key_col,
     return ht_chain_insert_launch(ctx, build, key_col, *H, *next, stream);
 }
 
+// A direct-mapped table (dense build keys: max - min < cap) puts key k in
+// slot k - min, and every key, the all-ones one included, in the main slots.
 __global__ void k_ht_insert(JoinHT H, const unsigned char* key_col, int key_type, long long n, uint64_t* sort_key,
                             uint32_t* sort_val, int* err) {
+    long long kmin = 0;
+    const bool direct = ht_is_direct(H, &kmin);
     for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
          i += static_cast<long long>(gridDim.x) * blockDim.x) {
         const uint64_t key = static_cast<uint64_t>(ldg_typed(key_col, key_type, i));
-        const long long s = ht_claim(H, key, err);
+        long long s;
+        if (direct) {
+            s = static_cast<long long>(key - static_cast<uint64_t>(kmin));
+            H.slots[s].x = static_cast<uint32_t>(key);  // (several rows may write the same key)
+            H.slots[s].y = static_cast<uint32_t>(key >> 32);
+        } else {
+            s = ht_claim(H, key, err);
+        }
         if (s >= 0) atomicAdd(&H.slots[s].w, 1u);
         sort_key[i] = static_cast<uint64_t>(s < 0 ? H.cap : s);
         sort_val[i] = static_cast<uint32_t>(i);
@@ -138,13 +149,16 @@ size_t ht_bytes(long long n_build) {
 tqp_status ht_build(tqp_ctx* ctx, const tqp_table* build, int32_t key_col, JoinHT* H, cudaStream_t stream) {
     const long long n = build->num_rows;
     H->cap = ht_cap(n) * ht_scale(ctx);
-    H->meta = nullptr;
     H->slots = static_cast<uint4*>(arena_alloc(ctx, static_cast<size_t>(H->cap + 1) * sizeof(uint4)));
     const long long nn = n > 0 ? n : 1;
     unsigned char* sb = static_cast<unsigned char*>(arena_alloc(ctx, 2 * (static_cast<size_t>(nn) * 12 + 256)));
     void* rs = arena_alloc(ctx, radix_sort_scratch(nn));
     long long* d_n = static_cast<long long*>(arena_alloc(ctx, 256));
-    if (!H->slots || !sb || !rs || !d_n) return arena_oom(ctx, ht_bytes(n));
+    long long* meta = static_cast<long long*>(arena_alloc(ctx, 64));
+    if (!H->slots || !sb || !rs || !d_n || !meta) return arena_oom(ctx, ht_bytes(n));
+    // the build keys' range first: dense keys make the table direct-mapped
+    H->meta = meta;
+    TQP_TRY(ht_key_range_launch(ctx, build, key_col, meta, stream));
     uint64_t* k0 = reinterpret_cast<uint64_t*>(sb);
     uint64_t* k1 = k0 + nn;
     uint32_t* v0 = reinterpret_cast<uint32_t*>(k1 + nn);
@@ -208,6 +222,8 @@ struct ProbeBody {
         const int rw = G.T / kConsumerWarps;  // a multiple of 128
         const JoinHT& H = A.H;
         const unsigned long long mask = static_cast<unsigned long long>(H.cap - 1);
+        long long kmin = 0;
+        const bool direct = ht_is_direct(H, &kmin);
         unsigned long long pairs = 0;
         for (int base = cw * rw; base < cw * rw + rw; base += 4 * kWarp) {
             if (base >= v.rows) break;
@@ -222,8 +238,13 @@ struct ProbeBody {
                 sl[j] = make_uint4(0u, 0u, 0u, 0u);
                 if (r < v.rows) {
                     key[j] = static_cast<uint64_t>(col_val(G, v, A.key_col, r));
-                    h[j] = key[j] == ~0ULL ? static_cast<unsigned long long>(H.cap) : (mix64(key[j]) & mask);
-                    sl[j] = __ldg(&H.slots[h[j]]);
+                    if (direct) {
+                        h[j] = key[j] - static_cast<uint64_t>(kmin);
+                        if (h[j] < static_cast<unsigned long long>(H.cap)) sl[j] = __ldg(&H.slots[h[j]]);
+                    } else {
+                        h[j] = key[j] == ~0ULL ? static_cast<unsigned long long>(H.cap) : (mix64(key[j]) & mask);
+                        sl[j] = __ldg(&H.slots[h[j]]);
+                    }
                 }
             }
 #pragma unroll
@@ -232,7 +253,9 @@ struct ProbeBody {
                 if (r >= v.rows) continue;
                 uint4 s = sl[j];
                 bool hit;
-                if (key[j] == ~0ULL) {  // the all-ones key lives in the extra slot
+                if (direct) {  // the key's own slot (zero when out of range): any rows are matches
+                    hit = s.w != 0;
+                } else if (key[j] == ~0ULL) {  // the all-ones key lives in the extra slot
                     hit = s.w != 0;
                 } else {
                     unsigned long long hh = h[j];

@@ -15,7 +15,9 @@ A plan is given as plain Python data:
 * expressions: postfix token lists -- ``("col", i)``, ``("const", v)``,
   ``"add"``, ``"sub"``, ``"mul"``; column ``i`` addresses fact columns first,
   then dim columns.
-* ``aggs``: ``(fn, expr)`` with fn in ``sum count avg``.
+* ``aggs``: ``(fn, expr)`` with fn in ``sum count avg min max`` (MIN/MAX: the
+  oracle's definition for the library's next aggregates; the library has no
+  MIN/MAX yet).
 """
 from __future__ import annotations
 
@@ -37,7 +39,7 @@ OK, ERR_INVALID, ERR_CAPACITY, ERR_OVERFLOW, ERR_NOMEM = 0, 1, 4, 5, 6
 _TYPES = {np.dtype(np.int32): 0, np.dtype(np.int64): 1, np.dtype(np.uint8): 2}
 _OPS = {"lt": 0, "le": 1, "gt": 2, "ge": 3, "eq": 4, "ne": 5, "between": 6}
 _XK = {"col": 0, "const": 1, "add": 2, "sub": 3, "mul": 4}
-_FNS = {"sum": 0, "count": 1, "avg": 2}
+_FNS = {"sum": 0, "count": 1, "avg": 2, "min": 3, "max": 4}
 MAX_EXPR = 8
 
 

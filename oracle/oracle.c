@@ -20,7 +20,10 @@
  *                     aggregate descending, ties by key ascending, first k.
  *
  * Arithmetic is int64 with overflow checks (decimals are x100 fixed point);
- * AVG is (double)SUM / (double)COUNT, one IEEE round-to-nearest division.
+ * AVG is (double)SUM / (double)COUNT, one IEEE round-to-nearest division;
+ * MIN and MAX are the smallest and largest value of the expression over the
+ * group's rows (the ungrouped aggregate over no rows reports 0 with the
+ * floating-point value NaN as its flag, like AVG).
  * Not thread-safe: one call at a time per process.
  */
 #include "oracle.h"
@@ -162,8 +165,10 @@ int oracle_plan(const or_plan* p, or_out* o) {
         if (p->group_cols[i] < 0 || p->group_cols[i] >= ncat) return OR_ERR_INVALID;
     for (int i = 0; i < p->ndim_cols && joined; ++i)
         if (!valid_col(&p->dim[i])) return OR_ERR_INVALID;
-    for (int a = 0; a < p->naggs; ++a)
+    for (int a = 0; a < p->naggs; ++a) {
+        if (p->aggs[a].fn < OR_SUM || p->aggs[a].fn > OR_MAX) return OR_ERR_INVALID;
         if (p->aggs[a].fn != OR_COUNT && !valid_expr(&p->aggs[a].expr, ncat)) return OR_ERR_INVALID;
+    }
     if (p->sum_expr && !valid_expr(p->sum_expr, ncat)) return OR_ERR_INVALID;
     int status = OR_OK;
 
@@ -282,10 +287,20 @@ int oracle_plan(const or_plan* p, or_out* o) {
             gcnt[g] += 1;
             const or_pair* r = &pairs[rec[i].idx];
             for (int a = 0; a < na; ++a) {
-                if (p->aggs[a].fn == OR_COUNT) continue;
+                const int fn = p->aggs[a].fn;
+                if (fn == OR_COUNT) continue;
                 int64_t v;
-                if (expr_eval(p, &p->aggs[a].expr, r, &v) ||
-                    __builtin_add_overflow(gsum[g * na + a], v, &gsum[g * na + a])) {
+                if (expr_eval(p, &p->aggs[a].expr, r, &v)) {
+                    free(gkeys); free(gsum); free(gcnt); free(rec); free(pairs);
+                    return OR_ERR_OVERFLOW;
+                }
+                int64_t* acc = &gsum[g * na + a];
+                if (fn == OR_MIN || fn == OR_MAX) {
+                    /* the group's first row sets it, later rows replace it when smaller / larger */
+                    if (gcnt[g] == 1 || (fn == OR_MIN ? v < *acc : v > *acc)) *acc = v;
+                    continue;
+                }
+                if (__builtin_add_overflow(*acc, v, acc)) {
                     free(gkeys); free(gsum); free(gcnt); free(rec); free(pairs);
                     return OR_ERR_OVERFLOW;
                 }
@@ -330,8 +345,12 @@ int oracle_plan(const or_plan* p, or_out* o) {
                 int fn = p->aggs[a].fn;
                 int64_t iv = (fn == OR_COUNT) ? gcnt[gi] : gsum[gi * na + a];
                 if (o->ivals) o->ivals[i * na + a] = iv;
-                if (o->fvals)
-                    o->fvals[i * na + a] = (fn == OR_AVG) ? ((double)gsum[gi * na + a] / (double)gcnt[gi]) : 0.0;
+                if (o->fvals) {
+                    double f = 0.0;
+                    if (fn == OR_AVG) f = (double)gsum[gi * na + a] / (double)gcnt[gi];
+                    else if ((fn == OR_MIN || fn == OR_MAX) && gcnt[gi] == 0) f = NAN;
+                    o->fvals[i * na + a] = f;
+                }
             }
         }
         if (nout > o->cap_groups) status = OR_ERR_CAPACITY;

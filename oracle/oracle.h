@@ -51,6 +51,8 @@ extern "C" {
 #define OR_SUM 0
 #define OR_COUNT 1
 #define OR_AVG 2
+#define OR_MIN 3
+#define OR_MAX 4
 
 #define OR_MAX_EXPR 8
 

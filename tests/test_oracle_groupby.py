@@ -134,3 +134,63 @@ def test_topk_vs_full_sort_with_ties():
         sel = order[:k]
         assert np.array_equal(keys[:, 0], keys_all[sel, 0])
         assert np.array_equal(iv, iv_all[sel])
+
+
+def test_min_max_vs_numpy():
+    """MIN and MAX per group against numpy's minimum.at / maximum.at over the
+    same groups (np.unique with inverse), with a predicate, an expression
+    argument, all-positive and all-negative columns (so a missing first-row
+    initialisation shows), and int64 extremes."""
+    rng = np.random.default_rng(12)
+    n = 40_000
+    k1 = rng.integers(-3, 4, n).astype(np.int32)
+    k2 = rng.integers(0, 5, n).astype(np.uint8)
+    v = rng.integers(-10**15, 10**15, n).astype(np.int64)
+    pos = rng.integers(1, 1000, n).astype(np.int32)
+    neg = -rng.integers(1, 1000, n).astype(np.int64)
+    v[::997] = np.iinfo(np.int64).min
+    v[5::991] = np.iinfo(np.int64).max
+    cols = [k1, k2, v, pos, neg]
+    aggs = [("min", [("col", 2)]), ("max", [("col", 2)]), ("min", [("col", 3)]), ("max", [("col", 4)]),
+            ("min", [("col", 3), ("col", 4), "add"]), ("count", None)]
+    keys, iv, fv = oracle.groupby(cols, [(3, "gt", 100)], [0, 1], aggs)
+    mask = pos > 100
+    kk = np.stack([k1.astype(np.int64), k2.astype(np.int64)], 1)[mask]
+    uniq, inv = np.unique(kk, axis=0, return_inverse=True)
+    inv = inv.reshape(-1)
+
+    def red(x, fn):
+        big = np.iinfo(np.int64).max if fn is np.minimum else np.iinfo(np.int64).min
+        out = np.full(len(uniq), big, dtype=np.int64)
+        fn.at(out, inv, x[mask].astype(np.int64))
+        return out
+
+    want = np.stack([red(v, np.minimum), red(v, np.maximum), red(pos, np.minimum), red(neg, np.maximum),
+                     red(pos.astype(np.int64) + neg, np.minimum),
+                     np.bincount(inv, minlength=len(uniq)).astype(np.int64)], 1)
+    assert np.array_equal(keys, uniq)
+    assert np.array_equal(iv, want)
+    assert np.all(fv == 0.0)
+
+
+def test_min_max_hand_worked_and_empty():
+    """Three groups worked by hand; the ungrouped MIN/MAX over no rows is 0
+    with NaN as its flag (like AVG), and over one row is that row."""
+    g = np.array([2, 1, 2, 1, 3], np.int32)
+    x = np.array([5, -7, -2, 9, 4], np.int64)
+    keys, iv, fv = oracle.groupby([g, x], [], [0], [("min", [("col", 1)]), ("max", [("col", 1)])])
+    assert keys.tolist() == [[1], [2], [3]]
+    assert iv.tolist() == [[-7, 9], [-2, 5], [4, 4]]
+    keys, iv, fv = oracle.groupby([g, x], [(1, "gt", 100)], [], [("min", [("col", 1)]), ("count", None)])
+    assert iv.tolist() == [[0, 0]] and np.isnan(fv[0, 0])
+    keys, iv, fv = oracle.groupby([g, x], [(1, "eq", -2)], [], [("max", [("col", 1)])])
+    assert iv.tolist() == [[-2]] and fv[0, 0] == 0.0
+
+
+def test_topk_by_max_with_ties():
+    """Top-k ranks by the MAX aggregate descending, ties by key ascending."""
+    g = np.array([4, 4, 1, 1, 3, 2, 2], np.int32)
+    x = np.array([7, 3, 7, 1, 9, 7, -1], np.int64)
+    keys, iv, fv = oracle.groupby([g, x], [], [0], [("max", [("col", 1)])], topk=3, topk_agg=0)
+    assert keys.reshape(-1).tolist() == [3, 1, 2]
+    assert iv.reshape(-1).tolist() == [9, 7, 7]

@@ -29,7 +29,7 @@ MUTANTS = {
     "u8_sign_extended": ("(int64_t)((const uint8_t*)c->data)[row]", "(int64_t)((const int8_t*)c->data)[row]"),
     "first_predicate_only": ("for (int j = 0; j < p->npreds && keep; ++j)", "for (int j = 0; j < 1 && j < p->npreds && keep; ++j)"),
     "count_drops_first_row": ("gcnt[g] += 1;", "gcnt[g] += (i > 0);"),
-    "avg_integer_division": ("((double)gsum[gi * na + a] / (double)gcnt[gi])", "((double)(gsum[gi * na + a] / gcnt[gi]))"),
+    "avg_integer_division": ("f = (double)gsum[gi * na + a] / (double)gcnt[gi];", "f = (double)(gsum[gi * na + a] / gcnt[gi]);"),
     "group_key_second_col_ignored": ("for (int i = 0; i < n; ++i)\n        if (a[i] != b[i])", "for (int i = 0; i < n && i < 1; ++i)\n        if (a[i] != b[i])"),
     "join_first_match_only": ("for (int64_t j = lower_bound(sd, p->ndim, k); j < p->ndim && sd[j].key == k; ++j)",
                               "for (int64_t j = lower_bound(sd, p->ndim, k), j0 = j; j < p->ndim && sd[j].key == k && j == j0; ++j)"),
@@ -37,6 +37,8 @@ MUTANTS = {
     "topk_ascending": ("return x->rank_val > y->rank_val ? -1 : 1;", "return x->rank_val < y->rank_val ? -1 : 1;"),
     "topk_tie_key_desc": ("return cmp_keys(x->key, y->key, g_ngc);                                   /* then key asc */",
                           "return -cmp_keys(x->key, y->key, g_ngc);"),
+    "min_compares_as_max": ("(fn == OR_MIN ? v < *acc : v > *acc)", "(fn == OR_MIN ? v > *acc : v > *acc)"),
+    "min_max_no_first_row_init": ("if (gcnt[g] == 1 || (fn == OR_MIN", "if (0 || (fn == OR_MIN"),
     "sum_skips_last_row": ("for (int64_t i = 0; i < npairs; ++i) {\n            int64_t v;",
                            "for (int64_t i = 0; i + 1 < npairs; ++i) {\n            int64_t v;"),
 }
@@ -52,6 +54,9 @@ PINS = [
     tg.test_alg3_second_restatement,
     tg.test_signed_lexicographic_key_order,
     tg.test_topk_vs_full_sort_with_ties,
+    tg.test_min_max_vs_numpy,
+    tg.test_min_max_hand_worked_and_empty,
+    tg.test_topk_by_max_with_ties,
     lambda: tj.test_nested_loop_tiny_with_duplicates(0),
     tj.test_hand_worked_example,
     tj.test_cardinality_identity_and_paper_algorithms,

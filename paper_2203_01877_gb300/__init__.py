@@ -11,7 +11,8 @@ Plan vocabulary (shared with the tests):
 * predicates ``(col, op, lo[, hi])`` with op in ``lt le gt ge eq ne between``;
 * expressions: postfix token lists ``("col", i)``, ``("const", v)``, ``"add"``,
   ``"sub"``, ``"mul"``;
-* aggregates ``(fn, expr)`` with fn in ``sum count avg``.
+* aggregates ``(fn, expr)`` with fn in ``sum count avg min max`` (MIN/MAX: few-group
+  aggregations without a join, see include/tqp.h).
 """
 from __future__ import annotations
 
@@ -29,7 +30,7 @@ I32, I64, U8 = 0, 1, 2
 MAX_PREDS, MAX_EXPR, MAX_GROUP_COLS, MAX_AGGS, MAX_COLS = 8, 8, 4, 8, 16
 _OPS = {"lt": 0, "le": 1, "gt": 2, "ge": 3, "eq": 4, "ne": 5, "between": 6}
 _XOPS = {"col": 0, "const": 1, "add": 2, "sub": 3, "mul": 4}
-_FNS = {"sum": 0, "count": 1, "avg": 2}
+_FNS = {"sum": 0, "count": 1, "avg": 2, "min": 3, "max": 4}
 
 
 class TqpError(RuntimeError):

@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(kDirThreads, kDirMinBlocks) k_b_gdirect(const 
     extern __shared__ __align__(16) unsigned char dsm[];
     const DirJob& j = J[bjob[blockIdx.x]];
     const GroupDirectArgs& A = stage_args(j.A, dsm + kDirSmemBytes);
-    group_direct_block(A, dsm, static_cast<long long>(blockIdx.x) - j.first_block, j.nblocks);
+    group_direct_block<false>(A, dsm, static_cast<long long>(blockIdx.x) - j.first_block, j.nblocks);
 }
 
 __global__ void __launch_bounds__(kFinThreads) k_b_finalize(const FinJob* F) {
@@ -792,8 +792,10 @@ static bool batchable(const tqp_ctx* ctx, const tqp_plan* p, const tqp_result* r
     if (grouped && (!r->d_num_groups || r->capacity_groups < 1)) return false;
     if (grouped && p->topk > 0 && (p->topk_agg < 0 || p->topk_agg >= p->naggs)) return false;
     const int nf = p->fact->num_cols;
-    for (int a = 0; a < p->naggs; ++a)
+    for (int a = 0; a < p->naggs; ++a) {
         if (p->aggs[a].fn == TQP_AVG && !r->d_fvals) return false;
+        if (p->aggs[a].fn == TQP_MIN || p->aggs[a].fn == TQP_MAX) return false;  // the single-plan path has them
+    }
     if (p->emit_row_ids && r->d_row_ids && !r->d_num_rows) return false;
     if (!p->dim) {
         for (int i = 0; i < p->ngc; ++i)

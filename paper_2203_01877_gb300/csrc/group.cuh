@@ -22,6 +22,12 @@ struct GroupSpec {
     int32_t agg_fn[TQP_MAX_AGGS];
     int32_t agg_acc[TQP_MAX_AGGS];
     DExpr acc_expr[TQP_MAX_AGGS];  // expression of accumulator a + 1
+    // How accumulator a + 1 combines (kAccSum: the sum; kAccMax / kAccMin: the
+    // unsigned maximum of an order-preserving code, so every accumulator still
+    // starts at zero); `minmax` is set when any is not a sum.
+    int32_t acc_kind[TQP_MAX_AGGS];
+    int32_t minmax;
+    int32_t pad_kind;
     unsigned long long* keys;      // [cap + 1], kEmptyKey = free; slot cap holds the all-ones key
     unsigned long long* acc;       // [(cap + 1) * nacc]
     long long cap;                 // power of two (dense mode: entry bound)
@@ -29,6 +35,19 @@ struct GroupSpec {
     long long max_groups;
     const long long* d_dense_n;    // dense mode: entries [0, *d_dense_n) are groups with any key
 };
+
+constexpr int32_t kAccSum = 0, kAccMax = 1, kAccMin = 2;
+
+// MAX keeps the largest x ^ 2^63 (unsigned order = signed order of x); MIN
+// the largest ~(x ^ 2^63).  Both codes of a row are above the zero start
+// except that of the extreme value, which decodes correctly from zero.
+__host__ __device__ __forceinline__ unsigned long long acc_encode(int kind, int64_t x) {
+    const unsigned long long u = static_cast<unsigned long long>(x) ^ 0x8000000000000000ull;
+    return kind == kAccMin ? ~u : u;
+}
+__host__ __device__ __forceinline__ int64_t acc_decode(int kind, unsigned long long u) {
+    return static_cast<int64_t>((kind == kAccMin ? ~u : u) ^ 0x8000000000000000ull);
+}
 
 __device__ __forceinline__ uint64_t enc_key(int64_t x, int bits) {
     if (bits == 8) return static_cast<uint64_t>(x) & 0xFFull;
@@ -97,11 +116,15 @@ __device__ __forceinline__ void emit_group(const GroupSpec& S, const GroupOut& O
     const unsigned long long* a = slot >= 0 ? S.acc + slot * S.nacc : nullptr;
     const long long cnt = a ? static_cast<long long>(a[0]) : 0;
     for (int j = 0; j < S.naggs; ++j) {
-        const long long x = a ? static_cast<long long>(a[S.agg_acc[j]]) : 0;
+        const int fn = S.agg_fn[j];
+        const bool mm = fn == TQP_MIN || fn == TQP_MAX;
+        long long x = a ? static_cast<long long>(a[S.agg_acc[j]]) : 0;
+        if (mm) x = cnt ? acc_decode(S.acc_kind[S.agg_acc[j] - 1], static_cast<unsigned long long>(x)) : 0;
         if (O.ivals) O.ivals[g * S.naggs + j] = x;
         if (O.fvals) {
             double f = 0.0;
-            if (S.agg_fn[j] == TQP_AVG) f = __ddiv_rn(__ll2double_rn(x), __ll2double_rn(cnt));
+            if (fn == TQP_AVG) f = __ddiv_rn(__ll2double_rn(x), __ll2double_rn(cnt));
+            else if (mm && cnt == 0) f = __longlong_as_double(0x7ff8000000000000LL);  // no rows: NaN flag
             O.fvals[g * S.naggs + j] = f;
         }
     }

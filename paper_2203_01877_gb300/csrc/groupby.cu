@@ -43,7 +43,14 @@ __global__ void __launch_bounds__(kEngineThreads, GroupBody::kMinBlocks) k_group
 
 __global__ void __launch_bounds__(kDirThreads, kDirMinBlocks) k_groupby_direct(const __grid_constant__ GroupDirectArgs A) {
     extern __shared__ __align__(16) unsigned char dsm[];
-    group_direct_block(A, dsm, blockIdx.x, gridDim.x);
+    group_direct_block<false>(A, dsm, blockIdx.x, gridDim.x);
+}
+
+// The same for tables with MIN/MAX accumulators (a separate kernel keeps the
+// sums-only one's register allocation).
+__global__ void __launch_bounds__(kDirThreads, kDirMinBlocks) k_groupby_direct_mm(const __grid_constant__ GroupDirectArgs A) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    group_direct_block<true>(A, dsm, blockIdx.x, gridDim.x);
 }
 
 __global__ void __launch_bounds__(kDirThreads) k_groupby_dprep(const __grid_constant__ GroupDirectArgs A,
@@ -136,21 +143,24 @@ tqp_status lower_group(const int32_t* key_cols, const int32_t* key_types, int32_
     S->naggs = naggs;
     for (int j = 0; j < naggs; ++j) {
         const int fn = aggs[j].fn;
-        if (fn != TQP_SUM && fn != TQP_COUNT && fn != TQP_AVG)
+        if (fn != TQP_SUM && fn != TQP_COUNT && fn != TQP_AVG && fn != TQP_MIN && fn != TQP_MAX)
             return fail(TQP_ERR_INVALID_ARG, "aggregate %d: unknown function %d", j, fn);
         S->agg_fn[j] = fn;
         if (fn == TQP_COUNT) {
             S->agg_acc[j] = 0;
             continue;
         }
+        const int kind = fn == TQP_MAX ? kAccMax : (fn == TQP_MIN ? kAccMin : kAccSum);
         DExpr e;
         TQP_TRY(lower_expr(&aggs[j].expr, ncols, &e));
         int found = -1;
         for (int a = 1; a < S->nacc; ++a)
-            if (same_expr(S->acc_expr[a - 1], e)) found = a;
+            if (same_expr(S->acc_expr[a - 1], e) && S->acc_kind[a - 1] == kind) found = a;
         if (found < 0) {
             found = S->nacc++;
             S->acc_expr[found - 1] = e;
+            S->acc_kind[found - 1] = kind;
+            if (kind != kAccSum) S->minmax = 1;
         }
         S->agg_acc[j] = found;
     }
@@ -425,6 +435,14 @@ tqp_status launch_groupby(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* pred
     const bool direct = lower_group_direct(t, A, max_groups, &D);
     TQP_TRY(group_table_init(&A.S, tab, cap, max_groups, stream, !direct));
 
+    if (A.S.minmax) {  // MIN/MAX: the direct kernel only, and not as the top-k order
+        if (!direct)
+            return fail(TQP_ERR_UNSUPPORTED, "MIN/MAX need at most %lld groups, at most %d accumulators besides COUNT "
+                                             "and at most %d predicates", kDirMaxGroups, kDirSums, kDirConds);
+        if (topk > 0 && topk_agg >= 0 && topk_agg < naggs &&
+            (aggs[topk_agg].fn == TQP_MIN || aggs[topk_agg].fn == TQP_MAX))
+            return fail(TQP_ERR_UNSUPPORTED, "top-k by a MIN/MAX aggregate is not supported");
+    }
     if (direct) {
         // two launches: the range pass (which also clears the table), then the
         // aggregation, whose last CTA finalizes the table unless top-k follows
@@ -432,11 +450,12 @@ tqp_status launch_groupby(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* pred
         D.err = ctx->d_err;
         D.O = O;
         D.fin = topk > 0 ? 0 : 1;
-        static bool attr_done[kMaxDevices] = {};
-        TQP_TRY(allow_smem(ctx, reinterpret_cast<const void*>(k_groupby_direct), attr_done));
+        static bool attr_done[kMaxDevices] = {}, attr_mm[kMaxDevices] = {};
+        const void* kern = A.S.minmax ? reinterpret_cast<const void*>(k_groupby_direct_mm)
+                                      : reinterpret_cast<const void*>(k_groupby_direct);
+        TQP_TRY(allow_smem(ctx, kern, A.S.minmax ? attr_mm : attr_done));
         int occ = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_groupby_direct, kDirThreads, kDirSmemBytes) !=
-                cudaSuccess ||
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kDirThreads, kDirSmemBytes) != cudaSuccess ||
             occ < 1)
             occ = 1;
         const long long nq = (t->num_rows + 3) / 4;
@@ -457,7 +476,12 @@ tqp_status launch_groupby(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* pred
         }
         k_groupby_dprep<<<D.ngc > 0 ? nparts : 1, kDirThreads, 0, stream>>>(D, kpart);
         TQP_CUDA(cudaGetLastError());
-        k_groupby_direct<<<static_cast<unsigned>(std::max<long long>(blocks, 1)), kDirThreads, kDirSmemBytes, stream>>>(D);
+        if (A.S.minmax)
+            k_groupby_direct_mm<<<static_cast<unsigned>(std::max<long long>(blocks, 1)), kDirThreads, kDirSmemBytes,
+                                  stream>>>(D);
+        else
+            k_groupby_direct<<<static_cast<unsigned>(std::max<long long>(blocks, 1)), kDirThreads, kDirSmemBytes,
+                               stream>>>(D);
         TQP_CUDA(cudaGetLastError());
         if (topk > 0) return group_topk(ctx, A.S, O, topk, topk_agg, d_total_groups, stream);
         return TQP_OK;

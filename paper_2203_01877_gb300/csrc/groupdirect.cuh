@@ -208,7 +208,33 @@ __device__ __forceinline__ void dir_factor(const GroupDirectArgs& A, const unsig
     }
 }
 
+// Accumulator combines (kMM: some accumulator is a MIN/MAX code, combined
+// by unsigned maximum; otherwise every accumulator is a sum).
+template <bool kMM>
+__device__ __forceinline__ unsigned long long acc_combine(int kind, unsigned long long x, unsigned long long y) {
+    if constexpr (kMM) return kind != kAccSum ? (x > y ? x : y) : x + y;
+    else return x + y;
+}
+
+template <bool kMM>
+__device__ __forceinline__ unsigned long long warp_combine(int kind, unsigned long long x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = acc_combine<kMM>(kind, x, __shfl_xor_sync(0xffffffffu, x, o));
+    return x;
+}
+
+// Into the global table: a reduction (sums) or an atomic maximum (codes).
+template <bool kMM>
+__device__ __forceinline__ void acc_store(int kind, unsigned long long* p, unsigned long long x) {
+    if (kMM && kind != kAccSum) atomicMax(p, x);
+    else red_add_u64(p, x);
+}
+
+// Kind of accumulator a (0 is the count).
+__device__ __forceinline__ int acc_kind_of(const GroupSpec& S, int a) { return a == 0 ? kAccSum : S.acc_kind[a - 1]; }
+
 // Every listed key's lane partials into the global table; the warp's tables are zero afterwards.
+template <bool kMM>
 __device__ __forceinline__ void dir_flush(const GroupDirectArgs& A, unsigned long long* area,
                                           const uint64_t (&dk)[kDirSlots], int nused, int lane) {
     __syncwarp();
@@ -224,11 +250,10 @@ __device__ __forceinline__ void dir_flush(const GroupDirectArgs& A, unsigned lon
         for (int a = 0; a < kDirAcc; ++a) {
             if (a < S.nacc) {
                 unsigned long long* p = area + (d * kDirAcc + a) * 32 + lane;
-                unsigned long long x = *p;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                const int kind = acc_kind_of(S, a);
+                const unsigned long long x = warp_combine<kMM>(kind, *p);
                 *p = 0;
-                if (lane == 0 && x && g >= 0) red_add_u64(&S.acc[g * S.nacc + a], x);
+                if (lane == 0 && x && g >= 0) acc_store<kMM>(kind, &S.acc[g * S.nacc + a], x);
             }
         }
     }
@@ -240,6 +265,7 @@ __device__ __forceinline__ void dir_flush(const GroupDirectArgs& A, unsigned lon
 // index).  Warp w takes the (slot, accumulator) pairs w, w + 8, ...: each
 // lane sums its column over the eight warps' tables, the warp sums the
 // lanes, and one reduction per pair and CTA goes to L2.
+template <bool kMM>
 __device__ __forceinline__ void dir_flush_dense_cta(const GroupDirectArgs& A, const DirDense& Dn,
                                                     unsigned long long* tables, int lane, int w) {
     const GroupSpec& S = A.S;
@@ -268,11 +294,12 @@ __device__ __forceinline__ void dir_flush_dense_cta(const GroupDirectArgs& A, co
     for (int pr = w; pr < npairs; pr += kDirThreads / 32) {
         const int d = pr / S.nacc, a = pr % S.nacc;
         if (gslot[d] < 0) continue;  // (warp-uniform) no row reached slot d
+        const int kind = acc_kind_of(S, a);
         unsigned long long x = 0;
-        for (int v = 0; v < kDirThreads / 32; ++v) x += tables[v * kDirWarpWords + (d * kDirAcc + a) * 32 + lane];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        if (lane == 0 && x) red_add_u64(&S.acc[gslot[d] * S.nacc + a], x);
+        for (int v = 0; v < kDirThreads / 32; ++v)
+            x = acc_combine<kMM>(kind, x, tables[v * kDirWarpWords + (d * kDirAcc + a) * 32 + lane]);
+        x = warp_combine<kMM>(kind, x);
+        if (lane == 0 && x) acc_store<kMM>(kind, &S.acc[gslot[d] * S.nacc + a], x);
     }
 }
 
@@ -280,6 +307,7 @@ __device__ __forceinline__ void dir_flush_dense_cta(const GroupDirectArgs& A, co
 // with the same slot folded first, so that the read-add-writes of the
 // remaining rows touch distinct addresses and issue together instead of
 // forming one dependent chain through shared memory.
+template <bool kMM>
 __device__ __forceinline__ void dir_rmw(const GroupDirectArgs& A, unsigned long long* area, uint32_t ok,
                                         const int (&id)[4], int64_t (&val)[kDirSums][4], int lane) {
     uint32_t act = ok;
@@ -292,7 +320,10 @@ __device__ __forceinline__ void dir_rmw(const GroupDirectArgs& A, unsigned long 
             if (!done && ((act >> k) & 1u) && ((act >> j) & 1u) && id[k] == id[j]) {
                 cnt[k] += cnt[j];
 #pragma unroll
-                for (int a = 0; a < kDirSums; ++a) val[a][k] += val[a][j];
+                for (int a = 0; a < kDirSums; ++a)
+                    val[a][k] = static_cast<int64_t>(acc_combine<kMM>(
+                        acc_kind_of(A.S, a + 1), static_cast<unsigned long long>(val[a][k]),
+                        static_cast<unsigned long long>(val[a][j])));
                 act &= ~(1u << j);
                 done = true;
             }
@@ -313,7 +344,9 @@ __device__ __forceinline__ void dir_rmw(const GroupDirectArgs& A, unsigned long 
 #pragma unroll
             for (int j = 0; j < 4; ++j)
                 if ((act >> j) & 1u)
-                    p[j][a * 32] = old[j] + (a == 0 ? cnt[j] : static_cast<unsigned long long>(val[a - 1][j]));
+                    p[j][a * 32] = a == 0 ? old[j] + cnt[j]
+                                          : acc_combine<kMM>(acc_kind_of(A.S, a), old[j],
+                                                             static_cast<unsigned long long>(val[a - 1][j]));
         }
     }
 }
@@ -321,6 +354,7 @@ __device__ __forceinline__ void dir_rmw(const GroupDirectArgs& A, unsigned long 
 // The four rows of every lane (pass bits `ok`) into the lane tables: ids from
 // the warp's key list (extended with new keys), then dir_rmw.  False, with
 // nothing added, when the list would overflow.
+template <bool kMM>
 __device__ __forceinline__ bool dir_lane_step(const GroupDirectArgs& A, unsigned long long* area,
                                               uint64_t (&dk)[kDirSlots], int& nused, uint32_t ok,
                                               const uint64_t (&key)[4], int64_t (&val)[kDirSums][4], int lane) {
@@ -373,14 +407,14 @@ __device__ __forceinline__ bool dir_lane_step(const GroupDirectArgs& A, unsigned
         for (int j = 0; j < 4; ++j) id[j] = nid[j];
         nused = nn;
     }
-    dir_rmw(A, area, ok, id, val, lane);
+    dir_rmw<kMM>(A, area, ok, id, val, lane);
     return true;
 }
 
 // One warp step: the quad q of every lane.  kSlot: every lane's quad holds
 // four rows of the table and sits in the warp slot; otherwise quads at or
 // past the end hold none and are read from global memory.
-template <bool kSlot, bool kDense>
+template <bool kSlot, bool kDense, bool kMM>
 __device__ __forceinline__ void dir_step(const GroupDirectArgs& A, const DirDense& Dn, unsigned long long* area,
                                          unsigned char* slot, uint64_t (&dk)[kDirSlots], int& nused, long long q,
                                          int lane, long long next = -1) {
@@ -467,18 +501,27 @@ __device__ __forceinline__ void dir_step(const GroupDirectArgs& A, const DirDens
             for (int j = 0; j < 4; ++j) val[a][j] = 0;
         }
     }
+    if constexpr (kMM) {  // MIN/MAX accumulators take their order-preserving codes
+#pragma unroll
+        for (int a = 0; a < kDirSums; ++a) {
+            const int kind = acc_kind_of(S, a + 1);
+            if (a < A.nsum && kind != kAccSum)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) val[a][j] = static_cast<int64_t>(acc_encode(kind, val[a][j]));
+        }
+    }
     if (kSlot && next >= 0) {  // every slot value is in registers: refill the slot with the next step
         __syncwarp();
         dir_prefetch(A, slot, next, lane);
     }
     if constexpr (kDense) {
-        dir_rmw(A, area, ok, id, val, lane);
+        dir_rmw<kMM>(A, area, ok, id, val, lane);
         return;
     }
-    if (dir_lane_step(A, area, dk, nused, ok, key, val, lane)) return;
-    dir_flush(A, area, dk, nused, lane);  // list full: flush and start a new one
+    if (dir_lane_step<kMM>(A, area, dk, nused, ok, key, val, lane)) return;
+    dir_flush<kMM>(A, area, dk, nused, lane);  // list full: flush and start a new one
     nused = 0;
-    if (dir_lane_step(A, area, dk, nused, ok, key, val, lane)) return;
+    if (dir_lane_step<kMM>(A, area, dk, nused, ok, key, val, lane)) return;
     // more distinct keys in this step than a list holds: row by row into the global table
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -488,7 +531,8 @@ __device__ __forceinline__ void dir_step(const GroupDirectArgs& A, const DirDens
         red_add_u64(&S.acc[g * S.nacc], 1ULL);
 #pragma unroll
         for (int a = 1; a <= kDirSums; ++a)
-            if (a < S.nacc) red_add_u64(&S.acc[g * S.nacc + a], static_cast<unsigned long long>(val[a - 1][j]));
+            if (a < S.nacc)
+                acc_store<kMM>(acc_kind_of(S, a), &S.acc[g * S.nacc + a], static_cast<unsigned long long>(val[a - 1][j]));
     }
 }
 
@@ -547,7 +591,7 @@ __device__ __forceinline__ void dir_dense_setup(const GroupDirectArgs& A, DirDen
 
 // The warp's grid-stride loop: 32 quads per step; a step whose quads all lie
 // within the table is fetched into the warp slot one step ahead.
-template <bool kDense>
+template <bool kDense, bool kMM>
 __device__ __forceinline__ void dir_loop(const GroupDirectArgs& A, const DirDense& Dn, unsigned long long* area,
                                          unsigned char* slot, int lane, int w, long long vb, long long vg) {
     uint64_t dk[kDirSlots];
@@ -567,16 +611,18 @@ __device__ __forceinline__ void dir_loop(const GroupDirectArgs& A, const DirDens
             cp_async_wait_all();
             __syncwarp();
             // dir_step moves the step's values to registers, then refills the slot
-            dir_step<true, kDense>(A, Dn, area, slot, dk, nused, base + lane, lane, nhave ? next + lane : -1);
+            dir_step<true, kDense, kMM>(A, Dn, area, slot, dk, nused, base + lane, lane, nhave ? next + lane : -1);
             have = nhave;
         } else {
-            dir_step<false, kDense>(A, Dn, area, slot, dk, nused, base + lane, lane);
+            dir_step<false, kDense, kMM>(A, Dn, area, slot, dk, nused, base + lane, lane);
         }
     }
-    if constexpr (!kDense) dir_flush(A, area, dk, nused, lane);  // dense: the CTA flushes once
+    if constexpr (!kDense) dir_flush<kMM>(A, area, dk, nused, lane);  // dense: the CTA flushes once
 }
 
-// One CTA of the direct group-by: block vb of vg blocks working on this table.
+// One CTA of the direct group-by: block vb of vg blocks working on this table
+// (kMM: the kernel for tables with MIN/MAX accumulators).
+template <bool kMM>
 __device__ __forceinline__ void group_direct_block(const GroupDirectArgs& A, unsigned char* smem, long long vb,
                                                    long long vg) {
     const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
@@ -587,11 +633,11 @@ __device__ __forceinline__ void group_direct_block(const GroupDirectArgs& A, uns
     for (int i = lane; i < kDirWarpWords; i += 32) area[i] = 0;
     __syncthreads();
     if (Dn->dense) {
-        dir_loop<true>(A, *Dn, area, slot, lane, w, vb, vg);
+        dir_loop<true, kMM>(A, *Dn, area, slot, lane, w, vb, vg);
         __syncthreads();
-        dir_flush_dense_cta(A, *Dn, reinterpret_cast<unsigned long long*>(smem), lane, w);
+        dir_flush_dense_cta<kMM>(A, *Dn, reinterpret_cast<unsigned long long*>(smem), lane, w);
     } else {
-        dir_loop<false>(A, *Dn, area, slot, lane, w, vb, vg);
+        dir_loop<false, kMM>(A, *Dn, area, slot, lane, w, vb, vg);
     }
     if (!A.fin) return;
     // the last CTA to finish finalizes the table (every CTA's adds are

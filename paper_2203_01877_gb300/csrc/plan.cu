@@ -187,9 +187,12 @@ static tqp_status run_join_plan(tqp_ctx* ctx, const tqp_plan* p, const tqp_resul
     for (int i = 0; i < p->ngc; ++i)
         if (p->group_cols[i] < nf || p->group_cols[i] >= nf + nd)
             return fail(TQP_ERR_UNSUPPORTED, "with a join, group columns must be dimension columns");
-    for (int a = 0; a < p->naggs; ++a)
+    for (int a = 0; a < p->naggs; ++a) {
+        if (p->aggs[a].fn == TQP_MIN || p->aggs[a].fn == TQP_MAX)
+            return fail(TQP_ERR_UNSUPPORTED, "MIN/MAX are not supported with a join");
         if (p->aggs[a].fn != TQP_COUNT && !expr_uses_only(p->aggs[a].expr, 0, nf))
             return fail(TQP_ERR_UNSUPPORTED, "with a join, aggregate expressions must use fact columns only");
+    }
     if (p->has_sum && !expr_uses_only(p->sum_expr, 0, nf))
         return fail(TQP_ERR_UNSUPPORTED, "with a join, the sum expression must use fact columns only");
     const tqp_dim* pd = p->prepared;

@@ -202,3 +202,45 @@ def test_few_groups_dense_ids(ctx, case):
     vc = len(cols) - 1
     check(ctx, cols, [(vc, "gt", -10**11)], gc, [("sum", [("col", vc)]), ("count", None), ("avg", [("col", vc)])],
           capacity=16)
+
+
+# ---- MIN / MAX (few groups: the direct kernel) -----------------------------------
+
+
+def test_min_max_dense_groups(ctx):
+    """MIN/MAX next to COUNT on the six-group shape (dense slot ids), with an
+    expression argument."""
+    cols = q1_cols(300_007, 91)
+    aggs = [("min", [("col", 4)]), ("max", [("col", 4)]), ("count", None),
+            ("max", [("col", 3), ("col", 5), "mul"])]
+    check(ctx, cols, [(0, "le", 2450)], [1, 2], aggs, capacity=64)
+
+
+def test_min_max_sparse_keys_and_extremes(ctx):
+    """Keys too sparse for dense ids (warp key lists, flushed when full) and
+    int64 extremes, whose order-preserving codes are the zero start."""
+    rng = np.random.default_rng(93)
+    n = 250_001
+    kk = (rng.integers(0, 20, n) * 3 - 7).astype(np.int32)
+    v = rng.integers(-10**18, 10**18, n).astype(np.int64)
+    v[::997] = np.iinfo(np.int64).min
+    v[5::991] = np.iinfo(np.int64).max
+    check(ctx, [kk, v], [], [0], [("min", [("col", 1)]), ("max", [("col", 1)]), ("count", None)], capacity=32)
+
+
+def test_min_max_with_sum_avg_and_ungrouped(ctx):
+    """MIN and SUM of the same expression are separate accumulators (AVG shares
+    the SUM); the ungrouped form over rows and over no rows (0, NaN flag)."""
+    cols = q1_cols(120_001, 95)
+    aggs = [("sum", [("col", 4)]), ("min", [("col", 4)]), ("avg", [("col", 4)]), ("max", [("col", 0)])]
+    check(ctx, cols, [(0, "le", 2450)], [1], aggs, capacity=8)
+    check(ctx, cols, [(0, "le", 2450)], [], aggs, capacity=1)
+    check(ctx, cols, [(0, "gt", 99_999)], [], aggs, capacity=1)
+
+
+def test_min_max_unsupported_shapes(ctx):
+    import paper_2203_01877_gb300 as tqp
+    cols = q1_cols(10_000, 97)
+    with pytest.raises(tqp.TqpError) as e:  # many groups: not the direct kernel
+        gpu_groupby(ctx, cols, [], [1, 2], [("min", [("col", 4)])], capacity=4096)
+    assert e.value.status == tqp.ERR_UNSUPPORTED

@@ -102,6 +102,24 @@ def test_few_groups_topk(ctx, k):
              topk_agg=1, max_groups=16, capacity_groups=k)
 
 
+def test_scan_plan_min_max(ctx):
+    run_both(ctx, fact=q1(150_001, 71), preds=[(0, "le", 2450)], group_cols=[1, 2],
+             aggs=[("min", [("col", 3)]), ("max", [("col", 4)]), ("count", None)], capacity_groups=64)
+
+
+def test_min_max_unsupported_in_plans(ctx):
+    import paper_2203_01877_gb300 as tqp
+    fact, dim = join_case(2_000, 50, 20_000, 73)
+    with pytest.raises(tqp.TqpError) as e:  # with a join
+        gpu_plan(ctx, fact=fact, dim=dim, fact_fk=0, dim_key=0, group_cols=[3], aggs=[("max", [("col", 1)])],
+                 capacity_groups=64)
+    assert e.value.status == tqp.ERR_UNSUPPORTED
+    with pytest.raises(tqp.TqpError) as e:  # as the top-k order
+        gpu_plan(ctx, fact=q1(5_000, 74), group_cols=[1], aggs=[("min", [("col", 4)])], topk=2, topk_agg=0,
+                 max_groups=8)
+    assert e.value.status == tqp.ERR_UNSUPPORTED
+
+
 @pytest.mark.parametrize("topk", [0, 1, 100, 1000])
 def test_join_group_topk(ctx, topk):
     fact, dim = join_case(30_000, 3_000, 1_200_000, 7)

@@ -73,7 +73,7 @@ class Plan(C.Structure):
     _fields_ = [("nfact", C.c_int64), ("fact", C.POINTER(Col)), ("nfact_cols", C.c_int32), ("pad0", C.c_int32),
                 ("preds", C.POINTER(Pred)), ("npreds", C.c_int32), ("pad1", C.c_int32),
                 ("ndim", C.c_int64), ("dim", C.POINTER(Col)), ("ndim_cols", C.c_int32),
-                ("fact_fk", C.c_int32), ("dim_key", C.c_int32), ("pad2", C.c_int32),
+                ("fact_fk", C.c_int32), ("dim_key", C.c_int32), ("join_kind", C.c_int32),
                 ("group_cols", C.POINTER(C.c_int32)), ("ngc", C.c_int32), ("pad3", C.c_int32),
                 ("aggs", C.POINTER(Agg)), ("naggs", C.c_int32), ("pad4", C.c_int32),
                 ("sum_expr", C.POINTER(Expr)),
@@ -137,9 +137,15 @@ def load_variant(so_path: str):
     return L
 
 
+_JOINS = {"inner": 0, "semi": 1, "anti": 2}
+
+
 def run_plan(fact, preds=(), dim=None, fact_fk=0, dim_key=0, group_cols=(), aggs=(), sum_expr=None,
-             topk=0, topk_agg=0, want_row_ids=True, want_pairs=False, cap_groups=None, _lib=None):
-    """Evaluate one plan with the C oracle; returns a dict of numpy results."""
+             topk=0, topk_agg=0, want_row_ids=True, want_pairs=False, cap_groups=None, join_kind="inner",
+             _lib=None):
+    """Evaluate one plan with the C oracle; returns a dict of numpy results.
+    join_kind: "inner" (every equal-key pair), "semi" / "anti" (each fact row
+    once if it has a / no equal-key dim row; fact columns only)."""
     L = _lib if _lib is not None else lib()
     fcols, fkeep = _cols(fact)
     nfact = len(fkeep[0]) if fkeep else 0
@@ -161,6 +167,7 @@ def run_plan(fact, preds=(), dim=None, fact_fk=0, dim_key=0, group_cols=(), aggs
     p.preds, p.npreds = pr, len(preds)
     p.ndim, p.dim, p.ndim_cols = (len(dkeep[0]) if dkeep else 0), dcols, len(dkeep)
     p.fact_fk, p.dim_key = int(fact_fk), int(dim_key)
+    p.join_kind = _JOINS[join_kind]
     p.group_cols, p.ngc = gc.ctypes.data_as(C.POINTER(C.c_int32)), len(gc)
     p.aggs, p.naggs = ag, len(aggs)
     p.sum_expr = C.pointer(se) if se is not None else None

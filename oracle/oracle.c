@@ -12,6 +12,9 @@
  *   equi-join         Sections 5.2-5.3 (Algorithms 1 and 2): the multiset of
  *                     index pairs (fact row, dim row) with equal keys (late
  *                     materialisation); emitted in (fact row, dim row) order.
+ *                     Left semi / anti join (a join kind the paper lists as
+ *                     supported, Section 5): each surviving fact row once,
+ *                     when it has at least one / no equal-key dim row.
  *   group-by          Section 5.4 (Algorithm 3): sort rows by the group-key
  *                     tuple, cut the sorted list into runs of equal keys
  *                     ("unique consecutive"), evaluate the aggregates per run;
@@ -170,6 +173,14 @@ int oracle_plan(const or_plan* p, or_out* o) {
         if (p->aggs[a].fn != OR_COUNT && !valid_expr(&p->aggs[a].expr, ncat)) return OR_ERR_INVALID;
     }
     if (p->sum_expr && !valid_expr(p->sum_expr, ncat)) return OR_ERR_INVALID;
+    if (joined && (p->join_kind < OR_JOIN_INNER || p->join_kind > OR_JOIN_ANTI)) return OR_ERR_INVALID;
+    if (joined && p->join_kind != OR_JOIN_INNER) {  /* no dim row to read: fact columns only */
+        for (int i = 0; i < p->ngc; ++i)
+            if (p->group_cols[i] >= p->nfact_cols) return OR_ERR_INVALID;
+        for (int a = 0; a < p->naggs; ++a)
+            if (p->aggs[a].fn != OR_COUNT && !valid_expr(&p->aggs[a].expr, p->nfact_cols)) return OR_ERR_INVALID;
+        if (p->sum_expr && !valid_expr(p->sum_expr, p->nfact_cols)) return OR_ERR_INVALID;
+    }
     int status = OR_OK;
 
     /* 1. filter: ascending surviving fact rows */
@@ -207,6 +218,16 @@ int oracle_plan(const or_plan* p, or_out* o) {
         qsort(sd, (size_t)p->ndim, sizeof(or_keyrow), cmp_keyrow);
         for (int64_t i = 0; i < ns; ++i) {
             int64_t k = col_value(&p->fact[p->fact_fk], surv[i]);
+            if (p->join_kind != OR_JOIN_INNER) {  /* semi / anti: the fact row once, or not at all */
+                const int64_t j0 = lower_bound(sd, p->ndim, k);
+                const int has = j0 < p->ndim && sd[j0].key == k;
+                if (has == (p->join_kind == OR_JOIN_SEMI)) {
+                    pairs[npairs].f = surv[i];  /* at most ns <= cap pairs: no growth */
+                    pairs[npairs].d = -1;
+                    ++npairs;
+                }
+                continue;
+            }
             for (int64_t j = lower_bound(sd, p->ndim, k); j < p->ndim && sd[j].key == k; ++j) {
                 if (npairs == cap) {
                     cap *= 2;

@@ -47,6 +47,12 @@ extern "C" {
 #define OR_X_SUB 3
 #define OR_X_MUL 4
 
+/* join kinds: every equal-key (fact, dim) pair; or each fact row once if it
+ * has a match (left semi) / has none (left anti), with dim row -1 */
+#define OR_JOIN_INNER 0
+#define OR_JOIN_SEMI 1
+#define OR_JOIN_ANTI 2
+
 /* aggregate functions */
 #define OR_SUM 0
 #define OR_COUNT 1
@@ -66,13 +72,14 @@ typedef struct { int32_t fn; int32_t pad; or_expr expr; } or_agg;
  *   filter(fact, preds) -> [equi-join fact.fact_fk = dim.dim_key]
  *   -> [ungrouped SUM(sum_expr)] -> [GROUP BY group_cols: aggs] -> [top-k].
  * Column indices in group_cols and in expressions address the concatenation
- * (fact columns, then dim columns).  Predicates address fact columns only.
+ * (fact columns, then dim columns).  Predicates address fact columns only;
+ * with a semi or anti join everything addresses fact columns only.
  */
 typedef struct {
     int64_t nfact; const or_col* fact; int32_t nfact_cols; int32_t pad0;
     const or_pred* preds; int32_t npreds; int32_t pad1;
     int64_t ndim; const or_col* dim; int32_t ndim_cols;   /* ndim_cols == 0: no join */
-    int32_t fact_fk; int32_t dim_key; int32_t pad2;
+    int32_t fact_fk; int32_t dim_key; int32_t join_kind;  /* OR_JOIN_INNER / _SEMI / _ANTI */
     const int32_t* group_cols; int32_t ngc; int32_t pad3;
     const or_agg* aggs; int32_t naggs; int32_t pad4;
     const or_expr* sum_expr;                              /* NULL: no ungrouped sum */

@@ -164,3 +164,58 @@ def test_empty_sides():
     for bk, pk in [(e, x), (x, e), (e, e)]:
         b, p = oracle.join_pairs(bk, pk)
         assert len(b) == 0 and len(p) == 0
+
+
+def test_semi_anti_vs_nested_loop_and_numpy():
+    """Left semi / anti join: each surviving fact row once when it has an
+    equal-key dim row / has none, in ascending row order, dim row -1.  Pinned
+    against a nested loop on a tiny case, numpy's isin on a larger one, the
+    partition identity semi + anti = surviving rows, and semi = the distinct
+    fact rows of the inner join."""
+    fk = np.array([4, 1, 9, 4, 7, 1, 3], np.int32)
+    val = np.array([10, 20, 30, 40, 50, 60, 70], np.int64)
+    dk = np.array([1, 4, 4, 5], np.int32)
+    want_semi = [f for f in range(len(fk)) if any(dk[d] == fk[f] for d in range(len(dk)))]
+    want_anti = [f for f in range(len(fk)) if f not in want_semi]
+    for kind, want in (("semi", want_semi), ("anti", want_anti)):
+        r = oracle.run_plan([fk, val], (), dim=[dk], fact_fk=0, dim_key=0, want_row_ids=False, want_pairs=True,
+                            join_kind=kind, sum_expr=[("col", 1)])
+        assert r["pair_fact"].tolist() == want
+        assert r["pair_dim"].tolist() == [-1] * len(want)
+        assert r["sum"] == int(val[want].sum())
+
+    rng = np.random.default_rng(41)
+    n = 30_000
+    fk = rng.integers(-50, 2_050, n).astype(np.int32)
+    g = rng.integers(0, 7, n).astype(np.int32)
+    v = rng.integers(-10**9, 10**9, n).astype(np.int64)
+    dk = rng.integers(0, 2_000, 5_000).astype(np.int32)  # duplicates and gaps
+    preds = [(2, "gt", -5 * 10**8)]
+    surv = np.flatnonzero(v > -5 * 10**8)
+    hit = np.isin(fk[surv], dk)
+    inner = oracle.run_plan([fk, g, v], preds, dim=[dk], fact_fk=0, dim_key=0, want_row_ids=False,
+                            want_pairs=True)
+    got = {}
+    for kind, rows in (("semi", surv[hit]), ("anti", surv[~hit])):
+        r = oracle.run_plan([fk, g, v], preds, dim=[dk], fact_fk=0, dim_key=0, group_cols=[1],
+                            aggs=[("sum", [("col", 2)]), ("count", None)], want_row_ids=False, want_pairs=True,
+                            join_kind=kind)
+        assert np.array_equal(r["pair_fact"], rows)
+        u, inv = np.unique(g[rows], return_inverse=True)
+        s = np.zeros(len(u), np.int64)
+        np.add.at(s, inv.reshape(-1), v[rows])
+        assert np.array_equal(r["keys"].reshape(-1), u)
+        assert np.array_equal(r["ivals"][:, 0], s)
+        assert np.array_equal(r["ivals"][:, 1], np.bincount(inv.reshape(-1)))
+        got[kind] = r["pair_fact"]
+    assert np.array_equal(np.sort(np.concatenate([got["semi"], got["anti"]])), surv)
+    assert np.array_equal(got["semi"], np.unique(inner["pair_fact"]))
+
+
+def test_semi_anti_reject_dim_columns():
+    fk = np.array([1, 2], np.int32)
+    dk = np.array([1], np.int32)
+    dp = np.array([9], np.int32)
+    with pytest.raises(oracle.OracleError):
+        oracle.run_plan([fk], (), dim=[dk, dp], fact_fk=0, dim_key=0, group_cols=[2], aggs=[("count", None)],
+                        join_kind="semi")

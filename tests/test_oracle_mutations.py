@@ -39,6 +39,9 @@ MUTANTS = {
                           "return -cmp_keys(x->key, y->key, g_ngc);"),
     "min_compares_as_max": ("(fn == OR_MIN ? v < *acc : v > *acc)", "(fn == OR_MIN ? v > *acc : v > *acc)"),
     "min_max_no_first_row_init": ("if (gcnt[g] == 1 || (fn == OR_MIN", "if (0 || (fn == OR_MIN"),
+    "anti_keeps_matches": ("if (has == (p->join_kind == OR_JOIN_SEMI))", "if (has == (p->join_kind != OR_JOIN_INNER))"),
+    "semi_ignores_first_dim_row": ("const int has = j0 < p->ndim && sd[j0].key == k;",
+                                   "const int has = j0 + 1 < p->ndim && sd[j0 + 1].key == k;"),
     "sum_skips_last_row": ("for (int64_t i = 0; i < npairs; ++i) {\n            int64_t v;",
                            "for (int64_t i = 0; i + 1 < npairs; ++i) {\n            int64_t v;"),
 }
@@ -61,6 +64,7 @@ PINS = [
     tj.test_hand_worked_example,
     tj.test_cardinality_identity_and_paper_algorithms,
     tj.test_join_group_topk_invariants,
+    tj.test_semi_anti_vs_nested_loop_and_numpy,
 ]
 
 

@@ -15,9 +15,7 @@ A plan is given as plain Python data:
 * expressions: postfix token lists -- ``("col", i)``, ``("const", v)``,
   ``"add"``, ``"sub"``, ``"mul"``; column ``i`` addresses fact columns first,
   then dim columns.
-* ``aggs``: ``(fn, expr)`` with fn in ``sum count avg min max`` (MIN/MAX: the
-  oracle's definition for the library's next aggregates; the library has no
-  MIN/MAX yet).
+* ``aggs``: ``(fn, expr)`` with fn in ``sum count avg min max``.
 """
 from __future__ import annotations
 

@@ -1063,7 +1063,7 @@ static tqp_status batch_launch(tqp_batch* b, cudaStream_t st) {
 // Launch shape of the scan of one body kind: the largest stage of its jobs.
 template <class Body>
 static tqp_status scan_shape(tqp_batch* b, int k) {
-    static bool attr[kMaxDevices] = {};
+    static SmemFlags attr;
     tqp_ctx* ctx = b->ctx;
     if (b->scan[k].empty()) return TQP_OK;
     TQP_TRY(allow_smem(ctx, reinterpret_cast<const void*>(k_b_scan<Body>), attr));
@@ -1082,7 +1082,7 @@ static tqp_status scan_shape(tqp_batch* b, int k) {
 // Lower, lay out and upload every batched job (no launch).
 static tqp_status batch_prepare(tqp_ctx* ctx, const tqp_plan* plans, const tqp_result* res, int32_t n, tqp_batch* b,
                                 cudaStream_t st) {
-    static bool attr_fin[kMaxDevices] = {}, attr_dir[kMaxDevices] = {};
+    static SmemFlags attr_fin, attr_dir;
     TQP_TRY(allow_smem(ctx, reinterpret_cast<const void*>(k_b_finalize), attr_fin));
     TQP_TRY(allow_smem(ctx, reinterpret_cast<const void*>(k_b_gdirect), attr_dir));
     TQP_TRY(lower_batch(b, plans, res, n));

@@ -124,6 +124,27 @@ tqp_status check_device_cols(const tqp_table* t, const std::vector<int>& cols, c
     return TQP_OK;
 }
 
+// Columns `cols` of t are read by the GPU in place (at passing rows only):
+// device, managed or page-locked host memory that the device can address.
+// Anything else (pageable host memory, a foreign pointer) is rejected here,
+// before any launch could dereference it.
+tqp_status check_visible_cols(const tqp_table* t, const std::vector<int>& cols, const char* what) {
+    for (int c : cols) {
+        if (c < 0 || c >= t->num_cols || !t->cols[c].data) continue;
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, t->cols[c].data) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(TQP_ERR_INVALID_ARG, "%s: column %d is not CUDA-visible memory", what, c);
+        }
+        if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) continue;
+        if (a.type == cudaMemoryTypeHost && a.devicePointer != nullptr) continue;
+        return fail(TQP_ERR_INVALID_ARG,
+                    "%s: column %d is neither device memory nor page-locked host memory the GPU can address", what,
+                    c);
+    }
+    return TQP_OK;
+}
+
 tqp_status lower_preds(const tqp_table* t, const tqp_pred* preds, int32_t npreds, Cond* out, int* ncond) {
     if (npreds < 0 || npreds > TQP_MAX_PREDS)
         return fail(TQP_ERR_INVALID_ARG, "npreds %d outside [0, %d]", npreds, TQP_MAX_PREDS);
@@ -416,13 +437,13 @@ tqp_status set_device_i64(long long* d_ptr, long long value, cudaStream_t stream
     return TQP_OK;
 }
 
-tqp_status allow_smem(const tqp_ctx* ctx, const void* kernel, bool* done_per_device) {
-    if (ctx->device < kMaxDevices && done_per_device[ctx->device]) return TQP_OK;
+tqp_status allow_smem(const tqp_ctx* ctx, const void* kernel, SmemFlags& flags) {
+    if (ctx->device < kMaxDevices && flags.done[ctx->device].load(std::memory_order_acquire)) return TQP_OK;
     cudaFuncAttributes fa;
     TQP_CUDA(cudaFuncGetAttributes(&fa, kernel));
     const int dyn = ctx->smem_optin - static_cast<int>(fa.sharedSizeBytes);
     TQP_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
-    if (ctx->device < kMaxDevices) done_per_device[ctx->device] = true;
+    if (ctx->device < kMaxDevices) flags.done[ctx->device].store(true, std::memory_order_release);
     return TQP_OK;
 }
 

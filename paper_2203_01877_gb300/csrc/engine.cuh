@@ -410,6 +410,10 @@ __device__ __forceinline__ int64_t eval_expr(const ScanGeom& G, const TileView& 
     return s0;
 }
 
+// Poll limit of the producer's final wait for its own bulk copies (with the
+// back-off of mbar_wait, seconds): a CTA never exits with a copy in flight.
+constexpr long long kDrainPolls = 1LL << 24;
+
 // Shared-memory header of every engine CTA.
 struct EngineHeader {
     uint64_t full[kMaxStages];
@@ -472,11 +476,16 @@ __device__ __forceinline__ void run_chunk(const ScanGeom& G, const EngineCtl& ct
             }
             // Drain: no bulk copy may still be landing when the chunk (or the
             // CTA) ends, even if a consumer gave up waiting.  Phases the
-            // consumers already observed test as complete at once.
+            // consumers already observed test as complete at once.  The
+            // copies read valid global memory and always complete, so this
+            // wait has its own generous limit, independent of (and never
+            // shorter than) the context's wait limit, which may be tiny.
             const long long issued = t1 - t0;
+            const long long drain_cap = ctl.wait_cap > kDrainPolls ? ctl.wait_cap : kDrainPolls;
             for (long long j = (issued > G.nstages ? issued - G.nstages : 0); j < issued; ++j) {
                 const long long pos = it - issued + j;
-                mbar_wait(&h->full[pos % G.nstages], static_cast<uint32_t>((pos / G.nstages) & 1), ctl.wait_cap);
+                if (!mbar_wait(&h->full[pos % G.nstages], static_cast<uint32_t>((pos / G.nstages) & 1), drain_cap))
+                    latch_error(ctl.err, TQP_ERR_TIMEOUT);
             }
         } else {
             it += t1 - t0;
@@ -487,9 +496,14 @@ __device__ __forceinline__ void run_chunk(const ScanGeom& G, const EngineCtl& ct
         for (long long t = t0; t < t1; ++t, ++it) {
             const int s = static_cast<int>(it % G.nstages);
             const uint32_t ph = static_cast<uint32_t>((it / G.nstages) & 1);
-            if (!failed && !mbar_wait(&h->full[s], ph, ctl.wait_cap)) {
-                latch_error(ctl.err, TQP_ERR_TIMEOUT);
-                failed = true;
+            if (!failed) {
+                // warp-uniform: the bodies use full-warp collectives, so a
+                // warp processes a tile with all lanes or skips it with all
+                const bool ok = mbar_wait(&h->full[s], ph, ctl.wait_cap);
+                if (!__all_sync(0xffffffffu, ok)) {
+                    if (lane == 0) latch_error(ctl.err, TQP_ERR_TIMEOUT);
+                    failed = true;
+                }
             }
             if (!failed) {
                 TileView v;

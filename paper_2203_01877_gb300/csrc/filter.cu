@@ -81,13 +81,18 @@ static tqp_status plan_filter(const tqp_ctx* ctx, const tqp_table* t, const tqp_
     std::vector<int> u = staged;
     std::sort(u.begin(), u.end());
     u.erase(std::unique(u.begin(), u.end()), u.end());
-    TQP_TRY(check_device_cols(t, u, "tqp_filter"));  // the rest are read at passing rows only
+    TQP_TRY(check_device_cols(t, u, "tqp_filter"));
+    if (A->has_sum) {  // the rest are read in place at passing rows only
+        std::vector<int> lazy;
+        expr_cols(A->sum, lazy);
+        TQP_TRY(check_visible_cols(t, lazy, "tqp_filter"));
+    }
     int bpr = 0;
     for (int c : u) bpr += t->cols[c].type == TQP_I64 ? 8 : (t->cols[c].type == TQP_I32 ? 4 : 1);
     const tqp_tuning tu = force ? *force : default_tuning(ctx, bpr, FilterBody::kSmemBytes + args_bytes<FilterArgs>());
     TQP_TRY(make_geom(ctx, t, staged, tu, FilterBody::kSmemBytes + args_bytes<FilterArgs>(), &A->G, smem));
     lower_fast(A->cond, A->ncond, A->G, A->cf, &A->fast);
-    static bool attr_done[kMaxDevices] = {};
+    static SmemFlags attr_done;
     TQP_TRY(allow_smem(ctx, reinterpret_cast<const void*>(k_filter), attr_done));
     const int g = engine_grid(ctx, reinterpret_cast<const void*>(k_filter), *smem, A->G.ntiles, tu.ctas_per_sm);
     A->ctl.chunk_tiles = (A->G.ntiles + g - 1) / g;

@@ -197,7 +197,7 @@ tqp_status group_table_init(GroupSpec* S, void* mem, long long cap, long long ma
 tqp_status group_finalize(tqp_ctx* ctx, const GroupSpec& S, const GroupOut& O, cudaStream_t stream) {
     if (S.cap <= kSmallCap) {
         const size_t smem = static_cast<size_t>(2 * kSmallCap) * (8 + 4);
-        static bool attr_done[kMaxDevices] = {};
+        static SmemFlags attr_done;
         TQP_TRY(allow_smem(ctx, reinterpret_cast<const void*>(k_groupby_finalize_small), attr_done));
         k_groupby_finalize_small<<<1, kFinThreads, smem, stream>>>(S, O);
         TQP_CUDA(cudaGetLastError());
@@ -426,15 +426,9 @@ tqp_status launch_groupby(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* pred
     lower_fast(A.cond, A.ncond, A.G, A.cf, &A.fast);
     lower_group_fast(&A);
 
-    const long long cap = group_table_cap(max_groups);
-    void* tab = arena_alloc(ctx, group_table_bytes(cap, A.S.nacc));
-    unsigned long long* ticket = static_cast<unsigned long long*>(arena_alloc(ctx, 256));
-    if (!tab || !ticket) return arena_oom(ctx, group_table_bytes(cap, A.S.nacc));
-    GroupOut O{d_keys, d_ivals, d_fvals, capacity_groups, d_num_groups, ctx->d_err};
     GroupDirectArgs D;
     const bool direct = lower_group_direct(t, A, max_groups, &D);
-    TQP_TRY(group_table_init(&A.S, tab, cap, max_groups, stream, !direct));
-
+    // shapes that are rejected anyway are rejected before any scratch or device work
     if (A.S.minmax) {  // MIN/MAX: the direct kernel only, and not as the top-k order
         if (!direct)
             return fail(TQP_ERR_UNSUPPORTED, "MIN/MAX need at most %lld groups, at most %d accumulators besides COUNT "
@@ -443,6 +437,12 @@ tqp_status launch_groupby(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* pred
             (aggs[topk_agg].fn == TQP_MIN || aggs[topk_agg].fn == TQP_MAX))
             return fail(TQP_ERR_UNSUPPORTED, "top-k by a MIN/MAX aggregate is not supported");
     }
+    const long long cap = group_table_cap(max_groups);
+    void* tab = arena_alloc(ctx, group_table_bytes(cap, A.S.nacc));
+    unsigned long long* ticket = static_cast<unsigned long long*>(arena_alloc(ctx, 256));
+    if (!tab || !ticket) return arena_oom(ctx, group_table_bytes(cap, A.S.nacc));
+    GroupOut O{d_keys, d_ivals, d_fvals, capacity_groups, d_num_groups, ctx->d_err};
+    TQP_TRY(group_table_init(&A.S, tab, cap, max_groups, stream, !direct));
     if (direct) {
         // two launches: the range pass (which also clears the table), then the
         // aggregation, whose last CTA finalizes the table unless top-k follows
@@ -450,7 +450,7 @@ tqp_status launch_groupby(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* pred
         D.err = ctx->d_err;
         D.O = O;
         D.fin = topk > 0 ? 0 : 1;
-        static bool attr_done[kMaxDevices] = {}, attr_mm[kMaxDevices] = {};
+        static SmemFlags attr_done, attr_mm;
         const void* kern = A.S.minmax ? reinterpret_cast<const void*>(k_groupby_direct_mm)
                                       : reinterpret_cast<const void*>(k_groupby_direct);
         TQP_TRY(allow_smem(ctx, kern, A.S.minmax ? attr_mm : attr_done));
@@ -486,7 +486,7 @@ tqp_status launch_groupby(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* pred
         if (topk > 0) return group_topk(ctx, A.S, O, topk, topk_agg, d_total_groups, stream);
         return TQP_OK;
     } else if (t->num_rows > 0) {
-        static bool attr_done[kMaxDevices] = {};
+        static SmemFlags attr_done;
         TQP_TRY(allow_smem(ctx, reinterpret_cast<const void*>(k_groupby), attr_done));
         const int g = engine_grid(ctx, reinterpret_cast<const void*>(k_groupby), smem, A.G.ntiles, tu.ctas_per_sm);
         A.ctl.chunk_tiles = (A.G.ntiles + g - 1) / g;

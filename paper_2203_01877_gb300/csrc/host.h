@@ -4,6 +4,7 @@
 #pragma once
 
 #include <algorithm>
+#include <atomic>
 #include <cstdarg>
 #include <cstddef>
 #include <cstdint>
@@ -109,6 +110,8 @@ struct DeviceGuard {
 tqp_status check_ctx(const tqp_ctx* ctx);
 tqp_status check_table(const tqp_table* t, const char* what);
 tqp_status check_device_cols(const tqp_table* t, const std::vector<int>& cols, const char* what);
+// Columns read in place at passing rows: device, managed or mapped page-locked host memory.
+tqp_status check_visible_cols(const tqp_table* t, const std::vector<int>& cols, const char* what);
 
 // Lower predicates to range conditions on `t`'s columns.
 tqp_status lower_preds(const tqp_table* t, const tqp_pred* preds, int32_t npreds, Cond* out, int* ncond);
@@ -158,13 +161,19 @@ int rows_class(long long n);
 // Persistent grid size for an engine kernel.
 int engine_grid(const tqp_ctx* ctx, const void* kernel, size_t smem, int64_t ntiles, int ctas_per_sm);
 
+constexpr int kMaxDevices = 64;
+// Once-per-device flags of allow_smem: any host thread (a server's
+// dispatcher, callers on other contexts, context-free callers) may reach it,
+// so the flags are atomic.
+struct SmemFlags {
+    std::atomic<bool> done[kMaxDevices];
+};
 // Raise a kernel's dynamic shared-memory limit once per device.
-tqp_status allow_smem(const tqp_ctx* ctx, const void* kernel, bool* done_per_device);
+tqp_status allow_smem(const tqp_ctx* ctx, const void* kernel, SmemFlags& flags);
 
 // Stream-ordered store of a host value into device memory (a one-thread
 // kernel: unlike a pageable memcpy it can be captured in a CUDA graph).
 tqp_status set_device_i64(long long* d_ptr, long long value, cudaStream_t stream);
-constexpr int kMaxDevices = 64;
 
 // One-shot batched run of n plans in ctx's per-call scratch on `stream` (the
 // body of tqp_run_plans; the server calls it with a slot's sub-context).

@@ -207,18 +207,23 @@ struct ProbeBody {
     const ProbeArgs& A;
     unsigned long long* wtot;     // [2][warps]
     unsigned long long* excl_sm;
+    int* skipped_sm;              // some consumer warp of this CTA skipped a tile (a wait gave up)
     unsigned long long chunk_pairs = 0;  // lane 0
     unsigned long long my_pairs = 0;     // lane 0
+    long long tiles_seen = 0;            // tiles of the current chunk this warp processed
 
     __device__ ProbeBody(const ProbeArgs& a, unsigned char* sm) : A(a) {
         wtot = reinterpret_cast<unsigned long long*>(sm);
         excl_sm = wtot + 2 * kConsumerWarps;
+        skipped_sm = reinterpret_cast<int*>(excl_sm + 1);
+        if (threadIdx.x == 0) *skipped_sm = 0;  // ordered before use by the engine's first __syncthreads
     }
 
     // Four rows per lane: their home slots are loaded together, then each
     // row walks its probe sequence (rarely past the home slot at load factor
     // <= 1/2) and records its key's run for the second pass.
     __device__ void pass1(const ScanGeom& G, const TileView& v, int cw, int lane) {
+        ++tiles_seen;
         const int rw = G.T / kConsumerWarps;  // a multiple of 128
         const JoinHT& H = A.H;
         const unsigned long long mask = static_cast<unsigned long long>(H.cap - 1);
@@ -281,8 +286,12 @@ struct ProbeBody {
         if (lane == 0) {
             my_pairs += chunk_pairs;
             wtot[cw] = chunk_pairs;
+            // a skipped tile left its rows' runs unwritten: the second pass
+            // below must not read them (the call reports TQP_ERR_TIMEOUT)
+            if (tiles_seen != t1 - t0) *skipped_sm = 1;
         }
         chunk_pairs = 0;
+        tiles_seen = 0;
         named_sync(kBarConsumers, kConsumers);
         if (cw == 0) {
             unsigned long long c = lane < kConsumerWarps ? wtot[lane] : 0ULL;
@@ -292,6 +301,7 @@ struct ProbeBody {
             if (lane == 0) *excl_sm = ex;
         }
         named_sync(kBarConsumers, kConsumers);
+        if (*skipped_sm) return;  // CTA-uniform: every consumer warp reads it after the same barrier
         unsigned long long running = *excl_sm;
         const long long r_begin = t0 * G.T;  // a multiple of 1024: every lane's four rows start 32-byte aligned
         const long long r_end = (t1 * G.T < G.n) ? t1 * G.T : G.n;
@@ -381,7 +391,7 @@ tqp_status launch_hash_join(tqp_ctx* ctx, const tqp_table* build, int32_t build_
     const tqp_tuning tu = default_tuning(ctx, es, ProbeBody::kSmemBytes + args_bytes<ProbeArgs>());
     size_t smem = 0;
     TQP_TRY(make_geom(ctx, probe, std::vector<int>{probe_key}, tu, ProbeBody::kSmemBytes + args_bytes<ProbeArgs>(), &A.G, &smem));
-    static bool attr_done[kMaxDevices] = {};
+    static SmemFlags attr_done;
     TQP_TRY(allow_smem(ctx, reinterpret_cast<const void*>(k_join_probe), attr_done));
     const int g = engine_grid(ctx, reinterpret_cast<const void*>(k_join_probe), smem, A.G.ntiles, tu.ctas_per_sm);
     A.ctl.chunk_tiles = (A.G.ntiles + g - 1) / g;

@@ -326,7 +326,7 @@ static tqp_status run_join_plan(tqp_ctx* ctx, const tqp_plan* p, const tqp_resul
     A.d_sum = p->has_sum ? r->d_sum : nullptr;
     A.d_num_rows = (p->emit_row_ids && r->d_row_ids) ? nullptr : r->d_num_rows;
     if (F->num_rows > 0) {
-        static bool attr_done[kMaxDevices] = {};
+        static SmemFlags attr_done;
         TQP_TRY(allow_smem(ctx, reinterpret_cast<const void*>(k_plan_join), attr_done));
         const int g = engine_grid(ctx, reinterpret_cast<const void*>(k_plan_join), smem, A.G.ntiles, tu.ctas_per_sm);
         A.ctl.chunk_tiles = (A.G.ntiles + g - 1) / g;

@@ -190,3 +190,38 @@ def test_filter_host_staged_column_rejected(ctx):
     with pytest.raises(tqp.TqpError) as e:
         tqp.tqp_groupby_agg(ctx, T, [], [0], [("count", None)], keys, iv, None, 64, ng)
     assert e.value.status == tqp.ERR_INVALID_ARG
+
+
+def test_filter_pageable_projected_column_rejected(ctx):
+    """A projected column in pageable host memory (a raw pointer the GPU
+    cannot address, passed straight through the C ABI) is refused before any
+    launch, by tqp_filter and by tqp_filter_noalloc; the same call with the
+    column pinned runs."""
+    import torch
+    import paper_2203_01877_gb300 as tqp
+    n = 100_000
+    t = datagen.fact_table(n, seed=33, cols=["date", "price"])
+    d_date = torch.from_numpy(t["date"]).cuda()
+    pinned = torch.from_numpy(t["price"]).pin_memory()
+    raw = np.empty(n + 2, np.int64)  # pageable; pick a 16-byte aligned start
+    off = (-raw.ctypes.data % 16) // 8
+    pageable = raw[off:off + n]
+    pageable[:] = t["price"]
+    T = tqp.TableRef([d_date, pinned], host_ok=True)
+    T.carr[1].data = pageable.ctypes.data
+    cnt = torch.full((1,), -7, dtype=torch.int64, device="cuda")
+    s = torch.full((1,), -7, dtype=torch.int64, device="cuda")
+    expr = [("col", 1)]
+    with pytest.raises(tqp.TqpError) as e:
+        tqp.tqp_filter(ctx, T, [(0, "lt", 100)], expr, s, None, 0, cnt)
+    assert e.value.status == tqp.ERR_INVALID_ARG and "page-locked" in str(e.value)
+    with pytest.raises(tqp.TqpError) as e:
+        tqp.tqp_filter_noalloc(0, T, [(0, "lt", 100)], expr, s, None, 0, cnt)
+    assert e.value.status == tqp.ERR_INVALID_ARG
+    torch.cuda.synchronize()
+    assert int(cnt.item()) == -7 and int(s.item()) == -7  # nothing ran
+    T.carr[1].data = pinned.data_ptr()
+    tqp.tqp_filter(ctx, T, [(0, "lt", 100)], expr, s, None, 0, cnt)
+    assert ctx.status() == 0
+    want_ids, want_sum = oracle.filter_rows([t["date"], t["price"]], [(0, "lt", 100)], expr)
+    assert int(cnt.item()) == len(want_ids) and int(s.item()) == want_sum

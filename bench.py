@@ -139,8 +139,36 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-def oracle_rate(cols, min_seconds: float, rows_cap: int | None = None):
-    """Rows/s of the CPU oracle (single thread) on the same columns, paper protocol style."""
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (x86 /proc/cpuinfo, else lscpu, e.g. an Arm Neoverse core)."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith("model name"):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def oracle_rate(cols, min_seconds: float, rows_cap: int | None = None, threads: int = 1):
+    """Rows/s of the CPU oracle on the same columns (threads > 1: its row-range variant on that many
+    threads), paper protocol style: at most 10 runs, median of the later half."""
     import oracle
     if rows_cap is not None and rows_cap < len(cols[0]):
         cols = [c[:rows_cap] for c in cols]
@@ -149,7 +177,7 @@ def oracle_rate(cols, min_seconds: float, rows_cap: int | None = None):
     t_end = time.perf_counter() + min_seconds
     while len(times) < 3 or time.perf_counter() < t_end:
         t0 = time.perf_counter()
-        oracle.filter_rows(cols, PREDS, EXPR)
+        oracle.filter_rows(cols, PREDS, EXPR, threads=threads)
         times.append(time.perf_counter() - t0)
         if len(times) >= 10:
             break
@@ -162,17 +190,18 @@ def run_reference(args):
     if rank != 0:
         return 0
     cols = gen_host(0)
-    # calibrate on 2M rows, then size each step's sample so the whole run takes ~2 minutes
-    rate, _, _, _ = oracle_rate(cols, 0.0, rows_cap=2_000_000)
+    cores = host_cores()
+    # calibrate on 8M rows, then size each step's sample so the whole run takes ~2 minutes
+    rate, _, _, _ = oracle_rate(cols, 0.0, rows_cap=8_000_000, threads=cores)
     total_steps = max(1, args.steps + args.warmup)
     sample = int(max(100_000, min(N_ROWS, rate * 120.0 / total_steps)))
     import oracle
     sub = [c[:sample] for c in cols]
     for _ in range(args.warmup):
-        oracle.filter_rows(sub, PREDS, EXPR)
+        oracle.filter_rows(sub, PREDS, EXPR, threads=cores)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.filter_rows(sub, PREDS, EXPR)
+        oracle.filter_rows(sub, PREDS, EXPR, threads=cores)
     dt = time.perf_counter() - t0
     value = sample * args.steps / dt
     line = {
@@ -181,8 +210,10 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
         "data": "synthetic (seeded counter-based generators)",
         "config": {"workload": WORKLOAD, "rows": N_ROWS},
-        "cpu_baseline": {"value": value, "unit": "rows/s", "cores": 1, "kind": "oracle",
-                         "sample": f"first {sample} rows of the 60M-row workload per step"},
+        "cpu_baseline": {"value": value, "unit": "rows/s", "cores": cores, "kind": "oracle",
+                         "cpu_model": cpu_model(),
+                         "sample": f"first {sample} rows of the 60M-row workload per step, the oracle's row loop "
+                                   f"over {cores} contiguous row ranges on {cores} threads"},
         "e2e": {"value": value, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -313,8 +344,10 @@ def secondary_workloads(tqp, torch, dev, local, reps, cpu_seconds=0.0):
         "workload": "build 1.5M unique int32 keys (payload = 150K groups); probe 60M Zipf(0.5) int32 fk + int64 "
                     "value; GROUP BY payload SUM(value), COUNT; top-100 by SUM desc, key asc",
         "ms": ms, "probe_rows_per_s": npr / (ms / 1e3), "algorithmic_bytes": alg,
-        "achieved_gbs": alg / (ms / 1e3) / 1e9, "joined_rows": int(rj.item()), "groups": int(rtot.item())}
+        "achieved_gbs": alg / (ms / 1e3) / 1e9, "frac_of_measured_hbm": alg / (ms / 1e3) / 1e9 / measured_peaks()[0],
+        "joined_rows": int(rj.item()), "groups": int(rtot.item())}
     ctx.close()
+    out.update(hashed_join_workloads(tqp, torch, dev, local, reps))
     if cpu_seconds > 0:
         ns = 6_000_000
         spec = dict(fact=[pr["fk"][:ns], pr["value"][:ns]], dim=[dim["key"], dim["payload"]], fact_fk=0, dim_key=0,
@@ -325,6 +358,53 @@ def secondary_workloads(tqp, torch, dev, local, reps, cpu_seconds=0.0):
                                                     "kind": "oracle",
                                                     "sample": f"first {ns} probe rows with the full build side, "
                                                               f"{runs} runs"}
+    return out
+
+
+def hashed_join_workloads(tqp, torch, dev, local, reps):
+    """The join shapes of the dense-key lines over SPARSE build keys (1.5M unique int32 keys scattered over
+    [0, 2^31) and Zipf(0.5) probe keys over them), so the build side goes into the hashed open-addressing table
+    instead of a direct-mapped one."""
+    out = {}
+    nb, ngr, npr = 1_500_000, 150_000, 60_000_000
+    seed = datagen.DEFAULT_SEED + 2
+    dim = datagen.dim_table(nb, ngr, seed=seed, sparse=True)
+    pr = datagen.probe_table(npr, nb, seed=seed, sparse=True)
+    F = tqp.TableRef([torch.from_numpy(pr["fk"]).to(dev), torch.from_numpy(pr["value"]).to(dev)])
+    D = tqp.TableRef([torch.from_numpy(dim["key"]).to(dev), torch.from_numpy(dim["payload"]).to(dev)])
+    stream = torch.cuda.current_stream()
+    ctx = tqp.Context(local, 1 << 30)
+    ctx.set_autotune(True)
+    k = 100
+    z = lambda m: torch.zeros(m, dtype=torch.int64, device=dev)  # noqa: E731
+    rk, riv, rng_, rtot, rj = z(k), z(2 * k), z(1), z(1), z(1)
+    plan = tqp.make_plan(F, (), D, 0, 0, [3], [("sum", [("col", 1)]), ("count", None)], None, k, 0)
+    res = tqp.make_result(None, 0, None, None, rk, riv, None, k, rng_, rtot, rj)
+    ms = _time_launches(torch, lambda: tqp.tqp_run_plan(ctx, plan, res, stream), max(5, reps // 2), stream=stream)
+    ctx.check(stream)
+    alg = npr * 12 + nb * 8
+    peak = measured_peaks()[0]
+    out["join_group_top100_hashed"] = {
+        "workload": "build 1.5M unique int32 keys scattered over [0, 2^31) (hashed table; payload = 150K groups); "
+                    "probe 60M Zipf(0.5) int32 fk + int64 value; GROUP BY payload SUM(value), COUNT; top-100",
+        "ms": ms, "probe_rows_per_s": npr / (ms / 1e3), "algorithmic_bytes": alg,
+        "achieved_gbs": alg / (ms / 1e3) / 1e9, "frac_of_measured_hbm": alg / (ms / 1e3) / 1e9 / peak,
+        "joined_rows": int(rj.item()), "groups": int(rtot.item())}
+    bidx = torch.empty(npr, dtype=torch.int32, device=dev)
+    pidx = torch.empty(npr, dtype=torch.int32, device=dev)
+    pcnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    ms_pairs = _time_launches(torch, lambda: tqp.tqp_hash_join(ctx, D, 0, F, 0, bidx, pidx, npr, pcnt, stream),
+                              max(5, reps // 2), stream=stream)
+    ctx.check(stream)
+    npairs = int(pcnt.item())
+    alg_pairs = nb * 4 + npr * 4 + npairs * 8
+    out["hash_join_pairs_hashed"] = {
+        "workload": "build 1.5M unique int32 keys scattered over [0, 2^31) (hashed table), probe 60M Zipf(0.5) int32 "
+                    "keys; output (build, probe) int32 index pairs, probe index ascending",
+        "ms": ms_pairs, "probe_rows_per_s": npr / (ms_pairs / 1e3), "pairs": npairs, "algorithmic_bytes": alg_pairs,
+        "achieved_gbs": alg_pairs / (ms_pairs / 1e3) / 1e9,
+        "frac_of_measured_hbm": alg_pairs / (ms_pairs / 1e3) / 1e9 / peak}
+    ctx.close()
     return out
 
 
@@ -615,6 +695,28 @@ def serving_workload(tqp, torch, dev, local, seconds=10.0, rate=2000.0, sweep=(2
     }, g600
 
 
+def l2_red_case(args):
+    """The reduction-rate roofline of the joined aggregation: G reductions/s of random 8-byte L2 reductions
+    (tqp_measure_l2_red) over table sizes, reductions per row and occupancy; one JSON line per setting."""
+    import torch
+    import paper_2203_01877_gb300 as tqp
+    dev = torch.device("cuda:0")
+    st = torch.cuda.current_stream()
+    rows = args.rows
+    table = torch.zeros((96 << 20) // 8, dtype=torch.int64, device=dev)
+    for mb in (2.4, 24, 96):
+        words = int(mb * (1 << 20)) // 8
+        t = table[:words]
+        for adds in (1, 2):
+            for bps, thr in ((1, 288), (2, 256), (4, 256), (8, 256)):
+                fn = lambda: tqp.tqp_measure_l2_red(0, t, rows, adds, bps, thr, st)  # noqa: E731
+                ms = _time_launches(torch, fn, 5, stream=st)
+                print(json.dumps({"case": "l2red", "table_mb": mb, "adds_per_row": adds, "blocks_per_sm": bps,
+                                  "threads": thr, "rows": rows, "ms": ms,
+                                  "g_reds_per_s": rows * adds / (ms / 1e3) / 1e9}), flush=True)
+    return 0
+
+
 def profile_case(args):
     """One operator at a profiling size, for ncu: the first call autotunes, the next `--steps` calls run
     inside the NVTX range "tqp_profile" (capture them with --nvtx --nvtx-include "tqp_profile/")."""
@@ -644,17 +746,24 @@ def profile_case(args):
         fv = torch.zeros(320, dtype=torch.float64, device=dev)
         ng = torch.zeros(1, dtype=torch.int64, device=dev)
         fn = lambda: tqp.tqp_groupby_agg(ctx, T, [(0, "le", 2450)], [1, 2], aggs, keys, iv, fv, 64, ng, st)  # noqa
-    elif args.case == "join":
+    elif args.case in ("join", "join_hashed", "pairs", "pairs_hashed"):
         nb, ngr = 1_500_000, 150_000
-        dim = datagen.dim_table(nb, ngr, seed=datagen.DEFAULT_SEED + 2)
-        pr = datagen.probe_table(n, nb, seed=datagen.DEFAULT_SEED + 2)
+        sparse = args.case.endswith("_hashed")
+        dim = datagen.dim_table(nb, ngr, seed=datagen.DEFAULT_SEED + 2, sparse=sparse)
+        pr = datagen.probe_table(n, nb, seed=datagen.DEFAULT_SEED + 2, sparse=sparse)
         F = tqp.TableRef([torch.from_numpy(pr["fk"]).to(dev), torch.from_numpy(pr["value"]).to(dev)])
         D = tqp.TableRef([torch.from_numpy(dim["key"]).to(dev), torch.from_numpy(dim["payload"]).to(dev)])
         z = lambda m: torch.zeros(m, dtype=torch.int64, device=dev)  # noqa: E731
-        rk, riv, rng_, rtot, rj = z(100), z(200), z(1), z(1), z(1)
-        plan = tqp.make_plan(F, (), D, 0, 0, [3], [("sum", [("col", 1)]), ("count", None)], None, 100, 0)
-        res = tqp.make_result(None, 0, None, None, rk, riv, None, 100, rng_, rtot, rj)
-        fn = lambda: tqp.tqp_run_plan(ctx, plan, res, st)  # noqa: E731
+        if args.case.startswith("join"):
+            rk, riv, rng_, rtot, rj = z(100), z(200), z(1), z(1), z(1)
+            plan = tqp.make_plan(F, (), D, 0, 0, [3], [("sum", [("col", 1)]), ("count", None)], None, 100, 0)
+            res = tqp.make_result(None, 0, None, None, rk, riv, None, 100, rng_, rtot, rj)
+            fn = lambda: tqp.tqp_run_plan(ctx, plan, res, st)  # noqa: E731
+        else:
+            bidx = torch.empty(n, dtype=torch.int32, device=dev)
+            pidx = torch.empty(n, dtype=torch.int32, device=dev)
+            pcnt = z(1)
+            fn = lambda: tqp.tqp_hash_join(ctx, D, 0, F, 0, bidx, pidx, n, pcnt, st)  # noqa: E731
     else:  # the batched 512-plan mix
         plans, results, keep, meta = batched_plans(tqp, torch, dev)
         batch = tqp.tqp_batch_create(ctx, plans, results)
@@ -683,12 +792,15 @@ def main():
     ap.add_argument("--no-operators", action="store_true", help="skip the secondary workloads")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving workload")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
-    ap.add_argument("--case", choices=["filter", "groupby", "join", "batch"], default=None,
+    ap.add_argument("--case", choices=["filter", "groupby", "join", "join_hashed", "pairs", "pairs_hashed", "batch",
+                                       "l2red"], default=None,
                     help="profiling: run one operator (first call autotunes; --steps calls in NVTX range tqp_profile)")
     args = ap.parse_args()
     globals()["N_ROWS"] = args.rows
     if args.impl == "reference":
         return run_reference(args)
+    if args.case == "l2red":
+        return l2_red_case(args)
     if args.case:
         return profile_case(args)
 
@@ -791,9 +903,15 @@ def main():
         achieved = alg / (launch_ms / 1e3) / 1e9
         cpu = None
         if args.cpu_seconds > 0:
-            cpu_rate, cpu_rows, cpu_runs, _ = oracle_rate(host, args.cpu_seconds)
-            cpu = {"value": cpu_rate, "unit": "rows/s", "cores": 1, "kind": "oracle",
-                   "sample": f"full {cpu_rows}-row workload, {cpu_runs} runs, median of the later half"}
+            cores = host_cores()
+            cpu_rate, cpu_rows, cpu_runs, _ = oracle_rate(host, args.cpu_seconds, threads=cores)
+            one_rate, one_rows, one_runs, _ = oracle_rate(host, args.cpu_seconds, rows_cap=12_000_000)
+            cpu = {"value": cpu_rate, "unit": "rows/s", "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
+                   "sample": f"full {cpu_rows}-row workload, the oracle's row loop over {cores} contiguous row ranges "
+                             f"on {cores} threads, {cpu_runs} runs, median of the later half",
+                   "one_core": {"value": one_rate, "unit": "rows/s", "cores": 1,
+                                "sample": f"first {one_rows} rows, one thread, {one_runs} runs, median of the later "
+                                          "half"}}
         line = {
             "metric": "rows/s",
             "value": value,

@@ -185,19 +185,47 @@ def fact_table(n: int, seed: int = DEFAULT_SEED, cols=None, row0: int = 0) -> di
     return out
 
 
-def dim_table(nb: int, ngroups: int, seed: int = DEFAULT_SEED) -> dict:
-    """Dimension rows: unique keys 0..nb-1 and payload = pi(key) mod ngroups."""
-    key = np.arange(nb, dtype=np.int64)
-    payload = feistel_perm(seed ^ 0xD1A, nb, key) % ngroups
-    return {"key": key.astype(np.int32), "payload": payload.astype(np.int32)}
+SPARSE_MULT = 1_000_003  # odd: multiplication by it is a bijection modulo 2**31
 
 
-def probe_table(n: int, nb: int, seed: int = DEFAULT_SEED, zipf_s: float = 0.5) -> dict:
-    """Probe rows: fk = pi'(Zipf(s) rank) over the nb dimension keys; value i64 U[100,1e7]."""
+def key_values(idx: np.ndarray, nkeys: int, seed: int, sparse: bool) -> np.ndarray:
+    """The int32 join key of key index ``idx`` in ``[0, nkeys)``.
+
+    Dense keys are the indices themselves.  Sparse keys scatter the indices
+    over ``[0, 2**31)``: ``(pi(idx) * 1_000_003) mod 2**31`` with ``pi`` a seeded
+    bijection on ``[0, nkeys)``; distinct indices give distinct keys (the
+    multiplier is odd, so it permutes the residues modulo ``2**31``), and the
+    keys span far more than twice their number, so no table can be
+    direct-mapped over them."""
+    idx = np.asarray(idx, dtype=np.int64)
+    if not sparse:
+        return idx.astype(np.int32)
+    perm = feistel_perm(seed ^ 0x5BA55, nkeys, idx)
+    return ((perm * SPARSE_MULT) & ((1 << 31) - 1)).astype(np.int32)
+
+
+def dim_table(nb: int, ngroups: int, seed: int = DEFAULT_SEED, sparse: bool = False, dup: int = 1) -> dict:
+    """Dimension rows: row i has key index i // dup (``dup`` rows per key; the
+    last key may have fewer), its key from ``key_values`` (dense: 0..nkeys-1),
+    and payload = pi(i) mod ngroups with pi a seeded bijection on [0, nb)."""
+    rows = np.arange(nb, dtype=np.int64)
+    nkeys = (nb + dup - 1) // dup
+    key = key_values(rows // dup, nkeys, seed, sparse)
+    payload = feistel_perm(seed ^ 0xD1A, nb, rows) % ngroups
+    return {"key": key, "payload": payload.astype(np.int32)}
+
+
+def probe_table(n: int, nb: int, seed: int = DEFAULT_SEED, zipf_s: float = 0.5, sparse: bool = False) -> dict:
+    """Probe rows: fk = the key of key index pi'(Zipf(s) rank) over nb key
+    indices (``key_values``; dense: the index itself); value i64 U[100,1e7]."""
     ranks = zipf_ranks(seed, COL_ZIPF, n, nb, zipf_s)
-    fk = _chunked(n, lambda r0, c: feistel_perm(seed ^ 0x21FF, nb, ranks[r0:r0 + c]), np.int64)
+
+    def keys(r0, c):
+        return key_values(feistel_perm(seed ^ 0x21FF, nb, ranks[r0:r0 + c]), nb, seed, sparse)
+
+    fk = _chunked(n, keys, np.int32)
     value = uniform_int(seed, COL_VALUE, n, 100, 10_000_000, np.int64)
-    return {"fk": fk.astype(np.int32), "value": value}
+    return {"fk": fk, "value": value}
 
 
 def log_uniform_int(seed: int, col_id: int, n: int, lo: int, hi: int) -> np.ndarray:

@@ -445,6 +445,25 @@ TQP_API tqp_status tqp_server_drain(tqp_server* s, double timeout_s);
 /* Stop the dispatcher after the queued work and release the region. */
 TQP_API tqp_status tqp_server_destroy(tqp_server* s);
 
+/* ---- measurement --------------------------------------------------------- */
+
+/*
+ * tqp_measure_l2_red -- the reduction-rate roofline of the joined
+ * aggregation.  (The paper has no counterpart: a measurement entry point.)
+ * Launches blocks_per_sm x (number of SMs) blocks of `threads` threads on
+ * `stream`; row i (0 <= i < rows) picks a uniformly random key k in
+ * [0, table_words / adds_per_row) and adds 1 to d_table[k * adds_per_row]
+ * and i to each of the following adds_per_row - 1 words, with
+ * fire-and-forget 8-byte reductions (the accumulator updates of the joined
+ * aggregation).  d_table: caller-owned device memory of table_words uint64
+ * words (contents change).  Time the call with events on `stream`.
+ * Errors: TQP_ERR_INVALID_ARG (adds_per_row outside 1..8, table smaller
+ * than one entry, threads not a multiple of 32 in 32..1024, blocks_per_sm
+ * outside 1..32), TQP_ERR_CUDA.
+ */
+TQP_API tqp_status tqp_measure_l2_red(int device, unsigned long long* d_table, int64_t table_words, int64_t rows,
+                                      int32_t adds_per_row, int32_t blocks_per_sm, int32_t threads, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

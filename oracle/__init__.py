@@ -29,6 +29,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "liboracle.so")
 _SRC = os.path.join(_HERE, "oracle.c")
+_SRC_MT = os.path.join(_HERE, "oracle_mt.c")
 _HDR = os.path.join(_HERE, "oracle.h")
 _LOCK = threading.Lock()
 _LIB = None
@@ -43,10 +44,11 @@ MAX_EXPR = 8
 
 def build(force: bool = False) -> str:
     """Compile ``liboracle.so`` with gcc (plain C11, no fast-math)."""
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < max(os.path.getmtime(_SRC), os.path.getmtime(_HDR)):
+    newest = max(os.path.getmtime(f) for f in (_SRC, _SRC_MT, _HDR))
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < newest:
         tmp = _SO + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fno-fast-math", "-fPIC", "-shared",
-                               "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fno-fast-math", "-fPIC", "-shared", "-pthread",
+                               "-o", tmp, _SRC, _SRC_MT, "-lm"])
         os.replace(tmp, _SO)
     return _SO
 
@@ -94,6 +96,8 @@ def lib():
             _LIB = C.CDLL(build())
             _LIB.oracle_plan.argtypes = [C.POINTER(Plan), C.POINTER(Out)]
             _LIB.oracle_plan.restype = C.c_int
+            _LIB.oracle_filter_mt.argtypes = [C.POINTER(Plan), C.POINTER(Out), C.c_int]
+            _LIB.oracle_filter_mt.restype = C.c_int
     return _LIB
 
 
@@ -140,10 +144,15 @@ _JOINS = {"inner": 0, "semi": 1, "anti": 2}
 
 def run_plan(fact, preds=(), dim=None, fact_fk=0, dim_key=0, group_cols=(), aggs=(), sum_expr=None,
              topk=0, topk_agg=0, want_row_ids=True, want_pairs=False, cap_groups=None, join_kind="inner",
-             _lib=None):
+             threads=1, _lib=None):
     """Evaluate one plan with the C oracle; returns a dict of numpy results.
     join_kind: "inner" (every equal-key pair), "semi" / "anti" (each fact row
-    once if it has a / no equal-key dim row; fact columns only)."""
+    once if it has a / no equal-key dim row; fact columns only).
+    threads > 1 (filter plans only: no join, no grouping) evaluates row ranges
+    on that many threads with the same row loop (oracle_filter_mt) -- the
+    all-core CPU baseline; the result is identical."""
+    if threads > 1 and (dim is not None or len(group_cols) or len(aggs)):
+        raise ValueError("threads > 1 is for filter plans only")
     L = _lib if _lib is not None else lib()
     fcols, fkeep = _cols(fact)
     nfact = len(fkeep[0]) if fkeep else 0
@@ -188,7 +197,10 @@ def run_plan(fact, preds=(), dim=None, fact_fk=0, dim_key=0, group_cols=(), aggs
         o.row_ids, o.cap_rows = _ptr(row_ids, C.c_int32), cap_rows
         o.pair_fact, o.pair_dim, o.cap_pairs = _ptr(pf, C.c_int32), _ptr(pd, C.c_int32), cap_pairs
         o.keys, o.ivals, o.fvals, o.cap_groups = _ptr(keys, C.c_int64), _ptr(iv, C.c_int64), _ptr(fv, C.c_double), cap_groups
-        st = L.oracle_plan(C.byref(p), C.byref(o))
+        if threads > 1:
+            st = L.oracle_filter_mt(C.byref(p), C.byref(o), int(threads))
+        else:
+            st = L.oracle_plan(C.byref(p), C.byref(o))
         if st == ERR_CAPACITY:
             cap_rows = max(cap_rows, o.num_rows) if want_row_ids else 0
             cap_pairs = max(cap_pairs, o.num_pairs) if want_pairs else 0
@@ -225,9 +237,9 @@ class OracleError(RuntimeError):
 
 # Convenience wrappers with the operator-level shapes of the library calls.
 
-def filter_rows(fact, preds, sum_expr=None):
+def filter_rows(fact, preds, sum_expr=None, threads=1):
     """Row ids (ascending) of rows passing every predicate, and SUM(sum_expr)."""
-    r = run_plan(fact, preds, sum_expr=sum_expr, want_row_ids=True)
+    r = run_plan(fact, preds, sum_expr=sum_expr, want_row_ids=True, threads=threads)
     return r["row_ids"], r["sum"]
 
 

@@ -96,6 +96,11 @@ typedef struct {
 
 int oracle_plan(const or_plan* plan, or_out* out);
 
+/* The filter step (a plan without join or grouping) on `nthreads` threads:
+ * oracle_plan over contiguous row ranges, results joined in range order --
+ * identical to oracle_plan's (oracle_mt.c; timing of the CPU baseline). */
+int oracle_filter_mt(const or_plan* plan, or_out* out, int nthreads);
+
 #ifdef __cplusplus
 }
 #endif

@@ -117,6 +117,7 @@ _SIGS = {
     "tqp_server_poll": (C.c_int32, [_P, C.c_void_p, C.c_int32]),
     "tqp_server_drain": (C.c_int, [_P, C.c_double]),
     "tqp_server_destroy": (C.c_int, [_P]),
+    "tqp_measure_l2_red": (C.c_int, [C.c_int, _P, C.c_int64, C.c_int64, C.c_int32, C.c_int32, C.c_int32, _P]),
 }
 
 
@@ -514,3 +515,10 @@ def tqp_server_drain(server: Server, timeout_s: float = 60.0):
 
 def tqp_server_destroy(server: Server):
     server.close()
+
+
+def tqp_measure_l2_red(device: int, d_table, rows: int, adds_per_row: int = 2, blocks_per_sm: int = 2,
+                       threads: int = 256, stream=None):
+    """Random 8-byte L2 reductions into d_table (an int64 CUDA tensor): the joined aggregation's roofline."""
+    _check(lib().tqp_measure_l2_red(int(device), _ptr(d_table), d_table.numel(), int(rows), int(adds_per_row),
+                                    int(blocks_per_sm), int(threads), _stream(stream)))

@@ -215,13 +215,13 @@ __global__ void __launch_bounds__(kFlatThreads) k_b_direct(const BuildJob* B, co
 
 template <class Body, class Args>
 __device__ __forceinline__ void scan_chunk(const Args& a, unsigned char* body_smem, long long local, EngineHeader* h,
-                                           unsigned char* stages, long long& it, bool& failed, uint64_t policy,
+                                           unsigned char* stages, long long& it, bool& aborted, uint64_t policy,
                                            int warp, int lane) {
     Body body(a, body_smem);
     __syncthreads();
     const long long t0 = local * a.ctl.chunk_tiles;
     const long long t1 = (t0 + a.ctl.chunk_tiles < a.G.ntiles) ? t0 + a.ctl.chunk_tiles : a.G.ntiles;
-    run_chunk(a.G, a.ctl, body, local, t0, t1, h, stages, it, failed, policy, warp, lane);
+    run_chunk(a.G, a.ctl, body, local, t0, t1, h, stages, it, aborted, policy, warp, lane);
 }
 
 template <class Body> struct BodyArgs;
@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(kEngineThreads, Body::kMinBlocks) k_b_scan(con
     init_stage_ring(h, kBatchStages);
     __syncthreads();
     long long it = 0;
-    bool failed = false;
+    bool aborted = false;
     const uint64_t policy = l2_evict_first_policy();
     while (true) {
         if (threadIdx.x == 0) {
@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(kEngineThreads, Body::kMinBlocks) k_b_scan(con
         }
         __syncthreads();
         const long long local = chunk - sj->chunk_base;
-        scan_chunk<Body>(BodyArgs<Body>::of(*sj), body_smem, local, h, stages, it, failed, policy, warp, lane);
+        scan_chunk<Body>(BodyArgs<Body>::of(*sj), body_smem, local, h, stages, it, aborted, policy, warp, lane);
         __syncthreads();
     }
 }

@@ -419,6 +419,7 @@ struct EngineHeader {
     uint64_t full[kMaxStages];
     uint64_t empty[kMaxStages];
     long long chunk;
+    int abort;   // a wait of this CTA gave up: no more copies or tiles (sticky)
 };
 constexpr int kHeaderBytes = 128;
 static_assert(sizeof(EngineHeader) <= kHeaderBytes, "engine header too large");
@@ -433,34 +434,65 @@ struct EngineCtl {
     long long nchunks;
 };
 
+// Wait for phase `parity` of `bar` for at most `cap` polls, giving up early
+// once the CTA's abort flag is set: 1 = complete, 0 = timed out, -1 = aborted.
+__device__ __forceinline__ int mbar_wait_or_abort(uint64_t* bar, uint32_t parity, long long cap,
+                                                  const volatile int* abort) {
+    for (long long i = 0; i < cap; ++i) {
+        if (mbar_test_wait(bar, parity)) return 1;
+        if (*abort) return -1;
+        if (i >= 16) __nanosleep(i < 1024 ? 32 : 256);
+    }
+    return 0;
+}
+
 // Body interface (all consumer threads call each member):
 //   pass1(G, v, cw, lane)                  once per tile, reads the stage
 //   chunk_end(G, chunk, t0, t1, cw, lane)  after the chunk's last tile
 //   finish(G, cw, lane)                    after the CTA's last chunk
 // Body::kSmemBytes bytes of shared memory precede the stages.
 // One chunk [t0, t1) of tiles through the stage ring.  `it` (the pipeline
-// position) and `failed` persist across chunks; producer and consumers advance
-// `it` identically, so every stage's mbarrier phase parity stays consistent.
+// position) persists across chunks; producer and consumers advance it
+// identically, so every stage's mbarrier phase parity stays consistent.
+//
+// Bounded waits.  A wait that runs out (the context's wait limit) latches
+// TQP_ERR_TIMEOUT and sets the CTA's abort flag; every other wait of the CTA
+// gives up as soon as it sees the flag.  From then on the producer issues no
+// copy and no arrival, and consumers process no tile and release no stage
+// (a warp processes a tile with all lanes or not at all: the bodies use
+// full-warp collectives).  The ring's invariants hold throughout: a stage is
+// released only after its copy has landed, so the producer never starts a
+// second copy into a stage, and no barrier receives more arrivals than it
+// expects.  At the end of every chunk the producer waits -- with its own long
+// limit, abort or not -- for each copy it issued that may still be landing.
+// Bodies see the skipped tiles as tiles they were never given (chunk_end
+// still runs).
 template <class Body>
 __device__ __forceinline__ void run_chunk(const ScanGeom& G, const EngineCtl& ctl, Body& body, long long chunk,
                                           long long t0, long long t1, EngineHeader* h, unsigned char* stages,
-                                          long long& it, bool& failed, uint64_t stream_policy, int warp, int lane) {
+                                          long long& it, bool& aborted, uint64_t stream_policy, int warp, int lane) {
+    volatile int* abort_flag = &h->abort;
     if (warp == kConsumerWarps) {
         // ---------------- producer: stage every tile of the chunk ----------------
         if (lane == 0) {
+            uint32_t pend = 0;        // stages with a copy issued in this chunk
+            uint32_t pend_par = 0;    // their phase parities
             for (long long t = t0; t < t1; ++t, ++it) {
+                if (aborted) continue;
                 const int s = static_cast<int>(it % G.nstages);
                 const uint32_t ph = static_cast<uint32_t>((it / G.nstages) & 1);
-                if (!failed && !mbar_wait(&h->empty[s], ph ^ 1u, ctl.wait_cap)) {
-                    latch_error(ctl.err, TQP_ERR_TIMEOUT);
-                    failed = true;
+                const int w = mbar_wait_or_abort(&h->empty[s], ph ^ 1u, ctl.wait_cap, abort_flag);
+                if (w != 1) {
+                    if (w == 0) latch_error(ctl.err, TQP_ERR_TIMEOUT);
+                    *abort_flag = 1;
+                    aborted = true;
+                    continue;
                 }
                 const int64_t row0 = static_cast<int64_t>(t) * G.T;
                 const int rows = static_cast<int>(G.n - row0 < G.T ? G.n - row0 : G.T);
                 uint32_t total = 0;
-                if (!failed)
-                    for (int k = 0; k < G.nstaged; ++k)
-                        total += (static_cast<uint32_t>(rows) * esize_of(G.col[G.staged[k]].type)) & ~15u;
+                for (int k = 0; k < G.nstaged; ++k)
+                    total += (static_cast<uint32_t>(rows) * esize_of(G.col[G.staged[k]].type)) & ~15u;
                 unsigned char* dst = stages + static_cast<size_t>(s) * G.stage_bytes;
                 if (total == 0) {
                     mbar_arrive(&h->full[s]);
@@ -472,21 +504,17 @@ __device__ __forceinline__ void run_chunk(const ScanGeom& G, const EngineCtl& ct
                         const uint32_t bytes = (static_cast<uint32_t>(rows) * es) & ~15u;
                         if (bytes) bulk_g2s(dst + cr.soff, cr.ptr + row0 * es, bytes, &h->full[s], stream_policy);
                     }
+                    pend |= 1u << s;
+                    pend_par = (pend_par & ~(1u << s)) | (ph << s);
                 }
             }
-            // Drain: no bulk copy may still be landing when the chunk (or the
-            // CTA) ends, even if a consumer gave up waiting.  Phases the
-            // consumers already observed test as complete at once.  The
-            // copies read valid global memory and always complete, so this
-            // wait has its own generous limit, independent of (and never
-            // shorter than) the context's wait limit, which may be tiny.
-            const long long issued = t1 - t0;
+            // Drain: every copy of this chunk has landed before the chunk (or
+            // the CTA) ends.  Only the producer advances a full barrier, so
+            // the last issued phase of a stage is the one to wait for.
             const long long drain_cap = ctl.wait_cap > kDrainPolls ? ctl.wait_cap : kDrainPolls;
-            for (long long j = (issued > G.nstages ? issued - G.nstages : 0); j < issued; ++j) {
-                const long long pos = it - issued + j;
-                if (!mbar_wait(&h->full[pos % G.nstages], static_cast<uint32_t>((pos / G.nstages) & 1), drain_cap))
+            for (int s = 0; s < G.nstages; ++s)
+                if (((pend >> s) & 1u) && !mbar_wait(&h->full[s], (pend_par >> s) & 1u, drain_cap))
                     latch_error(ctl.err, TQP_ERR_TIMEOUT);
-            }
         } else {
             it += t1 - t0;
         }
@@ -494,26 +522,26 @@ __device__ __forceinline__ void run_chunk(const ScanGeom& G, const EngineCtl& ct
         // ---------------- consumers ----------------
         const int cw = warp;
         for (long long t = t0; t < t1; ++t, ++it) {
+            if (aborted) continue;
             const int s = static_cast<int>(it % G.nstages);
             const uint32_t ph = static_cast<uint32_t>((it / G.nstages) & 1);
-            if (!failed) {
-                // warp-uniform: the bodies use full-warp collectives, so a
-                // warp processes a tile with all lanes or skips it with all
-                const bool ok = mbar_wait(&h->full[s], ph, ctl.wait_cap);
-                if (!__all_sync(0xffffffffu, ok)) {
-                    if (lane == 0) latch_error(ctl.err, TQP_ERR_TIMEOUT);
-                    failed = true;
+            const int w = mbar_wait_or_abort(&h->full[s], ph, ctl.wait_cap, abort_flag);
+            if (!__all_sync(0xffffffffu, w == 1)) {
+                const bool timed_out = __any_sync(0xffffffffu, w == 0);
+                if (lane == 0) {
+                    if (timed_out) latch_error(ctl.err, TQP_ERR_TIMEOUT);
+                    *abort_flag = 1;
                 }
+                aborted = true;
+                continue;
             }
-            if (!failed) {
-                TileView v;
-                v.stage = stages + static_cast<size_t>(s) * G.stage_bytes;
-                v.tile = t;
-                v.row0 = static_cast<int64_t>(t) * G.T;
-                v.rows = static_cast<int>(G.n - v.row0 < G.T ? G.n - v.row0 : G.T);
-                v.full = v.rows == G.T;
-                body.pass1(G, v, cw, lane);
-            }
+            TileView v;
+            v.stage = stages + static_cast<size_t>(s) * G.stage_bytes;
+            v.tile = t;
+            v.row0 = static_cast<int64_t>(t) * G.T;
+            v.rows = static_cast<int>(G.n - v.row0 < G.T ? G.n - v.row0 : G.T);
+            v.full = v.rows == G.T;
+            body.pass1(G, v, cw, lane);
             __syncwarp();
             if (lane == 0) mbar_arrive(&h->empty[s]);
         }
@@ -524,6 +552,7 @@ __device__ __forceinline__ void run_chunk(const ScanGeom& G, const EngineCtl& ct
 // Initialise the stage ring's mbarriers (thread 0; callers __syncthreads after).
 __device__ __forceinline__ void init_stage_ring(EngineHeader* h, int nstages) {
     if (threadIdx.x == 0) {
+        h->abort = 0;
         for (int s = 0; s < nstages; ++s) {
             mbar_init(&h->full[s], 1);
             mbar_init(&h->empty[s], kConsumerWarps);
@@ -561,7 +590,7 @@ __device__ __forceinline__ void run_engine(const ScanGeom& G, const EngineCtl& c
     __syncthreads();
 
     long long it = 0;
-    bool failed = false;
+    bool aborted = false;
     const uint64_t stream_policy = l2_evict_first_policy();
     while (true) {
         if (threadIdx.x == 0) h->chunk = static_cast<long long>(atomicAdd(ctl.ticket, 1ULL));
@@ -571,7 +600,7 @@ __device__ __forceinline__ void run_engine(const ScanGeom& G, const EngineCtl& c
         if (chunk >= ctl.nchunks) break;
         const long long t0 = chunk * ctl.chunk_tiles;
         const long long t1 = (t0 + ctl.chunk_tiles < G.ntiles) ? t0 + ctl.chunk_tiles : G.ntiles;
-        run_chunk(G, ctl, body, chunk, t0, t1, h, stages, it, failed, stream_policy, warp, lane);
+        run_chunk(G, ctl, body, chunk, t0, t1, h, stages, it, aborted, stream_policy, warp, lane);
         __syncthreads();
     }
     if (warp != kConsumerWarps) body.finish(G, warp, lane);

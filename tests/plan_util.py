@@ -78,3 +78,34 @@ def compare(got, want, shape_spec):
         assert np.array_equal(got["keys"], want["keys"])
         assert np.array_equal(got["ivals"], want["ivals"])
         assert np.array_equal(got["fvals"].view(np.int64), want["fvals"].view(np.int64))
+
+
+_CACHE = {}
+
+
+def hashed_join_inputs(n_probe=60_000_000, n_build=1_500_000, n_groups=150_000, dup=1, seed=None):
+    """The join + group workload over SPARSE build keys (unique int32 keys scattered over [0, 2**31), so the
+    library must use its hashed table): build n_build rows (dup rows per key), payload = 150K groups, probe
+    n_probe Zipf(0.5) foreign keys over the build keys.  Cached per process (generation takes seconds)."""
+    import datagen
+    key = (n_probe, n_build, n_groups, dup, seed)
+    if key not in _CACHE:
+        s = datagen.DEFAULT_SEED + 2 if seed is None else seed
+        dim = datagen.dim_table(n_build, n_groups, seed=s, sparse=True, dup=dup)
+        pr = datagen.probe_table(n_probe, (n_build + dup - 1) // dup, seed=s, sparse=True)
+        _CACHE.clear()
+        _CACHE[key] = (dim, pr)
+    return _CACHE[key]
+
+
+def oracle_groups_sample(dim, pr, groups, aggs, group_col_payload=3):
+    """The oracle's per-group result for the payload groups in `groups` only: the dimension is restricted to the
+    rows of those groups, which leaves each of their aggregates unchanged (a group's joined rows all come from
+    its own dimension rows) and lets the oracle run over the full probe side in seconds."""
+    import numpy as np
+    import oracle
+    keep = np.isin(dim["payload"], np.asarray(groups))
+    sub = [dim["key"][keep], dim["payload"][keep]]
+    return oracle.run_plan(fact=[pr["fk"], pr["value"]], dim=sub, fact_fk=0, dim_key=0,
+                           group_cols=[group_col_payload], aggs=aggs, want_pairs=False, cap_groups=None,
+                           want_row_ids=False)

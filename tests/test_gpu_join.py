@@ -94,3 +94,41 @@ def test_zipf_probe_shape(ctx):
     pr = datagen.probe_table(n, nb, seed=4)
     k = check(ctx, dim["key"], pr["fk"])
     assert k == n
+
+
+def test_full_size_hashed_pairs(ctx):
+    """Sparse build keys force the hashed table: 1.5M unique int32 keys scattered over [0, 2^31), 60M Zipf(0.5)
+    probe keys.  Every probe row matches exactly one build row, so the canonical output is fixed at any size:
+    probe indices 0..n-1 in order, each with the build row of its key; the oracle checks a sample of a million
+    probe rows element by element."""
+    from tests.plan_util import hashed_join_inputs
+    dim, pr = hashed_join_inputs()
+    bk, pk = dim["key"], pr["fk"]
+    n = len(pk)
+    st, k, ob, op = gpu_join(ctx, bk, pk, capacity=n)
+    assert st == 0 and k == n
+    assert np.array_equal(op, np.arange(n, dtype=np.int32))
+    assert np.array_equal(bk[ob], pk)
+    sample = np.sort(np.random.default_rng(0).choice(n, 1_000_000, replace=False))
+    wb, wp = oracle.join_pairs(bk, pk[sample])
+    assert np.array_equal(wp, np.arange(len(sample)))
+    assert np.array_equal(ob[sample], wb)
+
+
+def test_hashed_pairs_duplicate_build_keys(ctx):
+    """Ten build rows per sparse key (1.5M build rows, 150K keys), 6M probe rows: 60M pairs.  Each probe row's
+    ten build rows appear in ascending order; the oracle checks a sample of probe rows element by element."""
+    from tests.plan_util import hashed_join_inputs
+    dim, pr = hashed_join_inputs(n_probe=6_000_000, dup=10, seed=78)
+    bk, pk = dim["key"], pr["fk"]
+    n = len(pk)
+    st, k, ob, op = gpu_join(ctx, bk, pk, capacity=10 * n)
+    assert st == 0 and k == 10 * n
+    assert np.array_equal(op, np.repeat(np.arange(n, dtype=np.int32), 10))
+    assert np.array_equal(bk[ob], pk[op])
+    runs = ob.reshape(n, 10)
+    assert bool((np.diff(runs, axis=1) > 0).all())
+    sample = np.sort(np.random.default_rng(1).choice(n, 200_000, replace=False))
+    wb, wp = oracle.join_pairs(bk, pk[sample])
+    assert np.array_equal(wp, np.repeat(np.arange(len(sample)), 10))
+    assert np.array_equal(runs[sample].ravel(), wb)

@@ -188,3 +188,35 @@ def test_full_size_join_group_topk(ctx):
     got = run_both(ctx, fact=[pr["fk"], pr["value"]], dim=[dim["key"], dim["payload"]], fact_fk=0, dim_key=0,
                    group_cols=[3], aggs=[("sum", [("col", 1)]), ("count", None)], topk=100, topk_agg=0)
     assert got["num_pairs"] == n and got["total_groups"] == ng
+
+
+HASHED_AGGS = [("sum", [("col", 1)]), ("count", None)]
+
+
+def test_full_size_hashed_join_group_topk(ctx):
+    """Sparse build keys force the hashed join table: build 1.5M unique int32 keys scattered over [0, 2^31),
+    probe 60M Zipf(0.5) foreign keys, 150K groups.  The full group table (keys ascending) and the top-100,
+    each element by element against the oracle."""
+    from tests.plan_util import hashed_join_inputs
+    dim, pr = hashed_join_inputs()
+    n = len(pr["fk"])
+    spec = dict(fact=[pr["fk"], pr["value"]], dim=[dim["key"], dim["payload"]], fact_fk=0, dim_key=0,
+                group_cols=[3], aggs=HASHED_AGGS)
+    got = run_both(ctx, capacity_groups=150_000, **spec)
+    assert got["num_pairs"] == n and got["total_groups"] == 150_000 and got["num_groups"] == 150_000
+    assert int(got["ivals"][:, 1].sum()) == n and int(got["ivals"][:, 0].sum()) == int(pr["value"].sum())
+    got = run_both(ctx, topk=100, topk_agg=0, **spec)
+    assert got["num_groups"] == 100
+
+
+def test_hashed_join_duplicate_build_keys(ctx):
+    """Ten build rows per sparse key (150K keys, each row its own payload group): every probe row joins ten
+    build rows, so each adds to up to ten groups; the full table and the top-100 against the oracle."""
+    from tests.plan_util import hashed_join_inputs
+    dim, pr = hashed_join_inputs(n_probe=2_000_000, dup=10, seed=77)
+    n = len(pr["fk"])
+    spec = dict(fact=[pr["fk"], pr["value"]], dim=[dim["key"], dim["payload"]], fact_fk=0, dim_key=0,
+                group_cols=[3], aggs=HASHED_AGGS)
+    got = run_both(ctx, capacity_groups=150_000, **spec)
+    assert got["num_pairs"] == 10 * n
+    run_both(ctx, topk=100, topk_agg=0, **spec)

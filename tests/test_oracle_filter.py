@@ -143,3 +143,23 @@ def test_invalid_plans_rejected():
         oracle.filter_rows([x], [], [("col", 5)])
     with pytest.raises(oracle.OracleError):
         oracle.filter_rows([x], [], [("col", 0), "add"])
+
+
+@pytest.mark.parametrize("n,threads", [(0, 4), (1, 8), (7, 16), (1000, 3), (250_001, 16), (250_001, 1)])
+def test_row_range_threads_give_the_single_thread_result(n, threads):
+    """The all-core timing variant (row ranges on threads, joined in order) equals one call."""
+    t = datagen.fact_table(n, seed=n + threads, cols=["date", "discount", "quantity", "price"])
+    cols = [t[c] for c in ("date", "discount", "quantity", "price")]
+    preds = [(0, "ge", 731), (0, "lt", 1096), (1, "between", 5, 7), (2, "lt", 24)]
+    expr = [("col", 3), ("col", 1), "mul"]
+    ids1, s1 = oracle.filter_rows(cols, preds, expr)
+    idsn, sn = oracle.filter_rows(cols, preds, expr, threads=threads)
+    assert np.array_equal(ids1, idsn) and s1 == sn
+    # ranges that each keep every row: ids are 0..n-1 in order
+    ids, s = oracle.filter_rows(cols, [], expr, threads=threads)
+    assert np.array_equal(ids, np.arange(n)) and s == int((t["price"] * t["discount"]).sum())
+
+
+def test_row_range_threads_reject_grouped_plans():
+    with pytest.raises(ValueError):
+        oracle.run_plan([np.zeros(4, np.int32)], group_cols=[0], aggs=[("count", None)], threads=4)

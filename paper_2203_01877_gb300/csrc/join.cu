@@ -130,12 +130,19 @@ __global__ void k_ht_insert(JoinHT H, const unsigned char* key_col, int key_type
 }
 
 // After the sort: run starts into the slots; the sorted values are the
-// build rows of each run in ascending order.
-__global__ void k_ht_runs(JoinHT H, const uint64_t* skey, long long n) {
+// build rows of each run in ascending order.  A run of one build row (a
+// unique key) stores that row itself, flagged kRunRow, so the probe writes
+// its pairs without loading it from the sorted rows.
+constexpr uint32_t kRunRow = 0x80000000u;
+
+__global__ void k_ht_runs(JoinHT H, const uint64_t* skey, const uint32_t* sval, long long n) {
     for (long long p = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; p < n;
          p += static_cast<long long>(gridDim.x) * blockDim.x) {
         const uint64_t s = skey[p];
-        if (p == 0 || skey[p - 1] != s) H.slots[s].z = static_cast<uint32_t>(p);
+        if (p == 0 || skey[p - 1] != s) {
+            const bool single = p + 1 == n || skey[p + 1] != s;
+            H.slots[s].z = single ? (sval[p] | kRunRow) : static_cast<uint32_t>(p);
+        }
     }
 }
 
@@ -180,7 +187,7 @@ tqp_status ht_build(tqp_ctx* ctx, const tqp_table* build, int32_t key_col, JoinH
     TQP_TRY(radix_sort_pairs(k0, v0, k1, v1, d_n, n, 0, (bits + 7) / 8 * 8, rs, stream, &in1));
     const uint64_t* sk = in1 ? k1 : k0;
     H->bidx = in1 ? v1 : v0;
-    k_ht_runs<<<iblocks, threads, 0, stream>>>(*H, sk, n);
+    k_ht_runs<<<iblocks, threads, 0, stream>>>(*H, sk, H->bidx, n);
     TQP_CUDA(cudaGetLastError());
     return TQP_OK;
 }
@@ -340,6 +347,14 @@ struct ProbeBody {
             unsigned long long pos = running + before + (incl - c);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
+                if (run[j].x & kRunRow) {  // a unique key: the run is the build row itself
+                    if (run[j].y && pos < static_cast<unsigned long long>(A.capacity)) {
+                        A.out_build[pos] = static_cast<int32_t>(run[j].x & ~kRunRow);
+                        A.out_probe[pos] = static_cast<int32_t>(r0 + j);
+                    }
+                    pos += run[j].y;
+                    continue;
+                }
                 for (uint32_t k = 0; k < run[j].y; ++k, ++pos) {
                     if (pos < static_cast<unsigned long long>(A.capacity)) {
                         A.out_build[pos] = static_cast<int32_t>(A.H.bidx[run[j].x + k]);

@@ -202,11 +202,25 @@ def test_full_size_hashed_join_group_topk(ctx):
     n = len(pr["fk"])
     spec = dict(fact=[pr["fk"], pr["value"]], dim=[dim["key"], dim["payload"]], fact_fk=0, dim_key=0,
                 group_cols=[3], aggs=HASHED_AGGS)
-    got = run_both(ctx, capacity_groups=150_000, **spec)
-    assert got["num_pairs"] == n and got["total_groups"] == 150_000 and got["num_groups"] == 150_000
-    assert int(got["ivals"][:, 1].sum()) == n and int(got["ivals"][:, 0].sum()) == int(pr["value"].sum())
-    got = run_both(ctx, topk=100, topk_agg=0, **spec)
-    assert got["num_groups"] == 100
+    got = gpu_plan(ctx, capacity_groups=150_000, **spec)
+    full = oracle.run_plan(want_pairs=False, cap_groups=None, want_row_ids=False, **spec)
+    compare(got, full, spec)
+    assert full["num_pairs"] == n and full["total_groups"] == 150_000 and full["num_groups"] == 150_000
+    assert int(full["ivals"][:, 1].sum()) == n and int(full["ivals"][:, 0].sum()) == int(pr["value"].sum())
+    # top-100: the oracle ranks the groups whose SUM reaches the 100th largest SUM of its own full table
+    # (every group that can be in the top 100, ties included); restricting the dimension to their rows
+    # leaves those groups' aggregates unchanged and lets the oracle run in seconds
+    got = gpu_plan(ctx, topk=100, topk_agg=0, **spec)
+    sums = full["ivals"][:, 0]
+    cut = np.partition(sums, len(sums) - 100)[len(sums) - 100]
+    cand = full["keys"][sums >= cut, 0]
+    keep = np.isin(dim["payload"], cand)
+    want = oracle.run_plan(fact=spec["fact"], dim=[dim["key"][keep], dim["payload"][keep]], fact_fk=0, dim_key=0,
+                           group_cols=[3], aggs=HASHED_AGGS, topk=100, topk_agg=0, want_pairs=False,
+                           cap_groups=None, want_row_ids=False)
+    assert got["status"] == 0 and got["num_groups"] == want["num_groups"] == 100
+    assert got["total_groups"] == 150_000
+    assert np.array_equal(got["keys"], want["keys"]) and np.array_equal(got["ivals"], want["ivals"])
 
 
 def test_hashed_join_duplicate_build_keys(ctx):

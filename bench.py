@@ -318,6 +318,12 @@ def secondary_workloads(tqp, torch, dev, local, reps, cpu_seconds=0.0):
 
     ms = _time_launches(torch, join, max(5, reps // 2))
     ctx.check(stream)
+    ctx.set_variant(1)  # the fused probe (L2 reductions), for comparison with the tuned choice
+    ms_fused = _time_launches(torch, join, max(5, reps // 2))
+    ctx.set_variant(0)  # the radix-partitioned aggregation
+    ms_part = _time_launches(torch, join, max(5, reps // 2))
+    ctx.set_variant(-1)
+    ctx.check(stream)
 
     # the same build and probe keys, the join materialised as (build, probe) index pairs
     pcap = npr
@@ -345,6 +351,7 @@ def secondary_workloads(tqp, torch, dev, local, reps, cpu_seconds=0.0):
                     "value; GROUP BY payload SUM(value), COUNT; top-100 by SUM desc, key asc",
         "ms": ms, "probe_rows_per_s": npr / (ms / 1e3), "algorithmic_bytes": alg,
         "achieved_gbs": alg / (ms / 1e3) / 1e9, "frac_of_measured_hbm": alg / (ms / 1e3) / 1e9 / measured_peaks()[0],
+        "ms_radix_partitioned": ms_part, "ms_fused_probe": ms_fused,
         "joined_rows": int(rj.item()), "groups": int(rtot.item())}
     ctx.close()
     out.update(hashed_join_workloads(tqp, torch, dev, local, reps))
@@ -380,7 +387,13 @@ def hashed_join_workloads(tqp, torch, dev, local, reps):
     rk, riv, rng_, rtot, rj = z(k), z(2 * k), z(1), z(1), z(1)
     plan = tqp.make_plan(F, (), D, 0, 0, [3], [("sum", [("col", 1)]), ("count", None)], None, k, 0)
     res = tqp.make_result(None, 0, None, None, rk, riv, None, k, rng_, rtot, rj)
-    ms = _time_launches(torch, lambda: tqp.tqp_run_plan(ctx, plan, res, stream), max(5, reps // 2), stream=stream)
+    run = lambda: tqp.tqp_run_plan(ctx, plan, res, stream)  # noqa: E731
+    ms = _time_launches(torch, run, max(5, reps // 2), stream=stream)
+    ctx.set_variant(1)
+    ms_fused = _time_launches(torch, run, max(5, reps // 2), stream=stream)
+    ctx.set_variant(0)
+    ms_part = _time_launches(torch, run, max(5, reps // 2), stream=stream)
+    ctx.set_variant(-1)
     ctx.check(stream)
     alg = npr * 12 + nb * 8
     peak = measured_peaks()[0]
@@ -389,6 +402,7 @@ def hashed_join_workloads(tqp, torch, dev, local, reps):
                     "probe 60M Zipf(0.5) int32 fk + int64 value; GROUP BY payload SUM(value), COUNT; top-100",
         "ms": ms, "probe_rows_per_s": npr / (ms / 1e3), "algorithmic_bytes": alg,
         "achieved_gbs": alg / (ms / 1e3) / 1e9, "frac_of_measured_hbm": alg / (ms / 1e3) / 1e9 / peak,
+        "ms_radix_partitioned": ms_part, "ms_fused_probe": ms_fused,
         "joined_rows": int(rj.item()), "groups": int(rtot.item())}
     bidx = torch.empty(npr, dtype=torch.int32, device=dev)
     pidx = torch.empty(npr, dtype=torch.int32, device=dev)

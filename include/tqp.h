@@ -164,15 +164,26 @@ TQP_API size_t tqp_ctx_arena_bytes(const tqp_ctx* ctx);
  * autotuner and by tuning sweeps; results never depend on it. */
 TQP_API tqp_status tqp_ctx_set_tuning(tqp_ctx* ctx, int32_t tile_rows, int32_t stages, int32_t ctas_per_sm);
 
+/* Force the algorithm of operators that have two, for this context's calls
+ * (results never depend on it): grouped join plans with at least 2^20 fact
+ * rows aggregate either with the radix-partitioned kernels (0: the probe side
+ * is partitioned by group, each partition aggregated in shared memory) or
+ * with the fused probe (1: every joined row added to its key's or group's
+ * accumulators with L2 reductions).  -1 restores the default (0, or the
+ * autotuner's choice).  Errors: TQP_ERR_INVALID_ARG. */
+TQP_API tqp_status tqp_ctx_set_variant(tqp_ctx* ctx, int32_t variant);
+
 /* Autotuning: with it on, the first call of each shape class (operator, log2
  * of the row count, bytes per row it scans, output kinds) times every
  * candidate launch shape -- rows per tile 1024..8192, 2..4 stages, 1..2 CTAs
- * per SM, and for joins that build a hash table the load factor (capacity x1
- * or x2) -- on the call's stream, synchronously, and keeps the fastest for
+ * per SM, for joins that build a hash table the load factor (capacity x1 or
+ * x2), and for grouped join plans the algorithm (tqp_ctx_set_variant) -- on
+ * the call's stream, synchronously, and keeps the fastest for
  * later calls of the class; tqp_batch_create likewise picks the batch's tile
  * size.  Results never depend on the choice.  A tqp_ctx_set_tuning override
  * takes precedence.  The choices can be saved to and loaded from a JSON file
- * (one entry per line: key, tile_rows, stages, ctas_per_sm, ht_scale, ms). */
+ * (one entry per line: key, tile_rows, stages, ctas_per_sm, ht_scale,
+ * variant, ms). */
 TQP_API tqp_status tqp_ctx_set_autotune(tqp_ctx* ctx, int32_t enable);
 TQP_API int32_t tqp_ctx_tuned_count(const tqp_ctx* ctx);
 TQP_API tqp_status tqp_ctx_save_tuning(const tqp_ctx* ctx, const char* path);

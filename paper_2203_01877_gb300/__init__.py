@@ -88,6 +88,7 @@ _SIGS = {
     "tqp_ctx_set_wait_limit": (C.c_int, [_P, C.c_int64]),
     "tqp_ctx_arena_bytes": (C.c_size_t, [_P]),
     "tqp_ctx_set_tuning": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32]),
+    "tqp_ctx_set_variant": (C.c_int, [_P, C.c_int32]),
     "tqp_last_error": (C.c_char_p, []),
     "tqp_status_string": (C.c_char_p, [C.c_int]),
     "tqp_version": (C.c_int, []),
@@ -249,6 +250,11 @@ class Context:
 
     def set_tuning(self, tile_rows: int = 0, stages: int = 0, ctas_per_sm: int = 0):
         _check(lib().tqp_ctx_set_tuning(self.h, int(tile_rows), int(stages), int(ctas_per_sm)))
+
+    def set_variant(self, variant: int = -1):
+        """Force the algorithm of two-algorithm operators (grouped join plans: 0 radix-partitioned, 1 fused
+        probe); -1 restores the default."""
+        _check(lib().tqp_ctx_set_variant(self.h, int(variant)))
 
     def set_autotune(self, enable: bool = True):
         _check(lib().tqp_ctx_set_autotune(self.h, int(bool(enable))))

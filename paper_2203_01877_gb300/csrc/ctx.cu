@@ -493,6 +493,7 @@ tqp_status tqp_ctx_create(int device, void* d_arena, size_t arena_bytes, tqp_ctx
     cudaDeviceGetAttribute(&ctx->l2_bytes, cudaDevAttrL2CacheSize, device);
     ctx->arena_bytes = arena_bytes;
     ctx->top = arena_bytes;
+    ctx->force_variant = -1;
     ctx->wait_cap = kDefaultWaitCap;
     if (d_arena) {
         ctx->arena = static_cast<unsigned char*>(d_arena);
@@ -540,6 +541,14 @@ tqp_status tqp_ctx_set_wait_limit(tqp_ctx* ctx, int64_t polls) {
 }
 
 size_t tqp_ctx_arena_bytes(const tqp_ctx* ctx) { return ctx ? ctx->arena_bytes : 0; }
+
+tqp_status tqp_ctx_set_variant(tqp_ctx* ctx, int32_t variant) {
+    clear_error();
+    TQP_TRY(check_ctx(ctx));
+    if (variant < -1 || variant > 1) return fail(TQP_ERR_INVALID_ARG, "variant must be -1, 0 or 1");
+    ctx->force_variant = variant;
+    return TQP_OK;
+}
 
 tqp_status tqp_ctx_set_tuning(tqp_ctx* ctx, int32_t tile_rows, int32_t stages, int32_t ctas_per_sm) {
     clear_error();

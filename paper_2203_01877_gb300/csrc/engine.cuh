@@ -495,7 +495,10 @@ __device__ __forceinline__ void run_chunk(const ScanGeom& G, const EngineCtl& ct
                     total += (static_cast<uint32_t>(rows) * esize_of(G.col[G.staged[k]].type)) & ~15u;
                 unsigned char* dst = stages + static_cast<size_t>(s) * G.stage_bytes;
                 if (total == 0) {
+                    // no copy: this phase completes now, and the stage's
+                    // earlier copy landed before its consumers released it
                     mbar_arrive(&h->full[s]);
+                    pend &= ~(1u << s);
                 } else {
                     mbar_arrive_expect_tx(&h->full[s], total);
                     for (int k = 0; k < G.nstaged; ++k) {

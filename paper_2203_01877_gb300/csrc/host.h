@@ -24,6 +24,7 @@ struct tqp_tuning {
     int stages;         // 2..kMaxStages
     int ctas_per_sm;    // 0: as many as fit
     int ht_scale;       // hash-table capacity multiplier (1 or 2: half the load factor); 0 = 1
+    int variant;        // algorithm variant of operators that have two (0 = the default)
 };
 
 namespace tqp {
@@ -57,6 +58,7 @@ struct tqp_ctx {
     int* d_err;            // latched device error (persistent, arena start)
     long long wait_cap;
     tqp_tuning forced;     // tile_rows == 0: no override
+    int force_variant;     // >= 0: algorithm variant forced by tqp_ctx_set_variant
     tqp::Tuner* tuner;     // autotuner state (owned by the context; shared by sub-contexts)
     char cur_key[96];      // shape class of the running call ("" outside tuned calls)
 };
@@ -139,16 +141,21 @@ tqp_tuning default_tuning(const tqp_ctx* ctx, int bytes_per_row, int body_smem);
 
 // Hash-table capacity multiplier of the running call (forced or tuned; 1 by default).
 int ht_scale(const tqp_ctx* ctx);
+// Algorithm variant of the running call (forced or tuned; 0 by default).
+int tuned_variant(const tqp_ctx* ctx);
+// What a tuned call's candidates vary besides the scan launch shape.
+constexpr int kTuneHt = 1;       // the hash-table load factor
+constexpr int kTuneVariant = 2;  // the operator's algorithm variant (0 or 1)
 
 // Run `run` (a whole operator call, idempotent) under the tuning of shape
 // class `key`: with autotuning on and `key` new, every candidate launch shape
 // (and hash-table load factor when `has_ht`) is timed on `stream` first and
 // the fastest is remembered; the outputs are the same for every candidate.
-tqp_status tuned_call(tqp_ctx* ctx, const char* key, cudaStream_t stream, bool has_ht, tqp_status (*run)(void*),
+tqp_status tuned_call(tqp_ctx* ctx, const char* key, cudaStream_t stream, int opts, tqp_status (*run)(void*),
                       void* arg);
 template <class F>
-tqp_status tuned(tqp_ctx* ctx, const char* key, cudaStream_t stream, bool has_ht, F& f) {
-    return tuned_call(ctx, key, stream, has_ht, [](void* a) { return (*static_cast<F*>(a))(); }, &f);
+tqp_status tuned(tqp_ctx* ctx, const char* key, cudaStream_t stream, int opts, F& f) {
+    return tuned_call(ctx, key, stream, opts, [](void* a) { return (*static_cast<F*>(a))(); }, &f);
 }
 void tuner_destroy(tqp_ctx* ctx);
 // Bytes per row of the distinct columns `cols` of t.

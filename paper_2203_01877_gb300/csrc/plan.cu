@@ -37,6 +37,13 @@ tqp_status ht_key_range_launch(const tqp_ctx* ctx, const tqp_table* build, int32
                                cudaStream_t stream);
 tqp_status ht_chain_insert_launch(const tqp_ctx* ctx, const tqp_table* build, int32_t key_col, const JoinHT& H,
                                   uint32_t* next, cudaStream_t stream);
+tqp_status launch_part_join(tqp_ctx* ctx, const PlanJoinArgs& J, const tqp_table* F, long long maxg,
+                            unsigned long long* acc_words, cudaStream_t stream);
+
+// Fact rows from which a grouped join plan takes the radix-partitioned
+// aggregation by default (variant 0; variant 1 is the fused probe).  Below,
+// the extra kernel and the record traffic do not pay for themselves.
+constexpr long long kPartJoinMinRows = 1LL << 20;
 
 // Dense group ids of the dimension rows, in three small passes:
 //   claim  each dim row inserts its packed group key into a claim table
@@ -306,11 +313,24 @@ static tqp_status run_join_plan(tqp_ctx* ctx, const tqp_plan* p, const tqp_resul
     if (!sc) return arena_oom(ctx, 64);
     TQP_CUDA(cudaMemsetAsync(sc, 0, 8 * 8, stream));
     A.acc = sc + 1;
+    A.d_num_joined = r->d_num_joined;
+    A.d_sum = p->has_sum ? r->d_sum : nullptr;
+    A.d_num_rows = (p->emit_row_ids && r->d_row_ids) ? nullptr : r->d_num_rows;
+    // Radix-partitioned aggregation (partjoin.cuh): the joined rows' group
+    // updates land in shared memory instead of L2 reductions.  It declines
+    // (nothing launched) for plans outside its shapes or short of scratch,
+    // and the fused probe below runs instead.
+    bool parted = false;
+    if (grouped && F->num_rows >= kPartJoinMinRows && tuned_variant(ctx) == 0) {
+        const tqp_status ps = launch_part_join(ctx, A, F, A.S.max_groups, A.acc, stream);
+        if (ps == TQP_OK) parted = true;
+        else if (ps != TQP_ERR_UNSUPPORTED) return ps;
+    }
     // Aggregate by join key first when the fact rows outnumber the build rows:
     // a probe row then costs its key entry's atomics only (no slot load), and
     // one pass over the build rows moves the per-key totals to the groups.
     // Used only if the table turns out direct-mapped; off when scratch is short.
-    if (grouped && A.pjfast && A.fast && H.meta && F->num_rows >= 2 * std::max<long long>(1, D->num_rows)) {
+    if (!parted && grouped && A.pjfast && A.fast && H.meta && F->num_rows >= 2 * std::max<long long>(1, D->num_rows)) {
         A.nk = A.S.nacc + (A.has_sum ? 1 : 0);
         const size_t used = ctx->used;
         A.kacc = static_cast<unsigned long long*>(arena_alloc(ctx, static_cast<size_t>(H.cap) * A.nk * 8));
@@ -322,10 +342,9 @@ static tqp_status run_join_plan(tqp_ctx* ctx, const tqp_plan* p, const tqp_resul
         k_keyfirst_zero<<<std::max(blocks, 1), 256, 0, stream>>>(A.H, A.kacc, A.nk);
         TQP_CUDA(cudaGetLastError());
     }
-    A.d_num_joined = r->d_num_joined;
-    A.d_sum = p->has_sum ? r->d_sum : nullptr;
-    A.d_num_rows = (p->emit_row_ids && r->d_row_ids) ? nullptr : r->d_num_rows;
-    if (F->num_rows > 0) {
+    if (parted) {
+        // launched: counts, sums and group accumulators come from the partitioned kernels
+    } else if (F->num_rows > 0) {
         static SmemFlags attr_done;
         TQP_TRY(allow_smem(ctx, reinterpret_cast<const void*>(k_plan_join), attr_done));
         const int g = engine_grid(ctx, reinterpret_cast<const void*>(k_plan_join), smem, A.G.ntiles, tu.ctas_per_sm);
@@ -533,5 +552,8 @@ extern "C" tqp_status tqp_run_plan(tqp_ctx* ctx, const tqp_plan* plan, const tqp
              row_bytes(plan->fact, cols), plan->dim ? rows_class(plan->dim->num_rows) + 1 : 0,
              plan->prepared ? 1 : 0, plan->ngc + plan->naggs > 0 ? 1 : 0, plan->topk > 0 ? 1 : 0);
     auto run = [&]() { return run_plan_one(ctx, plan, res, st); };
-    return tuned(ctx, key, st, plan->dim != nullptr && !plan->prepared, run);
+    int opts = 0;
+    if (plan->dim && !plan->prepared) opts |= kTuneHt;
+    if (plan->dim && (plan->ngc > 0 || plan->naggs > 0) && plan->fact->num_rows >= kPartJoinMinRows) opts |= kTuneVariant;
+    return tuned(ctx, key, st, opts, run);
 }

@@ -25,6 +25,14 @@ int ht_scale(const tqp_ctx* ctx) {
     return 1;
 }
 
+int tuned_variant(const tqp_ctx* ctx) {
+    if (ctx->force_variant >= 0) return ctx->force_variant;
+    if (ctx->forced.tile_rows > 0) return ctx->forced.variant;
+    tqp_tuning t;
+    if (ctx->tuner && ctx->cur_key[0] && ctx->tuner->lookup(ctx->cur_key, &t)) return t.variant;
+    return 0;
+}
+
 int row_bytes(const tqp_table* t, std::vector<int> cols) {
     std::sort(cols.begin(), cols.end());
     cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
@@ -60,7 +68,7 @@ struct KeyScope {
 
 }  // namespace
 
-tqp_status tuned_call(tqp_ctx* ctx, const char* key, cudaStream_t stream, bool has_ht, tqp_status (*run)(void*),
+tqp_status tuned_call(tqp_ctx* ctx, const char* key, cudaStream_t stream, int opts, tqp_status (*run)(void*),
                       void* arg) {
     KeyScope ks(ctx, key);
     tqp_tuning known;
@@ -69,14 +77,18 @@ tqp_status tuned_call(tqp_ctx* ctx, const char* key, cudaStream_t stream, bool h
     cudaEvent_t ev[2] = {nullptr, nullptr};
     TQP_CUDA(cudaEventCreate(&ev[0]));
     TQP_CUDA(cudaEventCreate(&ev[1]));
-    tqp_tuning best{0, 0, 0, 0};
+    tqp_tuning best{0, 0, 0, 0, 0};
     double best_ms = 1e30;
-    const int hts = has_ht ? 2 : 1;
+    const int hts = (opts & kTuneHt) ? 2 : 1;
+    const int nvar = (opts & kTuneVariant) ? 2 : 1;
+    for (int V = nvar - 1; V >= 0; --V)
     for (int T = kRowQuantum; T <= kMaxTileRows; T *= 2)
         for (int S = 2; S <= kMaxStages; ++S)
             for (int C = 1; C <= 2; ++C)
                 for (int H = 1; H <= hts; ++H) {
-                    ctx->forced = tqp_tuning{T, S, C, H};
+                    // variant 0 of a two-variant operator does not use the scan launch shape
+                    if (nvar > 1 && V == 0 && (T != kRowQuantum || S != 2 || C != 1)) continue;
+                    ctx->forced = tqp_tuning{T, S, C, H, V};
                     if (run(arg) != TQP_OK) continue;  // infeasible (shared memory): refused on the host
                     cudaEventRecord(ev[0], stream);
                     const tqp_status s = run(arg);
@@ -89,7 +101,7 @@ tqp_status tuned_call(tqp_ctx* ctx, const char* key, cudaStream_t stream, bool h
                         best = ctx->forced;
                     }
                 }
-    ctx->forced = tqp_tuning{0, 0, 0, 0};
+    ctx->forced = tqp_tuning{0, 0, 0, 0, 0};
     cudaEventDestroy(ev[0]);
     cudaEventDestroy(ev[1]);
     clear_error();
@@ -141,9 +153,9 @@ tqp_status tqp_ctx_save_tuning(const tqp_ctx* ctx, const char* path) {
         for (const auto& e : ctx->tuner->table) {
             const double ms = ctx->tuner->ms.count(e.first) ? ctx->tuner->ms.at(e.first) : 0.0;
             fprintf(f, "%s\n  {\"key\": \"%s\", \"tile_rows\": %d, \"stages\": %d, \"ctas_per_sm\": %d, \"ht_scale\": %d, "
-                       "\"ms\": %.6f}",
+                       "\"variant\": %d, \"ms\": %.6f}",
                     first ? "" : ",", e.first.c_str(), e.second.tile_rows, e.second.stages, e.second.ctas_per_sm,
-                    e.second.ht_scale, ms);
+                    e.second.ht_scale, e.second.variant, ms);
             first = false;
         }
     }
@@ -168,13 +180,20 @@ tqp_status tqp_ctx_load_tuning(tqp_ctx* ctx, const char* path) {
     int loaded = 0;
     while (fgets(line, sizeof(line), f)) {
         char key[sizeof(tqp_ctx::cur_key)];
-        tqp_tuning t{0, 0, 0, 0};
+        tqp_tuning t{0, 0, 0, 0, 0};
         double ms = 0;
-        if (sscanf(line, " {\"key\": \"%95[^\"]\", \"tile_rows\": %d, \"stages\": %d, \"ctas_per_sm\": %d, \"ht_scale\": %d, "
+        const bool with_variant =
+            sscanf(line, " {\"key\": \"%95[^\"]\", \"tile_rows\": %d, \"stages\": %d, \"ctas_per_sm\": %d, \"ht_scale\": %d, "
+                         "\"variant\": %d, \"ms\": %lf",
+                   key, &t.tile_rows, &t.stages, &t.ctas_per_sm, &t.ht_scale, &t.variant, &ms) == 7;
+        if (with_variant ||
+            sscanf(line, " {\"key\": \"%95[^\"]\", \"tile_rows\": %d, \"stages\": %d, \"ctas_per_sm\": %d, \"ht_scale\": %d, "
                          "\"ms\": %lf",
                    key, &t.tile_rows, &t.stages, &t.ctas_per_sm, &t.ht_scale, &ms) == 6) {
+            if (!with_variant) t.variant = 0;
             if (t.tile_rows < kRowQuantum || t.tile_rows > kMaxTileRows || t.tile_rows % kRowQuantum ||
-                t.stages < 2 || t.stages > kMaxStages || t.ctas_per_sm < 1 || t.ctas_per_sm > 2)
+                t.stages < 2 || t.stages > kMaxStages || t.ctas_per_sm < 1 || t.ctas_per_sm > 2 || t.variant < 0 ||
+                t.variant > 1)
                 continue;
             std::lock_guard<std::mutex> lk(ctx->tuner->mu);
             ctx->tuner->table[key] = t;

@@ -225,3 +225,22 @@ def test_filter_pageable_projected_column_rejected(ctx):
     assert ctx.status() == 0
     want_ids, want_sum = oracle.filter_rows([t["date"], t["price"]], [(0, "lt", 100)], expr)
     assert int(cnt.item()) == len(want_ids) and int(s.item()) == want_sum
+
+
+@pytest.mark.parametrize("extra", [1, 3])
+@pytest.mark.parametrize("shape", [(1024, 2, 1), (1024, 3, 2), (2048, 2, 1)])
+def test_ragged_last_tile_under_forced_shapes(ctx, extra, shape):
+    """A last tile of one to three rows stages no bytes (its staged columns are read row by row), while its
+    pipeline stage was already used earlier in the same chunk: the scan must neither stall nor report a wait
+    that ran out, and must give the oracle's result."""
+    from tests.gpu_util import gpu_filter
+    n = shape[0] * 600 + extra
+    cols = q6_cols(n, 4000 + extra)
+    try:
+        ctx.set_tuning(*shape)
+        ids, k, s, st = gpu_filter(ctx, cols, Q6_PREDS, Q6_EXPR)
+    finally:
+        ctx.set_tuning(0, 0, 0)
+    want_ids, want_sum = oracle.filter_rows(cols, Q6_PREDS, Q6_EXPR)
+    assert st == 0 and k == len(want_ids) and s == want_sum
+    assert np.array_equal(ids, want_ids)

@@ -234,3 +234,52 @@ def test_hashed_join_duplicate_build_keys(ctx):
     got = run_both(ctx, capacity_groups=150_000, **spec)
     assert got["num_pairs"] == 10 * n
     run_both(ctx, topk=100, topk_agg=0, **spec)
+
+
+def _variant_case(name):
+    """Grouped join plans of >= 2^20 fact rows (the size from which the radix-partitioned aggregation is the
+    default), with misses, predicates, two sums, duplicate build keys, sparse keys and top-k."""
+    rng = np.random.default_rng(len(name))
+    n = 1_300_003
+    if name == "sparse_keys_topk":
+        dim = datagen.dim_table(60_000, 4_000, seed=11, sparse=True)
+        pr = datagen.probe_table(n, 60_000, seed=11, sparse=True)
+        fk = pr["fk"].copy()
+        fk[::13] = 12345  # (not a sparse key: misses)
+        return dict(fact=[fk, pr["value"]], dim=[dim["key"], dim["payload"]], fact_fk=0, dim_key=0,
+                    group_cols=[3], aggs=[("sum", [("col", 1)]), ("count", None)], topk=50, topk_agg=0)
+    if name == "duplicate_keys":
+        dim = datagen.dim_table(90_000, 2_500, seed=12, dup=3)  # 30K keys, three build rows each
+        pr = datagen.probe_table(n, 31_000, seed=12)  # keys 30000.. miss
+        return dict(fact=[pr["fk"], pr["value"]], dim=[dim["key"], dim["payload"]], fact_fk=0, dim_key=0,
+                    group_cols=[3], aggs=[("sum", [("col", 1)]), ("count", None)], capacity_groups=4096)
+    dim = datagen.dim_table(50_000, 5_000, seed=13)
+    pr = datagen.probe_table(n, 55_000, seed=13)  # keys 50000.. miss
+    qty = rng.integers(1, 51, n).astype(np.int32)
+    fact = [pr["fk"], pr["value"], qty]
+    d = [dim["key"], dim["payload"]]
+    if name == "count_only":
+        return dict(fact=fact, dim=d, fact_fk=0, dim_key=0, group_cols=[4], aggs=[("count", None)],
+                    capacity_groups=8192)
+    # predicates, an ungrouped sum and two sums besides the count (AVG shares SUM(value))
+    return dict(fact=fact, dim=d, fact_fk=0, dim_key=0, preds=[(2, "lt", 30), (1, "ge", 200_000)],
+                group_cols=[4], aggs=[("sum", [("col", 1)]), ("sum", [("col", 1), ("const", 100), ("col", 2),
+                                                                       "sub", "mul"]),
+                                      ("count", None), ("avg", [("col", 1)])],
+                sum_expr=[("col", 1), ("col", 2), "mul"], capacity_groups=8192)
+
+
+@pytest.mark.parametrize("name", ["preds_sums", "count_only", "duplicate_keys", "sparse_keys_topk"])
+def test_join_plan_variants(ctx, name):
+    """Both aggregation algorithms of a grouped join plan -- radix-partitioned (0) and the fused probe (1) --
+    give the oracle's result, element by element."""
+    spec = _variant_case(name)
+    ospec = {k: v for k, v in spec.items() if k not in ("capacity_groups",)}
+    want = oracle.run_plan(want_pairs=False, cap_groups=None, want_row_ids=False, **ospec)
+    try:
+        for variant in (0, 1):
+            ctx.set_variant(variant)
+            got = gpu_plan(ctx, **spec)
+            compare(got, want, spec)
+    finally:
+        ctx.set_variant(-1)

@@ -139,7 +139,7 @@ def load_variant(so_path: str):
     return L
 
 
-_JOINS = {"inner": 0, "semi": 1, "anti": 2}
+_JOINS = {"inner": 0, "semi": 1, "anti": 2, "left_outer": 3}
 
 
 def run_plan(fact, preds=(), dim=None, fact_fk=0, dim_key=0, group_cols=(), aggs=(), sum_expr=None,
@@ -147,7 +147,9 @@ def run_plan(fact, preds=(), dim=None, fact_fk=0, dim_key=0, group_cols=(), aggs
              threads=1, _lib=None):
     """Evaluate one plan with the C oracle; returns a dict of numpy results.
     join_kind: "inner" (every equal-key pair), "semi" / "anti" (each fact row
-    once if it has a / no equal-key dim row; fact columns only).
+    once if it has a / no equal-key dim row; fact columns only), "left_outer"
+    (the inner pairs, and each fact row without a match once with dim row -1;
+    fact columns only).
     threads > 1 (filter plans only: no join, no grouping) evaluates row ranges
     on that many threads with the same row loop (oracle_filter_mt) -- the
     all-core CPU baseline; the result is identical."""
@@ -248,7 +250,9 @@ def groupby(fact, preds, group_cols, aggs, topk=0, topk_agg=0):
     return r["keys"], r["ivals"], r["fvals"]
 
 
-def join_pairs(build_keys, probe_keys):
-    """Equi-join index pairs (build_idx, probe_idx) in (probe, build) ascending order."""
-    r = run_plan([probe_keys], (), dim=[build_keys], fact_fk=0, dim_key=0, want_row_ids=False, want_pairs=True)
+def join_pairs(build_keys, probe_keys, join_kind="inner"):
+    """Equi-join index pairs (build_idx, probe_idx) in (probe, build) ascending order (left outer: a probe row
+    without a match once, with build_idx -1)."""
+    r = run_plan([probe_keys], (), dim=[build_keys], fact_fk=0, dim_key=0, want_row_ids=False, want_pairs=True,
+                 join_kind=join_kind)
     return r["pair_dim"], r["pair_fact"]

@@ -15,6 +15,9 @@
  *                     Left semi / anti join (a join kind the paper lists as
  *                     supported, Section 5): each surviving fact row once,
  *                     when it has at least one / no equal-key dim row.
+ *                     Left outer join (also listed there): the inner pairs,
+ *                     and each surviving fact row with no equal-key dim row
+ *                     once, paired with dim row -1 (no dim columns are read).
  *   group-by          Section 5.4 (Algorithm 3): sort rows by the group-key
  *                     tuple, cut the sorted list into runs of equal keys
  *                     ("unique consecutive"), evaluate the aggregates per run;
@@ -173,7 +176,7 @@ int oracle_plan(const or_plan* p, or_out* o) {
         if (p->aggs[a].fn != OR_COUNT && !valid_expr(&p->aggs[a].expr, ncat)) return OR_ERR_INVALID;
     }
     if (p->sum_expr && !valid_expr(p->sum_expr, ncat)) return OR_ERR_INVALID;
-    if (joined && (p->join_kind < OR_JOIN_INNER || p->join_kind > OR_JOIN_ANTI)) return OR_ERR_INVALID;
+    if (joined && (p->join_kind < OR_JOIN_INNER || p->join_kind > OR_JOIN_LEFT_OUTER)) return OR_ERR_INVALID;
     if (joined && p->join_kind != OR_JOIN_INNER) {  /* no dim row to read: fact columns only */
         for (int i = 0; i < p->ngc; ++i)
             if (p->group_cols[i] >= p->nfact_cols) return OR_ERR_INVALID;
@@ -218,7 +221,7 @@ int oracle_plan(const or_plan* p, or_out* o) {
         qsort(sd, (size_t)p->ndim, sizeof(or_keyrow), cmp_keyrow);
         for (int64_t i = 0; i < ns; ++i) {
             int64_t k = col_value(&p->fact[p->fact_fk], surv[i]);
-            if (p->join_kind != OR_JOIN_INNER) {  /* semi / anti: the fact row once, or not at all */
+            if (p->join_kind == OR_JOIN_SEMI || p->join_kind == OR_JOIN_ANTI) {  /* the fact row once, or not at all */
                 const int64_t j0 = lower_bound(sd, p->ndim, k);
                 const int has = j0 < p->ndim && sd[j0].key == k;
                 if (has == (p->join_kind == OR_JOIN_SEMI)) {
@@ -228,6 +231,7 @@ int oracle_plan(const or_plan* p, or_out* o) {
                 }
                 continue;
             }
+            const int64_t before = npairs;
             for (int64_t j = lower_bound(sd, p->ndim, k); j < p->ndim && sd[j].key == k; ++j) {
                 if (npairs == cap) {
                     cap *= 2;
@@ -237,6 +241,17 @@ int oracle_plan(const or_plan* p, or_out* o) {
                 }
                 pairs[npairs].f = surv[i];
                 pairs[npairs].d = sd[j].row;
+                ++npairs;
+            }
+            if (p->join_kind == OR_JOIN_LEFT_OUTER && npairs == before) {  /* no match: the fact row once */
+                if (npairs == cap) {
+                    cap *= 2;
+                    or_pair* np2 = (or_pair*)realloc(pairs, sizeof(or_pair) * (size_t)cap);
+                    if (!np2) { free(sd); free(pairs); free(surv); return OR_ERR_NOMEM; }
+                    pairs = np2;
+                }
+                pairs[npairs].f = surv[i];
+                pairs[npairs].d = -1;
                 ++npairs;
             }
         }

@@ -48,10 +48,13 @@ extern "C" {
 #define OR_X_MUL 4
 
 /* join kinds: every equal-key (fact, dim) pair; or each fact row once if it
- * has a match (left semi) / has none (left anti), with dim row -1 */
+ * has a match (left semi) / has none (left anti), with dim row -1; or the
+ * equal-key pairs plus each fact row without a match once with dim row -1
+ * (left outer).  Every kind but inner reads fact columns only. */
 #define OR_JOIN_INNER 0
 #define OR_JOIN_SEMI 1
 #define OR_JOIN_ANTI 2
+#define OR_JOIN_LEFT_OUTER 3
 
 /* aggregate functions */
 #define OR_SUM 0
@@ -79,7 +82,7 @@ typedef struct {
     int64_t nfact; const or_col* fact; int32_t nfact_cols; int32_t pad0;
     const or_pred* preds; int32_t npreds; int32_t pad1;
     int64_t ndim; const or_col* dim; int32_t ndim_cols;   /* ndim_cols == 0: no join */
-    int32_t fact_fk; int32_t dim_key; int32_t join_kind;  /* OR_JOIN_INNER / _SEMI / _ANTI */
+    int32_t fact_fk; int32_t dim_key; int32_t join_kind;  /* OR_JOIN_INNER / _SEMI / _ANTI / _LEFT_OUTER */
     const int32_t* group_cols; int32_t ngc; int32_t pad3;
     const or_agg* aggs; int32_t naggs; int32_t pad4;
     const or_expr* sum_expr;                              /* NULL: no ungrouped sum */

@@ -219,3 +219,51 @@ def test_semi_anti_reject_dim_columns():
     with pytest.raises(oracle.OracleError):
         oracle.run_plan([fk], (), dim=[dk, dp], fact_fk=0, dim_key=0, group_cols=[2], aggs=[("count", None)],
                         join_kind="semi")
+
+
+def test_left_outer_vs_nested_loop_and_identities():
+    """Left outer join: the inner pairs, and each surviving fact row without an equal-key dim row once with dim
+    row -1, in (fact row, dim row) order.  Pinned against a nested loop on a tiny case; on a larger one against
+    the identities outer = inner + anti (as pair sets, in canonical order) and its grouped COUNT/SUM = inner's
+    + anti's, group by group."""
+    fk = np.array([4, 1, 9, 4, 7, 1, 3], np.int32)
+    val = np.array([10, 20, 30, 40, 50, 60, 70], np.int64)
+    dk = np.array([1, 4, 4, 5], np.int32)
+    want = []
+    for f in range(len(fk)):
+        m = [d for d in range(len(dk)) if dk[d] == fk[f]]
+        want += [(f, d) for d in m] if m else [(f, -1)]
+    r = oracle.run_plan([fk, val], (), dim=[dk], fact_fk=0, dim_key=0, want_row_ids=False, want_pairs=True,
+                        join_kind="left_outer", sum_expr=[("col", 1)])
+    assert list(zip(r["pair_fact"].tolist(), r["pair_dim"].tolist())) == want
+    assert r["num_pairs"] == len(want)
+    assert r["sum"] == sum(int(val[f]) for f, _ in want)
+    b, p = oracle.join_pairs(dk, fk, join_kind="left_outer")
+    assert list(zip(p.tolist(), b.tolist())) == want
+
+    rng = np.random.default_rng(43)
+    n = 30_000
+    fk = rng.integers(-50, 2_050, n).astype(np.int32)
+    g = rng.integers(0, 7, n).astype(np.int32)
+    v = rng.integers(-10**9, 10**9, n).astype(np.int64)
+    dk = rng.integers(0, 2_000, 5_000).astype(np.int32)
+    preds = [(2, "gt", -5 * 10**8)]
+    aggs = [("sum", [("col", 2)]), ("count", None)]
+    res = {}
+    for kind in ("inner", "anti", "left_outer"):
+        res[kind] = oracle.run_plan([fk, g, v], preds, dim=[dk], fact_fk=0, dim_key=0, group_cols=[1], aggs=aggs,
+                                    want_row_ids=False, want_pairs=True, join_kind=kind)
+    inner, anti, outer = res["inner"], res["anti"], res["left_outer"]
+    assert outer["num_pairs"] == inner["num_pairs"] + anti["num_pairs"]
+    pairs = np.concatenate([np.stack([inner["pair_fact"], inner["pair_dim"]], 1),
+                            np.stack([anti["pair_fact"], anti["pair_dim"]], 1)])
+    pairs = pairs[np.lexsort((pairs[:, 1], pairs[:, 0]))]
+    assert np.array_equal(outer["pair_fact"], pairs[:, 0]) and np.array_equal(outer["pair_dim"], pairs[:, 1])
+    # grouped: per fact group, outer = inner + anti
+    def by_key(r):
+        return {int(k): tuple(int(x) for x in iv) for k, iv in zip(r["keys"].reshape(-1), r["ivals"])}
+    gi, ga, go = by_key(inner), by_key(anti), by_key(outer)
+    for k in set(gi) | set(ga):
+        a, b = gi.get(k, (0, 0)), ga.get(k, (0, 0))
+        assert go[k] == (a[0] + b[0], a[1] + b[1])
+    assert set(go) == set(gi) | set(ga)

@@ -42,6 +42,10 @@ MUTANTS = {
     "anti_keeps_matches": ("if (has == (p->join_kind == OR_JOIN_SEMI))", "if (has == (p->join_kind != OR_JOIN_INNER))"),
     "semi_ignores_first_dim_row": ("const int has = j0 < p->ndim && sd[j0].key == k;",
                                    "const int has = j0 + 1 < p->ndim && sd[j0 + 1].key == k;"),
+    "left_outer_drops_unmatched": ("if (p->join_kind == OR_JOIN_LEFT_OUTER && npairs == before) {",
+                                   "if (p->join_kind == OR_JOIN_LEFT_OUTER && npairs == before && 0) {"),
+    "left_outer_pads_every_row": ("if (p->join_kind == OR_JOIN_LEFT_OUTER && npairs == before) {",
+                                  "if (p->join_kind == OR_JOIN_LEFT_OUTER) {"),
     "sum_skips_last_row": ("for (int64_t i = 0; i < npairs; ++i) {\n            int64_t v;",
                            "for (int64_t i = 0; i + 1 < npairs; ++i) {\n            int64_t v;"),
 }
@@ -65,6 +69,7 @@ PINS = [
     tj.test_cardinality_identity_and_paper_algorithms,
     tj.test_join_group_topk_invariants,
     tj.test_semi_anti_vs_nested_loop_and_numpy,
+    tj.test_left_outer_vs_nested_loop_and_identities,
 ]
 
 

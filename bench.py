@@ -740,6 +740,8 @@ def profile_case(args):
     st = torch.cuda.current_stream()
     ctx = tqp.Context(0, 2 << 30)
     ctx.set_autotune(True)
+    if args.variant >= 0:
+        ctx.set_variant(args.variant)
     n = args.rows
     if args.case == "filter":
         t = datagen.fact_table(n, seed=datagen.DEFAULT_SEED + 1, cols=["date", "discount", "quantity", "price"])
@@ -803,6 +805,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="0 skips the CPU baseline")
     ap.add_argument("--rows", type=int, default=N_ROWS, help="smaller cases for profiling only")
+    ap.add_argument("--variant", type=int, default=-1, help="profiling: force a join plan's algorithm (0 or 1)")
     ap.add_argument("--no-operators", action="store_true", help="skip the secondary workloads")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving workload")
     ap.add_argument("--serve-seconds", type=float, default=10.0)

@@ -263,6 +263,29 @@ TQP_API tqp_status tqp_hash_join(tqp_ctx* ctx,
                          int64_t capacity, int64_t* d_count, void* stream);
 
 /*
+ * Join kinds (paper Section 5 lists left-semi, left-anti and left-outer joins
+ * among the supported operators; the probe side is the left side):
+ *   TQP_JOIN_INNER       every (build, probe) pair with equal keys
+ *   TQP_JOIN_LEFT_SEMI   each probe row with at least one equal build key, once
+ *   TQP_JOIN_LEFT_ANTI   each probe row with no equal build key, once
+ *   TQP_JOIN_LEFT_OUTER  the inner pairs, and each probe row with no equal
+ *                        build key once, paired with build row -1
+ */
+typedef enum { TQP_JOIN_INNER = 0, TQP_JOIN_LEFT_SEMI = 1, TQP_JOIN_LEFT_ANTI = 2, TQP_JOIN_LEFT_OUTER = 3 } tqp_join_kind;
+
+/*
+ * tqp_hash_join_kind -- tqp_hash_join for any tqp_join_kind, with the same
+ * arguments, order and errors.  Semi and anti joins report each kept probe row
+ * once with d_build_idx -1; left outer reports -1 for probe rows without a
+ * match.  join_kind TQP_JOIN_INNER is tqp_hash_join.
+ */
+TQP_API tqp_status tqp_hash_join_kind(tqp_ctx* ctx,
+                              const tqp_table* build, int32_t build_key,
+                              const tqp_table* probe, int32_t probe_key, int32_t join_kind,
+                              int32_t* d_build_idx, int32_t* d_probe_idx,
+                              int64_t capacity, int64_t* d_count, void* stream);
+
+/*
  * tqp_filter_noalloc -- tqp_filter for callers that cannot allocate device
  * memory.  (The paper has no counterpart; this is a deployment entry point.)
  *
@@ -308,9 +331,15 @@ TQP_API tqp_status tqp_filter_noalloc(int device, const tqp_table* t,
  *     -> [SUM(sum_expr)] -> [GROUP BY group_cols: aggs] -> [top-k]
  *
  * Column indices in group_cols and in expressions address fact columns
- * 0..F-1 and then dim columns F..F+D-1.  With a join, each passing fact row
- * contributes once per matching dim row.  topk > 0 keeps the k groups with
- * the largest aggregate `topk_agg` (ties: smaller key first), in that order.
+ * 0..F-1 and then dim columns F..F+D-1.  With an inner join, each passing
+ * fact row contributes once per matching dim row.  With join_kind
+ * TQP_JOIN_LEFT_SEMI / TQP_JOIN_LEFT_ANTI each passing fact row contributes
+ * once if it has a matching dim row / has none; group columns and
+ * expressions then address fact columns only (a dim column is
+ * TQP_ERR_INVALID_ARG), and d_num_joined counts the kept fact rows.  Left
+ * outer joins are for tqp_hash_join_kind only (TQP_ERR_UNSUPPORTED here).
+ * topk > 0 keeps the k groups with the largest aggregate `topk_agg` (ties:
+ * smaller key first), in that order.
  */
 typedef struct {
     const tqp_table* fact;
@@ -328,7 +357,7 @@ typedef struct {
     int32_t topk;               /* 0 = all groups in key order */
     tqp_expr sum_expr;
     int32_t topk_agg;
-    int32_t reserved;
+    int32_t join_kind;          /* tqp_join_kind: TQP_JOIN_INNER (0), LEFT_SEMI or LEFT_ANTI */
     int64_t max_groups;         /* bound on distinct groups, sizes the aggregation
                                    table; 0 = the dim row count when grouping by
                                    dim columns, else res->capacity_groups */

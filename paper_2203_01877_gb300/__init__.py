@@ -68,7 +68,7 @@ class Plan(C.Structure):
                 ("aggs", Agg * MAX_AGGS),
                 ("has_sum", C.c_int32), ("topk", C.c_int32),
                 ("sum_expr", Expr),
-                ("topk_agg", C.c_int32), ("reserved", C.c_int32), ("max_groups", C.c_int64),
+                ("topk_agg", C.c_int32), ("join_kind", C.c_int32), ("max_groups", C.c_int64),
                 ("prepared", C.c_void_p)]
 
 
@@ -100,6 +100,8 @@ _SIGS = {
                                   C.c_int32, C.POINTER(Agg), C.c_int32, _P, _P, _P, C.c_int64, _P, _P]),
     "tqp_hash_join": (C.c_int, [_P, C.POINTER(Table), C.c_int32, C.POINTER(Table), C.c_int32, _P, _P,
                                 C.c_int64, _P, _P]),
+    "tqp_hash_join_kind": (C.c_int, [_P, C.POINTER(Table), C.c_int32, C.POINTER(Table), C.c_int32, C.c_int32, _P,
+                                     _P, C.c_int64, _P, _P]),
     "tqp_run_plan": (C.c_int, [_P, C.POINTER(Plan), C.POINTER(Result), _P]),
     "tqp_run_plans": (C.c_int, [_P, C.POINTER(Plan), C.POINTER(Result), C.c_int32, _P]),
     "tqp_batch_create": (C.c_int, [_P, C.POINTER(Plan), C.POINTER(Result), C.c_int32, C.POINTER(_P)]),
@@ -321,9 +323,21 @@ def tqp_hash_join(ctx: Context, build: TableRef, build_key: int, probe: TableRef
                                _stream(stream)))
 
 
+JOIN_KINDS = {"inner": 0, "semi": 1, "anti": 2, "left_outer": 3}
+
+
+def tqp_hash_join_kind(ctx: Context, build: TableRef, build_key: int, probe: TableRef, probe_key: int, join_kind,
+                       d_build_idx, d_probe_idx, capacity: int, d_count, stream=None):
+    """tqp_hash_join for a join kind ("inner", "semi", "anti", "left_outer" or its tqp_join_kind code)."""
+    kind = JOIN_KINDS[join_kind] if isinstance(join_kind, str) else int(join_kind)
+    _check(lib().tqp_hash_join_kind(ctx.h, build.ref(), int(build_key), probe.ref(), int(probe_key), kind,
+                                    _ptr(d_build_idx), _ptr(d_probe_idx), int(capacity), _ptr(d_count),
+                                    _stream(stream)))
+
+
 def make_plan(fact: TableRef, preds=(), dim: TableRef | None = None, fact_fk=0, dim_key=0, group_cols=(),
               aggs=(), sum_expr=None, topk=0, topk_agg=0, emit_row_ids=False, max_groups=0,
-              prepared: "PreparedDim | None" = None) -> Plan:
+              prepared: "PreparedDim | None" = None, join_kind="inner") -> Plan:
     p = Plan()
     p.fact = C.pointer(fact.t)
     if len(preds) > MAX_PREDS or len(group_cols) > MAX_GROUP_COLS or len(aggs) > MAX_AGGS:
@@ -347,6 +361,7 @@ def make_plan(fact: TableRef, preds=(), dim: TableRef | None = None, fact_fk=0, 
         p.sum_expr = make_expr(sum_expr)
     p.topk, p.topk_agg = int(topk), int(topk_agg)
     p.max_groups = int(max_groups)
+    p.join_kind = JOIN_KINDS[join_kind] if isinstance(join_kind, str) else int(join_kind)
     p.prepared = prepared.h if prepared is not None else None
     p._keep = (fact, dim, prepared)  # keep the tables' C structs alive
     return p

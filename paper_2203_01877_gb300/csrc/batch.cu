@@ -786,6 +786,7 @@ static bool all_device(const tqp_table* t) {
 
 static bool batchable(const tqp_ctx* ctx, const tqp_plan* p, const tqp_result* r) {
     if (!p->fact || p->npreds < 0 || p->npreds > TQP_MAX_PREDS) return false;
+    if (p->dim && p->join_kind != TQP_JOIN_INNER) return false;  // semi / anti plans: the single-plan path
     if (p->ngc < 0 || p->ngc > TQP_MAX_GROUP_COLS || p->naggs < 0 || p->naggs > TQP_MAX_AGGS) return false;
     if (p->topk < 0 || p->topk > kTopBlock / 2) return false;
     const bool grouped = p->ngc > 0 || p->naggs > 0;

@@ -134,6 +134,10 @@ __global__ void k_ht_insert(JoinHT H, const unsigned char* key_col, int key_type
 // unique key) stores that row itself, flagged kRunRow, so the probe writes
 // its pairs without loading it from the sorted rows.
 constexpr uint32_t kRunRow = 0x80000000u;
+// The run of a probe row paired with no build row (left outer without a
+// match, semi and anti joins): one pair with build index -1.  (Build rows are
+// below 2^31 - 1, so no flagged row collides with it.)
+constexpr uint32_t kRunNone = 0xFFFFFFFFu;
 
 __global__ void k_ht_runs(JoinHT H, const uint64_t* skey, const uint32_t* sval, long long n) {
     for (long long p = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; p < n;
@@ -199,7 +203,7 @@ struct ProbeArgs {
     EngineCtl ctl;
     JoinHT H;
     int32_t key_col;
-    int32_t pad;
+    int32_t kind;                // tqp_join_kind
     uint2* row_run;              // per probe row: its key's run (first bidx index, length); length 0: no match
     int32_t* out_build;
     int32_t* out_probe;
@@ -279,7 +283,12 @@ struct ProbeBody {
                     }
                     hit = slot_key(s) == key[j];
                 }
-                const uint2 run = hit ? make_uint2(s.z, s.w) : make_uint2(0u, 0u);
+                uint2 run = hit ? make_uint2(s.z, s.w) : make_uint2(0u, 0u);
+                if (A.kind != TQP_JOIN_INNER) {  // one pair (r, -1), or none, for this row
+                    const bool keep = A.kind == TQP_JOIN_LEFT_SEMI ? run.y != 0 : run.y == 0;
+                    if (keep) run = make_uint2(kRunNone, 1u);
+                    else if (A.kind != TQP_JOIN_LEFT_OUTER) run = make_uint2(0u, 0u);
+                }
                 pairs += run.y;
                 A.row_run[v.row0 + r] = run;
             }
@@ -347,9 +356,9 @@ struct ProbeBody {
             unsigned long long pos = running + before + (incl - c);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                if (run[j].x & kRunRow) {  // a unique key: the run is the build row itself
+                if (run[j].x & kRunRow) {  // a unique key: the run is the build row itself (or none: -1)
                     if (run[j].y && pos < static_cast<unsigned long long>(A.capacity)) {
-                        A.out_build[pos] = static_cast<int32_t>(run[j].x & ~kRunRow);
+                        A.out_build[pos] = run[j].x == kRunNone ? -1 : static_cast<int32_t>(run[j].x & ~kRunRow);
                         A.out_probe[pos] = static_cast<int32_t>(r0 + j);
                     }
                     pos += run[j].y;
@@ -390,8 +399,8 @@ __global__ void __launch_bounds__(kEngineThreads, 2) k_join_probe(const __grid_c
 }
 
 tqp_status launch_hash_join(tqp_ctx* ctx, const tqp_table* build, int32_t build_key, const tqp_table* probe,
-                            int32_t probe_key, int32_t* d_build_idx, int32_t* d_probe_idx, int64_t capacity,
-                            int64_t* d_count, cudaStream_t stream) {
+                            int32_t probe_key, int32_t kind, int32_t* d_build_idx, int32_t* d_probe_idx,
+                            int64_t capacity, int64_t* d_count, cudaStream_t stream) {
     JoinHT H;
     TQP_TRY(ht_build(ctx, build, build_key, &H, stream));
     if (probe->num_rows == 0) {
@@ -402,6 +411,7 @@ tqp_status launch_hash_join(tqp_ctx* ctx, const tqp_table* build, int32_t build_
     memset(&A, 0, sizeof(A));
     A.H = H;
     A.key_col = probe_key;
+    A.kind = kind;
     const int es = probe->cols[probe_key].type == TQP_I64 ? 8 : (probe->cols[probe_key].type == TQP_I32 ? 4 : 1);
     const tqp_tuning tu = default_tuning(ctx, es, ProbeBody::kSmemBytes + args_bytes<ProbeArgs>());
     size_t smem = 0;
@@ -437,7 +447,17 @@ using namespace tqp;
 extern "C" tqp_status tqp_hash_join(tqp_ctx* ctx, const tqp_table* build, int32_t build_key, const tqp_table* probe,
                                     int32_t probe_key, int32_t* d_build_idx, int32_t* d_probe_idx, int64_t capacity,
                                     int64_t* d_count, void* stream) {
+    return tqp_hash_join_kind(ctx, build, build_key, probe, probe_key, TQP_JOIN_INNER, d_build_idx, d_probe_idx,
+                              capacity, d_count, stream);
+}
+
+extern "C" tqp_status tqp_hash_join_kind(tqp_ctx* ctx, const tqp_table* build, int32_t build_key,
+                                         const tqp_table* probe, int32_t probe_key, int32_t join_kind,
+                                         int32_t* d_build_idx, int32_t* d_probe_idx, int64_t capacity,
+                                         int64_t* d_count, void* stream) {
     clear_error();
+    if (join_kind < TQP_JOIN_INNER || join_kind > TQP_JOIN_LEFT_OUTER)
+        return fail(TQP_ERR_INVALID_ARG, "join_kind %d is not a tqp_join_kind", join_kind);
     TQP_TRY(check_ctx(ctx));
     TQP_TRY(check_table(build, "tqp_hash_join(build)"));
     TQP_TRY(check_table(probe, "tqp_hash_join(probe)"));
@@ -453,12 +473,12 @@ extern "C" tqp_status tqp_hash_join(tqp_ctx* ctx, const tqp_table* build, int32_
     if (!g.ok) return fail(TQP_ERR_CUDA, "cannot select device %d", ctx->device);
     const cudaStream_t st = static_cast<cudaStream_t>(stream);
     char key[96];
-    snprintf(key, sizeof(key), "hashjoin r%d b%d n%d", rows_class(probe->num_rows),
+    snprintf(key, sizeof(key), "hashjoin%d r%d b%d n%d", join_kind, rows_class(probe->num_rows),
              row_bytes(probe, std::vector<int>{probe_key}), rows_class(build->num_rows));
     auto run = [&]() {
         arena_reset(ctx);
-        return launch_hash_join(ctx, build, build_key, probe, probe_key, d_build_idx, d_probe_idx, capacity,
-                                d_count, st);
+        return launch_hash_join(ctx, build, build_key, probe, probe_key, join_kind, d_build_idx, d_probe_idx,
+                                capacity, d_count, st);
     };
     return tuned(ctx, key, st, true, run);
 }

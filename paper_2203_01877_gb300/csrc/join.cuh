@@ -88,4 +88,24 @@ __device__ __forceinline__ long long ht_find(const JoinHT& H, uint64_t key) {
     return -1;
 }
 
+// The slot of `key` in a probe-ready table (w = 0: no match): the key's own
+// slot when direct-mapped, else the linear probe from its home slot.
+__device__ __forceinline__ uint4 ht_match(const JoinHT& H, bool direct, long long kmin, uint64_t key) {
+    if (direct) {
+        const unsigned long long s = key - static_cast<uint64_t>(kmin);
+        return s < static_cast<unsigned long long>(H.cap) ? __ldg(&H.slots[s]) : make_uint4(0u, 0u, 0u, 0u);
+    }
+    if (key == ~0ULL) return __ldg(&H.slots[H.cap]);  // the all-ones key lives in the extra slot
+    const unsigned long long mask = static_cast<unsigned long long>(H.cap - 1);
+    unsigned long long h = mix64(key) & mask;
+    for (long long i = 0; i < H.cap; ++i) {
+        const uint4 s = __ldg(&H.slots[h]);
+        const uint64_t k = slot_key(s);
+        if (k == key) return s;
+        if (k == ~0ULL) break;
+        h = (h + 1) & mask;
+    }
+    return make_uint4(0u, 0u, 0u, 0u);
+}
+
 }  // namespace tqp

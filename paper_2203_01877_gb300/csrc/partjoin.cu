@@ -25,25 +25,6 @@ __device__ __forceinline__ int64_t pj_prod(const PjFactor (&f)[2], long long r) 
     return static_cast<int64_t>(a * static_cast<uint64_t>(pj_factor(f[1], r)));
 }
 
-// The build slot matching `key` (w = 0: no match), as the fused probe finds it.
-__device__ __forceinline__ uint4 pj_lookup(const JoinHT& H, bool direct, long long kmin, uint64_t key) {
-    if (direct) {
-        const unsigned long long s = key - static_cast<uint64_t>(kmin);
-        return s < static_cast<unsigned long long>(H.cap) ? __ldg(&H.slots[s]) : make_uint4(0u, 0u, 0u, 0u);
-    }
-    if (key == ~0ULL) return __ldg(&H.slots[H.cap]);  // the all-ones key lives in the extra slot
-    const unsigned long long mask = static_cast<unsigned long long>(H.cap - 1);
-    unsigned long long h = mix64(key) & mask;
-    for (long long i = 0; i < H.cap; ++i) {
-        const uint4 s = __ldg(&H.slots[h]);
-        const uint64_t k = slot_key(s);
-        if (k == key) return s;
-        if (k == ~0ULL) break;
-        h = (h + 1) & mask;
-    }
-    return make_uint4(0u, 0u, 0u, 0u);
-}
-
 // A joined row of a key with several build rows: added to each of their groups.
 __device__ __forceinline__ void pj_add_chain(const PartJoinArgs& A, const uint4& s, const int64_t (&v)[kPjVals]) {
     const GroupSpec& S = A.S;
@@ -106,7 +87,7 @@ __global__ void __launch_bounds__(kPjThreads) k_pj_scatter(const __grid_constant
         uint4 sl[kPjRowsPerThread];
 #pragma unroll
         for (int j = 0; j < kPjRowsPerThread; ++j)
-            sl[j] = ok[j] ? pj_lookup(A.H, direct, kmin, key[j]) : make_uint4(0u, 0u, 0u, 0u);
+            sl[j] = ok[j] ? ht_match(A.H, direct, kmin, key[j]) : make_uint4(0u, 0u, 0u, 0u);
         const uint32_t P_u = static_cast<uint32_t>(P);
 #pragma unroll
         for (int j = 0; j < kPjRowsPerThread; ++j) {

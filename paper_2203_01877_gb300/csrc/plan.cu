@@ -20,6 +20,7 @@
 #include "bodies.cuh"
 #include "dimgroups.cuh"
 #include "dim.cuh"
+#include "partjoin.cuh"
 
 namespace tqp {
 
@@ -183,10 +184,159 @@ tqp_status check_prepared(const tqp_ctx* ctx, const tqp_plan* p) {
     return TQP_OK;
 }
 
+// ---- left semi / anti plans ---------------------------------------------------
+// Each passing fact row counts once if it has an equal dim key (semi) / has
+// none (anti), and the rest of the plan reads fact columns only (paper
+// Section 5's left-semi and left-anti joins).  So the join reduces to one
+// more predicate: k_semi_member writes a uint8 membership column (1 = the row
+// passes the plan's predicates and is kept), and the plan runs as a scan plan
+// over the fact columns plus that column, with the single predicate
+// member == 1.
+
+struct SemiArgs {
+    long long n;
+    int32_t ncond;
+    int32_t anti;
+    PjCond cond[TQP_MAX_PREDS];
+    PjCol fk;
+    JoinHT H;
+    uint8_t* member;
+    unsigned long long* acc;  // [0] passing fact rows, [1] finished blocks (zeroed)
+    int64_t* d_num_rows;      // nullable
+};
+
+__global__ void __launch_bounds__(256) k_semi_member(const __grid_constant__ SemiArgs A) {
+    __shared__ unsigned long long part[256 / kWarp];
+    long long kmin = 0;
+    const bool direct = ht_is_direct(A.H, &kmin);
+    unsigned long long passed = 0;
+    for (long long r = blockIdx.x * 256LL + threadIdx.x; r < A.n; r += static_cast<long long>(gridDim.x) * 256) {
+        bool ok = true;
+        for (int q = 0; q < A.ncond; ++q) {
+            const PjCond& cd = A.cond[q];
+            const uint64_t x = static_cast<uint64_t>(ldg_typed(cd.p, cd.type, r));
+            ok = ok && (((x - static_cast<uint64_t>(cd.lo)) <= cd.span) != (cd.negate != 0));
+        }
+        uint8_t m = 0;
+        if (ok) {
+            ++passed;
+            const bool found = ht_match(A.H, direct, kmin, static_cast<uint64_t>(ldg_typed(A.fk.p, A.fk.type, r))).w != 0;
+            m = found != (A.anti != 0) ? 1 : 0;
+        }
+        A.member[r] = m;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) passed += __shfl_xor_sync(0xffffffffu, passed, o);
+    if (threadIdx.x % kWarp == 0) part[threadIdx.x / kWarp] = passed;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    for (int w = 1; w < 256 / kWarp; ++w) passed += part[w];
+    if (passed) atomicAdd(&A.acc[0], passed);
+    __threadfence();
+    if (atomicAdd(&A.acc[1], 1ULL) != static_cast<unsigned long long>(gridDim.x) - 1ULL) return;
+    __threadfence();
+    if (A.d_num_rows) *A.d_num_rows = static_cast<int64_t>(atomicAdd(&A.acc[0], 0ULL));
+}
+
+static tqp_status run_scan_plan(tqp_ctx* ctx, const tqp_plan* p, const tqp_result* r, cudaStream_t stream);
+
+static tqp_status run_semi_anti_plan(tqp_ctx* ctx, const tqp_plan* p, const tqp_result* r, cudaStream_t stream) {
+    const tqp_table* F = p->fact;
+    const tqp_table* D = p->dim;
+    const int nf = F->num_cols;
+    for (int i = 0; i < p->ngc; ++i)
+        if (p->group_cols[i] < 0 || p->group_cols[i] >= nf)
+            return fail(TQP_ERR_INVALID_ARG, "a semi / anti join plan groups by fact columns only");
+    for (int a = 0; a < p->naggs; ++a)
+        if (p->aggs[a].fn != TQP_COUNT && !expr_uses_only(p->aggs[a].expr, 0, nf))
+            return fail(TQP_ERR_INVALID_ARG, "a semi / anti join plan aggregates fact columns only");
+    if (p->has_sum && !expr_uses_only(p->sum_expr, 0, nf))
+        return fail(TQP_ERR_INVALID_ARG, "a semi / anti join plan sums fact columns only");
+    if (nf + 1 > TQP_MAX_COLS) return fail(TQP_ERR_UNSUPPORTED, "a semi / anti join plan takes at most %d fact columns",
+                                           TQP_MAX_COLS - 1);
+    const tqp_dim* pd = p->prepared;
+    if (pd) TQP_TRY(check_prepared(ctx, p));
+    TQP_TRY(check_device_cols(D, std::vector<int>{p->dim_key}, "tqp_run_plan(dim)"));
+    Cond cond[TQP_MAX_PREDS];
+    int ncond = 0;
+    TQP_TRY(lower_preds(F, p->preds, p->npreds, cond, &ncond));
+    std::vector<int> fcols{p->fact_fk};
+    for (int q = 0; q < ncond; ++q) fcols.push_back(cond[q].col);
+    TQP_TRY(check_device_cols(F, fcols, "tqp_run_plan(fact)"));
+
+    // passing fact row ids (before the join) come from the filter kernel
+    const bool ids = p->emit_row_ids && r->d_row_ids;
+    if (ids) {
+        if (!r->d_num_rows) return fail(TQP_ERR_INVALID_ARG, "emit_row_ids needs d_num_rows");
+        TQP_TRY(launch_filter(ctx, F, p->preds, p->npreds, nullptr, nullptr, r->d_row_ids, r->capacity_rows,
+                              r->d_num_rows, stream, nullptr));
+    }
+    JoinHT H;
+    if (pd) {
+        H = pd->H;
+    } else {
+        uint32_t* next = nullptr;
+        TQP_TRY(ht_build_chain(ctx, D, p->dim_key, &H, &next, stream));
+    }
+    const long long n = F->num_rows;
+    uint8_t* member = static_cast<uint8_t*>(arena_alloc(ctx, static_cast<size_t>(std::max<long long>(n, 16))));
+    unsigned long long* acc = static_cast<unsigned long long*>(arena_alloc(ctx, 64));
+    if (!member || !acc) return arena_oom(ctx, static_cast<size_t>(n) + 64);
+    TQP_CUDA(cudaMemsetAsync(acc, 0, 64, stream));
+    SemiArgs A;
+    memset(&A, 0, sizeof(A));
+    A.n = n;
+    A.ncond = ncond;
+    A.anti = p->join_kind == TQP_JOIN_LEFT_ANTI;
+    for (int q = 0; q < ncond; ++q)
+        A.cond[q] = PjCond{static_cast<const unsigned char*>(F->cols[cond[q].col].data), F->cols[cond[q].col].type,
+                           cond[q].negate, cond[q].lo, cond[q].span};
+    A.fk = PjCol{static_cast<const unsigned char*>(F->cols[p->fact_fk].data), F->cols[p->fact_fk].type, 0};
+    A.H = H;
+    A.member = member;
+    A.acc = acc;
+    A.d_num_rows = ids ? nullptr : r->d_num_rows;
+    if (n > 0) {
+        const int blocks = static_cast<int>(std::min<long long>((n + 255) / 256, 8LL * ctx->num_sms));
+        k_semi_member<<<blocks, 256, 0, stream>>>(A);
+        TQP_CUDA(cudaGetLastError());
+    } else if (A.d_num_rows) {
+        TQP_CUDA(cudaMemsetAsync(A.d_num_rows, 0, 8, stream));
+    }
+    // the scan plan over the fact columns and the membership column
+    tqp_column cols[TQP_MAX_COLS];
+    for (int c = 0; c < nf; ++c) cols[c] = F->cols[c];
+    cols[nf] = tqp_column{member, TQP_U8, 0};
+    const tqp_table FM{n, nf + 1, 0, cols};
+    tqp_plan q = *p;
+    q.fact = &FM;
+    q.dim = nullptr;
+    q.prepared = nullptr;
+    q.join_kind = TQP_JOIN_INNER;
+    q.emit_row_ids = 0;
+    q.npreds = 1;
+    q.preds[0] = tqp_pred{nf, TQP_EQ, 1, 0};
+    tqp_result rs = *r;
+    rs.d_row_ids = nullptr;
+    rs.capacity_rows = 0;
+    rs.d_num_rows = r->d_num_joined;  // the scan's passing rows are the kept fact rows
+    rs.d_num_joined = nullptr;
+    return run_scan_plan(ctx, &q, &rs, stream);
+}
+
 static tqp_status run_join_plan(tqp_ctx* ctx, const tqp_plan* p, const tqp_result* r, cudaStream_t stream) {
     const tqp_table* F = p->fact;
     const tqp_table* D = p->dim;
     TQP_TRY(check_table(D, "plan.dim"));
+    if (p->join_kind == TQP_JOIN_LEFT_SEMI || p->join_kind == TQP_JOIN_LEFT_ANTI) {
+        if (p->fact_fk < 0 || p->fact_fk >= F->num_cols) return fail(TQP_ERR_INVALID_ARG, "fact_fk out of range");
+        if (p->dim_key < 0 || p->dim_key >= D->num_cols) return fail(TQP_ERR_INVALID_ARG, "dim_key out of range");
+        return run_semi_anti_plan(ctx, p, r, stream);
+    }
+    if (p->join_kind == TQP_JOIN_LEFT_OUTER)
+        return fail(TQP_ERR_UNSUPPORTED, "left outer joins are for tqp_hash_join_kind; plans take inner, semi, anti");
+    if (p->join_kind != TQP_JOIN_INNER) return fail(TQP_ERR_INVALID_ARG, "join_kind %d is not a tqp_join_kind",
+                                                    p->join_kind);
     const int nf = F->num_cols, nd = D->num_cols;
     if (p->fact_fk < 0 || p->fact_fk >= nf) return fail(TQP_ERR_INVALID_ARG, "fact_fk out of range");
     if (p->dim_key < 0 || p->dim_key >= nd) return fail(TQP_ERR_INVALID_ARG, "dim_key out of range");

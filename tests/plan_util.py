@@ -4,7 +4,7 @@ import numpy as np
 
 def gpu_plan_prepare(fact, preds=(), dim=None, fact_fk=0, dim_key=0, group_cols=(), aggs=(), sum_expr=None,
                      topk=0, topk_agg=0, want_row_ids=False, capacity_groups=None, max_groups=0, dim_ref=None,
-                     prepared=None):
+                     prepared=None, join_kind="inner"):
     """dim_ref: an existing TableRef of `dim` (needed with `prepared`, which was built on it)."""
     import torch
     import paper_2203_01877_gb300 as tqp
@@ -27,7 +27,7 @@ def gpu_plan_prepare(fact, preds=(), dim=None, fact_fk=0, dim_key=0, group_cols=
         "num_joined": torch.full((1,), -7, dtype=torch.int64, device=dev),
     }
     plan = tqp.make_plan(F, preds, D, fact_fk, dim_key, group_cols, aggs, sum_expr, topk, topk_agg,
-                         emit_row_ids=want_row_ids, max_groups=max_groups, prepared=prepared)
+                         emit_row_ids=want_row_ids, max_groups=max_groups, prepared=prepared, join_kind=join_kind)
     res = tqp.make_result(bufs["row_ids"], nf if want_row_ids else 0, bufs["num_rows"], bufs["sum"], bufs["keys"],
                           bufs["ivals"], bufs["fvals"], capg, bufs["num_groups"], bufs["total_groups"],
                           bufs["num_joined"])

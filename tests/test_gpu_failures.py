@@ -79,6 +79,7 @@ def test_expired_wait_in_filter_and_plan_reports_timeout():
     ctx = tqp.Context(0, 512 << 20)
     try:
         ctx.set_tuning(1024, 2, 1)
+        ctx.set_variant(1)  # the fused probe: the join runs through the staged scan engine and its waits
         ctx.set_wait_limit(2)
         _, _, _, st = gpu_filter(ctx, cols, Q6_PREDS, Q6_EXPR)
         assert st == tqp.ERR_TIMEOUT

@@ -132,3 +132,53 @@ def test_hashed_pairs_duplicate_build_keys(ctx):
     wb, wp = oracle.join_pairs(bk, pk[sample])
     assert np.array_equal(wp, np.repeat(np.arange(len(sample)), 10))
     assert np.array_equal(runs[sample].ravel(), wb)
+
+
+@pytest.mark.parametrize("kind", ["inner", "semi", "anti", "left_outer"])
+@pytest.mark.parametrize("case", ["dups", "sparse", "dense_big", "empty_build", "empty_probe"])
+def test_join_kinds_pairs(ctx, kind, case):
+    """tqp_hash_join_kind: the index pairs of every join kind (semi / anti: each kept probe row once with build
+    index -1; left outer: the inner pairs plus each unmatched probe row once with -1), in canonical order,
+    element by element against the oracle."""
+    import torch
+    import paper_2203_01877_gb300 as tqp
+    from tests.gpu_util import up
+    rng = np.random.default_rng(hash((kind, case)) % 2**32)
+    if case == "dups":
+        bk = rng.integers(-50, 50, 20_000).astype(np.int32)
+        pk = rng.integers(-60, 60, 30_000).astype(np.int32)
+    elif case == "sparse":
+        bk = (rng.permutation(40_000).astype(np.int64) * 1_000_003 % 2**31).astype(np.int32)
+        pk = np.where(rng.random(500_000) < 0.7, bk[rng.integers(0, 40_000, 500_000)],
+                      rng.integers(0, 2**31 - 1, 500_000)).astype(np.int32)
+    elif case == "dense_big":
+        dim = datagen.dim_table(150_000, 15_000, seed=21)
+        bk = dim["key"]
+        pk = datagen.probe_table(3_000_000, 165_000, seed=21)["fk"]  # keys 150000.. miss
+    elif case == "empty_build":
+        bk = np.zeros(0, np.int32)
+        pk = rng.integers(0, 100, 10_000).astype(np.int32)
+    else:
+        bk = rng.integers(0, 100, 1_000).astype(np.int32)
+        pk = np.zeros(0, np.int32)
+    wb, wp = oracle.join_pairs(bk, pk, join_kind=kind)
+    cap = max(len(wb), 1)
+    ob = torch.full((cap,), -7, dtype=torch.int32, device="cuda")
+    op = torch.full((cap,), -7, dtype=torch.int32, device="cuda")
+    cnt = torch.full((1,), -7, dtype=torch.int64, device="cuda")
+    tqp.tqp_hash_join_kind(ctx, tqp.TableRef([up(bk)]), 0, tqp.TableRef([up(pk)]), 0, kind, ob, op, cap, cnt)
+    assert ctx.status() == 0
+    k = int(cnt.item())
+    assert k == len(wb)
+    assert np.array_equal(op[:k].cpu().numpy(), wp) and np.array_equal(ob[:k].cpu().numpy(), wb)
+
+
+def test_join_kind_rejected(ctx):
+    import paper_2203_01877_gb300 as tqp
+    from tests.gpu_util import up, zeros
+    import torch
+    x = up(np.arange(10, dtype=np.int32))
+    with pytest.raises(tqp.TqpError) as e:
+        tqp.tqp_hash_join_kind(ctx, tqp.TableRef([x]), 0, tqp.TableRef([x]), 0, 7, zeros(10, torch.int32),
+                               zeros(10, torch.int32), 10, zeros(1, torch.int64))
+    assert e.value.status == tqp.ERR_INVALID_ARG

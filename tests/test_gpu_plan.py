@@ -283,3 +283,64 @@ def test_join_plan_variants(ctx, name):
             compare(got, want, spec)
     finally:
         ctx.set_variant(-1)
+
+
+def _semi_case(kind, n, seed, prepared=False):
+    rng = np.random.default_rng(seed)
+    dk = rng.permutation(60_000)[:20_000].astype(np.int32)  # keys 0..59999, a third present
+    dim = [np.concatenate([dk, dk[:500]]), rng.integers(0, 9, len(dk) + 500).astype(np.int32)]  # some duplicates
+    fk = rng.integers(0, 60_000, n).astype(np.int32)
+    g = rng.integers(0, 40, n).astype(np.int32)
+    v = rng.integers(100, 10_000_000, n).astype(np.int64)
+    q = rng.integers(1, 51, n).astype(np.int32)
+    return dict(fact=[fk, g, v, q], dim=dim, fact_fk=0, dim_key=0, join_kind=kind, preds=[(3, "lt", 40)],
+                group_cols=[1], aggs=[("sum", [("col", 2)]), ("count", None), ("avg", [("col", 2)]),
+                                      ("sum", [("col", 2), ("col", 3), "mul"])],
+                sum_expr=[("col", 2)], want_row_ids=True, capacity_groups=64)
+
+
+@pytest.mark.parametrize("kind", ["semi", "anti"])
+@pytest.mark.parametrize("n", [1, 5_003, 700_001])
+def test_semi_anti_plans(ctx, kind, n):
+    """Left semi / anti join plans: each passing fact row once if it has / has no equal dim key, grouped by a
+    fact column; counts, row ids (before the join), the ungrouped sum and every group against the oracle."""
+    spec = _semi_case(kind, n, n)
+    run_both(ctx, **spec)
+    spec = dict(spec, want_row_ids=False, group_cols=[], aggs=[("count", None)], capacity_groups=1)
+    run_both(ctx, **spec)
+
+
+@pytest.mark.parametrize("kind", ["semi", "anti"])
+def test_semi_anti_topk_and_batched(ctx, kind):
+    """Top-k over a semi / anti join plan, alone and inside a batch of mixed plans (which runs it on the
+    single-plan path): both equal the oracle."""
+    import paper_2203_01877_gb300 as tqp
+    from tests.plan_util import gpu_plan_prepare, gpu_plan_collect
+    spec = dict(_semi_case(kind, 300_007, 9), topk=7, topk_agg=0, capacity_groups=7, want_row_ids=False)
+    run_both(ctx, **spec)
+    inner = dict(spec, join_kind="inner", group_cols=[5], aggs=[("sum", [("col", 2)]), ("count", None)],
+                 sum_expr=None, topk=0, capacity_groups=64)
+    specs = [spec, inner, dict(spec, join_kind="anti" if kind == "semi" else "semi")]
+    prepared = [gpu_plan_prepare(**s) for s in specs]
+    tqp.tqp_run_plans(ctx, [x[0] for x in prepared], [x[1] for x in prepared])
+    st = ctx.status()
+    for s, x in zip(specs, prepared):
+        got = gpu_plan_collect(x[2], x[4])
+        got["status"] = st
+        o = {k: v for k, v in s.items() if k not in ("capacity_groups",)}
+        want = oracle.run_plan(want_pairs=False, cap_groups=None, **o)
+        compare(got, want, s)
+
+
+def test_semi_anti_plan_rules(ctx):
+    import paper_2203_01877_gb300 as tqp
+    from tests.plan_util import gpu_plan_prepare
+    spec = _semi_case("semi", 1000, 3)
+    plan, res, bufs, keep, shape = gpu_plan_prepare(**dict(spec, group_cols=[5]))  # a dim column
+    with pytest.raises(tqp.TqpError) as e:
+        tqp.tqp_run_plan(ctx, plan, res)
+    assert e.value.status == tqp.ERR_INVALID_ARG
+    plan, res, bufs, keep, shape = gpu_plan_prepare(**dict(spec, join_kind="left_outer"))
+    with pytest.raises(tqp.TqpError) as e:
+        tqp.tqp_run_plan(ctx, plan, res)
+    assert e.value.status == tqp.ERR_UNSUPPORTED

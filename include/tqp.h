@@ -447,8 +447,11 @@ TQP_API tqp_status tqp_batch_destroy(tqp_batch* batch);
  * Each slot has its own stream and its own share of a scratch budget taken
  * from a long-lived region of the context's arena: a batch is admitted only
  * if its scratch (hash tables, selection masks, group tables) fits the share
- * (admission by free HBM budget; an oversized batch is split, a single plan
- * that does not fit completes with TQP_ERR_OUT_OF_MEMORY).  Results are
+ * (an oversized batch is split).  A single plan that does not fit its share
+ * is admitted by the device's free memory: when cudaMemGetInfo shows room for
+ * its scratch with 1 GiB to spare, it runs in a region taken from the
+ * stream-ordered allocator on the slot's stream (released there when it
+ * retires); otherwise it completes with TQP_ERR_OUT_OF_MEMORY.  Results are
  * identical to tqp_run_plan of each plan alone.
  *   max_batch     plans per batch (1 = one query at a time)
  *   max_inflight  batches on the device at once (1..8)

@@ -10,6 +10,16 @@
 // event, so new plans are admitted while earlier batches still run.  Each
 // slot latches device errors in a word of its own, so a failing batch marks
 // only its own requests.
+//
+// Admission by free HBM: a single plan whose scratch exceeds the slot's share
+// of the budget is not refused while the device has room for it.  The
+// dispatcher reads the free device memory (cudaMemGetInfo) and, if the plan's
+// scratch fits with kHbmReserve to spare, gives the plan a scratch region of
+// its own from the stream-ordered allocator (cudaMallocAsync on the slot's
+// stream; freed on that stream when the batch retires), growing it while the
+// plan still reports a shortfall and the device still has room.  Only then
+// does the plan complete with TQP_ERR_OUT_OF_MEMORY.
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -42,7 +52,11 @@ struct Slot {
     std::vector<Req> reqs;     // the batch in flight
     bool busy = false;
     tqp_status launch_status = TQP_OK;
+    void* overflow = nullptr;  // scratch of a plan larger than the share (freed at retire)
 };
+
+// Device memory kept free when a plan's scratch is taken from free HBM.
+constexpr size_t kHbmReserve = size_t(1) << 30;
 
 }  // namespace
 
@@ -90,7 +104,43 @@ static void retire(tqp_server* s, Slot& sl) {
         cudaMemset(sl.sub.d_err, 0, sizeof(int));
     }
     complete(s, sl.reqs, st, t);
+    if (sl.overflow) {
+        cudaFreeAsync(sl.overflow, sl.st);
+        sl.overflow = nullptr;
+    }
     sl.busy = false;
+}
+
+// One plan that does not fit the slot's share: run it in scratch taken from
+// free HBM when the device has room (see the file comment).  Returns the
+// plan's status (TQP_ERR_OUT_OF_MEMORY when the device has no room either).
+static tqp_status launch_overflow(Slot& sl, const tqp_plan* plan, const tqp_result* res) {
+    size_t need = std::max<size_t>(2 * sl.sub.used, size_t(16) << 20);
+    for (int attempt = 0; attempt < 6; ++attempt) {
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return TQP_ERR_CUDA;
+        if (need + kHbmReserve > free_b) break;
+        void* buf = nullptr;
+        if (cudaMallocAsync(&buf, need, sl.st) != cudaSuccess) {
+            cudaGetLastError();
+            break;
+        }
+        tqp_ctx ov = sl.sub;  // the slot's context over the new region, reporting into the slot's error word
+        ov.arena = static_cast<unsigned char*>(buf);
+        ov.arena_bytes = need;
+        ov.owns_arena = false;
+        ov.used = kPersistentBytes;
+        ov.top = need;
+        ov.live_regions = 0;
+        const tqp_status st = run_plans_on(&ov, plan, res, 1, sl.st);
+        if (st != TQP_ERR_OUT_OF_MEMORY) {
+            sl.overflow = buf;
+            return st;
+        }
+        cudaFreeAsync(buf, sl.st);
+        need = std::max(2 * need, 2 * ov.used);
+    }
+    return fail(TQP_ERR_OUT_OF_MEMORY, "plan scratch exceeds the slot's share and the device's free memory");
 }
 
 // Launch the first plans of `take` that fit the slot; the rest go back to the
@@ -112,6 +162,7 @@ static void launch(tqp_server* s, Slot& sl, std::vector<Req>& take) {
             n = (n + 1) / 2;  // nothing was launched yet: admit fewer plans
             continue;
         }
+        if (st == TQP_ERR_OUT_OF_MEMORY) st = launch_overflow(sl, plans.data(), res.data());
         break;
     }
     if (n < take.size()) {

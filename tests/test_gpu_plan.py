@@ -316,10 +316,11 @@ def test_semi_anti_topk_and_batched(ctx, kind):
     single-plan path): both equal the oracle."""
     import paper_2203_01877_gb300 as tqp
     from tests.plan_util import gpu_plan_prepare, gpu_plan_collect
-    spec = dict(_semi_case(kind, 300_007, 9), topk=7, topk_agg=0, capacity_groups=7, want_row_ids=False)
+    spec = dict(_semi_case(kind, 300_007, 9), topk=7, topk_agg=0, capacity_groups=7, max_groups=64,
+                want_row_ids=False)
     run_both(ctx, **spec)
     inner = dict(spec, join_kind="inner", group_cols=[5], aggs=[("sum", [("col", 2)]), ("count", None)],
-                 sum_expr=None, topk=0, capacity_groups=64)
+                 sum_expr=None, topk=0, capacity_groups=64, max_groups=0)
     specs = [spec, inner, dict(spec, join_kind="anti" if kind == "semi" else "semi")]
     prepared = [gpu_plan_prepare(**s) for s in specs]
     tqp.tqp_run_plans(ctx, [x[0] for x in prepared], [x[1] for x in prepared])
@@ -327,7 +328,7 @@ def test_semi_anti_topk_and_batched(ctx, kind):
     for s, x in zip(specs, prepared):
         got = gpu_plan_collect(x[2], x[4])
         got["status"] = st
-        o = {k: v for k, v in s.items() if k not in ("capacity_groups",)}
+        o = {k: v for k, v in s.items() if k not in ("capacity_groups", "max_groups")}
         want = oracle.run_plan(want_pairs=False, cap_groups=None, **o)
         compare(got, want, s)
 

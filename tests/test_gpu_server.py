@@ -1,9 +1,9 @@
 """GPU: the serving loop (tqp_server_*).  Mixed queries over seeded row ranges
 of a resident fact table and a prepared dimension arrive with seeded random
 gaps; every result must equal the same plan run alone (byte for byte), a
-sample also equals the oracle, one-at-a-time mode gives the same, and the
-HBM-budget admission splits batches and refuses a plan that alone does not
-fit its slot."""
+sample also equals the oracle, one-at-a-time mode gives the same, the
+budget admission splits batches, and a plan that alone does not fit its slot
+runs in scratch taken from the device's free memory."""
 import time
 
 import numpy as np
@@ -168,8 +168,15 @@ def test_server_one_at_a_time_and_admission(world):
     assert max(c[2] for c in done2.values()) > 1
     for i in range(len(qs)):
         assert torch.equal(outputs(torch, made2[i][2]), got1[i])
-    # a plan that alone exceeds its slot is refused, the others still run
+    # a plan that alone exceeds its slot's share runs in scratch taken from free HBM (admission by free
+    # device memory); its result is the oracle's, and the others still run in the slots
     big = [(2, 0, 100_000)] + [q for q in qs if q[0] != 2][:5]  # a join builds a ~4 MB table
     made3, done3 = run_server(tqp, torch, world, big, None, 8, 2, 2 << 20, None)
-    assert done3[0][1] == tqp.ERR_OUT_OF_MEMORY
-    assert all(done3[i][1] == 0 for i in range(1, len(big)))
+    assert all(done3[i][1] == 0 for i in range(len(big))), sorted((k, c[1]) for k, c in done3.items())
+    from tests.plan_util import gpu_plan_collect
+    plan, res, bufs, T, ospec, shape = made3[0]
+    got0 = gpu_plan_collect(bufs, shape)
+    got0["status"] = 0
+    want0 = oracle.run_plan(want_pairs=False, cap_groups=None,
+                            **{k: v for k, v in ospec.items() if k != "capacity_groups"})
+    compare(got0, want0, ospec)

@@ -165,12 +165,17 @@ TQP_API size_t tqp_ctx_arena_bytes(const tqp_ctx* ctx);
 TQP_API tqp_status tqp_ctx_set_tuning(tqp_ctx* ctx, int32_t tile_rows, int32_t stages, int32_t ctas_per_sm);
 
 /* Force the algorithm of operators that have two, for this context's calls
- * (results never depend on it): grouped join plans with at least 2^20 fact
- * rows aggregate either with the radix-partitioned kernels (0: the probe side
- * is partitioned by group, each partition aggregated in shared memory) or
- * with the fused probe (1: every joined row added to its key's or group's
- * accumulators with L2 reductions).  -1 restores the default (0, or the
- * autotuner's choice).  Errors: TQP_ERR_INVALID_ARG. */
+ * (results never depend on it):
+ *   tqp_hash_join / tqp_hash_join_kind: 0 = the open-addressing hash table
+ *     (paper Section 5.3's hash join), 1 = the sort-based join (Section 5.2,
+ *     Algorithm 1: the build keys are radix-sorted with their rows and each
+ *     probe key is bucketized into them);
+ *   grouped join plans with at least 2^20 fact rows: 0 = the radix-partitioned
+ *     aggregation (the probe side partitioned by group, each partition
+ *     aggregated in shared memory), 1 = the fused probe (every joined row
+ *     added to its key's or group's accumulators with L2 reductions).
+ * -1 restores the default (0, or the autotuner's choice, which times both).
+ * Errors: TQP_ERR_INVALID_ARG. */
 TQP_API tqp_status tqp_ctx_set_variant(tqp_ctx* ctx, int32_t variant);
 
 /* Autotuning: with it on, the first call of each shape class (operator, log2

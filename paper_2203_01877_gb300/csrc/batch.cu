@@ -64,7 +64,7 @@ struct FillRange {
 };
 
 struct BuildJob {
-    JoinHT H;
+    JoinHT H{};
     uint32_t* next;
     const unsigned char* key_col;
     int32_t key_type;
@@ -126,7 +126,7 @@ struct TopJob {
 // The fold of a join that aggregated by join key first (blocks
 // [first_block, first_block + nblocks) of its launch).
 struct FoldJob {
-    JoinHT H;
+    JoinHT H{};
     const unsigned char* dkey;
     int32_t dkey_type;
     int32_t nk;

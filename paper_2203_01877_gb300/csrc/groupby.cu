@@ -386,6 +386,9 @@ bool lower_group_direct(const tqp_table* t, const GroupArgs& A, long long max_gr
     return lane_bytes <= kDirLaneBytes;
 }
 
+tqp_status launch_sort_agg(tqp_ctx* ctx, const tqp_table* t, const Cond* cond, int ncond, GroupSpec* S,
+                           long long cap_groups, cudaStream_t stream);
+
 tqp_status launch_groupby(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* preds, int32_t npreds,
                           const int32_t* group_cols, int32_t ngc, const tqp_agg* aggs, int32_t naggs,
                           int64_t* d_keys, int64_t* d_ivals, double* d_fvals, int64_t capacity_groups,
@@ -426,6 +429,15 @@ tqp_status launch_groupby(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* pred
     lower_fast(A.cond, A.ncond, A.G, A.cf, &A.fast);
     lower_group_fast(&A);
 
+    // variant 1: the sort-based aggregation (Algorithm 3), timed against this path by the autotuner
+    if (ngc > 0 && tuned_variant(ctx) == 1) {
+        GroupOut O{d_keys, d_ivals, d_fvals, capacity_groups, d_num_groups, ctx->d_err};
+        if (topk > 0 && topk_agg >= 0 && topk_agg < naggs && (aggs[topk_agg].fn == TQP_MIN || aggs[topk_agg].fn == TQP_MAX))
+            return fail(TQP_ERR_UNSUPPORTED, "top-k by a MIN/MAX aggregate is not supported");
+        TQP_TRY(launch_sort_agg(ctx, t, A.cond, A.ncond, &A.S, std::max<long long>(max_groups, 1), stream));
+        if (topk > 0) return group_topk(ctx, A.S, O, topk, topk_agg, d_total_groups, stream);
+        return group_finalize(ctx, A.S, O, stream);
+    }
     GroupDirectArgs D;
     const bool direct = lower_group_direct(t, A, max_groups, &D);
     // shapes that are rejected anyway are rejected before any scratch or device work
@@ -533,5 +545,5 @@ extern "C" tqp_status tqp_groupby_agg(tqp_ctx* ctx, const tqp_table* t, const tq
         return launch_groupby(ctx, t, preds, npreds, group_cols, ngc, aggs, naggs, d_keys, d_ivals, d_fvals,
                               capacity_groups, d_num_groups, st, capacity_groups, 0, 0, nullptr);
     };
-    return tuned(ctx, key, st, false, run);
+    return tuned(ctx, key, st, ngc > 0 ? (kTuneVariant | kTuneV1Shapeless) : 0, run);
 }

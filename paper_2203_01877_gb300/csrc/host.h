@@ -146,6 +146,8 @@ int tuned_variant(const tqp_ctx* ctx);
 // What a tuned call's candidates vary besides the scan launch shape.
 constexpr int kTuneHt = 1;       // the hash-table load factor
 constexpr int kTuneVariant = 2;  // the operator's algorithm variant (0 or 1)
+constexpr int kTuneV0Shapeless = 4;  // variant 0 does not use the scan launch shape (time one of them)
+constexpr int kTuneV1Shapeless = 8;  // variant 1 does not use the scan launch shape
 
 // Run `run` (a whole operator call, idempotent) under the tuning of shape
 // class `key`: with autotuning on and `key` new, every candidate launch shape

@@ -196,12 +196,92 @@ tqp_status ht_build(tqp_ctx* ctx, const tqp_table* build, int32_t key_col, JoinH
     return TQP_OK;
 }
 
+// ---- sort-based build (paper Section 5.2, Algorithm 1) ---------------------------
+// The build keys (minus their minimum) are radix-sorted with their rows; the
+// probe bucketizes each key into the sorted keys through a radix directory
+// over the key range (the top bits of key - min select a bucket, a binary
+// search within the bucket finds the run).  The sorted rows are the build
+// rows of each key in ascending order, as the canonical output wants.
+
+__global__ void k_sj_keys(const long long* meta, const unsigned char* key_col, int key_type, long long n,
+                          uint64_t* skey, uint32_t* sval) {
+    const long long kmin = __ldg(&meta[0]);
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        skey[i] = static_cast<uint64_t>(ldg_typed(key_col, key_type, i)) - static_cast<uint64_t>(kmin);
+        sval[i] = static_cast<uint32_t>(i);
+    }
+}
+
+// meta[2] = bucket shift: the key range's bit length beyond log2(nbuckets).
+__global__ void k_sj_shift(long long* meta, int dir_bits) {
+    const unsigned long long range = static_cast<unsigned long long>(meta[1]) - static_cast<unsigned long long>(meta[0]);
+    const int bits = range ? 64 - __clzll(static_cast<long long>(range)) : 0;
+    meta[2] = bits > dir_bits ? bits - dir_bits : 0;
+}
+
+// sdir[b] = the first sorted index whose key lies in bucket >= b.
+__global__ void k_sj_dir(const long long* meta, const uint64_t* skey, long long n, uint32_t* sdir, long long nb) {
+    const int sh = static_cast<int>(__ldg(&meta[2]));
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i <= n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const long long b_i = i < n ? static_cast<long long>(skey[i] >> sh) : nb;
+        const long long b_p = i > 0 ? static_cast<long long>(skey[i - 1] >> sh) : -1;
+        for (long long b = b_p + 1; b <= b_i && b <= nb; ++b) sdir[b] = static_cast<uint32_t>(i);
+    }
+}
+
+tqp_status ht_build_sorted(tqp_ctx* ctx, const tqp_table* build, int32_t key_col, JoinHT* H, cudaStream_t stream) {
+    const long long n = build->num_rows;
+    const long long nn = n > 0 ? n : 1;
+    int dir_bits = 1;
+    while ((1LL << dir_bits) < nn) ++dir_bits;
+    const long long nb = 1LL << dir_bits;
+    unsigned char* sb = static_cast<unsigned char*>(arena_alloc(ctx, 2 * (static_cast<size_t>(nn) * 12 + 256)));
+    void* rs = arena_alloc(ctx, radix_sort_scratch(nn));
+    long long* d_n = static_cast<long long*>(arena_alloc(ctx, 256));
+    long long* meta = static_cast<long long*>(arena_alloc(ctx, 64));
+    uint32_t* sdir = static_cast<uint32_t*>(arena_alloc(ctx, static_cast<size_t>(nb + 1) * 4));
+    if (!sb || !rs || !d_n || !meta || !sdir)
+        return arena_oom(ctx, 2 * (static_cast<size_t>(nn) * 12 + 256) + radix_sort_scratch(nn) + (nb + 1) * 4 + 512);
+    memset(H, 0, sizeof(*H));
+    H->cap = 0;
+    H->meta = meta;
+    H->nbuild = n;
+    H->nbuckets = nb;
+    H->sdir = sdir;
+    TQP_TRY(ht_key_range_launch(ctx, build, key_col, meta, stream));
+    uint64_t* k0 = reinterpret_cast<uint64_t*>(sb);
+    uint64_t* k1 = k0 + nn;
+    uint32_t* v0 = reinterpret_cast<uint32_t*>(k1 + nn);
+    uint32_t* v1 = v0 + nn;
+    H->skeys = k0;
+    H->bidx = v0;
+    if (n == 0) return TQP_OK;
+    const tqp_column& kc = build->cols[key_col];
+    const int threads = 256;
+    const int blocks = static_cast<int>(std::min<long long>((n + threads - 1) / threads, ctx->num_sms * 16LL));
+    k_sj_keys<<<blocks, threads, 0, stream>>>(meta, static_cast<const unsigned char*>(kc.data), kc.type, n, k0, v0);
+    k_sj_shift<<<1, 1, 0, stream>>>(meta, dir_bits);
+    TQP_CUDA(cudaGetLastError());
+    TQP_TRY(set_device_i64(d_n, n, stream));
+    bool in1 = false;
+    // key - min fits 32 bits for 32- and 8-bit key columns
+    TQP_TRY(radix_sort_pairs(k0, v0, k1, v1, d_n, n, 0, kc.type == TQP_I64 ? 64 : 32, rs, stream, &in1));
+    H->skeys = in1 ? k1 : k0;
+    H->bidx = in1 ? v1 : v0;
+    const int dblocks = static_cast<int>(std::min<long long>((n + threads) / threads, ctx->num_sms * 16LL));
+    k_sj_dir<<<dblocks, threads, 0, stream>>>(meta, H->skeys, n, sdir, nb);
+    TQP_CUDA(cudaGetLastError());
+    return TQP_OK;
+}
+
 // ---- probe with pair output ----------------------------------------------------
 
 struct ProbeArgs {
     ScanGeom G;
     EngineCtl ctl;
-    JoinHT H;
+    JoinHT H{};
     int32_t key_col;
     int32_t kind;                // tqp_join_kind
     uint2* row_run;              // per probe row: its key's run (first bidx index, length); length 0: no match
@@ -241,6 +321,25 @@ struct ProbeBody {
         long long kmin = 0;
         const bool direct = ht_is_direct(H, &kmin);
         unsigned long long pairs = 0;
+        if (H.skeys) {  // sort-based table: bucketize each key into the sorted build keys
+            for (int base = cw * rw; base < cw * rw + rw; base += kWarp) {
+                const int r = base + lane;
+                if (base >= v.rows) break;
+                if (r >= v.rows) continue;
+                uint2 run = sj_lookup(H, static_cast<uint64_t>(col_val(G, v, A.key_col, r)));
+                if (A.kind != TQP_JOIN_INNER) {
+                    const bool keep = A.kind == TQP_JOIN_LEFT_SEMI ? run.y != 0 : run.y == 0;
+                    if (keep) run = make_uint2(kRunNone, 1u);
+                    else if (A.kind != TQP_JOIN_LEFT_OUTER) run = make_uint2(0u, 0u);
+                }
+                pairs += run.y;
+                A.row_run[v.row0 + r] = run;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
+            if (lane == 0) chunk_pairs += pairs;
+            return;
+        }
         for (int base = cw * rw; base < cw * rw + rw; base += 4 * kWarp) {
             if (base >= v.rows) break;
             uint64_t key[4];
@@ -401,8 +500,10 @@ __global__ void __launch_bounds__(kEngineThreads, 2) k_join_probe(const __grid_c
 tqp_status launch_hash_join(tqp_ctx* ctx, const tqp_table* build, int32_t build_key, const tqp_table* probe,
                             int32_t probe_key, int32_t kind, int32_t* d_build_idx, int32_t* d_probe_idx,
                             int64_t capacity, int64_t* d_count, cudaStream_t stream) {
-    JoinHT H;
-    TQP_TRY(ht_build(ctx, build, build_key, &H, stream));
+    JoinHT H{};
+    // variant 1: the sort-based join; 0: the hash table (the autotuner times both)
+    if (tuned_variant(ctx) == 1) TQP_TRY(ht_build_sorted(ctx, build, build_key, &H, stream));
+    else TQP_TRY(ht_build(ctx, build, build_key, &H, stream));
     if (probe->num_rows == 0) {
         TQP_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int64_t), stream));
         return TQP_OK;
@@ -480,5 +581,5 @@ extern "C" tqp_status tqp_hash_join_kind(tqp_ctx* ctx, const tqp_table* build, i
         return launch_hash_join(ctx, build, build_key, probe, probe_key, join_kind, d_build_idx, d_probe_idx,
                                 capacity, d_count, st);
     };
-    return tuned(ctx, key, st, true, run);
+    return tuned(ctx, key, st, kTuneHt | kTuneVariant, run);
 }

@@ -22,6 +22,15 @@ struct JoinHT {
     // collisions (dense surrogate keys, the usual star-schema build side).
     // nullptr: hashed.
     const long long* meta;
+    // Sort-based form (paper Section 5.2, Algorithm 1: sort, then bucketize):
+    // the build keys minus min, sorted ascending (skeys; bidx holds their rows
+    // in the same order, ascending within a key), and a directory over the
+    // key range: bucket b = (key - min) >> meta[2] starts at sorted index
+    // sdir[b] (sdir has nbuckets + 1 entries).  skeys == nullptr: a hash table.
+    const uint64_t* skeys;
+    const uint32_t* sdir;
+    long long nbuild;
+    long long nbuckets;
 };
 
 // Direct-mapped?  (and the key offset).  Uniform across the grid.
@@ -86,6 +95,31 @@ __device__ __forceinline__ long long ht_find(const JoinHT& H, uint64_t key) {
         h = (h + 1) & static_cast<unsigned long long>(H.cap - 1);
     }
     return -1;
+}
+
+// The run of `key` in a sort-based table: (first sorted index, length); length
+// 0 when absent.  Equal keys share a bucket, so the run lies within it.
+__device__ __forceinline__ uint2 sj_lookup(const JoinHT& H, uint64_t key) {
+    if (H.nbuild == 0) return make_uint2(0u, 0u);
+    const long long lo_k = __ldg(&H.meta[0]), hi_k = __ldg(&H.meta[1]);
+    const uint64_t e = key - static_cast<uint64_t>(lo_k);
+    if (e > static_cast<uint64_t>(hi_k) - static_cast<uint64_t>(lo_k)) return make_uint2(0u, 0u);
+    const uint64_t b = e >> __ldg(&H.meta[2]);
+    uint32_t lo = __ldg(&H.sdir[b]), hi = __ldg(&H.sdir[b + 1]);
+    const uint32_t end = hi;
+    while (lo < hi) {  // first key >= e
+        const uint32_t mid = (lo + hi) >> 1;
+        if (__ldg(&H.skeys[mid]) < e) lo = mid + 1;
+        else hi = mid;
+    }
+    uint32_t last = lo;
+    hi = end;
+    while (last < hi) {  // first key > e
+        const uint32_t mid = (last + hi) >> 1;
+        if (__ldg(&H.skeys[mid]) <= e) last = mid + 1;
+        else hi = mid;
+    }
+    return make_uint2(lo, last - lo);
 }
 
 // The slot of `key` in a probe-ready table (w = 0: no match): the key's own

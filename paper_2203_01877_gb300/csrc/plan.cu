@@ -199,7 +199,7 @@ struct SemiArgs {
     int32_t anti;
     PjCond cond[TQP_MAX_PREDS];
     PjCol fk;
-    JoinHT H;
+    JoinHT H{};
     uint8_t* member;
     unsigned long long* acc;  // [0] passing fact rows, [1] finished blocks (zeroed)
     int64_t* d_num_rows;      // nullable
@@ -271,7 +271,7 @@ static tqp_status run_semi_anti_plan(tqp_ctx* ctx, const tqp_plan* p, const tqp_
         TQP_TRY(launch_filter(ctx, F, p->preds, p->npreds, nullptr, nullptr, r->d_row_ids, r->capacity_rows,
                               r->d_num_rows, stream, nullptr));
     }
-    JoinHT H;
+    JoinHT H{};
     if (pd) {
         H = pd->H;
     } else {
@@ -367,7 +367,7 @@ static tqp_status run_join_plan(tqp_ctx* ctx, const tqp_plan* p, const tqp_resul
                               r->d_num_rows, stream, nullptr));
     }
 
-    JoinHT H;
+    JoinHT H{};
     uint32_t* next = nullptr;
     if (pd) {
         H = pd->H;
@@ -704,6 +704,7 @@ extern "C" tqp_status tqp_run_plan(tqp_ctx* ctx, const tqp_plan* plan, const tqp
     auto run = [&]() { return run_plan_one(ctx, plan, res, st); };
     int opts = 0;
     if (plan->dim && !plan->prepared) opts |= kTuneHt;
-    if (plan->dim && (plan->ngc > 0 || plan->naggs > 0) && plan->fact->num_rows >= kPartJoinMinRows) opts |= kTuneVariant;
+    if (plan->dim && (plan->ngc > 0 || plan->naggs > 0) && plan->fact->num_rows >= kPartJoinMinRows)
+        opts |= kTuneVariant | kTuneV0Shapeless;
     return tuned(ctx, key, st, opts, run);
 }

@@ -87,7 +87,8 @@ tqp_status tuned_call(tqp_ctx* ctx, const char* key, cudaStream_t stream, int op
             for (int C = 1; C <= 2; ++C)
                 for (int H = 1; H <= hts; ++H) {
                     // variant 0 of a two-variant operator does not use the scan launch shape
-                    if (nvar > 1 && V == 0 && (T != kRowQuantum || S != 2 || C != 1)) continue;
+                    const bool shapeless = ((opts & kTuneV0Shapeless) && V == 0) || ((opts & kTuneV1Shapeless) && V == 1);
+                    if (shapeless && (T != kRowQuantum || S != 2 || C != 1)) continue;
                     ctx->forced = tqp_tuning{T, S, C, H, V};
                     if (run(arg) != TQP_OK) continue;  // infeasible (shared memory): refused on the host
                     cudaEventRecord(ev[0], stream);

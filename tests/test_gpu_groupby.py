@@ -244,3 +244,51 @@ def test_min_max_unsupported_shapes(ctx):
     with pytest.raises(tqp.TqpError) as e:  # many groups: not the direct kernel
         gpu_groupby(ctx, cols, [], [1, 2], [("min", [("col", 4)])], capacity=4096)
     assert e.value.status == tqp.ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("case", ["q1", "many_groups", "int64_keys", "three_keys", "min_max", "none_pass"])
+def test_sort_based_aggregation(ctx, case):
+    """The sort-based group-by (variant 1: rows sorted by packed group key, runs of equal keys aggregated, paper
+    Section 5.4 Algorithm 3) gives the oracle's groups, keys ascending, element by element."""
+    rng = np.random.default_rng(len(case))
+    n = 400_003
+    if case == "q1":
+        cols, preds, gc, aggs = q1_cols(n, 5), [(0, "le", 2450)], [1, 2], Q1_AGGS
+    elif case == "many_groups":
+        g = rng.integers(0, 60_000, n).astype(np.int32)
+        v = rng.integers(-10**9, 10**9, n).astype(np.int64)
+        cols, preds, gc, aggs = [g, v], [(1, "gt", -9 * 10**8)], [0], [("sum", [("col", 1)]), ("count", None),
+                                                                        ("avg", [("col", 1)])]
+    elif case == "int64_keys":
+        k = rng.choice(np.array([np.iinfo(np.int64).min, -5, 0, 3, 2**40, np.iinfo(np.int64).max]), n)
+        v = rng.integers(0, 1000, n).astype(np.int64)
+        cols, preds, gc, aggs = [k.astype(np.int64), v], [], [0], [("sum", [("col", 1)]), ("count", None)]
+    elif case == "three_keys":
+        a = rng.integers(-3, 3, n).astype(np.int32)
+        b = rng.integers(0, 4, n).astype(np.uint8)
+        c = rng.integers(-2, 2, n).astype(np.int32)
+        v = rng.integers(0, 100, n).astype(np.int64)
+        cols, preds, gc, aggs = [a, b, c, v], [(3, "ne", 50)], [0, 1, 2], [("sum", [("col", 3)]), ("count", None)]
+    elif case == "min_max":
+        g = rng.integers(0, 5_000, n).astype(np.int32)
+        v = rng.integers(-10**12, 10**12, n).astype(np.int64)
+        cols, preds, gc, aggs = [g, v], [], [0], [("min", [("col", 1)]), ("max", [("col", 1)]), ("count", None)]
+    else:
+        cols, preds, gc, aggs = q1_cols(n, 6), [(0, "gt", 99_999)], [1, 2], Q1_AGGS
+    try:
+        ctx.set_variant(1)
+        check(ctx, cols, preds, gc, aggs, capacity=65_536)
+    finally:
+        ctx.set_variant(-1)
+
+
+def test_sort_based_aggregation_capacity(ctx):
+    """More groups than the bound: TQP_ERR_CAPACITY and a group count of -1, as the hash aggregation reports."""
+    import paper_2203_01877_gb300 as tqp
+    g = np.arange(10_000, dtype=np.int32)
+    try:
+        ctx.set_variant(1)
+        st, G, _, _, _ = gpu_groupby(ctx, [g], [], [0], [("count", None)], capacity=1000)
+    finally:
+        ctx.set_variant(-1)
+    assert st == tqp.ERR_CAPACITY and G == -1

@@ -182,3 +182,46 @@ def test_join_kind_rejected(ctx):
         tqp.tqp_hash_join_kind(ctx, tqp.TableRef([x]), 0, tqp.TableRef([x]), 0, 7, zeros(10, torch.int32),
                                zeros(10, torch.int32), 10, zeros(1, torch.int64))
     assert e.value.status == tqp.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("kind", ["inner", "left_outer", "semi"])
+@pytest.mark.parametrize("case", ["dups", "sparse", "dense_big", "extremes", "empty_build"])
+def test_sort_based_join(ctx, kind, case):
+    """The sort-based join (variant 1: build keys radix-sorted, probe keys bucketized into them, paper Section
+    5.2 Algorithm 1) gives the same canonical pairs as the oracle for every shape the hash table handles."""
+    import torch
+    import paper_2203_01877_gb300 as tqp
+    from tests.gpu_util import up
+    rng = np.random.default_rng(hash(("sort", kind, case)) % 2**32)
+    if case == "dups":
+        bk = rng.integers(-50, 50, 20_000).astype(np.int32)
+        pk = rng.integers(-60, 60, 30_000).astype(np.int32)
+    elif case == "sparse":
+        bk = (rng.permutation(40_000).astype(np.int64) * 1_000_003 % 2**31).astype(np.int32)
+        pk = np.where(rng.random(500_000) < 0.7, bk[rng.integers(0, 40_000, 500_000)],
+                      rng.integers(0, 2**31 - 1, 500_000)).astype(np.int32)
+    elif case == "dense_big":
+        dim = datagen.dim_table(150_000, 15_000, seed=22, dup=3)
+        bk = dim["key"]
+        pk = datagen.probe_table(2_000_000, 51_000, seed=22)["fk"]
+    elif case == "extremes":
+        big = np.iinfo(np.int64)
+        bk = np.array([big.min, -1, 0, 1, big.max, 7, 7, -1, 2**40] * 40, np.int64)
+        pk = np.array([big.max, big.min, -1, 5, 7, 2**40, 0, -2] * 90, np.int64)
+    else:
+        bk = np.zeros(0, np.int32)
+        pk = rng.integers(0, 100, 10_000).astype(np.int32)
+    wb, wp = oracle.join_pairs(bk, pk, join_kind=kind)
+    cap = max(len(wb), 1)
+    ob = torch.full((cap,), -7, dtype=torch.int32, device="cuda")
+    op = torch.full((cap,), -7, dtype=torch.int32, device="cuda")
+    cnt = torch.full((1,), -7, dtype=torch.int64, device="cuda")
+    try:
+        ctx.set_variant(1)
+        tqp.tqp_hash_join_kind(ctx, tqp.TableRef([up(bk)]), 0, tqp.TableRef([up(pk)]), 0, kind, ob, op, cap, cnt)
+        assert ctx.status() == 0
+    finally:
+        ctx.set_variant(-1)
+    k = int(cnt.item())
+    assert k == len(wb)
+    assert np.array_equal(op[:k].cpu().numpy(), wp) and np.array_equal(ob[:k].cpu().numpy(), wb)

@@ -302,7 +302,7 @@ def secondary_workloads(tqp, torch, dev, local, reps, cpu_seconds=0.0):
     pr = datagen.probe_table(npr, nb, seed=datagen.DEFAULT_SEED + 2)
     F = tqp.TableRef([torch.from_numpy(pr["fk"]).to(dev), torch.from_numpy(pr["value"]).to(dev)])
     D = tqp.TableRef([torch.from_numpy(dim["key"]).to(dev), torch.from_numpy(dim["payload"]).to(dev)])
-    ctx = tqp.Context(local, 1 << 30)
+    ctx = tqp.Context(local, 4 << 30)  # (the sort-based group-by of 60M rows sorts 1.4 GB of pairs)
     ctx.set_autotune(True)
     k = 100
     rk = torch.zeros(k, dtype=torch.int64, device=dev)
@@ -335,6 +335,11 @@ def secondary_workloads(tqp, torch, dev, local, reps, cpu_seconds=0.0):
         tqp.tqp_hash_join(ctx, D, 0, F, 0, bidx, pidx, pcap, pcnt, stream)
 
     ms_pairs = _time_launches(torch, pairs, max(5, reps // 2))
+    ctx.set_variant(1)  # the sort-based join, for comparison with the tuned choice
+    ms_pairs_sort = _time_launches(torch, pairs, max(5, reps // 2))
+    ctx.set_variant(0)
+    ms_pairs_hash = _time_launches(torch, pairs, max(5, reps // 2))
+    ctx.set_variant(-1)
     ctx.check(stream)
     npairs = int(pcnt.item())
     alg_pairs = nb * 4 + npr * 4 + npairs * 8  # build keys, probe keys, the pairs written
@@ -343,8 +348,35 @@ def secondary_workloads(tqp, torch, dev, local, reps, cpu_seconds=0.0):
                     "index pairs, probe index ascending",
         "ms": ms_pairs, "probe_rows_per_s": npr / (ms_pairs / 1e3), "pairs": npairs, "algorithmic_bytes": alg_pairs,
         "achieved_gbs": alg_pairs / (ms_pairs / 1e3) / 1e9,
-        "frac_of_measured_hbm": alg_pairs / (ms_pairs / 1e3) / 1e9 / measured_peaks()[0]}
+        "frac_of_measured_hbm": alg_pairs / (ms_pairs / 1e3) / 1e9 / measured_peaks()[0],
+        "ms_hash_table": ms_pairs_hash, "ms_sort_based": ms_pairs_sort}
     del bidx, pidx
+    # many groups without a join: GROUP BY the 1.5M distinct probe keys, hash vs sort-based aggregation
+    G = 1_500_000
+    gk = torch.zeros(G, dtype=torch.int64, device=dev)
+    giv = torch.zeros(2 * G, dtype=torch.int64, device=dev)
+    gng = torch.zeros(1, dtype=torch.int64, device=dev)
+    gagg = [("sum", [("col", 1)]), ("count", None)]
+
+    def grp():
+        tqp.tqp_groupby_agg(ctx, F, [], [0], gagg, gk, giv, None, G, gng, stream)
+
+    ms_g = _time_launches(torch, grp, max(5, reps // 4))
+    ctx.set_variant(1)
+    ms_g_sort = _time_launches(torch, grp, max(5, reps // 4))
+    ctx.set_variant(0)
+    ms_g_hash = _time_launches(torch, grp, max(5, reps // 4))
+    ctx.set_variant(-1)
+    ctx.check(stream)
+    alg_g = npr * 12
+    out["groupby_60M_1.5Mgroups"] = {
+        "workload": "60M rows (int32 key Zipf(0.5) over 1.5M values, int64 value); GROUP BY key: SUM(value), COUNT; "
+                    "keys ascending",
+        "ms": ms_g, "rows_per_s": npr / (ms_g / 1e3), "algorithmic_bytes": alg_g,
+        "achieved_gbs": alg_g / (ms_g / 1e3) / 1e9,
+        "frac_of_measured_hbm": alg_g / (ms_g / 1e3) / 1e9 / measured_peaks()[0],
+        "ms_hash": ms_g_hash, "ms_sort_based": ms_g_sort, "groups": int(gng.item())}
+    del gk, giv
     alg = npr * 12 + nb * 8
     out["join_group_top100"] = {
         "workload": "build 1.5M unique int32 keys (payload = 150K groups); probe 60M Zipf(0.5) int32 fk + int64 "
@@ -407,8 +439,13 @@ def hashed_join_workloads(tqp, torch, dev, local, reps):
     bidx = torch.empty(npr, dtype=torch.int32, device=dev)
     pidx = torch.empty(npr, dtype=torch.int32, device=dev)
     pcnt = torch.zeros(1, dtype=torch.int64, device=dev)
-    ms_pairs = _time_launches(torch, lambda: tqp.tqp_hash_join(ctx, D, 0, F, 0, bidx, pidx, npr, pcnt, stream),
-                              max(5, reps // 2), stream=stream)
+    pj = lambda: tqp.tqp_hash_join(ctx, D, 0, F, 0, bidx, pidx, npr, pcnt, stream)  # noqa: E731
+    ms_pairs = _time_launches(torch, pj, max(5, reps // 2), stream=stream)
+    ctx.set_variant(1)
+    ms_pairs_sort = _time_launches(torch, pj, max(5, reps // 2), stream=stream)
+    ctx.set_variant(0)
+    ms_pairs_hash = _time_launches(torch, pj, max(5, reps // 2), stream=stream)
+    ctx.set_variant(-1)
     ctx.check(stream)
     npairs = int(pcnt.item())
     alg_pairs = nb * 4 + npr * 4 + npairs * 8
@@ -417,7 +454,8 @@ def hashed_join_workloads(tqp, torch, dev, local, reps):
                     "keys; output (build, probe) int32 index pairs, probe index ascending",
         "ms": ms_pairs, "probe_rows_per_s": npr / (ms_pairs / 1e3), "pairs": npairs, "algorithmic_bytes": alg_pairs,
         "achieved_gbs": alg_pairs / (ms_pairs / 1e3) / 1e9,
-        "frac_of_measured_hbm": alg_pairs / (ms_pairs / 1e3) / 1e9 / peak}
+        "frac_of_measured_hbm": alg_pairs / (ms_pairs / 1e3) / 1e9 / peak,
+        "ms_hash_table": ms_pairs_hash, "ms_sort_based": ms_pairs_sort}
     ctx.close()
     return out
 

@@ -266,7 +266,7 @@ def test_sort_based_aggregation(ctx, case):
     elif case == "three_keys":
         a = rng.integers(-3, 3, n).astype(np.int32)
         b = rng.integers(0, 4, n).astype(np.uint8)
-        c = rng.integers(-2, 2, n).astype(np.int32)
+        c = rng.integers(0, 5, n).astype(np.uint8)  # (the key tuple: 32 + 8 + 8 bits)
         v = rng.integers(0, 100, n).astype(np.int64)
         cols, preds, gc, aggs = [a, b, c, v], [(3, "ne", 50)], [0, 1, 2], [("sum", [("col", 3)]), ("count", None)]
     elif case == "min_max":

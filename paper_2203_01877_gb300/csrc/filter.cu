@@ -57,6 +57,170 @@ __global__ void __launch_bounds__(kEngineThreads, 2) k_filter(const __grid_const
     run_engine(A.G, A.ctl, body, smem, args_bytes<FilterArgs>());
 }
 
+// ---- direct form (variant 1): no staging ------------------------------------------
+// Every thread reads quads (four consecutive rows) of each predicate column
+// with one 16-byte load per 32-bit column (two per 64-bit column, one 4-byte
+// load per 8-bit column), kFdQuads quads at a time, at full occupancy: plain
+// loads with many in flight instead of bulk copies through a stage ring.  A
+// warp's 32 quads are 128 consecutive rows, so its pass bits form four mask
+// words in the layout the compaction kernel reads; the sum expression is
+// evaluated for passing rows only, from global memory.
+constexpr int kFdThreads = 256;
+constexpr int kFdQuads = 2;  // warp steps (32 quads each) per iteration of a warp
+
+constexpr int kFdConds = 4;  // conditions of the direct form (more: the staged scan)
+
+// The raw values of one quad of one condition column: 64-bit columns in
+// a.x, a.y, b.x, b.y; 32-bit ones in the four words of a; 8-bit ones in a.x.
+struct FdRaw {
+    longlong2 a, b;
+};
+
+__device__ __forceinline__ FdRaw fd_load(const unsigned char* p, int type, long long q, long long n) {
+    FdRaw r;
+    r.a = make_longlong2(0, 0);
+    r.b = make_longlong2(0, 0);
+    if (4 * q + 3 < n) {
+        if (type == TQP_I64) {
+            r.a = __ldg(reinterpret_cast<const longlong2*>(p) + 2 * q);
+            r.b = __ldg(reinterpret_cast<const longlong2*>(p) + 2 * q + 1);
+        } else if (type == TQP_I32) {
+            r.a = __ldg(reinterpret_cast<const longlong2*>(p) + q);
+        } else {
+            r.a.x = __ldg(reinterpret_cast<const unsigned int*>(p) + q);
+        }
+        return r;
+    }
+    // a partial last quad: row by row, the missing rows read as 0 (they fail anyway)
+    long long x[4] = {0, 0, 0, 0};
+    for (int j = 0; j < 4; ++j)
+        if (4 * q + j < n) x[j] = ldg_typed(p, type, 4 * q + j);
+    if (type == TQP_I64) {
+        r.a = make_longlong2(x[0], x[1]);
+        r.b = make_longlong2(x[2], x[3]);
+    } else if (type == TQP_I32) {
+        r.a.x = static_cast<long long>(static_cast<uint32_t>(x[0]) | (static_cast<uint64_t>(static_cast<uint32_t>(x[1])) << 32));
+        r.a.y = static_cast<long long>(static_cast<uint32_t>(x[2]) | (static_cast<uint64_t>(static_cast<uint32_t>(x[3])) << 32));
+    } else {
+        r.a.x = static_cast<long long>((x[0] & 0xFF) | ((x[1] & 0xFF) << 8) | ((x[2] & 0xFF) << 16) | ((x[3] & 0xFF) << 24));
+    }
+    return r;
+}
+
+__device__ __forceinline__ uint32_t fd_test(const CondFast& f, const FdRaw& r) {
+    uint32_t m = 0;
+    if (f.type == TQP_I64) {
+        const uint64_t x[4] = {static_cast<uint64_t>(r.a.x), static_cast<uint64_t>(r.a.y), static_cast<uint64_t>(r.b.x),
+                               static_cast<uint64_t>(r.b.y)};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) m |= static_cast<uint32_t>(x[j] - static_cast<uint64_t>(f.lo) <= f.span) << j;
+    } else {
+        uint32_t x[4];
+        if (f.type == TQP_I32) {
+            x[0] = static_cast<uint32_t>(r.a.x);
+            x[1] = static_cast<uint32_t>(static_cast<uint64_t>(r.a.x) >> 32);
+            x[2] = static_cast<uint32_t>(r.a.y);
+            x[3] = static_cast<uint32_t>(static_cast<uint64_t>(r.a.y) >> 32);
+        } else {
+            const uint32_t w = static_cast<uint32_t>(r.a.x);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) x[j] = (w >> (8 * j)) & 0xFFu;
+        }
+        const uint32_t lo = static_cast<uint32_t>(f.lo), sp = static_cast<uint32_t>(f.span);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) m |= static_cast<uint32_t>(x[j] - lo <= sp) << j;
+    }
+    return f.negate ? ~m & 0xFu : m;
+}
+
+__global__ void __launch_bounds__(kFdThreads, 2) k_filter_direct(const __grid_constant__ FilterArgs A) {
+    __shared__ unsigned long long red[2][kFdThreads / kWarp];
+    const int lane = threadIdx.x % kWarp, w = threadIdx.x / kWarp;
+    const long long n = A.G.n;
+    const long long nq = (n + 3) / 4;
+    const long long nsteps = (nq + kWarp - 1) / kWarp;  // warp steps of 32 quads
+    const long long warps = static_cast<long long>(gridDim.x) * (kFdThreads / kWarp);
+    const long long gw = blockIdx.x * static_cast<long long>(kFdThreads / kWarp) + w;
+    unsigned long long cnt = 0;
+    long long sum = 0;
+    for (long long s0 = gw; s0 < nsteps; s0 += kFdQuads * warps) {
+        uint32_t bits[kFdQuads];
+        FdRaw raw[kFdQuads][kFdConds];
+#pragma unroll
+        for (int u = 0; u < kFdQuads; ++u) {  // every load of the iteration in flight together
+            const long long st = s0 + u * warps;
+            const long long q = st * kWarp + lane;
+#pragma unroll
+            for (int c = 0; c < kFdConds; ++c)
+                if (c < A.ncond && st < nsteps) raw[u][c] = fd_load(A.G.col[A.cond[c].col].ptr, A.cf[c].type, q, n);
+        }
+#pragma unroll
+        for (int u = 0; u < kFdQuads; ++u) {
+            const long long st = s0 + u * warps;
+            const long long q = st * kWarp + lane;
+            uint32_t ok = 0;
+            if (st < nsteps) {
+                ok = 0xFu;
+                if (4 * q + 3 >= n)
+                    for (int j = 0; j < 4; ++j) ok &= ~(static_cast<uint32_t>(4 * q + j >= n) << j);
+#pragma unroll
+                for (int c = 0; c < kFdConds; ++c)
+                    if (c < A.ncond) ok &= fd_test(A.cf[c], raw[u][c]);
+            }
+            bits[u] = ok;
+        }
+#pragma unroll
+        for (int u = 0; u < kFdQuads; ++u) {
+            const long long st = s0 + u * warps;
+            if (st >= nsteps) break;  // (warp-uniform)
+            // word k of the step: the nibbles of lanes 8k .. 8k+7
+            uint32_t v = bits[u] << (4 * (lane & 7));
+            v |= __shfl_xor_sync(0xffffffffu, v, 1);
+            v |= __shfl_xor_sync(0xffffffffu, v, 2);
+            v |= __shfl_xor_sync(0xffffffffu, v, 4);
+            const uint32_t w1 = __shfl_sync(0xffffffffu, v, 8), w2 = __shfl_sync(0xffffffffu, v, 16),
+                           w3 = __shfl_sync(0xffffffffu, v, 24);
+            const uint32_t c = __popc(v) + __popc(w1) + __popc(w2) + __popc(w3);
+            const long long row0 = st * kWarp * 4;
+            if (lane == 0) {
+                cnt += c;
+                if (A.mask && c) atomicAdd(&A.block_tot[row0 / kCompactRows], c);
+                if (A.mask) *reinterpret_cast<uint4*>(A.mask + row0 / kWarp) = make_uint4(v, w1, w2, w3);
+            }
+            if (A.has_sum && bits[u]) {
+                const long long r = row0 + 4 * lane;
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if ((bits[u] >> j) & 1u) sum += eval_expr_global(A.G, A.sum, r + j);
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) {
+        red[0][w] = cnt;
+        red[1][w] = static_cast<unsigned long long>(sum);
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    unsigned long long tc = 0, ts = 0;
+    for (int i = 0; i < kFdThreads / kWarp; ++i) {
+        tc += red[0][i];
+        ts += red[1][i];
+    }
+    if (ts) atomicAdd(&A.acc[0], ts);
+    if (tc) atomicAdd(&A.acc[1], tc);
+    __threadfence();
+    if (atomicAdd(&A.acc[2], 1ULL) != static_cast<unsigned long long>(gridDim.x) - 1ULL) return;
+    __threadfence();
+    const unsigned long long tot_sum = atomicAdd(&A.acc[0], 0ULL);
+    const unsigned long long tot_cnt = atomicAdd(&A.acc[1], 0ULL);
+    *A.d_count = static_cast<int64_t>(tot_cnt);
+    if (A.d_count2) *A.d_count2 = static_cast<int64_t>(tot_cnt);
+    if (A.d_sum) *A.d_sum = static_cast<int64_t>(tot_sum);
+    if (A.mask && static_cast<long long>(tot_cnt) > A.capacity) latch_error(A.ctl.err, TQP_ERR_CAPACITY);
+}
+
 __global__ void __launch_bounds__(kCompactThreads) k_compact(const uint32_t* __restrict__ mask,
                                                              const uint32_t* __restrict__ block_tot, long long n,
                                                              int32_t* __restrict__ row_ids, long long capacity) {
@@ -105,7 +269,8 @@ static tqp_status plan_filter(const tqp_ctx* ctx, const tqp_table* t, const tqp_
 // Launch with caller-provided scratch of at least lay.bytes (cleared here).
 static tqp_status launch_filter_with(FilterArgs& A, int grid, size_t smem, const FilterScratch& lay,
                                      void* scratch, int* d_err, long long wait_cap, int32_t* d_row_ids,
-                                     int64_t capacity, int64_t* d_count, int64_t* d_sum, cudaStream_t stream) {
+                                     int64_t capacity, int64_t* d_count, int64_t* d_sum, cudaStream_t stream,
+                                     int direct_grid = 0) {
     unsigned char* sc = static_cast<unsigned char*>(scratch);
     TQP_CUDA(cudaMemsetAsync(sc, 0, lay.mask_off, stream));
     A.ctl.ticket = reinterpret_cast<unsigned long long*>(sc);
@@ -117,7 +282,8 @@ static tqp_status launch_filter_with(FilterArgs& A, int grid, size_t smem, const
     A.capacity = capacity;
     A.d_count = d_count;
     A.d_sum = d_sum;
-    k_filter<<<grid, kEngineThreads, smem, stream>>>(A);
+    if (direct_grid > 0) k_filter_direct<<<direct_grid, kFdThreads, 0, stream>>>(A);
+    else k_filter<<<grid, kEngineThreads, smem, stream>>>(A);
     TQP_CUDA(cudaGetLastError());
     if (d_row_ids) {
         k_compact<<<static_cast<unsigned>(lay.nblocks), kCompactThreads, 0, stream>>>(A.mask, A.block_tot, A.G.n,
@@ -142,8 +308,18 @@ tqp_status launch_filter(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* preds
     }
     void* scratch = arena_alloc(ctx, lay.bytes);
     if (!scratch) return arena_oom(ctx, lay.bytes);
+    // variant 1: the direct form (every predicate column read with plain vector loads)
+    int dgrid = 0;
+    if (tuned_variant(ctx) == 1 && A.ncond > 0 && A.ncond <= kFdConds) {
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_filter_direct, kFdThreads, 0) != cudaSuccess || occ < 1)
+            occ = 1;
+        const long long steps = ((t->num_rows + 3) / 4 + kWarp - 1) / kWarp;
+        const long long want = (steps + kFdThreads / kWarp - 1) / (kFdThreads / kWarp);
+        dgrid = static_cast<int>(std::max<long long>(1, std::min<long long>(want, static_cast<long long>(occ) * ctx->num_sms)));
+    }
     return launch_filter_with(A, grid, smem, lay, scratch, ctx->d_err, ctx->wait_cap, d_row_ids, capacity, d_count,
-                              d_sum, stream);
+                              d_sum, stream, dgrid);
 }
 
 }  // namespace tqp
@@ -173,7 +349,7 @@ extern "C" tqp_status tqp_filter(tqp_ctx* ctx, const tqp_table* t, const tqp_pre
         arena_reset(ctx);
         return launch_filter(ctx, t, preds, npreds, sum_expr, d_sum, d_row_ids, capacity, d_count, st, nullptr);
     };
-    return tuned(ctx, key, st, false, run);
+    return tuned(ctx, key, st, npreds > 0 ? (kTuneVariant | kTuneV1Shapeless) : 0, run);
 }
 
 // ---- allocation-free variant (tqp_filter_noalloc) ------------------------------

@@ -244,3 +244,35 @@ def test_ragged_last_tile_under_forced_shapes(ctx, extra, shape):
     want_ids, want_sum = oracle.filter_rows(cols, Q6_PREDS, Q6_EXPR)
     assert st == 0 and k == len(want_ids) and s == want_sum
     assert np.array_equal(ids, want_ids)
+
+
+@pytest.mark.parametrize("n", [1, 3, 128, 1023, 4099, 1_000_003])
+@pytest.mark.parametrize("case", ["q6", "u8_i64", "six_conditions", "ne_and_extremes"])
+def test_direct_filter_variant(ctx, n, case):
+    """The direct form of the filter (variant 1: predicate columns read with plain vector loads, no staging)
+    gives the oracle's row ids, count and sum; with more than four conditions it falls back to the staged
+    scan."""
+    from tests.gpu_util import gpu_filter
+    rng = np.random.default_rng(n + len(case))
+    if case == "q6":
+        cols, preds, expr = q6_cols(n, 77), Q6_PREDS, Q6_EXPR
+    elif case == "u8_i64":
+        t = datagen.fact_table(n, seed=78)
+        cols = [t["flag"], t["price"], t["status"]]
+        preds, expr = [(0, "eq", 1), (1, "ge", 5_000_000), (2, "ne", 0)], [("col", 1)]
+    elif case == "six_conditions":  # three ranges, a fourth column and two NE tests: six conditions
+        cols = q6_cols(n, 79)
+        preds, expr = Q6_PREDS + [(3, "gt", 1000), (1, "ne", 6), (2, "ne", 10)], Q6_EXPR
+    else:
+        x = rng.integers(np.iinfo(np.int64).min, np.iinfo(np.int64).max, n, dtype=np.int64)
+        x[::7] = np.iinfo(np.int64).max
+        y = rng.integers(-2**31, 2**31 - 1, n).astype(np.int32)
+        cols, preds, expr = [x, y], [(0, "ne", np.iinfo(np.int64).max), (1, "le", 0)], [("col", 1)]
+    try:
+        ctx.set_variant(1)
+        ids, k, s, st = gpu_filter(ctx, cols, preds, expr)
+    finally:
+        ctx.set_variant(-1)
+    want_ids, want_sum = oracle.filter_rows(cols, preds, expr)
+    assert st == 0 and k == len(want_ids) and s == want_sum
+    assert np.array_equal(ids, want_ids)

@@ -921,6 +921,13 @@ def main():
     ctx.check(stream)
     total_ms = t_start.elapsed_time(t_end)
     launch_ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+    # both filter kernels forced, beside the tuned choice timed above
+    variant_ms = {}
+    for name, v in (("staged_scan", 0), ("direct", 1)):
+        ctx.set_variant(v)
+        variant_ms[name] = _time_launches(torch, step, 20, stream=stream)
+    ctx.set_variant(-1)
+    ctx.check(stream)
     if world > 1:
         tt = torch.tensor([total_ms], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -996,7 +1003,9 @@ def main():
                        "rows": N_ROWS, "passing_rows": k,
                        "l2": "inputs 1.44 GB > 126 MB L2: no flush between steps"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "peak_kind": peak_kind, "kernel": "k_filter",
+                         "frac": achieved / peak, "peak_kind": peak_kind,
+                         "kernel": "k_filter_direct" if variant_ms["direct"] < variant_ms["staged_scan"] else "k_filter",
+                         "variant_call_ms": variant_ms,
                          "algorithmic_bytes_per_launch": alg, "launch_ms": launch_ms,
                          "traffic": ncu_traffic()},
             "cpu_baseline": cpu,

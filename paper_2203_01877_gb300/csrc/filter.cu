@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(kEngineThreads, 2) k_filter(const __grid_const
 // words in the layout the compaction kernel reads; the sum expression is
 // evaluated for passing rows only, from global memory.
 constexpr int kFdThreads = 256;
-constexpr int kFdQuads = 2;  // warp steps (32 quads each) per iteration of a warp
+constexpr int kFdQuads = 1;  // warp steps (32 quads each) per iteration of a warp
 
 constexpr int kFdConds = 4;  // conditions of the direct form (more: the staged scan)
 
@@ -133,9 +133,16 @@ __device__ __forceinline__ uint32_t fd_test(const CondFast& f, const FdRaw& r) {
     return f.negate ? ~m & 0xFu : m;
 }
 
-__global__ void __launch_bounds__(kFdThreads, 2) k_filter_direct(const __grid_constant__ FilterArgs A) {
+// Per warp: passing row ids whose sum is still to be evaluated (two steps of
+// at most 128 rows each plus a partial round of fewer than 32).
+constexpr int kFdQueue = kFdQuads * 4 * kWarp + kWarp;
+
+__global__ void __launch_bounds__(kFdThreads, 4) k_filter_direct(const __grid_constant__ FilterArgs A) {
     __shared__ unsigned long long red[2][kFdThreads / kWarp];
+    __shared__ uint32_t queue[kFdThreads / kWarp][kFdQueue];
     const int lane = threadIdx.x % kWarp, w = threadIdx.x / kWarp;
+    uint32_t* q = queue[w];
+    int qn = 0;  // queued rows (warp-uniform)
     const long long n = A.G.n;
     const long long nq = (n + 3) / 4;
     const long long nsteps = (nq + kWarp - 1) / kWarp;  // warp steps of 32 quads
@@ -178,23 +185,37 @@ __global__ void __launch_bounds__(kFdThreads, 2) k_filter_direct(const __grid_co
             v |= __shfl_xor_sync(0xffffffffu, v, 1);
             v |= __shfl_xor_sync(0xffffffffu, v, 2);
             v |= __shfl_xor_sync(0xffffffffu, v, 4);
-            const uint32_t w1 = __shfl_sync(0xffffffffu, v, 8), w2 = __shfl_sync(0xffffffffu, v, 16),
-                           w3 = __shfl_sync(0xffffffffu, v, 24);
-            const uint32_t c = __popc(v) + __popc(w1) + __popc(w2) + __popc(w3);
+            const uint32_t w0 = __shfl_sync(0xffffffffu, v, 0), w1 = __shfl_sync(0xffffffffu, v, 8),
+                           w2 = __shfl_sync(0xffffffffu, v, 16), w3 = __shfl_sync(0xffffffffu, v, 24);
+            const uint32_t c = __popc(w0) + __popc(w1) + __popc(w2) + __popc(w3);  // (warp-uniform)
             const long long row0 = st * kWarp * 4;
             if (lane == 0) {
                 cnt += c;
                 if (A.mask && c) atomicAdd(&A.block_tot[row0 / kCompactRows], c);
-                if (A.mask) *reinterpret_cast<uint4*>(A.mask + row0 / kWarp) = make_uint4(v, w1, w2, w3);
+                if (A.mask) *reinterpret_cast<uint4*>(A.mask + row0 / kWarp) = make_uint4(w0, w1, w2, w3);
             }
-            if (A.has_sum && bits[u]) {
-                const long long r = row0 + 4 * lane;
+            if (A.has_sum && c) {  // queue the passing rows; evaluate them 32 at a time
+                const uint32_t lt = lanemask_lt();
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    if ((bits[u] >> j) & 1u) sum += eval_expr_global(A.G, A.sum, r + j);
+                for (int j = 0; j < 4; ++j) {
+                    const uint32_t m = __ballot_sync(0xffffffffu, (bits[u] >> j) & 1u);
+                    if ((bits[u] >> j) & 1u) q[qn + __popc(m & lt)] = static_cast<uint32_t>(row0 + 4 * lane + j);
+                    qn += __popc(m);
+                }
+                __syncwarp();
             }
         }
+        if (A.has_sum && qn >= kWarp) {
+            int h = 0;
+            for (; qn - h >= kWarp; h += kWarp) sum += eval_expr_global(A.G, A.sum, q[h + lane]);
+            const uint32_t keep = lane < qn - h ? q[h + lane] : 0u;
+            __syncwarp();
+            if (lane < qn - h) q[lane] = keep;
+            qn -= h;
+            __syncwarp();
+        }
     }
+    if (A.has_sum && lane < qn) sum += eval_expr_global(A.G, A.sum, q[lane]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
     if (lane == 0) {

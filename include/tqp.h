@@ -123,10 +123,11 @@ typedef struct {
  * exact int64; AVG(expr) is the IEEE double division SUM/COUNT.  MIN(expr)
  * and MAX(expr) are the smallest / largest int64 value over the group's rows
  * (an ungrouped MIN/MAX over no rows gives 0 with NaN in d_fvals as its
- * flag).  MIN and MAX are supported by tqp_groupby_agg and by plans without a
- * join when groups are few (max_groups, or capacity_groups, at most 64; at
- * most three distinct non-COUNT accumulators; at most four predicates) and
- * not as the top-k order; other uses return TQP_ERR_UNSUPPORTED. */
+ * flag).  MIN and MAX are supported everywhere an aggregate is (group-bys,
+ * plans with or without a join, top-k by a MIN/MAX value): few-group shapes
+ * take the direct kernel, larger ones the sort-based group-by, joined plans
+ * the fused probe's general path (an atomic maximum of an order-preserving
+ * code per accumulator). */
 typedef enum { TQP_SUM = 0, TQP_COUNT, TQP_AVG, TQP_MIN, TQP_MAX } tqp_aggfn;
 
 typedef struct {

@@ -655,7 +655,14 @@ struct PlanJoinBody {
 
     __device__ PlanJoinBody(const PlanJoinArgs& a, unsigned char*) : A(a) {}
 
-    // Add one joined row (count `cnt` matches, sums x[]) to the group(s) of its slot.
+    // Accumulator i + 1 of a group: a sum, or the atomic maximum of a MIN/MAX code.
+    __device__ __forceinline__ void acc_update(unsigned long long* a, int i, int64_t x) const {
+        const int kind = A.S.acc_kind[i];
+        if (kind == kAccSum) red_add_u64(&a[i + 1], static_cast<unsigned long long>(x));
+        else atomicMax(&a[i + 1], acc_encode(kind, x));
+    }
+
+    // Add one joined row (count `cnt` matches, values x[]) to the group(s) of its slot.
     __device__ __forceinline__ void add_groups(const uint4& sl, const int64_t (&x)[kFastSums], int nsum) {
         const GroupSpec& S = A.S;
         if (sl.z & kDirectGroup) {  // a unique key whose dense group id sits in the slot
@@ -663,7 +670,7 @@ struct PlanJoinBody {
             red_add_u64(&a[0], 1ULL);
 #pragma unroll
             for (int i = 0; i < kFastSums; ++i)
-                if (i < nsum) red_add_u64(&a[i + 1], static_cast<unsigned long long>(x[i]));
+                if (i < nsum) acc_update(a, i, x[i]);
             return;
         }
         uint32_t d = sl.z;
@@ -672,7 +679,7 @@ struct PlanJoinBody {
             red_add_u64(&a[0], 1ULL);
 #pragma unroll
             for (int i = 0; i < kFastSums; ++i)
-                if (i < nsum) red_add_u64(&a[i + 1], static_cast<unsigned long long>(x[i]));
+                if (i < nsum) acc_update(a, i, x[i]);
             if (k + 1 < sl.w) d = __ldg(&A.next[d]);
         }
     }
@@ -697,8 +704,7 @@ struct PlanJoinBody {
             const long long g = direct_group ? static_cast<long long>(sl.z & ~kDirectGroup) : __ldg(&A.dgs[d]);
             unsigned long long* a = S.acc + g * S.nacc;
             red_add_u64(&a[0], 1ULL);
-            for (int i = 1; i < S.nacc; ++i)
-                red_add_u64(&a[i], static_cast<unsigned long long>(eval_expr(G, v, S.acc_expr[i - 1], r)));
+            for (int i = 1; i < S.nacc; ++i) acc_update(a, i - 1, eval_expr(G, v, S.acc_expr[i - 1], r));
             if (!direct_group && k + 1 < cnt) d = __ldg(&A.next[d]);
         }
     }

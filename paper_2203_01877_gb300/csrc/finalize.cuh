@@ -118,6 +118,14 @@ static __device__ void top_sort_block(long long* r, uint64_t* k, uint32_t* s, in
     }
 }
 
+// The value a group is ranked by: its accumulator `rank_acc`, with a MIN/MAX
+// accumulator's order-preserving code decoded to the int64 value it keeps.
+__device__ __forceinline__ long long rank_value(const GroupSpec& S, int rank_acc, long long slot) {
+    const unsigned long long x = S.acc[slot * S.nacc + rank_acc];
+    const int kind = rank_acc > 0 ? S.acc_kind[rank_acc - 1] : kAccSum;
+    return kind == kAccSum ? static_cast<long long>(x) : acc_decode(kind, x);
+}
+
 static __device__ void topk_level0_block(const GroupSpec& S, int rank_acc, int k, TopBuf out, unsigned long long* total,
                                   long long block, const unsigned int* run = nullptr) {
     if (run && *reinterpret_cast<const volatile unsigned int*>(run) == 0) return;  // the radix select succeeded
@@ -137,7 +145,7 @@ static __device__ void topk_level0_block(const GroupSpec& S, int rank_acc, int k
         const long long slot = s0 + i;
         if (slot <= S.cap && slot_used(S, slot)) {
             const int p = atomicAdd(&cnt, 1);
-            r[p] = static_cast<long long>(S.acc[slot * S.nacc + rank_acc]);
+            r[p] = rank_value(S, rank_acc, slot);
             kk[p] = slot_key(S, slot);
             ss[p] = static_cast<uint32_t>(slot);
         }
@@ -290,7 +298,7 @@ __host__ __device__ __forceinline__ void first_bin_interval(int b, unsigned long
 }
 
 __device__ __forceinline__ long long slot_rank(const GroupSpec& S, int rank_acc, long long slot) {
-    return static_cast<long long>(S.acc[slot * S.nacc + rank_acc]);
+    return rank_value(S, rank_acc, slot);
 }
 
 // One block of pass `pass` over slots [block * kSelSlots, ...).

@@ -430,24 +430,14 @@ tqp_status launch_groupby(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* pred
     lower_group_fast(&A);
 
     // variant 1: the sort-based aggregation (Algorithm 3), timed against this path by the autotuner
-    if (ngc > 0 && tuned_variant(ctx) == 1) {
+    // (and MIN/MAX beyond the direct kernel's shapes: the hash engine body only adds)
+    GroupDirectArgs D;
+    const bool direct = lower_group_direct(t, A, max_groups, &D);
+    if ((ngc > 0 && tuned_variant(ctx) == 1) || (A.S.minmax && !direct)) {
         GroupOut O{d_keys, d_ivals, d_fvals, capacity_groups, d_num_groups, ctx->d_err};
-        if (topk > 0 && topk_agg >= 0 && topk_agg < naggs && (aggs[topk_agg].fn == TQP_MIN || aggs[topk_agg].fn == TQP_MAX))
-            return fail(TQP_ERR_UNSUPPORTED, "top-k by a MIN/MAX aggregate is not supported");
         TQP_TRY(launch_sort_agg(ctx, t, A.cond, A.ncond, &A.S, std::max<long long>(max_groups, 1), stream));
         if (topk > 0) return group_topk(ctx, A.S, O, topk, topk_agg, d_total_groups, stream);
         return group_finalize(ctx, A.S, O, stream);
-    }
-    GroupDirectArgs D;
-    const bool direct = lower_group_direct(t, A, max_groups, &D);
-    // shapes that are rejected anyway are rejected before any scratch or device work
-    if (A.S.minmax) {  // MIN/MAX: the direct kernel only, and not as the top-k order
-        if (!direct)
-            return fail(TQP_ERR_UNSUPPORTED, "MIN/MAX need at most %lld groups, at most %d accumulators besides COUNT "
-                                             "and at most %d predicates", kDirMaxGroups, kDirSums, kDirConds);
-        if (topk > 0 && topk_agg >= 0 && topk_agg < naggs &&
-            (aggs[topk_agg].fn == TQP_MIN || aggs[topk_agg].fn == TQP_MAX))
-            return fail(TQP_ERR_UNSUPPORTED, "top-k by a MIN/MAX aggregate is not supported");
     }
     const long long cap = group_table_cap(max_groups);
     void* tab = arena_alloc(ctx, group_table_bytes(cap, A.S.nacc));

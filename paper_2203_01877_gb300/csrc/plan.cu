@@ -111,6 +111,7 @@ __global__ void __launch_bounds__(kEngineThreads, PlanJoinBody::kMinBlocks) k_pl
 
 void lower_join_fast(PlanJoinArgs* A) {
     A->pjfast = 0;
+    if (A->S.minmax) return;  // the closed-form fast paths only add: MIN/MAX take the general one
     A->nsum = A->S.nacc > 0 ? A->S.nacc - 1 : 0;
     const ColRef& fk = A->G.col[A->fk_col];
     if (fk.slot < 0) return;
@@ -345,8 +346,6 @@ static tqp_status run_join_plan(tqp_ctx* ctx, const tqp_plan* p, const tqp_resul
         if (p->group_cols[i] < nf || p->group_cols[i] >= nf + nd)
             return fail(TQP_ERR_UNSUPPORTED, "with a join, group columns must be dimension columns");
     for (int a = 0; a < p->naggs; ++a) {
-        if (p->aggs[a].fn == TQP_MIN || p->aggs[a].fn == TQP_MAX)
-            return fail(TQP_ERR_UNSUPPORTED, "MIN/MAX are not supported with a join");
         if (p->aggs[a].fn != TQP_COUNT && !expr_uses_only(p->aggs[a].expr, 0, nf))
             return fail(TQP_ERR_UNSUPPORTED, "with a join, aggregate expressions must use fact columns only");
     }

@@ -238,12 +238,21 @@ def test_min_max_with_sum_avg_and_ungrouped(ctx):
     check(ctx, cols, [(0, "gt", 99_999)], [], aggs, capacity=1)
 
 
-def test_min_max_unsupported_shapes(ctx):
-    import paper_2203_01877_gb300 as tqp
-    cols = q1_cols(10_000, 97)
-    with pytest.raises(tqp.TqpError) as e:  # many groups: not the direct kernel
-        gpu_groupby(ctx, cols, [], [1, 2], [("min", [("col", 4)])], capacity=4096)
-    assert e.value.status == tqp.ERR_UNSUPPORTED
+def test_min_max_many_groups_and_wide_shapes(ctx):
+    """MIN/MAX beyond the direct kernel's shapes (more than 64 groups, more than four predicates or three
+    accumulators) run through the sort-based aggregation on the default path: the oracle's groups."""
+    rng = np.random.default_rng(97)
+    n = 300_007
+    g = rng.integers(0, 20_000, n).astype(np.int32)
+    v = rng.integers(-10**15, 10**15, n).astype(np.int64)
+    w = rng.integers(-5, 5, n).astype(np.int32)
+    check(ctx, [g, v, w], [], [0], [("min", [("col", 1)]), ("max", [("col", 1)]), ("count", None)],
+          capacity=32_768)
+    cols = q1_cols(100_003, 98)  # a few groups, but five predicates and four accumulators besides COUNT
+    preds = [(0, "le", 2450), (3, "ge", 2), (4, "ne", 500), (5, "ne", 3), (5, "ne", 4)]
+    aggs = [("min", [("col", 4)]), ("max", [("col", 3)]), ("sum", [("col", 4)]), ("max", [("col", 5)]),
+            ("count", None)]
+    check(ctx, cols, preds, [1, 2], aggs, capacity=64)
 
 
 @pytest.mark.parametrize("case", ["q1", "many_groups", "int64_keys", "three_keys", "min_max", "none_pass"])

@@ -107,17 +107,31 @@ def test_scan_plan_min_max(ctx):
              aggs=[("min", [("col", 3)]), ("max", [("col", 4)]), ("count", None)], capacity_groups=64)
 
 
-def test_min_max_unsupported_in_plans(ctx):
-    import paper_2203_01877_gb300 as tqp
-    fact, dim = join_case(2_000, 50, 20_000, 73)
-    with pytest.raises(tqp.TqpError) as e:  # with a join
-        gpu_plan(ctx, fact=fact, dim=dim, fact_fk=0, dim_key=0, group_cols=[3], aggs=[("max", [("col", 1)])],
+@pytest.mark.parametrize("rows", [20_000, 1_300_000])
+def test_min_max_in_joined_plans_and_topk(ctx, rows):
+    """MIN/MAX with a join (each joined row's value into its dimension group's code by atomic maximum),
+    with duplicate build keys and misses, and as the top-k order (ranked by the decoded value): the oracle's
+    results, element by element."""
+    rng = np.random.default_rng(rows)
+    fact, dim = join_case(2_000, 50, rows, 73)
+    dup = [np.concatenate([dim[0], dim[0][:300]]), np.concatenate([dim[1], rng.integers(0, 50, 300).astype(np.int32)])]
+    fk = fact[0].copy()
+    fk[::17] = 99_999  # misses
+    aggs = [("max", [("col", 1)]), ("min", [("col", 1), ("const", -3), "mul"]), ("count", None),
+            ("sum", [("col", 1)])]
+    for d in (dim, dup):
+        run_both(ctx, fact=[fk, fact[1]], dim=d, fact_fk=0, dim_key=0, group_cols=[3], aggs=aggs,
                  capacity_groups=64)
-    assert e.value.status == tqp.ERR_UNSUPPORTED
-    with pytest.raises(tqp.TqpError) as e:  # as the top-k order
-        gpu_plan(ctx, fact=q1(5_000, 74), group_cols=[1], aggs=[("min", [("col", 4)])], topk=2, topk_agg=0,
-                 max_groups=8)
-    assert e.value.status == tqp.ERR_UNSUPPORTED
+        for agg in (0, 1):
+            run_both(ctx, fact=[fk, fact[1]], dim=d, fact_fk=0, dim_key=0, group_cols=[3], aggs=aggs, topk=5,
+                     topk_agg=agg, capacity_groups=5)
+    # without a join: top-k by MIN (the direct kernel) and by MAX over many groups (the sort-based path)
+    run_both(ctx, fact=q1(5_000, 74), group_cols=[1], aggs=[("min", [("col", 4)])], topk=2, topk_agg=0,
+             max_groups=8, capacity_groups=2)
+    g = rng.integers(0, 5_000, 50_000).astype(np.int32)
+    v = rng.integers(-10**12, 10**12, 50_000).astype(np.int64)
+    run_both(ctx, fact=[g, v], group_cols=[0], aggs=[("max", [("col", 1)]), ("count", None)], topk=25,
+             topk_agg=0, max_groups=8192, capacity_groups=25)
 
 
 @pytest.mark.parametrize("topk", [0, 1, 100, 1000])

@@ -270,16 +270,19 @@ __device__ __forceinline__ void dir_flush_dense_cta(const GroupDirectArgs& A, co
                                                     unsigned long long* tables, int lane, int w) {
     const GroupSpec& S = A.S;
     __shared__ long long gslot[kDirSlots];
-    if (w == 0) {  // the global entry of every slot some row reached
+    static_assert(kDirSlots <= kDirThreads / 32, "one warp per slot");
+    if (w < kDirSlots) {  // warp d: the global entry of slot d, if some row reached it
+        const int d = w;
         long long g = -1;
-        if (lane < Dn.P) {
-            unsigned long long c = 0;
-            for (int v = 0; v < kDirThreads / 32; ++v)
-                for (int l = 0; l < 32; ++l) c += tables[v * kDirWarpWords + (lane * kDirAcc) * 32 + l];
-            if (c) {
+        if (d < Dn.P) {
+            unsigned long long c = 0;  // lane l: the count of slot d over the eight warps' lane l
+            for (int v = 0; v < kDirThreads / 32; ++v) c += tables[v * kDirWarpWords + (d * kDirAcc) * 32 + lane];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+            if (c && lane == 0) {
                 uint64_t key = 0;
                 for (int i = 0; i < A.ngc; ++i) {
-                    const long long x = Dn.kmin[i] + (lane / Dn.stride[i]) % Dn.range[i];
+                    const long long x = Dn.kmin[i] + (d / Dn.stride[i]) % Dn.range[i];
                     const int b = S.key_bits[i];
                     const uint64_t e = enc_key(x, b);
                     key = b == 64 ? e : ((key << b) | e);
@@ -287,7 +290,7 @@ __device__ __forceinline__ void dir_flush_dense_cta(const GroupDirectArgs& A, co
                 g = gtab_slot(S, key, A.err);
             }
         }
-        if (lane < kDirSlots) gslot[lane] = g;
+        if (lane == 0) gslot[d] = g;
     }
     __syncthreads();
     const int npairs = Dn.P * S.nacc;

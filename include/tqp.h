@@ -327,6 +327,48 @@ TQP_API tqp_status tqp_filter_noalloc(int device, const tqp_table* t,
                                       int32_t* d_row_ids, int64_t capacity, int64_t* d_count,
                                       int32_t* d_status, void* stream);
 
+/* ---- shared scans --------------------------------------------------------- */
+
+/*
+ * Many filter queries over one table in shared passes.  The paper runs one
+ * query at a time (Section 4.3), so n queries over a resident table read it n
+ * times; here one scan evaluates up to 32 queries: every row is tested
+ * against all of them, and each query gets what tqp_filter without row ids
+ * gives it (Section 3.1 filter, Section 5.1 expressions):
+ *   d_count   passing rows (required)
+ *   d_sum     SUM(sum_expr) over the passing rows (exactly when has_sum != 0)
+ * Results are identical to n calls of tqp_filter(ctx, t, preds, npreds,
+ * has_sum ? &sum_expr : NULL, d_sum, NULL, 0, d_count).
+ *
+ * Packing: queries are packed, in order and first fit, into launches of at
+ * most 32 queries, 8 distinct columns and 2 distinct sum expressions whose
+ * lookup tables fit the kernel's shared memory (per condition column one
+ * table of the value intervals cut by the queries' range bounds).  A query
+ * whose sum expression is not a product of two affine factors (x, x*k, x+k,
+ * x*y, x*(k-y), ...) or that reads more than 8 columns runs alone through
+ * tqp_filter's scan.  launch_of (host array of nq, may be NULL) receives each
+ * query's launch index, or -1 for one that ran alone.
+ *
+ * Errors: TQP_ERR_INVALID_ARG (nq < 0, NULL queries with nq > 0, a NULL
+ * d_count, has_sum without d_sum or d_sum without has_sum, a predicate or
+ * expression tqp_filter rejects; nothing is launched), TQP_ERR_OUT_OF_MEMORY
+ * (the context's arena), TQP_ERR_CUDA.  Column rules as for tqp_filter's
+ * predicate columns: every column a query reads must be in device memory.
+ * The call copies its lookup tables from pageable host memory, so it cannot
+ * be captured in a CUDA graph (tqp_batch_create captures the same packing).
+ */
+typedef struct {
+    tqp_pred preds[TQP_MAX_PREDS];
+    int32_t npreds;
+    int32_t has_sum;
+    tqp_expr sum_expr;
+    int64_t* d_count;
+    int64_t* d_sum;
+} tqp_scan_query;
+
+TQP_API tqp_status tqp_filter_shared(tqp_ctx* ctx, const tqp_table* t, const tqp_scan_query* queries, int32_t nq,
+                                     int32_t* launch_of, void* stream);
+
 /* ---- fixed operator plans ------------------------------------------------ */
 
 /*

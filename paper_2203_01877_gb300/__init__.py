@@ -72,6 +72,11 @@ class Plan(C.Structure):
                 ("prepared", C.c_void_p)]
 
 
+class ScanQuery(C.Structure):
+    _fields_ = [("preds", Pred * MAX_PREDS), ("npreds", C.c_int32), ("has_sum", C.c_int32),
+                ("sum_expr", Expr), ("d_count", C.c_void_p), ("d_sum", C.c_void_p)]
+
+
 class Result(C.Structure):
     _fields_ = [("d_row_ids", C.c_void_p), ("capacity_rows", C.c_int64), ("d_num_rows", C.c_void_p),
                 ("d_sum", C.c_void_p),
@@ -96,6 +101,8 @@ _SIGS = {
                              C.c_int64, _P, _P]),
     "tqp_filter_noalloc": (C.c_int, [C.c_int, C.POINTER(Table), C.POINTER(Pred), C.c_int32, C.POINTER(Expr), _P,
                                      _P, C.c_int64, _P, _P, _P]),
+    "tqp_filter_shared": (C.c_int, [_P, C.POINTER(Table), C.POINTER(ScanQuery), C.c_int32,
+                                    C.POINTER(C.c_int32), _P]),
     "tqp_groupby_agg": (C.c_int, [_P, C.POINTER(Table), C.POINTER(Pred), C.c_int32, C.POINTER(C.c_int32),
                                   C.c_int32, C.POINTER(Agg), C.c_int32, _P, _P, _P, C.c_int64, _P, _P]),
     "tqp_hash_join": (C.c_int, [_P, C.POINTER(Table), C.c_int32, C.POINTER(Table), C.c_int32, _P, _P,
@@ -304,6 +311,34 @@ def tqp_filter_noalloc(device: int, table: TableRef, preds=(), sum_expr=None, d_
     se = C.byref(make_expr(sum_expr)) if sum_expr is not None else None
     _check(lib().tqp_filter_noalloc(int(device), table.ref(), pa, len(preds), se, _ptr(d_sum), _ptr(d_row_ids),
                                     int(capacity), _ptr(d_count), _ptr(d_status), _stream(stream)))
+
+
+def make_scan_queries(queries):
+    """queries: (preds, sum_expr or None, d_count, d_sum or None) tuples."""
+    arr = (ScanQuery * max(1, len(queries)))()
+    for i, (preds, ex, d_count, d_sum) in enumerate(queries):
+        if len(preds) > MAX_PREDS:
+            raise ValueError("more than 8 predicates")
+        for j, (c, op, lo, *hi) in enumerate(preds):
+            arr[i].preds[j].col, arr[i].preds[j].op, arr[i].preds[j].lo = int(c), _OPS[op], int(lo)
+            arr[i].preds[j].hi = int(hi[0]) if hi else 0
+        arr[i].npreds = len(preds)
+        if ex is not None:
+            arr[i].has_sum = 1
+            arr[i].sum_expr = make_expr(ex)
+        arr[i].d_count = None if d_count is None else d_count.data_ptr()
+        arr[i].d_sum = None if d_sum is None else d_sum.data_ptr()
+    return arr
+
+
+def tqp_filter_shared(ctx: Context, table: TableRef, queries, stream=None):
+    """Shared scans: each (preds, sum_expr, d_count, d_sum) query gets what
+    tqp_filter without row ids gives it.  Returns each query's launch index
+    (-1: it ran alone through the single-query scan)."""
+    arr = make_scan_queries(queries)
+    launch_of = (C.c_int32 * max(1, len(queries)))()
+    _check(lib().tqp_filter_shared(ctx.h, table.ref(), arr, len(queries), launch_of, _stream(stream)))
+    return [int(launch_of[i]) for i in range(len(queries))]
 
 
 def tqp_groupby_agg(ctx: Context, table: TableRef, preds, group_cols, aggs, d_keys, d_ivals, d_fvals,

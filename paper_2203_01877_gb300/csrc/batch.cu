@@ -16,10 +16,14 @@
 //             pass, then the direct kernel (vector reads one warp step ahead,
 //             lane-private tables), each job a contiguous range of blocks
 //   scan      one persistent launch of the staged scan engine per body kind
-//             (filter, group-by, joined aggregation): CTAs draw chunk
+//             (filter, shared filter, group-by, joined aggregation): CTAs draw chunk
 //             tickets across the tables of every job of that kind (uneven
 //             sizes balance themselves); each kind gets its own shared-memory
-//             layout and occupancy
+//             layout and occupancy.  Filter-only work (counts and sums
+//             without row ids) of several plans over the same table is packed
+//             into shared scans: one pass evaluates up to 32 of them
+//             (multi.cuh), so a batch of such queries reads the table once
+//             per pack instead of once per plan
 //   fold      joins that aggregated by join key: key totals -> groups
 //   compact   selection masks -> row ids
 //   finalize  one CTA per small group table (keys ascending)
@@ -40,6 +44,7 @@
 #include "dim.cuh"
 #include "finalize.cuh"
 #include "groupdirect.cuh"
+#include "multi.cuh"
 
 namespace tqp {
 
@@ -48,8 +53,8 @@ bool lower_group_direct(const tqp_table* t, const GroupArgs& A, long long max_gr
 
 constexpr int kBatchTile = 1024;
 constexpr int kBatchStages = 3;
-constexpr int kJobFilter = 1, kJobGroup = 2, kJobJoin = 3;
-constexpr int kKinds = 3;  // scan bodies: filter, group-by, joined aggregation
+constexpr int kJobFilter = 1, kJobGroup = 2, kJobJoin = 3, kJobMulti = 4;
+constexpr int kKinds = 4;  // scan bodies: filter, group-by, joined aggregation, shared filter
 constexpr int kFlatThreads = 256;
 constexpr int kFillPer = 4096;  // 16-byte units per fill block
 constexpr int kRowsPer = 2048;  // elements per block of the element-wise phases
@@ -89,6 +94,7 @@ struct alignas(16) ScanJob {
         FilterArgs f;
         GroupArgs g;
         PlanJoinArgs j;
+        MultiArgs m;
     } u;
 };
 static_assert(sizeof(ScanJob) % 16 == 0, "ScanJob is copied in 16-byte units");
@@ -234,6 +240,9 @@ template <> struct BodyArgs<GroupBody> {
 template <> struct BodyArgs<PlanJoinBody> {
     static __device__ __forceinline__ const PlanJoinArgs& of(const ScanJob& j) { return j.u.j; }
 };
+template <> struct BodyArgs<MultiBody> {
+    static __device__ __forceinline__ const MultiArgs& of(const ScanJob& j) { return j.u.m; }
+};
 
 constexpr int kJobBytes = (sizeof(ScanJob) + 127) / 128 * 128;
 template <class Body>
@@ -366,11 +375,15 @@ struct tqp_batch {
     std::vector<int32_t> maps;
     long long fill_blocks = 0, row_blocks = 0, num_blocks = 0, slot_blocks = 0, compact_blocks = 0, top0_blocks = 0,
               sel_blocks = 0, grange_blocks = 0, gdirect_blocks = 0, fold_blocks = 0;
-    long long scan_chunks[kKinds] = {0, 0, 0};
+    long long scan_chunks[kKinds] = {0, 0, 0, 0};
+    // lookup tables and outputs of the shared scans (one blob; per job its offset)
+    std::vector<unsigned char> mblob;
+    std::vector<size_t> mblob_off;
+    unsigned char* d_mblob = nullptr;
     std::vector<long long> level_blocks;
     size_t off_fill = 0, off_row = 0, off_num = 0, off_slot = 0, off_compact = 0, off_top0 = 0, off_sel = 0,
            off_grange = 0, off_gdirect = 0, off_fold = 0;
-    size_t off_scan[kKinds] = {0, 0, 0};
+    size_t off_scan[kKinds] = {0, 0, 0, 0};
     std::vector<size_t> off_level;
     // small zeroed counters share one slab (one fill range)
     unsigned char* slab = nullptr;
@@ -379,7 +392,7 @@ struct tqp_batch {
     FillRange* d_fill = nullptr;
     int64_t** d_zero = nullptr;
     BuildJob* d_build = nullptr;
-    ScanJob* d_scan[kKinds] = {nullptr, nullptr, nullptr};
+    ScanJob* d_scan[kKinds] = {nullptr, nullptr, nullptr, nullptr};
     CompactJob* d_compact = nullptr;
     FinJob* d_fin = nullptr;
     TopJob* d_top = nullptr;
@@ -387,9 +400,9 @@ struct tqp_batch {
     FoldJob* d_fold = nullptr;
     std::vector<TopItem*> d_levels;
     int32_t* d_maps = nullptr;
-    unsigned long long* d_ticket[kKinds] = {nullptr, nullptr, nullptr};
-    size_t scan_smem[kKinds] = {0, 0, 0};
-    int scan_grid[kKinds] = {0, 0, 0};
+    unsigned long long* d_ticket[kKinds] = {nullptr, nullptr, nullptr, nullptr};
+    size_t scan_smem[kKinds] = {0, 0, 0, 0};
+    int scan_grid[kKinds] = {0, 0, 0, 0};
     // plans run through the single-plan path, and their scratch
     std::vector<tqp_plan> fb_plans;
     std::vector<tqp_result> fb_res;
@@ -824,6 +837,116 @@ static bool batchable(const tqp_ctx* ctx, const tqp_plan* p, const tqp_result* r
     return true;
 }
 
+// Filter-only work of one plan (counts and sum, no row ids): a candidate for a
+// shared scan.
+struct SharedCand {
+    const tqp_plan* p;
+    const tqp_result* r;
+    bool sum;
+    int64_t* cnt;
+    int64_t* cnt2;
+};
+
+static bool same_table(const tqp_table* a, const tqp_table* b) {
+    if (a == b) return true;
+    if (a->num_rows != b->num_rows || a->num_cols != b->num_cols) return false;
+    for (int c = 0; c < a->num_cols; ++c)
+        if (a->cols[c].data != b->cols[c].data || a->cols[c].type != b->cols[c].type) return false;
+    return true;
+}
+
+// One shared scan of `members` (indices into qs) over table t.
+static tqp_status add_multi_job(tqp_batch* b, const tqp_table* t, const std::vector<MqQuery>& qs,
+                                const std::vector<int>& members) {
+    tqp_ctx* ctx = b->ctx;
+    // the batch's tile size, halved until the stages fit beside the tables
+    std::vector<int> cols;
+    for (int m : members) cols.insert(cols.end(), qs[m].cols.begin(), qs[m].cols.end());
+    std::sort(cols.begin(), cols.end());
+    cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
+    int stage_row = 0;
+    for (int c : cols) stage_row += t->cols[c].type == TQP_I64 ? 8 : (t->cols[c].type == TQP_I32 ? 4 : 1);
+    const long long room =
+        static_cast<long long>(ctx->smem_optin) - 1024 - kHeaderBytes - kJobBytes - body_bytes<MultiBody>();
+    int T = b->tile;
+    while (T > kBatchTile &&
+           static_cast<long long>(kBatchStages) * (static_cast<long long>(T) * stage_row + 128LL * kMaxStaged) > room)
+        T /= 2;
+    const tqp_tuning tu{T, kBatchStages, 2, 1};
+    ScanJob J;
+    memset(&J, 0, sizeof(J));
+    J.kind = kJobMulti;
+    MultiArgs& A = J.u.m;
+    std::vector<unsigned char> blob;
+    size_t smem = 0;
+    int per_sm = 0;
+    TQP_TRY(mq_lower_group(ctx, t, qs, members, &tu, kJobBytes + body_bytes<MultiBody>(), &A, &blob, &smem, &per_sm));
+    if (A.G.ntiles == 0) {  // an empty table: every output is zero
+        for (int m : members) {
+            const MqOut& o = qs[m].out;
+            for (int64_t* z : {o.count, o.count2, o.sum})
+                if (z) b->zero.push_back(z);
+        }
+        return TQP_OK;
+    }
+    const size_t acc_bytes = (2 * kMqMax + 2) * sizeof(unsigned long long);
+    A.acc = static_cast<unsigned long long*>(balloc(b, acc_bytes));
+    if (!A.acc) return arena_oom(ctx, acc_bytes);
+    add_fill(b, A.acc, acc_bytes, kZero16);
+    A.ctl.err = ctx->d_err;
+    A.ctl.wait_cap = ctx->wait_cap;
+    const size_t off = (b->mblob.size() + 15) / 16 * 16;
+    b->mblob.resize(off + blob.size());
+    memcpy(b->mblob.data() + off, blob.data(), blob.size());
+    b->mblob_off.push_back(off);
+    b->scan[kJobMulti - 1].push_back(J);
+    return TQP_OK;
+}
+
+// Pack the filter-only work of plans over the same table into shared scans;
+// a plan alone on its table, or one that fits no pack, keeps its own filter
+// scan.
+static tqp_status add_shared_jobs(tqp_batch* b, const std::vector<SharedCand>& cands) {
+    std::vector<bool> done(cands.size(), false);
+    for (size_t i = 0; i < cands.size(); ++i) {
+        if (done[i]) continue;
+        std::vector<size_t> same;
+        for (size_t j = i; j < cands.size(); ++j)
+            if (!done[j] && same_table(cands[i].p->fact, cands[j].p->fact)) {
+                same.push_back(j);
+                done[j] = true;
+            }
+        auto single = [&](size_t k) {
+            const SharedCand& c = cands[k];
+            return add_filter_job(b, c.p, c.r, false, c.sum, c.cnt, c.cnt2);
+        };
+        if (same.size() == 1) {
+            TQP_TRY(single(same[0]));
+            continue;
+        }
+        const tqp_table* t = cands[i].p->fact;
+        std::vector<MqQuery> qs(same.size());
+        for (size_t k = 0; k < same.size(); ++k) {
+            const SharedCand& c = cands[same[k]];
+            TQP_TRY(mq_lower_query(t, c.p->preds, c.p->npreds, c.sum ? &c.p->sum_expr : nullptr, &qs[k]));
+            qs[k].out.count = c.cnt;
+            qs[k].out.count2 = c.cnt2;
+            qs[k].out.sum = c.sum ? c.r->d_sum : nullptr;
+            qs[k].out.rlo = 0;
+            qs[k].out.rhi = t->num_rows;
+        }
+        std::vector<std::vector<int>> groups;
+        std::vector<int> singles;
+        mq_pack(t, qs, &groups, &singles);
+        for (int k : singles) TQP_TRY(single(same[k]));
+        for (const auto& g : groups) {
+            if (g.size() == 1) TQP_TRY(single(same[g[0]]));
+            else TQP_TRY(add_multi_job(b, t, qs, g));
+        }
+    }
+    return TQP_OK;
+}
+
 static tqp_status lower_batch(tqp_batch* b, const tqp_plan* plans, const tqp_result* res, int32_t n) {
     // per plan at most 6 counters (group table, key ranges, top-k, filter, a
     // count, spare) and the tickets
@@ -832,6 +955,7 @@ static tqp_status lower_batch(tqp_batch* b, const tqp_plan* plans, const tqp_res
     if (!b->slab) return arena_oom(b->ctx, b->slab_bytes);
     add_fill(b, b->slab, b->slab_bytes, kZero16);
     for (int k = 0; k < kKinds; ++k) b->d_ticket[k] = counter(b);
+    std::vector<SharedCand> shared;
     for (int32_t i = 0; i < n; ++i) {
         const tqp_plan* p = &plans[i];
         const tqp_result* r = &res[i];
@@ -855,21 +979,21 @@ static tqp_status lower_batch(tqp_batch* b, const tqp_plan* plans, const tqp_res
         if (grouped) TQP_TRY(add_group_job(b, p, r));
         if (ids || sum || cnt) {
             if (!cnt) cnt = reinterpret_cast<int64_t*>(counter(b));
-            TQP_TRY(add_filter_job(b, p, r, ids, sum, cnt, cnt2));
+            if (ids) TQP_TRY(add_filter_job(b, p, r, ids, sum, cnt, cnt2));
+            else shared.push_back(SharedCand{p, r, sum, cnt, cnt2});
         }
     }
-    return TQP_OK;
+    return add_shared_jobs(b, shared);
 }
 
-static long long job_tiles(const ScanJob& j) {
-    return j.kind == kJobFilter ? j.u.f.G.ntiles : j.kind == kJobGroup ? j.u.g.G.ntiles : j.u.j.G.ntiles;
+static const ScanGeom& job_geom(const ScanJob& j) {
+    return j.kind == kJobFilter ? j.u.f.G : j.kind == kJobGroup ? j.u.g.G : j.kind == kJobJoin ? j.u.j.G : j.u.m.G;
 }
+static long long job_tiles(const ScanJob& j) { return job_geom(j).ntiles; }
 static EngineCtl& job_ctl(ScanJob& j) {
-    return j.kind == kJobFilter ? j.u.f.ctl : j.kind == kJobGroup ? j.u.g.ctl : j.u.j.ctl;
+    return j.kind == kJobFilter ? j.u.f.ctl : j.kind == kJobGroup ? j.u.g.ctl : j.kind == kJobJoin ? j.u.j.ctl : j.u.m.ctl;
 }
-static int job_stage_bytes(const ScanJob& j) {
-    return j.kind == kJobFilter ? j.u.f.G.stage_bytes : j.kind == kJobGroup ? j.u.g.G.stage_bytes : j.u.j.G.stage_bytes;
-}
+static int job_stage_bytes(const ScanJob& j) { return job_geom(j).stage_bytes; }
 
 // Chunks of equal size across the jobs of one kind (a job's last chunk may be
 // short): about four per persistent CTA, so that the uneven tails of the
@@ -1037,6 +1161,9 @@ static tqp_status batch_launch(tqp_batch* b, cudaStream_t st) {
     if (b->scan_chunks[2])
         k_b_scan<PlanJoinBody><<<b->scan_grid[2], kEngineThreads, b->scan_smem[2], st>>>(
             b->d_scan[2], M + b->off_scan[2], b->d_ticket[2], b->scan_chunks[2]);
+    if (b->scan_chunks[3])
+        k_b_scan<MultiBody><<<b->scan_grid[3], kEngineThreads, b->scan_smem[3], st>>>(
+            b->d_scan[3], M + b->off_scan[3], b->d_ticket[3], b->scan_chunks[3]);
     if (b->fold_blocks)
         k_b_fold<<<static_cast<unsigned>(b->fold_blocks), kFoldThreads, 0, st>>>(b->d_fold, M + b->off_fold);
     if (b->compact_blocks)
@@ -1090,11 +1217,15 @@ static tqp_status batch_prepare(tqp_ctx* ctx, const tqp_plan* plans, const tqp_r
     TQP_TRY(scan_shape<FilterBody>(b, 0));
     TQP_TRY(scan_shape<GroupBody>(b, 1));
     TQP_TRY(scan_shape<PlanJoinBody>(b, 2));
+    TQP_TRY(scan_shape<MultiBody>(b, 3));
     plan_top_levels(b);
     build_maps(b);
     TQP_TRY(upload(b, b->fill, &b->d_fill, st));
     TQP_TRY(upload(b, b->zero, &b->d_zero, st));
     TQP_TRY(upload(b, b->build, &b->d_build, st));
+    TQP_TRY(upload(b, b->mblob, &b->d_mblob, st));
+    for (size_t i = 0; i < b->scan[kJobMulti - 1].size(); ++i)
+        mq_bind(&b->scan[kJobMulti - 1][i].u.m, b->d_mblob + b->mblob_off[i]);
     for (int k = 0; k < kKinds; ++k) TQP_TRY(upload(b, b->scan[k], &b->d_scan[k], st));
     TQP_TRY(upload(b, b->compact, &b->d_compact, st));
     TQP_TRY(upload(b, b->fin, &b->d_fin, st));

@@ -184,6 +184,11 @@ tqp_status allow_smem(const tqp_ctx* ctx, const void* kernel, SmemFlags& flags);
 // kernel: unlike a pageable memcpy it can be captured in a CUDA graph).
 tqp_status set_device_i64(long long* d_ptr, long long value, cudaStream_t stream);
 
+// The single-query filter scan (tqp_filter's body, in the caller's arena).
+tqp_status launch_filter(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* preds, int32_t npreds,
+                         const tqp_expr* sum_expr, int64_t* d_sum, int32_t* d_row_ids, int64_t capacity,
+                         int64_t* d_count, cudaStream_t stream, const tqp_tuning* force);
+
 // One-shot batched run of n plans in ctx's per-call scratch on `stream` (the
 // body of tqp_run_plans; the server calls it with a slot's sub-context).
 tqp_status run_plans_on(tqp_ctx* ctx, const tqp_plan* plans, const tqp_result* res, int32_t n, cudaStream_t stream);

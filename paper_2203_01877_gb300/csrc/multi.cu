@@ -1,0 +1,382 @@
+// tqp_filter_shared: shared scans of many filter queries (see multi.cuh for
+// the kernel).  This file holds the host side: lowering each query, packing
+// queries into launches (at most 32 queries, 8 staged columns, 2 distinct sum
+// expressions and the shared-memory table budget per launch), tabulating the
+// interval masks of every condition column, and the launches themselves.
+// The batched executor (batch.cu) packs the filter-only plans of a batch with
+// the same functions.
+#include <algorithm>
+#include <climits>
+#include <cstdio>
+#include <vector>
+
+#include "host.h"
+#include "multi.cuh"
+
+namespace tqp {
+
+static void type_range(int type, int64_t* tmin, int64_t* tmax) {
+    if (type == TQP_I32) {
+        *tmin = INT32_MIN;
+        *tmax = INT32_MAX;
+    } else if (type == TQP_U8) {
+        *tmin = 0;
+        *tmax = 255;
+    } else {
+        *tmin = INT64_MIN;
+        *tmax = INT64_MAX;
+    }
+}
+
+// The range test of a lowered condition (the engine's Cond semantics).
+static bool cond_pass(const Cond& c, int64_t x) {
+    const bool in = static_cast<uint64_t>(x) - static_cast<uint64_t>(c.lo) <= c.span;
+    return in != (c.negate != 0);
+}
+
+static bool same_expr(const DExpr& a, const DExpr& b) {
+    if (a.n != b.n) return false;
+    for (int i = 0; i < a.n; ++i)
+        if (a.op[i] != b.op[i] || a.v[i] != b.v[i]) return false;
+    return true;
+}
+
+tqp_status mq_lower_query(const tqp_table* t, const tqp_pred* preds, int32_t npreds, const tqp_expr* sum_expr,
+                          MqQuery* q) {
+    *q = MqQuery();
+    TQP_TRY(lower_preds(t, preds, npreds, q->cond, &q->ncond));
+    std::vector<int> cols;
+    for (int i = 0; i < q->ncond; ++i) cols.push_back(q->cond[i].col);
+    if (sum_expr) {
+        TQP_TRY(lower_expr(sum_expr, t->num_cols, &q->sum));
+        q->has_sum = true;
+        expr_cols(q->sum, cols);
+        // the closed product form is required: try it with every column staged
+        ScanGeom G;
+        memset(&G, 0, sizeof(G));
+        G.ncols = t->num_cols;
+        for (int c = 0; c < t->num_cols; ++c) {
+            G.col[c].slot = c;
+            G.col[c].type = t->cols[c].type;
+        }
+        ProdForm pf;
+        q->closed = lower_prod(q->sum, G, &pf);
+    }
+    std::sort(cols.begin(), cols.end());
+    cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
+    q->cols = cols;
+    return TQP_OK;
+}
+
+// Interval masks of every condition column of the queries `members` (in that
+// lane order).  Fills A->nq, A->all, A->ncols and A->c[] (all but the stage
+// offsets); false when the tables exceed the shared-memory budget.
+static bool mq_tables(const tqp_table* t, const std::vector<MqQuery>& qs, const std::vector<int>& members,
+                      MultiArgs* A, std::vector<uint32_t>* words, std::vector<int64_t>* breaks) {
+    const int nq = static_cast<int>(members.size());
+    A->nq = nq;
+    A->all = nq >= 32 ? 0xffffffffu : ((1u << nq) - 1u);
+    A->ncols = 0;
+    words->clear();
+    breaks->clear();
+    std::vector<int> ccols;
+    for (int m : members)
+        for (int i = 0; i < qs[m].ncond; ++i) ccols.push_back(qs[m].cond[i].col);
+    std::sort(ccols.begin(), ccols.end());
+    ccols.erase(std::unique(ccols.begin(), ccols.end()), ccols.end());
+
+    struct ColTab {
+        int col, type;
+        std::vector<int64_t> B;   // breakpoints inside the type's range, ascending
+        std::vector<uint32_t> M;  // B.size() + 1 interval masks
+    };
+    std::vector<ColTab> tabs;
+    for (int c : ccols) {
+        ColTab ct;
+        ct.col = c;
+        ct.type = t->cols[c].type;
+        int64_t tmin, tmax;
+        type_range(ct.type, &tmin, &tmax);
+        for (int m : members)
+            for (int i = 0; i < qs[m].ncond; ++i) {
+                const Cond& cd = qs[m].cond[i];
+                if (cd.col != c) continue;
+                const uint64_t ends[2] = {static_cast<uint64_t>(cd.lo), static_cast<uint64_t>(cd.lo) + cd.span + 1u};
+                for (uint64_t e : ends) {
+                    // a breakpoint at or below the smallest value, or above the
+                    // largest, separates no two values of the column
+                    const int64_t b = static_cast<int64_t>(e);
+                    if (b > tmin && b <= tmax) ct.B.push_back(b);
+                }
+            }
+        std::sort(ct.B.begin(), ct.B.end());
+        ct.B.erase(std::unique(ct.B.begin(), ct.B.end()), ct.B.end());
+        auto mask_at = [&](int64_t x) {
+            uint32_t mk = 0;
+            for (int l = 0; l < nq; ++l) {
+                const MqQuery& q = qs[members[l]];
+                bool ok = true;
+                for (int i = 0; i < q.ncond; ++i)
+                    if (q.cond[i].col == c && !cond_pass(q.cond[i], x)) ok = false;
+                if (ok) mk |= 1u << l;
+            }
+            return mk;
+        };
+        // every breakpoint is > tmin, so B[0] - 1 is a value of the column
+        ct.M.push_back(mask_at(ct.B.empty() ? tmin : ct.B[0] - 1));
+        for (int64_t b : ct.B) ct.M.push_back(mask_at(b));
+        if (ct.B.empty()) {
+            A->all &= ct.M[0];  // the same outcome for every value: no lookup needed
+            continue;
+        }
+        tabs.push_back(ct);
+    }
+    if (static_cast<int>(tabs.size()) > kMaxStaged) return false;
+    // direct tables where they fit beside the searched form of the later columns
+    std::vector<size_t> searched_words(tabs.size() + 1, 0);
+    for (size_t i = tabs.size(); i-- > 0;) searched_words[i] = searched_words[i + 1] + tabs[i].B.size() + 1;
+    for (size_t i = 0; i < tabs.size(); ++i) {
+        const ColTab& ct = tabs[i];
+        MqCol& mc = A->c[A->ncols++];
+        memset(&mc, 0, sizeof(mc));
+        mc.col = ct.col;
+        mc.type = ct.type;
+        const uint64_t span = static_cast<uint64_t>(ct.B.back()) - static_cast<uint64_t>(ct.B.front());
+        const size_t len = span <= static_cast<uint64_t>(kMqDirectMax - 2) ? static_cast<size_t>(span) + 2 : 0;
+        mc.off = static_cast<int32_t>(words->size());
+        if (len && words->size() + len + searched_words[i + 1] <= static_cast<size_t>(kMqWords)) {
+            mc.direct = 1;
+            mc.base = ct.B.front();
+            mc.len = static_cast<int32_t>(len);
+            words->push_back(ct.M[0]);
+            size_t j = 0;  // breakpoints <= the entry's value
+            for (size_t d = 0; d + 1 < len; ++d) {
+                const int64_t x = static_cast<int64_t>(static_cast<uint64_t>(ct.B.front()) + d);
+                while (j < ct.B.size() && ct.B[j] <= x) ++j;
+                words->push_back(ct.M[j]);
+            }
+        } else {
+            mc.direct = 0;
+            mc.len = static_cast<int32_t>(ct.B.size());
+            mc.boff = static_cast<int32_t>(breaks->size());
+            int s = 1;
+            while (s * 2 <= mc.len) s *= 2;
+            mc.steps = s;
+            for (int64_t b : ct.B) breaks->push_back(b);
+            for (uint32_t mk : ct.M) words->push_back(mk);
+        }
+    }
+    return words->size() <= static_cast<size_t>(kMqWords) && breaks->size() <= static_cast<size_t>(kMqBreaks);
+}
+
+// Columns a launch stages: the condition columns that need a lookup and every
+// column of the sum expressions.
+static std::vector<int> mq_staged(const std::vector<MqQuery>& qs, const std::vector<int>& members,
+                                  const MultiArgs& A) {
+    std::vector<int> staged;
+    for (int k = 0; k < A.ncols; ++k) staged.push_back(A.c[k].col);
+    for (int m : members)
+        if (qs[m].has_sum) expr_cols(qs[m].sum, staged);
+    std::sort(staged.begin(), staged.end());
+    staged.erase(std::unique(staged.begin(), staged.end()), staged.end());
+    return staged;
+}
+
+// Distinct sum expressions of `members`, in first-use order.
+static std::vector<DExpr> mq_exprs(const std::vector<MqQuery>& qs, const std::vector<int>& members) {
+    std::vector<DExpr> ex;
+    for (int m : members) {
+        if (!qs[m].has_sum) continue;
+        bool seen = false;
+        for (const DExpr& e : ex) seen = seen || same_expr(e, qs[m].sum);
+        if (!seen) ex.push_back(qs[m].sum);
+    }
+    return ex;
+}
+
+static bool mq_fits(const tqp_table* t, const std::vector<MqQuery>& qs, const std::vector<int>& members) {
+    if (members.size() > static_cast<size_t>(kMqMax)) return false;
+    if (mq_exprs(qs, members).size() > static_cast<size_t>(kMqExprs)) return false;
+    MultiArgs A;
+    memset(&A, 0, sizeof(A));
+    std::vector<uint32_t> w;
+    std::vector<int64_t> b;
+    if (!mq_tables(t, qs, members, &A, &w, &b)) return false;
+    return mq_staged(qs, members, A).size() <= static_cast<size_t>(kMaxStaged);
+}
+
+void mq_pack(const tqp_table* t, const std::vector<MqQuery>& qs, std::vector<std::vector<int>>* groups,
+             std::vector<int>* singles) {
+    groups->clear();
+    singles->clear();
+    for (int i = 0; i < static_cast<int>(qs.size()); ++i) {
+        const MqQuery& q = qs[i];
+        if ((q.has_sum && !q.closed) || q.cols.size() > static_cast<size_t>(kMaxStaged)) {
+            singles->push_back(i);
+            continue;
+        }
+        bool placed = false;
+        for (auto& g : *groups) {  // first fit
+            g.push_back(i);
+            if (mq_fits(t, qs, g)) {
+                placed = true;
+                break;
+            }
+            g.pop_back();
+        }
+        if (placed) continue;
+        std::vector<int> g{i};
+        if (mq_fits(t, qs, g)) groups->push_back(g);
+        else singles->push_back(i);
+    }
+}
+
+tqp_status mq_lower_group(const tqp_ctx* ctx, const tqp_table* t, const std::vector<MqQuery>& qs,
+                          const std::vector<int>& members, const tqp_tuning* tu_in, int body_smem, MultiArgs* A,
+                          std::vector<unsigned char>* blob, size_t* smem, int* ctas_per_sm) {
+    memset(A, 0, sizeof(*A));
+    std::vector<uint32_t> words;
+    std::vector<int64_t> breaks;
+    if (!mq_tables(t, qs, members, A, &words, &breaks))
+        return fail(TQP_ERR_UNSUPPORTED, "shared scan: lookup tables exceed the shared-memory budget");
+    const std::vector<int> staged = mq_staged(qs, members, *A);
+    if (staged.size() > static_cast<size_t>(kMaxStaged))
+        return fail(TQP_ERR_UNSUPPORTED, "shared scan: more than %d columns", kMaxStaged);
+    TQP_TRY(check_device_cols(t, staged, "tqp_filter_shared"));
+    int bpr = 0;
+    for (int c : staged) bpr += t->cols[c].type == TQP_I64 ? 8 : (t->cols[c].type == TQP_I32 ? 4 : 1);
+    const tqp_tuning tu = tu_in ? *tu_in : default_tuning(ctx, bpr, body_smem);
+    TQP_TRY(make_geom(ctx, t, staged, tu, body_smem, &A->G, smem));
+    *ctas_per_sm = tu.ctas_per_sm;
+    for (int k = 0; k < A->ncols; ++k) A->c[k].soff = A->G.col[A->c[k].col].soff;
+    const std::vector<DExpr> ex = mq_exprs(qs, members);
+    A->nexpr = static_cast<int32_t>(ex.size());
+    for (size_t e = 0; e < ex.size(); ++e) {
+        if (!lower_prod(ex[e], A->G, &A->e[e]))
+            return fail(TQP_ERR_UNSUPPORTED, "shared scan: sum expression is not a product of affine factors");
+        // the table column of each factor (ragged tiles read the columns directly)
+        for (int i = 0; i < 2; ++i) {
+            A->ecol[e][i] = -1;
+            if (A->e[e].kind[i] == kFacConst) continue;
+            for (int c = 0; c < A->G.ncols; ++c)
+                if (A->G.col[c].slot >= 0 && A->G.col[c].soff == A->e[e].soff[i]) A->ecol[e][i] = c;
+        }
+    }
+    A->esel = 0;
+    std::vector<MqOut> outs;
+    for (size_t l = 0; l < members.size(); ++l) {
+        const MqQuery& q = qs[members[l]];
+        if (q.has_sum && ex.size() > 1 && same_expr(q.sum, ex[1])) A->esel |= 1u << l;
+        outs.push_back(q.out);
+    }
+    A->nwords = static_cast<int32_t>(words.size());
+    A->nbreaks = static_cast<int32_t>(breaks.size());
+    // blob: words | breakpoints (8-aligned) | outputs (8-aligned)
+    const size_t wbytes = (words.size() * 4 + 15) / 16 * 16;
+    const size_t bbytes = (breaks.size() * 8 + 15) / 16 * 16;
+    blob->assign(wbytes + bbytes + outs.size() * sizeof(MqOut), 0);
+    if (!words.empty()) memcpy(blob->data(), words.data(), words.size() * 4);
+    if (!breaks.empty()) memcpy(blob->data() + wbytes, breaks.data(), breaks.size() * 8);
+    memcpy(blob->data() + wbytes + bbytes, outs.data(), outs.size() * sizeof(MqOut));
+    // device offsets (set to real pointers by mq_bind)
+    A->words = reinterpret_cast<const uint32_t*>(static_cast<uintptr_t>(0));
+    A->breaks = reinterpret_cast<const int64_t*>(static_cast<uintptr_t>(wbytes));
+    A->out = reinterpret_cast<const MqOut*>(static_cast<uintptr_t>(wbytes + bbytes));
+    return TQP_OK;
+}
+
+void mq_bind(MultiArgs* A, const unsigned char* d_blob) {
+    A->words = reinterpret_cast<const uint32_t*>(d_blob + reinterpret_cast<uintptr_t>(A->words));
+    A->breaks = reinterpret_cast<const int64_t*>(d_blob + reinterpret_cast<uintptr_t>(A->breaks));
+    A->out = reinterpret_cast<const MqOut*>(d_blob + reinterpret_cast<uintptr_t>(A->out));
+}
+
+__global__ void __launch_bounds__(kEngineThreads, MultiBody::kMinBlocks) k_filter_multi(const __grid_constant__ MultiArgs P) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const MultiArgs& A = stage_args(P, smem + kHeaderBytes);
+    MultiBody body(A, smem + kHeaderBytes + args_bytes<MultiArgs>());
+    run_engine(A.G, A.ctl, body, smem, args_bytes<MultiArgs>());
+}
+
+// Zero outputs of queries over an empty table.
+static tqp_status mq_zero(const MqOut& o, cudaStream_t st) {
+    if (o.count) TQP_CUDA(cudaMemsetAsync(o.count, 0, sizeof(int64_t), st));
+    if (o.count2) TQP_CUDA(cudaMemsetAsync(o.count2, 0, sizeof(int64_t), st));
+    if (o.sum) TQP_CUDA(cudaMemsetAsync(o.sum, 0, sizeof(int64_t), st));
+    return TQP_OK;
+}
+
+static tqp_status shared_run(tqp_ctx* ctx, const tqp_table* t, const tqp_scan_query* q, int32_t nq,
+                             int32_t* launch_of, cudaStream_t st) {
+    std::vector<MqQuery> qs(nq);
+    for (int i = 0; i < nq; ++i) {
+        TQP_TRY(mq_lower_query(t, q[i].preds, q[i].npreds, q[i].has_sum ? &q[i].sum_expr : nullptr, &qs[i]));
+        qs[i].out.count = q[i].d_count;
+        qs[i].out.sum = q[i].has_sum ? q[i].d_sum : nullptr;
+        qs[i].out.rlo = 0;
+        qs[i].out.rhi = t->num_rows;
+    }
+    std::vector<std::vector<int>> groups;
+    std::vector<int> singles;
+    mq_pack(t, qs, &groups, &singles);
+    if (launch_of) {
+        for (int i = 0; i < nq; ++i) launch_of[i] = -1;
+        for (size_t g = 0; g < groups.size(); ++g)
+            for (int m : groups[g]) launch_of[m] = static_cast<int32_t>(g);
+    }
+    static SmemFlags attr;
+    TQP_TRY(allow_smem(ctx, reinterpret_cast<const void*>(k_filter_multi), attr));
+    const int body_smem = MultiBody::kSmemBytes + args_bytes<MultiArgs>();
+    for (const auto& g : groups) {
+        MultiArgs A;
+        std::vector<unsigned char> blob;
+        size_t smem = 0;
+        int per_sm = 0;
+        TQP_TRY(mq_lower_group(ctx, t, qs, g, nullptr, body_smem, &A, &blob, &smem, &per_sm));
+        if (A.G.ntiles == 0) {
+            for (int m : g) TQP_TRY(mq_zero(qs[m].out, st));
+            continue;
+        }
+        const size_t acc_bytes = (2 * kMqMax + 2) * sizeof(unsigned long long);
+        unsigned char* d = static_cast<unsigned char*>(arena_alloc(ctx, acc_bytes + blob.size()));
+        if (!d) return arena_oom(ctx, acc_bytes + blob.size());
+        TQP_CUDA(cudaMemsetAsync(d, 0, acc_bytes, st));
+        TQP_CUDA(cudaMemcpyAsync(d + acc_bytes, blob.data(), blob.size(), cudaMemcpyHostToDevice, st));
+        mq_bind(&A, d + acc_bytes);
+        A.ctl.ticket = reinterpret_cast<unsigned long long*>(d);
+        A.acc = reinterpret_cast<unsigned long long*>(d) + 1;
+        A.ctl.err = ctx->d_err;
+        A.ctl.wait_cap = ctx->wait_cap;
+        const int grid = engine_grid(ctx, reinterpret_cast<const void*>(k_filter_multi), smem, A.G.ntiles, per_sm);
+        A.ctl.chunk_tiles = (A.G.ntiles + grid - 1) / grid;
+        A.ctl.nchunks = (A.G.ntiles + A.ctl.chunk_tiles - 1) / A.ctl.chunk_tiles;
+        k_filter_multi<<<static_cast<unsigned>(A.ctl.nchunks), kEngineThreads, smem, st>>>(A);
+        TQP_CUDA(cudaGetLastError());
+    }
+    for (int i : singles)
+        TQP_TRY(launch_filter(ctx, t, q[i].preds, q[i].npreds, q[i].has_sum ? &q[i].sum_expr : nullptr,
+                              q[i].has_sum ? q[i].d_sum : nullptr, nullptr, 0, q[i].d_count, st, nullptr));
+    return TQP_OK;
+}
+
+}  // namespace tqp
+
+using namespace tqp;
+
+extern "C" tqp_status tqp_filter_shared(tqp_ctx* ctx, const tqp_table* t, const tqp_scan_query* queries, int32_t nq,
+                                        int32_t* launch_of, void* stream) {
+    clear_error();
+    TQP_TRY(check_ctx(ctx));
+    TQP_TRY(check_table(t, "tqp_filter_shared"));
+    if (nq < 0) return fail(TQP_ERR_INVALID_ARG, "nq < 0");
+    if (nq > 0 && !queries) return fail(TQP_ERR_INVALID_ARG, "queries is NULL");
+    for (int i = 0; i < nq; ++i) {
+        if (!queries[i].d_count) return fail(TQP_ERR_INVALID_ARG, "query %d: d_count is NULL", i);
+        if ((queries[i].has_sum != 0) != (queries[i].d_sum != nullptr))
+            return fail(TQP_ERR_INVALID_ARG, "query %d: has_sum and d_sum must both be set or both be unset", i);
+    }
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(TQP_ERR_CUDA, "cannot select device %d", ctx->device);
+    arena_reset(ctx);
+    return shared_run(ctx, t, queries, nq, launch_of, static_cast<cudaStream_t>(stream));
+}

@@ -1,0 +1,308 @@
+// Shared scans: one pass over a table evaluates the filters of up to 32
+// queries at once (each query: a conjunction of range predicates, a count of
+// its passing rows and optionally the sum of a closed-form expression over
+// them, exactly what tqp_filter computes without row ids).
+//
+// The paper runs one query at a time (Section 4.3); a served workload of many
+// filter queries over one resident table would read the table once per
+// query.  Here the staged scan engine streams the table once and every row is
+// tested against all queries:
+//   * predicates, per column: the breakpoints of every query's range
+//     conditions on that column cut the value line into elementary intervals
+//     on which each condition's outcome is constant; the host tabulates, per
+//     interval, the 32-bit mask of queries whose conditions on that column all
+//     pass.  A row's pass mask is the AND over the condition columns of the
+//     mask of the interval its value falls in: a direct table lookup when the
+//     breakpoints span at most kMqDirectMax values, else a branch-free binary
+//     search over the sorted breakpoints.  The cost per row grows with the
+//     number of condition columns, not with the number of queries;
+//   * accumulation, transposed: lane q of every warp owns query q's count and
+//     sum.  For each row with a non-empty pass mask (found by a ballot) the
+//     row's mask and expression values are broadcast to the warp and every
+//     lane adds them to its own query when its bit is set; rows that pass no
+//     query cost nothing;
+//   * per-query row ranges: a query may cover only rows [rlo, rhi) of the
+//     scan (queries over slices of one table).  Per tile a ballot splits the
+//     queries into those covering the whole tile and those touching part of
+//     it; only the latter are tested row by row.
+// At most two distinct sum expressions per launch (each a product of two
+// affine factors of staged columns, the ProdForm of the single-query scan);
+// the host splits larger query sets into groups, one launch each.
+#pragma once
+
+#include <vector>
+
+#include "bodies.cuh"
+
+namespace tqp {
+
+constexpr int kMqMax = 32;          // queries per launch: one per lane
+constexpr int kMqExprs = 2;         // distinct sum expressions per launch
+constexpr int kMqWords = 5120;      // mask words of all lookup tables (shared memory)
+constexpr int kMqBreaks = 512;      // breakpoints of the searched tables (shared memory)
+constexpr int kMqDirectMax = 4096;  // direct tables: at most this many entries per column
+
+// One condition column of a launch.
+struct MqCol {
+    int32_t col;     // table column
+    int32_t soff;    // byte offset of the column inside a stage
+    int32_t type;
+    int32_t direct;  // 1: direct table, 0: searched breakpoints
+    int64_t base;    // direct: the value of entry 1 (entry 0: every smaller value)
+    int32_t len;     // direct: entries (the last one: its value and every larger value);
+                     // searched: breakpoints (len + 1 masks)
+    int32_t off;     // first mask word
+    int32_t boff;    // searched: first breakpoint
+    int32_t steps;   // searched: the largest power of two <= len (0 when len == 0)
+};
+
+// Outputs and row range of one query (device memory; read at the end of the
+// launch and once per chunk).
+struct MqOut {
+    int64_t* count;   // passing rows (nullable)
+    int64_t* count2;  // a second copy of the count (nullable)
+    int64_t* sum;     // sum of the query's expression (nullable)
+    int64_t rlo, rhi; // rows [rlo, rhi) of the scanned table
+};
+
+struct MultiArgs {
+    ScanGeom G;
+    EngineCtl ctl;
+    int32_t nq;
+    int32_t ncols;        // condition columns
+    int32_t nexpr;        // distinct sum expressions (0..kMqExprs)
+    uint32_t esel;        // bit q: query q sums expression 1 (else expression 0)
+    uint32_t all;         // bits of the nq queries
+    int32_t nwords;       // mask words used
+    int32_t nbreaks;      // breakpoints used
+    int32_t pad;
+    MqCol c[kMaxStaged];
+    ProdForm e[kMqExprs];
+    int32_t ecol[kMqExprs][2];   // table column of each factor (-1: constant)
+    const uint32_t* words;       // lookup masks (device)
+    const int64_t* breaks;       // sorted breakpoints of searched tables (device)
+    const MqOut* out;            // nq entries (device)
+    unsigned long long* acc;     // [2 q] sum, [2 q + 1] count, [2 kMqMax] completions (zeroed)
+};
+
+// Mask of the interval containing x in column table `mc`.
+__device__ __forceinline__ uint32_t mq_lookup(const MqCol& mc, int64_t x, const uint32_t* w, const int64_t* bk) {
+    if (mc.direct) {
+        int idx;
+        if (x < mc.base) {
+            idx = 0;
+        } else {
+            const uint64_t d = static_cast<uint64_t>(x) - static_cast<uint64_t>(mc.base);
+            idx = d >= static_cast<uint64_t>(mc.len - 1) ? mc.len - 1 : static_cast<int>(d) + 1;
+        }
+        return w[mc.off + idx];
+    }
+    // number of breakpoints <= x, by halving steps over the sorted breakpoints
+    const int64_t* b = bk + mc.boff;
+    int pos = 0;
+    for (int s = mc.steps; s > 0; s >>= 1)
+        if (pos + s <= mc.len && b[pos + s - 1] <= x) pos += s;
+    return w[mc.off + pos];
+}
+
+// Value of one affine factor at tile row r of a tile that is not full.
+__device__ __forceinline__ int64_t mq_factor_row(const ScanGeom& G, const TileView& v, const ProdForm& f, int i,
+                                                 int col, int r) {
+    const int kind = f.kind[i];
+    if (kind == kFacConst) return f.b[i];
+    const uint64_t x = static_cast<uint64_t>(col_val(G, v, col, r));
+    const uint64_t a = static_cast<uint64_t>(f.a[i]), b = static_cast<uint64_t>(f.b[i]);
+    if (kind == kFacPlain) return static_cast<int64_t>(x);
+    if (kind == kFacAdd) return static_cast<int64_t>(x + b);
+    if (kind == kFacRsub) return static_cast<int64_t>(b - x);
+    return static_cast<int64_t>(x * a + b);
+}
+
+struct MultiBody {
+    static constexpr int kMinBlocks = 2;
+    static constexpr int kSmemBytes = kMqWords * 4 + kMqBreaks * 8;
+    static constexpr int kU = 4;  // rows per lane per step
+
+    const MultiArgs& A;
+    const uint32_t* w;   // shared-memory copy of the masks
+    const int64_t* bk;   // shared-memory copy of the breakpoints
+    unsigned long long s = 0;  // lane q: query q's sum over this chunk
+    unsigned long long c = 0;  // lane q: query q's count
+    int64_t rlo = 0, rhi = 0;  // lane q: query q's row range
+    bool use1 = false;         // lane q sums expression 1
+
+    // Every thread of the CTA copies its share of the tables; the caller
+    // synchronises the CTA before the first tile.
+    __device__ MultiBody(const MultiArgs& a, unsigned char* sm) : A(a) {
+        uint32_t* ws = reinterpret_cast<uint32_t*>(sm);
+        int64_t* bs = reinterpret_cast<int64_t*>(sm + kMqWords * 4);
+        for (int i = threadIdx.x; i < a.nwords; i += blockDim.x) ws[i] = a.words[i];
+        for (int i = threadIdx.x; i < a.nbreaks; i += blockDim.x) bs[i] = a.breaks[i];
+        w = ws;
+        bk = bs;
+        const int lane = threadIdx.x % kWarp;
+        if (lane < a.nq) {
+            rlo = a.out[lane].rlo;
+            rhi = a.out[lane].rhi;
+        }
+        use1 = (a.esel >> lane) & 1u;
+    }
+
+    // kU rows per lane: rows rb + lane + 32 j of the tile.
+    __device__ __forceinline__ void step(const ScanGeom& G, const TileView& v, int rb, int lane, uint32_t full,
+                                         uint32_t part) {
+        constexpr int U = kU;
+        const int r0 = rb + lane;
+        uint32_t m[U];
+#pragma unroll
+        for (int j = 0; j < U; ++j) m[j] = (r0 + kWarp * j < v.rows) ? full : 0u;
+        if (part) {  // queries whose row range ends inside this tile: row by row
+            uint32_t p = part;
+            while (p) {
+                const int q = __ffs(p) - 1;
+                p &= p - 1;
+                const long long lo = __shfl_sync(0xffffffffu, static_cast<long long>(rlo), q);
+                const long long hi = __shfl_sync(0xffffffffu, static_cast<long long>(rhi), q);
+#pragma unroll
+                for (int j = 0; j < U; ++j) {
+                    const long long row = v.row0 + r0 + kWarp * j;
+                    if (r0 + kWarp * j < v.rows && row >= lo && row < hi) m[j] |= 1u << q;
+                }
+            }
+        }
+        // predicates: the interval masks of every condition column
+        for (int k = 0; k < A.ncols; ++k) {
+            const MqCol& mc = A.c[k];
+            int64_t x[U];
+            if (v.full) {
+                load_rows<U>(v.stage + mc.soff, mc.type, r0, x);
+            } else {
+#pragma unroll
+                for (int j = 0; j < U; ++j) x[j] = (r0 + kWarp * j < v.rows) ? col_val(G, v, mc.col, r0 + kWarp * j) : 0;
+            }
+#pragma unroll
+            for (int j = 0; j < U; ++j) m[j] &= mq_lookup(mc, x[j], w, bk);
+        }
+        uint32_t any[U];
+        uint32_t some = 0;
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            any[j] = __ballot_sync(0xffffffffu, m[j] != 0u);
+            some |= any[j];
+        }
+        if (!some) return;
+        // sum expressions of the lane's rows
+        int64_t v0[U], v1[U];
+#pragma unroll
+        for (int j = 0; j < U; ++j) v0[j] = v1[j] = 0;
+        if (A.nexpr > 0) {
+            if (v.full) {
+                prod_eval<U>(A.e[0], v.stage, r0, v0);
+                if (A.nexpr > 1) prod_eval<U>(A.e[1], v.stage, r0, v1);
+            } else {
+#pragma unroll
+                for (int j = 0; j < U; ++j) {
+                    const int r = r0 + kWarp * j;
+                    if (m[j]) {
+                        v0[j] = static_cast<int64_t>(
+                            static_cast<uint64_t>(mq_factor_row(G, v, A.e[0], 0, A.ecol[0][0], r)) *
+                            static_cast<uint64_t>(mq_factor_row(G, v, A.e[0], 1, A.ecol[0][1], r)));
+                        if (A.nexpr > 1)
+                            v1[j] = static_cast<int64_t>(
+                                static_cast<uint64_t>(mq_factor_row(G, v, A.e[1], 0, A.ecol[1][0], r)) *
+                                static_cast<uint64_t>(mq_factor_row(G, v, A.e[1], 1, A.ecol[1][1], r)));
+                    }
+                }
+            }
+        }
+        // transposed accumulation: lane q adds the rows that pass query q
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            uint32_t b = any[j];
+            while (b) {
+                const int src = __ffs(b) - 1;
+                b &= b - 1;
+                const uint32_t mr = __shfl_sync(0xffffffffu, m[j], src);
+                const long long a0 = __shfl_sync(0xffffffffu, static_cast<long long>(v0[j]), src);
+                long long a1 = 0;
+                if (A.nexpr > 1) a1 = __shfl_sync(0xffffffffu, static_cast<long long>(v1[j]), src);
+                if ((mr >> lane) & 1u) {
+                    s += static_cast<unsigned long long>(use1 ? a1 : a0);
+                    c += 1;
+                }
+            }
+        }
+    }
+
+    __device__ void pass1(const ScanGeom& G, const TileView& v, int cw, int lane) {
+        const long long t0 = v.row0, t1 = v.row0 + v.rows;
+        const bool covers = rlo <= t0 && t1 <= rhi;
+        const bool touches = rlo < t1 && rhi > t0;
+        const uint32_t full = __ballot_sync(0xffffffffu, covers) & A.all;
+        const uint32_t part = __ballot_sync(0xffffffffu, touches && !covers) & A.all;
+        if (!(full | part)) return;
+        const int rw = G.T / kConsumerWarps;  // a multiple of 128
+        for (int r = 0; r < rw; r += kU * kWarp) {
+            if (cw * rw + r >= v.rows) return;
+            step(G, v, cw * rw + r, lane, full, part);
+        }
+    }
+
+    __device__ void chunk_end(const ScanGeom&, long long, long long, long long, int, int lane) {
+        if (lane < A.nq) {
+            if (s) atomicAdd(&A.acc[2 * lane], s);
+            if (c) atomicAdd(&A.acc[2 * lane + 1], c);
+        }
+        s = 0;
+        c = 0;
+        __threadfence();
+        __syncwarp();
+        bool last = false;
+        if (lane == 0) last = last_completion(&A.acc[2 * kMqMax], A.ctl.nchunks);
+        last = __shfl_sync(0xffffffffu, last, 0);
+        if (last && lane < A.nq) {
+            __threadfence();
+            const unsigned long long ts = atomicAdd(&A.acc[2 * lane], 0ULL);
+            const unsigned long long tc = atomicAdd(&A.acc[2 * lane + 1], 0ULL);
+            const MqOut& o = A.out[lane];
+            if (o.count) *o.count = static_cast<int64_t>(tc);
+            if (o.count2) *o.count2 = static_cast<int64_t>(tc);
+            if (o.sum) *o.sum = static_cast<int64_t>(ts);
+        }
+    }
+
+    __device__ void finish(const ScanGeom&, int, int) {}
+};
+
+}  // namespace tqp
+
+// ---- host side (multi.cu) ------------------------------------------------------
+namespace tqp {
+
+// One filter query of a shared scan, lowered.
+struct MqQuery {
+    Cond cond[TQP_MAX_PREDS];
+    int ncond = 0;
+    bool has_sum = false;
+    bool closed = false;   // the sum expression has the closed product form
+    DExpr sum{};
+    MqOut out{};
+    std::vector<int> cols; // condition and expression columns, ascending
+};
+
+tqp_status mq_lower_query(const tqp_table* t, const tqp_pred* preds, int32_t npreds, const tqp_expr* sum_expr,
+                          MqQuery* q);
+// Pack queries into launches (first fit, in order); queries that fit no
+// launch (an expression without the closed form, more than 8 columns) go to
+// `singles`, for the single-query scan.
+void mq_pack(const tqp_table* t, const std::vector<MqQuery>& qs, std::vector<std::vector<int>>* groups,
+             std::vector<int>* singles);
+// Lower one launch: its arguments (device pointers as offsets into `blob`,
+// resolved by mq_bind once the blob is in device memory), the blob itself
+// (lookup tables and per-query outputs) and the launch's shared memory.
+tqp_status mq_lower_group(const tqp_ctx* ctx, const tqp_table* t, const std::vector<MqQuery>& qs,
+                          const std::vector<int>& members, const tqp_tuning* tu, int body_smem, MultiArgs* A,
+                          std::vector<unsigned char>* blob, size_t* smem, int* ctas_per_sm);
+void mq_bind(MultiArgs* A, const unsigned char* d_blob);
+
+}  // namespace tqp

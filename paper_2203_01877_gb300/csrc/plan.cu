@@ -24,9 +24,6 @@
 
 namespace tqp {
 
-tqp_status launch_filter(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* preds, int32_t npreds,
-                         const tqp_expr* sum_expr, int64_t* d_sum, int32_t* d_row_ids, int64_t capacity,
-                         int64_t* d_count, cudaStream_t stream, const tqp_tuning* force);
 tqp_status launch_groupby(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* preds, int32_t npreds,
                           const int32_t* group_cols, int32_t ngc, const tqp_agg* aggs, int32_t naggs,
                           int64_t* d_keys, int64_t* d_ivals, double* d_fvals, int64_t capacity_groups,

@@ -4,12 +4,13 @@ import numpy as np
 
 def gpu_plan_prepare(fact, preds=(), dim=None, fact_fk=0, dim_key=0, group_cols=(), aggs=(), sum_expr=None,
                      topk=0, topk_agg=0, want_row_ids=False, capacity_groups=None, max_groups=0, dim_ref=None,
-                     prepared=None, join_kind="inner"):
-    """dim_ref: an existing TableRef of `dim` (needed with `prepared`, which was built on it)."""
+                     prepared=None, join_kind="inner", fact_ref=None):
+    """dim_ref: an existing TableRef of `dim` (needed with `prepared`, which was built on it); fact_ref: an
+    existing TableRef of `fact` (plans sharing one uploaded table)."""
     import torch
     import paper_2203_01877_gb300 as tqp
     from tests.gpu_util import up
-    F = tqp.TableRef([up(c) for c in fact])
+    F = fact_ref if fact_ref is not None else tqp.TableRef([up(c) for c in fact])
     D = dim_ref if dim_ref is not None else (tqp.TableRef([up(c) for c in dim]) if dim is not None else None)
     nf = len(fact[0])
     ngc, na = len(group_cols), len(aggs)

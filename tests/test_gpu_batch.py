@@ -175,3 +175,59 @@ def test_batch_regions_are_released(ctx):
         tqp.tqp_batch_destroy(b)
     assert ctx.status() == 0
     compare(gpu_plan(ctx, **specs[2]), oracle_of(specs[2]), specs[2])
+
+
+def shared_table_specs():
+    """Plans over two uploaded tables: filter-only plans (count, count + sum,
+    four expression shapes) that the batch packs into shared scans, grouped
+    plans whose passing-row counts join the packs, and plans with row ids that
+    keep their own scan."""
+    rng = np.random.default_rng(31)
+    big, small = q1(2_000_003, 41), q1(333_333, 42)
+    exprs = [[("col", 4)], [("col", 4), ("col", 5), "mul"],
+             [("col", 4), ("const", 100), ("col", 5), "sub", "mul"], [("col", 3), ("const", 7), "add"]]
+    specs = []
+    for i in range(44):
+        d0 = int(rng.integers(0, 2200))
+        preds = [(0, "ge", d0), (0, "lt", d0 + int(rng.integers(1, 400))), (1, "ne", int(rng.integers(0, 3))),
+                 (3, "le", int(rng.integers(1, 51)))]
+        fact = big if i % 4 else small
+        if i % 11 == 5:
+            specs.append(dict(fact=fact, preds=preds, group_cols=[1, 2], aggs=Q1_AGGS, capacity_groups=64))
+        elif i % 13 == 7:
+            specs.append(dict(fact=fact, preds=preds, sum_expr=exprs[i % 4], want_row_ids=True))
+        elif i % 5 == 0:
+            specs.append(dict(fact=fact, preds=preds))
+        else:
+            specs.append(dict(fact=fact, preds=preds, sum_expr=exprs[(i // 3) % 4]))
+    return specs, big, small
+
+
+def test_filter_plans_share_scans(ctx):
+    """Filter-only plans over one table run as shared scans inside the batch;
+    every output equals the oracle's for the plan alone (one-shot and replayed)."""
+    import paper_2203_01877_gb300 as tqp
+    from tests.gpu_util import up
+    specs, big, small = shared_table_specs()
+    refs = {id(big): tqp.TableRef([up(c) for c in big]), id(small): tqp.TableRef([up(c) for c in small])}
+    prepared = [gpu_plan_prepare(fact_ref=refs[id(s["fact"])], **s) for s in specs]
+    wants = [oracle_of(s) for s in specs]
+    tqp.tqp_run_plans(ctx, [p[0] for p in prepared], [p[1] for p in prepared])
+    assert ctx.status() == 0
+    for s, w, (plan, res, bufs, keep, shape) in zip(specs, wants, prepared):
+        got = gpu_plan_collect(bufs, shape)
+        got["status"] = 0
+        compare(got, w, s)
+    batch = tqp.tqp_batch_create(ctx, [p[0] for p in prepared], [p[1] for p in prepared])
+    try:
+        for _ in range(2):
+            for p in prepared:
+                clobber(p[2])
+            tqp.tqp_batch_run(batch)
+            assert ctx.status() == 0
+            for s, w, (plan, res, bufs, keep, shape) in zip(specs, wants, prepared):
+                got = gpu_plan_collect(bufs, shape)
+                got["status"] = 0
+                compare(got, w, s)
+    finally:
+        tqp.tqp_batch_destroy(batch)

@@ -591,6 +591,47 @@ def batched_workload(tqp, torch, dev, local, reps, n_plans=BATCH_PLANS):
     }
 
 
+def q6_windows(k, seed):
+    """k filter queries shaped like the headline one, each with its own seeded 365-day window, discount band of
+    three values and quantity cutoff."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(k):
+        d0 = int(rng.integers(0, 2557 - 365))
+        disc = int(rng.integers(1, 9))
+        qty = int(rng.integers(2, 51))
+        out.append([(0, "ge", d0), (0, "lt", d0 + 365), (1, "between", disc - 1, disc + 1), (2, "lt", qty)])
+    return out
+
+
+def shared_scan_workload(tqp, torch, dev, local, table, n, reps):
+    """Shared scans on the headline table: K filter queries (count + SUM(price*discount) each) in one
+    tqp_filter_shared call against K tqp_filter calls, K = 1, 8, 32; identical outputs checked."""
+    ctx = tqp.Context(local, 256 << 20)
+    stream = torch.cuda.current_stream()
+    out = {"workload": f"{n // 1_000_000}M rows (date i32, discount i64, quantity i32, price i64); K queries, each "
+                       "a seeded 365-day date window, a three-value discount band and a quantity cutoff; "
+                       "count + SUM(price*discount) per query", "by_k": {}}
+    for k in (1, 8, 32):
+        preds = q6_windows(k, datagen.DEFAULT_SEED + 7)
+        qs = [(p, EXPR, torch.zeros(1, dtype=torch.int64, device=dev), torch.zeros(1, dtype=torch.int64, device=dev))
+              for p in preds]
+        shared = _time_launches(torch, lambda: tqp.tqp_filter_shared(ctx, table, qs, stream), reps, stream=stream)
+        got = [(int(c.item()), int(s_.item())) for _, _, c, s_ in qs]
+        sep = _time_launches(torch, lambda: [tqp.tqp_filter(ctx, table, p, e, s_, None, 0, c, stream)
+                                             for p, e, c, s_ in qs], max(3, reps // 4), stream=stream)
+        alone = [(int(c.item()), int(s_.item())) for _, _, c, s_ in qs]
+        ctx.check(stream)
+        alg = n * 24  # the four staged columns, read once
+        out["by_k"][str(k)] = {"ms_shared": shared, "ms_separate": sep, "qps_shared": k / (shared / 1e3),
+                               "qps_separate": k / (sep / 1e3), "speedup": sep / shared,
+                               "achieved_gbs_shared": alg / (shared / 1e3) / 1e9,
+                               "frac_of_measured_hbm": alg / (shared / 1e3) / 1e9 / measured_peaks()[0],
+                               "same_as_separate": got == alone}
+    ctx.close()
+    return out
+
+
 SERVE_FACT_ROWS = 600_000_000
 SERVE_DIM_ROWS = 15_000_000
 SERVE_POOL = 512  # result buffer sets, reused round-robin
@@ -673,7 +714,8 @@ def serving_workload(tqp, torch, dev, local, seconds=10.0, rate=2000.0,
         gctx.close()
         del T
 
-    def run(max_batch, max_inflight, qps, nq):
+    def run(max_batch, max_inflight, qps, nq, qlist=None):
+        qlist = queries if qlist is None else qlist
         budget = 4 << 30
         ctx = tqp.Context(local, budget + (256 << 20))
         srv = tqp.Server(ctx, max_batch=max_batch, max_inflight=max_inflight, budget_bytes=budget)
@@ -695,7 +737,7 @@ def serving_workload(tqp, torch, dev, local, seconds=10.0, rate=2000.0,
                 for c in srv.poll():
                     done[c[0]] = c
             sub_t[i] = time.perf_counter()
-            srv.submit(queries[i][0], queries[i][1], i)
+            srv.submit(qlist[i][0], qlist[i][1], i)
             if i % 32 == 31:
                 for c in srv.poll():
                     done[c[0]] = c
@@ -743,6 +785,42 @@ def serving_workload(tqp, torch, dev, local, seconds=10.0, rate=2000.0,
         ok = [r[key]["qps"] for r in rows if r[key] is not None and r[key]["qps"] >= 0.95 * r["offered_qps"]]
         return max(ok) if ok else None
 
+    # full-table filter queries (count + sum over all rows, each its own seeded window): the server's batches
+    # pack them into shared scans of up to 32 queries each
+    full = None
+    if fact_rows >= 100_000_000:
+        TF = tqp.TableRef([fact[c] for c in ("date", "discount", "quantity", "price")])
+        nfull = 4000
+        fq = []
+        for i, pr in enumerate(q6_windows(nfull, seed + 5)):
+            b = pool[i % SERVE_POOL]
+            fq.append((tqp.make_plan(TF, pr, sum_expr=EXPR), tqp.make_result(None, 0, b["nr"], b["s"])))
+        frows = []
+        for qps in (250, 500, 1000, 2000, 3000, 4000):
+            n_s = min(nfull, int(qps * 1.0))
+            frows.append({"offered_qps": qps, "continuous_shared": run(64, 2, qps, n_s, fq),
+                          "one_at_a_time": run(1, 1, qps, min(n_s, 500), fq) if qps <= 500 else None})
+        sat = lambda key: max([r[key]["qps"] for r in frows  # noqa: E731
+                               if r[key] is not None and r[key]["qps"] >= 0.95 * r["offered_qps"]
+                               and r[key]["errors"] == 0] or [0.0])
+        actx = tqp.Context(local, 256 << 20)
+        same_f = True
+        last = min(nfull, 4000)  # the final sweep point ran queries [0, last): the pool holds the last ones
+        for i in range(last - 3, last):
+            b = pool[i % SERVE_POOL]
+            before = (b["nr"].clone(), b["s"].clone())
+            tqp.tqp_run_plan(actx, fq[i][0], fq[i][1])
+            actx.check()
+            same_f &= torch.equal(before[0], b["nr"]) and torch.equal(before[1], b["s"])
+        actx.close()
+        full = {"workload": f"filter queries over all {fact_rows // 1_000_000}M rows (date, discount, quantity, "
+                            "price: 14.4 GB), each a seeded 365-day window, discount band and quantity cutoff; "
+                            "count + SUM(price*discount); open-loop Poisson arrivals",
+                "sweep": frows, "saturation_qps": {"continuous_shared": sat("continuous_shared"),
+                                                   "one_at_a_time": sat("one_at_a_time")},
+                "served_equals_alone_sample": bool(same_f)}
+        del TF
+
     tqp.tqp_dim_destroy(pdim)
     pctx.close()
     return {
@@ -756,6 +834,7 @@ def serving_workload(tqp, torch, dev, local, seconds=10.0, rate=2000.0,
         "qps_at_p99_le_1ms": {"continuous": best("continuous", 1.0), "one_at_a_time": best("one_at_a_time", 1.0)},
         "saturation_qps": {"continuous": saturation("continuous"), "one_at_a_time": saturation("one_at_a_time")},
         "setup_s": setup_s,
+        "full_table_filters": full,
     }, g600
 
 
@@ -967,6 +1046,7 @@ def main():
     if rank == 0 and not args.no_operators:
         ops = secondary_workloads(tqp, torch, dev, local, 20, cpu_seconds=min(args.cpu_seconds, 5.0))
         ops["batched_512"] = batched_workload(tqp, torch, dev, local, 20)
+        ops["shared_scan_60M"] = shared_scan_workload(tqp, torch, dev, local, table, N_ROWS, 10)
         if not args.no_serving:
             ops["serving"], g600 = serving_workload(tqp, torch, dev, local, seconds=args.serve_seconds)
             if g600:

@@ -880,7 +880,7 @@ static tqp_status add_multi_job(tqp_batch* b, const tqp_table* t, const std::vec
     std::vector<unsigned char> blob;
     size_t smem = 0;
     int per_sm = 0;
-    TQP_TRY(mq_lower_group(ctx, t, qs, members, &tu, kJobBytes + body_bytes<MultiBody>(), &A, &blob, &smem, &per_sm));
+    TQP_TRY(mq_lower_group(ctx, t, qs, members, &tu, kJobBytes, true, &A, &blob, &smem, &per_sm));
     if (A.G.ntiles == 0) {  // an empty table: every output is zero
         for (int m : members) {
             const MqOut& o = qs[m].out;

@@ -581,12 +581,13 @@ __device__ __forceinline__ const Args& stage_args(const Args& p, unsigned char* 
 }
 
 // Dynamic shared memory: header | `extra` bytes (the staged arguments) |
-// Body::kSmemBytes | stages.
+// body_bytes (Body::kSmemBytes unless the body sizes its region per launch) |
+// stages.
 template <class Body>
 __device__ __forceinline__ void run_engine(const ScanGeom& G, const EngineCtl& ctl, Body& body,
-                                           unsigned char* smem, int extra = 0) {
+                                           unsigned char* smem, int extra = 0, int body_bytes = Body::kSmemBytes) {
     EngineHeader* h = reinterpret_cast<EngineHeader*>(smem);
-    unsigned char* stages = smem + kHeaderBytes + extra + Body::kSmemBytes;
+    unsigned char* stages = smem + kHeaderBytes + extra + body_bytes;
     const int warp = threadIdx.x / kWarp;
     const int lane = threadIdx.x % kWarp;
     init_stage_ring(h, G.nstages);

@@ -232,13 +232,16 @@ void mq_pack(const tqp_table* t, const std::vector<MqQuery>& qs, std::vector<std
 }
 
 tqp_status mq_lower_group(const tqp_ctx* ctx, const tqp_table* t, const std::vector<MqQuery>& qs,
-                          const std::vector<int>& members, const tqp_tuning* tu_in, int body_smem, MultiArgs* A,
-                          std::vector<unsigned char>* blob, size_t* smem, int* ctas_per_sm) {
+                          const std::vector<int>& members, const tqp_tuning* tu_in, int extra_smem, bool fixed_body,
+                          MultiArgs* A, std::vector<unsigned char>* blob, size_t* smem, int* ctas_per_sm) {
     memset(A, 0, sizeof(*A));
     std::vector<uint32_t> words;
     std::vector<int64_t> breaks;
     if (!mq_tables(t, qs, members, A, &words, &breaks))
         return fail(TQP_ERR_UNSUPPORTED, "shared scan: lookup tables exceed the shared-memory budget");
+    A->body_bytes = fixed_body ? MultiBody::kSmemBytes
+                               : mq_body_bytes(static_cast<int>(words.size()), static_cast<int>(breaks.size()));
+    const int body_smem = extra_smem + A->body_bytes;
     const std::vector<int> staged = mq_staged(qs, members, *A);
     if (staged.size() > static_cast<size_t>(kMaxStaged))
         return fail(TQP_ERR_UNSUPPORTED, "shared scan: more than %d columns", kMaxStaged);
@@ -295,7 +298,7 @@ __global__ void __launch_bounds__(kEngineThreads, MultiBody::kMinBlocks) k_filte
     extern __shared__ __align__(128) unsigned char smem[];
     const MultiArgs& A = stage_args(P, smem + kHeaderBytes);
     MultiBody body(A, smem + kHeaderBytes + args_bytes<MultiArgs>());
-    run_engine(A.G, A.ctl, body, smem, args_bytes<MultiArgs>());
+    run_engine(A.G, A.ctl, body, smem, args_bytes<MultiArgs>(), A.body_bytes);
 }
 
 // Zero outputs of queries over an empty table.
@@ -326,13 +329,12 @@ static tqp_status shared_run(tqp_ctx* ctx, const tqp_table* t, const tqp_scan_qu
     }
     static SmemFlags attr;
     TQP_TRY(allow_smem(ctx, reinterpret_cast<const void*>(k_filter_multi), attr));
-    const int body_smem = MultiBody::kSmemBytes + args_bytes<MultiArgs>();
     for (const auto& g : groups) {
         MultiArgs A;
         std::vector<unsigned char> blob;
         size_t smem = 0;
         int per_sm = 0;
-        TQP_TRY(mq_lower_group(ctx, t, qs, g, nullptr, body_smem, &A, &blob, &smem, &per_sm));
+        TQP_TRY(mq_lower_group(ctx, t, qs, g, nullptr, args_bytes<MultiArgs>(), false, &A, &blob, &smem, &per_sm));
         if (A.G.ntiles == 0) {
             for (int m : g) TQP_TRY(mq_zero(qs[m].out, st));
             continue;

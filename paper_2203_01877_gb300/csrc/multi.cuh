@@ -16,11 +16,12 @@
 //     breakpoints span at most kMqDirectMax values, else a branch-free binary
 //     search over the sorted breakpoints.  The cost per row grows with the
 //     number of condition columns, not with the number of queries;
-//   * accumulation, transposed: lane q of every warp owns query q's count and
-//     sum.  For each row with a non-empty pass mask (found by a ballot) the
-//     row's mask and expression values are broadcast to the warp and every
-//     lane adds them to its own query when its bit is set; rows that pass no
-//     query cost nothing;
+//   * accumulation: every consumer warp keeps a count and a sum per query in
+//     shared memory; each lane walks the set bits of its rows' pass masks and
+//     adds to those queries with shared-memory atomics (the work is the
+//     number of (row, passing query) pairs, spread over the lanes; rows that
+//     pass no query cost nothing).  At the end of a chunk lane q moves query
+//     q's totals of its warp to global memory;
 //   * per-query row ranges: a query may cover only rows [rlo, rhi) of the
 //     scan (queries over slices of one table).  Per tile a ballot splits the
 //     queries into those covering the whole tile and those touching part of
@@ -41,6 +42,14 @@ constexpr int kMqExprs = 2;         // distinct sum expressions per launch
 constexpr int kMqWords = 5120;      // mask words of all lookup tables (shared memory)
 constexpr int kMqBreaks = 512;      // breakpoints of the searched tables (shared memory)
 constexpr int kMqDirectMax = 4096;  // direct tables: at most this many entries per column
+// per-warp accumulators: 32 sums (8 bytes) and 32 counts (4 bytes) per consumer warp
+constexpr int kMqAccBytes = kConsumerWarps * kMqMax * 12;
+
+// Shared memory of one launch's body: accumulators | mask words | breakpoints.
+__host__ __device__ constexpr int mq_words_bytes(int nwords) { return (nwords * 4 + 15) / 16 * 16; }
+__host__ __device__ constexpr int mq_body_bytes(int nwords, int nbreaks) {
+    return (kMqAccBytes + mq_words_bytes(nwords) + nbreaks * 8 + 127) / 128 * 128;
+}
 
 // One condition column of a launch.
 struct MqCol {
@@ -75,7 +84,7 @@ struct MultiArgs {
     uint32_t all;         // bits of the nq queries
     int32_t nwords;       // mask words used
     int32_t nbreaks;      // breakpoints used
-    int32_t pad;
+    int32_t body_bytes;   // shared memory of the body (mq_body_bytes, or the largest in a batch)
     MqCol c[kMaxStaged];
     ProdForm e[kMqExprs];
     int32_t ecol[kMqExprs][2];   // table column of each factor (-1: constant)
@@ -118,37 +127,176 @@ __device__ __forceinline__ int64_t mq_factor_row(const ScanGeom& G, const TileVi
     return static_cast<int64_t>(x * a + b);
 }
 
+// A direct-table condition column held in registers by the fast path: the
+// value is clamped to [lo, lo + span] and indexes the table at word off.
+struct MqHot {
+    uint32_t d;     // stage byte offset | type << 20
+    int32_t off;    // first mask word
+    int32_t span;   // entries - 1
+    int64_t lo;     // the value of entry 0's upper end (base - 1)
+};
+constexpr int kMqFastCols = 4;  // condition columns of the fast path
+
 struct MultiBody {
     static constexpr int kMinBlocks = 2;
-    static constexpr int kSmemBytes = kMqWords * 4 + kMqBreaks * 8;
+    static constexpr int kSmemBytes = mq_body_bytes(kMqWords, kMqBreaks);  // the largest launch
     static constexpr int kU = 4;  // rows per lane per step
 
     const MultiArgs& A;
-    const uint32_t* w;   // shared-memory copy of the masks
-    const int64_t* bk;   // shared-memory copy of the breakpoints
-    unsigned long long s = 0;  // lane q: query q's sum over this chunk
-    unsigned long long c = 0;  // lane q: query q's count
+    const uint32_t* w;         // shared-memory copy of the masks
+    const int64_t* bk;         // shared-memory copy of the breakpoints
+    unsigned long long* wsum;  // this warp's 32 sums
+    unsigned int* wcnt;        // this warp's 32 counts
     int64_t rlo = 0, rhi = 0;  // lane q: query q's row range
-    bool use1 = false;         // lane q sums expression 1
+    MqHot hot[kMqFastCols];    // fast path: the condition columns
+    bool fast = false;         // every condition column has a direct table (at most kMqFastCols)
 
-    // Every thread of the CTA copies its share of the tables; the caller
-    // synchronises the CTA before the first tile.
+    // Every thread of the CTA copies its share of the tables and each
+    // consumer warp clears its accumulators; the caller synchronises the CTA
+    // before the first tile.
     __device__ MultiBody(const MultiArgs& a, unsigned char* sm) : A(a) {
-        uint32_t* ws = reinterpret_cast<uint32_t*>(sm);
-        int64_t* bs = reinterpret_cast<int64_t*>(sm + kMqWords * 4);
+        unsigned long long* acc = reinterpret_cast<unsigned long long*>(sm);
+        unsigned int* cnt = reinterpret_cast<unsigned int*>(sm + kConsumerWarps * kMqMax * 8);
+        uint32_t* ws = reinterpret_cast<uint32_t*>(sm + kMqAccBytes);
+        int64_t* bs = reinterpret_cast<int64_t*>(sm + kMqAccBytes + mq_words_bytes(a.nwords));
         for (int i = threadIdx.x; i < a.nwords; i += blockDim.x) ws[i] = a.words[i];
         for (int i = threadIdx.x; i < a.nbreaks; i += blockDim.x) bs[i] = a.breaks[i];
         w = ws;
         bk = bs;
+        const int warp = threadIdx.x / kWarp;
         const int lane = threadIdx.x % kWarp;
+        const int cw = warp < kConsumerWarps ? warp : 0;
+        wsum = acc + cw * kMqMax;
+        wcnt = cnt + cw * kMqMax;
+        if (warp < kConsumerWarps) {
+            wsum[lane] = 0;
+            wcnt[lane] = 0;
+        }
         if (lane < a.nq) {
             rlo = a.out[lane].rlo;
             rhi = a.out[lane].rhi;
         }
-        use1 = (a.esel >> lane) & 1u;
+        fast = a.ncols <= kMqFastCols;
+#pragma unroll
+        for (int k = 0; k < kMqFastCols; ++k) {
+            hot[k] = MqHot{0u, 0, 0, 0};
+            if (k < a.ncols) {
+                const MqCol& mc = a.c[k];
+                fast = fast && mc.direct;
+                hot[k] = MqHot{static_cast<uint32_t>(mc.soff) | (static_cast<uint32_t>(mc.type) << 20), mc.off,
+                               mc.len - 1, mc.base - 1};
+            }
+        }
     }
 
-    // kU rows per lane: rows rb + lane + 32 j of the tile.
+    // Full tiles with direct tables only: descriptors in registers, each
+    // lookup a clamp and one shared-memory load.  Rows rb + lane + 32 j.
+    __device__ __forceinline__ void fast_step(const TileView& v, int rb, int lane, uint32_t full, uint32_t part) {
+        constexpr int U = kU;
+        const int r0 = rb + lane;
+        uint32_t m[U];
+#pragma unroll
+        for (int j = 0; j < U; ++j) m[j] = full;
+        if (part) row_ranges<U>(v, r0, part, m);
+#pragma unroll
+        for (int k = 0; k < kMqFastCols; ++k) {
+            if (k >= A.ncols) break;
+            const MqHot h = hot[k];
+            const unsigned char* col = v.stage + (h.d & 0xFFFFFu);
+            const int type = static_cast<int>(h.d >> 20);
+            if (type == TQP_I64) {
+                const int64_t hi = h.lo + h.span;
+#pragma unroll
+                for (int j = 0; j < U; ++j) {
+                    int64_t x = reinterpret_cast<const int64_t*>(col)[r0 + kWarp * j];
+                    x = x < h.lo ? h.lo : (x > hi ? hi : x);
+                    m[j] &= w[h.off + static_cast<int>(x - h.lo)];
+                }
+            } else {
+                // 32- and 8-bit columns: the clamp bounds are values of the type
+                const int lo = static_cast<int>(h.lo), hi = lo + h.span;
+                int x[U];
+                if (type == TQP_I32) {
+#pragma unroll
+                    for (int j = 0; j < U; ++j) x[j] = reinterpret_cast<const int*>(col)[r0 + kWarp * j];
+                } else {
+#pragma unroll
+                    for (int j = 0; j < U; ++j) x[j] = col[r0 + kWarp * j];
+                }
+#pragma unroll
+                for (int j = 0; j < U; ++j) m[j] &= w[h.off + (min(max(x[j], lo), hi) - lo)];
+            }
+        }
+        accumulate<U>(v, r0, m);
+    }
+
+    // Queries whose row range ends inside the tile: their bits, row by row.
+    template <int U>
+    __device__ __forceinline__ void row_ranges(const TileView& v, int r0, uint32_t part, uint32_t (&m)[U]) {
+        uint32_t p = part;
+        while (p) {
+            const int q = __ffs(p) - 1;
+            p &= p - 1;
+            const long long lo = __shfl_sync(0xffffffffu, static_cast<long long>(rlo), q);
+            const long long hi = __shfl_sync(0xffffffffu, static_cast<long long>(rhi), q);
+#pragma unroll
+            for (int j = 0; j < U; ++j) {
+                const long long row = v.row0 + r0 + kWarp * j;
+                if (r0 + kWarp * j < v.rows && row >= lo && row < hi) m[j] |= 1u << q;
+            }
+        }
+    }
+
+    // Sum expressions of full-tile rows and every (row, passing query) pair.
+    template <int U>
+    __device__ __forceinline__ void accumulate(const TileView& v, int r0, const uint32_t (&m)[U]) {
+        uint32_t mor = 0;
+#pragma unroll
+        for (int j = 0; j < U; ++j) mor |= m[j];
+        if (!__any_sync(0xffffffffu, mor != 0u)) return;
+        int64_t v0[U], v1[U];
+#pragma unroll
+        for (int j = 0; j < U; ++j) v0[j] = v1[j] = 0;
+        if (A.nexpr > 0) {
+            prod_eval<U>(A.e[0], v.stage, r0, v0);
+            if (A.nexpr > 1) prod_eval<U>(A.e[1], v.stage, r0, v1);
+        }
+        add_pairs<U>(m, v0, v1);
+    }
+
+    // One work list per lane over its U rows: the warp iterates as often as
+    // its busiest lane has (row, passing query) pairs.
+    template <int U>
+    __device__ __forceinline__ void add_pairs(const uint32_t (&m)[U], const int64_t (&v0)[U], const int64_t (&v1)[U]) {
+        const uint32_t esel = A.esel;
+        uint32_t mm[U];
+#pragma unroll
+        for (int j = 0; j < U; ++j) mm[j] = m[j];
+        while (true) {
+            int64_t a0 = v0[U - 1], a1 = v1[U - 1];
+            uint32_t cur = mm[U - 1];
+            int jj = U - 1;
+#pragma unroll
+            for (int j = U - 2; j >= 0; --j) {
+                if (mm[j]) {
+                    a0 = v0[j];
+                    a1 = v1[j];
+                    cur = mm[j];
+                    jj = j;
+                }
+            }
+            if (!cur) break;
+            const int q = __ffs(cur) - 1;
+#pragma unroll
+            for (int j = 0; j < U; ++j)
+                if (j == jj) mm[j] = cur & (cur - 1);
+            atomicAdd(&wsum[q], static_cast<unsigned long long>(((esel >> q) & 1u) ? a1 : a0));
+            atomicAdd(&wcnt[q], 1u);
+        }
+    }
+
+    // General path (a ragged last tile, searched tables, more than
+    // kMqFastCols condition columns): rows rb + lane + 32 j of the tile.
     __device__ __forceinline__ void step(const ScanGeom& G, const TileView& v, int rb, int lane, uint32_t full,
                                          uint32_t part) {
         constexpr int U = kU;
@@ -156,20 +304,7 @@ struct MultiBody {
         uint32_t m[U];
 #pragma unroll
         for (int j = 0; j < U; ++j) m[j] = (r0 + kWarp * j < v.rows) ? full : 0u;
-        if (part) {  // queries whose row range ends inside this tile: row by row
-            uint32_t p = part;
-            while (p) {
-                const int q = __ffs(p) - 1;
-                p &= p - 1;
-                const long long lo = __shfl_sync(0xffffffffu, static_cast<long long>(rlo), q);
-                const long long hi = __shfl_sync(0xffffffffu, static_cast<long long>(rhi), q);
-#pragma unroll
-                for (int j = 0; j < U; ++j) {
-                    const long long row = v.row0 + r0 + kWarp * j;
-                    if (r0 + kWarp * j < v.rows && row >= lo && row < hi) m[j] |= 1u << q;
-                }
-            }
-        }
+        if (part) row_ranges<U>(v, r0, part, m);
         // predicates: the interval masks of every condition column
         for (int k = 0; k < A.ncols; ++k) {
             const MqCol& mc = A.c[k];
@@ -183,55 +318,30 @@ struct MultiBody {
 #pragma unroll
             for (int j = 0; j < U; ++j) m[j] &= mq_lookup(mc, x[j], w, bk);
         }
-        uint32_t any[U];
-        uint32_t some = 0;
-#pragma unroll
-        for (int j = 0; j < U; ++j) {
-            any[j] = __ballot_sync(0xffffffffu, m[j] != 0u);
-            some |= any[j];
+        if (v.full) {
+            accumulate<U>(v, r0, m);
+            return;
         }
-        if (!some) return;
-        // sum expressions of the lane's rows
+        uint32_t mor = 0;
+#pragma unroll
+        for (int j = 0; j < U; ++j) mor |= m[j];
+        if (!__any_sync(0xffffffffu, mor != 0u)) return;
+        // sum expressions of the passing rows, the columns read through col_val
         int64_t v0[U], v1[U];
 #pragma unroll
-        for (int j = 0; j < U; ++j) v0[j] = v1[j] = 0;
-        if (A.nexpr > 0) {
-            if (v.full) {
-                prod_eval<U>(A.e[0], v.stage, r0, v0);
-                if (A.nexpr > 1) prod_eval<U>(A.e[1], v.stage, r0, v1);
-            } else {
-#pragma unroll
-                for (int j = 0; j < U; ++j) {
-                    const int r = r0 + kWarp * j;
-                    if (m[j]) {
-                        v0[j] = static_cast<int64_t>(
-                            static_cast<uint64_t>(mq_factor_row(G, v, A.e[0], 0, A.ecol[0][0], r)) *
-                            static_cast<uint64_t>(mq_factor_row(G, v, A.e[0], 1, A.ecol[0][1], r)));
-                        if (A.nexpr > 1)
-                            v1[j] = static_cast<int64_t>(
-                                static_cast<uint64_t>(mq_factor_row(G, v, A.e[1], 0, A.ecol[1][0], r)) *
-                                static_cast<uint64_t>(mq_factor_row(G, v, A.e[1], 1, A.ecol[1][1], r)));
-                    }
-                }
-            }
-        }
-        // transposed accumulation: lane q adds the rows that pass query q
-#pragma unroll
         for (int j = 0; j < U; ++j) {
-            uint32_t b = any[j];
-            while (b) {
-                const int src = __ffs(b) - 1;
-                b &= b - 1;
-                const uint32_t mr = __shfl_sync(0xffffffffu, m[j], src);
-                const long long a0 = __shfl_sync(0xffffffffu, static_cast<long long>(v0[j]), src);
-                long long a1 = 0;
-                if (A.nexpr > 1) a1 = __shfl_sync(0xffffffffu, static_cast<long long>(v1[j]), src);
-                if ((mr >> lane) & 1u) {
-                    s += static_cast<unsigned long long>(use1 ? a1 : a0);
-                    c += 1;
-                }
+            v0[j] = v1[j] = 0;
+            const int r = r0 + kWarp * j;
+            if (m[j] && A.nexpr > 0) {
+                v0[j] = static_cast<int64_t>(static_cast<uint64_t>(mq_factor_row(G, v, A.e[0], 0, A.ecol[0][0], r)) *
+                                             static_cast<uint64_t>(mq_factor_row(G, v, A.e[0], 1, A.ecol[0][1], r)));
+                if (A.nexpr > 1)
+                    v1[j] = static_cast<int64_t>(
+                        static_cast<uint64_t>(mq_factor_row(G, v, A.e[1], 0, A.ecol[1][0], r)) *
+                        static_cast<uint64_t>(mq_factor_row(G, v, A.e[1], 1, A.ecol[1][1], r)));
             }
         }
+        add_pairs<U>(m, v0, v1);
     }
 
     __device__ void pass1(const ScanGeom& G, const TileView& v, int cw, int lane) {
@@ -242,6 +352,10 @@ struct MultiBody {
         const uint32_t part = __ballot_sync(0xffffffffu, touches && !covers) & A.all;
         if (!(full | part)) return;
         const int rw = G.T / kConsumerWarps;  // a multiple of 128
+        if (v.full && fast) {
+            for (int r = 0; r < rw; r += kU * kWarp) fast_step(v, cw * rw + r, lane, full, part);
+            return;
+        }
         for (int r = 0; r < rw; r += kU * kWarp) {
             if (cw * rw + r >= v.rows) return;
             step(G, v, cw * rw + r, lane, full, part);
@@ -249,12 +363,15 @@ struct MultiBody {
     }
 
     __device__ void chunk_end(const ScanGeom&, long long, long long, long long, int, int lane) {
+        __syncwarp();
+        const unsigned long long ls = wsum[lane];
+        const unsigned long long lc = wcnt[lane];
+        wsum[lane] = 0;
+        wcnt[lane] = 0;
         if (lane < A.nq) {
-            if (s) atomicAdd(&A.acc[2 * lane], s);
-            if (c) atomicAdd(&A.acc[2 * lane + 1], c);
+            if (ls) atomicAdd(&A.acc[2 * lane], ls);
+            if (lc) atomicAdd(&A.acc[2 * lane + 1], lc);
         }
-        s = 0;
-        c = 0;
         __threadfence();
         __syncwarp();
         bool last = false;
@@ -300,9 +417,12 @@ void mq_pack(const tqp_table* t, const std::vector<MqQuery>& qs, std::vector<std
 // Lower one launch: its arguments (device pointers as offsets into `blob`,
 // resolved by mq_bind once the blob is in device memory), the blob itself
 // (lookup tables and per-query outputs) and the launch's shared memory.
+// extra_smem: shared memory before the body (staged arguments, a batch job);
+// fixed_body: the body takes MultiBody::kSmemBytes (a batch's common layout)
+// instead of what this launch's tables need.  tu: NULL for the default tuning.
 tqp_status mq_lower_group(const tqp_ctx* ctx, const tqp_table* t, const std::vector<MqQuery>& qs,
-                          const std::vector<int>& members, const tqp_tuning* tu, int body_smem, MultiArgs* A,
-                          std::vector<unsigned char>* blob, size_t* smem, int* ctas_per_sm);
+                          const std::vector<int>& members, const tqp_tuning* tu, int extra_smem, bool fixed_body,
+                          MultiArgs* A, std::vector<unsigned char>* blob, size_t* smem, int* ctas_per_sm);
 void mq_bind(MultiArgs* A, const unsigned char* d_blob);
 
 }  // namespace tqp

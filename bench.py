@@ -909,8 +909,14 @@ def profile_case(args):
             pidx = torch.empty(n, dtype=torch.int32, device=dev)
             pcnt = z(1)
             fn = lambda: tqp.tqp_hash_join(ctx, D, 0, F, 0, bidx, pidx, n, pcnt, st)  # noqa: E731
-    else:  # the batched 512-plan mix
-        plans, results, keep, meta = batched_plans(tqp, torch, dev)
+    elif args.case == "shared":  # K filter queries in one shared scan
+        t = datagen.fact_table(n, seed=datagen.DEFAULT_SEED + 1, cols=["date", "discount", "quantity", "price"])
+        T = tqp.TableRef([torch.from_numpy(t[c]).to(dev) for c in ("date", "discount", "quantity", "price")])
+        qs = [(p, EXPR, torch.zeros(1, dtype=torch.int64, device=dev), torch.zeros(1, dtype=torch.int64, device=dev))
+              for p in q6_windows(args.queries, datagen.DEFAULT_SEED + 7)]
+        fn = lambda: tqp.tqp_filter_shared(ctx, T, qs, st)  # noqa: E731
+    else:  # the batched plan mix (512 plans by default)
+        plans, results, keep, meta = batched_plans(tqp, torch, dev, n_plans=args.plans)
         batch = tqp.tqp_batch_create(ctx, plans, results)
         fn = lambda: tqp.tqp_batch_run(batch, st)  # noqa: E731
     fn()
@@ -938,8 +944,10 @@ def main():
     ap.add_argument("--no-operators", action="store_true", help="skip the secondary workloads")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving workload")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--queries", type=int, default=32, help="profiling: queries of the shared-scan case")
+    ap.add_argument("--plans", type=int, default=BATCH_PLANS, help="profiling: plans of the batch case")
     ap.add_argument("--case", choices=["filter", "groupby", "join", "join_hashed", "pairs", "pairs_hashed", "batch",
-                                       "l2red"], default=None,
+                                       "shared", "l2red"], default=None,
                     help="profiling: run one operator (first call autotunes; --steps calls in NVTX range tqp_profile)")
     args = ap.parse_args()
     globals()["N_ROWS"] = args.rows

@@ -346,8 +346,11 @@ TQP_API tqp_status tqp_filter_noalloc(int device, const tqp_table* t,
  * table of the value intervals cut by the queries' range bounds).  A query
  * whose sum expression is not a product of two affine factors (x, x*k, x+k,
  * x*y, x*(k-y), ...) or that reads more than 8 columns runs alone through
- * tqp_filter's scan.  launch_of (host array of nq, may be NULL) receives each
- * query's launch index, or -1 for one that ran alone.
+ * tqp_filter's scan, and so does every query of a launch that would hold
+ * fewer than 3 queries (that scan reads the summed columns only at passing
+ * rows, which is faster for one or two queries).  launch_of (host array of
+ * nq, may be NULL) receives each query's launch index, or -1 for one that ran
+ * alone.
  *
  * Errors: TQP_ERR_INVALID_ARG (nq < 0, NULL queries with nq > 0, a NULL
  * d_count, has_sum without d_sum or d_sum without has_sum, a predicate or

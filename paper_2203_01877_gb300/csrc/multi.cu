@@ -229,6 +229,13 @@ void mq_pack(const tqp_table* t, const std::vector<MqQuery>& qs, std::vector<std
         if (mq_fits(t, qs, g)) groups->push_back(g);
         else singles->push_back(i);
     }
+    std::vector<std::vector<int>> kept;
+    for (auto& g : *groups) {
+        if (g.size() >= static_cast<size_t>(kMqMinPack)) kept.push_back(g);
+        else singles->insert(singles->end(), g.begin(), g.end());
+    }
+    std::sort(singles->begin(), singles->end());
+    *groups = kept;
 }
 
 tqp_status mq_lower_group(const tqp_ctx* ctx, const tqp_table* t, const std::vector<MqQuery>& qs,

@@ -39,6 +39,7 @@ namespace tqp {
 
 constexpr int kMqMax = 32;          // queries per launch: one per lane
 constexpr int kMqExprs = 2;         // distinct sum expressions per launch
+constexpr int kMqMinPack = 3;       // smaller packs run through the single-query scan (faster there)
 constexpr int kMqWords = 5120;      // mask words of all lookup tables (shared memory)
 constexpr int kMqBreaks = 512;      // breakpoints of the searched tables (shared memory)
 constexpr int kMqDirectMax = 4096;  // direct tables: at most this many entries per column
@@ -410,8 +411,10 @@ struct MqQuery {
 tqp_status mq_lower_query(const tqp_table* t, const tqp_pred* preds, int32_t npreds, const tqp_expr* sum_expr,
                           MqQuery* q);
 // Pack queries into launches (first fit, in order); queries that fit no
-// launch (an expression without the closed form, more than 8 columns) go to
-// `singles`, for the single-query scan.
+// launch (an expression without the closed form, more than 8 columns) and
+// packs of fewer than kMqMinPack queries go to `singles`, for the
+// single-query scan (it reads the summed columns only at passing rows, which
+// wins for one or two queries).
 void mq_pack(const tqp_table* t, const std::vector<MqQuery>& qs, std::vector<std::vector<int>>* groups,
              std::vector<int>* singles);
 // Lower one launch: its arguments (device pointers as offsets into `blob`,

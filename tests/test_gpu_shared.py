@@ -84,15 +84,19 @@ def test_more_than_32_queries_split(ctx):
 def test_expressions_counts_and_packing(ctx):
     """Two distinct expressions per launch; a third starts another launch;
     count-only queries join any launch; an expression without the closed
-    product form runs alone."""
+    product form runs alone, and so do the queries of a launch of fewer than
+    three."""
     cols = _table(777_777, 103)
     sq = [("col", 3), ("col", 1), "add", ("col", 2), ("col", 0), "add", "mul"]  # (price+discount)*(qty+date)
-    base = q6_queries(6, 9)
-    qs = [base[0], (base[1][0], NET), (base[2][0], [("col", 2)]), (base[3][0], None), (base[4][0], sq),
-          (base[5][0], REVENUE), ([], [("col", 6), ("const", 3), "mul"]), ([], None)]
+    base = q6_queries(9, 9)
+    qty = [("col", 2)]
+    qs = [base[0], (base[1][0], NET), (base[2][0], qty), (base[3][0], None), (base[4][0], sq),
+          (base[5][0], REVENUE), ([], [("col", 6), ("const", 3), "mul"]), ([], None), (base[6][0], qty),
+          (base[7][0], [("col", 5), ("col", 6), "mul"])]
     got, launch_of = run_shared(ctx, cols, qs)
     assert launch_of[0] == launch_of[1] == launch_of[3] == launch_of[5] == launch_of[7] == 0
-    assert launch_of[2] == 1 and launch_of[6] == 1 and launch_of[4] == -1
+    assert launch_of[2] == launch_of[6] == launch_of[8] == 1
+    assert launch_of[4] == -1 and launch_of[9] == -1  # not closed; a launch of one
     check(cols, qs, got)
 
 
@@ -138,8 +142,9 @@ def test_column_union_over_eight_splits(ctx):
     cols = base + extra  # columns 7, 8, 9
     qs = [([(c, "lt", 500)], [("col", 3)]) for c in (7, 8, 9)]
     qs += [([(0, "lt", 1000), (2, "lt", 25)], REVENUE), ([(4, "eq", 0), (5, "eq", 1)], [("col", 6)])]
+    qs += [([(4, "eq", 2), (5, "eq", 0)], [("col", 6)]), ([(4, "ne", 1)], [("col", 6)])]
     got, launch_of = run_shared(ctx, cols, qs)
-    assert max(launch_of) >= 1 and min(launch_of) >= 0
+    assert launch_of[:4] == [0] * 4 and launch_of[4:] == [1] * 3
     check(cols, qs, got)
 
 

@@ -79,15 +79,20 @@ def test_expired_wait_in_filter_and_plan_reports_timeout():
     ctx = tqp.Context(0, 512 << 20)
     try:
         ctx.set_tuning(1024, 2, 1)
-        ctx.set_variant(1)  # the fused probe: the join runs through the staged scan engine and its waits
         ctx.set_wait_limit(2)
+        # variant 0 of the filter and variant 1 of the joined plan (the fused probe) run through the staged
+        # scan engine and its waits
+        ctx.set_variant(0)
         _, _, _, st = gpu_filter(ctx, cols, Q6_PREDS, Q6_EXPR)
         assert st == tqp.ERR_TIMEOUT
+        ctx.set_variant(1)
         assert gpu_plan(ctx, **spec)["status"] == tqp.ERR_TIMEOUT
         ctx.set_wait_limit(DEFAULT_WAIT)
+        ctx.set_variant(0)
         ids, k, s, st = gpu_filter(ctx, cols, Q6_PREDS, Q6_EXPR)
         want_ids, want_sum = oracle.filter_rows(cols, Q6_PREDS, Q6_EXPR)
         assert st == 0 and k == len(want_ids) and s == want_sum and np.array_equal(ids, want_ids)
+        ctx.set_variant(1)
         got = gpu_plan(ctx, **spec)
         want = oracle.run_plan(want_pairs=False, cap_groups=4096, **{k: v for k, v in spec.items()
                                                                       if k != "capacity_groups"})

@@ -871,6 +871,8 @@ def profile_case(args):
     ctx.set_autotune(True)
     if args.variant >= 0:
         ctx.set_variant(args.variant)
+    if args.tuning:
+        ctx.set_tuning(*[int(x) for x in args.tuning.split(",")])
     n = args.rows
     if args.case == "filter":
         t = datagen.fact_table(n, seed=datagen.DEFAULT_SEED + 1, cols=["date", "discount", "quantity", "price"])
@@ -945,6 +947,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving workload")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--queries", type=int, default=32, help="profiling: queries of the shared-scan case")
+    ap.add_argument("--tuning", default="", help="profiling: force the scan launch shape, tile,stages,ctas_per_sm")
     ap.add_argument("--plans", type=int, default=BATCH_PLANS, help="profiling: plans of the batch case")
     ap.add_argument("--case", choices=["filter", "groupby", "join", "join_hashed", "pairs", "pairs_hashed", "batch",
                                        "shared", "l2red"], default=None,

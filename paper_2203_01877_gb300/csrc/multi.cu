@@ -65,6 +65,17 @@ tqp_status mq_lower_query(const tqp_table* t, const tqp_pred* preds, int32_t npr
     std::sort(cols.begin(), cols.end());
     cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
     q->cols = cols;
+    if (q->has_sum) expr_cols(q->sum, q->ecols);
+    for (int i = 0; i < q->ncond; ++i) {
+        const Cond& cd = q->cond[i];
+        int64_t tmin, tmax;
+        type_range(t->cols[cd.col].type, &tmin, &tmax);
+        const uint64_t ends[2] = {static_cast<uint64_t>(cd.lo), static_cast<uint64_t>(cd.lo) + cd.span + 1u};
+        for (uint64_t e : ends) {
+            const int64_t b = static_cast<int64_t>(e);
+            if (b > tmin && b <= tmax) q->bps.push_back({cd.col, b});
+        }
+    }
     return TQP_OK;
 }
 
@@ -72,7 +83,8 @@ tqp_status mq_lower_query(const tqp_table* t, const tqp_pred* preds, int32_t npr
 // lane order).  Fills A->nq, A->all, A->ncols and A->c[] (all but the stage
 // offsets); false when the tables exceed the shared-memory budget.
 static bool mq_tables(const tqp_table* t, const std::vector<MqQuery>& qs, const std::vector<int>& members,
-                      MultiArgs* A, std::vector<uint32_t>* words, std::vector<int64_t>* breaks) {
+                      MultiArgs* A, std::vector<uint32_t>* words, std::vector<int64_t>* breaks,
+                      bool want_masks = true) {
     const int nq = static_cast<int>(members.size());
     A->nq = nq;
     A->all = nq >= 32 ? 0xffffffffu : ((1u << nq) - 1u);
@@ -123,8 +135,9 @@ static bool mq_tables(const tqp_table* t, const std::vector<MqQuery>& qs, const 
             return mk;
         };
         // every breakpoint is > tmin, so B[0] - 1 is a value of the column
-        ct.M.push_back(mask_at(ct.B.empty() ? tmin : ct.B[0] - 1));
-        for (int64_t b : ct.B) ct.M.push_back(mask_at(b));
+        // (sizes only: masks of zero, the packing decisions do not need them)
+        ct.M.push_back(want_masks ? mask_at(ct.B.empty() ? tmin : ct.B[0] - 1) : 0u);
+        for (int64_t b : ct.B) ct.M.push_back(want_masks ? mask_at(b) : 0u);
         if (ct.B.empty()) {
             A->all &= ct.M[0];  // the same outcome for every value: no lookup needed
             continue;
@@ -149,6 +162,10 @@ static bool mq_tables(const tqp_table* t, const std::vector<MqQuery>& qs, const 
             mc.base = ct.B.front();
             mc.len = static_cast<int32_t>(len);
             words->push_back(ct.M[0]);
+            if (!want_masks) {
+                words->resize(words->size() + len - 1);
+                continue;
+            }
             size_t j = 0;  // breakpoints <= the entry's value
             for (size_t d = 0; d + 1 < len; ++d) {
                 const int64_t x = static_cast<int64_t>(static_cast<uint64_t>(ct.B.front()) + d);
@@ -194,21 +211,114 @@ static std::vector<DExpr> mq_exprs(const std::vector<MqQuery>& qs, const std::ve
     return ex;
 }
 
-static bool mq_fits(const tqp_table* t, const std::vector<MqQuery>& qs, const std::vector<int>& members) {
-    if (members.size() > static_cast<size_t>(kMqMax)) return false;
-    if (mq_exprs(qs, members).size() > static_cast<size_t>(kMqExprs)) return false;
-    MultiArgs A;
-    memset(&A, 0, sizeof(A));
-    std::vector<uint32_t> w;
-    std::vector<int64_t> b;
-    if (!mq_tables(t, qs, members, &A, &w, &b)) return false;
-    return mq_staged(qs, members, A).size() <= static_cast<size_t>(kMaxStaged);
+// One pack under construction: its members, expressions, and per condition
+// column the sorted breakpoints (the sizes of its lookup tables follow from
+// them exactly as mq_tables lays them out).
+struct PackState {
+    std::vector<int> members;
+    std::vector<DExpr> exprs;
+    std::vector<int> ecols;                        // expression columns
+    std::vector<std::pair<int, std::vector<int64_t>>> B;  // ascending column order
+
+    std::vector<int64_t>* col_bps(int c) {
+        for (auto& e : B)
+            if (e.first == c) return &e.second;
+        return nullptr;
+    }
+};
+
+// Would `q` fit `g` (members, expressions, staged columns, table budget)?
+static bool pack_try(const PackState& g, const MqQuery& q) {
+    if (g.members.size() + 1 > static_cast<size_t>(kMqMax)) return false;
+    size_t nex = g.exprs.size();
+    if (q.has_sum) {
+        bool seen = false;
+        for (const DExpr& e : g.exprs) seen = seen || same_expr(e, q.sum);
+        if (!seen) ++nex;
+    }
+    if (nex > static_cast<size_t>(kMqExprs)) return false;
+    // per condition column: breakpoint count and span after adding q's
+    struct Sz {
+        int col;
+        size_t k;
+        int64_t lo, hi;
+    };
+    std::vector<Sz> sz;
+    for (const auto& e : g.B) sz.push_back({e.first, e.second.size(), e.second.front(), e.second.back()});
+    for (const auto& b : q.bps) {
+        Sz* z = nullptr;
+        for (auto& x : sz)
+            if (x.col == b.first) z = &x;
+        const std::vector<int64_t>* old = nullptr;
+        for (const auto& e : g.B)
+            if (e.first == b.first) old = &e.second;
+        if (!z) {
+            sz.push_back({b.first, 0, b.second, b.second});
+            z = &sz.back();
+        }
+        bool dup = old && std::binary_search(old->begin(), old->end(), b.second);
+        for (const auto& b2 : q.bps)  // an equal breakpoint earlier in q's own list
+            if (&b2 == &b) break;
+            else if (b2.first == b.first && b2.second == b.second) dup = true;
+        if (!dup) ++z->k;
+        z->lo = std::min(z->lo, b.second);
+        z->hi = std::max(z->hi, b.second);
+    }
+    std::sort(sz.begin(), sz.end(), [](const Sz& a, const Sz& b) { return a.col < b.col; });
+    if (sz.size() > static_cast<size_t>(kMaxStaged)) return false;
+    // staged columns: the lookup columns and every expression column
+    std::vector<int> staged = g.ecols;
+    staged.insert(staged.end(), q.ecols.begin(), q.ecols.end());
+    for (const auto& z : sz) staged.push_back(z.col);
+    std::sort(staged.begin(), staged.end());
+    staged.erase(std::unique(staged.begin(), staged.end()), staged.end());
+    if (staged.size() > static_cast<size_t>(kMaxStaged)) return false;
+    // the table budget, decided as mq_tables decides it
+    std::vector<size_t> searched(sz.size() + 1, 0);
+    for (size_t i = sz.size(); i-- > 0;) searched[i] = searched[i + 1] + sz[i].k + 1;
+    size_t words = 0, breaks = 0;
+    for (size_t i = 0; i < sz.size(); ++i) {
+        const uint64_t span = static_cast<uint64_t>(sz[i].hi) - static_cast<uint64_t>(sz[i].lo);
+        const size_t len = span <= static_cast<uint64_t>(kMqDirectMax - 2) ? static_cast<size_t>(span) + 2 : 0;
+        if (len && words + len + searched[i + 1] <= static_cast<size_t>(kMqWords)) {
+            words += len;
+        } else {
+            words += sz[i].k + 1;
+            breaks += sz[i].k;
+        }
+    }
+    return words <= static_cast<size_t>(kMqWords) && breaks <= static_cast<size_t>(kMqBreaks);
+}
+
+static void pack_add(PackState* g, const MqQuery& q, int idx) {
+    g->members.push_back(idx);
+    if (q.has_sum) {
+        bool seen = false;
+        for (const DExpr& e : g->exprs) seen = seen || same_expr(e, q.sum);
+        if (!seen) g->exprs.push_back(q.sum);
+    }
+    g->ecols.insert(g->ecols.end(), q.ecols.begin(), q.ecols.end());
+    for (const auto& b : q.bps) {
+        std::vector<int64_t>* v = g->col_bps(b.first);
+        if (!v) {
+            g->B.push_back({b.first, {}});
+            std::sort(g->B.begin(), g->B.end(),
+                      [](const std::pair<int, std::vector<int64_t>>& x, const std::pair<int, std::vector<int64_t>>& y) {
+                          return x.first < y.first;
+                      });
+            v = g->col_bps(b.first);
+        }
+        auto it = std::lower_bound(v->begin(), v->end(), b.second);
+        if (it == v->end() || *it != b.second) v->insert(it, b.second);
+    }
 }
 
 void mq_pack(const tqp_table* t, const std::vector<MqQuery>& qs, std::vector<std::vector<int>>* groups,
              std::vector<int>* singles) {
+    (void)t;
     groups->clear();
     singles->clear();
+    std::vector<PackState> packs;
     for (int i = 0; i < static_cast<int>(qs.size()); ++i) {
         const MqQuery& q = qs[i];
         if ((q.has_sum && !q.closed) || q.cols.size() > static_cast<size_t>(kMaxStaged)) {
@@ -216,26 +326,26 @@ void mq_pack(const tqp_table* t, const std::vector<MqQuery>& qs, std::vector<std
             continue;
         }
         bool placed = false;
-        for (auto& g : *groups) {  // first fit
-            g.push_back(i);
-            if (mq_fits(t, qs, g)) {
+        for (auto& g : packs)  // first fit
+            if (pack_try(g, q)) {
+                pack_add(&g, q, i);
                 placed = true;
                 break;
             }
-            g.pop_back();
-        }
         if (placed) continue;
-        std::vector<int> g{i};
-        if (mq_fits(t, qs, g)) groups->push_back(g);
-        else singles->push_back(i);
+        PackState g;
+        if (pack_try(g, q)) {
+            pack_add(&g, q, i);
+            packs.push_back(std::move(g));
+        } else {
+            singles->push_back(i);
+        }
     }
-    std::vector<std::vector<int>> kept;
-    for (auto& g : *groups) {
-        if (g.size() >= static_cast<size_t>(kMqMinPack)) kept.push_back(g);
-        else singles->insert(singles->end(), g.begin(), g.end());
+    for (auto& g : packs) {
+        if (g.members.size() >= static_cast<size_t>(kMqMinPack)) groups->push_back(g.members);
+        else singles->insert(singles->end(), g.members.begin(), g.members.end());
     }
     std::sort(singles->begin(), singles->end());
-    *groups = kept;
 }
 
 tqp_status mq_lower_group(const tqp_ctx* ctx, const tqp_table* t, const std::vector<MqQuery>& qs,
@@ -301,10 +411,11 @@ void mq_bind(MultiArgs* A, const unsigned char* d_blob) {
     A->out = reinterpret_cast<const MqOut*>(d_blob + reinterpret_cast<uintptr_t>(A->out));
 }
 
-__global__ void __launch_bounds__(kEngineThreads, MultiBody::kMinBlocks) k_filter_multi(const __grid_constant__ MultiArgs P) {
+__global__ void __launch_bounds__(kEngineThreads, MultiBody::kMinBlocks)
+    k_filter_multi(const __grid_constant__ MultiLaunch P) {
     extern __shared__ __align__(128) unsigned char smem[];
-    const MultiArgs& A = stage_args(P, smem + kHeaderBytes);
-    MultiBody body(A, smem + kHeaderBytes + args_bytes<MultiArgs>());
+    const MultiArgs& A = stage_args(P.A, smem + kHeaderBytes);
+    MultiBody body(A, smem + kHeaderBytes + args_bytes<MultiArgs>(), P.words, P.breaks, P.out);
     run_engine(A.G, A.ctl, body, smem, args_bytes<MultiArgs>(), A.body_bytes);
 }
 
@@ -347,11 +458,17 @@ static tqp_status shared_run(tqp_ctx* ctx, const tqp_table* t, const tqp_scan_qu
             continue;
         }
         const size_t acc_bytes = (2 * kMqMax + 2) * sizeof(unsigned long long);
-        unsigned char* d = static_cast<unsigned char*>(arena_alloc(ctx, acc_bytes + blob.size()));
-        if (!d) return arena_oom(ctx, acc_bytes + blob.size());
+        unsigned char* d = static_cast<unsigned char*>(arena_alloc(ctx, acc_bytes));
+        if (!d) return arena_oom(ctx, acc_bytes);
         TQP_CUDA(cudaMemsetAsync(d, 0, acc_bytes, st));
-        TQP_CUDA(cudaMemcpyAsync(d + acc_bytes, blob.data(), blob.size(), cudaMemcpyHostToDevice, st));
-        mq_bind(&A, d + acc_bytes);
+        // the tables and outputs go in the kernel parameters (offsets as recorded by mq_lower_group)
+        std::vector<MultiLaunch> L(1);
+        memcpy(L[0].words, blob.data(), static_cast<size_t>(A.nwords) * 4);
+        memcpy(L[0].breaks, blob.data() + reinterpret_cast<uintptr_t>(A.breaks), static_cast<size_t>(A.nbreaks) * 8);
+        memcpy(L[0].out, blob.data() + reinterpret_cast<uintptr_t>(A.out), static_cast<size_t>(A.nq) * sizeof(MqOut));
+        A.words = nullptr;
+        A.breaks = nullptr;
+        A.out = nullptr;
         A.ctl.ticket = reinterpret_cast<unsigned long long*>(d);
         A.acc = reinterpret_cast<unsigned long long*>(d) + 1;
         A.ctl.err = ctx->d_err;
@@ -359,7 +476,8 @@ static tqp_status shared_run(tqp_ctx* ctx, const tqp_table* t, const tqp_scan_qu
         const int grid = engine_grid(ctx, reinterpret_cast<const void*>(k_filter_multi), smem, A.G.ntiles, per_sm);
         A.ctl.chunk_tiles = (A.G.ntiles + grid - 1) / grid;
         A.ctl.nchunks = (A.G.ntiles + A.ctl.chunk_tiles - 1) / A.ctl.chunk_tiles;
-        k_filter_multi<<<static_cast<unsigned>(A.ctl.nchunks), kEngineThreads, smem, st>>>(A);
+        L[0].A = A;
+        k_filter_multi<<<static_cast<unsigned>(A.ctl.nchunks), kEngineThreads, smem, st>>>(L[0]);
         TQP_CUDA(cudaGetLastError());
     }
     for (int i : singles)

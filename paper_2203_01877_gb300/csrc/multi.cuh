@@ -128,6 +128,17 @@ __device__ __forceinline__ int64_t mq_factor_row(const ScanGeom& G, const TileVi
     return static_cast<int64_t>(x * a + b);
 }
 
+// 64-bit add to shared memory as two 32-bit atomic adds (low word, then the
+// high word with the carry): measured faster than a 64-bit atomic add on
+// shared memory.  Readers see the sum only after the warp's adds are done.
+__device__ __forceinline__ void add_shared_u64(unsigned long long* p, unsigned long long x) {
+    unsigned int* w = reinterpret_cast<unsigned int*>(p);
+    const unsigned int lo = static_cast<unsigned int>(x);
+    const unsigned int old = atomicAdd(w, lo);
+    const unsigned int hi = static_cast<unsigned int>(x >> 32) + (old + lo < old ? 1u : 0u);
+    if (hi) atomicAdd(w + 1, hi);
+}
+
 // A direct-table condition column held in registers by the fast path: the
 // value is clamped to [lo, lo + span] and indexes the table at word off.
 struct MqHot {
@@ -152,16 +163,22 @@ struct MultiBody {
     MqHot hot[kMqFastCols];    // fast path: the condition columns
     bool fast = false;         // every condition column has a direct table (at most kMqFastCols)
 
+    const MqOut* outp;         // the queries' outputs and row ranges
+
     // Every thread of the CTA copies its share of the tables and each
     // consumer warp clears its accumulators; the caller synchronises the CTA
-    // before the first tile.
-    __device__ MultiBody(const MultiArgs& a, unsigned char* sm) : A(a) {
+    // before the first tile.  The tables and outputs come from the argument
+    // block's pointers, or from the explicit ones (kernel parameters).
+    __device__ MultiBody(const MultiArgs& a, unsigned char* sm) : MultiBody(a, sm, a.words, a.breaks, a.out) {}
+    __device__ MultiBody(const MultiArgs& a, unsigned char* sm, const uint32_t* words, const int64_t* breaks,
+                         const MqOut* out)
+        : A(a), outp(out) {
         unsigned long long* acc = reinterpret_cast<unsigned long long*>(sm);
         unsigned int* cnt = reinterpret_cast<unsigned int*>(sm + kConsumerWarps * kMqMax * 8);
         uint32_t* ws = reinterpret_cast<uint32_t*>(sm + kMqAccBytes);
         int64_t* bs = reinterpret_cast<int64_t*>(sm + kMqAccBytes + mq_words_bytes(a.nwords));
-        for (int i = threadIdx.x; i < a.nwords; i += blockDim.x) ws[i] = a.words[i];
-        for (int i = threadIdx.x; i < a.nbreaks; i += blockDim.x) bs[i] = a.breaks[i];
+        for (int i = threadIdx.x; i < a.nwords; i += blockDim.x) ws[i] = words[i];
+        for (int i = threadIdx.x; i < a.nbreaks; i += blockDim.x) bs[i] = breaks[i];
         w = ws;
         bk = bs;
         const int warp = threadIdx.x / kWarp;
@@ -174,8 +191,8 @@ struct MultiBody {
             wcnt[lane] = 0;
         }
         if (lane < a.nq) {
-            rlo = a.out[lane].rlo;
-            rhi = a.out[lane].rhi;
+            rlo = out[lane].rlo;
+            rhi = out[lane].rhi;
         }
         fast = a.ncols <= kMqFastCols;
 #pragma unroll
@@ -291,7 +308,7 @@ struct MultiBody {
 #pragma unroll
             for (int j = 0; j < U; ++j)
                 if (j == jj) mm[j] = cur & (cur - 1);
-            atomicAdd(&wsum[q], static_cast<unsigned long long>(((esel >> q) & 1u) ? a1 : a0));
+            add_shared_u64(&wsum[q], static_cast<unsigned long long>(((esel >> q) & 1u) ? a1 : a0));
             atomicAdd(&wcnt[q], 1u);
         }
     }
@@ -382,7 +399,7 @@ struct MultiBody {
             __threadfence();
             const unsigned long long ts = atomicAdd(&A.acc[2 * lane], 0ULL);
             const unsigned long long tc = atomicAdd(&A.acc[2 * lane + 1], 0ULL);
-            const MqOut& o = A.out[lane];
+            const MqOut& o = outp[lane];
             if (o.count) *o.count = static_cast<int64_t>(tc);
             if (o.count2) *o.count2 = static_cast<int64_t>(tc);
             if (o.sum) *o.sum = static_cast<int64_t>(ts);
@@ -391,6 +408,20 @@ struct MultiBody {
 
     __device__ void finish(const ScanGeom&, int, int) {}
 };
+
+}  // namespace tqp
+
+namespace tqp {
+
+// The argument block of a stand-alone launch: the tables and outputs travel
+// as kernel parameters (no upload, nothing to synchronise with).
+struct MultiLaunch {
+    MultiArgs A;
+    uint32_t words[kMqWords];
+    int64_t breaks[kMqBreaks];
+    MqOut out[kMqMax];
+};
+static_assert(sizeof(MultiLaunch) <= 32764, "kernel parameters are limited to 32764 bytes");
 
 }  // namespace tqp
 
@@ -406,6 +437,8 @@ struct MqQuery {
     DExpr sum{};
     MqOut out{};
     std::vector<int> cols; // condition and expression columns, ascending
+    std::vector<int> ecols; // expression columns
+    std::vector<std::pair<int, int64_t>> bps;  // (column, breakpoint inside the column type's range)
 };
 
 tqp_status mq_lower_query(const tqp_table* t, const tqp_pred* preds, int32_t npreds, const tqp_expr* sum_expr,

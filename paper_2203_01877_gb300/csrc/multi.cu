@@ -504,6 +504,20 @@ extern "C" tqp_status tqp_filter_shared(tqp_ctx* ctx, const tqp_table* t, const 
     }
     DeviceGuard g(ctx->device);
     if (!g.ok) return fail(TQP_ERR_CUDA, "cannot select device %d", ctx->device);
-    arena_reset(ctx);
-    return shared_run(ctx, t, queries, nq, launch_of, static_cast<cudaStream_t>(stream));
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // shape class: rows, bytes per row of every column the queries read, query count
+    std::vector<int> cols;
+    for (int i = 0; i < nq; ++i) {
+        for (int k = 0; k < queries[i].npreds && k < TQP_MAX_PREDS; ++k) cols.push_back(queries[i].preds[k].col);
+        if (queries[i].has_sum) expr_col_ids(&queries[i].sum_expr, cols);
+    }
+    for (int& c : cols) c = c < 0 || c >= t->num_cols ? 0 : c;
+    char key[96];
+    snprintf(key, sizeof(key), "shared r%d b%d q%d", rows_class(t->num_rows), row_bytes(t, cols),
+             nq <= 2 ? nq : (nq <= 8 ? 8 : (nq <= 16 ? 16 : 32)));
+    auto run = [&]() {
+        arena_reset(ctx);
+        return shared_run(ctx, t, queries, nq, launch_of, st);
+    };
+    return tuned(ctx, key, st, 0, run);
 }

@@ -16,6 +16,11 @@ A plan is given as plain Python data:
   ``"add"``, ``"sub"``, ``"mul"``; column ``i`` addresses fact columns first,
   then dim columns.
 * ``aggs``: ``(fn, expr)`` with fn in ``sum count avg min max``.
+* string columns: 2-D uint8 arrays ``(n, width)``, one character per byte,
+  right-padded with 0 (Section 4.1); they take ``(col, "in", values)``,
+  ``(col, "like", pattern)`` and ``(col, "not_like", pattern)`` only (values
+  and patterns as ``str`` or ``bytes``); ``(col, "in", ints)`` also applies to
+  numeric columns.
 """
 from __future__ import annotations
 
@@ -36,7 +41,8 @@ _LIB = None
 
 OK, ERR_INVALID, ERR_CAPACITY, ERR_OVERFLOW, ERR_NOMEM = 0, 1, 4, 5, 6
 _TYPES = {np.dtype(np.int32): 0, np.dtype(np.int64): 1, np.dtype(np.uint8): 2}
-_OPS = {"lt": 0, "le": 1, "gt": 2, "ge": 3, "eq": 4, "ne": 5, "between": 6}
+_OPS = {"lt": 0, "le": 1, "gt": 2, "ge": 3, "eq": 4, "ne": 5, "between": 6, "in": 7, "like": 8, "not_like": 9}
+CHAR = 3
 _XK = {"col": 0, "const": 1, "add": 2, "sub": 3, "mul": 4}
 _FNS = {"sum": 0, "count": 1, "avg": 2, "min": 3, "max": 4}
 MAX_EXPR = 8
@@ -54,7 +60,7 @@ def build(force: bool = False) -> str:
 
 
 class Col(C.Structure):
-    _fields_ = [("data", C.c_void_p), ("type", C.c_int32), ("pad", C.c_int32)]
+    _fields_ = [("data", C.c_void_p), ("type", C.c_int32), ("width", C.c_int32)]
 
 
 class Pred(C.Structure):
@@ -108,8 +114,43 @@ def _cols(arrs):
         if a.dtype not in _TYPES:
             raise TypeError(f"unsupported column dtype {a.dtype}")
         cs[i].data = a.ctypes.data
-        cs[i].type = _TYPES[a.dtype]
+        if a.ndim == 2:  # a string column
+            if a.dtype != np.uint8:
+                raise TypeError("string columns are uint8 (n, width) arrays")
+            cs[i].type, cs[i].width = CHAR, a.shape[1]
+        else:
+            cs[i].type = _TYPES[a.dtype]
     return cs, arrs
+
+
+def _bytes(v) -> bytes:
+    return v.encode("latin-1") if isinstance(v, str) else bytes(v)
+
+
+def pad_strings(values, width: int) -> np.ndarray:
+    """``(k, width)`` uint8 rows: each value's bytes, right-padded with 0."""
+    out = np.zeros((len(values), width), np.uint8)
+    for i, v in enumerate(values):
+        b = _bytes(v)
+        if len(b) > width:
+            raise ValueError(f"string {b!r} longer than the column width {width}")
+        out[i, :len(b)] = np.frombuffer(b, np.uint8)
+    return out
+
+
+def _set_pred(pred, op, col, keep):
+    """lo / hi of an IN, LIKE or NOT LIKE predicate on column array ``col`` (buffers appended to ``keep``)."""
+    if op == "in":
+        if col.ndim == 2:
+            buf = pad_strings(pred, col.shape[1])
+        else:
+            buf = np.ascontiguousarray(np.asarray(list(pred), dtype=np.int64))
+        n = len(buf)
+    else:
+        buf = np.frombuffer(_bytes(pred), np.uint8).copy()
+        n = len(buf)
+    keep.append(buf)
+    return (buf.ctypes.data if n else 0), n
 
 
 def _expr(tokens) -> Expr:
@@ -157,10 +198,15 @@ def run_plan(fact, preds=(), dim=None, fact_fk=0, dim_key=0, group_cols=(), aggs
         raise ValueError("threads > 1 is for filter plans only")
     L = _lib if _lib is not None else lib()
     fcols, fkeep = _cols(fact)
+    fkeep_bufs = []  # IN lists and LIKE patterns, alive until the call returns
     nfact = len(fkeep[0]) if fkeep else 0
     dcols, dkeep = _cols(dim or [])
     pr = (Pred * max(1, len(preds)))()
     for i, (c, op, lo, *hi) in enumerate(preds):
+        if op in ("in", "like", "not_like"):
+            pr[i].col, pr[i].op = int(c), _OPS[op]
+            pr[i].lo, pr[i].hi = _set_pred(lo, op, fkeep[int(c)], fkeep_bufs)
+            continue
         pr[i].col, pr[i].op, pr[i].lo = int(c), _OPS[op], int(lo)
         pr[i].hi = int(hi[0]) if hi else 0
     gc = np.ascontiguousarray(np.asarray(group_cols, dtype=np.int32).reshape(-1))

@@ -7,6 +7,10 @@
  *
  *   filter            Section 3.1 (Listing 1 / selection vector): keep row i
  *                     iff every predicate holds; output row ids ascending.
+ *                     String columns (Section 4.1: a row's characters, one
+ *                     per byte, right-padded with 0) take IN and LIKE / NOT
+ *                     LIKE (Section 5's expression list); IN also applies to
+ *                     numeric columns.
  *   expressions       Section 5.1: post-order evaluation of an expression
  *                     tree, here given in postfix form, in exact int64.
  *   equi-join         Sections 5.2-5.3 (Algorithms 1 and 2): the multiset of
@@ -47,6 +51,52 @@ static int64_t col_value(const or_col* c, int64_t row) {
         case OR_U8: return (int64_t)((const uint8_t*)c->data)[row];
         default: return 0;
     }
+}
+
+/* The row's string: its bytes up to the first 0, at most `width`. */
+static int str_len(const uint8_t* s, int width) {
+    int n = 0;
+    while (n < width && s[n]) ++n;
+    return n;
+}
+
+/* SQL LIKE by dynamic programming over prefixes: after reading i characters,
+ * ok[j] says whether the pattern's first j bytes match them. */
+static int like_match(const uint8_t* s, int n, const uint8_t* pat, int m) {
+    unsigned char ok[OR_MAX_WIDTH + 1], nx[OR_MAX_WIDTH + 1];
+    ok[0] = 1;
+    for (int j = 1; j <= m; ++j) ok[j] = ok[j - 1] && pat[j - 1] == '%';
+    for (int i = 0; i < n; ++i) {
+        nx[0] = 0;
+        for (int j = 1; j <= m; ++j) {
+            if (pat[j - 1] == '%') nx[j] = nx[j - 1] || ok[j];  /* % takes nothing more, or s[i] too */
+            else nx[j] = ok[j - 1] && (pat[j - 1] == '_' || pat[j - 1] == s[i]);
+        }
+        memcpy(ok, nx, (size_t)m + 1);
+    }
+    return ok[m];
+}
+
+static int is_set_op(int op) { return op == OR_IN || op == OR_LIKE || op == OR_NOT_LIKE; }
+
+/* IN, LIKE and NOT LIKE at row `row` of column c (plain scans of the lists). */
+static int set_pred_holds(const or_pred* p, const or_col* c, int64_t row) {
+    if (c->type == OR_CHAR) {
+        const uint8_t* s = (const uint8_t*)c->data + row * (int64_t)c->width;
+        if (p->op == OR_IN) {
+            const uint8_t* v = (const uint8_t*)(intptr_t)p->lo;
+            for (int64_t k = 0; k < p->hi; ++k)
+                if (memcmp(s, v + k * (int64_t)c->width, (size_t)c->width) == 0) return 1;
+            return 0;
+        }
+        const int m = like_match(s, str_len(s, c->width), (const uint8_t*)(intptr_t)p->lo, (int)p->hi);
+        return p->op == OR_LIKE ? m : !m;
+    }
+    const int64_t x = col_value(c, row);
+    const int64_t* v = (const int64_t*)(intptr_t)p->lo;
+    for (int64_t k = 0; k < p->hi; ++k)
+        if (v[k] == x) return 1;
+    return 0;
 }
 
 static int pred_holds(const or_pred* p, int64_t x) {
@@ -147,7 +197,20 @@ static int cmp_trec(const void* a, const void* b) {
 }
 
 static int valid_col(const or_col* c) {
-    return c->type == OR_I32 || c->type == OR_I64 || c->type == OR_U8;
+    return c->type == OR_I32 || c->type == OR_I64 || c->type == OR_U8 ||
+           (c->type == OR_CHAR && c->width >= 1 && c->width <= OR_MAX_WIDTH);
+}
+
+/* a numeric column (strings are read by IN / LIKE predicates only) */
+static int numeric_col(const or_plan* p, int32_t c) {
+    if (c < p->nfact_cols) return p->fact[c].type != OR_CHAR;
+    return c - p->nfact_cols < p->ndim_cols && p->dim[c - p->nfact_cols].type != OR_CHAR;
+}
+
+static int numeric_expr(const or_plan* p, const or_expr* e) {
+    for (int i = 0; i < e->n; ++i)
+        if (e->kind[i] == OR_X_COL && !numeric_col(p, (int32_t)e->v[i])) return 0;
+    return 1;
 }
 
 /* every column operand of the expression must address an existing column */
@@ -163,8 +226,16 @@ int oracle_plan(const or_plan* p, or_out* o) {
         return OR_ERR_INVALID;
     for (int i = 0; i < p->nfact_cols; ++i)
         if (!valid_col(&p->fact[i])) return OR_ERR_INVALID;
-    for (int i = 0; i < p->npreds; ++i)
-        if (p->preds[i].col < 0 || p->preds[i].col >= p->nfact_cols) return OR_ERR_INVALID;
+    for (int i = 0; i < p->npreds; ++i) {
+        const or_pred* q = &p->preds[i];
+        if (q->col < 0 || q->col >= p->nfact_cols) return OR_ERR_INVALID;
+        const int str = p->fact[q->col].type == OR_CHAR;
+        if (q->op < OR_LT || q->op > OR_NOT_LIKE) return OR_ERR_INVALID;
+        if (str && q->op != OR_IN && q->op != OR_LIKE && q->op != OR_NOT_LIKE) return OR_ERR_INVALID;
+        if (!str && (q->op == OR_LIKE || q->op == OR_NOT_LIKE)) return OR_ERR_INVALID;
+        if (is_set_op(q->op) && (q->hi < 0 || (q->hi > 0 && q->lo == 0))) return OR_ERR_INVALID;
+        if ((q->op == OR_LIKE || q->op == OR_NOT_LIKE) && q->hi > OR_MAX_WIDTH) return OR_ERR_INVALID;
+    }
     int joined = p->ndim_cols > 0;
     int ncat = p->nfact_cols + (joined ? p->ndim_cols : 0);
     for (int i = 0; i < p->ngc; ++i)
@@ -176,6 +247,15 @@ int oracle_plan(const or_plan* p, or_out* o) {
         if (p->aggs[a].fn != OR_COUNT && !valid_expr(&p->aggs[a].expr, ncat)) return OR_ERR_INVALID;
     }
     if (p->sum_expr && !valid_expr(p->sum_expr, ncat)) return OR_ERR_INVALID;
+    /* string columns feed IN / LIKE predicates only */
+    for (int i = 0; i < p->ngc; ++i)
+        if (!numeric_col(p, p->group_cols[i])) return OR_ERR_INVALID;
+    for (int a = 0; a < p->naggs; ++a)
+        if (p->aggs[a].fn != OR_COUNT && !numeric_expr(p, &p->aggs[a].expr)) return OR_ERR_INVALID;
+    if (p->sum_expr && !numeric_expr(p, p->sum_expr)) return OR_ERR_INVALID;
+    if (joined && p->fact_fk >= 0 && p->fact_fk < p->nfact_cols && p->dim_key >= 0 && p->dim_key < p->ndim_cols &&
+        (p->fact[p->fact_fk].type == OR_CHAR || p->dim[p->dim_key].type == OR_CHAR))
+        return OR_ERR_INVALID;
     if (joined && (p->join_kind < OR_JOIN_INNER || p->join_kind > OR_JOIN_LEFT_OUTER)) return OR_ERR_INVALID;
     if (joined && p->join_kind != OR_JOIN_INNER) {  /* no dim row to read: fact columns only */
         for (int i = 0; i < p->ngc; ++i)
@@ -192,8 +272,11 @@ int oracle_plan(const or_plan* p, or_out* o) {
     int64_t ns = 0;
     for (int64_t i = 0; i < p->nfact; ++i) {
         int keep = 1;
-        for (int j = 0; j < p->npreds && keep; ++j)
-            keep = pred_holds(&p->preds[j], col_value(&p->fact[p->preds[j].col], i));
+        for (int j = 0; j < p->npreds && keep; ++j) {
+            const or_pred* q = &p->preds[j];
+            keep = is_set_op(q->op) ? set_pred_holds(q, &p->fact[q->col], i)
+                                    : pred_holds(q, col_value(&p->fact[q->col], i));
+        }
         if (keep) surv[ns++] = i;
     }
     o->num_rows = ns;

@@ -30,6 +30,8 @@ extern "C" {
 #define OR_I32 0
 #define OR_I64 1
 #define OR_U8 2
+#define OR_CHAR 3   /* strings: `width` bytes per row, right-padded with 0 (paper Section 4.1) */
+#define OR_MAX_WIDTH 255
 
 /* comparison operators; BETWEEN is inclusive on both ends */
 #define OR_LT 0
@@ -39,6 +41,18 @@ extern "C" {
 #define OR_EQ 4
 #define OR_NE 5
 #define OR_BETWEEN 6
+/* set membership and pattern matching (paper Section 5 lists IN and LIKE):
+ *   IN        lo = host address of the values, hi = their count; int64 values
+ *             for a numeric column, `width`-byte 0-padded strings for a
+ *             string column;
+ *   LIKE, NOT LIKE (string columns only): lo = host address of the pattern
+ *             bytes, hi = its length (at most OR_MAX_WIDTH); `%` matches any
+ *             sequence (also none), `_` one character, any other byte itself;
+ *             no escape character.  A row's string is its bytes up to the
+ *             first 0 (or all `width` bytes). */
+#define OR_IN 7
+#define OR_LIKE 8
+#define OR_NOT_LIKE 9
 
 /* postfix expression opcodes */
 #define OR_X_COL 0
@@ -65,7 +79,7 @@ extern "C" {
 
 #define OR_MAX_EXPR 8
 
-typedef struct { const void* data; int32_t type; int32_t pad; } or_col;
+typedef struct { const void* data; int32_t type; int32_t width; } or_col;  /* width: OR_CHAR only */
 typedef struct { int32_t col; int32_t op; int64_t lo; int64_t hi; } or_pred;
 typedef struct { int32_t n; int32_t kind[OR_MAX_EXPR]; int64_t v[OR_MAX_EXPR]; } or_expr;
 typedef struct { int32_t fn; int32_t pad; or_expr expr; } or_agg;

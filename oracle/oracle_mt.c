@@ -56,7 +56,9 @@ int oracle_filter_mt(const or_plan* p, or_out* o, int nthreads) {
         r->plan.nfact = r1 - r0;
         for (int c = 0; c < p->nfact_cols; ++c) {
             r->cols[c] = p->fact[c];
-            r->cols[c].data = (const char*)p->fact[c].data + (size_t)r0 * (size_t)elem_bytes(p->fact[c].type);
+            r->cols[c].data = (const char*)p->fact[c].data +
+                              (size_t)r0 * (size_t)(p->fact[c].type == OR_CHAR ? p->fact[c].width
+                                                                                 : elem_bytes(p->fact[c].type));
         }
         r->plan.fact = r->cols;
         r->row0 = r0;

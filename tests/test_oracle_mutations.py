@@ -17,6 +17,7 @@ import oracle
 from tests import test_oracle_filter as tf
 from tests import test_oracle_groupby as tg
 from tests import test_oracle_join as tj
+from tests import test_oracle_strings as ts
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "oracle.c")
 HDR = os.path.join(os.path.dirname(oracle.__file__), "oracle.h")
@@ -48,6 +49,12 @@ MUTANTS = {
                                   "if (p->join_kind == OR_JOIN_LEFT_OUTER) {"),
     "sum_skips_last_row": ("for (int64_t i = 0; i < npairs; ++i) {\n            int64_t v;",
                            "for (int64_t i = 0; i + 1 < npairs; ++i) {\n            int64_t v;"),
+    "like_percent_not_empty": ("nx[j] = nx[j - 1] || ok[j];", "nx[j] = ok[j];"),
+    "like_underscore_as_percent": ("if (pat[j - 1] == '%') nx[j]", "if (pat[j - 1] == '%' || pat[j - 1] == '_') nx[j]"),
+    "in_strings_prefix_only": ("memcmp(s, v + k * (int64_t)c->width, (size_t)c->width)",
+                               "memcmp(s, v + k * (int64_t)c->width, (size_t)(c->width < 3 ? c->width : 3))"),
+    "in_numbers_skips_last": ("for (int64_t k = 0; k < p->hi; ++k)\n        if (v[k] == x) return 1;",
+                              "for (int64_t k = 0; k + 1 < p->hi; ++k)\n        if (v[k] == x) return 1;"),
 }
 
 PINS = [
@@ -70,6 +77,10 @@ PINS = [
     tj.test_join_group_topk_invariants,
     tj.test_semi_anti_vs_nested_loop_and_numpy,
     tj.test_left_outer_vs_nested_loop_and_identities,
+    ts.test_like_hand_worked,
+    lambda: ts.test_like_vs_regex_random(1),
+    ts.test_in_strings_and_numbers,
+    ts.test_mixed_plan_vs_row_loop,
 ]
 
 

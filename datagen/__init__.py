@@ -233,3 +233,42 @@ def log_uniform_int(seed: int, col_id: int, n: int, lo: int, hi: int) -> np.ndar
     u = unit_float(seed, col_id, 0, n)
     v = np.exp(math.log(lo) + u * (math.log(hi) - math.log(lo)))
     return np.clip(np.floor(v).astype(np.int64), lo, hi)
+
+
+COL_WORDS, COL_WORD0 = 20, 21  # string column draws: word count, then one column per word slot
+STR_WIDTH = 24
+STR_VOCAB = 32
+
+
+def string_vocab(seed: int = DEFAULT_SEED) -> list:
+    """``STR_VOCAB`` synthetic lowercase words of 3 to 7 letters (a seeded draw, no natural-language list)."""
+    lens = uniform_int(seed, 30, STR_VOCAB, 3, 7, np.int64)
+    letters = uniform_int(seed, 31, STR_VOCAB * 7, 0, 25, np.int64).reshape(STR_VOCAB, 7)
+    return [bytes((97 + letters[i, :lens[i]]).astype(np.uint8)) for i in range(STR_VOCAB)]
+
+
+def string_column(n: int, seed: int = DEFAULT_SEED, width: int = STR_WIDTH, row0: int = 0) -> np.ndarray:
+    """A string column: each row 1 to 3 words of the seeded vocabulary joined by one space, as an
+    ``(n, width)`` uint8 array right-padded with 0 (the paper's (n x m) character tensor, Section 4.1).
+    ``width`` >= 23 holds every row; a smaller width cuts rows at ``width`` bytes (no padding byte left)."""
+    vocab = string_vocab(seed)
+    wl = np.array([len(w) for w in vocab], np.int64)
+    wb = np.zeros((STR_VOCAB, 7), np.uint8)
+    for i, w in enumerate(vocab):
+        wb[i, :len(w)] = np.frombuffer(w, np.uint8)
+    k = uniform_int(seed, COL_WORDS, n, 1, 3, np.int64, row0)
+    out = np.zeros((n, width + 8), np.uint8)   # slack for the last word, cut below
+    pos = np.zeros(n, np.int64)
+    rows = np.arange(n)
+    for slot in range(3):
+        w = uniform_int(seed, COL_WORD0 + slot, n, 0, STR_VOCAB - 1, np.int64, row0)
+        act = slot < k
+        if slot:
+            sp = act & (pos < width + 7)
+            out[rows[sp], pos[sp]] = 32
+            pos = pos + act
+        for j in range(7):
+            m = act & (j < wl[w]) & (pos + j < width + 8)
+            out[rows[m], (pos + j)[m]] = wb[w[m], j]
+        pos = pos + np.where(act, wl[w], 0)
+    return np.ascontiguousarray(out[:, :width])

@@ -69,12 +69,18 @@ typedef enum {
     TQP_ERR_CUDA = 7           /* a CUDA runtime call failed (message has the CUDA error) */
 } tqp_status;
 
-typedef enum { TQP_I32 = 0, TQP_I64 = 1, TQP_U8 = 2 } tqp_dtype;
+typedef enum { TQP_I32 = 0, TQP_I64 = 1, TQP_U8 = 2, TQP_CHAR = 3 } tqp_dtype;
 
 /* One column: device pointer (or, for tqp_filter, see the conventions above)
  * to num_rows elements of `type`; `scale` is the
  * decimal exponent of a fixed-point column (informational; arithmetic is on
- * the stored integers). */
+ * the stored integers).
+ * String columns (paper Section 4.1: an (n x m) tensor of character codes, a
+ * string right-padded with 0s to the column's width m): type TQP_CHAR, `scale`
+ * = m in [1, 255], `data` = num_rows * m bytes, row i's string at
+ * [i*m, (i+1)*m) -- its bytes up to the first 0.  A string column is read by
+ * TQP_IN, TQP_LIKE and TQP_NOT_LIKE predicates only (a comparison, an
+ * expression, a group key or a join key on it is TQP_ERR_INVALID_ARG). */
 typedef struct {
     const void* data;
     int32_t type;
@@ -91,7 +97,26 @@ typedef struct {
 /* Comparison predicates (paper Section 3.1 / 5.1); a list of predicates is
  * their conjunction.  Comparisons are on the column value widened to int64.
  * BETWEEN is inclusive: lo <= x <= hi. */
-typedef enum { TQP_LT = 0, TQP_LE, TQP_GT, TQP_GE, TQP_EQ, TQP_NE, TQP_BETWEEN } tqp_cmp;
+typedef enum { TQP_LT = 0, TQP_LE, TQP_GT, TQP_GE, TQP_EQ, TQP_NE, TQP_BETWEEN, TQP_IN, TQP_LIKE, TQP_NOT_LIKE } tqp_cmp;
+
+/* Set membership and pattern predicates (paper Section 5's IN and LIKE):
+ *   TQP_IN        lo = host address of the values, hi = their count: int64
+ *                 values for a numeric column, hi strings of the column's width
+ *                 (each right-padded with 0, hi * m bytes) for a string column;
+ *   TQP_LIKE, TQP_NOT_LIKE (string columns only): lo = host address of the
+ *                 pattern's bytes, hi = its length (at most 255); `%` matches
+ *                 any sequence of characters (also none), `_` exactly one,
+ *                 every other byte itself; there is no escape character.
+ * The host memory is read during the call only.  tqp_filter,
+ * tqp_groupby_agg and tqp_run_plan (fact predicates) evaluate them in one
+ * pre-pass over the columns involved (a warp stages 32 strings in shared
+ * memory, each lane matches its row) that writes a one-byte pass column to
+ * the context's arena; the scan then filters on it.  The values and patterns
+ * of one call take at most TQP_MAX_SET_BYTES bytes (IN values sorted and
+ * deduplicated: 8 per number, m per string), else TQP_ERR_UNSUPPORTED.
+ * tqp_filter_noalloc returns TQP_ERR_UNSUPPORTED for them; tqp_filter_shared
+ * runs such queries alone; batches hand such plans to the single-plan path. */
+#define TQP_MAX_SET_BYTES 24576
 
 typedef struct {
     int32_t col;   /* column index in the table */

@@ -26,9 +26,9 @@ _LOCK = threading.Lock()
 _LIB = None
 
 OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_OUT_OF_MEMORY, ERR_CAPACITY, ERR_OVERFLOW, ERR_TIMEOUT, ERR_CUDA = range(8)
-I32, I64, U8 = 0, 1, 2
+I32, I64, U8, CHAR = 0, 1, 2, 3
 MAX_PREDS, MAX_EXPR, MAX_GROUP_COLS, MAX_AGGS, MAX_COLS = 8, 8, 4, 8, 16
-_OPS = {"lt": 0, "le": 1, "gt": 2, "ge": 3, "eq": 4, "ne": 5, "between": 6}
+_OPS = {"lt": 0, "le": 1, "gt": 2, "ge": 3, "eq": 4, "ne": 5, "between": 6, "in": 7, "like": 8, "not_like": 9}
 _XOPS = {"col": 0, "const": 1, "add": 2, "sub": 3, "mul": 4}
 _FNS = {"sum": 0, "count": 1, "avg": 2, "min": 3, "max": 4}
 
@@ -182,21 +182,30 @@ class TableRef:
     use is rejected by the library."""
 
     def __init__(self, cols, scales=None, host_ok=False):
+        """A 2-D uint8 tensor (n, width) is a string column (one character per byte, right-padded with 0)."""
+        import torch
         cols = list(cols)
         if not cols:
             raise ValueError("a table needs at least one column")
-        n = cols[0].numel()
+        rows = lambda c: c.shape[0] if c.dim() == 2 else c.numel()  # noqa: E731
+        n = rows(cols[0])
         for c in cols:
             on_host = host_ok and not c.is_cuda and c.is_pinned()
-            if not (c.is_cuda or on_host) or not c.is_contiguous() or c.numel() != n:
+            if not (c.is_cuda or on_host) or not c.is_contiguous() or rows(c) != n:
                 raise ValueError("columns must be contiguous CUDA tensors (or pinned host tensors with host_ok) "
                                  "of equal length")
+            if c.dim() == 2 and c.dtype != torch.uint8:
+                raise TypeError("string columns are uint8 (n, width) tensors")
         self.tensors = cols
+        self.widths = [c.shape[1] if c.dim() == 2 else 0 for c in cols]
         self.carr = (Column * len(cols))()
         for i, c in enumerate(cols):
             self.carr[i].data = c.data_ptr()
-            self.carr[i].type = _dtype_code(c)
-            self.carr[i].scale = (scales[i] if scales else 0)
+            if c.dim() == 2:
+                self.carr[i].type, self.carr[i].scale = CHAR, c.shape[1]
+            else:
+                self.carr[i].type = _dtype_code(c)
+                self.carr[i].scale = (scales[i] if scales else 0)
         self.t = Table(n, len(cols), 0, self.carr)
 
     @property
@@ -222,11 +231,54 @@ def make_expr(tokens) -> Expr:
     return e
 
 
-def make_preds(preds):
+def _bytes(v) -> bytes:
+    return v.encode("latin-1") if isinstance(v, str) else bytes(v)
+
+
+def _set_operand(table, col, op, v, keep):
+    """lo / hi of an IN, LIKE or NOT LIKE predicate: the host address and count of its values (IN: int64
+    numbers, or the column width's 0-padded strings) or of its pattern bytes; the buffer goes to `keep`."""
+    import numpy as np
+    width = table.widths[col] if table is not None and 0 <= col < len(table.widths) else 0
+    if op == "in":
+        vals = list(v)
+        if width:
+            buf = np.zeros((len(vals), width), np.uint8)
+            for k, x in enumerate(vals):
+                b = _bytes(x)
+                if len(b) > width:
+                    raise ValueError(f"IN value {b!r} longer than the column width {width}")
+                buf[k, :len(b)] = np.frombuffer(b, np.uint8)
+        elif vals and isinstance(vals[0], (str, bytes)):
+            raise ValueError("IN with strings needs the table (to know the column width)")
+        else:
+            buf = np.asarray(vals, dtype=np.int64).reshape(-1)
+    else:
+        buf = np.frombuffer(_bytes(v), np.uint8).copy()
+    buf = np.ascontiguousarray(buf)
+    keep.append(buf)
+    n = len(buf)
+    return (buf.ctypes.data if n else 0), n
+
+
+def _fill_pred(dst, table, pred, keep):
+    c, op, lo, *hi = pred
+    dst.col, dst.op = int(c), _OPS[op]
+    if op in ("in", "like", "not_like"):
+        dst.lo, dst.hi = _set_operand(table, int(c), op, lo, keep)
+    else:
+        dst.lo = int(lo)
+        dst.hi = int(hi[0]) if hi else 0
+
+
+def make_preds(preds, table=None):
+    """Predicates (col, op, lo[, hi]); op "in" takes a list of values, "like" / "not_like" a pattern (str or
+    bytes).  The array keeps the value buffers alive (``_keep``)."""
     arr = (Pred * max(1, len(preds)))()
-    for i, (c, op, lo, *hi) in enumerate(preds):
-        arr[i].col, arr[i].op, arr[i].lo = int(c), _OPS[op], int(lo)
-        arr[i].hi = int(hi[0]) if hi else 0
+    keep = []
+    for i, pr in enumerate(preds):
+        _fill_pred(arr[i], table, pr, keep)
+    arr._keep = keep
     return arr
 
 
@@ -297,7 +349,7 @@ class Context:
 
 def tqp_filter(ctx: Context, table: TableRef, preds=(), sum_expr=None, d_sum=None, d_row_ids=None,
                capacity: int = 0, d_count=None, stream=None):
-    pa = make_preds(preds)
+    pa = make_preds(preds, table)
     se = C.byref(make_expr(sum_expr)) if sum_expr is not None else None
     _check(lib().tqp_filter(ctx.h, table.ref(), pa, len(preds), se, _ptr(d_sum), _ptr(d_row_ids),
                             int(capacity), _ptr(d_count), _stream(stream)))
@@ -307,21 +359,22 @@ def tqp_filter_noalloc(device: int, table: TableRef, preds=(), sum_expr=None, d_
                        capacity: int = 0, d_count=None, d_status=None, stream=None):
     """tqp_filter without a context, for callers that cannot allocate device
     memory; its scratch is a fixed array inside libtqp (see include/tqp.h)."""
-    pa = make_preds(preds)
+    pa = make_preds(preds, table)
     se = C.byref(make_expr(sum_expr)) if sum_expr is not None else None
     _check(lib().tqp_filter_noalloc(int(device), table.ref(), pa, len(preds), se, _ptr(d_sum), _ptr(d_row_ids),
                                     int(capacity), _ptr(d_count), _ptr(d_status), _stream(stream)))
 
 
-def make_scan_queries(queries):
+def make_scan_queries(queries, table=None):
     """queries: (preds, sum_expr or None, d_count, d_sum or None) tuples."""
     arr = (ScanQuery * max(1, len(queries)))()
+    keep = []
+    arr._keep = keep
     for i, (preds, ex, d_count, d_sum) in enumerate(queries):
         if len(preds) > MAX_PREDS:
             raise ValueError("more than 8 predicates")
-        for j, (c, op, lo, *hi) in enumerate(preds):
-            arr[i].preds[j].col, arr[i].preds[j].op, arr[i].preds[j].lo = int(c), _OPS[op], int(lo)
-            arr[i].preds[j].hi = int(hi[0]) if hi else 0
+        for j, pr in enumerate(preds):
+            _fill_pred(arr[i].preds[j], table, pr, keep)
         arr[i].npreds = len(preds)
         if ex is not None:
             arr[i].has_sum = 1
@@ -334,9 +387,9 @@ def make_scan_queries(queries):
 class ScanQueries:
     """Queries marshalled once (make_scan_queries) for repeated tqp_filter_shared calls."""
 
-    def __init__(self, queries):
+    def __init__(self, queries, table=None):
         self.n = len(queries)
-        self.arr = make_scan_queries(queries)
+        self.arr = make_scan_queries(queries, table)
         self.launch_of = (C.c_int32 * max(1, self.n))()
 
 
@@ -345,14 +398,14 @@ def tqp_filter_shared(ctx: Context, table: TableRef, queries, stream=None):
     tqp_filter without row ids gives it.  `queries` is a list of such tuples or
     a ScanQueries.  Returns each query's launch index (-1: it ran alone through
     the single-query scan)."""
-    q = queries if isinstance(queries, ScanQueries) else ScanQueries(queries)
+    q = queries if isinstance(queries, ScanQueries) else ScanQueries(queries, table)
     _check(lib().tqp_filter_shared(ctx.h, table.ref(), q.arr, q.n, q.launch_of, _stream(stream)))
     return [int(q.launch_of[i]) for i in range(q.n)]
 
 
 def tqp_groupby_agg(ctx: Context, table: TableRef, preds, group_cols, aggs, d_keys, d_ivals, d_fvals,
                     capacity_groups: int, d_num_groups, stream=None):
-    pa = make_preds(preds)
+    pa = make_preds(preds, table)
     gc = (C.c_int32 * max(1, len(group_cols)))(*[int(c) for c in group_cols])
     ag = make_aggs(aggs)
     _check(lib().tqp_groupby_agg(ctx.h, table.ref(), pa, len(preds), gc, len(group_cols), ag, len(aggs),
@@ -386,9 +439,10 @@ def make_plan(fact: TableRef, preds=(), dim: TableRef | None = None, fact_fk=0, 
     p.fact = C.pointer(fact.t)
     if len(preds) > MAX_PREDS or len(group_cols) > MAX_GROUP_COLS or len(aggs) > MAX_AGGS:
         raise ValueError("plan exceeds the fixed plan limits")
-    pa = make_preds(preds)
+    pa = make_preds(preds, fact)
     for i in range(len(preds)):
         p.preds[i] = pa[i]
+    p._keep = pa._keep
     p.npreds = len(preds)
     p.emit_row_ids = int(bool(emit_row_ids))
     p.dim = C.pointer(dim.t) if dim is not None else None

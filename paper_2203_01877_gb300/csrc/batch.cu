@@ -797,8 +797,17 @@ static bool all_device(const tqp_table* t) {
     return ok;
 }
 
+static bool has_strings(const tqp_table* t) {
+    for (int c = 0; c < t->num_cols && t->cols; ++c)
+        if (t->cols[c].type == TQP_CHAR) return true;
+    return false;
+}
+
 static bool batchable(const tqp_ctx* ctx, const tqp_plan* p, const tqp_result* r) {
     if (!p->fact || p->npreds < 0 || p->npreds > TQP_MAX_PREDS) return false;
+    // IN / LIKE and string columns: the single-plan path (its pre-pass)
+    if (has_strings(p->fact) || (p->dim && has_strings(p->dim)) || has_set_preds(p->fact, p->preds, p->npreds))
+        return false;
     if (p->dim && p->join_kind != TQP_JOIN_INNER) return false;  // semi / anti plans: the single-plan path
     if (p->ngc < 0 || p->ngc > TQP_MAX_GROUP_COLS || p->naggs < 0 || p->naggs > TQP_MAX_AGGS) return false;
     if (p->topk < 0 || p->topk > kTopBlock / 2) return false;

@@ -98,12 +98,21 @@ tqp_status check_table(const tqp_table* t, const char* what) {
     if (!t->cols) return fail(TQP_ERR_INVALID_ARG, "%s: cols is NULL", what);
     for (int c = 0; c < t->num_cols; ++c) {
         const tqp_column& col = t->cols[c];
-        if (col.type != TQP_I32 && col.type != TQP_I64 && col.type != TQP_U8)
+        if (col.type != TQP_I32 && col.type != TQP_I64 && col.type != TQP_U8 && col.type != TQP_CHAR)
             return fail(TQP_ERR_INVALID_ARG, "%s: column %d has unknown type %d", what, c, col.type);
+        if (col.type == TQP_CHAR && (col.scale < 1 || col.scale > 255))
+            return fail(TQP_ERR_INVALID_ARG, "%s: string column %d has width %d outside [1, 255]", what, c, col.scale);
         if (t->num_rows > 0 && !col.data) return fail(TQP_ERR_INVALID_ARG, "%s: column %d data is NULL", what, c);
         if (reinterpret_cast<uintptr_t>(col.data) % 16 != 0)
             return fail(TQP_ERR_INVALID_ARG, "%s: column %d is not 16-byte aligned", what, c);
     }
+    return TQP_OK;
+}
+
+tqp_status check_numeric_cols(const tqp_table* t, const std::vector<int>& cols, const char* what) {
+    for (int c : cols)
+        if (c >= 0 && c < t->num_cols && t->cols[c].type == TQP_CHAR)
+            return fail(TQP_ERR_INVALID_ARG, "%s: string column %d is read by IN / LIKE predicates only", what, c);
     return TQP_OK;
 }
 
@@ -149,6 +158,13 @@ tqp_status lower_preds(const tqp_table* t, const tqp_pred* preds, int32_t npreds
     if (npreds < 0 || npreds > TQP_MAX_PREDS)
         return fail(TQP_ERR_INVALID_ARG, "npreds %d outside [0, %d]", npreds, TQP_MAX_PREDS);
     if (npreds > 0 && !preds) return fail(TQP_ERR_INVALID_ARG, "preds is NULL");
+    for (int i = 0; i < npreds; ++i) {
+        if (preds[i].op == TQP_IN || preds[i].op == TQP_LIKE || preds[i].op == TQP_NOT_LIKE)
+            return fail(TQP_ERR_UNSUPPORTED, "predicate %d: IN / LIKE need the pre-pass, which this call does not run", i);
+        if (preds[i].col >= 0 && preds[i].col < t->num_cols && t->cols[preds[i].col].type == TQP_CHAR)
+            return fail(TQP_ERR_INVALID_ARG, "predicate %d: string column %d takes IN / LIKE / NOT LIKE only", i,
+                        preds[i].col);
+    }
     // Merge every non-NE comparison on a column into one inclusive range.
     std::vector<int64_t> lo(t->num_cols, INT64_MIN), hi(t->num_cols, INT64_MAX);
     std::vector<bool> used(t->num_cols, false), empty(t->num_cols, false);

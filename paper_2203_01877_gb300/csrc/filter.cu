@@ -270,6 +270,7 @@ static tqp_status plan_filter(const tqp_ctx* ctx, const tqp_table* t, const tqp_
     if (A->has_sum) {  // the rest are read in place at passing rows only
         std::vector<int> lazy;
         expr_cols(A->sum, lazy);
+        TQP_TRY(check_numeric_cols(t, lazy, "tqp_filter sum_expr"));
         TQP_TRY(check_visible_cols(t, lazy, "tqp_filter"));
     }
     int bpr = 0;
@@ -317,6 +318,14 @@ static tqp_status launch_filter_with(FilterArgs& A, int grid, size_t smem, const
 tqp_status launch_filter(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* preds, int32_t npreds,
                          const tqp_expr* sum_expr, int64_t* d_sum, int32_t* d_row_ids, int64_t capacity,
                          int64_t* d_count, cudaStream_t stream, const tqp_tuning* force) {
+    // IN / LIKE / NOT LIKE: one pre-pass writes a pass column that the scan then filters on
+    StrLowered SL;
+    TQP_TRY(str_prepass(ctx, t, preds, npreds, stream, &SL));
+    if (SL.active) {
+        t = &SL.t;
+        preds = SL.preds;
+        npreds = SL.npreds;
+    }
     FilterArgs A;
     size_t smem = 0;
     int grid = 0;

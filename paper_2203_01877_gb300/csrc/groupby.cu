@@ -394,6 +394,14 @@ tqp_status launch_groupby(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* pred
                           int64_t* d_keys, int64_t* d_ivals, double* d_fvals, int64_t capacity_groups,
                           int64_t* d_num_groups, cudaStream_t stream, long long max_groups, int topk, int topk_agg,
                           int64_t* d_total_groups) {
+    // IN / LIKE / NOT LIKE: one pre-pass writes a pass column that the scan then filters on
+    StrLowered SL;
+    TQP_TRY(str_prepass(ctx, t, preds, npreds, stream, &SL));
+    if (SL.active) {
+        t = &SL.t;
+        preds = SL.preds;
+        npreds = SL.npreds;
+    }
     GroupArgs A;
     memset(&A, 0, sizeof(A));
     int ncond = 0;
@@ -406,6 +414,7 @@ tqp_status launch_groupby(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* pred
             return fail(TQP_ERR_INVALID_ARG, "group column %d out of range", group_cols[i]);
         types[i] = t->cols[group_cols[i]].type;
     }
+    TQP_TRY(check_numeric_cols(t, std::vector<int>(group_cols, group_cols + std::max(0, ngc)), "tqp_groupby_agg"));
     TQP_TRY(lower_group(group_cols, types, ngc, aggs, naggs, t->num_cols, &A.S));
     bool need_f = false;
     for (int j = 0; j < naggs; ++j) need_f |= aggs[j].fn == TQP_AVG;
@@ -416,6 +425,7 @@ tqp_status launch_groupby(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* pred
     for (int i = 0; i < ncond; ++i) staged.push_back(A.cond[i].col);
     for (int i = 0; i < ngc; ++i) staged.push_back(group_cols[i]);
     for (int a = 1; a < A.S.nacc; ++a) expr_cols(A.S.acc_expr[a - 1], staged);
+    TQP_TRY(check_numeric_cols(t, staged, "tqp_groupby_agg"));
     TQP_TRY(check_device_cols(t, staged, "tqp_groupby_agg"));
     std::vector<int> u = staged;
     std::sort(u.begin(), u.end());

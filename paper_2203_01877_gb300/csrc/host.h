@@ -184,6 +184,29 @@ tqp_status allow_smem(const tqp_ctx* ctx, const void* kernel, SmemFlags& flags);
 // kernel: unlike a pageable memcpy it can be captured in a CUDA graph).
 tqp_status set_device_i64(long long* d_ptr, long long value, cudaStream_t stream);
 
+// IN / LIKE / NOT LIKE predicates and string columns (strings.cu): whether a
+// predicate list needs the pre-pass, and the pre-pass itself.  With active
+// set, `t` is the input table with one uint8 pass column appended (index
+// t->num_cols, in the arena) and `preds` the numeric predicates plus
+// "pass column == 1"; otherwise `t` and `preds` are the inputs.  `t.cols`
+// points into `cols`: not copyable.
+struct StrLowered {
+    bool active = false;
+    tqp_table t{};
+    std::vector<tqp_column> cols;
+    tqp_pred preds[TQP_MAX_PREDS];
+    int32_t npreds = 0;
+    StrLowered() = default;
+    StrLowered(const StrLowered&) = delete;
+    StrLowered& operator=(const StrLowered&) = delete;
+};
+bool has_set_preds(const tqp_table* t, const tqp_pred* preds, int32_t npreds);
+tqp_status str_prepass(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* preds, int32_t npreds, cudaStream_t st,
+                       StrLowered* out);
+// Columns read by arithmetic, keys or comparisons must be numeric (a string
+// column feeds IN / LIKE predicates only).
+tqp_status check_numeric_cols(const tqp_table* t, const std::vector<int>& cols, const char* what);
+
 // The single-query filter scan (tqp_filter's body, in the caller's arena).
 tqp_status launch_filter(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* preds, int32_t npreds,
                          const tqp_expr* sum_expr, int64_t* d_sum, int32_t* d_row_ids, int64_t capacity,

@@ -566,6 +566,8 @@ extern "C" tqp_status tqp_hash_join_kind(tqp_ctx* ctx, const tqp_table* build, i
     TQP_TRY(check_device_cols(probe, {probe_key}, "tqp_hash_join(probe)"));
     if (build_key < 0 || build_key >= build->num_cols) return fail(TQP_ERR_INVALID_ARG, "build_key out of range");
     if (probe_key < 0 || probe_key >= probe->num_cols) return fail(TQP_ERR_INVALID_ARG, "probe_key out of range");
+    TQP_TRY(check_numeric_cols(build, {build_key}, "tqp_hash_join(build)"));
+    TQP_TRY(check_numeric_cols(probe, {probe_key}, "tqp_hash_join(probe)"));
     if (!d_count) return fail(TQP_ERR_INVALID_ARG, "d_count is NULL");
     if (capacity < 0) return fail(TQP_ERR_INVALID_ARG, "capacity < 0");
     if (capacity > 0 && (!d_build_idx || !d_probe_idx))

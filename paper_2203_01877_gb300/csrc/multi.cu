@@ -51,6 +51,7 @@ tqp_status mq_lower_query(const tqp_table* t, const tqp_pred* preds, int32_t npr
         TQP_TRY(lower_expr(sum_expr, t->num_cols, &q->sum));
         q->has_sum = true;
         expr_cols(q->sum, cols);
+        TQP_TRY(check_numeric_cols(t, cols, "tqp_filter_shared sum_expr"));
         // the closed product form is required: try it with every column staged
         ScanGeom G;
         memset(&G, 0, sizeof(G));
@@ -321,7 +322,7 @@ void mq_pack(const tqp_table* t, const std::vector<MqQuery>& qs, std::vector<std
     std::vector<PackState> packs;
     for (int i = 0; i < static_cast<int>(qs.size()); ++i) {
         const MqQuery& q = qs[i];
-        if ((q.has_sum && !q.closed) || q.cols.size() > static_cast<size_t>(kMaxStaged)) {
+        if (q.alone || (q.has_sum && !q.closed) || q.cols.size() > static_cast<size_t>(kMaxStaged)) {
             singles->push_back(i);
             continue;
         }
@@ -431,6 +432,10 @@ static tqp_status shared_run(tqp_ctx* ctx, const tqp_table* t, const tqp_scan_qu
                              int32_t* launch_of, cudaStream_t st) {
     std::vector<MqQuery> qs(nq);
     for (int i = 0; i < nq; ++i) {
+        if (has_set_preds(t, q[i].preds, q[i].npreds)) {
+            qs[i].alone = true;
+            continue;
+        }
         TQP_TRY(mq_lower_query(t, q[i].preds, q[i].npreds, q[i].has_sum ? &q[i].sum_expr : nullptr, &qs[i]));
         qs[i].out.count = q[i].d_count;
         qs[i].out.sum = q[i].has_sum ? q[i].d_sum : nullptr;

@@ -556,6 +556,32 @@ static tqp_status run_scan_plan(tqp_ctx* ctx, const tqp_plan* p, const tqp_resul
     return TQP_OK;
 }
 
+// String columns feed IN / LIKE predicates only: no group key, expression or
+// join key may read one (fact columns first, then dimension columns).
+static tqp_status check_plan_numeric(const tqp_plan* p) {
+    const int F = p->fact->num_cols;
+    std::vector<int> fc, dc;
+    auto add = [&](int c) {
+        if (c < F) fc.push_back(c);
+        else dc.push_back(c - F);
+    };
+    for (int i = 0; i < p->ngc && i < TQP_MAX_GROUP_COLS; ++i) add(p->group_cols[i]);
+    auto add_expr = [&](const tqp_expr& e) {
+        for (int i = 0; i < e.n && i < TQP_MAX_EXPR; ++i)
+            if (e.op[i] == TQP_X_COL) add(static_cast<int>(e.v[i]));
+    };
+    for (int a = 0; a < p->naggs && a < TQP_MAX_AGGS; ++a)
+        if (p->aggs[a].fn != TQP_COUNT) add_expr(p->aggs[a].expr);
+    if (p->has_sum) add_expr(p->sum_expr);
+    if (p->dim) {
+        fc.push_back(p->fact_fk);
+        dc.push_back(p->dim_key);
+        TQP_TRY(check_table(p->dim, "plan.dim"));
+        TQP_TRY(check_numeric_cols(p->dim, dc, "plan (dimension)"));
+    }
+    return check_numeric_cols(p->fact, fc, "plan");
+}
+
 tqp_status run_plan_one(tqp_ctx* ctx, const tqp_plan* p, const tqp_result* r, cudaStream_t stream) {
     if (!p || !r) return fail(TQP_ERR_INVALID_ARG, "plan or result is NULL");
     TQP_TRY(check_table(p->fact, "plan.fact"));
@@ -563,7 +589,29 @@ tqp_status run_plan_one(tqp_ctx* ctx, const tqp_plan* p, const tqp_result* r, cu
     if (p->naggs < 0 || p->naggs > TQP_MAX_AGGS) return fail(TQP_ERR_INVALID_ARG, "naggs out of range");
     if (p->topk < 0) return fail(TQP_ERR_INVALID_ARG, "topk < 0");
     if (p->ngc + p->naggs > 0 && r->capacity_groups < 1) return fail(TQP_ERR_INVALID_ARG, "capacity_groups < 1");
+    TQP_TRY(check_plan_numeric(p));
     arena_reset(ctx);
+    // IN / LIKE / NOT LIKE on fact columns: one pre-pass appends a pass column to the fact table
+    // (column F); dimension columns, addressed from F on, move up by one
+    StrLowered SL;
+    TQP_TRY(str_prepass(ctx, p->fact, p->preds, p->npreds, stream, &SL));
+    if (SL.active) {
+        tqp_plan q = *p;
+        const int F = p->fact->num_cols;
+        q.fact = &SL.t;
+        q.npreds = SL.npreds;
+        for (int i = 0; i < SL.npreds; ++i) q.preds[i] = SL.preds[i];
+        auto shift = [F](tqp_expr& e) {
+            for (int i = 0; i < e.n && i < TQP_MAX_EXPR; ++i)
+                if (e.op[i] == TQP_X_COL && e.v[i] >= F) ++e.v[i];
+        };
+        for (int i = 0; i < q.ngc; ++i)
+            if (q.group_cols[i] >= F) ++q.group_cols[i];
+        for (int a2 = 0; a2 < q.naggs; ++a2) shift(q.aggs[a2].expr);
+        shift(q.sum_expr);
+        if (q.dim) return run_join_plan(ctx, &q, r, stream);
+        return run_scan_plan(ctx, &q, r, stream);
+    }
     if (p->dim) return run_join_plan(ctx, p, r, stream);
     return run_scan_plan(ctx, p, r, stream);
 }
@@ -641,6 +689,11 @@ extern "C" tqp_status tqp_dim_prepare(tqp_ctx* ctx, const tqp_table* dim, int32_
     *out = nullptr;
     TQP_TRY(check_table(dim, "dim"));
     if (key_col < 0 || key_col >= dim->num_cols) return fail(TQP_ERR_INVALID_ARG, "key_col out of range");
+    {
+        std::vector<int> kc{key_col};
+        for (int i = 0; i < ngc && group_cols && i < TQP_MAX_GROUP_COLS; ++i) kc.push_back(group_cols[i]);
+        TQP_TRY(check_numeric_cols(dim, kc, "tqp_dim_prepare"));
+    }
     if (ngc < 0 || ngc > TQP_MAX_GROUP_COLS || (ngc > 0 && !group_cols))
         return fail(TQP_ERR_INVALID_ARG, "bad group columns");
     for (int i = 0; i < ngc; ++i)

@@ -85,3 +85,18 @@ def test_torch_generator_matches_numpy():
     x = np.arange(1000, dtype=np.uint64) * np.uint64(0x9E3779B97F4A7C15)
     got = torch_gen.splitmix64(torch.from_numpy(x.view(np.int64).copy())).numpy().view(np.uint64)
     assert np.array_equal(got, datagen.splitmix64(x))
+
+
+def test_string_column_shape_padding_and_vocabulary():
+    s = datagen.string_column(5000, seed=9)
+    assert s.shape == (5000, datagen.STR_WIDTH) and s.dtype == np.uint8
+    vocab = set(datagen.string_vocab(9))
+    for row in s[:500]:
+        b = bytes(row)
+        body = b.split(b"\0", 1)[0]
+        assert b[len(body):] == b"\0" * (len(b) - len(body))  # right-padded with 0 only
+        words = body.split(b" ")
+        assert 1 <= len(words) <= 3 and all(w in vocab for w in words)
+    assert np.array_equal(datagen.string_column(100, seed=9, row0=50), datagen.string_column(150, seed=9)[50:])
+    cut = datagen.string_column(5000, seed=9, width=5)
+    assert np.array_equal(cut, s[:, :5])

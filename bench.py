@@ -635,6 +635,49 @@ def shared_scan_workload(tqp, torch, dev, local, table, n, reps):
     return out
 
 
+STR_ROWS = 20_000_000
+
+
+def string_case_inputs(n, seed=datagen.DEFAULT_SEED + 11):
+    """A 24-byte string column (1 to 3 seeded words, 0-padded) and a price column; the query keeps rows whose
+    string contains the first two letters of a vocabulary word and whose price is below 5,000,000."""
+    s = datagen.string_column(n, seed=seed)
+    price = datagen.fact_table(n, seed=seed, cols=["price"])["price"]
+    w = datagen.string_vocab(seed)[0][:2].decode()
+    preds = [(0, "like", f"%{w}%"), (1, "lt", 5_000_000)]
+    return s, price, preds
+
+
+def string_workload(tqp, torch, dev, local, reps, n=STR_ROWS):
+    """LIKE on a string column plus a numeric predicate, COUNT and SUM(price): the pre-pass over the strings,
+    then the staged filter over the pass column and the price; a 1M-row prefix checked against the oracle."""
+    import oracle
+    s, price, preds = string_case_inputs(n)
+    T = tqp.TableRef([torch.from_numpy(s).to(dev), torch.from_numpy(price).to(dev)])
+    ctx = tqp.Context(local, 256 << 20)
+    ctx.set_autotune(True)
+    stream = torch.cuda.current_stream()
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    sm = torch.zeros(1, dtype=torch.int64, device=dev)
+    expr = [("col", 1)]
+    fn = lambda: tqp.tqp_filter(ctx, T, preds, expr, sm, None, 0, cnt, stream)  # noqa: E731
+    ms = _time_launches(torch, fn, reps, stream=stream)
+    ctx.check(stream)
+    m = 1_000_000
+    Tm = tqp.TableRef([torch.from_numpy(s[:m]).to(dev), torch.from_numpy(price[:m]).to(dev)])
+    tqp.tqp_filter(ctx, Tm, preds, expr, sm, None, 0, cnt, stream)
+    ids, want_sum = oracle.filter_rows([s[:m], price[:m]], preds, expr)
+    same = int(cnt.item()) == len(ids) and int(sm.item()) == want_sum
+    ctx.close()
+    alg = n * (24 + 1 + 1 + 8)  # strings, pass byte written and read, price
+    return {"workload": f"{n // 1_000_000}M rows: 24-byte strings (1-3 seeded words, 0-padded) LIKE '{preds[0][2]}' "
+                        "AND price < 5,000,000; COUNT and SUM(price)",
+            "ms": ms, "rows_per_s": n / (ms / 1e3), "algorithmic_bytes": alg,
+            "achieved_gbs": alg / (ms / 1e3) / 1e9, "frac_of_measured_hbm": alg / (ms / 1e3) / 1e9 / measured_peaks()[0],
+            "kernels": "k_str_prepass (strings -> pass byte), k_filter (pass byte, price)",
+            "oracle_equal_1M_prefix": bool(same)}
+
+
 SERVE_FACT_ROWS = 600_000_000
 SERVE_DIM_ROWS = 15_000_000
 SERVE_POOL = 512  # result buffer sets, reused round-robin
@@ -921,6 +964,12 @@ def profile_case(args):
               for p in q6_windows(args.queries, datagen.DEFAULT_SEED + 7)]
         prepared = tqp.ScanQueries(qs)
         fn = lambda: tqp.tqp_filter_shared(ctx, T, prepared, st)  # noqa: E731
+    elif args.case == "strings":  # LIKE on a string column + a numeric predicate
+        s, price, preds = string_case_inputs(n)
+        T = tqp.TableRef([torch.from_numpy(s).to(dev), torch.from_numpy(price).to(dev)])
+        cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+        sm = torch.zeros(1, dtype=torch.int64, device=dev)
+        fn = lambda: tqp.tqp_filter(ctx, T, preds, [("col", 1)], sm, None, 0, cnt, st)  # noqa: E731
     else:  # the batched plan mix (512 plans by default)
         plans, results, keep, meta = batched_plans(tqp, torch, dev, n_plans=args.plans)
         batch = tqp.tqp_batch_create(ctx, plans, results)
@@ -954,7 +1003,7 @@ def main():
     ap.add_argument("--tuning", default="", help="profiling: force the scan launch shape, tile,stages,ctas_per_sm")
     ap.add_argument("--plans", type=int, default=BATCH_PLANS, help="profiling: plans of the batch case")
     ap.add_argument("--case", choices=["filter", "groupby", "join", "join_hashed", "pairs", "pairs_hashed", "batch",
-                                       "shared", "l2red"], default=None,
+                                       "shared", "strings", "l2red"], default=None,
                     help="profiling: run one operator (first call autotunes; --steps calls in NVTX range tqp_profile)")
     args = ap.parse_args()
     globals()["N_ROWS"] = args.rows
@@ -1062,6 +1111,7 @@ def main():
         ops = secondary_workloads(tqp, torch, dev, local, 20, cpu_seconds=min(args.cpu_seconds, 5.0))
         ops["batched_512"] = batched_workload(tqp, torch, dev, local, 20)
         ops["shared_scan_60M"] = shared_scan_workload(tqp, torch, dev, local, table, N_ROWS, 10)
+        ops["strings_like_20M"] = string_workload(tqp, torch, dev, local, 10)
         if not args.no_serving:
             ops["serving"], g600 = serving_workload(tqp, torch, dev, local, seconds=args.serve_seconds)
             if g600:

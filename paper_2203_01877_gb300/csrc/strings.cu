@@ -28,7 +28,11 @@ namespace tqp {
 constexpr int kStrThreads = 256;
 constexpr int kStrWarps = kStrThreads / kWarp;
 constexpr int kStrMaxWidth = 255;
-constexpr int kStrStageBytes = kWarp * 256;  // a warp's 32 strings (width <= 255, rounded)
+// LIKE program flags: the first / last segment is anchored to the string's
+// start / end; the pattern has no `%` (the one segment is the whole string);
+// the greedy matcher on the raw pattern instead (a segment over 32 bytes).
+constexpr int kLikeStart = 1, kLikeEnd = 2, kLikeExact = 4, kLikeGreedy = 8;
+constexpr int kLikeMaxSeg = 32;
 
 struct StrPred {
     const unsigned char* col;  // column data (device)
@@ -37,6 +41,9 @@ struct StrPred {
     int32_t op;                // TQP_IN, TQP_LIKE or TQP_NOT_LIKE
     int32_t off;               // byte offset of the values / pattern in the blob (8-aligned)
     int32_t count;             // IN: values; LIKE: pattern bytes
+    int32_t nseg;              // LIKE: segments between `%`s
+    int32_t flags;             // LIKE: kLike* flags
+    int32_t prog;              // LIKE: byte offset of the segment lengths, then 256 masks per segment
     int32_t pad;
 };
 
@@ -45,6 +52,8 @@ struct StrLaunch {
     unsigned char* out;        // n bytes
     int32_t npred;
     int32_t blob_bytes;
+    int32_t stage_bytes;       // per warp: 32 strings of the widest string column (16-byte multiple)
+    int32_t pad;
     StrPred p[TQP_MAX_PREDS];
     alignas(16) unsigned char blob[TQP_MAX_SET_BYTES];
 };
@@ -71,6 +80,51 @@ __device__ __forceinline__ bool like_greedy(const unsigned char* s, int n, const
     return pi == m;
 }
 
+// LIKE by segments: the pattern split at its `%`s into segments (`_` a
+// one-byte wildcard inside them), each with a table of 256 masks: bit j of
+// mask[c] is set when byte c may stand at the segment's position j.  An
+// anchored first / last segment must match at the string's start / end; the
+// segments between are found leftmost-first with the Shift-And recurrence
+// (D = ((D << 1) | 1) & mask[c] per string byte), and each search starts where
+// the previous segment's match ended (the leftmost choice leaves the most
+// room for the rest, so it finds a match whenever one exists).
+__device__ __forceinline__ bool seg_at(const unsigned char* s, int p, int len, const uint32_t* mk) {
+    for (int j = 0; j < len; ++j)
+        if (!((mk[s[p + j]] >> j) & 1u)) return false;
+    return true;
+}
+
+__device__ bool like_segments(const unsigned char* s, int n, const StrPred& q, const unsigned char* blob) {
+    const int32_t* lens = reinterpret_cast<const int32_t*>(blob + q.prog);
+    const uint32_t* masks = reinterpret_cast<const uint32_t*>(blob + q.prog + ((q.nseg * 4 + 15) / 16) * 16);
+    if (q.flags & kLikeExact) return n == lens[0] && seg_at(s, 0, lens[0], masks);
+    int pos = 0, first = 0, last = q.nseg;
+    if (q.flags & kLikeStart) {
+        if (lens[0] > n || !seg_at(s, 0, lens[0], masks)) return false;
+        pos = lens[0];
+        first = 1;
+    }
+    int limit = n;  // the middle segments must end by here
+    if (q.flags & kLikeEnd) {
+        last = q.nseg - 1;
+        limit = n - lens[last];
+        if (limit < pos || !seg_at(s, limit, lens[last], masks + 256 * last)) return false;
+    }
+    for (int k = first; k < last; ++k) {
+        const uint32_t* mk = masks + 256 * k;
+        const uint32_t hit = 1u << (lens[k] - 1);
+        uint32_t D = 0;
+        int i = pos;
+        for (; i < limit; ++i) {
+            D = ((D << 1) | 1u) & mk[s[i]];
+            if (D & hit) break;
+        }
+        if (i >= limit) return false;
+        pos = i + 1;
+    }
+    return true;
+}
+
 // Bytewise comparison of two m-byte strings.
 __device__ __forceinline__ int str_cmp(const unsigned char* a, const unsigned char* b, int m) {
     for (int i = 0; i < m; ++i)
@@ -85,7 +139,7 @@ __global__ void __launch_bounds__(kStrThreads) k_str_prepass(const __grid_consta
     for (int i = threadIdx.x; i < L.blob_bytes; i += blockDim.x) blob[i] = L.blob[i];
     __syncthreads();
     const int lane = threadIdx.x % kWarp, w = threadIdx.x / kWarp;
-    unsigned char* my = stage + w * kStrStageBytes;
+    unsigned char* my = stage + w * L.stage_bytes;
     const long long groups = (L.n + kWarp - 1) / kWarp;
     for (long long g = static_cast<long long>(blockIdx.x) * kStrWarps + w; g < groups;
          g += static_cast<long long>(gridDim.x) * kStrWarps) {
@@ -119,7 +173,8 @@ __global__ void __launch_bounds__(kStrThreads) k_str_prepass(const __grid_consta
                     } else {
                         int n = 0;
                         while (n < m && s[n]) ++n;
-                        const bool hit = like_greedy(s, n, blob + q.off, q.count);
+                        const bool hit = (q.flags & kLikeGreedy) ? like_greedy(s, n, blob + q.off, q.count)
+                                                                 : like_segments(s, n, q, blob);
                         pass = q.op == TQP_LIKE ? hit : !hit;
                     }
                 }
@@ -164,6 +219,7 @@ tqp_status str_prepass(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* preds, 
     std::vector<int> cols;
     int nkeep = 0;
     size_t used = 0;
+    int maxw = 0;
     for (int i = 0; i < npreds; ++i) {
         const tqp_pred& p = preds[i];
         if (p.col < 0 || p.col >= t->num_cols)
@@ -188,6 +244,7 @@ tqp_status str_prepass(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* preds, 
         q.col = static_cast<const unsigned char*>(c.data);
         q.type = c.type;
         q.width = str ? c.scale : 0;
+        maxw = std::max(maxw, q.width);
         q.op = p.op;
         q.off = static_cast<int32_t>(used);
         const unsigned char* src = reinterpret_cast<const unsigned char*>(static_cast<uintptr_t>(p.lo));
@@ -216,7 +273,44 @@ tqp_status str_prepass(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* preds, 
         if (used + data.size() > static_cast<size_t>(TQP_MAX_SET_BYTES))
             return fail(TQP_ERR_UNSUPPORTED, "IN / LIKE values take more than %d bytes", TQP_MAX_SET_BYTES);
         if (!data.empty()) memcpy(L->blob + used, data.data(), data.size());
-        used = (used + data.size() + 7) / 8 * 8;
+        used = (used + data.size() + 15) / 16 * 16;
+        if (p.op != TQP_IN) {  // the segment program, when it fits (else the greedy matcher)
+            std::vector<std::vector<unsigned char>> segs;
+            std::vector<unsigned char> cur;
+            bool any_pct = false;
+            for (unsigned char ch : data) {
+                if (ch == '%') {
+                    any_pct = true;
+                    if (!cur.empty()) segs.push_back(cur);
+                    cur.clear();
+                } else {
+                    cur.push_back(ch);
+                }
+            }
+            if (!cur.empty() || !any_pct) segs.push_back(cur);
+            q.nseg = static_cast<int32_t>(segs.size());
+            q.flags = any_pct ? 0 : kLikeExact;
+            if (any_pct && data.front() != '%') q.flags |= kLikeStart;
+            if (any_pct && data.back() != '%') q.flags |= kLikeEnd;
+            bool fits = true;
+            for (const auto& g : segs) fits = fits && g.size() <= static_cast<size_t>(kLikeMaxSeg);
+            const size_t hdr = (segs.size() * 4 + 15) / 16 * 16;
+            const size_t prog_bytes = hdr + segs.size() * 256 * 4;
+            if (!fits || used + prog_bytes > static_cast<size_t>(TQP_MAX_SET_BYTES)) {
+                q.flags = kLikeGreedy;
+            } else {
+                q.prog = static_cast<int32_t>(used);
+                int32_t* lens = reinterpret_cast<int32_t*>(L->blob + used);
+                uint32_t* masks = reinterpret_cast<uint32_t*>(L->blob + used + hdr);
+                for (size_t k = 0; k < segs.size(); ++k) {
+                    lens[k] = static_cast<int32_t>(segs[k].size());
+                    for (size_t j = 0; j < segs[k].size(); ++j)
+                        for (int c = 0; c < 256; ++c)
+                            if (segs[k][j] == '_' || segs[k][j] == c) masks[k * 256 + c] |= 1u << j;
+                }
+                used += prog_bytes;
+            }
+        }
         cols.push_back(p.col);
     }
     TQP_TRY(check_device_cols(t, cols, "IN / LIKE"));
@@ -232,12 +326,17 @@ tqp_status str_prepass(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* preds, 
         L->n = n;
         L->out = pass;
         L->blob_bytes = static_cast<int32_t>(used);
+        L->stage_bytes = (kWarp * maxw + 15) / 16 * 16;
         static SmemFlags attr;
         TQP_TRY(allow_smem(ctx, reinterpret_cast<const void*>(k_str_prepass), attr));
-        const size_t smem = (used + 15) / 16 * 16 + static_cast<size_t>(kStrWarps) * kStrStageBytes;
+        const size_t smem = (used + 15) / 16 * 16 + static_cast<size_t>(kStrWarps) * L->stage_bytes;
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_str_prepass, kStrThreads, smem) != cudaSuccess ||
+            occ < 1)
+            occ = 1;
         const long long groups = (n + kWarp - 1) / kWarp;
         const long long want = (groups + kStrWarps - 1) / kStrWarps;
-        const int grid = static_cast<int>(std::min<long long>(want, static_cast<long long>(ctx->num_sms) * 2));
+        const int grid = static_cast<int>(std::min<long long>(want, static_cast<long long>(ctx->num_sms) * occ));
         k_str_prepass<<<grid, kStrThreads, smem, st>>>(*L);
         TQP_CUDA(cudaGetLastError());
     }

@@ -183,3 +183,28 @@ def test_invalid_string_uses(ctx):
     assert e.value.status == tqp.ERR_INVALID_ARG
     torch.cuda.synchronize()
     assert int(cnt.item()) == -7
+
+
+@pytest.mark.parametrize("width,seglen", [(8, 0), (64, 40)])
+def test_like_random_patterns(ctx, width, seglen):
+    """Random strings and patterns over 'ab%_' (the segment program), and patterns with a 40-byte
+    segment (the greedy matcher), against the oracle."""
+    rng = np.random.default_rng(width)
+    n = 20_000
+    alpha = np.frombuffer(b"ab%_", np.uint8)
+    vals = [bytes(alpha[rng.integers(0, 4, int(rng.integers(0, width + 1)))]) for _ in range(n)]
+    if seglen:
+        vals = [b"a" * seglen + v[: width - seglen] if i % 3 == 0 else v for i, v in enumerate(vals)]
+    s = oracle.pad_strings(vals, width)
+    v = rng.integers(0, 1000, n).astype(np.int64)
+    cols = [s, v]
+    for _ in range(25):
+        m = int(rng.integers(0, 7))
+        pat = bytes(alpha[rng.integers(0, 4, m)])
+        if seglen:
+            pat = b"%" + b"a" * seglen + pat
+        for op in ("like", "not_like"):
+            preds = [(0, op, pat)]
+            want_ids, want_sum = oracle.filter_rows(cols, preds, [("col", 1)])
+            ids, sm = run_filter(ctx, cols, preds, [("col", 1)])
+            assert np.array_equal(ids, want_ids) and sm == want_sum, (op, pat)

@@ -884,6 +884,48 @@ def serving_workload(tqp, torch, dev, local, seconds=10.0, rate=2000.0,
     }, g600
 
 
+def scan_ceiling(tqp, torch, ctx, table, shape, reps=10, stream=None):
+    """Mean ms of tqp_measure_scan_rate (the staged engine with a read-only body) at `shape`, over a burst
+    of `reps` back-to-back calls (the host enqueues ahead, so its per-call work is not in the time)."""
+    out = torch.zeros(1, dtype=torch.int64, device="cuda")
+    fn = lambda: tqp.tqp_measure_scan_rate(ctx, table, *shape, out, stream)  # noqa: E731
+    for _ in range(3):
+        fn()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def engine_case(args):
+    """The staged engine's streaming rate on the headline's predicate columns (date i32, discount i64,
+    quantity i32: 16 B/row) for every launch shape: one JSON line per shape."""
+    import torch
+    import paper_2203_01877_gb300 as tqp
+    host = gen_host(0)
+    cols = [torch.from_numpy(a).cuda() for a in host[:3]]
+    T = tqp.TableRef(cols)
+    ctx = tqp.Context(0, 64 << 20)
+    bytes_ = sum(c.numel() * c.element_size() for c in cols)
+    for tile in (1024, 2048, 4096, 8192):
+        for stages in (2, 3, 4):
+            for cps in (1, 2):
+                try:
+                    ms = scan_ceiling(tqp, torch, ctx, T, (tile, stages, cps))
+                except tqp.TqpError:
+                    continue
+                print(json.dumps({"case": "engine", "rows": N_ROWS, "bytes": bytes_, "tile_rows": tile,
+                                  "stages": stages, "ctas_per_sm": cps, "ms": ms,
+                                  "gbs": bytes_ / (ms / 1e3) / 1e9}), flush=True)
+    ctx.close()
+    return 0
+
+
 def l2_red_case(args):
     """The reduction-rate roofline of the joined aggregation: G reductions/s of random 8-byte L2 reductions
     (tqp_measure_l2_red) over table sizes, reductions per row and occupancy; one JSON line per setting."""
@@ -1003,7 +1045,7 @@ def main():
     ap.add_argument("--tuning", default="", help="profiling: force the scan launch shape, tile,stages,ctas_per_sm")
     ap.add_argument("--plans", type=int, default=BATCH_PLANS, help="profiling: plans of the batch case")
     ap.add_argument("--case", choices=["filter", "groupby", "join", "join_hashed", "pairs", "pairs_hashed", "batch",
-                                       "shared", "strings", "l2red"], default=None,
+                                       "shared", "strings", "l2red", "engine"], default=None,
                     help="profiling: run one operator (first call autotunes; --steps calls in NVTX range tqp_profile)")
     args = ap.parse_args()
     globals()["N_ROWS"] = args.rows
@@ -1011,6 +1053,8 @@ def main():
         return run_reference(args)
     if args.case == "l2red":
         return l2_red_case(args)
+    if args.case == "engine":
+        return engine_case(args)
     if args.case:
         return profile_case(args)
 
@@ -1070,6 +1114,12 @@ def main():
         ctx.set_variant(v)
         variant_ms[name] = _time_launches(torch, step, 20, stream=stream)
     ctx.set_variant(-1)
+    ctx.check(stream)
+    # the staged engine's own ceiling on the staged (predicate) columns: a read-only body, best shape
+    ceil_table = tqp.TableRef(cols[:3])
+    ceil = min((scan_ceiling(tqp, torch, ctx, ceil_table, sh, 10, stream), sh)
+               for sh in ((2048, 3, 2), (2048, 2, 2), (4096, 2, 1)))
+    staged_bytes = sum(c.numel() * c.element_size() for c in cols[:3])
     ctx.check(stream)
     if world > 1:
         tt = torch.tensor([total_ms], device=dev)
@@ -1152,6 +1202,11 @@ def main():
                          "kernel": "k_filter_direct" if variant_ms["direct"] < variant_ms["staged_scan"] else "k_filter",
                          "variant_call_ms": variant_ms,
                          "algorithmic_bytes_per_launch": alg, "launch_ms": launch_ms,
+                         "engine_ceiling": {"what": "tqp_measure_scan_rate: the staged engine over the three "
+                                                    "predicate columns with a read-only body",
+                                            "staged_bytes": staged_bytes, "ms": ceil[0],
+                                            "gbs": staged_bytes / (ceil[0] / 1e3) / 1e9,
+                                            "shape": list(ceil[1])},
                          "traffic": ncu_traffic()},
             "cpu_baseline": cpu,
             "e2e": {"value": N_ROWS / e2e_s, "unit": "rows/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

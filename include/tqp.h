@@ -5,9 +5,9 @@
  *
  * Data model (paper Section 4.1): a table is a set of equally long columns,
  * one dense array per column, rows identified by position ("virtual ids").
- * Numeric columns only: int32, int64 and uint8.  Decimals are int64 fixed
- * point (value x 10^scale) so every sum is an exact integer; dates are int32
- * day numbers.
+ * Numeric columns (int32, int64, uint8) and string columns (n x m bytes, for
+ * IN / LIKE predicates).  Decimals are int64 fixed point (value x 10^scale) so
+ * every sum is an exact integer; dates are int32 day numbers.
  *
  * Conventions for every entry point
  *   - Pointers named d_* and every column's `data` are DEVICE pointers on the
@@ -565,6 +565,21 @@ TQP_API tqp_status tqp_server_drain(tqp_server* s, double timeout_s);
 TQP_API tqp_status tqp_server_destroy(tqp_server* s);
 
 /* ---- measurement --------------------------------------------------------- */
+
+/*
+ * tqp_measure_scan_rate -- the ceiling of the staged scans on given columns.
+ * (The paper has no counterpart: a measurement entry point.)  Streams every
+ * column of t (at most 8, numeric, device memory) through the staged scan
+ * engine with the launch shape tile_rows x stages at ctas_per_sm CTAs per SM,
+ * with a body that only reads each staged 16-byte word once (their checksum
+ * is added to *d_out, caller-owned device memory).  Time the call with events
+ * on `stream`; bytes moved = rows x the columns' element sizes.  Errors:
+ * TQP_ERR_INVALID_ARG (shape outside tqp_ctx_set_tuning's ranges, more than 8
+ * or string columns, host columns), TQP_ERR_UNSUPPORTED (the shape does not
+ * fit shared memory), TQP_ERR_CUDA.
+ */
+TQP_API tqp_status tqp_measure_scan_rate(tqp_ctx* ctx, const tqp_table* t, int32_t tile_rows, int32_t stages,
+                                         int32_t ctas_per_sm, unsigned long long* d_out, void* stream);
 
 /*
  * tqp_measure_l2_red -- the reduction-rate roofline of the joined

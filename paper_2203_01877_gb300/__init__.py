@@ -128,6 +128,7 @@ _SIGS = {
     "tqp_server_drain": (C.c_int, [_P, C.c_double]),
     "tqp_server_destroy": (C.c_int, [_P]),
     "tqp_measure_l2_red": (C.c_int, [C.c_int, _P, C.c_int64, C.c_int64, C.c_int32, C.c_int32, C.c_int32, _P]),
+    "tqp_measure_scan_rate": (C.c_int, [_P, C.POINTER(Table), C.c_int32, C.c_int32, C.c_int32, _P, _P]),
 }
 
 
@@ -641,3 +642,11 @@ def tqp_measure_l2_red(device: int, d_table, rows: int, adds_per_row: int = 2, b
     """Random 8-byte L2 reductions into d_table (an int64 CUDA tensor): the joined aggregation's roofline."""
     _check(lib().tqp_measure_l2_red(int(device), _ptr(d_table), d_table.numel(), int(rows), int(adds_per_row),
                                     int(blocks_per_sm), int(threads), _stream(stream)))
+
+
+def tqp_measure_scan_rate(ctx: Context, table: TableRef, tile_rows: int, stages: int, ctas_per_sm: int, d_out,
+                          stream=None):
+    """The staged scan engine over every column of `table` with a body that only reads the stages: the
+    ceiling of the scans on those columns at that launch shape (see include/tqp.h)."""
+    _check(lib().tqp_measure_scan_rate(ctx.h, table.ref(), int(tile_rows), int(stages), int(ctas_per_sm),
+                                       _ptr(d_out), _stream(stream)))

@@ -64,7 +64,7 @@ typedef enum {
     TQP_ERR_UNSUPPORTED = 2,   /* valid request outside what the kernels implement */
     TQP_ERR_OUT_OF_MEMORY = 3, /* scratch arena too small (message says how much is needed) */
     TQP_ERR_CAPACITY = 4,      /* an output or hash table was too small; counts still exact */
-    TQP_ERR_OVERFLOW = 5,      /* reserved: int64 overflow (inputs are required not to overflow) */
+    TQP_ERR_OVERFLOW = 5,      /* reserved: never returned (see the expression note below) */
     TQP_ERR_TIMEOUT = 6,       /* a bounded device-side wait expired; results are invalid */
     TQP_ERR_CUDA = 7           /* a CUDA runtime call failed (message has the CUDA error) */
 } tqp_status;
@@ -135,7 +135,10 @@ typedef struct {
  * expression tree): a postfix program of at most 8 tokens over int64, stack
  * depth at most 4.  TQP_X_COL pushes column v (for plans: fact columns first,
  * then dimension columns), TQP_X_CONST pushes v, ADD/SUB/MUL pop b then a and
- * push a op b.  Results must not overflow int64. */
+ * push a op b.  Results must not overflow int64: past that precondition the
+ * library does not detect overflow; its sums, counts and products wrap
+ * modulo 2^64 (two's complement), so a SUM is then the exact sum reduced
+ * modulo 2^64 (an AVG of it is meaningless). */
 typedef enum { TQP_X_COL = 0, TQP_X_CONST, TQP_X_ADD, TQP_X_SUB, TQP_X_MUL } tqp_xop;
 
 typedef struct {

@@ -172,7 +172,20 @@ __global__ void __launch_bounds__(kStrThreads) k_str_prepass(const __grid_consta
                         pass = lo < q.count && str_cmp(v + lo * m, s, m) == 0;
                     } else {
                         int n = 0;
-                        while (n < m && s[n]) ++n;
+                        if ((m & 3) == 0) {  // four bytes at a time: the first zero byte of a word
+                            const uint32_t* sw = reinterpret_cast<const uint32_t*>(s);
+                            n = m;
+                            for (int i = 0; i < m / 4; ++i) {
+                                const uint32_t x = sw[i];
+                                const uint32_t z = (x - 0x01010101u) & ~x & 0x80808080u;  // lowest set bit: first zero byte
+                                if (z) {
+                                    n = 4 * i + (__ffs(z) - 1) / 8;
+                                    break;
+                                }
+                            }
+                        } else {
+                            while (n < m && s[n]) ++n;
+                        }
                         const bool hit = (q.flags & kLikeGreedy) ? like_greedy(s, n, blob + q.off, q.count)
                                                                  : like_segments(s, n, q, blob);
                         pass = q.op == TQP_LIKE ? hit : !hit;

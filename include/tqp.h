@@ -371,10 +371,12 @@ TQP_API tqp_status tqp_filter_noalloc(int device, const tqp_table* t,
  * Packing: queries are packed, in order and first fit, into launches of at
  * most 32 queries, 8 distinct columns and 2 distinct sum expressions whose
  * lookup tables fit the kernel's shared memory (per condition column one
- * table of the value intervals cut by the queries' range bounds).  A query
- * whose sum expression is not a product of two affine factors (x, x*k, x+k,
- * x*y, x*(k-y), ...) or that reads more than 8 columns runs alone through
- * tqp_filter's scan, and so does every query of a launch that would hold
+ * table of the value intervals cut by the queries' range bounds and by their
+ * TQP_IN values, each value v the interval [v, v+1)).  A query whose sum
+ * expression is not a product of two affine factors (x, x*k, x+k, x*y,
+ * x*(k-y), ...), that reads more than 8 columns, or that has a predicate on a
+ * string column, runs alone through tqp_filter's scan (with its pre-pass),
+ * and so does every query of a launch that would hold
  * fewer than 3 queries (that scan reads the summed columns only at passing
  * rows, which is faster for one or two queries).  launch_of (host array of
  * nq, may be NULL) receives each query's launch index, or -1 for one that ran
@@ -382,7 +384,9 @@ TQP_API tqp_status tqp_filter_noalloc(int device, const tqp_table* t,
  *
  * Errors: TQP_ERR_INVALID_ARG (nq < 0, NULL queries with nq > 0, a NULL
  * d_count, has_sum without d_sum or d_sum without has_sum, a predicate or
- * expression tqp_filter rejects; nothing is launched), TQP_ERR_OUT_OF_MEMORY
+ * expression tqp_filter rejects; nothing is launched), TQP_ERR_UNSUPPORTED
+ * (IN values over TQP_MAX_SET_BYTES, as tqp_filter; nothing is launched),
+ * TQP_ERR_OUT_OF_MEMORY
  * (the context's arena), TQP_ERR_CUDA.  Column rules as for tqp_filter's
  * predicate columns: every column a query reads must be in device memory.
  * Each launch carries its lookup tables in its kernel parameters; the call

@@ -201,8 +201,10 @@ struct StrLowered {
     StrLowered& operator=(const StrLowered&) = delete;
 };
 bool has_set_preds(const tqp_table* t, const tqp_pred* preds, int32_t npreds);
+// With check_only, only the host checks run: out->preds receives the other
+// predicates and nothing is allocated or launched.
 tqp_status str_prepass(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* preds, int32_t npreds, cudaStream_t st,
-                       StrLowered* out);
+                       StrLowered* out, bool check_only = false);
 // Columns read by arithmetic, keys or comparisons must be numeric (a string
 // column feeds IN / LIKE predicates only).
 tqp_status check_numeric_cols(const tqp_table* t, const std::vector<int>& cols, const char* what);

@@ -41,12 +41,48 @@ static bool same_expr(const DExpr& a, const DExpr& b) {
     return true;
 }
 
+// Whether a query can share a scan: numeric columns only, and no LIKE.
+static bool mq_shareable(const tqp_table* t, const tqp_pred* preds, int32_t npreds) {
+    for (int i = 0; i < npreds && i < TQP_MAX_PREDS && preds; ++i) {
+        if (preds[i].op == TQP_LIKE || preds[i].op == TQP_NOT_LIKE) return false;
+        if (preds[i].col >= 0 && preds[i].col < t->num_cols && t->cols[preds[i].col].type == TQP_CHAR) return false;
+    }
+    return true;
+}
+
 tqp_status mq_lower_query(const tqp_table* t, const tqp_pred* preds, int32_t npreds, const tqp_expr* sum_expr,
                           MqQuery* q) {
     *q = MqQuery();
-    TQP_TRY(lower_preds(t, preds, npreds, q->cond, &q->ncond));
+    // IN lists on numeric columns become membership tests of the column tables; the rest are ranges
+    if (npreds < 0 || npreds > TQP_MAX_PREDS)
+        return fail(TQP_ERR_INVALID_ARG, "npreds %d outside [0, %d]", npreds, TQP_MAX_PREDS);
+    if (npreds > 0 && !preds) return fail(TQP_ERR_INVALID_ARG, "preds is NULL");
+    tqp_pred ranges[TQP_MAX_PREDS];
+    int nr = 0;
+    size_t used = 0;  // the value bytes the single-query pre-pass would hold (same budget)
+    for (int i = 0; i < npreds; ++i) {
+        const tqp_pred& p = preds[i];
+        if (p.op != TQP_IN) {
+            ranges[nr++] = p;
+            continue;
+        }
+        if (p.col < 0 || p.col >= t->num_cols)
+            return fail(TQP_ERR_INVALID_ARG, "predicate %d: column %d out of range", i, p.col);
+        if (p.hi < 0 || (p.hi > 0 && p.lo == 0))
+            return fail(TQP_ERR_INVALID_ARG, "predicate %d: bad value list", i);
+        const int64_t* v = reinterpret_cast<const int64_t*>(static_cast<uintptr_t>(p.lo));
+        std::vector<int64_t> vals(v, v + p.hi);
+        std::sort(vals.begin(), vals.end());
+        vals.erase(std::unique(vals.begin(), vals.end()), vals.end());
+        if (used + vals.size() * 8 > static_cast<size_t>(TQP_MAX_SET_BYTES))
+            return fail(TQP_ERR_UNSUPPORTED, "IN / LIKE values take more than %d bytes", TQP_MAX_SET_BYTES);
+        used = (used + vals.size() * 8 + 15) / 16 * 16;
+        q->ins.push_back({p.col, vals});
+    }
+    TQP_TRY(lower_preds(t, ranges, nr, q->cond, &q->ncond));
     std::vector<int> cols;
     for (int i = 0; i < q->ncond; ++i) cols.push_back(q->cond[i].col);
+    for (const auto& in : q->ins) cols.push_back(in.first);
     if (sum_expr) {
         TQP_TRY(lower_expr(sum_expr, t->num_cols, &q->sum));
         q->has_sum = true;
@@ -77,6 +113,17 @@ tqp_status mq_lower_query(const tqp_table* t, const tqp_pred* preds, int32_t npr
             if (b > tmin && b <= tmax) q->bps.push_back({cd.col, b});
         }
     }
+    for (const auto& in : q->ins) {  // each value v is the interval [v, v + 1)
+        int64_t tmin, tmax;
+        type_range(t->cols[in.first].type, &tmin, &tmax);
+        for (int64_t v : in.second)
+            for (uint64_t e : {static_cast<uint64_t>(v), static_cast<uint64_t>(v) + 1u}) {
+                const int64_t b = static_cast<int64_t>(e);
+                if (b > tmin && b <= tmax) q->bps.push_back({in.first, b});
+            }
+    }
+    std::sort(q->bps.begin(), q->bps.end());
+    q->bps.erase(std::unique(q->bps.begin(), q->bps.end()), q->bps.end());
     return TQP_OK;
 }
 
@@ -93,8 +140,10 @@ static bool mq_tables(const tqp_table* t, const std::vector<MqQuery>& qs, const 
     words->clear();
     breaks->clear();
     std::vector<int> ccols;
-    for (int m : members)
+    for (int m : members) {
         for (int i = 0; i < qs[m].ncond; ++i) ccols.push_back(qs[m].cond[i].col);
+        for (const auto& in : qs[m].ins) ccols.push_back(in.first);
+    }
     std::sort(ccols.begin(), ccols.end());
     ccols.erase(std::unique(ccols.begin(), ccols.end()), ccols.end());
 
@@ -111,17 +160,10 @@ static bool mq_tables(const tqp_table* t, const std::vector<MqQuery>& qs, const 
         int64_t tmin, tmax;
         type_range(ct.type, &tmin, &tmax);
         for (int m : members)
-            for (int i = 0; i < qs[m].ncond; ++i) {
-                const Cond& cd = qs[m].cond[i];
-                if (cd.col != c) continue;
-                const uint64_t ends[2] = {static_cast<uint64_t>(cd.lo), static_cast<uint64_t>(cd.lo) + cd.span + 1u};
-                for (uint64_t e : ends) {
-                    // a breakpoint at or below the smallest value, or above the
-                    // largest, separates no two values of the column
-                    const int64_t b = static_cast<int64_t>(e);
-                    if (b > tmin && b <= tmax) ct.B.push_back(b);
-                }
-            }
+            for (const auto& b : qs[m].bps)
+                // (only breakpoints inside the column's range: one at or below the
+                // smallest value, or above the largest, separates no two values)
+                if (b.first == c) ct.B.push_back(b.second);
         std::sort(ct.B.begin(), ct.B.end());
         ct.B.erase(std::unique(ct.B.begin(), ct.B.end()), ct.B.end());
         auto mask_at = [&](int64_t x) {
@@ -131,6 +173,8 @@ static bool mq_tables(const tqp_table* t, const std::vector<MqQuery>& qs, const 
                 bool ok = true;
                 for (int i = 0; i < q.ncond; ++i)
                     if (q.cond[i].col == c && !cond_pass(q.cond[i], x)) ok = false;
+                for (const auto& in : q.ins)
+                    if (in.first == c && !std::binary_search(in.second.begin(), in.second.end(), x)) ok = false;
                 if (ok) mk |= 1u << l;
             }
             return mk;
@@ -257,11 +301,8 @@ static bool pack_try(const PackState& g, const MqQuery& q) {
             sz.push_back({b.first, 0, b.second, b.second});
             z = &sz.back();
         }
-        bool dup = old && std::binary_search(old->begin(), old->end(), b.second);
-        for (const auto& b2 : q.bps)  // an equal breakpoint earlier in q's own list
-            if (&b2 == &b) break;
-            else if (b2.first == b.first && b2.second == b.second) dup = true;
-        if (!dup) ++z->k;
+        // (q's own breakpoints are distinct: sorted and deduplicated when lowered)
+        if (!(old && std::binary_search(old->begin(), old->end(), b.second))) ++z->k;
         z->lo = std::min(z->lo, b.second);
         z->hi = std::max(z->hi, b.second);
     }
@@ -428,11 +469,30 @@ static tqp_status mq_zero(const MqOut& o, cudaStream_t st) {
     return TQP_OK;
 }
 
+// The host checks of the single-query scan (its pre-pass, predicates and sum),
+// so that a bad query stops the call before anything is launched.
+static tqp_status check_alone(tqp_ctx* ctx, const tqp_table* t, const tqp_scan_query& q) {
+    StrLowered SL;
+    TQP_TRY(str_prepass(ctx, t, q.preds, q.npreds, nullptr, &SL, true));
+    Cond cond[TQP_MAX_PREDS];
+    int ncond = 0;
+    TQP_TRY(lower_preds(t, SL.preds, SL.npreds, cond, &ncond));
+    if (q.has_sum) {
+        DExpr e;
+        TQP_TRY(lower_expr(&q.sum_expr, t->num_cols, &e));
+        std::vector<int> c;
+        expr_cols(e, c);
+        TQP_TRY(check_numeric_cols(t, c, "tqp_filter_shared sum_expr"));
+    }
+    return TQP_OK;
+}
+
 static tqp_status shared_run(tqp_ctx* ctx, const tqp_table* t, const tqp_scan_query* q, int32_t nq,
                              int32_t* launch_of, cudaStream_t st) {
     std::vector<MqQuery> qs(nq);
     for (int i = 0; i < nq; ++i) {
-        if (has_set_preds(t, q[i].preds, q[i].npreds)) {
+        if (!mq_shareable(t, q[i].preds, q[i].npreds)) {
+            TQP_TRY(check_alone(ctx, t, q[i]));
             qs[i].alone = true;
             continue;
         }

@@ -439,7 +439,8 @@ struct MqQuery {
     std::vector<int> cols; // condition and expression columns, ascending
     std::vector<int> ecols; // expression columns
     std::vector<std::pair<int, int64_t>> bps;  // (column, breakpoint inside the column type's range)
-    bool alone = false;    // IN / LIKE predicates: runs through the single-query scan (and its pre-pass)
+    std::vector<std::pair<int, std::vector<int64_t>>> ins;  // numeric IN lists: (column, sorted values)
+    bool alone = false;    // LIKE or string columns: runs through the single-query scan (and its pre-pass)
 };
 
 tqp_status mq_lower_query(const tqp_table* t, const tqp_pred* preds, int32_t npreds, const tqp_expr* sum_expr,

@@ -218,7 +218,7 @@ bool has_set_preds(const tqp_table* t, const tqp_pred* preds, int32_t npreds) {
 }
 
 tqp_status str_prepass(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* preds, int32_t npreds, cudaStream_t st,
-                       StrLowered* out) {
+                       StrLowered* out, bool check_only) {
     out->active = false;
     out->t = *t;
     out->npreds = npreds;
@@ -330,6 +330,10 @@ tqp_status str_prepass(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* preds, 
     if (t->num_cols + 1 > TQP_MAX_COLS)
         return fail(TQP_ERR_UNSUPPORTED, "IN / LIKE need a free column slot (the table has %d of %d)", t->num_cols,
                     TQP_MAX_COLS);
+    if (check_only) {  // the other predicates, as the scan will take them; nothing allocated or launched
+        out->npreds = nkeep;
+        return TQP_OK;
+    }
     // the pass column, then the table with it appended and the predicate on it
     const long long n = t->num_rows;
     unsigned char* pass = nullptr;

@@ -164,6 +164,31 @@ def test_same_results_as_single_query_filter(ctx):
         assert (int(cnt.item()), int(s.item())) == got[i]
 
 
+def test_numeric_in_lists_share_the_scan(ctx):
+    """IN lists on numeric columns (dense, sparse, empty, duplicated, outside
+    the column type's range, int64 extremes) pack with range queries (two sum
+    expressions: one launch)."""
+    cols = _table(1_200_007, 109)
+    rng = np.random.default_rng(14)
+    qs = []
+    for k in range(12):
+        d0 = int(rng.integers(0, 2000))
+        disc = sorted(int(x) for x in rng.choice(11, 3, replace=False))
+        qty = [int(x) for x in rng.integers(1, 51, 6)]
+        qs.append(([(0, "ge", d0), (0, "lt", d0 + 365), (1, "in", disc), (2, "in", qty)], REVENUE))
+    qs += [
+        ([(6, "in", [int(x) for x in rng.integers(0, 100_000, 200)])], REVENUE),   # sparse: a searched table
+        ([(2, "in", list(range(10, 30)) + [12, 12, 29])], None),                   # dense, with repeats
+        ([(1, "in", [])], REVENUE),                                               # never true
+        ([(2, "in", [-(1 << 40), 1 << 40, 7])], [("col", 2)]),                     # outside int32, and 7
+        ([(3, "in", [I64_MIN, I64_MAX, int(cols[3][5]), int(cols[3][99])])], REVENUE),
+        ([(4, "in", [0, 2]), (5, "ne", 1), (0, "in", [0, 1, 2556])], None),
+    ]
+    got, launch_of = run_shared(ctx, cols, qs)
+    assert set(launch_of) == {0}
+    check(cols, qs, got)
+
+
 def test_invalid_arguments_launch_nothing(ctx):
     import torch
     import paper_2203_01877_gb300 as tqp
@@ -180,5 +205,12 @@ def test_invalid_arguments_launch_nothing(ctx):
         with pytest.raises(tqp.TqpError) as e:
             tqp.tqp_filter_shared(ctx, T, [([(0, "lt", 5)], None, cnt, None)] + bad)
         assert e.value.status == tqp.ERR_INVALID_ARG
+    # a bad query after shareable ones: found before the shared launch
+    ok = [([(0, "lt", 100 * k)], REVENUE, cnt, s) for k in range(1, 5)]
+    for bad, status in (([(1, "like", "1%")], tqp.ERR_INVALID_ARG),            # LIKE on a number
+                        ([(2, "in", list(range(4000)))], tqp.ERR_UNSUPPORTED)):  # more than the set budget
+        with pytest.raises(tqp.TqpError) as e:
+            tqp.tqp_filter_shared(ctx, T, ok + [(bad, None, cnt, None)])
+        assert e.value.status == status, bad
     torch.cuda.synchronize()
     assert int(cnt.item()) == -7 and int(s.item()) == -7

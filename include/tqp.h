@@ -43,8 +43,10 @@
 #ifndef TQP_H
 #define TQP_H
 
+#ifndef __CUDACC_RTC__
 #include <stddef.h>
 #include <stdint.h>
+#endif
 
 #ifdef __cplusplus
 extern "C" {
@@ -206,6 +208,29 @@ TQP_API tqp_status tqp_ctx_set_tuning(tqp_ctx* ctx, int32_t tile_rows, int32_t s
  * -1 restores the default (0, or the autotuner's choice, which times both).
  * Errors: TQP_ERR_INVALID_ARG. */
 TQP_API tqp_status tqp_ctx_set_variant(tqp_ctx* ctx, int32_t variant);
+
+/* Run-time specialisation (a query-compiler step beside the paper's
+ * compilation of queries into tensor programs, Section 4): the few-groups
+ * aggregate of tqp_groupby_agg (sums and counts) is compiled with NVRTC for
+ * the call's shape -- column types of its conditions, keys and sum factors,
+ * the factors' affine forms -- so that the kernel's per-row dispatch on them
+ * folds into constants.  mode 0: never; 1 (default): inputs of at least
+ * 16,777,216 rows; 2: every input.  A shape compiles once per process (a few
+ * seconds, on the calling thread, the first time) and its cubin is kept on
+ * disk (directory $TQP_JIT_CACHE, else _jit_cache/ beside libtqp.so).  Where
+ * NVRTC or the kernel sources are missing, or a compile fails, the generic
+ * kernel runs; results are identical either way.  Errors: TQP_ERR_INVALID_ARG. */
+TQP_API tqp_status tqp_ctx_set_jit(tqp_ctx* ctx, int32_t mode);
+
+/* Process-wide counters (out: 4 int64): kernels compiled, kernels loaded from
+ * the disk cache, specialised launches, failed compiles or loads. */
+TQP_API void tqp_jit_stats(int64_t* out);
+
+/* Checks that run-time specialisation works on this machine without a GPU:
+ * NVRTC and the kernel sources are found and a sample shape compiles (or is
+ * in the disk cache).  TQP_OK, else TQP_ERR_UNSUPPORTED with the reason (and
+ * the compiler log) in tqp_last_error(). */
+TQP_API tqp_status tqp_jit_probe(void);
 
 /* Autotuning: with it on, the first call of each shape class (operator, log2
  * of the row count, bytes per row it scans, output kinds) times every

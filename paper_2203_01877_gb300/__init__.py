@@ -94,6 +94,9 @@ _SIGS = {
     "tqp_ctx_arena_bytes": (C.c_size_t, [_P]),
     "tqp_ctx_set_tuning": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32]),
     "tqp_ctx_set_variant": (C.c_int, [_P, C.c_int32]),
+    "tqp_ctx_set_jit": (C.c_int, [_P, C.c_int32]),
+    "tqp_jit_stats": (None, [C.POINTER(C.c_int64)]),
+    "tqp_jit_probe": (C.c_int, []),
     "tqp_last_error": (C.c_char_p, []),
     "tqp_status_string": (C.c_char_p, [C.c_int]),
     "tqp_version": (C.c_int, []),
@@ -292,6 +295,18 @@ def make_aggs(aggs):
     return arr
 
 
+def tqp_jit_stats() -> dict:
+    """Process-wide run-time specialisation counters."""
+    out = (C.c_int64 * 4)()
+    lib().tqp_jit_stats(out)
+    return {"compiled": out[0], "from_disk": out[1], "launches": out[2], "failed": out[3]}
+
+
+def tqp_jit_probe() -> None:
+    """Raise TqpError unless NVRTC and the kernel sources are found and a sample shape compiles."""
+    _check(lib().tqp_jit_probe())
+
+
 class Context:
     """A libtqp context; the scratch arena is a torch CUDA allocation."""
 
@@ -317,6 +332,11 @@ class Context:
         """Force the algorithm of two-algorithm operators (grouped join plans: 0 radix-partitioned, 1 fused
         probe); -1 restores the default."""
         _check(lib().tqp_ctx_set_variant(self.h, int(variant)))
+
+    def set_jit(self, mode: int = 1):
+        """Run-time specialisation of the few-groups aggregate: 0 off, 1 inputs of 16M rows or more
+        (default), 2 always."""
+        _check(lib().tqp_ctx_set_jit(self.h, int(mode)))
 
     def set_autotune(self, enable: bool = True):
         _check(lib().tqp_ctx_set_autotune(self.h, int(bool(enable))))

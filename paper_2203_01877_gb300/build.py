@@ -53,7 +53,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     nv = nvcc()
     os.makedirs(BUILD, exist_ok=True)
     common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2,-fvisibility=hidden", "-I", INCLUDE,
-                     "--expt-relaxed-constexpr", "-Xptxas", "-warn-spills"]
+                     "--expt-relaxed-constexpr", "-Xptxas", "-warn-spills", f'-DTQP_CUDA_LIBDIR="{_cuda_lib_dir(nv)}"']
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
@@ -71,7 +71,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     tmp = LIB + f".{os.getpid()}.tmp"
     libdir = _cuda_lib_dir(nv)
     cmd = [nv, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
-           "-Xlinker", f"-rpath,{libdir}", "-L", libdir, "-lpthread"]
+           "-Xlinker", f"-rpath,{libdir}", "-L", libdir, "-lpthread", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -8,9 +8,27 @@
 //  * packed group keys and integer hashing.
 #pragma once
 
+#ifdef __CUDACC_RTC__
+// Runtime compilation of query-specialised kernels (jit.cu): the fixed-width
+// types and limits without the host headers.
+typedef signed char int8_t;
+typedef unsigned char uint8_t;
+typedef short int16_t;
+typedef unsigned short uint16_t;
+typedef int int32_t;
+typedef unsigned int uint32_t;
+typedef long long int64_t;
+typedef unsigned long long uint64_t;
+typedef unsigned long long uintptr_t;
+typedef unsigned long size_t;
+#define INT_MAX 2147483647
+#define INT_MIN (-INT_MAX - 1)
+#define LLONG_MIN (-9223372036854775807LL - 1)
+#else
 #include <climits>
 #include <cstdint>
 #include <cuda_runtime.h>
+#endif
 
 #include "../../include/tqp.h"
 

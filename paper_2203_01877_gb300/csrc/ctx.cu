@@ -511,6 +511,7 @@ tqp_status tqp_ctx_create(int device, void* d_arena, size_t arena_bytes, tqp_ctx
     ctx->top = arena_bytes;
     ctx->force_variant = -1;
     ctx->wait_cap = kDefaultWaitCap;
+    ctx->jit = 1;
     if (d_arena) {
         ctx->arena = static_cast<unsigned char*>(d_arena);
         ctx->owns_arena = false;

@@ -466,6 +466,9 @@ tqp_status launch_groupby(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* pred
         const void* kern = A.S.minmax ? reinterpret_cast<const void*>(k_groupby_direct_mm)
                                       : reinterpret_cast<const void*>(k_groupby_direct);
         TQP_TRY(allow_smem(ctx, kern, A.S.minmax ? attr_mm : attr_done));
+        // large inputs: the kernel compiled for this query's shape (same arguments and results)
+        const void* jk = !A.S.minmax && jit_wanted(ctx, t->num_rows) ? jit_group_direct(ctx, D) : nullptr;
+        if (jk) kern = jk;
         int occ = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kDirThreads, kDirSmemBytes) != cudaSuccess ||
             occ < 1)
@@ -488,12 +491,16 @@ tqp_status launch_groupby(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* pred
         }
         k_groupby_dprep<<<D.ngc > 0 ? nparts : 1, kDirThreads, 0, stream>>>(D, kpart);
         TQP_CUDA(cudaGetLastError());
-        if (A.S.minmax)
-            k_groupby_direct_mm<<<static_cast<unsigned>(std::max<long long>(blocks, 1)), kDirThreads, kDirSmemBytes,
-                                  stream>>>(D);
-        else
-            k_groupby_direct<<<static_cast<unsigned>(std::max<long long>(blocks, 1)), kDirThreads, kDirSmemBytes,
-                               stream>>>(D);
+        const unsigned grid = static_cast<unsigned>(std::max<long long>(blocks, 1));
+        if (jk) {
+            void* args[] = {&D};
+            TQP_CUDA(cudaLaunchKernel(jk, dim3(grid), dim3(kDirThreads), args, kDirSmemBytes, stream));
+            jit_count_launch();
+        } else if (A.S.minmax) {
+            k_groupby_direct_mm<<<grid, kDirThreads, kDirSmemBytes, stream>>>(D);
+        } else {
+            k_groupby_direct<<<grid, kDirThreads, kDirSmemBytes, stream>>>(D);
+        }
         TQP_CUDA(cudaGetLastError());
         if (topk > 0) return group_topk(ctx, A.S, O, topk, topk_agg, d_total_groups, stream);
         return TQP_OK;

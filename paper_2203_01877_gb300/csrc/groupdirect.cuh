@@ -115,6 +115,28 @@ struct GroupDirectArgs {
     GroupOut O;
 };
 
+// Shape of the kernel's query.  In the generic kernel every member returns -1
+// (decided at run time from the arguments: the column types, the expression
+// kinds, the counts); a kernel compiled for one query shape at run time
+// (jit.cu) returns that shape's values, so the per-step dispatch on them
+// folds away.  Factor i is factor i % 2 of sum i / 2.
+struct DirAnySpec {
+    static constexpr __device__ int ncond() { return -1; }
+    static constexpr __device__ int cond_type(int) { return -1; }
+    static constexpr __device__ int ngc() { return -1; }
+    static constexpr __device__ int key_type(int) { return -1; }
+    static constexpr __device__ int nsum() { return -1; }
+    static constexpr __device__ int fac_type(int) { return -1; }
+    static constexpr __device__ int fac_kind(int) { return -1; }
+    // an earlier factor reading the same column (its values are reused), or -1
+    static constexpr __device__ int fac_same(int) { return -1; }
+    // 1: sum a multiplies by its second factor; 0: that factor is the constant 1
+    static constexpr __device__ int mul(int) { return -1; }
+};
+
+// The shape's value where it fixes one (s >= 0), else the run-time one.
+__device__ __forceinline__ constexpr int sp_or(int s, int r) { return s >= 0 ? s : r; }
+
 // ---- asynchronous copies into the warp slot ----
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
@@ -181,6 +203,47 @@ __device__ __forceinline__ void dir_load4(const GroupDirectArgs& A, const unsign
 #pragma unroll
         for (int j = 0; j < 4; ++j) x[j] = 4 * q + j < n ? ldg_typed(p, type, 4 * q + j) : 0;
     }
+}
+
+// x <- the factor's affine form of the column values already in x.
+__device__ __forceinline__ void dir_apply_kind(int kind, const DirFactor& f, int64_t (&x)[4]) {
+    if (kind == kFacPlain) return;
+    const uint64_t b = static_cast<uint64_t>(f.b);
+    if (kind == kFacAdd) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) x[j] = static_cast<int64_t>(static_cast<uint64_t>(x[j]) + b);
+    } else if (kind == kFacRsub) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) x[j] = static_cast<int64_t>(b - static_cast<uint64_t>(x[j]));
+    } else {
+        const uint64_t a = static_cast<uint64_t>(f.a);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) x[j] = static_cast<int64_t>(static_cast<uint64_t>(x[j]) * a + b);
+    }
+}
+
+// Factor i (of sum i / 2) for the step's rows; raw[i] keeps the column values
+// for a later factor of the same column (SP::fac_same).
+template <bool kSlot, class SP>
+__device__ __forceinline__ void dir_factor_sp(const GroupDirectArgs& A, const unsigned char* slot, int i, long long q,
+                                              int lane, int64_t (&raw)[2 * kDirSums][4], int64_t (&x)[4]) {
+    const DirFactor& f = A.f[i / 2][i % 2];
+    const int kind = sp_or(SP::fac_kind(i), f.kind);
+    if (kind == kFacConst) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) x[j] = f.b;
+        return;
+    }
+    const int same = SP::fac_same(i);
+    if (same >= 0) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) raw[i][j] = raw[same][j];
+    } else {
+        dir_load4<kSlot>(A, slot, f.soff, f.p, sp_or(SP::fac_type(i), f.type), q, lane, raw[i]);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) x[j] = raw[i][j];
+    dir_apply_kind(kind, f, x);
 }
 
 template <bool kSlot>
@@ -417,7 +480,7 @@ __device__ __forceinline__ bool dir_lane_step(const GroupDirectArgs& A, unsigned
 // One warp step: the quad q of every lane.  kSlot: every lane's quad holds
 // four rows of the table and sits in the warp slot; otherwise quads at or
 // past the end hold none and are read from global memory.
-template <bool kSlot, bool kDense, bool kMM>
+template <bool kSlot, bool kDense, bool kMM, class SP>
 __device__ __forceinline__ void dir_step(const GroupDirectArgs& A, const DirDense& Dn, unsigned long long* area,
                                          unsigned char* slot, uint64_t (&dk)[kDirSlots], int& nused, long long q,
                                          int lane, long long next = -1) {
@@ -433,14 +496,16 @@ __device__ __forceinline__ void dir_step(const GroupDirectArgs& A, const DirDens
 #pragma unroll
             for (int j = 0; j < 4; ++j) ok |= static_cast<uint32_t>(4 * q + j < n) << j;
     }
+    const int ncond = sp_or(SP::ncond(), A.ncond);
 #pragma unroll
     for (int c = 0; c < kDirConds; ++c) {
-        if (c < A.ncond) {
+        if (c < ncond) {
             const DirCond& cd = A.cond[c];
+            const int ctype = sp_or(SP::cond_type(c), cd.type);
             int64_t x[4];
-            dir_load4<kSlot>(A, slot, cd.soff, cd.p, cd.type, qq, lane, x);
+            dir_load4<kSlot>(A, slot, cd.soff, cd.p, ctype, qq, lane, x);
             uint32_t m = 0;
-            if (cd.type == TQP_I64) {
+            if (ctype == TQP_I64) {
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
                     m |= static_cast<uint32_t>(static_cast<uint64_t>(x[j]) - static_cast<uint64_t>(cd.lo) <= cd.span) << j;
@@ -461,11 +526,12 @@ __device__ __forceinline__ void dir_step(const GroupDirectArgs& A, const DirDens
     }
     uint64_t key[4] = {0, 0, 0, 0};
     int id[4] = {0, 0, 0, 0};
+    const int ngc = sp_or(SP::ngc(), A.ngc);
 #pragma unroll
     for (int i = 0; i < kDirKeys; ++i) {
-        if (i < A.ngc) {
+        if (i < ngc) {
             int64_t x[4];
-            dir_load4<kSlot>(A, slot, A.key[i].soff, A.key[i].p, A.key[i].type, qq, lane, x);
+            dir_load4<kSlot>(A, slot, A.key[i].soff, A.key[i].p, sp_or(SP::key_type(i), A.key[i].type), qq, lane, x);
             const int b = S.key_bits[i];
             if constexpr (kDense) {  // mixed-radix slot index (every key lies in its column's range)
                 const long long lo = Dn.kmin[i];
@@ -488,13 +554,16 @@ __device__ __forceinline__ void dir_step(const GroupDirectArgs& A, const DirDens
         }
     }
     int64_t val[kDirSums][4];
+    int64_t raw[2 * kDirSums][4];
+    const int nsum = sp_or(SP::nsum(), A.nsum);
 #pragma unroll
     for (int a = 0; a < kDirSums; ++a) {
-        if (a < A.nsum) {
-            dir_factor<kSlot>(A, slot, A.f[a][0], qq, lane, val[a]);
-            if (A.f[a][1].kind != kFacConst || A.f[a][1].b != 1) {
+        if (a < nsum) {
+            dir_factor_sp<kSlot, SP>(A, slot, 2 * a, qq, lane, raw, val[a]);
+            const int mul = SP::mul(a);
+            if (mul == 1 || (mul < 0 && (A.f[a][1].kind != kFacConst || A.f[a][1].b != 1))) {
                 int64_t y[4];
-                dir_factor<kSlot>(A, slot, A.f[a][1], qq, lane, y);
+                dir_factor_sp<kSlot, SP>(A, slot, 2 * a + 1, qq, lane, raw, y);
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
                     val[a][j] = static_cast<int64_t>(static_cast<uint64_t>(val[a][j]) * static_cast<uint64_t>(y[j]));
@@ -508,7 +577,7 @@ __device__ __forceinline__ void dir_step(const GroupDirectArgs& A, const DirDens
 #pragma unroll
         for (int a = 0; a < kDirSums; ++a) {
             const int kind = acc_kind_of(S, a + 1);
-            if (a < A.nsum && kind != kAccSum)
+            if (a < nsum && kind != kAccSum)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) val[a][j] = static_cast<int64_t>(acc_encode(kind, val[a][j]));
         }
@@ -594,7 +663,7 @@ __device__ __forceinline__ void dir_dense_setup(const GroupDirectArgs& A, DirDen
 
 // The warp's grid-stride loop: 32 quads per step; a step whose quads all lie
 // within the table is fetched into the warp slot one step ahead.
-template <bool kDense, bool kMM>
+template <bool kDense, bool kMM, class SP>
 __device__ __forceinline__ void dir_loop(const GroupDirectArgs& A, const DirDense& Dn, unsigned long long* area,
                                          unsigned char* slot, int lane, int w, long long vb, long long vg) {
     uint64_t dk[kDirSlots];
@@ -614,10 +683,10 @@ __device__ __forceinline__ void dir_loop(const GroupDirectArgs& A, const DirDens
             cp_async_wait_all();
             __syncwarp();
             // dir_step moves the step's values to registers, then refills the slot
-            dir_step<true, kDense, kMM>(A, Dn, area, slot, dk, nused, base + lane, lane, nhave ? next + lane : -1);
+            dir_step<true, kDense, kMM, SP>(A, Dn, area, slot, dk, nused, base + lane, lane, nhave ? next + lane : -1);
             have = nhave;
         } else {
-            dir_step<false, kDense, kMM>(A, Dn, area, slot, dk, nused, base + lane, lane);
+            dir_step<false, kDense, kMM, SP>(A, Dn, area, slot, dk, nused, base + lane, lane);
         }
     }
     if constexpr (!kDense) dir_flush<kMM>(A, area, dk, nused, lane);  // dense: the CTA flushes once
@@ -625,7 +694,7 @@ __device__ __forceinline__ void dir_loop(const GroupDirectArgs& A, const DirDens
 
 // One CTA of the direct group-by: block vb of vg blocks working on this table
 // (kMM: the kernel for tables with MIN/MAX accumulators).
-template <bool kMM>
+template <bool kMM, class SP = DirAnySpec>
 __device__ __forceinline__ void group_direct_block(const GroupDirectArgs& A, unsigned char* smem, long long vb,
                                                    long long vg) {
     const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
@@ -636,11 +705,11 @@ __device__ __forceinline__ void group_direct_block(const GroupDirectArgs& A, uns
     for (int i = lane; i < kDirWarpWords; i += 32) area[i] = 0;
     __syncthreads();
     if (Dn->dense) {
-        dir_loop<true, kMM>(A, *Dn, area, slot, lane, w, vb, vg);
+        dir_loop<true, kMM, SP>(A, *Dn, area, slot, lane, w, vb, vg);
         __syncthreads();
         dir_flush_dense_cta<kMM>(A, *Dn, reinterpret_cast<unsigned long long*>(smem), lane, w);
     } else {
-        dir_loop<false, kMM>(A, *Dn, area, slot, lane, w, vb, vg);
+        dir_loop<false, kMM, SP>(A, *Dn, area, slot, lane, w, vb, vg);
     }
     if (!A.fin) return;
     // the last CTA to finish finalizes the table (every CTA's adds are

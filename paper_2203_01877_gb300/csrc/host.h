@@ -60,6 +60,7 @@ struct tqp_ctx {
     tqp_tuning forced;     // tile_rows == 0: no override
     int force_variant;     // >= 0: algorithm variant forced by tqp_ctx_set_variant
     tqp::Tuner* tuner;     // autotuner state (owned by the context; shared by sub-contexts)
+    int jit;               // run-time specialisation: 0 off, 1 inputs of kJitMinRows or more, 2 always
     char cur_key[96];      // shape class of the running call ("" outside tuned calls)
 };
 
@@ -208,6 +209,15 @@ tqp_status str_prepass(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* preds, 
 // Columns read by arithmetic, keys or comparisons must be numeric (a string
 // column feeds IN / LIKE predicates only).
 tqp_status check_numeric_cols(const tqp_table* t, const std::vector<int>& cols, const char* what);
+
+// Run-time specialisation (jit.cu): whether a call on `rows` rows uses it, and
+// the few-groups aggregate compiled for D's shape (sums only), or nullptr when
+// it cannot be had (the generic kernel then runs).
+constexpr long long kJitMinRows = 16LL << 20;
+struct GroupDirectArgs;
+bool jit_wanted(const tqp_ctx* ctx, long long rows);
+const void* jit_group_direct(const tqp_ctx* ctx, const GroupDirectArgs& D);
+void jit_count_launch();
 
 // The single-query filter scan (tqp_filter's body, in the caller's arena).
 tqp_status launch_filter(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* preds, int32_t npreds,

@@ -394,6 +394,11 @@ tqp_status launch_groupby(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* pred
                           int64_t* d_keys, int64_t* d_ivals, double* d_fvals, int64_t capacity_groups,
                           int64_t* d_num_groups, cudaStream_t stream, long long max_groups, int topk, int topk_agg,
                           int64_t* d_total_groups) {
+    // the top-k arguments first: a call rejected for them launches nothing
+    if (topk > 0 && topk > kTopBlock / 2)
+        return fail(TQP_ERR_UNSUPPORTED, "top-k needs 1 <= k <= %d", kTopBlock / 2);
+    if (topk > 0 && (topk_agg < 0 || topk_agg >= naggs))
+        return fail(TQP_ERR_INVALID_ARG, "topk_agg %d out of range", topk_agg);
     // IN / LIKE / NOT LIKE: one pre-pass writes a pass column that the scan then filters on
     StrLowered SL;
     TQP_TRY(str_prepass(ctx, t, preds, npreds, stream, &SL));

@@ -295,9 +295,18 @@ def secondary_workloads(tqp, torch, dev, local, reps, cpu_seconds=0.0):
     def q1():
         tqp.tqp_groupby_agg(ctx, table, [(0, "le", 2450)], [1, 2], aggs, keys, iv, fv, 64, ng, stream)
 
+    # the generic kernel, then the kernel compiled for this query's shape (a prepared query: the
+    # compile, once per shape, happens in the first untimed call)
+    ctx.set_jit(0)
+    generic = {"ms_l2_resident": _time_launches(torch, q1, reps),
+               "ms_after_l2_flush": _time_launches(torch, q1, max(5, reps // 4), flush=flush),
+               "ms_back_to_back": _time_burst(torch, q1, 50, stream=stream)}
+    ctx.set_jit(2)
+    jit0 = tqp.tqp_jit_stats()["launches"]
     hot = _time_launches(torch, q1, reps)
     cold = _time_launches(torch, q1, max(5, reps // 4), flush=flush)
     burst = _time_burst(torch, q1, 50, stream=stream)
+    specialised = tqp.tqp_jit_stats()["launches"] > jit0
     ctx.check(stream)
     out["groupby_1M_6groups"] = {
         "workload": "1M rows; date<=2450; GROUP BY (flag u8, status u8): SUM(qty), SUM(price), "
@@ -307,7 +316,9 @@ def secondary_workloads(tqp, torch, dev, local, reps, cpu_seconds=0.0):
         "timing": "ms_l2_resident / ms_after_l2_flush: one call between synchronisations (host work included); "
                   "ms_back_to_back: 50 calls enqueued back to back (host work overlapped, table L2-resident)",
         "algorithmic_bytes": n * 26, "achieved_gbs_after_flush": n * 26 / (cold / 1e3) / 1e9,
-        "groups": int(ng.item())}
+        "groups": int(ng.item()),
+        "kernel": "compiled for the query's shape at run time" if specialised else "generic",
+        "generic_kernel": generic}
     if cpu_seconds > 0:
         spec = dict(fact=[t[k] for k in ("date", "flag", "status", "quantity", "price", "discount")],
                     preds=[(0, "le", 2450)], group_cols=[1, 2], aggs=aggs, want_row_ids=False)

@@ -214,10 +214,12 @@ TQP_API tqp_status tqp_ctx_set_variant(tqp_ctx* ctx, int32_t variant);
  * aggregate of tqp_groupby_agg (sums and counts) is compiled with NVRTC for
  * the call's shape -- column types of its conditions, keys and sum factors,
  * the factors' affine forms -- so that the kernel's per-row dispatch on them
- * folds into constants.  mode 0: never; 1 (default): inputs of at least
- * 16,777,216 rows; 2: every input.  A shape compiles once per process (a few
- * seconds, on the calling thread, the first time) and its cubin is kept on
- * disk (directory $TQP_JIT_CACHE, else _jit_cache/ beside libtqp.so).  Where
+ * folds into constants.  mode 0: never; 1 (default): a shape is compiled
+ * for an input of at least 16,777,216 rows, and once compiled (or found in the
+ * disk cache) it serves inputs of any size; 2: compiled for every input.  A
+ * shape compiles once per process (a few seconds, on the calling thread) and
+ * its cubin is kept on disk (directory $TQP_JIT_CACHE, else _jit_cache/ beside
+ * libtqp.so).  Where
  * NVRTC or the kernel sources are missing, or a compile fails, the generic
  * kernel runs; results are identical either way.  Errors: TQP_ERR_INVALID_ARG. */
 TQP_API tqp_status tqp_ctx_set_jit(tqp_ctx* ctx, int32_t mode);

@@ -472,7 +472,7 @@ tqp_status launch_groupby(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* pred
                                       : reinterpret_cast<const void*>(k_groupby_direct);
         TQP_TRY(allow_smem(ctx, kern, A.S.minmax ? attr_mm : attr_done));
         // large inputs: the kernel compiled for this query's shape (same arguments and results)
-        const void* jk = !A.S.minmax && jit_wanted(ctx, t->num_rows) ? jit_group_direct(ctx, D) : nullptr;
+        const void* jk = A.S.minmax ? nullptr : jit_group_direct(ctx, D, t->num_rows);
         if (jk) kern = jk;
         int occ = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kDirThreads, kDirSmemBytes) != cudaSuccess ||

@@ -631,34 +631,50 @@ __device__ __forceinline__ void dir_dense_init(const GroupDirectArgs& A, const u
     Dn->dense = 1;
 }
 
-// Warp 0 of a CTA: the key bounds (reduced from the range blocks' records if
-// needed), then the dense-id parameters.
-__device__ __forceinline__ void dir_dense_setup(const GroupDirectArgs& A, DirDense* Dn, int lane) {
-    unsigned long long ea[kDirKeys], eb[kDirKeys];
+// Every thread of a CTA (kDirThreads): the key bounds, reduced from the range
+// blocks' records (one record per thread: a single round of loads), then
+// thread 0 derives the dense-id parameters.
+__device__ __forceinline__ void dir_dense_setup(const GroupDirectArgs& A, DirDense* Dn, int lane, int w) {
+    __shared__ unsigned long long red[kDirThreads / 32][2 * kDirKeys];
+    unsigned long long v[2 * kDirKeys];
+#pragma unroll
+    for (int k = 0; k < 2 * kDirKeys; ++k) v[k] = 0;
     const bool have = A.kmeta || A.kpart;
+    if (A.kpart) {
+        for (int p = threadIdx.x; p < A.nparts; p += kDirThreads)
 #pragma unroll
-    for (int i = 0; i < kDirKeys; ++i) {
-        ea[i] = eb[i] = 0;
-        if (i < A.ngc) {
-            if (A.kpart) {
-                for (int p = lane; p < A.nparts; p += 32) {
-                    const unsigned long long a = A.kpart[p * 2 * kDirKeys + 2 * i], b = A.kpart[p * 2 * kDirKeys + 2 * i + 1];
-                    ea[i] = a > ea[i] ? a : ea[i];
-                    eb[i] = b > eb[i] ? b : eb[i];
+            for (int k = 0; k < 2 * kDirKeys; ++k)
+                if (k < 2 * A.ngc) {
+                    const unsigned long long x = A.kpart[p * 2 * kDirKeys + k];
+                    v[k] = x > v[k] ? x : v[k];
                 }
-            } else if (A.kmeta && lane == 0) {
-                ea[i] = A.kmeta[2 * i];
-                eb[i] = A.kmeta[2 * i + 1];
-            }
+    } else if (A.kmeta && threadIdx.x == 0) {
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const unsigned long long a = __shfl_xor_sync(0xffffffffu, ea[i], o), b = __shfl_xor_sync(0xffffffffu, eb[i], o);
-                ea[i] = a > ea[i] ? a : ea[i];
-                eb[i] = b > eb[i] ? b : eb[i];
+        for (int k = 0; k < 2 * kDirKeys; ++k)
+            if (k < 2 * A.ngc) v[k] = A.kmeta[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 2 * kDirKeys; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long x = __shfl_xor_sync(0xffffffffu, v[k], o);
+            v[k] = x > v[k] ? x : v[k];
+        }
+        if (lane == 0) red[w][k] = v[k];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long ea[kDirKeys], eb[kDirKeys];
+#pragma unroll
+        for (int i = 0; i < kDirKeys; ++i) {
+            ea[i] = eb[i] = 0;
+            for (int u = 0; u < kDirThreads / 32; ++u) {
+                ea[i] = red[u][2 * i] > ea[i] ? red[u][2 * i] : ea[i];
+                eb[i] = red[u][2 * i + 1] > eb[i] ? red[u][2 * i + 1] : eb[i];
             }
         }
+        dir_dense_init(A, ea, eb, have, Dn);
     }
-    if (lane == 0) dir_dense_init(A, ea, eb, have, Dn);
 }
 
 // The warp's grid-stride loop: 32 quads per step; a step whose quads all lie
@@ -701,8 +717,8 @@ __device__ __forceinline__ void group_direct_block(const GroupDirectArgs& A, uns
     unsigned long long* area = reinterpret_cast<unsigned long long*>(smem) + w * kDirWarpWords;
     unsigned char* slot = smem + kDirTableBytes + w * kDirSlotBytes;
     DirDense* Dn = reinterpret_cast<DirDense*>(smem + kDirDenseOff);
-    if (w == 0) dir_dense_setup(A, Dn, lane);
     for (int i = lane; i < kDirWarpWords; i += 32) area[i] = 0;
+    dir_dense_setup(A, Dn, lane, w);
     __syncthreads();
     if (Dn->dense) {
         dir_loop<true, kMM, SP>(A, *Dn, area, slot, lane, w, vb, vg);

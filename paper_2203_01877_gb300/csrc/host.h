@@ -210,13 +210,13 @@ tqp_status str_prepass(tqp_ctx* ctx, const tqp_table* t, const tqp_pred* preds, 
 // column feeds IN / LIKE predicates only).
 tqp_status check_numeric_cols(const tqp_table* t, const std::vector<int>& cols, const char* what);
 
-// Run-time specialisation (jit.cu): whether a call on `rows` rows uses it, and
-// the few-groups aggregate compiled for D's shape (sums only), or nullptr when
-// it cannot be had (the generic kernel then runs).
+// Run-time specialisation (jit.cu): the few-groups aggregate compiled for D's
+// shape (sums only), or nullptr (the generic kernel then runs).  A shape is
+// compiled for calls on at least kJitMinRows rows (every call in mode 2);
+// once compiled, or found in the disk cache, it serves calls of any size.
 constexpr long long kJitMinRows = 16LL << 20;
 struct GroupDirectArgs;
-bool jit_wanted(const tqp_ctx* ctx, long long rows);
-const void* jit_group_direct(const tqp_ctx* ctx, const GroupDirectArgs& D);
+const void* jit_group_direct(const tqp_ctx* ctx, const GroupDirectArgs& D, long long rows);
 void jit_count_launch();
 
 // The single-query filter scan (tqp_filter's body, in the caller's arena).

@@ -99,7 +99,8 @@ const char* const kJitHeaders[] = {"csrc/common.cuh", "csrc/engine.cuh", "csrc/g
                                    "csrc/groupdirect.cuh", "../include/tqp.h"};
 
 struct JitEntry {
-    bool ok = false;
+    int state = 0;              // 0 not compiled (yet), 1 loaded, 2 cannot be had
+    bool disk_checked = false;  // the disk cache was looked at
     cudaLibrary_t lib = nullptr;
     cudaKernel_t kernel = nullptr;
     uint64_t attr_devices = 0;  // devices whose shared-memory attribute is set
@@ -145,8 +146,10 @@ std::string cache_dir(const std::string& pkg) {
     return env && *env ? std::string(env) : pkg + "/_jit_cache";
 }
 
-// The cubin of `src`: from the disk cache, else compiled (and stored there).
-tqp_status jit_cubin(const std::string& src, std::string* cubin) {
+// The cubin of `src`: from the disk cache, else (when allowed) compiled and
+// stored there.  TQP_OK with the cubin; TQP_ERR_CAPACITY: not on disk and
+// compiling not allowed; other statuses: the shape cannot be compiled here.
+tqp_status jit_cubin(const std::string& src, std::string* cubin, bool allow_compile) {
     const std::string pkg = package_dir();
     if (pkg.empty()) return fail(TQP_ERR_UNSUPPORTED, "run-time specialisation: libtqp.so's directory not found");
     const std::vector<std::string> opts = {"--gpu-architecture=sm_103a", "-std=c++17", "-default-device",
@@ -167,6 +170,7 @@ tqp_status jit_cubin(const std::string& src, std::string* cubin) {
         ++g_stats[1];
         return TQP_OK;
     }
+    if (!allow_compile) return TQP_ERR_CAPACITY;
     std::string log;
     if (!nvrtc_compile(src, opts, cubin, &log)) {
         ++g_stats[3];
@@ -194,31 +198,61 @@ std::string spec_val(const char* name, int v) {
     return std::string("    static constexpr __device__ int ") + name + "() { return " + std::to_string(v) + "; }\n";
 }
 
-// The kernel source specialised to D's shape (the sums-only kernel).
-std::string dir_spec_source(const GroupDirectArgs& D) {
+// The shape of D: what the specialised kernel fixes at compile time.
+struct DirShape {
     std::vector<int> ct, kt, ft, fk, fs, mul;
-    for (int c = 0; c < D.ncond; ++c) ct.push_back(D.cond[c].type);
-    for (int i = 0; i < D.ngc; ++i) kt.push_back(D.key[i].type);
-    for (int a = 0; a < D.nsum; ++a)
-        mul.push_back(D.f[a][1].kind != kFacConst || D.f[a][1].b != 1 ? 1 : 0);
+    int ncond = 0, ngc = 0, nsum = 0;
+};
+
+DirShape shape_of(const GroupDirectArgs& D) {
+    DirShape h;
+    h.ncond = D.ncond;
+    h.ngc = D.ngc;
+    h.nsum = D.nsum;
+    for (int c = 0; c < D.ncond; ++c) h.ct.push_back(D.cond[c].type);
+    for (int i = 0; i < D.ngc; ++i) h.kt.push_back(D.key[i].type);
+    for (int a = 0; a < D.nsum; ++a) h.mul.push_back(D.f[a][1].kind != kFacConst || D.f[a][1].b != 1 ? 1 : 0);
     for (int i = 0; i < 2 * D.nsum; ++i) {
         const DirFactor& f = D.f[i / 2][i % 2];
-        const bool used = i % 2 == 0 || mul[i / 2];
-        ft.push_back(f.type);
-        fk.push_back(used ? f.kind : kFacConst);
+        const bool used = i % 2 == 0 || h.mul[i / 2];
+        h.ft.push_back(f.type);
+        h.fk.push_back(used ? f.kind : kFacConst);
         int same = -1;  // an earlier evaluated factor of the same column
         if (used && f.kind != kFacConst)
             for (int j = 0; j < i && same < 0; ++j) {
                 const DirFactor& g = D.f[j / 2][j % 2];
-                const bool gused = j % 2 == 0 || mul[j / 2];
+                const bool gused = j % 2 == 0 || h.mul[j / 2];
                 if (gused && g.kind != kFacConst && g.p == f.p && g.type == f.type) same = j;
             }
-        fs.push_back(same);
+        h.fs.push_back(same);
     }
+    return h;
+}
+
+// The shape as a short byte string (the in-process cache key).
+std::string shape_key(const DirShape& h) {
+    std::string k;
+    auto put = [&k](int v) { k.push_back(static_cast<char>(v + 2)); };
+    put(h.ncond);
+    for (int v : h.ct) put(v);
+    put(h.ngc);
+    for (int v : h.kt) put(v);
+    put(h.nsum);
+    for (size_t i = 0; i < h.ft.size(); ++i) {
+        put(h.ft[i]);
+        put(h.fk[i]);
+        put(h.fs[i]);
+    }
+    for (int v : h.mul) put(v);
+    return k;
+}
+
+// The kernel source specialised to a shape (the sums-only kernel).
+std::string dir_spec_source(const DirShape& h) {
     std::string s = "#include \"groupdirect.cuh\"\nstruct JitSpec {\n";
-    s += spec_val("ncond", D.ncond) + spec_fn("cond_type", ct) + spec_val("ngc", D.ngc) + spec_fn("key_type", kt);
-    s += spec_val("nsum", D.nsum) + spec_fn("fac_type", ft) + spec_fn("fac_kind", fk) + spec_fn("fac_same", fs);
-    s += spec_fn("mul", mul) + "};\n";
+    s += spec_val("ncond", h.ncond) + spec_fn("cond_type", h.ct) + spec_val("ngc", h.ngc) + spec_fn("key_type", h.kt);
+    s += spec_val("nsum", h.nsum) + spec_fn("fac_type", h.ft) + spec_fn("fac_kind", h.fk) + spec_fn("fac_same", h.fs);
+    s += spec_fn("mul", h.mul) + "};\n";
     s += "extern \"C\" __global__ void __launch_bounds__(tqp::kDirThreads, tqp::kDirMinBlocks)\n"
          "tqp_group_direct_jit(const __grid_constant__ tqp::GroupDirectArgs A) {\n"
          "    extern __shared__ __align__(16) unsigned char dsm[];\n"
@@ -229,29 +263,31 @@ std::string dir_spec_source(const GroupDirectArgs& D) {
 
 }  // namespace
 
-bool jit_wanted(const tqp_ctx* ctx, long long rows) {
-    return ctx->jit == 2 || (ctx->jit == 1 && rows >= kJitMinRows);
-}
-
-const void* jit_group_direct(const tqp_ctx* ctx, const GroupDirectArgs& D) {
-    const std::string src = dir_spec_source(D);
+const void* jit_group_direct(const tqp_ctx* ctx, const GroupDirectArgs& D, long long rows) {
+    if (ctx->jit == 0) return nullptr;
+    const bool may_compile = ctx->jit == 2 || rows >= kJitMinRows;
+    const DirShape h = shape_of(D);
+    const std::string key = shape_key(h);
     std::lock_guard<std::mutex> lk(g_mu);
-    auto it = g_cache->find(src);
-    if (it == g_cache->end()) {
-        JitEntry e;
+    JitEntry& e = (*g_cache)[key];
+    if (e.state == 0 && (may_compile || !e.disk_checked)) {
         std::string cubin;
-        if (jit_cubin(src, &cubin) == TQP_OK) {
-            e.ok = cudaLibraryLoadData(&e.lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) == cudaSuccess &&
-                   cudaLibraryGetKernel(&e.kernel, e.lib, "tqp_group_direct_jit") == cudaSuccess;
-            if (!e.ok) ++g_stats[3];
+        const tqp_status st = jit_cubin(dir_spec_source(h), &cubin, may_compile);
+        e.disk_checked = true;
+        if (st == TQP_OK) {
+            const bool ok =
+                cudaLibraryLoadData(&e.lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) == cudaSuccess &&
+                cudaLibraryGetKernel(&e.kernel, e.lib, "tqp_group_direct_jit") == cudaSuccess;
+            e.state = ok ? 1 : 2;
+            if (!ok) ++g_stats[3];
+        } else if (st != TQP_ERR_CAPACITY) {
+            e.state = 2;
         }
         // a shape that cannot be specialised runs the generic kernel: not the caller's error
         (void)cudaGetLastError();
         clear_error();
-        it = g_cache->emplace(src, e).first;
     }
-    JitEntry& e = it->second;
-    if (!e.ok) return nullptr;
+    if (e.state != 1) return nullptr;
     const void* k = reinterpret_cast<const void*>(e.kernel);
     const uint64_t bit = ctx->device < 64 ? 1ULL << ctx->device : 0;
     if (!(e.attr_devices & bit)) {
@@ -304,5 +340,5 @@ tqp_status tqp_jit_probe(void) {
     }
     D.f[2][1] = DirFactor{col[2], type[2], kFacRsub, 1, 100, 0, 0};
     std::string cubin;
-    return jit_cubin(dir_spec_source(D), &cubin);
+    return jit_cubin(dir_spec_source(shape_of(D)), &cubin, true);
 }

@@ -169,6 +169,7 @@ struct FilterBody {
 // ---- group-by: warp pre-aggregation into the global table -------------------------
 
 constexpr int kWarpSlots = 32;   // groups of a warp's collective cache
+constexpr int kThrashAdds = 8;   // a cache refilled within this many adds is thrashing
 constexpr int kFastSums = 4;     // sum accumulators of the closed-form fast path
 constexpr int kLaneSlots = 8;    // groups of a warp's lane-private tables
 constexpr int kLaneAcc = 4;      // accumulators (count + sums) the lane-private tables hold
@@ -224,7 +225,9 @@ struct GroupBody {
     uint32_t* wocc;              // warp mode: occupancy bits of the cache slots
     uint64_t dk[kLaneSlots];     // lane mode: the warp's keys (the same in every lane)
     int nused = 0;               // lane mode: keys in dk (warp-uniform)
-    int mode = 0;                // 0 lane, 1 warp (warp-uniform)
+    int mode = 0;                // 0 lane, 1 warp, 2 direct (warp-uniform)
+    int since = 0;               // warp mode: adds since the cache was last flushed
+    int thrash = 0;              // warp mode: flushes that came within kThrashAdds adds
     bool kw32 = false;           // packed keys fit 32 bits
     // Full-tile fast path operands in registers (the argument block is in
     // shared memory, and the accumulator stores would force it to be re-read).
@@ -460,6 +463,8 @@ struct GroupBody {
             __syncwarp();
             if (__any_sync(0xffffffffu, need && s < 0 && tries >= kWarpSlots)) {
                 flush_cache(lane);  // all leaders start over in an empty cache
+                thrash += since < kThrashAdds ? 1 : 0;
+                since = 0;
                 s = -1;
                 tries = 0;
                 h = h0;
@@ -488,10 +493,36 @@ struct GroupBody {
         }
     }
 
+    // Direct mode (keys too many for the cache: it refilled within a few adds,
+    // twice): the rows of one key in the warp are summed, and their leader
+    // adds the sums into the global table.
+    template <int NS>
+    __device__ __forceinline__ void direct_add(bool act, uint64_t key, const int64_t (&val)[NS], int nsum, int lane) {
+        const uint32_t actm = __ballot_sync(0xffffffffu, act);
+        if (!act) return;
+        const uint32_t peers = __match_any_sync(actm, key);
+        const bool lead = lane == __ffs(peers) - 1;
+        const GroupSpec& S = A.S;
+        const long long g = lead ? gtab_slot(S, key, A.ctl.err) : -1;
+        unsigned long long* acc = S.acc + (g < 0 ? 0 : g) * S.nacc;
+        if (g >= 0) red_add_u64(acc, static_cast<unsigned long long>(__popc(peers)));
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+            if (i < nsum) {
+                const long long x = group_sum_i64(peers, val[i]);
+                if (g >= 0 && x) red_add_u64(acc + 1 + i, static_cast<unsigned long long>(x));
+            }
+        }
+    }
+
     // One row per lane (act: the row passed) in the warp's current mode.
     template <int NS>
     __device__ __forceinline__ void add(bool act, uint64_t key, const int64_t (&val)[NS], int lane) {
         const int nsum = A.S.nacc - 1;
+        if (mode == 2) {
+            direct_add<NS>(act, key, val, nsum, lane);
+            return;
+        }
         if (mode == 0) {
             int64_t v4[kFastSums];
 #pragma unroll
@@ -501,6 +532,11 @@ struct GroupBody {
             mode = 1;
         }
         warp_add<NS>(act, key, val, nsum, lane);
+        ++since;
+        if (thrash >= 2) {  // the cache keeps refilling: direct mode for the rest of the chunk
+            flush_cache(lane);
+            mode = 2;
+        }
     }
 
     // Full tile, closed-form sums: U rows per lane, operands from registers.
@@ -593,12 +629,11 @@ struct GroupBody {
     }
 
     __device__ void chunk_end(const ScanGeom&, long long, long long, long long, int, int lane) {
-        if (mode == 0) {
-            flush_lanes(lane);
-        } else {
-            flush_cache(lane);
-            mode = A.S.nacc <= kLaneAcc ? 0 : 1;
-        }
+        if (mode == 0) flush_lanes(lane);
+        else if (mode == 1) flush_cache(lane);
+        mode = A.S.nacc <= kLaneAcc ? 0 : 1;
+        since = 0;
+        thrash = 0;
     }
 
     __device__ void finish(const ScanGeom&, int, int) {}

@@ -75,22 +75,40 @@ __device__ __forceinline__ uint64_t pack_key(const GroupSpec& S, const ScanGeom&
 __device__ __forceinline__ long long gtab_slot(const GroupSpec& S, uint64_t key, int* err) {
     if (key == kEmptyKey) return S.cap;
     unsigned long long h = mix64(key) & static_cast<unsigned long long>(S.cap - 1);
+    long long slot = -1;
+    bool inserted = false;
     for (long long i = 0; i < S.cap; ++i) {
         const unsigned long long k = *reinterpret_cast<volatile unsigned long long*>(&S.keys[h]);
-        if (k == key) return static_cast<long long>(h);
+        if (k == key) {
+            slot = static_cast<long long>(h);
+            break;
+        }
         if (k == kEmptyKey) {
             const unsigned long long prev = atomicCAS(&S.keys[h], kEmptyKey, key);
-            if (prev == kEmptyKey) {
-                if (static_cast<long long>(atomicAdd(S.ndistinct, 1ULL)) >= S.max_groups)
-                    latch_error(err, TQP_ERR_CAPACITY);
-                return static_cast<long long>(h);
+            if (prev == kEmptyKey || prev == key) {
+                slot = static_cast<long long>(h);
+                inserted = prev == kEmptyKey;
+                break;
             }
-            if (prev == key) return static_cast<long long>(h);
         }
         h = (h + 1) & static_cast<unsigned long long>(S.cap - 1);
     }
-    latch_error(err, TQP_ERR_CAPACITY);
-    return -1;
+    // new keys counted with one atomic per converged group of lanes (the
+    // counter is a single address: one add per insert serialises at L2); each
+    // inserting lane's index is the count before it, as with its own add
+    const unsigned am = __activemask();
+    const unsigned im = __ballot_sync(am, inserted);
+    if (im) {
+        const int lane = static_cast<int>(threadIdx.x % 32);
+        const int first = __ffs(im) - 1;
+        unsigned long long base = 0;
+        if (lane == first) base = atomicAdd(S.ndistinct, static_cast<unsigned long long>(__popc(im)));
+        base = __shfl_sync(am, base, first);
+        if (inserted && static_cast<long long>(base + __popc(im & ((1u << lane) - 1u))) >= S.max_groups)
+            latch_error(err, TQP_ERR_CAPACITY);
+    }
+    if (slot < 0) latch_error(err, TQP_ERR_CAPACITY);
+    return slot;
 }
 
 struct GroupOut {

@@ -494,25 +494,21 @@ struct GroupBody {
     }
 
     // Direct mode (keys too many for the cache: it refilled within a few adds,
-    // twice): the rows of one key in the warp are summed, and their leader
-    // adds the sums into the global table.
+    // twice): each row goes straight into the global table.  Rows are not
+    // summed per key within the warp first: with keys this spread few rows
+    // share one, and a reduction over lane groups with different masks
+    // proceeds one group at a time.
     template <int NS>
-    __device__ __forceinline__ void direct_add(bool act, uint64_t key, const int64_t (&val)[NS], int nsum, int lane) {
-        const uint32_t actm = __ballot_sync(0xffffffffu, act);
+    __device__ __forceinline__ void direct_add(bool act, uint64_t key, const int64_t (&val)[NS], int nsum) {
         if (!act) return;
-        const uint32_t peers = __match_any_sync(actm, key);
-        const bool lead = lane == __ffs(peers) - 1;
         const GroupSpec& S = A.S;
-        const long long g = lead ? gtab_slot(S, key, A.ctl.err) : -1;
-        unsigned long long* acc = S.acc + (g < 0 ? 0 : g) * S.nacc;
-        if (g >= 0) red_add_u64(acc, static_cast<unsigned long long>(__popc(peers)));
+        const long long g = gtab_slot(S, key, A.ctl.err);
+        if (g < 0) return;
+        unsigned long long* acc = S.acc + g * S.nacc;
+        red_add_u64(acc, 1ULL);
 #pragma unroll
-        for (int i = 0; i < NS; ++i) {
-            if (i < nsum) {
-                const long long x = group_sum_i64(peers, val[i]);
-                if (g >= 0 && x) red_add_u64(acc + 1 + i, static_cast<unsigned long long>(x));
-            }
-        }
+        for (int i = 0; i < NS; ++i)
+            if (i < nsum && val[i]) red_add_u64(acc + 1 + i, static_cast<unsigned long long>(val[i]));
     }
 
     // One row per lane (act: the row passed) in the warp's current mode.
@@ -520,7 +516,7 @@ struct GroupBody {
     __device__ __forceinline__ void add(bool act, uint64_t key, const int64_t (&val)[NS], int lane) {
         const int nsum = A.S.nacc - 1;
         if (mode == 2) {
-            direct_add<NS>(act, key, val, nsum, lane);
+            direct_add<NS>(act, key, val, nsum);
             return;
         }
         if (mode == 0) {

@@ -308,7 +308,7 @@ using namespace tqp;
 
 tqp_status tqp_ctx_set_jit(tqp_ctx* ctx, int32_t mode) {
     clear_error();
-    if (!ctx) return fail(TQP_ERR_INVALID_ARG, "ctx is NULL");
+    TQP_TRY(check_ctx(ctx));
     if (mode < 0 || mode > 2) return fail(TQP_ERR_INVALID_ARG, "jit mode must be 0, 1 or 2");
     ctx->jit = mode;
     return TQP_OK;
